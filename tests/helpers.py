@@ -1,0 +1,48 @@
+"""Small test-only helpers: Minkowski products and Lorentz transformations."""
+import numpy as np
+
+
+def mdot(a, b):
+    return a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3]
+
+
+def boost(p, beta):
+    """Pure boost of four-vectors p[..., 4 on axis 0] by velocity beta (3-vector)."""
+    b = np.asarray(beta, dtype=float)
+    b2 = b @ b
+    g = 1.0 / np.sqrt(1.0 - b2)
+    bp = b[0] * p[1] + b[1] * p[2] + b[2] * p[3]
+    out = np.empty_like(p)
+    out[0] = g * (p[0] + bp)
+    for k in range(3):
+        out[k + 1] = p[k + 1] + ((g - 1.0) * bp / b2 + g * p[0]) * b[k]
+    return out
+
+
+def rotate(p, axis, angle):
+    """Rotation of the spatial part about a unit axis (Rodrigues)."""
+    k = np.asarray(axis, dtype=float)
+    k = k / np.linalg.norm(k)
+    K = np.array([[0, -k[2], k[1]], [k[2], 0, -k[0]], [-k[1], k[0], 0]])
+    R = np.eye(3) + np.sin(angle) * K + (1 - np.cos(angle)) * K @ K
+    out = p.copy()
+    out[1:] = np.tensordot(R, p[1:], axes=(1, 0))
+    return out
+
+
+def two_body(ecm, m, cth, phi):
+    """Beams along +-z and a back-to-back final pair of mass m at angles (cth, phi):
+    exactly on shell up to one rounding, independent of any phase-space generator."""
+    n = len(cth)
+    e = ecm / 2.0
+    k = np.sqrt(e * e - m * m)
+    sth = np.sqrt(1.0 - cth ** 2)
+    mom = np.zeros((4, 4, n))
+    mom[0] = np.array([e, 0.0, 0.0, e])[:, None]
+    mom[1] = np.array([e, 0.0, 0.0, -e])[:, None]
+    d = np.stack([sth * np.cos(phi), sth * np.sin(phi), cth])
+    mom[2, 0] = e
+    mom[2, 1:] = k * d
+    mom[3, 0] = e
+    mom[3, 1:] = -k * d
+    return mom
