@@ -1,0 +1,330 @@
+"""Throughput of the matrix-element hot path on GB300 (one JSON line on stdout).
+
+A step is one pass of the whole path over one batch of seeded synthetic
+events of gg -> t t~ g g at sqrt(s) = 1500 GeV (2^20 events per GPU):
+  RAMBO on the 16 filter events -> helicity filter -> RAMBO on the batch ->
+  SIGMAKIN (mixed precision by default) -> FP64 event sum.
+The random numbers are resident in HBM before the timed region.  The
+per-step working set (random numbers 128 MiB + momenta 192 MiB + outputs) is
+larger than the 126 MB L2, so no L2 flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mine|reference]
+
+--impl reference times the FP64 CPU oracle (the reference arm of this
+benchmark) on the host cores on a bounded sample of the same workload.
+Under torchrun every rank processes its own 2^20 events (weak scaling);
+rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "gg_ttgg"
+METRIC = "matrix elements/sec on 1 GB300 (gg->ttgg), mixed-precision vs FP64 at stated rel. error"
+UNIT = "ME/s"
+FP32_LANES_PER_SM = 128
+SMS = 152
+SM_MAX_MHZ = 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--mode", default="mixed", choices=["mixed", "mixed_simt", "fp64"])
+    ap.add_argument("--nevt", type=int, default=1 << 20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    return ap.parse_args()
+
+
+def dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return rank, world, local
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def cpu_oracle_rate(nevt_sample: int, seed: int, threads: int):
+    """Oracle ME/s on the host cores for a bounded sample (RAMBO + |M|^2, FP64)."""
+    import numpy as np
+
+    import oracle
+    from paper_2106_12631_gb300 import inputs as I
+    oracle.build()
+    rnd = I.uniforms(seed, 16, nevt_sample)
+    oracle.me(4, oracle.rambo(4, rnd[:, :2], 1500.0)[0])  # colour set-up outside the timing
+    t0 = time.perf_counter()
+    mom, _ = oracle.rambo(4, rnd, 1500.0)
+    oracle.me(4, mom, nthreads=threads)
+    dt = time.perf_counter() - t0
+    return nevt_sample / dt, dt
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 CPU oracle on the host cores, bounded sample per step."""
+    if rank != 0:
+        return
+    from paper_2106_12631_gb300 import inputs as I
+    cores = os.cpu_count() or 1
+    sample = 2048
+    seed = I.seed_of(WORKLOAD)
+    for _ in range(args.warmup):
+        cpu_oracle_rate(256, seed, cores)
+    rates, times = [], []
+    for _ in range(args.steps):
+        r, dt = cpu_oracle_rate(sample, seed, cores)
+        rates.append(r)
+        times.append(dt)
+    value = sample * len(times) / sum(times)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded SplitMix64 uniforms -> RAMBO)",
+        "config": {"workload": "gg->ttgg tree-level |M|^2, RAMBO 4-body at 1500 GeV, FP64 CPU oracle",
+                   "events_per_step": sample, "nevt_full": args.nevt},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "%d events of the gg->ttgg workload per step (RAMBO + all 64 "
+                                   "helicities, explicit colour), std::thread over %d cores" % (sample, cores)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_init(args)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import numpy as np
+    import torch
+
+    from paper_2106_12631_gb300 import inputs as I
+    from paper_2106_12631_gb300 import mg
+    from paper_2106_12631_gb300.gen import procgen
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    proc, ecm, nevt = 4, 1500.0, args.nevt
+    seed = I.seed_of(WORKLOAD)
+    # inputs resident in HBM: this rank's own event range
+    rnd = torch.from_numpy(I.uniforms(seed, 16, nevt, first_event=rank * nevt)).to(dev)
+    frnd = torch.from_numpy(I.uniforms(I.filter_seed_of(WORKLOAD), 16, 16)).to(dev)
+    info = mg.process_info(proc)
+    mom = torch.empty((info["npar"], 4, nevt), dtype=torch.float64, device=dev)
+    wgt = torch.empty(nevt, dtype=torch.float64, device=dev)
+    fmom = torch.empty((info["npar"], 4, 16), dtype=torch.float64, device=dev)
+    fwgt = torch.empty(16, dtype=torch.float64, device=dev)
+    mask = torch.empty(info["nhel"], dtype=torch.int32, device=dev)
+    me = torch.empty(nevt, dtype=torch.float64, device=dev)
+    out = torch.empty(3, dtype=torch.float64, device=dev)
+    scratch = torch.empty(mg.event_sum_scratch_bytes(nevt) // 8 + 2, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    kernel_launches_per_step = 6  # rambo(filter), filter, rambo, sigmakin, event_sum x2
+
+    def step(mode, ev=None):
+        mg.rambo(proc, frnd, ecm, mom=fmom, wgt=fwgt, stream=stream)
+        mg.filter_helicities(proc, fmom, mask=mask, stream=stream)
+        mg.rambo(proc, rnd, ecm, mom=mom, wgt=wgt, stream=stream)
+        if ev is not None:
+            ev[0].record(stream)
+        mg.sigmakin(proc, mom, mask, mode=mode, me=me, stream=stream)
+        if ev is not None:
+            ev[1].record(stream)
+        mg.event_sum(me, wgt, out=out, scratch=scratch, stream=stream)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def timed(mode, steps):
+        for _ in range(args.warmup):
+            step(mode)
+        torch.cuda.synchronize()
+        barrier()
+        kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        barrier()
+        t0.record(stream)
+        for k in range(steps):
+            step(mode, kev[k])
+        t1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        total = t0.elapsed_time(t1) / 1e3
+        kern = [a.elapsed_time(b) / 1e3 for a, b in kev]
+        if world > 1:
+            t = torch.tensor([total], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            total = float(t.item())
+        return total, kern
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    total, kern = timed(args.mode, args.steps)
+    clk = clocks.stop()
+    me_main = me.clone()
+    sums = out.clone()
+    ngood = int(mask.sum().item())
+    value = world * nevt * args.steps / total
+
+    fp64 = None
+    if not args.no_fp64 and args.mode != "fp64":
+        t64, k64 = timed("fp64", max(1, min(args.steps, 2)))
+        me64 = me.clone()
+        rel = (me_main - me64).abs() / me64.abs()
+        relh = rel.cpu().numpy()
+        fp64 = {"value": world * nevt * max(1, min(args.steps, 2)) / t64, "unit": UNIT,
+                "sigmakin_ms": 1e3 * statistics.mean(k64),
+                "mixed_vs_fp64_rel_err": {"max": float(relh.max()), "median": float(np.median(relh)),
+                                          "p99.99": float(np.quantile(relh, 0.9999)),
+                                          "nonfinite": int((~torch.isfinite(me_main)).sum().item()),
+                                          "events": nevt}}
+
+    # end to end through the C ABI with host buffers (H2D of the random numbers,
+    # D2H of the matrix elements inside the timed region)
+    rnd_h = torch.from_numpy(I.uniforms(seed, 16, nevt, first_event=rank * nevt)).pin_memory()
+    me_h = torch.empty(nevt, dtype=torch.float64).pin_memory()
+    ws = torch.empty(mg.pipeline_workspace_bytes(proc, nevt, 16) // 8 + 1, dtype=torch.float64, device=dev)
+    for _ in range(args.warmup):
+        mg.pipeline_host(proc, rnd_h, ecm, mask, mode=args.mode, me_host=me_h, workspace=ws, stream=stream)
+    torch.cuda.synchronize()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        mg.pipeline_host(proc, rnd_h, ecm, mask, mode=args.mode, me_host=me_h, workspace=ws, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    te2e = e0.elapsed_time(e1) / 1e3
+    if world > 1:
+        t = torch.tensor([te2e], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        te2e = float(t.item())
+        torch.distributed.all_reduce(sums)  # the path's one exchange: sum over all events
+    e2e = {"value": world * nevt * args.steps / te2e, "unit": UNIT, "h2d_bytes_per_step": 16 * 8 * nevt,
+           "d2h_bytes_per_step": 8 * nevt}
+
+    # roofline of the dominant kernel (SIGMAKIN): FP32 CUDA-core arithmetic
+    s = procgen.summary(proc)
+    flops_per_me = ngood * (s["flops_amp"] + s["flops_csum"])
+    ksec = statistics.mean(kern)
+    achieved = flops_per_me * nevt / ksec / 1e12
+    peak32 = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak32, "unit": "TFLOP/s",
+                "frac": achieved / peak32, "traffic": None,
+                "kernel": "sigmakin_kernel<Proc4,float>", "flops_per_me": flops_per_me,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if args.mode != "fp64" else "f64",
+        "data": "synthetic (seeded SplitMix64 uniforms -> RAMBO)",
+        "config": {"workload": "gg->ttgg tree-level |M|^2, 2^20 events/GPU, RAMBO 4-body at 1500 GeV, "
+                               "mt=173 wt=1.491 alpha_s=0.118",
+                   "mode": args.mode, "events_per_gpu": nevt, "good_helicities": ngood,
+                   "l2": "inputs larger than L2 (336 MiB per step), no flush",
+                   "parallelism": "dp%d (independent event batches)" % world},
+        "sigmakin_ms": 1e3 * ksec,
+        "fp64": fp64,
+        "event_sum": [float(x) for x in sums.cpu().numpy()],
+        "roofline": roofline,
+        "clocks": clk,
+        "e2e": e2e,
+        "gpu_launches": kernel_launches_per_step * args.steps,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        rate, dt = cpu_oracle_rate(2048, seed, cores)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": "2048 gg->ttgg events (RAMBO + |M|^2 over all 64 helicities, "
+                                          "explicit colour), FP64, %.1f s wall" % dt}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,147 @@
+/*
+ * mg.h -- C ABI of the GB300 matrix-element library (libmg.so).
+ *
+ * Per-event tree-level squared matrix elements for the data-parallel
+ * workflow of arXiv:2106.12631 (Valassi, Roiser, Mattelaer, Hageboeck):
+ * uniform random numbers -> RAMBO momenta and weights -> helicity filtering ->
+ * |M|^2 from helicity amplitudes and the colour-flow colour sum -> event sum.
+ *
+ * Processes (proc ids):
+ *   1  e+ e- -> mu+ mu-   (photon + Z, 2 diagrams, 16 helicities, 1 colour flow)
+ *   2  g g -> t t~        (3 diagrams, 16 helicities, 2 colour flows)
+ *   3  g g -> t t~ g      (16 diagrams, 32 helicities, 6 colour flows)
+ *   4  g g -> t t~ g g    (123 diagrams, 64 helicities, 24 colour flows)
+ *
+ * Conventions shared by every entry point
+ *  - Arrays are device pointers unless the name starts with h_; they are
+ *    structure-of-arrays with the event index fastest (the paper's AOSOA
+ *    layout, Sec. 4, with a single page spanning all events):
+ *      rnd[k * nevt + i]                 random number k of event i
+ *      mom[((p * 4) + mu) * nevt + i]    particle p, component mu = (E, px, py, pz)
+ *      me[i], wgt[i]                     per-event outputs
+ *    Particle order is the process string above; legs 0 and 1 are the beams.
+ *  - Device pointers must be 16-byte aligned (MG_ERR_ALIGN otherwise).
+ *  - The caller allocates and frees every buffer; the library keeps no
+ *    per-call allocations and no device state besides compiled kernels.
+ *  - Work is enqueued asynchronously on `stream` (a cudaStream_t; NULL =
+ *    legacy default stream).  The return value reports argument validation
+ *    and launch errors only; faults inside a kernel surface at the next
+ *    synchronisation.  Nothing aborts and nothing throws across the ABI.
+ *  - nevt == 0 is valid and enqueues nothing (mg_event_sum writes zeros).
+ */
+#ifndef MG_H_
+#define MG_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MG_ABI_VERSION 1
+
+typedef enum {
+  MG_OK = 0,
+  MG_ERR_ARG = -1,     /* bad size, null pointer, bad mode or out-of-range value */
+  MG_ERR_PROC = -2,    /* unknown process id */
+  MG_ERR_ALIGN = -3,   /* a device pointer is not 16-byte aligned */
+  MG_ERR_CUDA = -5,    /* a CUDA call failed; see mg_last_cuda_error() */
+  MG_ERR_SPACE = -6    /* workspace or scratch smaller than required */
+} mg_status;
+
+/* Precision modes of mg_sigmakin (the paper's precision switch, Sec. 5,
+ * extended to a mixed mode). */
+typedef enum {
+  MG_FP64 = 0,        /* everything in FP64 */
+  MG_MIXED = 1,       /* FP32 wavefunctions, currents and amplitudes; FP64 momenta,
+                         propagator denominators and helicity/event sums; colour
+                         sum on the tensor cores (split-BF16, FP32 accumulation) */
+  MG_MIXED_SIMT = 2   /* as MG_MIXED with the colour sum on CUDA cores in FP32 */
+} mg_mode;
+
+typedef struct {
+  int npar;          /* external particles */
+  int nhel;          /* helicity combinations (2^npar) */
+  int ncolor;        /* colour flows */
+  int ndiagrams;     /* Feynman diagrams (a four-gluon vertex counts once) */
+  int namplitudes;   /* amplitude terms (four-gluon vertices split in 3) */
+  int nrand;         /* random numbers RAMBO consumes per event (4 per final particle) */
+  double mass[8];    /* particle masses for the current parameters [GeV] */
+} mg_process_info;
+
+/* Standard-Model inputs.  Defaults: mz 91.188, wz 2.441, alpha_inv 132.507,
+ * sw2 0.2222, mt 173, wt 1.491, alpha_s 0.118. */
+typedef struct {
+  double mz, wz;       /* Z mass and width [GeV] */
+  double alpha_inv;    /* 1 / alpha_em */
+  double sw2;          /* sin^2 theta_W */
+  double mt, wt;       /* top mass and width [GeV] */
+  double alpha_s;      /* strong coupling */
+} mg_params;
+
+/* Static description of a process.  Host only.  MG_ERR_PROC for a bad id. */
+int mg_get_process_info(int proc, mg_process_info* out);
+
+/* Replace the physics parameters used by subsequent launches (host state of
+ * the library, read at launch time; not thread safe against concurrent
+ * launches).  MG_ERR_ARG for non-finite or non-physical values. */
+int mg_set_params(const mg_params* p);
+int mg_get_params(mg_params* out);
+
+/* RAMBO (Sec. 3, "RAMBO" step of the toy workflow; Kleiss, Stirling, Ellis).
+ * rnd: [nrows][nevt] uniforms in (0,1); rows 4i..4i+3 drive final particle i
+ * (cos theta = 2 r1 - 1, phi = 2 pi r2, E ~ -log(r3 r4)); rows beyond
+ * 4*nfinal are ignored.  Output mom [npar][4][nevt] (beams along +z and -z at
+ * ecm/2 each) and wgt [nevt], the flat phase-space volume element without
+ * (2 pi) factors.  FP64.  MG_ERR_ARG if nrows < 4*nfinal or the final masses
+ * exceed ecm. */
+int mg_rambo(int proc, int64_t nevt, double ecm, const double* rnd, int nrows,
+             double* mom, double* wgt, void* stream);
+
+/* Helicity filtering (Sec. 2: allowed helicity combinations are found on a
+ * small set of events).  Computes |M_h|^2 in FP64 for every helicity h on the
+ * nevt events of mom and sets mask[h] = 1 if any event gives a non-zero
+ * value, else 0.  mask: [nhel] int32, overwritten (zeroed on the stream first).
+ * Typical nevt: 16. */
+int mg_filter_helicities(int proc, int64_t nevt, const double* mom, int32_t* mask, void* stream);
+
+/* Squared matrix elements (the paper's SIGMAKIN, Sec. 4): for every event,
+ *   me = 1/(helicity avg x colour avg x identical-particle factor)
+ *        x sum_{h : mask[h] != 0} J_h^dagger C J_h
+ * with J_h the colour-flow dual amplitudes of helicity h (Sec. 2) and C the
+ * colour matrix.  mask: [nhel] int32 from mg_filter_helicities (an all-zero
+ * mask gives me = 0).  mode: mg_mode.  me has units GeV^(8 - 2 npar):
+ * dimensionless for 2 -> 2, GeV^-2 for 2 -> 3, GeV^-4 for 2 -> 4. */
+int mg_sigmakin(int proc, int64_t nevt, const double* mom, const int32_t* mask, double* me, int mode,
+                void* stream);
+
+/* Event accumulation in FP64 (Sec. 3: average matrix element of a run):
+ * out3 = (sum_i wgt_i me_i, sum_i (wgt_i me_i)^2, nevt), by a two-pass tree
+ * reduction whose order depends only on nevt (bitwise reproducible).
+ * scratch: device buffer of at least mg_event_sum_scratch_bytes(nevt) bytes,
+ * owned by the caller, overwritten.  MG_ERR_SPACE if too small. */
+int64_t mg_event_sum_scratch_bytes(int64_t nevt);
+int mg_event_sum(int64_t nevt, const double* me, const double* wgt, double* out3, void* scratch,
+                 int64_t scratch_bytes, void* stream);
+
+/* End-to-end pipeline from HOST buffers (copies inside): h_rnd [nrows][nevt]
+ * -> host-to-device copy -> RAMBO -> SIGMAKIN (mask from mg_filter_helicities,
+ * on the device) -> device-to-host copy of me (and wgt if h_wgt != NULL).
+ * Host buffers should be pinned for asynchronous copies.  workspace: device
+ * buffer of at least mg_pipeline_workspace_bytes(proc, nevt, nrows) bytes.
+ * Enqueued on stream; the host buffers are valid after the stream
+ * synchronises. */
+int64_t mg_pipeline_workspace_bytes(int proc, int64_t nevt, int nrows);
+int mg_pipeline_host(int proc, int64_t nevt, double ecm, const double* h_rnd, int nrows, const int32_t* mask,
+                     int mode, double* h_me, double* h_wgt, void* workspace, int64_t workspace_bytes,
+                     void* stream);
+
+/* Human-readable status; the CUDA error code of the last MG_ERR_CUDA. */
+const char* mg_status_string(int status);
+int mg_last_cuda_error(void);
+int mg_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MG_H_ */

@@ -1,0 +1,54 @@
+// GENERATED by paper_2106_12631_gb300/gen/procgen.py -- do not edit.
+// Process 1: ee_mumu (e+ e- mu+ mu-)
+// 2 Feynman diagrams (2 amplitude terms), 1 colour flows, 6 wavefunctions
+// colour-flow coefficients used: [(1+0j)]
+#pragma once
+namespace mg {
+struct Proc1 {
+  static constexpr int NPAR = 4;
+  static constexpr int NHEL = 16;
+  static constexpr int NCOLOR = 1;
+  static constexpr int NDIAGRAMS = 2;
+  static constexpr int NAMPS = 2;
+  static constexpr int NMOM = 5;
+  static constexpr int NPROP = 2;
+  static constexpr int NFINAL = 2;
+  // floating-point operations per helicity: diagram program, CUDA-core colour sum
+  static constexpr long FLOPS_AMP = 604;
+  static constexpr long FLOPS_CSUM = 9;
+  static constexpr double NORM = 1.0 / 4.0;  // 1/(helicity avg x colour avg x symmetry)
+  // momentum table: {0 physical / 1 all-outgoing sum, leg mask, mask of legs entering as -p}
+  static __host__ __device__ constexpr int mom(int j, int k) {
+    constexpr int t[NMOM][3] = {{0, 1, 0}, {0, 2, 0}, {0, 4, 0}, {0, 8, 0}, {1, 3, 3}};
+    return t[j][k];
+  }
+  // propagators: {momentum entry, 0 gluon / 1 top / 2 photon / 3 Z}
+  static __host__ __device__ constexpr int prop(int j, int k) {
+    constexpr int t[NPROP][2] = {{4, 2}, {4, 3}};
+    return t[j][k];
+  }
+  // colour matrix = CNUM / CDEN (real symmetric)
+  static constexpr int CDEN = 1;
+  static __host__ __device__ constexpr int cnum(int i, int j) {
+    constexpr int t[NCOLOR][NCOLOR] = {{1}};
+    return t[i][j];
+  }
+  // dual amplitudes J[NCOLOR] of one helicity combination (hel[k] = +-1)
+  template <class R>
+  static __device__ __forceinline__ void amplitudes(const R* __restrict__ K, const cx<R>* __restrict__ prop, const int* hel, const Couplings<R>& cp, cx<R>* J) {
+    #pragma unroll
+    for (int s = 0; s < NCOLOR; ++s) J[s] = cx<R>(R(0), R(0));
+  cx<R> amp;
+  const W4<R> w2 = ixxxxx<R>(K + 8, R(0), hel[2], -1);
+  const W4<R> w0 = oxxxxx<R>(K + 0, R(0), hel[0], -1);
+  const W4<R> w1 = ixxxxx<R>(K + 4, R(0), hel[1], 1);
+  const W4<R> w3 = FFV1P0_3<R>(w0, w1, cp.ee, prop[0]);
+  const W4<R> w5 = oxxxxx<R>(K + 12, R(0), hel[3], 1);
+  amp = FFV1_0<R>(w5, w2, w3, cp.ee);
+  J[0] += amp;
+  const W4<R> w4 = FFV2_4_3<R>(w0, w1, cp.gz, cp.gzl, cp.gzr, prop[1]);
+  amp = FFV2_4_0<R>(w5, w2, w4, cp.gz, cp.gzl, cp.gzr);
+  J[0] += amp;
+  }
+};
+}  // namespace mg

@@ -1,0 +1,58 @@
+// Complex numbers, wavefunction objects and couplings for the matrix-element
+// kernels.  R is the working precision: double (plain FP64 path) or float
+// (mixed path).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mg {
+
+template <class R>
+struct cx {
+  R re, im;
+  cx() = default;
+  __host__ __device__ constexpr cx(R r, R i) : re(r), im(i) {}
+};
+template <class R> __device__ __forceinline__ cx<R> operator+(cx<R> a, cx<R> b) { return cx<R>(a.re + b.re, a.im + b.im); }
+template <class R> __device__ __forceinline__ cx<R> operator-(cx<R> a, cx<R> b) { return cx<R>(a.re - b.re, a.im - b.im); }
+template <class R> __device__ __forceinline__ cx<R> operator-(cx<R> a) { return cx<R>(-a.re, -a.im); }
+template <class R> __device__ __forceinline__ cx<R> operator*(cx<R> a, cx<R> b) {
+  return cx<R>(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+template <class R> __device__ __forceinline__ cx<R> operator*(R s, cx<R> a) { return cx<R>(s * a.re, s * a.im); }
+template <class R> __device__ __forceinline__ cx<R> operator*(cx<R> a, R s) { return cx<R>(s * a.re, s * a.im); }
+template <class R> __device__ __forceinline__ cx<R>& operator+=(cx<R>& a, cx<R> b) { a.re += b.re; a.im += b.im; return a; }
+template <class R> __device__ __forceinline__ cx<R>& operator-=(cx<R>& a, cx<R> b) { a.re -= b.re; a.im -= b.im; return a; }
+template <class R> __device__ __forceinline__ cx<R> conj(cx<R> a) { return cx<R>(a.re, -a.im); }
+template <class R> __device__ __forceinline__ cx<R> mul_i(cx<R> a) { return cx<R>(-a.im, a.re); }   // i * a
+template <class R> __device__ __forceinline__ cx<R> mul_mi(cx<R> a) { return cx<R>(a.im, -a.re); }  // -i * a
+
+// Four complex components: a Dirac spinor (chiral basis, upper pair
+// left-handed; a row spinor for flowing-out fermions, a column spinor for
+// flowing-in ones) or a Lorentz vector with upper index.  The paper's
+// six-component wavefunction (Sec. 2) also carries the momentum; here the
+// momenta are helicity independent and live in a per-event table instead.
+template <class R>
+struct W4 {
+  cx<R> w[4];
+};
+
+// Couplings and masses in the working precision.
+template <class R>
+struct Couplings {
+  R gs;    // strong coupling g_s (quark-gluon i g_s gamma^mu T^a, three-gluon g_s f^abc [..])
+  R gs2;   // g_s^2 (four-gluon -i g_s^2 [..])
+  R ee;    // e; photon-lepton vertex -i e Q gamma^mu with Q = -1
+  R gz;    // e / (sin theta_W cos theta_W)
+  R gzl;   // Z left coupling of charged leptons, T3 - Q sin^2 theta_W
+  R gzr;   // Z right coupling, -Q sin^2 theta_W
+  R mt;    // top mass
+};
+
+// Physics parameters in FP64 (propagator denominators are formed in FP64 in
+// both precision modes).
+struct PhysParams {
+  double mz, wz, mt, wt;
+};
+
+}  // namespace mg

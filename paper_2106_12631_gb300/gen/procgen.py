@@ -1,0 +1,632 @@
+"""Restricted process generator: Feynman diagrams -> straight-line CUDA.
+
+For each of the four processes of the paper's benchmarks (Sec. 2 and Table 1:
+e+e- -> mu+mu-, gg -> t tbar, gg -> t tbar g, gg -> t tbar g g) this script
+enumerates the tree-level Feynman diagrams, decomposes their colour factors
+into colour flows (the colour-flow method of Sec. 2: each diagram's amplitude
+is added, with a coefficient, to the dual amplitudes J_sigma of the flows it
+contributes to), computes the colour matrix of the flows, and emits one
+straight-line device function per process that evaluates every J_sigma for
+one helicity combination from external wavefunctions, internal currents and
+vertex amplitudes (the three routine categories of Sec. 2 / Fig. 1).
+
+Design (independent of the CPU oracle, which uses explicit colour tensors):
+
+* All momenta are taken outgoing.  The antitop (QCD processes) or the mu-
+  (e+e- -> mu+mu-) is the root leg; every other leg subset S gets the list
+  of off-shell currents whose external legs are exactly S; each unordered
+  partition into 2 (or 3, four-gluon vertex) parts is visited once.  With the
+  antitop as root, the fermion line never closes into a gluon, so every
+  diagram's colour factor is a product, along the quark line, of matrices
+  M built from gluon sub-trees by nested commutators:
+      external gluon a        M = T^a
+      three-gluon vertex      M = -i [M1, M2]          (f^{abx} T^x = -i [T^a, T^b])
+      four-gluon term 0/1/2   M = -[[M1,M2],M3] / -[[M1,M3],M2] / -[[M2,M3],M1]
+  Expanding the commutators gives the diagram's coefficient on each colour
+  chain (T^{a_s1} ... T^{a_sn})_{i j} exactly (powers of i, integers).
+* The colour matrix C_{st} = sum over colours of chain_s conj(chain_t) is
+  computed with explicit Gell-Mann matrices and reconstructed as exact
+  rationals (common denominator, integer numerators).
+* Conventions: Peskin & Schroeder Feynman rules (quark-gluon i g gamma^mu T^a,
+  three-gluon g f^abc [...], four-gluon -i g^2 [...], fermion propagator
+  i(p/ + m)/(p^2 - m^2 + i m Gamma), Feynman-gauge vector propagator
+  -i g^{mu nu}/(p^2 - M^2 + i M Gamma)).  The Z propagator's q^mu q^nu term
+  is dropped: it vanishes on the massless lepton currents.
+
+Run ``python -m paper_2106_12631_gb300.gen`` to regenerate ``csrc/gen/``.
+"""
+from __future__ import annotations
+
+import itertools
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+# ---------------------------------------------------------------------------
+# process definitions
+# ---------------------------------------------------------------------------
+# line kinds: "g" gluon, "A" photon, "Z", ("row", fl) flowing-out fermion
+# (u-bar / v-bar), ("col", fl) flowing-in fermion (u / v); fl in {"t","e","mu"}
+
+
+@dataclass
+class LegSpec:
+    name: str
+    kind: object
+    incoming: bool
+    particle: bool
+    mass: str  # "0" or "mt"
+
+
+@dataclass
+class ProcSpec:
+    pid: int
+    name: str
+    legs: list
+    root: int
+    hel_avg: int
+    col_avg: int
+    sym: int
+
+
+PROCS = {
+    1: ProcSpec(1, "ee_mumu", [
+        LegSpec("e+", ("row", "e"), True, False, "0"),
+        LegSpec("e-", ("col", "e"), True, True, "0"),
+        LegSpec("mu+", ("col", "mu"), False, False, "0"),
+        LegSpec("mu-", ("row", "mu"), False, True, "0")], root=3, hel_avg=4, col_avg=1, sym=1),
+    2: ProcSpec(2, "gg_tt", [
+        LegSpec("g", "g", True, True, "0"), LegSpec("g", "g", True, True, "0"),
+        LegSpec("t", ("row", "t"), False, True, "mt"),
+        LegSpec("t~", ("col", "t"), False, False, "mt")], root=3, hel_avg=4, col_avg=64, sym=1),
+    3: ProcSpec(3, "gg_ttg", [
+        LegSpec("g", "g", True, True, "0"), LegSpec("g", "g", True, True, "0"),
+        LegSpec("t", ("row", "t"), False, True, "mt"),
+        LegSpec("t~", ("col", "t"), False, False, "mt"),
+        LegSpec("g", "g", False, True, "0")], root=3, hel_avg=4, col_avg=64, sym=1),
+    4: ProcSpec(4, "gg_ttgg", [
+        LegSpec("g", "g", True, True, "0"), LegSpec("g", "g", True, True, "0"),
+        LegSpec("t", ("row", "t"), False, True, "mt"),
+        LegSpec("t~", ("col", "t"), False, False, "mt"),
+        LegSpec("g", "g", False, True, "0"), LegSpec("g", "g", False, True, "0")],
+        root=3, hel_avg=4, col_avg=64, sym=2),
+}
+
+
+def _is_row(k):
+    return isinstance(k, tuple) and k[0] == "row"
+
+
+def _is_col(k):
+    return isinstance(k, tuple) and k[0] == "col"
+
+
+# ---------------------------------------------------------------------------
+# symbolic colour: polynomials in non-commuting generators T^{a_g}
+# represented as {tuple(gluon legs in order): complex coefficient}
+# ---------------------------------------------------------------------------
+def cmul(x, y):
+    out = {}
+    for kx, vx in x.items():
+        for ky, vy in y.items():
+            k = kx + ky
+            out[k] = out.get(k, 0) + vx * vy
+    return {k: v for k, v in out.items() if v != 0}
+
+
+def cadd(x, y, s=1):
+    out = dict(x)
+    for k, v in y.items():
+        out[k] = out.get(k, 0) + s * v
+    return {k: v for k, v in out.items() if v != 0}
+
+
+def cscale(x, s):
+    return {k: v * s for k, v in x.items() if v * s != 0}
+
+
+def comm(x, y):
+    return cadd(cmul(x, y), cmul(y, x), -1)
+
+
+# ---------------------------------------------------------------------------
+# diagram enumeration
+# ---------------------------------------------------------------------------
+@dataclass
+class Cur:
+    idx: int
+    legs: frozenset
+    kind: object              # line kind of the current
+    vertex: str               # "ext", "qqg_row", "qqg_col", "ggg", "gggg0/1/2", "ffa", "ffz", ...
+    children: tuple = ()
+    colour: dict = field(default_factory=dict)  # gluon currents: matrix rep M; fermion: line product
+    n4: int = 0               # four-gluon vertices below
+    nz4: int = 0              # ... with term != 0
+
+
+@dataclass
+class Amp:
+    vertex: str               # "ffv_t", "ffv_a", "ffz"
+    row: int                  # current indices (row fermion, col fermion, boson)
+    col: int
+    bos: int
+    colour: dict
+    counted: bool             # first member of its four-gluon family
+
+
+class Process:
+    def __init__(self, spec: ProcSpec):
+        self.spec = spec
+        self.n = len(spec.legs)
+        self.cur = []
+        self.by_legs = {}
+        self.amps = []
+        rest = frozenset(i for i in range(self.n) if i != spec.root)
+        self._currents(rest)
+        self._amplitudes(rest)
+
+    # ---- currents -------------------------------------------------------
+    def _new(self, **kw):
+        c = Cur(idx=len(self.cur), **kw)
+        self.cur.append(c)
+        return c.idx
+
+    def _currents(self, S):
+        if S in self.by_legs:
+            return self.by_legs[S]
+        out = []
+        if len(S) == 1:
+            (leg,) = S
+            L = self.spec.legs[leg]
+            col = {(leg,): 1} if L.kind == "g" else ({(): 1} if isinstance(L.kind, tuple) else {})
+            out.append(self._new(legs=S, kind=L.kind, vertex="ext", children=(leg,), colour=col))
+            self.by_legs[S] = out
+            return out
+        items = sorted(S)
+        first = items[0]
+        others = items[1:]
+        # two-part partitions: the part holding `first` is S1
+        for r in range(0, len(others)):
+            for sub in itertools.combinations(others, r):
+                S1 = frozenset((first,) + sub)
+                S2 = S - S1
+                if not S2:
+                    continue
+                for a in self._currents(S1):
+                    for b in self._currents(S2):
+                        out.extend(self._join2(S, a, b))
+        # three-part partitions (four-gluon vertex)
+        for r1 in range(0, len(others)):
+            for sub1 in itertools.combinations(others, r1):
+                S1 = frozenset((first,) + sub1)
+                R = sorted(S - S1)
+                if len(R) < 2:
+                    continue
+                f2 = R[0]
+                for r2 in range(0, len(R) - 1):
+                    for sub2 in itertools.combinations(R[1:], r2):
+                        S2 = frozenset((f2,) + sub2)
+                        S3 = frozenset(R) - S2
+                        if not S3:
+                            continue
+                        for a in self._currents(S1):
+                            for b in self._currents(S2):
+                                for c in self._currents(S3):
+                                    out.extend(self._join3(S, a, b, c))
+        self.by_legs[S] = out
+        return out
+
+    def _join2(self, S, ia, ib):
+        A, B = self.cur[ia], self.cur[ib]
+        made = []
+        for x, y in ((A, B), (B, A)):
+            if x is B and A.kind == B.kind:
+                continue
+            kx, ky = x.kind, y.kind
+            n4, nz4 = x.n4 + y.n4, x.nz4 + y.nz4
+            if kx == "g" and ky == "g" and x is A:
+                col = cscale(comm(x.colour, y.colour), -1j)
+                made.append(self._new(legs=S, kind="g", vertex="ggg", children=(x.idx, y.idx),
+                                      colour=col, n4=n4, nz4=nz4))
+            elif _is_row(kx) and ky == "g" and kx[1] == "t":
+                made.append(self._new(legs=S, kind=kx, vertex="qqg_row", children=(x.idx, y.idx),
+                                      colour=cmul(x.colour, y.colour), n4=n4, nz4=nz4))
+            elif _is_col(kx) and ky == "g" and kx[1] == "t":
+                made.append(self._new(legs=S, kind=kx, vertex="qqg_col", children=(x.idx, y.idx),
+                                      colour=cmul(y.colour, x.colour), n4=n4, nz4=nz4))
+            elif _is_row(kx) and _is_col(ky) and kx[1] == ky[1] and kx[1] != "t":
+                for bos in ("A", "Z"):
+                    made.append(self._new(legs=S, kind=bos, vertex="ff" + bos.lower() + "_cur",
+                                          children=(x.idx, y.idx), colour={(): 1}, n4=n4, nz4=nz4))
+            elif _is_row(kx) and _is_col(ky) and kx[1] == "t":
+                raise NotImplementedError("quark line closing into a gluon: choose a quark root")
+        return made
+
+    def _join3(self, S, ia, ib, ic):
+        A, B, C = self.cur[ia], self.cur[ib], self.cur[ic]
+        if not (A.kind == B.kind == C.kind == "g"):
+            return []
+        m1, m2, m3 = A.colour, B.colour, C.colour
+        cols = [cscale(comm(comm(m1, m2), m3), -1), cscale(comm(comm(m1, m3), m2), -1),
+                cscale(comm(comm(m2, m3), m1), -1)]
+        made = []
+        n4 = 1 + A.n4 + B.n4 + C.n4
+        nz = A.nz4 + B.nz4 + C.nz4
+        for t in range(3):
+            made.append(self._new(legs=S, kind="g", vertex="gggg%d" % t, children=(ia, ib, ic),
+                                  colour=cols[t], n4=n4, nz4=nz + (t != 0)))
+        return made
+
+    # ---- amplitudes at the root -------------------------------------------
+    def _amplitudes(self, rest):
+        spec = self.spec
+        rk = spec.legs[spec.root].kind
+        root_cur = self._new(legs=frozenset([spec.root]), kind=rk, vertex="ext",
+                             children=(spec.root,), colour={(): 1})
+        self.root_cur = root_cur
+        items = sorted(rest)
+        for r in range(1, len(items)):
+            for sub in itertools.combinations(items, r):
+                S1 = frozenset(sub)
+                S2 = rest - S1
+                for a in self._currents(S1):
+                    for b in self._currents(S2):
+                        A, B = self.cur[a], self.cur[b]
+                        if B.kind == "g" and _is_row(A.kind) and _is_col(rk) and A.kind[1] == "t":
+                            # quark line: row (top end) . T^b . root column
+                            self.amps.append(Amp("ffv_t", a, root_cur, b, cmul(A.colour, B.colour),
+                                                 A.nz4 + B.nz4 == 0))
+                        elif B.kind in ("A", "Z") and _is_col(A.kind) and _is_row(rk) \
+                                and A.kind[1] == rk[1]:
+                            self.amps.append(Amp("ffv_a" if B.kind == "A" else "ffz", root_cur, a, b,
+                                                 {(): 1}, True))
+
+    @property
+    def ndiagrams(self):
+        return sum(1 for a in self.amps if a.counted)
+
+    def gluon_legs(self):
+        return [i for i, L in enumerate(self.spec.legs) if L.kind == "g"]
+
+
+# ---------------------------------------------------------------------------
+# colour flows and colour matrix
+# ---------------------------------------------------------------------------
+def gell_mann():
+    lam = np.zeros((8, 3, 3), complex)
+    lam[0][0, 1] = lam[0][1, 0] = 1
+    lam[1][0, 1], lam[1][1, 0] = -1j, 1j
+    lam[2][0, 0], lam[2][1, 1] = 1, -1
+    lam[3][0, 2] = lam[3][2, 0] = 1
+    lam[4][0, 2], lam[4][2, 0] = -1j, 1j
+    lam[5][1, 2] = lam[5][2, 1] = 1
+    lam[6][1, 2], lam[6][2, 1] = -1j, 1j
+    lam[7] = np.diag([1, 1, -2]) / math.sqrt(3)
+    return lam / 2
+
+
+def chain_matrix(ng: int):
+    """C_{st} for the ng! chains in lexicographic permutation order, as (numerators, den)."""
+    T = gell_mann()
+    perms = list(itertools.permutations(range(ng)))
+    # tensor of each chain over (a_1..a_ng, i, j)
+    ch = []
+    for p in perms:
+        acc = np.zeros((8,) * ng + (3, 3), complex)
+        for a in itertools.product(range(8), repeat=ng):
+            M = np.eye(3, dtype=complex)
+            for k in p:
+                M = M @ T[a[k]]
+            acc[a] = M
+        ch.append(acc.reshape(-1))
+    ch = np.array(ch)
+    C = ch @ ch.conj().T
+    assert np.max(np.abs(C.imag)) < 1e-10
+    C = C.real
+    den = 8 * 3 ** ng  # SU(3) chain traces are rationals with denominators 2^a 3^b
+    num = np.rint(C * den)
+    assert np.max(np.abs(num - C * den)) < 1e-8, "colour matrix not rational with denominator 8 3^n"
+    num = num.astype(np.int64)
+    g = int(np.gcd.reduce(np.append(num.reshape(-1), den)))
+    return perms, num // g, den // g
+
+
+def colour_flows(proc: Process):
+    """Coefficient of every amplitude on every chain; returns (perms, coef[namp][nflow])."""
+    gl = proc.gluon_legs()
+    ng = len(gl)
+    if ng == 0:
+        return [()], np.ones((len(proc.amps), 1), complex)
+    perms = list(itertools.permutations(range(ng)))
+    index = {tuple(gl[k] for k in p): i for i, p in enumerate(perms)}
+    coef = np.zeros((len(proc.amps), len(perms)), complex)
+    for d, a in enumerate(proc.amps):
+        for word, v in a.colour.items():
+            coef[d, index[word]] += v
+    return perms, coef
+
+
+# ---------------------------------------------------------------------------
+# CUDA emission
+# ---------------------------------------------------------------------------
+def _cpx(z):
+    z = complex(z)
+    return "cx<R>(R(%r), R(%r))" % (z.real, z.imag)
+
+
+# Floating-point operations of each device routine as written in
+# csrc/helas.cuh (complex add 2, complex multiply 6, real x complex 2; an FMA
+# counts as 2).  External wavefunctions include their square roots and
+# divisions as one operation each.
+FLOPS = {
+    "ixxxxx": 45, "oxxxxx": 45, "vxxxxx": 20,
+    "FFV1_0": 96, "FFV2_4_0": 104,
+    "FFV1_1": 148, "FFV1_2": 148, "FFV1P0_3": 106, "FFV2_4_3": 114,
+    "VVV1P0_1": 176, "VVVV1P0_1": 142, "VVVV3P0_1": 142, "VVVV4P0_1": 142,
+    "jamp": 2,
+}
+
+
+def colour_sum_flops(cnum) -> int:
+    """Real colour sum J^dagger C J with C = CNUM / CDEN on CUDA cores: per row
+    two FMAs per non-zero entry, then re/im products, the row sum and the scale."""
+    nz = int(np.count_nonzero(cnum))
+    return 4 * nz + 4 * cnum.shape[0] + 1
+
+
+class Emitter:
+    """Straight-line device code for one process."""
+
+    def __init__(self, proc: Process):
+        self.p = proc
+        self.spec = proc.spec
+        self.perms, self.coef = colour_flows(proc)
+        ng = len(proc.gluon_legs())
+        if ng:
+            _, self.cnum, self.cden = chain_matrix(ng)
+        else:
+            self.cnum, self.cden = np.ones((1, 1), np.int64), 1
+        self.mom = []        # momentum table entries: (legs tuple) all-outgoing sums
+        self.mom_index = {}
+        self.props = []      # (mom index, kind)
+        self.prop_index = {}
+
+    def momentum(self, legs):
+        key = tuple(sorted(legs))
+        if key not in self.mom_index:
+            self.mom_index[key] = len(self.mom)
+            self.mom.append(key)
+        return self.mom_index[key]
+
+    def prop(self, legs, kind):
+        key = (tuple(sorted(legs)), kind)
+        if key not in self.prop_index:
+            self.prop_index[key] = len(self.props)
+            self.props.append((self.momentum(legs), kind))
+        return self.prop_index[key]
+
+    def _current_code(self, c, var):
+        """One line of device code computing current c (children already emitted)."""
+        p, spec = self.p, self.spec
+        v = var[c.idx]
+        if c.vertex == "ext":
+            leg = c.children[0]
+            L = spec.legs[leg]
+            m = "cp.mt" if L.mass == "mt" else "R(0)"
+            pm = "K + %d" % (4 * self.momentum_phys(leg))
+            h = "hel[%d]" % leg
+            if L.kind == "g":
+                return "  const W4<R> %s = vxxxxx<R>(%s, %s, %d);" % (v, pm, h, 1 if L.incoming else -1)
+            if _is_col(L.kind):
+                return "  const W4<R> %s = ixxxxx<R>(%s, %s, %s, %d);" % (v, pm, m, h, 1 if L.particle else -1)
+            return "  const W4<R> %s = oxxxxx<R>(%s, %s, %s, %d);" % (v, pm, m, h, 1 if L.particle else -1)
+        ch = [var[i] for i in c.children]
+        if c.vertex == "ggg":
+            a, b = p.cur[c.children[0]], p.cur[c.children[1]]
+            k1, k2 = self.momentum(a.legs), self.momentum(b.legs)
+            pr = self.prop(c.legs, "g")
+            return ("  const W4<R> %s = VVV1P0_1<R>(%s, %s, K + %d, K + %d, cp.gs, prop[%d]);"
+                    % (v, ch[0], ch[1], 4 * k1, 4 * k2, pr))
+        if c.vertex.startswith("gggg"):
+            fn = ("VVVV1P0_1", "VVVV3P0_1", "VVVV4P0_1")[int(c.vertex[-1])]
+            pr = self.prop(c.legs, "g")
+            return "  const W4<R> %s = %s<R>(%s, %s, %s, cp.gs2, prop[%d]);" % (v, fn, ch[0], ch[1], ch[2], pr)
+        if c.vertex in ("qqg_row", "qqg_col"):
+            k = self.momentum(c.legs)
+            pr = self.prop(c.legs, "t")
+            fn = "FFV1_2" if c.vertex == "qqg_row" else "FFV1_1"
+            return ("  const W4<R> %s = %s<R>(%s, %s, cp.gs, K + %d, cp.mt, prop[%d]);"
+                    % (v, fn, ch[0], ch[1], 4 * k, pr))
+        if c.vertex == "ffa_cur":
+            pr = self.prop(c.legs, "A")
+            return "  const W4<R> %s = FFV1P0_3<R>(%s, %s, cp.ee, prop[%d]);" % (v, ch[0], ch[1], pr)
+        if c.vertex == "ffz_cur":
+            pr = self.prop(c.legs, "Z")
+            return ("  const W4<R> %s = FFV2_4_3<R>(%s, %s, cp.gz, cp.gzl, cp.gzr, prop[%d]);"
+                    % (v, ch[0], ch[1], pr))
+        raise ValueError(c.vertex)
+
+    def _deps(self, i, out):
+        """All currents (transitively) needed by current i, children first."""
+        c = self.p.cur[i]
+        if c.vertex != "ext":
+            for ch in c.children:
+                self._deps(ch, out)
+        if i not in out:
+            out[i] = None
+        return out
+
+    def schedule(self):
+        """Order amplitudes so consecutive ones share currents; each current is
+        emitted just before its first use, which keeps the live set small."""
+        p = self.p
+        need = [list(self._deps(a.row, self._deps(a.bos, self._deps(a.col, {})))) for a in p.amps]
+        uses = {}
+        for d, n in enumerate(need):
+            for i in n:
+                uses[i] = uses.get(i, 0) + 1
+        done = set()
+        order = []
+        left = set(range(len(p.amps)))
+        live = set()
+        while left:
+            def cost(d):
+                new = sum(1 for i in need[d] if i not in done)
+                frees = sum(1 for i in need[d] if i in live and uses[i] == 1)
+                return (new - frees, d)
+            d = min(left, key=cost)
+            left.discard(d)
+            order.append(d)
+            for i in need[d]:
+                if i not in done:
+                    done.add(i)
+                    live.add(i)
+                uses[i] -= 1
+                if uses[i] == 0:
+                    live.discard(i)
+        return order, need
+
+    def emit(self) -> str:
+        p = self.p
+        order, need = self.schedule()
+        var = {}
+        self.flops = 0
+        body = ["  cx<R> amp;"]
+        for d in order:
+            a = p.amps[d]
+            for i in need[d]:
+                if i not in var:
+                    var[i] = "w%d" % i
+                    line = self._current_code(p.cur[i], var)
+                    self.flops += FLOPS[line.split("=")[1].split("<")[0].strip()]
+                    body.append(line)
+            if a.vertex == "ffv_t":
+                body.append("  amp = FFV1_0<R>(%s, %s, %s, cp.gs);" % (var[a.row], var[a.col], var[a.bos]))
+            elif a.vertex == "ffv_a":
+                body.append("  amp = FFV1_0<R>(%s, %s, %s, cp.ee);" % (var[a.row], var[a.col], var[a.bos]))
+            else:
+                body.append("  amp = FFV2_4_0<R>(%s, %s, %s, cp.gz, cp.gzl, cp.gzr);"
+                            % (var[a.row], var[a.col], var[a.bos]))
+            self.flops += FLOPS["FFV2_4_0" if a.vertex == "ffz" else "FFV1_0"]
+            for s_ in np.nonzero(self.coef[d])[0]:
+                body.append("  " + self._accum(s_, self.coef[d, s_]))
+                self.flops += FLOPS["jamp"]
+        self.ncurrents = len(var)
+        self.body = body
+        return "\n".join(body)
+
+    def momentum_phys(self, leg):
+        key = ("phys", leg)
+        if key not in self.mom_index:
+            self.mom_index[key] = len(self.mom)
+            self.mom.append(key)
+        return self.mom_index[key]
+
+    @staticmethod
+    def _accum(s, z):
+        z = complex(z)
+        if z == 1:
+            return "J[%d] += amp;" % s
+        if z == -1:
+            return "J[%d] -= amp;" % s
+        if z == 1j:
+            return "J[%d] += mul_i(amp);" % s
+        if z == -1j:
+            return "J[%d] -= mul_i(amp);" % s
+        return "J[%d] += %s * amp;" % (s, _cpx(z))
+
+
+def generate(pid: int) -> str:
+    proc = Process(PROCS[pid])
+    em = Emitter(proc)
+    # physical momenta first so that external legs have fixed slots
+    for leg in range(proc.n):
+        em.momentum_phys(leg)
+    body = em.emit()
+    spec = proc.spec
+    ncol = em.coef.shape[1]
+    nflow_used = int(np.count_nonzero(np.any(em.coef != 0, axis=0)))
+    assert nflow_used == ncol
+    coefs = set(complex(z) for z in em.coef.reshape(-1) if z != 0)
+    out = []
+    out.append("// GENERATED by paper_2106_12631_gb300/gen/procgen.py -- do not edit.")
+    out.append("// Process %d: %s (%s)" % (pid, spec.name, " ".join(L.name for L in spec.legs)))
+    out.append("// %d Feynman diagrams (%d amplitude terms), %d colour flows, %d wavefunctions"
+               % (proc.ndiagrams, len(proc.amps), ncol, em.ncurrents))
+    out.append("// colour-flow coefficients used: %s" % sorted(coefs, key=lambda z: (z.real, z.imag)))
+    out.append("#pragma once")
+    out.append("namespace mg {")
+    out.append("struct Proc%d {" % pid)
+    out.append("  static constexpr int NPAR = %d;" % proc.n)
+    out.append("  static constexpr int NHEL = %d;" % (1 << proc.n))
+    out.append("  static constexpr int NCOLOR = %d;" % ncol)
+    out.append("  static constexpr int NDIAGRAMS = %d;" % proc.ndiagrams)
+    out.append("  static constexpr int NAMPS = %d;" % len(proc.amps))
+    out.append("  static constexpr int NMOM = %d;" % len(em.mom))
+    out.append("  static constexpr int NPROP = %d;" % len(em.props))
+    out.append("  static constexpr int NFINAL = %d;" % (proc.n - 2))
+    out.append("  // floating-point operations per helicity: diagram program, CUDA-core colour sum")
+    out.append("  static constexpr long FLOPS_AMP = %d;" % em.flops)
+    out.append("  static constexpr long FLOPS_CSUM = %d;" % colour_sum_flops(em.cnum))
+    out.append("  static constexpr double NORM = 1.0 / %d.0;  // 1/(helicity avg x colour avg x symmetry)"
+               % (spec.hel_avg * spec.col_avg * spec.sym))
+    # momentum table: for each entry, the legs (signs: incoming legs enter as -p)
+    mrows = []
+    for key in em.mom:
+        mask = 0
+        sign = 0
+        if key[0] == "phys":
+            mask = 1 << key[1]
+            sgn_mask = 0
+            kind = 0
+        else:
+            for leg in key:
+                mask |= 1 << leg
+            sgn_mask = sum(1 << leg for leg in key if spec.legs[leg].incoming)
+            kind = 1
+        mrows.append("{%d, %d, %d}" % (kind, mask, sgn_mask))
+    out.append("  // momentum table: {0 physical / 1 all-outgoing sum, leg mask, mask of legs entering as -p}")
+    out.append("  static __host__ __device__ constexpr int mom(int j, int k) {")
+    out.append("    constexpr int t[NMOM][3] = {%s};" % ", ".join(mrows))
+    out.append("    return t[j][k];")
+    out.append("  }")
+    prows = []
+    kinds = {"g": 0, "t": 1, "A": 2, "Z": 3}
+    for (mi, kind) in em.props:
+        prows.append("{%d, %d}" % (mi, kinds[kind]))
+    out.append("  // propagators: {momentum entry, 0 gluon / 1 top / 2 photon / 3 Z}")
+    out.append("  static __host__ __device__ constexpr int prop(int j, int k) {")
+    out.append("    constexpr int t[NPROP][2] = {%s};" % ", ".join(prows))
+    out.append("    return t[j][k];")
+    out.append("  }")
+    out.append("  // colour matrix = CNUM / CDEN (real symmetric)")
+    out.append("  static constexpr int CDEN = %d;" % em.cden)
+    out.append("  static __host__ __device__ constexpr int cnum(int i, int j) {")
+    out.append("    constexpr int t[NCOLOR][NCOLOR] = {%s};"
+               % ", ".join("{" + ", ".join(str(int(x)) for x in row) + "}" for row in em.cnum))
+    out.append("    return t[i][j];")
+    out.append("  }")
+    out.append("  // dual amplitudes J[NCOLOR] of one helicity combination (hel[k] = +-1)")
+    out.append("  template <class R>")
+    out.append("  static __device__ __forceinline__ void amplitudes(const R* __restrict__ K,"
+               " const cx<R>* __restrict__ prop, const int* hel, const Couplings<R>& cp, cx<R>* J) {")
+    out.append("    #pragma unroll")
+    out.append("    for (int s = 0; s < NCOLOR; ++s) J[s] = cx<R>(R(0), R(0));")
+    out.append(body)
+    out.append("  }")
+    out.append("};")
+    out.append("}  // namespace mg")
+    return "\n".join(out) + "\n"
+
+
+def summary(pid: int) -> dict:
+    proc = Process(PROCS[pid])
+    em = Emitter(proc)
+    for leg in range(proc.n):
+        em.momentum_phys(leg)
+    em.emit()
+    return dict(flops_amp=em.flops, flops_csum=colour_sum_flops(em.cnum), ncurrents=em.ncurrents,
+                ndiagrams=proc.ndiagrams, namps=len(proc.amps), ncolor=em.coef.shape[1],
+                nmom=len(em.mom), nprop=len(em.props), coef=em.coef, cnum=em.cnum, cden=em.cden,
+                perms=em.perms, gluon_legs=proc.gluon_legs())

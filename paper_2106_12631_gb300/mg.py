@@ -1,0 +1,204 @@
+"""Python binding of the C ABI in include/mg.h (argument marshalling only).
+
+Every computation runs in libmg.so's CUDA kernels; this module checks tensor
+shapes, dtypes, devices and contiguity, passes raw pointers and the current
+torch stream, and turns status codes into exceptions.  There is no CPU path:
+if the library cannot be built or loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+MG_FP64, MG_MIXED, MG_MIXED_SIMT = 0, 1, 2
+MODES = {"fp64": MG_FP64, "mixed": MG_MIXED, "mixed_simt": MG_MIXED_SIMT}
+PROCS = {"ee_mumu": 1, "gg_tt": 2, "gg_ttg": 3, "gg_ttgg": 4}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class MGError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        msg = lib().mg_status_string(status).decode()
+        if status == -5:
+            msg += " (cudaError %d)" % lib().mg_last_cuda_error()
+        super().__init__("%s: %s" % (what, msg))
+        self.status = status
+
+
+class ProcessInfo(ctypes.Structure):
+    _fields_ = [("npar", ctypes.c_int), ("nhel", ctypes.c_int), ("ncolor", ctypes.c_int),
+                ("ndiagrams", ctypes.c_int), ("namplitudes", ctypes.c_int), ("nrand", ctypes.c_int),
+                ("mass", ctypes.c_double * 8)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("mz", ctypes.c_double), ("wz", ctypes.c_double), ("alpha_inv", ctypes.c_double),
+                ("sw2", ctypes.c_double), ("mt", ctypes.c_double), ("wt", ctypes.c_double),
+                ("alpha_s", ctypes.c_double)]
+
+
+def lib():
+    """Load libmg.so (building it in-tree first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = ctypes.CDLL(path)
+            vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+            L.mg_get_process_info.argtypes = [i32, ctypes.POINTER(ProcessInfo)]
+            L.mg_set_params.argtypes = [ctypes.POINTER(Params)]
+            L.mg_get_params.argtypes = [ctypes.POINTER(Params)]
+            L.mg_rambo.argtypes = [i32, i64, ctypes.c_double, vp, i32, vp, vp, vp]
+            L.mg_filter_helicities.argtypes = [i32, i64, vp, vp, vp]
+            L.mg_sigmakin.argtypes = [i32, i64, vp, vp, vp, i32, vp]
+            L.mg_event_sum_scratch_bytes.argtypes = [i64]
+            L.mg_event_sum_scratch_bytes.restype = i64
+            L.mg_event_sum.argtypes = [i64, vp, vp, vp, vp, i64, vp]
+            L.mg_pipeline_workspace_bytes.argtypes = [i32, i64, i32]
+            L.mg_pipeline_workspace_bytes.restype = i64
+            L.mg_pipeline_host.argtypes = [i32, i64, ctypes.c_double, vp, i32, vp, i32, vp, vp, vp, i64, vp]
+            L.mg_status_string.argtypes = [i32]
+            L.mg_status_string.restype = ctypes.c_char_p
+            _lib = L
+    return _lib
+
+
+def _check(status: int, what: str):
+    if status != 0:
+        raise MGError(status, what)
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _dev(t: torch.Tensor, dtype, name: str, shape=None):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise ValueError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError("%s must have shape %s, got %s" % (name, tuple(shape), tuple(t.shape)))
+    return t.data_ptr()
+
+
+def _proc(proc) -> int:
+    return PROCS[proc] if isinstance(proc, str) else int(proc)
+
+
+def process_info(proc) -> dict:
+    info = ProcessInfo()
+    _check(lib().mg_get_process_info(_proc(proc), ctypes.byref(info)), "mg_get_process_info")
+    return {"npar": info.npar, "nhel": info.nhel, "ncolor": info.ncolor, "ndiagrams": info.ndiagrams,
+            "namplitudes": info.namplitudes, "nrand": info.nrand, "mass": list(info.mass)[: info.npar]}
+
+
+def get_params() -> dict:
+    p = Params()
+    _check(lib().mg_get_params(ctypes.byref(p)), "mg_get_params")
+    return {k: getattr(p, k) for k, _ in Params._fields_}
+
+
+def set_params(**kw):
+    d = get_params()
+    d.update(kw)
+    _check(lib().mg_set_params(ctypes.byref(Params(**d))), "mg_set_params")
+
+
+def rambo(proc, rnd: torch.Tensor, ecm: float, mom=None, wgt=None, stream=None):
+    """rnd (nrows, nevt) float64 CUDA -> (mom (npar, 4, nevt), wgt (nevt,))."""
+    p = _proc(proc)
+    nrows, nevt = rnd.shape
+    npar = process_info(p)["npar"]
+    if mom is None:
+        mom = torch.empty((npar, 4, nevt), dtype=torch.float64, device=rnd.device)
+    if wgt is None:
+        wgt = torch.empty((nevt,), dtype=torch.float64, device=rnd.device)
+    _check(lib().mg_rambo(p, nevt, float(ecm), _dev(rnd, torch.float64, "rnd"), nrows,
+                          _dev(mom, torch.float64, "mom", (npar, 4, nevt)),
+                          _dev(wgt, torch.float64, "wgt", (nevt,)), _stream(stream)), "mg_rambo")
+    return mom, wgt
+
+
+def filter_helicities(proc, mom: torch.Tensor, mask=None, stream=None) -> torch.Tensor:
+    p = _proc(proc)
+    info = process_info(p)
+    if mask is None:
+        mask = torch.empty((info["nhel"],), dtype=torch.int32, device=mom.device)
+    nevt = mom.shape[2]
+    _check(lib().mg_filter_helicities(p, nevt, _dev(mom, torch.float64, "mom", (info["npar"], 4, nevt)),
+                                      _dev(mask, torch.int32, "mask", (info["nhel"],)), _stream(stream)),
+           "mg_filter_helicities")
+    return mask
+
+
+def sigmakin(proc, mom: torch.Tensor, mask: torch.Tensor, mode="mixed", me=None, stream=None) -> torch.Tensor:
+    p = _proc(proc)
+    info = process_info(p)
+    nevt = mom.shape[2]
+    m = MODES[mode] if isinstance(mode, str) else int(mode)
+    if me is None:
+        me = torch.empty((nevt,), dtype=torch.float64, device=mom.device)
+    _check(lib().mg_sigmakin(p, nevt, _dev(mom, torch.float64, "mom", (info["npar"], 4, nevt)),
+                             _dev(mask, torch.int32, "mask", (info["nhel"],)),
+                             _dev(me, torch.float64, "me", (nevt,)), m, _stream(stream)), "mg_sigmakin")
+    return me
+
+
+def event_sum_scratch_bytes(nevt: int) -> int:
+    return int(lib().mg_event_sum_scratch_bytes(nevt))
+
+
+def event_sum(me: torch.Tensor, wgt: torch.Tensor, out=None, scratch=None, stream=None) -> torch.Tensor:
+    nevt = me.shape[0]
+    if out is None:
+        out = torch.empty((3,), dtype=torch.float64, device=me.device)
+    nb = event_sum_scratch_bytes(nevt)
+    if scratch is None:
+        scratch = torch.empty((max(nb, 16) + 7) // 8, dtype=torch.float64, device=me.device)
+    _check(lib().mg_event_sum(nevt, _dev(me, torch.float64, "me", (nevt,)),
+                              _dev(wgt, torch.float64, "wgt", (nevt,)), _dev(out, torch.float64, "out", (3,)),
+                              scratch.data_ptr(), scratch.numel() * scratch.element_size(), _stream(stream)),
+           "mg_event_sum")
+    return out
+
+
+def pipeline_workspace_bytes(proc, nevt: int, nrows: int) -> int:
+    return int(lib().mg_pipeline_workspace_bytes(_proc(proc), nevt, nrows))
+
+
+def pipeline_host(proc, rnd_host: torch.Tensor, ecm: float, mask: torch.Tensor, mode="mixed", me_host=None,
+                  wgt_host=None, workspace=None, stream=None):
+    """Host random numbers -> (H2D) RAMBO -> SIGMAKIN -> (D2H) host me.  Async on the stream;
+    synchronise before reading me_host.  rnd_host should be pinned."""
+    p = _proc(proc)
+    if rnd_host.is_cuda or rnd_host.dtype != torch.float64 or not rnd_host.is_contiguous():
+        raise ValueError("rnd_host must be a contiguous float64 CPU tensor")
+    nrows, nevt = rnd_host.shape
+    m = MODES[mode] if isinstance(mode, str) else int(mode)
+    if me_host is None:
+        me_host = torch.empty((nevt,), dtype=torch.float64, pin_memory=True)
+    nb = pipeline_workspace_bytes(p, nevt, nrows)
+    if workspace is None:
+        workspace = torch.empty(((nb + 7) // 8,), dtype=torch.float64, device=mask.device)
+    _check(lib().mg_pipeline_host(p, nevt, float(ecm), rnd_host.data_ptr(), nrows,
+                                  _dev(mask, torch.int32, "mask"), m, me_host.data_ptr(),
+                                  wgt_host.data_ptr() if wgt_host is not None else None,
+                                  workspace.data_ptr(), workspace.numel() * workspace.element_size(),
+                                  _stream(stream)), "mg_pipeline_host")
+    return me_host
+
+
+def library_path() -> str:
+    return os.path.abspath(_build.LIB)

@@ -46,3 +46,16 @@ def two_body(ecm, m, cth, phi):
     mom[3, 0] = e
     mom[3, 1:] = -k * d
     return mom
+
+
+def rambo_gamma(rnd, nfin):
+    """Lorentz factor Q0/M of the unconstrained massless system RAMBO boosts back
+    to rest; its rounding is amplified by about gamma^2 (condition estimate)."""
+    Q = np.zeros((4, rnd.shape[1]))
+    for i in range(nfin):
+        c = 2 * rnd[4 * i] - 1
+        s = np.sqrt(1 - c * c)
+        f = 2 * np.pi * rnd[4 * i + 1]
+        e = -np.log(rnd[4 * i + 2] * rnd[4 * i + 3])
+        Q += np.stack([e, e * s * np.cos(f), e * s * np.sin(f), e * c])
+    return Q[0] / np.sqrt(mdot(Q, Q))

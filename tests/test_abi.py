@@ -1,0 +1,103 @@
+"""Host-side checks of the C ABI and of the process generator (no GPU needed).
+
+* libmg.so loads and exports every function include/mg.h declares.
+* Process descriptions and host-side argument validation (these return before
+  any CUDA call).
+* The generated CUDA headers are up to date with the generator.
+* The generator's diagram counts, colour-flow coefficients and colour matrix
+  agree with the paper's counts and with the oracle's explicit-SU(3) chain
+  matrix (two independent constructions).
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2106_12631_gb300 import mg
+    return mg.lib()
+
+
+def header_functions():
+    text = open(os.path.join(ROOT, "include", "mg.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:int|int64_t|const char\*)\s+(mg_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_exports_every_declared_symbol(L):
+    names = header_functions()
+    assert len(names) >= 12
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_process_info():
+    from paper_2106_12631_gb300 import mg
+    want = {1: (4, 16, 1, 2, 8), 2: (4, 16, 2, 3, 8), 3: (5, 32, 6, 16, 12), 4: (6, 64, 24, 123, 16)}
+    for p, (npar, nhel, ncol, ndiag, nrand) in want.items():
+        info = mg.process_info(p)
+        assert (info["npar"], info["nhel"], info["ncolor"], info["ndiagrams"], info["nrand"]) == \
+            (npar, nhel, ncol, ndiag, nrand)
+    assert mg.process_info(4)["mass"] == [0, 0, 173.0, 173.0, 0, 0]
+
+
+def test_host_side_validation(L):
+    vp = ctypes.c_void_p
+    fake = 0x10000  # never dereferenced: every call below fails validation first
+    assert L.mg_sigmakin(0, 1, vp(fake), vp(fake), vp(fake), 0, None) == -2
+    assert L.mg_sigmakin(1, -5, vp(fake), vp(fake), vp(fake), 0, None) == -1
+    assert L.mg_sigmakin(1, 3, vp(fake + 4), vp(fake), vp(fake), 0, None) == -3
+    assert L.mg_sigmakin(1, 3, None, vp(fake), vp(fake), 0, None) == -1
+    assert L.mg_sigmakin(1, 0, None, None, None, 0, None) == 0  # empty batch is a no-op
+    assert L.mg_sigmakin(1, 3, vp(fake), vp(fake), vp(fake), 3, None) == -1
+    L.mg_rambo.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_double, vp, ctypes.c_int, vp, vp, vp]
+    assert L.mg_rambo(4, 8, 300.0, vp(fake), 16, vp(fake), vp(fake), None) == -1
+    assert L.mg_rambo(4, 8, 1500.0, vp(fake), 12, vp(fake), vp(fake), None) == -1
+    assert L.mg_rambo(4, 0, 1500.0, None, 16, None, None, None) == 0
+    L.mg_event_sum_scratch_bytes.restype = ctypes.c_int64
+    assert L.mg_event_sum_scratch_bytes(ctypes.c_int64(-1)) == -1
+    L.mg_status_string.restype = ctypes.c_char_p
+    assert L.mg_status_string(-3) == b"device pointer not 16-byte aligned"
+
+
+def test_params_roundtrip():
+    from paper_2106_12631_gb300 import mg
+    old = mg.get_params()
+    assert old["mt"] == 173.0 and old["alpha_s"] == 0.118
+    mg.set_params(mt=172.5)
+    assert mg.get_params()["mt"] == 172.5
+    with pytest.raises(mg.MGError):
+        mg.set_params(sw2=1.5)
+    mg.set_params(**old)
+    assert mg.get_params() == old
+
+
+def test_generated_code_up_to_date():
+    from paper_2106_12631_gb300.gen.__main__ import main
+    assert main(check=True) == 0
+
+
+@pytest.mark.parametrize("pid,ndiag,ncol", [(1, 2, 1), (2, 3, 2), (3, 16, 6), (4, 123, 24)])
+def test_generator_counts_and_coefficients(pid, ndiag, ncol):
+    from paper_2106_12631_gb300.gen import procgen
+    s = procgen.summary(pid)
+    assert s["ndiagrams"] == ndiag and s["ncolor"] == ncol
+    vals = set(complex(z) for z in s["coef"].reshape(-1) if z != 0)
+    assert vals <= {1, -1, 1j, -1j}
+    # every amplitude contributes to at least one flow, every flow gets amplitudes
+    assert np.all(np.any(s["coef"] != 0, axis=1)) and np.all(np.any(s["coef"] != 0, axis=0))
+
+
+@pytest.mark.parametrize("ng", [2, 3, 4])
+def test_generator_colour_matrix_matches_oracle(orc, ng):
+    from paper_2106_12631_gb300.gen import procgen
+    perms, num, den = procgen.chain_matrix(ng)
+    C = orc.chain_colour_matrix(ng).real
+    np.testing.assert_allclose(num / den, C, rtol=0, atol=1e-12)
+    assert np.all(np.diag(num) * 3 ** ng == den * 3 * 4 ** ng)

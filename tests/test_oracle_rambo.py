@@ -11,23 +11,13 @@ import math
 import numpy as np
 import pytest
 
-from helpers import mdot
+from helpers import mdot, rambo_gamma
 from paper_2106_12631_gb300 import inputs as I
 
 MT = I.SM_PARAMS["mt"]
 
 
-def boost_gamma(rnd, nfin):
-    """Lorentz factor Q0/M of the unconstrained system RAMBO boosts back to rest:
-    the boost amplifies rounding by about gamma^2 (condition estimate only)."""
-    Q = np.zeros((4, rnd.shape[1]))
-    for i in range(nfin):
-        c = 2 * rnd[4 * i] - 1
-        s = np.sqrt(1 - c * c)
-        f = 2 * np.pi * rnd[4 * i + 1]
-        e = -np.log(rnd[4 * i + 2] * rnd[4 * i + 3])
-        Q += np.stack([e, e * s * np.cos(f), e * s * np.sin(f), e * c])
-    return Q[0] / np.sqrt(mdot(Q, Q))
+boost_gamma = rambo_gamma
 
 
 EPS = np.finfo(float).eps
