@@ -198,9 +198,12 @@ template <class T> Vec4<T> dirac_bar(const Vec4<T>& c) {
 // Helicity eigenspinors chi_lambda(p^) of sigma.p^ with eigenvalue lambda.
 // ----------------------------------------------------------------------------
 template <class T> void helicity_chi(const Mom<T>& p, int lam, Cx<T> chi[2]) {
-  T pp = sqrt(p[1] * p[1] + p[2] * p[2] + p[3] * p[3]);
-  T ppz = pp + p[3];
-  if (val(ppz) <= 1e-14 * val(pp)) {  // momentum along -z: fixed phase choice
+  T pt2 = p[1] * p[1] + p[2] * p[2];
+  T pp = sqrt(pt2 + p[3] * p[3]);
+  // |p| + pz, written as pT^2 / (|p| - pz) for pz < 0 (the same number without
+  // cancellation for momenta close to -z)
+  T ppz = val(p[3]) >= 0 ? pp + p[3] : pt2 / (pp - p[3]);
+  if (val(ppz) <= 0.0) {  // momentum exactly along -z: fixed phase choice
     if (lam > 0) { chi[0] = Cx<T>(T(0.0)); chi[1] = Cx<T>(T(1.0)); }
     else { chi[0] = Cx<T>(T(-1.0)); chi[1] = Cx<T>(T(0.0)); }
     return;
