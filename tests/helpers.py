@@ -59,3 +59,19 @@ def rambo_gamma(rnd, nfin):
         e = -np.log(rnd[4 * i + 2] * rnd[4 * i + 3])
         Q += np.stack([e, e * s * np.cos(f), e * s * np.sin(f), e * c])
     return Q[0] / np.sqrt(mdot(Q, Q))
+
+
+ROTATIONS = (([0.3, 0.5, 0.8], 0.77), ([-0.6, 0.2, 0.1], 2.3))
+
+
+def oracle_conditioning(orc, proc, mom, prm=None, nthreads=8):
+    """Sensitivity of the FP64 oracle to rounding-level changes of the momenta:
+    the largest relative change of me under exact rotations of the event (a
+    rotation only re-rounds the inputs).  Events near a collinear or soft
+    limit cancel strongly between diagrams and show large values."""
+    me0 = orc.me(proc, mom, prm, nthreads=nthreads)
+    worst = np.zeros_like(me0)
+    for axis, ang in ROTATIONS:
+        mr = np.ascontiguousarray(np.stack([rotate(mom[l], axis, ang) for l in range(mom.shape[0])]))
+        worst = np.maximum(worst, np.abs(orc.me(proc, mr, prm, nthreads=nthreads) / me0 - 1))
+    return me0, worst

@@ -1,11 +1,15 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
 
 Bars:
-* RAMBO momenta and weights: per event within 8 eps (1 + gamma^2), gamma the
-  Lorentz factor of RAMBO's boost (its rounding is amplified by gamma^2).
-* FP64 matrix elements on identical momenta: 1e-12 relative per event.
-* Mixed precision (FP32 amplitudes, FP64 denominators and sums): max relative
-  error <= MIXED_MAX_REL, median <= MIXED_MEDIAN_REL, no NaN/Inf.
+* RAMBO momenta and weights: per event within 16 eps (1 + gamma^2), gamma the
+  Lorentz factor of RAMBO's boost: each side rounds to about 2.5 eps gamma^2.
+* FP64 matrix elements on identical momenta: 1e-12 relative per event, except
+  for events whose own FP64 conditioning is worse: there the bar is 4 d_rot,
+  d_rot = the oracle's relative change under exact rotations of the event
+  (rounding-level input changes).  At most 0.1% of events may need that.
+* Mixed precision (FP32 amplitudes, FP64 denominators and sums): median <=
+  1e-6, 99.9th percentile <= 1e-5, max <= 1e-3, no NaN/Inf; for events with
+  d_rot <= 1e-14 (well conditioned) every event is within 1e-5.
 * Helicity mask: identical to the oracle's set of non-zero helicities.
 * Event sum: 1e-14 relative to the oracle's pairwise sum, bitwise
   reproducible run to run.
@@ -14,14 +18,17 @@ import numpy as np
 import pytest
 import torch
 
-from helpers import rambo_gamma
+from helpers import oracle_conditioning, rambo_gamma
 from paper_2106_12631_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
 
 FP64_REL = 1e-12
+FP64_ILL_FRACTION = 1e-3
 MIXED_MAX_REL = 1e-3
-MIXED_MEDIAN_REL = 1e-5
+MIXED_P999_REL = 1e-5
+MIXED_MEDIAN_REL = 1e-6
+WELL_CONDITIONED = 1e-14
 EPS = np.finfo(float).eps
 NR = {1: 8, 2: 8, 3: 12, 4: 16}
 ECM = {1: 500.0, 2: 1500.0, 3: 1500.0, 4: 1500.0}
@@ -58,7 +65,7 @@ def test_rambo_parity(mg, orc, proc, nevt):
     mom, wgt = mg.rambo(proc, dev(rnd), ECM[proc])
     m_o, w_o = orc.rambo(proc, rnd, ECM[proc])
     m_g, w_g = host(mom), host(wgt)
-    tol = 8 * EPS * (1 + rambo_gamma(rnd, m_o.shape[0] - 2) ** 2)
+    tol = 16 * EPS * (1 + rambo_gamma(rnd, m_o.shape[0] - 2) ** 2)
     err = np.max(np.abs(m_g - m_o), axis=(0, 1)) / ECM[proc]
     assert np.all(err <= tol), (err / tol).max()
     assert np.all(np.abs(w_g / w_o - 1) <= tol)
@@ -80,11 +87,17 @@ def test_filter_mask(mg, orc, proc):
 def test_sigmakin_fp64_parity(mg, orc, proc, nevt):
     rnd = I.uniforms(51 + proc, NR[proc], nevt)
     mom_o, _ = orc.rambo(proc, rnd, ECM[proc])
-    me_o = orc.me(proc, mom_o, nthreads=8)
+    me_o, d_rot = oracle_conditioning(orc, proc, mom_o)
     mask = gpu_mask(mg, proc)
     me_g = host(mg.sigmakin(proc, dev(mom_o), mask, mode="fp64"))
     rel = np.abs(me_g / me_o - 1)
-    assert np.all(rel <= FP64_REL), (rel.max(), int(rel.argmax()))
+    check_fp64(rel, d_rot)
+
+
+def check_fp64(rel, d_rot):
+    tol = np.maximum(FP64_REL, 4 * d_rot)
+    assert np.all(rel <= tol), (rel.max(), int(np.argmax(rel / tol)))
+    assert np.mean(rel > FP64_REL) <= FP64_ILL_FRACTION + 1.0 / len(rel)
 
 
 @pytest.mark.parametrize("mode", ["mixed_simt", "mixed"])
@@ -92,15 +105,22 @@ def test_sigmakin_fp64_parity(mg, orc, proc, nevt):
 def test_sigmakin_mixed(mg, orc, proc, nevt, mode):
     rnd = I.uniforms(61 + proc, NR[proc], nevt)
     mom_o, _ = orc.rambo(proc, rnd, ECM[proc])
-    me_o = orc.me(proc, mom_o, nthreads=8)
+    me_o, d_rot = oracle_conditioning(orc, proc, mom_o)
     mask = gpu_mask(mg, proc)
     me_g = host(mg.sigmakin(proc, dev(mom_o), mask, mode=mode))
     assert np.all(np.isfinite(me_g))
     rel = np.abs(me_g / me_o - 1)
-    print("proc %d %s: max %.3g median %.3g p99.99 %.3g" % (proc, mode, rel.max(), np.median(rel),
-                                                          np.quantile(rel, 0.9999)))
+    print("proc %d %s: max %.3g median %.3g p99.9 %.3g (well-conditioned max %.3g)"
+          % (proc, mode, rel.max(), np.median(rel), np.quantile(rel, 0.999),
+             rel[d_rot <= WELL_CONDITIONED].max()))
+    check_mixed(rel, d_rot)
+
+
+def check_mixed(rel, d_rot):
     assert rel.max() <= MIXED_MAX_REL
+    assert np.quantile(rel, 0.999) <= MIXED_P999_REL
     assert np.median(rel) <= MIXED_MEDIAN_REL
+    assert np.all(rel[d_rot <= WELL_CONDITIONED] <= MIXED_P999_REL)
 
 
 @pytest.mark.parametrize("proc", [1, 3, 4])
@@ -115,9 +135,11 @@ def test_mask_subset(mg, orc, proc):
     sub = (rng.uniform(size=nhel) < 0.4).astype(np.int32)
     sub[1] = 1
     want = ph[sub == 1].sum(axis=0)
+    _, d_rot = oracle_conditioning(orc, proc, mom_o)
     me_g = host(mg.sigmakin(proc, dev(mom_o), dev(sub), mode="fp64"))
     ok = want != 0
-    np.testing.assert_allclose(me_g[ok], want[ok], rtol=FP64_REL)
+    rel = np.abs(me_g[ok] / want[ok] - 1)
+    assert np.all(rel <= np.maximum(FP64_REL, 4 * d_rot[ok]))
     assert np.all(me_g[~ok] == 0)
 
 
@@ -175,11 +197,14 @@ def test_full_size_sampled(mg, orc, mode):
     me_g = host(me)[idx]
     r = I.uniforms_at(seed, 16, idx)
     mom_o, _ = orc.rambo(4, r, 1500.0)
-    tol = 8 * EPS * (1 + rambo_gamma(r, 4) ** 2)
+    tol = 16 * EPS * (1 + rambo_gamma(r, 4) ** 2)
     assert np.all(np.max(np.abs(mom_g - mom_o), axis=(0, 1)) / 1500.0 <= tol)
-    me_o = orc.me(4, np.ascontiguousarray(mom_g), nthreads=8)
+    me_o, d_rot = oracle_conditioning(orc, 4, np.ascontiguousarray(mom_g))
     rel = np.abs(me_g / me_o - 1)
-    assert rel.max() <= (FP64_REL if mode == "fp64" else MIXED_MAX_REL)
+    if mode == "fp64":
+        assert np.all(rel <= np.maximum(FP64_REL, 4 * d_rot))
+    else:
+        assert rel.max() <= MIXED_MAX_REL and np.all(rel[d_rot <= WELL_CONDITIONED] <= MIXED_P999_REL)
     s = host(out)
     assert s[2] == nevt and np.isfinite(s[0]) and s[0] > 0
 
