@@ -124,6 +124,24 @@ int64_t mg_event_sum_scratch_bytes(int64_t nevt);
 int mg_event_sum(int64_t nevt, const double* me, const double* wgt, double* out3, void* scratch,
                  int64_t scratch_bytes, void* stream);
 
+/* The event sum above without caller scratch, for callers that cannot
+ * allocate device memory: code that runs while a stream is being captured into
+ * a CUDA graph (cudaMalloc is not allowed there), host programs whose device
+ * memory is owned by another framework's pool, or integrator loops that must
+ * not trigger the device-wide synchronisation a cudaMalloc/cudaFree can cause.
+ * The paper has no counterpart; this is a convenience of this library.
+ * The partial sums live in a fixed array compiled into libmg.so, on every
+ * device that loads the library, kept until the process exits: room for
+ * mg_event_sum_noalloc_max_events() = 2^26 events (256 KiB per device).
+ * Larger nevt returns MG_ERR_SPACE and launches nothing.  The call allocates
+ * nothing.  Its first call on a device looks up that array's device address
+ * (once per device, with the device current), so make the first call before
+ * any stream capture.  All calls share the array: calls that overlap on the
+ * GPU (two streams, two host threads) race and give wrong sums; serialise
+ * them.  Results are identical to mg_event_sum's. */
+int64_t mg_event_sum_noalloc_max_events(void);
+int mg_event_sum_noalloc(int64_t nevt, const double* me, const double* wgt, double* out3, void* stream);
+
 /* End-to-end pipeline from HOST buffers (copies inside): h_rnd [nrows][nevt]
  * -> host-to-device copy -> RAMBO -> SIGMAKIN (mask from mg_filter_helicities,
  * on the device) -> device-to-host copy of me (and wgt if h_wgt != NULL).

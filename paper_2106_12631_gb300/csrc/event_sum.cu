@@ -6,6 +6,7 @@
 // Pass 1: block b sums events [b*CHUNK, (b+1)*CHUNK) -> partial[b] (2 doubles)
 // in caller-provided scratch; pass 2: one block reduces the partials.
 #include <cstdint>
+#include <mutex>
 
 #include "launch.h"
 
@@ -73,6 +74,53 @@ int64_t event_sum_blocks(int64_t n) { return n > 0 ? (n + kSumChunk - 1) / kSumC
 
 cudaError_t launch_event_sum(int64_t n, const double* me, const double* w, double* out3, double* partial,
                              cudaStream_t s) {
+  const int64_t nblk = event_sum_blocks(n);
+  if (nblk > 0) event_sum_pass1<<<(unsigned)nblk, kSumThreads, 0, s>>>(n, me, w, partial);
+  event_sum_pass2<<<1, kSumThreads, 0, s>>>(nblk, partial, out3, n);
+  return cudaGetLastError();
+}
+
+// ---- allocation-free variant --------------------------------------------
+// Partials live in a fixed device array instead of caller scratch, for callers
+// that cannot allocate device memory.  One array per loaded library on every
+// device, shared by all calls; pass 1 writes every partial pass 2 reads, so no
+// clearing is needed, but calls that overlap on the GPU (e.g. on two streams)
+// race on it.
+constexpr int64_t kNoAllocMaxEvents = int64_t(1) << 26;
+constexpr int64_t kNoAllocMaxBlocks = kNoAllocMaxEvents / kSumChunk;
+static __device__ __align__(256) double g_noalloc_partials[2 * kNoAllocMaxBlocks];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[kMaxDevices] = {};
+}  // namespace
+
+int64_t event_sum_noalloc_max_events() { return kNoAllocMaxEvents; }
+
+// Device address of the array on the current device, looked up once per
+// device (the host-side symbol is only a stand-in and must not be passed to a
+// kernel).
+cudaError_t event_sum_noalloc_scratch(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> g(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+
+cudaError_t launch_event_sum_noalloc(int64_t n, const double* me, const double* w, double* out3, cudaStream_t s) {
+  double* partial = nullptr;
+  cudaError_t e = event_sum_noalloc_scratch(&partial);
+  if (e != cudaSuccess) return e;
   const int64_t nblk = event_sum_blocks(n);
   if (nblk > 0) event_sum_pass1<<<(unsigned)nblk, kSumThreads, 0, s>>>(n, me, w, partial);
   event_sum_pass2<<<1, kSumThreads, 0, s>>>(nblk, partial, out3, n);

@@ -31,6 +31,8 @@ cudaError_t launch_rambo(int nfinal, int64_t nevt, double ecm, const double* rnd
 int64_t event_sum_blocks(int64_t n);
 cudaError_t launch_event_sum(int64_t n, const double* me, const double* w, double* out3, double* partial,
                              cudaStream_t s);
+int64_t event_sum_noalloc_max_events();
+cudaError_t launch_event_sum_noalloc(int64_t n, const double* me, const double* w, double* out3, cudaStream_t s);
 
 // mode: 0 FP64, 1 mixed (tensor-core colour sum), 2 mixed (CUDA-core colour sum)
 cudaError_t launch_sigmakin_p1(const SigLaunch& a, int mode, cudaStream_t s);

@@ -224,6 +224,16 @@ int mg_event_sum(int64_t nevt, const double* me, const double* wgt, double* out3
   return cuda_status(mg::launch_event_sum(nevt, me, wgt, out3, (double*)scratch, (cudaStream_t)stream));
 }
 
+int64_t mg_event_sum_noalloc_max_events(void) { return mg::event_sum_noalloc_max_events(); }
+
+int mg_event_sum_noalloc(int64_t nevt, const double* me, const double* wgt, double* out3, void* stream) {
+  if (nevt < 0 || !out3) return MG_ERR_ARG;
+  if (nevt > mg::event_sum_noalloc_max_events()) return MG_ERR_SPACE;
+  if (nevt > 0 && (!me || !wgt)) return MG_ERR_ARG;
+  if (!aligned(out3) || (me && !aligned(me)) || (wgt && !aligned(wgt))) return MG_ERR_ALIGN;
+  return cuda_status(mg::launch_event_sum_noalloc(nevt, me, wgt, out3, (cudaStream_t)stream));
+}
+
 int64_t mg_pipeline_workspace_bytes(int proc, int64_t nevt, int nrows) {
   if (!valid_proc(proc) || nevt < 0 || nrows < 0) return -1;
   const int64_t n = nevt;

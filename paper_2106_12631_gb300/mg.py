@@ -61,6 +61,9 @@ def lib():
             L.mg_event_sum_scratch_bytes.argtypes = [i64]
             L.mg_event_sum_scratch_bytes.restype = i64
             L.mg_event_sum.argtypes = [i64, vp, vp, vp, vp, i64, vp]
+            L.mg_event_sum_noalloc_max_events.argtypes = []
+            L.mg_event_sum_noalloc_max_events.restype = i64
+            L.mg_event_sum_noalloc.argtypes = [i64, vp, vp, vp, vp]
             L.mg_pipeline_workspace_bytes.argtypes = [i32, i64, i32]
             L.mg_pipeline_workspace_bytes.restype = i64
             L.mg_pipeline_host.argtypes = [i32, i64, ctypes.c_double, vp, i32, vp, i32, vp, vp, vp, i64, vp]
@@ -171,6 +174,18 @@ def event_sum(me: torch.Tensor, wgt: torch.Tensor, out=None, scratch=None, strea
                               _dev(wgt, torch.float64, "wgt", (nevt,)), _dev(out, torch.float64, "out", (3,)),
                               scratch.data_ptr(), scratch.numel() * scratch.element_size(), _stream(stream)),
            "mg_event_sum")
+    return out
+
+
+def event_sum_noalloc(me: torch.Tensor, wgt: torch.Tensor, out=None, stream=None) -> torch.Tensor:
+    """event_sum without caller scratch (fixed library-owned array; see include/mg.h)."""
+    nevt = me.shape[0]
+    if out is None:
+        out = torch.empty((3,), dtype=torch.float64, device=me.device)
+    _check(lib().mg_event_sum_noalloc(nevt, _dev(me, torch.float64, "me", (nevt,)),
+                                      _dev(wgt, torch.float64, "wgt", (nevt,)),
+                                      _dev(out, torch.float64, "out", (3,)), _stream(stream)),
+           "mg_event_sum_noalloc")
     return out
 
 
