@@ -4,6 +4,8 @@
 // colour-flow coefficients used: [(1+0j)]
 #pragma once
 namespace mg {
+// colour-matrix numerators as the BF16 B operand of the tensor-core colour sum
+static __device__ __align__(16) const uint32_t kColourB1[128] = {0x00003f80, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000};
 struct Proc1 {
   static constexpr int NPAR = 4;
   static constexpr int NHEL = 16;
@@ -27,17 +29,19 @@ struct Proc1 {
     constexpr int t[NPROP][2] = {{4, 2}, {4, 3}};
     return t[j][k];
   }
+  static __device__ __forceinline__ const uint32_t* colour_bf16_image() { return kColourB1; }
   // colour matrix = CNUM / CDEN (real symmetric)
   static constexpr int CDEN = 1;
   static __host__ __device__ constexpr int cnum(int i, int j) {
     constexpr int t[NCOLOR][NCOLOR] = {{1}};
     return t[i][j];
   }
-  // dual amplitudes J[NCOLOR] of one helicity combination (hel[k] = +-1)
-  template <class R>
-  static __device__ __forceinline__ void amplitudes(const R* __restrict__ K, const cx<R>* __restrict__ prop, const int* hel, const Couplings<R>& cp, cx<R>* J) {
-    #pragma unroll
-    for (int s = 0; s < NCOLOR; ++s) J[s] = cx<R>(R(0), R(0));
+  // Dual amplitudes J_s of one helicity combination (hel[k] = +-1), accumulated
+  // through J.add/sub/addi/subi(s, amp) (J_s += amp, -amp, i amp, -i amp);
+  // Lock::sync() marks points where a CTA may re-align its warps.
+  template <class R, class Acc, class Lock>
+  static __device__ __forceinline__ void amplitudes(const R* __restrict__ K, const cx<R>* __restrict__ prop, const int* hel, const Couplings<R>& cp, Acc& J) {
+    J.zero();
   cx<R> amp;
   const W4<R> w2 = ixxxxx<R>(K + 8, R(0), hel[2], -1);
   const W4<R> w0 = oxxxxx<R>(K + 0, R(0), hel[0], -1);
@@ -45,10 +49,11 @@ struct Proc1 {
   const W4<R> w3 = FFV1P0_3<R>(w0, w1, cp.ee, prop[0]);
   const W4<R> w5 = oxxxxx<R>(K + 12, R(0), hel[3], 1);
   amp = FFV1_0<R>(w5, w2, w3, cp.ee);
-  J[0] += amp;
+  J.add(0, amp);
   const W4<R> w4 = FFV2_4_3<R>(w0, w1, cp.gz, cp.gzl, cp.gzr, prop[1]);
   amp = FFV2_4_0<R>(w5, w2, w4, cp.gz, cp.gzl, cp.gzr);
-  J[0] += amp;
+  Lock::sync();
+  J.add(0, amp);
   }
 };
 }  // namespace mg

@@ -4,6 +4,8 @@
 // colour-flow coefficients used: [-1j, 1j, (1+0j)]
 #pragma once
 namespace mg {
+// colour-matrix numerators as the BF16 B operand of the tensor-core colour sum
+static __device__ __align__(16) const uint32_t kColourB2[128] = {0xc0004180, 0x00000000, 0x00000000, 0x00000000, 0x4180c000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000};
 struct Proc2 {
   static constexpr int NPAR = 4;
   static constexpr int NHEL = 16;
@@ -27,17 +29,19 @@ struct Proc2 {
     constexpr int t[NPROP][2] = {{6, 0}, {7, 1}, {8, 1}};
     return t[j][k];
   }
+  static __device__ __forceinline__ const uint32_t* colour_bf16_image() { return kColourB2; }
   // colour matrix = CNUM / CDEN (real symmetric)
   static constexpr int CDEN = 3;
   static __host__ __device__ constexpr int cnum(int i, int j) {
     constexpr int t[NCOLOR][NCOLOR] = {{16, -2}, {-2, 16}};
     return t[i][j];
   }
-  // dual amplitudes J[NCOLOR] of one helicity combination (hel[k] = +-1)
-  template <class R>
-  static __device__ __forceinline__ void amplitudes(const R* __restrict__ K, const cx<R>* __restrict__ prop, const int* hel, const Couplings<R>& cp, cx<R>* J) {
-    #pragma unroll
-    for (int s = 0; s < NCOLOR; ++s) J[s] = cx<R>(R(0), R(0));
+  // Dual amplitudes J_s of one helicity combination (hel[k] = +-1), accumulated
+  // through J.add/sub/addi/subi(s, amp) (J_s += amp, -amp, i amp, -i amp);
+  // Lock::sync() marks points where a CTA may re-align its warps.
+  template <class R, class Acc, class Lock>
+  static __device__ __forceinline__ void amplitudes(const R* __restrict__ K, const cx<R>* __restrict__ prop, const int* hel, const Couplings<R>& cp, Acc& J) {
+    J.zero();
   cx<R> amp;
   const W4<R> w9 = ixxxxx<R>(K + 12, cp.mt, hel[3], -1);
   const W4<R> w0 = vxxxxx<R>(K + 0, hel[0], 1);
@@ -45,14 +49,15 @@ struct Proc2 {
   const W4<R> w5 = VVV1P0_1<R>(w0, w1, K + 16, K + 20, cp.gs, prop[0]);
   const W4<R> w2 = oxxxxx<R>(K + 8, cp.mt, hel[2], 1);
   amp = FFV1_0<R>(w2, w9, w5, cp.gs);
-  J[0] -= mul_i(amp);
-  J[1] += mul_i(amp);
+  J.subi(0, amp);
+  J.addi(1, amp);
   const W4<R> w7 = FFV1_2<R>(w2, w0, cp.gs, K + 28, cp.mt, prop[1]);
   amp = FFV1_0<R>(w7, w9, w1, cp.gs);
-  J[0] += amp;
+  Lock::sync();
+  J.add(0, amp);
   const W4<R> w3 = FFV1_2<R>(w2, w1, cp.gs, K + 32, cp.mt, prop[2]);
   amp = FFV1_0<R>(w3, w9, w0, cp.gs);
-  J[1] += amp;
+  J.add(1, amp);
   }
 };
 }  // namespace mg

@@ -4,6 +4,8 @@
 // colour-flow coefficients used: [(-1+0j), -1j, 1j, (1+0j)]
 #pragma once
 namespace mg {
+// colour-matrix numerators as the BF16 B operand of the tensor-core colour sum
+static __device__ __align__(16) const uint32_t kColourB3[128] = {0xc1004280, 0x3f80c100, 0x41203f80, 0x00000000, 0x4280c100, 0x41203f80, 0x3f80c100, 0x00000000, 0x3f80c100, 0xc1004280, 0x3f804120, 0x00000000, 0x41203f80, 0x4280c100, 0xc1003f80, 0x00000000, 0xc1003f80, 0x3f804120, 0xc1004280, 0x00000000, 0x3f804120, 0xc1003f80, 0x4280c100, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000};
 struct Proc3 {
   static constexpr int NPAR = 5;
   static constexpr int NHEL = 32;
@@ -27,17 +29,19 @@ struct Proc3 {
     constexpr int t[NPROP][2] = {{5, 0}, {8, 0}, {10, 1}, {11, 1}, {12, 1}, {13, 1}, {14, 0}, {15, 1}, {16, 0}, {17, 1}};
     return t[j][k];
   }
+  static __device__ __forceinline__ const uint32_t* colour_bf16_image() { return kColourB3; }
   // colour matrix = CNUM / CDEN (real symmetric)
   static constexpr int CDEN = 9;
   static __host__ __device__ constexpr int cnum(int i, int j) {
     constexpr int t[NCOLOR][NCOLOR] = {{64, -8, -8, 1, 1, 10}, {-8, 64, 1, 10, -8, 1}, {-8, 1, 64, -8, 10, 1}, {1, 10, -8, 64, 1, -8}, {1, -8, 10, 1, 64, -8}, {10, 1, 1, -8, -8, 64}};
     return t[i][j];
   }
-  // dual amplitudes J[NCOLOR] of one helicity combination (hel[k] = +-1)
-  template <class R>
-  static __device__ __forceinline__ void amplitudes(const R* __restrict__ K, const cx<R>* __restrict__ prop, const int* hel, const Couplings<R>& cp, cx<R>* J) {
-    #pragma unroll
-    for (int s = 0; s < NCOLOR; ++s) J[s] = cx<R>(R(0), R(0));
+  // Dual amplitudes J_s of one helicity combination (hel[k] = +-1), accumulated
+  // through J.add/sub/addi/subi(s, amp) (J_s += amp, -amp, i amp, -i amp);
+  // Lock::sync() marks points where a CTA may re-align its warps.
+  template <class R, class Acc, class Lock>
+  static __device__ __forceinline__ void amplitudes(const R* __restrict__ K, const cx<R>* __restrict__ prop, const int* hel, const Couplings<R>& cp, Acc& J) {
+    J.zero();
   cx<R> amp;
   const W4<R> w43 = ixxxxx<R>(K + 12, cp.mt, hel[3], -1);
   const W4<R> w0 = vxxxxx<R>(K + 0, hel[0], 1);
@@ -46,85 +50,90 @@ struct Proc3 {
   const W4<R> w28 = VVVV1P0_1<R>(w0, w1, w3, cp.gs2, prop[0]);
   const W4<R> w2 = oxxxxx<R>(K + 8, cp.mt, hel[2], 1);
   amp = FFV1_0<R>(w2, w43, w28, cp.gs);
-  J[0] -= amp;
-  J[2] += amp;
-  J[4] += amp;
-  J[5] -= amp;
+  J.sub(0, amp);
+  J.add(2, amp);
+  J.add(4, amp);
+  J.sub(5, amp);
   const W4<R> w29 = VVVV3P0_1<R>(w0, w1, w3, cp.gs2, prop[0]);
+  Lock::sync();
   amp = FFV1_0<R>(w2, w43, w29, cp.gs);
-  J[1] -= amp;
-  J[2] += amp;
-  J[3] -= amp;
-  J[4] += amp;
+  J.sub(1, amp);
+  J.add(2, amp);
+  J.sub(3, amp);
+  J.add(4, amp);
   const W4<R> w30 = VVVV4P0_1<R>(w0, w1, w3, cp.gs2, prop[0]);
   amp = FFV1_0<R>(w2, w43, w30, cp.gs);
-  J[0] += amp;
-  J[1] -= amp;
-  J[3] -= amp;
-  J[5] += amp;
+  J.add(0, amp);
+  J.sub(1, amp);
+  J.sub(3, amp);
+  J.add(5, amp);
   const W4<R> w8 = VVV1P0_1<R>(w1, w3, K + 24, K + 28, cp.gs, prop[1]);
   const W4<R> w25 = VVV1P0_1<R>(w0, w8, K + 36, K + 32, cp.gs, prop[0]);
   amp = FFV1_0<R>(w2, w43, w25, cp.gs);
-  J[0] -= amp;
-  J[1] += amp;
-  J[3] += amp;
-  J[5] -= amp;
+  J.sub(0, amp);
+  J.add(1, amp);
+  J.add(3, amp);
+  J.sub(5, amp);
   const W4<R> w15 = FFV1_2<R>(w2, w0, cp.gs, K + 40, cp.mt, prop[2]);
   amp = FFV1_0<R>(w15, w43, w8, cp.gs);
-  J[0] -= mul_i(amp);
-  J[1] += mul_i(amp);
+  Lock::sync();
+  J.subi(0, amp);
+  J.addi(1, amp);
   const W4<R> w9 = FFV1_2<R>(w2, w8, cp.gs, K + 44, cp.mt, prop[3]);
   amp = FFV1_0<R>(w9, w43, w0, cp.gs);
-  J[3] -= mul_i(amp);
-  J[5] += mul_i(amp);
+  J.subi(3, amp);
+  J.addi(5, amp);
   const W4<R> w21 = FFV1_2<R>(w15, w1, cp.gs, K + 48, cp.mt, prop[4]);
   amp = FFV1_0<R>(w21, w43, w3, cp.gs);
-  J[0] += amp;
+  J.add(0, amp);
   const W4<R> w38 = FFV1_2<R>(w15, w3, cp.gs, K + 52, cp.mt, prop[5]);
   amp = FFV1_0<R>(w38, w43, w1, cp.gs);
-  J[1] += amp;
+  J.add(1, amp);
   const W4<R> w13 = VVV1P0_1<R>(w0, w1, K + 36, K + 24, cp.gs, prop[6]);
   const W4<R> w26 = VVV1P0_1<R>(w13, w3, K + 56, K + 28, cp.gs, prop[0]);
+  Lock::sync();
   amp = FFV1_0<R>(w2, w43, w26, cp.gs);
-  J[0] -= amp;
-  J[2] += amp;
-  J[4] += amp;
-  J[5] -= amp;
+  J.sub(0, amp);
+  J.add(2, amp);
+  J.add(4, amp);
+  J.sub(5, amp);
   const W4<R> w4 = FFV1_2<R>(w2, w3, cp.gs, K + 60, cp.mt, prop[7]);
   amp = FFV1_0<R>(w4, w43, w13, cp.gs);
-  J[4] -= mul_i(amp);
-  J[5] += mul_i(amp);
+  J.subi(4, amp);
+  J.addi(5, amp);
   const W4<R> w20 = FFV1_2<R>(w2, w13, cp.gs, K + 48, cp.mt, prop[4]);
   amp = FFV1_0<R>(w20, w43, w3, cp.gs);
-  J[0] -= mul_i(amp);
-  J[2] += mul_i(amp);
+  J.subi(0, amp);
+  J.addi(2, amp);
   const W4<R> w37 = FFV1_2<R>(w4, w0, cp.gs, K + 52, cp.mt, prop[5]);
   amp = FFV1_0<R>(w37, w43, w1, cp.gs);
-  J[4] += amp;
+  J.add(4, amp);
   const W4<R> w5 = FFV1_2<R>(w4, w1, cp.gs, K + 44, cp.mt, prop[3]);
+  Lock::sync();
   amp = FFV1_0<R>(w5, w43, w0, cp.gs);
-  J[5] += amp;
+  J.add(5, amp);
   const W4<R> w17 = VVV1P0_1<R>(w0, w3, K + 36, K + 28, cp.gs, prop[8]);
   const W4<R> w27 = VVV1P0_1<R>(w17, w1, K + 64, K + 24, cp.gs, prop[0]);
   amp = FFV1_0<R>(w2, w43, w27, cp.gs);
-  J[1] -= amp;
-  J[2] += amp;
-  J[3] -= amp;
-  J[4] += amp;
+  J.sub(1, amp);
+  J.add(2, amp);
+  J.sub(3, amp);
+  J.add(4, amp);
   const W4<R> w6 = FFV1_2<R>(w2, w1, cp.gs, K + 68, cp.mt, prop[9]);
   amp = FFV1_0<R>(w6, w43, w17, cp.gs);
-  J[2] -= mul_i(amp);
-  J[3] += mul_i(amp);
+  J.subi(2, amp);
+  J.addi(3, amp);
   const W4<R> w39 = FFV1_2<R>(w2, w17, cp.gs, K + 52, cp.mt, prop[5]);
   amp = FFV1_0<R>(w39, w43, w1, cp.gs);
-  J[1] -= mul_i(amp);
-  J[4] += mul_i(amp);
+  Lock::sync();
+  J.subi(1, amp);
+  J.addi(4, amp);
   const W4<R> w19 = FFV1_2<R>(w6, w0, cp.gs, K + 48, cp.mt, prop[4]);
   amp = FFV1_0<R>(w19, w43, w3, cp.gs);
-  J[2] += amp;
+  J.add(2, amp);
   const W4<R> w7 = FFV1_2<R>(w6, w3, cp.gs, K + 44, cp.mt, prop[3]);
   amp = FFV1_0<R>(w7, w43, w0, cp.gs);
-  J[3] += amp;
+  J.add(3, amp);
   }
 };
 }  // namespace mg

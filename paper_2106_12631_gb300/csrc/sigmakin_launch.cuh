@@ -6,35 +6,60 @@
 
 namespace mg {
 
+template <class P, class R, int CS>
+cudaError_t launch_sigmakin_variant(const SigArgs& a, const Couplings<R>& cp, int64_t grid, cudaStream_t s) {
+  using L = SigLayout<P, R, CS>;
+  auto k = sigmakin_kernel<P, R, CS>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
+  if (e != cudaSuccess) return e;
+  k<<<(unsigned)grid, SigCfg<P>::NT, L::bytes, s>>>(a, cp);
+  return cudaGetLastError();
+}
+
 template <class P>
 cudaError_t launch_sigmakin_impl(const SigLaunch& l, int mode, cudaStream_t s) {
   SigArgs a{l.nevt, l.mom, l.mask, l.me, l.mask_out, l.pp};
   const int64_t grid = (l.nevt + SigCfg<P>::EVMIN - 1) / SigCfg<P>::EVMIN;
   if (grid == 0) return cudaSuccess;
   switch (mode) {
-    case 0: sigmakin_kernel<P, double><<<(unsigned)grid, kSigmaThreads, 0, s>>>(a, l.cd); break;
-    case 1:
-    case 2: sigmakin_kernel<P, float><<<(unsigned)grid, kSigmaThreads, 0, s>>>(a, l.cf); break;
-    default: return cudaErrorInvalidValue;
+    case 0: return launch_sigmakin_variant<P, double, CS_SIMT>(a, l.cd, grid, s);
+    case 1: return launch_sigmakin_variant<P, float, CS_TC>(a, l.cf, grid, s);
+    case 2: return launch_sigmakin_variant<P, float, CS_SIMT>(a, l.cf, grid, s);
   }
-  return cudaGetLastError();
+  return cudaErrorInvalidValue;
 }
 
 template <class P>
 cudaError_t launch_filter_impl(const SigLaunch& l, cudaStream_t s) {
+  using L = SigLayout<P, double, CS_SIMT>;
   SigArgs a{l.nevt, l.mom, l.mask, l.me, l.mask_out, l.pp};
   const int64_t grid = (l.nevt + SigCfg<P>::EVMIN - 1) / SigCfg<P>::EVMIN;
   if (grid == 0) return cudaSuccess;
-  filter_kernel<P><<<(unsigned)grid, kSigmaThreads, 0, s>>>(a, l.cd);
+  auto k = filter_kernel<P>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
+  if (e != cudaSuccess) return e;
+  k<<<(unsigned)grid, SigCfg<P>::NT, L::bytes, s>>>(a, l.cd);
   return cudaGetLastError();
 }
 
 }  // namespace mg
 
-#define MG_DEFINE_PROCESS_LAUNCHERS(N)                                                              \
-  namespace mg {                                                                                     \
-  cudaError_t launch_sigmakin_p##N(const SigLaunch& a, int mode, cudaStream_t s) {                  \
-    return launch_sigmakin_impl<Proc##N>(a, mode, s);                                                \
-  }                                                                                                  \
+// The FP64 kernels of a process (sum and filter) are instantiated in their own
+// translation unit (MG_INSTANTIATE_FP64), the FP32 ones with the dispatcher.
+#define MG_DEFINE_PROCESS_LAUNCHERS(N)                                                                  \
+  namespace mg {                                                                                         \
+  extern template cudaError_t launch_sigmakin_variant<Proc##N, double, CS_SIMT>(                        \
+      const SigArgs&, const Couplings<double>&, int64_t, cudaStream_t);                                  \
+  extern template cudaError_t launch_filter_impl<Proc##N>(const SigLaunch&, cudaStream_t);              \
+  cudaError_t launch_sigmakin_p##N(const SigLaunch& a, int mode, cudaStream_t s) {                      \
+    return launch_sigmakin_impl<Proc##N>(a, mode, s);                                                    \
+  }                                                                                                      \
   cudaError_t launch_filter_p##N(const SigLaunch& a, cudaStream_t s) { return launch_filter_impl<Proc##N>(a, s); } \
+  }
+
+#define MG_INSTANTIATE_FP64(N)                                                                          \
+  namespace mg {                                                                                         \
+  template cudaError_t launch_sigmakin_variant<Proc##N, double, CS_SIMT>(                               \
+      const SigArgs&, const Couplings<double>&, int64_t, cudaStream_t);                                  \
+  template cudaError_t launch_filter_impl<Proc##N>(const SigLaunch&, cudaStream_t);                     \
   }

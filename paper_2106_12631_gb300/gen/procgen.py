@@ -375,6 +375,9 @@ def colour_sum_flops(cnum) -> int:
     return 4 * nz + 4 * cnum.shape[0] + 1
 
 
+LOCK_EVERY = 8  # routine calls between CTA-wide lockstep points
+
+
 class Emitter:
     """Straight-line device code for one process."""
 
@@ -492,6 +495,7 @@ class Emitter:
         order, need = self.schedule()
         var = {}
         self.flops = 0
+        ncalls = 0
         body = ["  cx<R> amp;"]
         for d in order:
             a = p.amps[d]
@@ -501,6 +505,9 @@ class Emitter:
                     line = self._current_code(p.cur[i], var)
                     self.flops += FLOPS[line.split("=")[1].split("<")[0].strip()]
                     body.append(line)
+                    ncalls += 1
+                    if ncalls % LOCK_EVERY == 0:
+                        body.append("  Lock::sync();")
             if a.vertex == "ffv_t":
                 body.append("  amp = FFV1_0<R>(%s, %s, %s, cp.gs);" % (var[a.row], var[a.col], var[a.bos]))
             elif a.vertex == "ffv_a":
@@ -509,6 +516,9 @@ class Emitter:
                 body.append("  amp = FFV2_4_0<R>(%s, %s, %s, cp.gz, cp.gzl, cp.gzr);"
                             % (var[a.row], var[a.col], var[a.bos]))
             self.flops += FLOPS["FFV2_4_0" if a.vertex == "ffz" else "FFV1_0"]
+            ncalls += 1
+            if ncalls % LOCK_EVERY == 0:
+                body.append("  Lock::sync();")
             for s_ in np.nonzero(self.coef[d])[0]:
                 body.append("  " + self._accum(s_, self.coef[d, s_]))
                 self.flops += FLOPS["jamp"]
@@ -527,14 +537,33 @@ class Emitter:
     def _accum(s, z):
         z = complex(z)
         if z == 1:
-            return "J[%d] += amp;" % s
+            return "J.add(%d, amp);" % s
         if z == -1:
-            return "J[%d] -= amp;" % s
+            return "J.sub(%d, amp);" % s
         if z == 1j:
-            return "J[%d] += mul_i(amp);" % s
+            return "J.addi(%d, amp);" % s
         if z == -1j:
-            return "J[%d] -= mul_i(amp);" % s
-        return "J[%d] += %s * amp;" % (s, _cpx(z))
+            return "J.subi(%d, amp);" % s
+        raise ValueError("colour-flow coefficient %r outside {+-1, +-i}" % z)
+
+
+def bf16_colour_image(cnum) -> np.ndarray:
+    """B operand of the tensor-core colour sum: B[n][k] = cnum[k][n] in BF16,
+    laid out in the canonical K-major no-swizzle layout (8-row x 16-byte core
+    matrices; K-adjacent core matrices 128 bytes apart, 8-row groups KP*16
+    bytes apart), as little-endian 32-bit words."""
+    nc = cnum.shape[0]
+    kp = (nc + 15) // 16 * 16
+    img = np.zeros(kp * kp, dtype=np.uint16)  # NP = KP rows
+    for n in range(kp):
+        for k in range(kp):
+            v = np.float32(cnum[k, n] if (n < nc and k < nc) else 0)
+            bits = int(np.array([v], dtype=np.float32).view(np.uint32)[0])
+            if bits & 0xFFFF:
+                raise ValueError("colour numerator %r not exact in BF16" % float(v))
+            off = (n >> 3) * (kp // 8) * 128 + (k >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2
+            img[off // 2] = bits >> 16
+    return img.view(np.uint32)
 
 
 def generate(pid: int) -> str:
@@ -557,6 +586,10 @@ def generate(pid: int) -> str:
     out.append("// colour-flow coefficients used: %s" % sorted(coefs, key=lambda z: (z.real, z.imag)))
     out.append("#pragma once")
     out.append("namespace mg {")
+    img = bf16_colour_image(em.cnum)
+    out.append("// colour-matrix numerators as the BF16 B operand of the tensor-core colour sum")
+    out.append("static __device__ __align__(16) const uint32_t kColourB%d[%d] = {%s};"
+               % (pid, img.size, ", ".join("0x%08x" % int(w) for w in img)))
     out.append("struct Proc%d {" % pid)
     out.append("  static constexpr int NPAR = %d;" % proc.n)
     out.append("  static constexpr int NHEL = %d;" % (1 << proc.n))
@@ -600,6 +633,7 @@ def generate(pid: int) -> str:
     out.append("    constexpr int t[NPROP][2] = {%s};" % ", ".join(prows))
     out.append("    return t[j][k];")
     out.append("  }")
+    out.append("  static __device__ __forceinline__ const uint32_t* colour_bf16_image() { return kColourB%d; }" % pid)
     out.append("  // colour matrix = CNUM / CDEN (real symmetric)")
     out.append("  static constexpr int CDEN = %d;" % em.cden)
     out.append("  static __host__ __device__ constexpr int cnum(int i, int j) {")
@@ -607,12 +641,13 @@ def generate(pid: int) -> str:
                % ", ".join("{" + ", ".join(str(int(x)) for x in row) + "}" for row in em.cnum))
     out.append("    return t[i][j];")
     out.append("  }")
-    out.append("  // dual amplitudes J[NCOLOR] of one helicity combination (hel[k] = +-1)")
-    out.append("  template <class R>")
+    out.append("  // Dual amplitudes J_s of one helicity combination (hel[k] = +-1), accumulated")
+    out.append("  // through J.add/sub/addi/subi(s, amp) (J_s += amp, -amp, i amp, -i amp);")
+    out.append("  // Lock::sync() marks points where a CTA may re-align its warps.")
+    out.append("  template <class R, class Acc, class Lock>")
     out.append("  static __device__ __forceinline__ void amplitudes(const R* __restrict__ K,"
-               " const cx<R>* __restrict__ prop, const int* hel, const Couplings<R>& cp, cx<R>* J) {")
-    out.append("    #pragma unroll")
-    out.append("    for (int s = 0; s < NCOLOR; ++s) J[s] = cx<R>(R(0), R(0));")
+               " const cx<R>* __restrict__ prop, const int* hel, const Couplings<R>& cp, Acc& J) {")
+    out.append("    J.zero();")
     out.append(body)
     out.append("  }")
     out.append("};")
