@@ -115,6 +115,20 @@ int mg_filter_helicities(int proc, int64_t nevt, const double* mom, int32_t* mas
 int mg_sigmakin(int proc, int64_t nevt, const double* mom, const int32_t* mask, double* me, int mode,
                 void* stream);
 
+/* Gradient of the matrix element with respect to the random numbers (not in
+ * the paper): for every event i, grad[k][i] = gout[i] * d me_i / d rnd[k][i],
+ * through RAMBO and the helicity amplitudes by a hand-written adjoint (the
+ * diagram program of each helicity is recomputed, then reversed; RAMBO's
+ * Newton step enters through its implicit-function derivative).  rnd: [nrows]
+ * [nevt] as for mg_rambo; rows beyond 4*nfinal get exactly 0.  gout: [nevt]
+ * dL/dme or NULL for 1.  me: [nevt] receives the matrix elements (or NULL).
+ * mode: MG_FP64 (FP64 forward and adjoint) or MG_MIXED / MG_MIXED_SIMT (FP32
+ * forward and adjoint; FP64 RAMBO, propagator denominators and sums).
+ * Available for proc 2 (g g -> t t~) and 3 (g g -> t t~ g); MG_ERR_PROC
+ * otherwise. */
+int mg_sigmakin_grad(int proc, int64_t nevt, double ecm, const double* rnd, int nrows, const int32_t* mask,
+                     const double* gout, double* grad, double* me, int mode, void* stream);
+
 /* Event accumulation in FP64 (Sec. 3: average matrix element of a run):
  * out3 = (sum_i wgt_i me_i, sum_i (wgt_i me_i)^2, nevt), by a two-pass tree
  * reduction whose order depends only on nevt (bitwise reproducible).

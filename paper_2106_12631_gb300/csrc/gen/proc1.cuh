@@ -55,5 +55,6 @@ struct Proc1 {
   Lock::sync();
   J.add(0, amp);
   }
+  static constexpr bool HAS_GRAD = false;
 };
 }  // namespace mg

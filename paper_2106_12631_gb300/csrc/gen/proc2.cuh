@@ -59,5 +59,99 @@ struct Proc2 {
   amp = FFV1_0<R>(w3, w9, w0, cp.gs);
   J.add(1, amp);
   }
+  static constexpr bool HAS_GRAD = true;
+  // |M_h|^2 of one helicity (colour summed) and its gradient with respect to the
+  // physical momenta of the final-state legs, accumulated into pb[4 * leg + mu]
+  template <class R>
+  static __device__ __forceinline__ R amplitudes_grad(const R* __restrict__ K, const cx<R>* __restrict__ prop, const int* hel, const Couplings<R>& cp, R* pb) {
+    cx<R> J[NCOLOR];
+    #pragma unroll
+    for (int s = 0; s < NCOLOR; ++s) J[s] = cx<R>(R(0), R(0));
+    cx<R> amp;
+    const W4<R> w9 = ixxxxx<R>(K + 12, cp.mt, hel[3], -1);
+    const W4<R> w0 = vxxxxx<R>(K + 0, hel[0], 1);
+    const W4<R> w1 = vxxxxx<R>(K + 4, hel[1], 1);
+    const W4<R> w5 = VVV1P0_1<R>(w0, w1, K + 16, K + 20, cp.gs, prop[0]);
+    const W4<R> w2 = oxxxxx<R>(K + 8, cp.mt, hel[2], 1);
+    amp = FFV1_0<R>(w2, w9, w5, cp.gs);
+    J[0] -= mul_i(amp);
+    J[1] += mul_i(amp);
+    const W4<R> w7 = FFV1_2<R>(w2, w0, cp.gs, K + 28, cp.mt, prop[1]);
+    amp = FFV1_0<R>(w7, w9, w1, cp.gs);
+    J[0] += amp;
+    const W4<R> w3 = FFV1_2<R>(w2, w1, cp.gs, K + 32, cp.mt, prop[2]);
+    amp = FFV1_0<R>(w3, w9, w0, cp.gs);
+    J[1] += amp;
+    R m2 = R(0);
+    cx<R> Jb[NCOLOR];
+    { const R tr = R(16) * J[0].re + R(-2) * J[1].re, ti = R(16) * J[0].im + R(-2) * J[1].im; m2 += J[0].re * tr + J[0].im * ti; Jb[0] = cx<R>(R(2) * tr / R(CDEN), R(2) * ti / R(CDEN)); }
+    { const R tr = R(-2) * J[0].re + R(16) * J[1].re, ti = R(-2) * J[0].im + R(16) * J[1].im; m2 += J[1].re * tr + J[1].im * ti; Jb[1] = cx<R>(R(2) * tr / R(CDEN), R(2) * ti / R(CDEN)); }
+    m2 /= R(CDEN);
+    W4<R> w9b = w4_zero<R>();
+    W4<R> w0b = w4_zero<R>();
+    W4<R> w1b = w4_zero<R>();
+    W4<R> w5b = w4_zero<R>();
+    W4<R> w2b = w4_zero<R>();
+    W4<R> w7b = w4_zero<R>();
+    W4<R> w3b = w4_zero<R>();
+    cx<R> propb[NPROP];
+    #pragma unroll
+    for (int j = 0; j < NPROP; ++j) propb[j] = cx<R>(R(0), R(0));
+    { const cx<R> ab = Jb[1];
+      FFV1_0_adj<R>(w3, w9, w0, cp.gs, ab, w3b, w9b, w0b); }
+    { const cx<R> ab = Jb[0];
+      FFV1_0_adj<R>(w7, w9, w1, cp.gs, ab, w7b, w9b, w1b); }
+    { const cx<R> ab = mul_i(Jb[0]) + mul_mi(Jb[1]);
+      FFV1_0_adj<R>(w2, w9, w5, cp.gs, ab, w2b, w9b, w5b); }
+    { R kb[4] = {R(0), R(0), R(0), R(0)};
+      FFV1_2_adj<R>(w2, w1, cp.gs, K + 32, cp.mt, prop[2], w3b, w2b, w1b, kb, propb[2]);
+    pb[8] += kb[0];
+    pb[9] += kb[1];
+    pb[10] += kb[2];
+    pb[11] += kb[3];
+    }
+    { R kb[4] = {R(0), R(0), R(0), R(0)};
+      FFV1_2_adj<R>(w2, w0, cp.gs, K + 28, cp.mt, prop[1], w7b, w2b, w0b, kb, propb[1]);
+    pb[8] += kb[0];
+    pb[9] += kb[1];
+    pb[10] += kb[2];
+    pb[11] += kb[3];
+    }
+    { R kb1[4] = {R(0), R(0), R(0), R(0)}, kb2[4] = {R(0), R(0), R(0), R(0)};
+      VVV1P0_1_adj<R>(w0, w1, K + 16, K + 20, cp.gs, prop[0], w5b, w0b, w1b, kb1, kb2, propb[0]);
+    }
+    { R kb[4] = {R(0), R(0), R(0), R(0)};
+      prop_adj<R>(prop[0], false, K + 24, propb[0], kb);
+    }
+    { R kb[4] = {R(0), R(0), R(0), R(0)};
+      prop_adj<R>(prop[1], true, K + 28, propb[1], kb);
+    pb[8] += kb[0];
+    pb[9] += kb[1];
+    pb[10] += kb[2];
+    pb[11] += kb[3];
+    }
+    { R kb[4] = {R(0), R(0), R(0), R(0)};
+      prop_adj<R>(prop[2], true, K + 32, propb[2], kb);
+    pb[8] += kb[0];
+    pb[9] += kb[1];
+    pb[10] += kb[2];
+    pb[11] += kb[3];
+    }
+    { R kb[4] = {R(0), R(0), R(0), R(0)};
+      external_adj<R>(0, K + 12, cp.mt, hel[3], -1, w9b, kb);
+    pb[12] += kb[0];
+    pb[13] += kb[1];
+    pb[14] += kb[2];
+    pb[15] += kb[3];
+    }
+    { R kb[4] = {R(0), R(0), R(0), R(0)};
+      external_adj<R>(1, K + 8, cp.mt, hel[2], 1, w2b, kb);
+    pb[8] += kb[0];
+    pb[9] += kb[1];
+    pb[10] += kb[2];
+    pb[11] += kb[3];
+    }
+    return m2;
+  }
 };
 }  // namespace mg

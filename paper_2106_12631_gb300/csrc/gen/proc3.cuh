@@ -135,5 +135,428 @@ struct Proc3 {
   amp = FFV1_0<R>(w7, w43, w0, cp.gs);
   J.add(3, amp);
   }
+  static constexpr bool HAS_GRAD = true;
+  // |M_h|^2 of one helicity (colour summed) and its gradient with respect to the
+  // physical momenta of the final-state legs, accumulated into pb[4 * leg + mu]
+  template <class R>
+  static __device__ __forceinline__ R amplitudes_grad(const R* __restrict__ K, const cx<R>* __restrict__ prop, const int* hel, const Couplings<R>& cp, R* pb) {
+    cx<R> J[NCOLOR];
+    #pragma unroll
+    for (int s = 0; s < NCOLOR; ++s) J[s] = cx<R>(R(0), R(0));
+    cx<R> amp;
+    const W4<R> w43 = ixxxxx<R>(K + 12, cp.mt, hel[3], -1);
+    const W4<R> w0 = vxxxxx<R>(K + 0, hel[0], 1);
+    const W4<R> w1 = vxxxxx<R>(K + 4, hel[1], 1);
+    const W4<R> w3 = vxxxxx<R>(K + 16, hel[4], -1);
+    const W4<R> w28 = VVVV1P0_1<R>(w0, w1, w3, cp.gs2, prop[0]);
+    const W4<R> w2 = oxxxxx<R>(K + 8, cp.mt, hel[2], 1);
+    amp = FFV1_0<R>(w2, w43, w28, cp.gs);
+    J[0] -= amp;
+    J[2] += amp;
+    J[4] += amp;
+    J[5] -= amp;
+    const W4<R> w29 = VVVV3P0_1<R>(w0, w1, w3, cp.gs2, prop[0]);
+    amp = FFV1_0<R>(w2, w43, w29, cp.gs);
+    J[1] -= amp;
+    J[2] += amp;
+    J[3] -= amp;
+    J[4] += amp;
+    const W4<R> w30 = VVVV4P0_1<R>(w0, w1, w3, cp.gs2, prop[0]);
+    amp = FFV1_0<R>(w2, w43, w30, cp.gs);
+    J[0] += amp;
+    J[1] -= amp;
+    J[3] -= amp;
+    J[5] += amp;
+    const W4<R> w8 = VVV1P0_1<R>(w1, w3, K + 24, K + 28, cp.gs, prop[1]);
+    const W4<R> w25 = VVV1P0_1<R>(w0, w8, K + 36, K + 32, cp.gs, prop[0]);
+    amp = FFV1_0<R>(w2, w43, w25, cp.gs);
+    J[0] -= amp;
+    J[1] += amp;
+    J[3] += amp;
+    J[5] -= amp;
+    const W4<R> w15 = FFV1_2<R>(w2, w0, cp.gs, K + 40, cp.mt, prop[2]);
+    amp = FFV1_0<R>(w15, w43, w8, cp.gs);
+    J[0] -= mul_i(amp);
+    J[1] += mul_i(amp);
+    const W4<R> w9 = FFV1_2<R>(w2, w8, cp.gs, K + 44, cp.mt, prop[3]);
+    amp = FFV1_0<R>(w9, w43, w0, cp.gs);
+    J[3] -= mul_i(amp);
+    J[5] += mul_i(amp);
+    const W4<R> w21 = FFV1_2<R>(w15, w1, cp.gs, K + 48, cp.mt, prop[4]);
+    amp = FFV1_0<R>(w21, w43, w3, cp.gs);
+    J[0] += amp;
+    const W4<R> w38 = FFV1_2<R>(w15, w3, cp.gs, K + 52, cp.mt, prop[5]);
+    amp = FFV1_0<R>(w38, w43, w1, cp.gs);
+    J[1] += amp;
+    const W4<R> w13 = VVV1P0_1<R>(w0, w1, K + 36, K + 24, cp.gs, prop[6]);
+    const W4<R> w26 = VVV1P0_1<R>(w13, w3, K + 56, K + 28, cp.gs, prop[0]);
+    amp = FFV1_0<R>(w2, w43, w26, cp.gs);
+    J[0] -= amp;
+    J[2] += amp;
+    J[4] += amp;
+    J[5] -= amp;
+    const W4<R> w4 = FFV1_2<R>(w2, w3, cp.gs, K + 60, cp.mt, prop[7]);
+    amp = FFV1_0<R>(w4, w43, w13, cp.gs);
+    J[4] -= mul_i(amp);
+    J[5] += mul_i(amp);
+    const W4<R> w20 = FFV1_2<R>(w2, w13, cp.gs, K + 48, cp.mt, prop[4]);
+    amp = FFV1_0<R>(w20, w43, w3, cp.gs);
+    J[0] -= mul_i(amp);
+    J[2] += mul_i(amp);
+    const W4<R> w37 = FFV1_2<R>(w4, w0, cp.gs, K + 52, cp.mt, prop[5]);
+    amp = FFV1_0<R>(w37, w43, w1, cp.gs);
+    J[4] += amp;
+    const W4<R> w5 = FFV1_2<R>(w4, w1, cp.gs, K + 44, cp.mt, prop[3]);
+    amp = FFV1_0<R>(w5, w43, w0, cp.gs);
+    J[5] += amp;
+    const W4<R> w17 = VVV1P0_1<R>(w0, w3, K + 36, K + 28, cp.gs, prop[8]);
+    const W4<R> w27 = VVV1P0_1<R>(w17, w1, K + 64, K + 24, cp.gs, prop[0]);
+    amp = FFV1_0<R>(w2, w43, w27, cp.gs);
+    J[1] -= amp;
+    J[2] += amp;
+    J[3] -= amp;
+    J[4] += amp;
+    const W4<R> w6 = FFV1_2<R>(w2, w1, cp.gs, K + 68, cp.mt, prop[9]);
+    amp = FFV1_0<R>(w6, w43, w17, cp.gs);
+    J[2] -= mul_i(amp);
+    J[3] += mul_i(amp);
+    const W4<R> w39 = FFV1_2<R>(w2, w17, cp.gs, K + 52, cp.mt, prop[5]);
+    amp = FFV1_0<R>(w39, w43, w1, cp.gs);
+    J[1] -= mul_i(amp);
+    J[4] += mul_i(amp);
+    const W4<R> w19 = FFV1_2<R>(w6, w0, cp.gs, K + 48, cp.mt, prop[4]);
+    amp = FFV1_0<R>(w19, w43, w3, cp.gs);
+    J[2] += amp;
+    const W4<R> w7 = FFV1_2<R>(w6, w3, cp.gs, K + 44, cp.mt, prop[3]);
+    amp = FFV1_0<R>(w7, w43, w0, cp.gs);
+    J[3] += amp;
+    R m2 = R(0);
+    cx<R> Jb[NCOLOR];
+    { const R tr = R(64) * J[0].re + R(-8) * J[1].re + R(-8) * J[2].re + R(1) * J[3].re + R(1) * J[4].re + R(10) * J[5].re, ti = R(64) * J[0].im + R(-8) * J[1].im + R(-8) * J[2].im + R(1) * J[3].im + R(1) * J[4].im + R(10) * J[5].im; m2 += J[0].re * tr + J[0].im * ti; Jb[0] = cx<R>(R(2) * tr / R(CDEN), R(2) * ti / R(CDEN)); }
+    { const R tr = R(-8) * J[0].re + R(64) * J[1].re + R(1) * J[2].re + R(10) * J[3].re + R(-8) * J[4].re + R(1) * J[5].re, ti = R(-8) * J[0].im + R(64) * J[1].im + R(1) * J[2].im + R(10) * J[3].im + R(-8) * J[4].im + R(1) * J[5].im; m2 += J[1].re * tr + J[1].im * ti; Jb[1] = cx<R>(R(2) * tr / R(CDEN), R(2) * ti / R(CDEN)); }
+    { const R tr = R(-8) * J[0].re + R(1) * J[1].re + R(64) * J[2].re + R(-8) * J[3].re + R(10) * J[4].re + R(1) * J[5].re, ti = R(-8) * J[0].im + R(1) * J[1].im + R(64) * J[2].im + R(-8) * J[3].im + R(10) * J[4].im + R(1) * J[5].im; m2 += J[2].re * tr + J[2].im * ti; Jb[2] = cx<R>(R(2) * tr / R(CDEN), R(2) * ti / R(CDEN)); }
+    { const R tr = R(1) * J[0].re + R(10) * J[1].re + R(-8) * J[2].re + R(64) * J[3].re + R(1) * J[4].re + R(-8) * J[5].re, ti = R(1) * J[0].im + R(10) * J[1].im + R(-8) * J[2].im + R(64) * J[3].im + R(1) * J[4].im + R(-8) * J[5].im; m2 += J[3].re * tr + J[3].im * ti; Jb[3] = cx<R>(R(2) * tr / R(CDEN), R(2) * ti / R(CDEN)); }
+    { const R tr = R(1) * J[0].re + R(-8) * J[1].re + R(10) * J[2].re + R(1) * J[3].re + R(64) * J[4].re + R(-8) * J[5].re, ti = R(1) * J[0].im + R(-8) * J[1].im + R(10) * J[2].im + R(1) * J[3].im + R(64) * J[4].im + R(-8) * J[5].im; m2 += J[4].re * tr + J[4].im * ti; Jb[4] = cx<R>(R(2) * tr / R(CDEN), R(2) * ti / R(CDEN)); }
+    { const R tr = R(10) * J[0].re + R(1) * J[1].re + R(1) * J[2].re + R(-8) * J[3].re + R(-8) * J[4].re + R(64) * J[5].re, ti = R(10) * J[0].im + R(1) * J[1].im + R(1) * J[2].im + R(-8) * J[3].im + R(-8) * J[4].im + R(64) * J[5].im; m2 += J[5].re * tr + J[5].im * ti; Jb[5] = cx<R>(R(2) * tr / R(CDEN), R(2) * ti / R(CDEN)); }
+    m2 /= R(CDEN);
+    W4<R> w43b = w4_zero<R>();
+    W4<R> w0b = w4_zero<R>();
+    W4<R> w1b = w4_zero<R>();
+    W4<R> w3b = w4_zero<R>();
+    W4<R> w28b = w4_zero<R>();
+    W4<R> w2b = w4_zero<R>();
+    W4<R> w29b = w4_zero<R>();
+    W4<R> w30b = w4_zero<R>();
+    W4<R> w8b = w4_zero<R>();
+    W4<R> w25b = w4_zero<R>();
+    W4<R> w15b = w4_zero<R>();
+    W4<R> w9b = w4_zero<R>();
+    W4<R> w21b = w4_zero<R>();
+    W4<R> w38b = w4_zero<R>();
+    W4<R> w13b = w4_zero<R>();
+    W4<R> w26b = w4_zero<R>();
+    W4<R> w4b = w4_zero<R>();
+    W4<R> w20b = w4_zero<R>();
+    W4<R> w37b = w4_zero<R>();
+    W4<R> w5b = w4_zero<R>();
+    W4<R> w17b = w4_zero<R>();
+    W4<R> w27b = w4_zero<R>();
+    W4<R> w6b = w4_zero<R>();
+    W4<R> w39b = w4_zero<R>();
+    W4<R> w19b = w4_zero<R>();
+    W4<R> w7b = w4_zero<R>();
+    cx<R> propb[NPROP];
+    #pragma unroll
+    for (int j = 0; j < NPROP; ++j) propb[j] = cx<R>(R(0), R(0));
+    { const cx<R> ab = Jb[3];
+      FFV1_0_adj<R>(w7, w43, w0, cp.gs, ab, w7b, w43b, w0b); }
+    { const cx<R> ab = Jb[2];
+      FFV1_0_adj<R>(w19, w43, w3, cp.gs, ab, w19b, w43b, w3b); }
+    { const cx<R> ab = mul_i(Jb[1]) + mul_mi(Jb[4]);
+      FFV1_0_adj<R>(w39, w43, w1, cp.gs, ab, w39b, w43b, w1b); }
+    { const cx<R> ab = mul_i(Jb[2]) + mul_mi(Jb[3]);
+      FFV1_0_adj<R>(w6, w43, w17, cp.gs, ab, w6b, w43b, w17b); }
+    { const cx<R> ab = -Jb[1] + Jb[2] + -Jb[3] + Jb[4];
+      FFV1_0_adj<R>(w2, w43, w27, cp.gs, ab, w2b, w43b, w27b); }
+    { const cx<R> ab = Jb[5];
+      FFV1_0_adj<R>(w5, w43, w0, cp.gs, ab, w5b, w43b, w0b); }
+    { const cx<R> ab = Jb[4];
+      FFV1_0_adj<R>(w37, w43, w1, cp.gs, ab, w37b, w43b, w1b); }
+    { const cx<R> ab = mul_i(Jb[0]) + mul_mi(Jb[2]);
+      FFV1_0_adj<R>(w20, w43, w3, cp.gs, ab, w20b, w43b, w3b); }
+    { const cx<R> ab = mul_i(Jb[4]) + mul_mi(Jb[5]);
+      FFV1_0_adj<R>(w4, w43, w13, cp.gs, ab, w4b, w43b, w13b); }
+    { const cx<R> ab = -Jb[0] + Jb[2] + Jb[4] + -Jb[5];
+      FFV1_0_adj<R>(w2, w43, w26, cp.gs, ab, w2b, w43b, w26b); }
+    { const cx<R> ab = Jb[1];
+      FFV1_0_adj<R>(w38, w43, w1, cp.gs, ab, w38b, w43b, w1b); }
+    { const cx<R> ab = Jb[0];
+      FFV1_0_adj<R>(w21, w43, w3, cp.gs, ab, w21b, w43b, w3b); }
+    { const cx<R> ab = mul_i(Jb[3]) + mul_mi(Jb[5]);
+      FFV1_0_adj<R>(w9, w43, w0, cp.gs, ab, w9b, w43b, w0b); }
+    { const cx<R> ab = mul_i(Jb[0]) + mul_mi(Jb[1]);
+      FFV1_0_adj<R>(w15, w43, w8, cp.gs, ab, w15b, w43b, w8b); }
+    { const cx<R> ab = -Jb[0] + Jb[1] + Jb[3] + -Jb[5];
+      FFV1_0_adj<R>(w2, w43, w25, cp.gs, ab, w2b, w43b, w25b); }
+    { const cx<R> ab = Jb[0] + -Jb[1] + -Jb[3] + Jb[5];
+      FFV1_0_adj<R>(w2, w43, w30, cp.gs, ab, w2b, w43b, w30b); }
+    { const cx<R> ab = -Jb[1] + Jb[2] + -Jb[3] + Jb[4];
+      FFV1_0_adj<R>(w2, w43, w29, cp.gs, ab, w2b, w43b, w29b); }
+    { const cx<R> ab = -Jb[0] + Jb[2] + Jb[4] + -Jb[5];
+      FFV1_0_adj<R>(w2, w43, w28, cp.gs, ab, w2b, w43b, w28b); }
+    { R kb[4] = {R(0), R(0), R(0), R(0)};
+      FFV1_2_adj<R>(w6, w3, cp.gs, K + 44, cp.mt, prop[3], w7b, w6b, w3b, kb, propb[3]);
+    pb[8] += kb[0];
+    pb[9] += kb[1];
+    pb[10] += kb[2];
+    pb[11] += kb[3];
+    pb[16] += kb[0];
+    pb[17] += kb[1];
+    pb[18] += kb[2];
+    pb[19] += kb[3];
+    }
+    { R kb[4] = {R(0), R(0), R(0), R(0)};
+      FFV1_2_adj<R>(w6, w0, cp.gs, K + 48, cp.mt, prop[4], w19b, w6b, w0b, kb, propb[4]);
+    pb[8] += kb[0];
+    pb[9] += kb[1];
+    pb[10] += kb[2];
+    pb[11] += kb[3];
+    }
+    { R kb[4] = {R(0), R(0), R(0), R(0)};
+      FFV1_2_adj<R>(w2, w17, cp.gs, K + 52, cp.mt, prop[5], w39b, w2b, w17b, kb, propb[5]);
+    pb[8] += kb[0];
+    pb[9] += kb[1];
+    pb[10] += kb[2];
+    pb[11] += kb[3];
+    pb[16] += kb[0];
+    pb[17] += kb[1];
+    pb[18] += kb[2];
+    pb[19] += kb[3];
+    }
+    { R kb[4] = {R(0), R(0), R(0), R(0)};
+      FFV1_2_adj<R>(w2, w1, cp.gs, K + 68, cp.mt, prop[9], w6b, w2b, w1b, kb, propb[9]);
+    pb[8] += kb[0];
+    pb[9] += kb[1];
+    pb[10] += kb[2];
+    pb[11] += kb[3];
+    }
+    { R kb1[4] = {R(0), R(0), R(0), R(0)}, kb2[4] = {R(0), R(0), R(0), R(0)};
+      VVV1P0_1_adj<R>(w17, w1, K + 64, K + 24, cp.gs, prop[0], w27b, w17b, w1b, kb1, kb2, propb[0]);
+    pb[16] += kb1[0];
+    pb[17] += kb1[1];
+    pb[18] += kb1[2];
+    pb[19] += kb1[3];
+    }
+    { R kb1[4] = {R(0), R(0), R(0), R(0)}, kb2[4] = {R(0), R(0), R(0), R(0)};
+      VVV1P0_1_adj<R>(w0, w3, K + 36, K + 28, cp.gs, prop[8], w17b, w0b, w3b, kb1, kb2, propb[8]);
+    pb[16] += kb2[0];
+    pb[17] += kb2[1];
+    pb[18] += kb2[2];
+    pb[19] += kb2[3];
+    }
+    { R kb[4] = {R(0), R(0), R(0), R(0)};
+      FFV1_2_adj<R>(w4, w1, cp.gs, K + 44, cp.mt, prop[3], w5b, w4b, w1b, kb, propb[3]);
+    pb[8] += kb[0];
+    pb[9] += kb[1];
+    pb[10] += kb[2];
+    pb[11] += kb[3];
+    pb[16] += kb[0];
+    pb[17] += kb[1];
+    pb[18] += kb[2];
+    pb[19] += kb[3];
+    }
+    { R kb[4] = {R(0), R(0), R(0), R(0)};
+      FFV1_2_adj<R>(w4, w0, cp.gs, K + 52, cp.mt, prop[5], w37b, w4b, w0b, kb, propb[5]);
+    pb[8] += kb[0];
+    pb[9] += kb[1];
+    pb[10] += kb[2];
+    pb[11] += kb[3];
+    pb[16] += kb[0];
+    pb[17] += kb[1];
+    pb[18] += kb[2];
+    pb[19] += kb[3];
+    }
+    { R kb[4] = {R(0), R(0), R(0), R(0)};
+      FFV1_2_adj<R>(w2, w13, cp.gs, K + 48, cp.mt, prop[4], w20b, w2b, w13b, kb, propb[4]);
+    pb[8] += kb[0];
+    pb[9] += kb[1];
+    pb[10] += kb[2];
+    pb[11] += kb[3];
+    }
+    { R kb[4] = {R(0), R(0), R(0), R(0)};
+      FFV1_2_adj<R>(w2, w3, cp.gs, K + 60, cp.mt, prop[7], w4b, w2b, w3b, kb, propb[7]);
+    pb[8] += kb[0];
+    pb[9] += kb[1];
+    pb[10] += kb[2];
+    pb[11] += kb[3];
+    pb[16] += kb[0];
+    pb[17] += kb[1];
+    pb[18] += kb[2];
+    pb[19] += kb[3];
+    }
+    { R kb1[4] = {R(0), R(0), R(0), R(0)}, kb2[4] = {R(0), R(0), R(0), R(0)};
+      VVV1P0_1_adj<R>(w13, w3, K + 56, K + 28, cp.gs, prop[0], w26b, w13b, w3b, kb1, kb2, propb[0]);
+    pb[16] += kb2[0];
+    pb[17] += kb2[1];
+    pb[18] += kb2[2];
+    pb[19] += kb2[3];
+    }
+    { R kb1[4] = {R(0), R(0), R(0), R(0)}, kb2[4] = {R(0), R(0), R(0), R(0)};
+      VVV1P0_1_adj<R>(w0, w1, K + 36, K + 24, cp.gs, prop[6], w13b, w0b, w1b, kb1, kb2, propb[6]);
+    }
+    { R kb[4] = {R(0), R(0), R(0), R(0)};
+      FFV1_2_adj<R>(w15, w3, cp.gs, K + 52, cp.mt, prop[5], w38b, w15b, w3b, kb, propb[5]);
+    pb[8] += kb[0];
+    pb[9] += kb[1];
+    pb[10] += kb[2];
+    pb[11] += kb[3];
+    pb[16] += kb[0];
+    pb[17] += kb[1];
+    pb[18] += kb[2];
+    pb[19] += kb[3];
+    }
+    { R kb[4] = {R(0), R(0), R(0), R(0)};
+      FFV1_2_adj<R>(w15, w1, cp.gs, K + 48, cp.mt, prop[4], w21b, w15b, w1b, kb, propb[4]);
+    pb[8] += kb[0];
+    pb[9] += kb[1];
+    pb[10] += kb[2];
+    pb[11] += kb[3];
+    }
+    { R kb[4] = {R(0), R(0), R(0), R(0)};
+      FFV1_2_adj<R>(w2, w8, cp.gs, K + 44, cp.mt, prop[3], w9b, w2b, w8b, kb, propb[3]);
+    pb[8] += kb[0];
+    pb[9] += kb[1];
+    pb[10] += kb[2];
+    pb[11] += kb[3];
+    pb[16] += kb[0];
+    pb[17] += kb[1];
+    pb[18] += kb[2];
+    pb[19] += kb[3];
+    }
+    { R kb[4] = {R(0), R(0), R(0), R(0)};
+      FFV1_2_adj<R>(w2, w0, cp.gs, K + 40, cp.mt, prop[2], w15b, w2b, w0b, kb, propb[2]);
+    pb[8] += kb[0];
+    pb[9] += kb[1];
+    pb[10] += kb[2];
+    pb[11] += kb[3];
+    }
+    { R kb1[4] = {R(0), R(0), R(0), R(0)}, kb2[4] = {R(0), R(0), R(0), R(0)};
+      VVV1P0_1_adj<R>(w0, w8, K + 36, K + 32, cp.gs, prop[0], w25b, w0b, w8b, kb1, kb2, propb[0]);
+    pb[16] += kb2[0];
+    pb[17] += kb2[1];
+    pb[18] += kb2[2];
+    pb[19] += kb2[3];
+    }
+    { R kb1[4] = {R(0), R(0), R(0), R(0)}, kb2[4] = {R(0), R(0), R(0), R(0)};
+      VVV1P0_1_adj<R>(w1, w3, K + 24, K + 28, cp.gs, prop[1], w8b, w1b, w3b, kb1, kb2, propb[1]);
+    pb[16] += kb2[0];
+    pb[17] += kb2[1];
+    pb[18] += kb2[2];
+    pb[19] += kb2[3];
+    }
+    VVVV4P0_1_adj<R>(w0, w1, w3, cp.gs2, prop[0], w30b, w0b, w1b, w3b, propb[0]);
+    VVVV3P0_1_adj<R>(w0, w1, w3, cp.gs2, prop[0], w29b, w0b, w1b, w3b, propb[0]);
+    VVVV1P0_1_adj<R>(w0, w1, w3, cp.gs2, prop[0], w28b, w0b, w1b, w3b, propb[0]);
+    { R kb[4] = {R(0), R(0), R(0), R(0)};
+      prop_adj<R>(prop[0], false, K + 20, propb[0], kb);
+    pb[16] += kb[0];
+    pb[17] += kb[1];
+    pb[18] += kb[2];
+    pb[19] += kb[3];
+    }
+    { R kb[4] = {R(0), R(0), R(0), R(0)};
+      prop_adj<R>(prop[1], false, K + 32, propb[1], kb);
+    pb[16] += kb[0];
+    pb[17] += kb[1];
+    pb[18] += kb[2];
+    pb[19] += kb[3];
+    }
+    { R kb[4] = {R(0), R(0), R(0), R(0)};
+      prop_adj<R>(prop[2], true, K + 40, propb[2], kb);
+    pb[8] += kb[0];
+    pb[9] += kb[1];
+    pb[10] += kb[2];
+    pb[11] += kb[3];
+    }
+    { R kb[4] = {R(0), R(0), R(0), R(0)};
+      prop_adj<R>(prop[3], true, K + 44, propb[3], kb);
+    pb[8] += kb[0];
+    pb[9] += kb[1];
+    pb[10] += kb[2];
+    pb[11] += kb[3];
+    pb[16] += kb[0];
+    pb[17] += kb[1];
+    pb[18] += kb[2];
+    pb[19] += kb[3];
+    }
+    { R kb[4] = {R(0), R(0), R(0), R(0)};
+      prop_adj<R>(prop[4], true, K + 48, propb[4], kb);
+    pb[8] += kb[0];
+    pb[9] += kb[1];
+    pb[10] += kb[2];
+    pb[11] += kb[3];
+    }
+    { R kb[4] = {R(0), R(0), R(0), R(0)};
+      prop_adj<R>(prop[5], true, K + 52, propb[5], kb);
+    pb[8] += kb[0];
+    pb[9] += kb[1];
+    pb[10] += kb[2];
+    pb[11] += kb[3];
+    pb[16] += kb[0];
+    pb[17] += kb[1];
+    pb[18] += kb[2];
+    pb[19] += kb[3];
+    }
+    { R kb[4] = {R(0), R(0), R(0), R(0)};
+      prop_adj<R>(prop[6], false, K + 56, propb[6], kb);
+    }
+    { R kb[4] = {R(0), R(0), R(0), R(0)};
+      prop_adj<R>(prop[7], true, K + 60, propb[7], kb);
+    pb[8] += kb[0];
+    pb[9] += kb[1];
+    pb[10] += kb[2];
+    pb[11] += kb[3];
+    pb[16] += kb[0];
+    pb[17] += kb[1];
+    pb[18] += kb[2];
+    pb[19] += kb[3];
+    }
+    { R kb[4] = {R(0), R(0), R(0), R(0)};
+      prop_adj<R>(prop[8], false, K + 64, propb[8], kb);
+    pb[16] += kb[0];
+    pb[17] += kb[1];
+    pb[18] += kb[2];
+    pb[19] += kb[3];
+    }
+    { R kb[4] = {R(0), R(0), R(0), R(0)};
+      prop_adj<R>(prop[9], true, K + 68, propb[9], kb);
+    pb[8] += kb[0];
+    pb[9] += kb[1];
+    pb[10] += kb[2];
+    pb[11] += kb[3];
+    }
+    { R kb[4] = {R(0), R(0), R(0), R(0)};
+      external_adj<R>(0, K + 12, cp.mt, hel[3], -1, w43b, kb);
+    pb[12] += kb[0];
+    pb[13] += kb[1];
+    pb[14] += kb[2];
+    pb[15] += kb[3];
+    }
+    { R kb[4] = {R(0), R(0), R(0), R(0)};
+      external_adj<R>(2, K + 16, R(0), hel[4], -1, w3b, kb);
+    pb[16] += kb[0];
+    pb[17] += kb[1];
+    pb[18] += kb[2];
+    pb[19] += kb[3];
+    }
+    { R kb[4] = {R(0), R(0), R(0), R(0)};
+      external_adj<R>(1, K + 8, cp.mt, hel[2], 1, w2b, kb);
+    pb[8] += kb[0];
+    pb[9] += kb[1];
+    pb[10] += kb[2];
+    pb[11] += kb[3];
+    }
+    return m2;
+  }
 };
 }  // namespace mg

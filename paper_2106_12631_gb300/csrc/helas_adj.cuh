@@ -1,0 +1,268 @@
+// Adjoints (reverse mode) of the helicity-amplitude routines in helas.cuh.
+//
+// Convention: for a real loss L and a complex intermediate z = x + i y the
+// adjoint is zb = dL/dx + i dL/dy.  For w = f(z) holomorphic, zb += conj(f'(z)) wb;
+// for a real input t entering a complex w, tb += Re(conj(dw/dt) wb).  Every
+// routine below is multilinear in its wavefunction inputs, so its adjoint is
+// the conjugate-transposed map, written out term by term from the forward
+// formula (each comment names the forward routine).  Adjoint arguments are
+// accumulated (+=).  Momentum adjoints Kb are real 4-vectors; propagator
+// adjoints are complex.
+#pragma once
+#include <type_traits>
+
+#include "helas.cuh"
+
+namespace mg {
+
+template <class R>
+__device__ __forceinline__ W4<R> w4_zero() {
+  W4<R> o;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) o.w[k] = cx<R>(R(0), R(0));
+  return o;
+}
+template <class R>
+__device__ __forceinline__ R re_dot(cx<R> a, cx<R> b) {  // Re(conj(a) b)
+  return a.re * b.re + a.im * b.im;
+}
+
+// (vp, vm, xp, xm) = (V0 + V3, V0 - V3, V1 + i V2, V1 - i V2): scatter adjoints to V
+template <class R>
+__device__ __forceinline__ void slash_parts_adj(cx<R> bp, cx<R> bm, cx<R> bxp, cx<R> bxm, W4<R>& Vb) {
+  Vb.w[0] += bp + bm;
+  Vb.w[3] += bp - bm;
+  Vb.w[1] += bxp + bxm;
+  Vb.w[2] += mul_mi(bxp) + mul_i(bxm);
+}
+
+// row_slash: o0 = f2 vp + f3 xp, o1 = f2 xm + f3 vm, o2 = f0 vm - f1 xp, o3 = f1 vp - f0 xm
+template <class R>
+__device__ __forceinline__ void row_slash_adj(const W4<R>& f, const W4<R>& V, const W4<R>& ob, W4<R>& fb, W4<R>& Vb) {
+  const cx<R> vp = V.w[0] + V.w[3], vm = V.w[0] - V.w[3];
+  const cx<R> xp = V.w[1] + mul_i(V.w[2]), xm = V.w[1] - mul_i(V.w[2]);
+  fb.w[2] += conj(vp) * ob.w[0] + conj(xm) * ob.w[1];
+  fb.w[3] += conj(xp) * ob.w[0] + conj(vm) * ob.w[1];
+  fb.w[0] += conj(vm) * ob.w[2] - conj(xm) * ob.w[3];
+  fb.w[1] += conj(vp) * ob.w[3] - conj(xp) * ob.w[2];
+  const cx<R> bp = conj(f.w[2]) * ob.w[0] + conj(f.w[1]) * ob.w[3];
+  const cx<R> bm = conj(f.w[3]) * ob.w[1] + conj(f.w[0]) * ob.w[2];
+  const cx<R> bxp = conj(f.w[3]) * ob.w[0] - conj(f.w[1]) * ob.w[2];
+  const cx<R> bxm = conj(f.w[2]) * ob.w[1] - conj(f.w[0]) * ob.w[3];
+  slash_parts_adj(bp, bm, bxp, bxm, Vb);
+}
+
+// row_kslash_m: o0 = kp f2 + f3 kxp + m f0, o1 = f2 kxm + km f3 + m f1,
+//               o2 = km f0 - f1 kxp + m f2, o3 = kp f1 - f0 kxm + m f3
+template <class R>
+__device__ __forceinline__ void row_kslash_m_adj(const W4<R>& f, const R* K, R m, const W4<R>& ob, W4<R>& fb, R* Kb) {
+  const R kp = K[0] + K[3], km = K[0] - K[3];
+  const cx<R> kxp(K[1], K[2]), kxm(K[1], -K[2]);
+  fb.w[0] += m * ob.w[0] + km * ob.w[2] - conj(kxm) * ob.w[3];
+  fb.w[1] += m * ob.w[1] - conj(kxp) * ob.w[2] + kp * ob.w[3];
+  fb.w[2] += kp * ob.w[0] + conj(kxm) * ob.w[1] + m * ob.w[2];
+  fb.w[3] += conj(kxp) * ob.w[0] + km * ob.w[1] + m * ob.w[3];
+  const R bkp = re_dot(f.w[2], ob.w[0]) + re_dot(f.w[1], ob.w[3]);
+  const R bkm = re_dot(f.w[3], ob.w[1]) + re_dot(f.w[0], ob.w[2]);
+  const cx<R> bxp = conj(f.w[3]) * ob.w[0] - conj(f.w[1]) * ob.w[2];
+  const cx<R> bxm = conj(f.w[2]) * ob.w[1] - conj(f.w[0]) * ob.w[3];
+  Kb[0] += bkp + bkm;
+  Kb[3] += bkp - bkm;
+  Kb[1] += bxp.re + bxm.re;
+  Kb[2] += bxp.im - bxm.im;
+}
+
+// FFV1_0 = i g row_col(row_slash(fo, v), fi)
+template <class R>
+__device__ __forceinline__ void FFV1_0_adj(const W4<R>& fo, const W4<R>& fi, const W4<R>& v, R g, cx<R> ab, W4<R>& fob,
+                                           W4<R>& fib, W4<R>& vb) {
+  const W4<R> r = row_slash(fo, v);
+  const cx<R> sb = mul_mi(g * ab);  // conj(i g) ab
+  W4<R> rb;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    rb.w[k] = conj(fi.w[k]) * sb;
+    fib.w[k] += conj(r.w[k]) * sb;
+  }
+  row_slash_adj(fo, v, rb, fob, vb);
+}
+
+// FFV1_2 = [row_kslash_m(row_slash(fo, v), K, m)] (i g prop)
+template <class R>
+__device__ __forceinline__ void FFV1_2_adj(const W4<R>& fo, const W4<R>& v, R g, const R* K, R m, cx<R> prop,
+                                           const W4<R>& ob, W4<R>& fob, W4<R>& vb, R* Kb, cx<R>& propb) {
+  const W4<R> u = row_slash(fo, v);
+  const W4<R> w = row_kslash_m(u, K, m);
+  const cx<R> s = mul_i(g * prop);
+  W4<R> wb;
+  cx<R> sb(R(0), R(0));
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    wb.w[k] = conj(s) * ob.w[k];
+    sb += conj(w.w[k]) * ob.w[k];
+  }
+  propb += mul_mi(g * sb);  // conj(i g) sb
+  W4<R> ub = w4_zero<R>();
+  row_kslash_m_adj(u, K, m, wb, ub, Kb);
+  row_slash_adj(fo, v, ub, fob, vb);
+}
+
+// VVV1P0_1 = (d12 (a1.a2) + a2 (d23.a1) + a1 (d31.a2)) g prop,
+// d12 = K2 - K1, d23 = -(K1 + 2 K2), d31 = 2 K1 + K2
+template <class R>
+__device__ __forceinline__ void VVV1P0_1_adj(const W4<R>& a1, const W4<R>& a2, const R* K1, const R* K2, R g, cx<R> prop,
+                                             const W4<R>& ob, W4<R>& a1b, W4<R>& a2b, R* K1b, R* K2b, cx<R>& propb) {
+  R d12[4], d23[4], d31[4];
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    d12[mu] = K2[mu] - K1[mu];
+    d23[mu] = -(K1[mu] + R(2) * K2[mu]);
+    d31[mu] = R(2) * K1[mu] + K2[mu];
+  }
+  const cx<R> a12 = vdot(a1, a2), c1 = kdot(d23, a1), c2 = kdot(d31, a2);
+  const cx<R> s = g * prop;
+  cx<R> sb(R(0), R(0)), a12b(R(0), R(0)), c1b(R(0), R(0)), c2b(R(0), R(0));
+  R d12b[4], d23b[4], d31b[4];
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    const cx<R> t = d12[mu] * a12 + a2.w[mu] * c1 + a1.w[mu] * c2;
+    const cx<R> tb = conj(s) * ob.w[mu];
+    sb += conj(t) * ob.w[mu];
+    a12b += d12[mu] * tb;
+    d12b[mu] = re_dot(a12, tb);
+    a2b.w[mu] += conj(c1) * tb;
+    c1b += conj(a2.w[mu]) * tb;
+    a1b.w[mu] += conj(c2) * tb;
+    c2b += conj(a1.w[mu]) * tb;
+  }
+  propb += g * sb;
+  const R eta[4] = {R(1), R(-1), R(-1), R(-1)};
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    a1b.w[mu] += (eta[mu] * d23[mu]) * c1b + eta[mu] * (conj(a2.w[mu]) * a12b);
+    a2b.w[mu] += (eta[mu] * d31[mu]) * c2b + eta[mu] * (conj(a1.w[mu]) * a12b);
+    d23b[mu] = eta[mu] * re_dot(a1.w[mu], c1b);
+    d31b[mu] = eta[mu] * re_dot(a2.w[mu], c2b);
+    K1b[mu] += -d12b[mu] - d23b[mu] + R(2) * d31b[mu];
+    K2b[mu] += d12b[mu] - R(2) * d23b[mu] + d31b[mu];
+  }
+}
+
+// four-gluon terms: o = ((A.B) X - (C.D) Y) (-i g2 prop)
+template <class R>
+__device__ __forceinline__ void vvvv_adj(const W4<R>& X, const W4<R>& A, const W4<R>& B, const W4<R>& Y, const W4<R>& C,
+                                         const W4<R>& D, R g2, cx<R> prop, const W4<R>& ob, W4<R>& Xb, W4<R>& Ab,
+                                         W4<R>& Bb, W4<R>& Yb, W4<R>& Cb, W4<R>& Db, cx<R>& propb) {
+  const cx<R> cxv = vdot(A, B), cyv = vdot(C, D);
+  const cx<R> s = mul_mi(g2 * prop);
+  cx<R> sb(R(0), R(0)), cxb(R(0), R(0)), cyb(R(0), R(0));
+  W4<R> tb;
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    const cx<R> t = cxv * X.w[mu] - cyv * Y.w[mu];
+    tb.w[mu] = conj(s) * ob.w[mu];
+    sb += conj(t) * ob.w[mu];
+    cxb += conj(X.w[mu]) * tb.w[mu];
+    cyb -= conj(Y.w[mu]) * tb.w[mu];
+  }
+  propb += mul_i(g2 * sb);  // conj(-i g2) sb
+  const R eta[4] = {R(1), R(-1), R(-1), R(-1)};
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    Xb.w[mu] += conj(cxv) * tb.w[mu];
+    Yb.w[mu] -= conj(cyv) * tb.w[mu];
+  }
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    Ab.w[mu] += eta[mu] * (conj(B.w[mu]) * cxb);
+    Bb.w[mu] += eta[mu] * (conj(A.w[mu]) * cxb);
+    Cb.w[mu] += eta[mu] * (conj(D.w[mu]) * cyb);
+    Db.w[mu] += eta[mu] * (conj(C.w[mu]) * cyb);
+  }
+}
+// VVVV1P0_1: (a1.a3) a2 - (a2.a3) a1
+template <class R>
+__device__ __forceinline__ void VVVV1P0_1_adj(const W4<R>& a1, const W4<R>& a2, const W4<R>& a3, R g2, cx<R> prop,
+                                              const W4<R>& ob, W4<R>& a1b, W4<R>& a2b, W4<R>& a3b, cx<R>& propb) {
+  vvvv_adj(a2, a1, a3, a1, a2, a3, g2, prop, ob, a2b, a1b, a3b, a1b, a2b, a3b, propb);
+}
+// VVVV3P0_1: (a1.a2) a3 - (a2.a3) a1
+template <class R>
+__device__ __forceinline__ void VVVV3P0_1_adj(const W4<R>& a1, const W4<R>& a2, const W4<R>& a3, R g2, cx<R> prop,
+                                              const W4<R>& ob, W4<R>& a1b, W4<R>& a2b, W4<R>& a3b, cx<R>& propb) {
+  vvvv_adj(a3, a1, a2, a1, a2, a3, g2, prop, ob, a3b, a1b, a2b, a1b, a2b, a3b, propb);
+}
+// VVVV4P0_1: (a1.a2) a3 - (a1.a3) a2
+template <class R>
+__device__ __forceinline__ void VVVV4P0_1_adj(const W4<R>& a1, const W4<R>& a2, const W4<R>& a3, R g2, cx<R> prop,
+                                              const W4<R>& ob, W4<R>& a1b, W4<R>& a2b, W4<R>& a3b, cx<R>& propb) {
+  vvvv_adj(a3, a1, a2, a2, a1, a3, g2, prop, ob, a3b, a1b, a2b, a2b, a1b, a3b, propb);
+}
+
+// Propagator factor prop = c / (K^2 - M^2 + i M W), c = i (fermion) or -i (vector):
+// d prop / d K_mu = kappa 2 eta_mu K_mu with kappa = i prop^2 (fermion), -i prop^2 (vector)
+template <class R>
+__device__ __forceinline__ void prop_adj(cx<R> prop, bool fermion, const R* K, cx<R> propb, R* Kb) {
+  const cx<R> p2 = prop * prop;
+  const cx<R> kappa = fermion ? mul_i(p2) : mul_mi(p2);
+  const R f = R(2) * re_dot(kappa, propb);
+  Kb[0] += f * K[0];
+  Kb[1] -= f * K[1];
+  Kb[2] -= f * K[2];
+  Kb[3] -= f * K[3];
+}
+
+// ---- external wavefunctions: momentum Jacobian by forward mode ----------------
+// A number with derivatives along the four momentum components.
+template <class R>
+struct D4 {
+  R v, d[4];
+  D4() = default;
+  template <class T, class = typename std::enable_if<std::is_arithmetic<T>::value>::type>
+  __device__ __forceinline__ D4(T x) : v(R(x)) {
+    d[0] = d[1] = d[2] = d[3] = R(0);
+  }
+};
+using ::sqrt;
+template <class R> __device__ __forceinline__ D4<R> operator+(D4<R> a, D4<R> b) { D4<R> r(a.v + b.v); for (int k = 0; k < 4; ++k) r.d[k] = a.d[k] + b.d[k]; return r; }
+template <class R> __device__ __forceinline__ D4<R> operator-(D4<R> a, D4<R> b) { D4<R> r(a.v - b.v); for (int k = 0; k < 4; ++k) r.d[k] = a.d[k] - b.d[k]; return r; }
+template <class R> __device__ __forceinline__ D4<R> operator-(D4<R> a) { D4<R> r(-a.v); for (int k = 0; k < 4; ++k) r.d[k] = -a.d[k]; return r; }
+template <class R> __device__ __forceinline__ D4<R> operator*(D4<R> a, D4<R> b) { D4<R> r(a.v * b.v); for (int k = 0; k < 4; ++k) r.d[k] = a.d[k] * b.v + a.v * b.d[k]; return r; }
+template <class R> __device__ __forceinline__ D4<R> operator/(D4<R> a, D4<R> b) {
+  D4<R> r(a.v / b.v);
+  const R ib = R(1) / b.v;
+  for (int k = 0; k < 4; ++k) r.d[k] = (a.d[k] - r.v * b.d[k]) * ib;
+  return r;
+}
+template <class R> __device__ __forceinline__ D4<R>& operator+=(D4<R>& a, D4<R> b) { a = a + b; return a; }
+template <class R> __device__ __forceinline__ D4<R>& operator-=(D4<R>& a, D4<R> b) { a = a - b; return a; }
+template <class R> __device__ __forceinline__ bool operator>=(D4<R> a, D4<R> b) { return a.v >= b.v; }
+template <class R> __device__ __forceinline__ bool operator<=(D4<R> a, D4<R> b) { return a.v <= b.v; }
+template <class R> __device__ __forceinline__ bool operator==(D4<R> a, D4<R> b) { return a.v == b.v; }
+template <class R> __device__ __forceinline__ D4<R> sqrt(D4<R> a) {
+  D4<R> r(sqrt(a.v));
+  const R h = R(0.5) / r.v;
+  for (int k = 0; k < 4; ++k) r.d[k] = a.d[k] * h;
+  return r;
+}
+template <> __device__ __forceinline__ D4<float> rsqrt_<D4<float>>(D4<float> x) { return D4<float>(1.0f) / sqrt(x); }
+template <> __device__ __forceinline__ D4<double> rsqrt_<D4<double>>(D4<double> x) { return D4<double>(1.0) / sqrt(x); }
+
+// pb_nu += Re(sum_c conj(dW_c/dp_nu) Wb_c) for an external wavefunction W(p).
+// kind: 0 ixxxxx, 1 oxxxxx, 2 vxxxxx.
+template <class R>
+__device__ __forceinline__ void external_adj(int kind, const R* p, R m, int hel, int ns, const W4<R>& wb, R* pb) {
+  D4<R> pd[4];
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) { pd[mu] = D4<R>(p[mu]); pd[mu].d[mu] = R(1); }
+  W4<D4<R>> w;
+  if (kind == 0) w = ixxxxx<D4<R>>(pd, D4<R>(m), hel, ns);
+  else if (kind == 1) w = oxxxxx<D4<R>>(pd, D4<R>(m), hel, ns);
+  else w = vxxxxx<D4<R>>(pd, hel, ns);
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+#pragma unroll
+    for (int nu = 0; nu < 4; ++nu) pb[nu] += w.w[c].re.d[nu] * wb.w[c].re + w.w[c].im.d[nu] * wb.w[c].im;
+}
+
+}  // namespace mg

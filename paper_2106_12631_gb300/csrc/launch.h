@@ -5,15 +5,10 @@
 #include <cuda_runtime.h>
 
 #include "mg_types.cuh"
+#include "rambo.cuh"
 
 namespace mg {
 
-struct RamboSetup {
-  double w0;       // flat massless volume (pi/2)^(n-1) s^(n-2) / ((n-1)! (n-2)!)
-  int massive;     // any final-state mass != 0
-  double xi0;      // Newton start sqrt(1 - (sum m / ecm)^2)
-  double m2[4];    // final-state masses squared
-};
 
 struct SigLaunch {
   int64_t nevt;
@@ -39,6 +34,25 @@ cudaError_t launch_sigmakin_p1(const SigLaunch& a, int mode, cudaStream_t s);
 cudaError_t launch_sigmakin_p2(const SigLaunch& a, int mode, cudaStream_t s);
 cudaError_t launch_sigmakin_p3(const SigLaunch& a, int mode, cudaStream_t s);
 cudaError_t launch_sigmakin_p4(const SigLaunch& a, int mode, cudaStream_t s);
+struct GradLaunch {
+  int64_t nevt;
+  double ecm;
+  const double* rnd;
+  int nrows;
+  const int32_t* mask;
+  const double* gout;  // dL/dme per event, or null for 1
+  double* grad;        // [nrows][nevt]
+  double* me;          // [nevt] or null
+  PhysParams pp;
+  Couplings<double> cd;
+  Couplings<float> cf;
+  RamboSetup st;
+};
+// mode 0: FP64 forward and adjoint; 1, 2: FP32 forward and adjoint (FP64 RAMBO,
+// denominators and sums)
+cudaError_t launch_grad_p2(const GradLaunch& a, int mode, cudaStream_t s);
+cudaError_t launch_grad_p3(const GradLaunch& a, int mode, cudaStream_t s);
+
 cudaError_t launch_filter_p1(const SigLaunch& a, cudaStream_t s);
 cudaError_t launch_filter_p2(const SigLaunch& a, cudaStream_t s);
 cudaError_t launch_filter_p3(const SigLaunch& a, cudaStream_t s);

@@ -209,6 +209,38 @@ int mg_sigmakin(int proc, int64_t nevt, const double* mom, const int32_t* mask, 
   return cuda_status(dispatch_sigmakin(proc, l, mode, (cudaStream_t)stream));
 }
 
+int mg_sigmakin_grad(int proc, int64_t nevt, double ecm, const double* rnd, int nrows, const int32_t* mask,
+                     const double* gout, double* grad, double* me, int mode, void* stream) {
+  if (!valid_proc(proc)) return MG_ERR_PROC;
+  if (proc != 2 && proc != 3) return MG_ERR_PROC;
+  const ProcDesc& d = kProcs[proc];
+  if (nevt < 0 || mode < 0 || mode > 2 || !(ecm > 0) || !std::isfinite(ecm) || nrows < 4 * (d.npar - 2))
+    return MG_ERR_ARG;
+  mg::RamboSetup st;
+  if (int r = rambo_setup(proc, ecm, st)) return r;
+  if (nevt == 0) return MG_OK;
+  if (!rnd || !mask || !grad) return MG_ERR_ARG;
+  if (!aligned(rnd) || !aligned(mask) || !aligned(grad) || (gout && !aligned(gout)) || (me && !aligned(me)))
+    return MG_ERR_ALIGN;
+  if (nevt > (int64_t)INT32_MAX) return MG_ERR_ARG;
+  const mg_params p = params_snapshot();
+  mg::GradLaunch l;
+  l.nevt = nevt;
+  l.ecm = ecm;
+  l.rnd = rnd;
+  l.nrows = nrows;
+  l.mask = mask;
+  l.gout = gout;
+  l.grad = grad;
+  l.me = me;
+  l.pp = mg::PhysParams{p.mz, p.wz, p.mt, p.wt};
+  l.cd = couplings<double>(p);
+  l.cf = couplings<float>(p);
+  l.st = st;
+  cudaStream_t s = (cudaStream_t)stream;
+  return cuda_status(proc == 2 ? mg::launch_grad_p2(l, mode, s) : mg::launch_grad_p3(l, mode, s));
+}
+
 int64_t mg_event_sum_scratch_bytes(int64_t nevt) {
   if (nevt < 0) return -1;
   return 16 * mg::event_sum_blocks(nevt) + 16;

@@ -1,7 +1,7 @@
 // The four processes: generated diagram programs plus the per-process
 // constants the kernels need.
 #pragma once
-#include "helas.cuh"
+#include "helas_adj.cuh"
 
 #include "gen/proc1.cuh"
 #include "gen/proc2.cuh"

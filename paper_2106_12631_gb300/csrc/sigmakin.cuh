@@ -126,9 +126,9 @@ struct SigLayout {
   static constexpr uint32_t TMEM_COLS = C::MBLK * 2 * C::NP;
 };
 
-// Phase 1: per-event tables.
+// Phase 1b: per-event tables from the FP64 momenta already in shared memory.
 template <class P, class R, class L>
-__device__ __forceinline__ void event_tables(unsigned char* smem, const SigArgs& a, int64_t e0, int nev) {
+__device__ __forceinline__ void build_tables(unsigned char* smem, const PhysParams& pp, int nev) {
   using C = SigCfg<P>;
   const int tid = threadIdx.x;
   auto p = reinterpret_cast<double(*)[P::NPAR][4]>(smem + L::o_p);
@@ -136,11 +136,6 @@ __device__ __forceinline__ void event_tables(unsigned char* smem, const SigArgs&
   auto pr = reinterpret_cast<cx<R>(*)[P::NPROP]>(smem + L::o_pr);
   const int(*mom_tab)[3] = reinterpret_cast<const int(*)[3]>(smem + L::o_momtab);
   const int(*prop_tab)[2] = reinterpret_cast<const int(*)[2]>(smem + L::o_proptab);
-  for (int t = tid; t < nev * P::NPAR * 4; t += C::NT) {
-    const int e = t % nev, c = t / nev;
-    p[e][c >> 2][c & 3] = a.mom[(int64_t)c * a.nevt + e0 + e];
-  }
-  __syncthreads();
   for (int t = tid; t < nev * (P::NMOM + P::NPROP); t += C::NT) {
     const int e = t % nev, j = t / nev;
     const int mj = j < P::NMOM ? j : prop_tab[j - P::NMOM][0];
@@ -158,11 +153,25 @@ __device__ __forceinline__ void event_tables(unsigned char* smem, const SigArgs&
       for (int mu = 0; mu < 4; ++mu) K[e][j][mu] = R(k[mu]);
     } else {
       double re, im;
-      propagator_fp64(k, prop_tab[j - P::NMOM][1], a.pp, re, im);
+      propagator_fp64(k, prop_tab[j - P::NMOM][1], pp, re, im);
       pr[e][j - P::NMOM] = cx<R>(R(re), R(im));
     }
   }
   __syncthreads();
+}
+
+// Phase 1: external momenta (global -> shared) and the per-event tables.
+template <class P, class R, class L>
+__device__ __forceinline__ void event_tables(unsigned char* smem, const SigArgs& a, int64_t e0, int nev) {
+  using C = SigCfg<P>;
+  const int tid = threadIdx.x;
+  auto p = reinterpret_cast<double(*)[P::NPAR][4]>(smem + L::o_p);
+  for (int t = tid; t < nev * P::NPAR * 4; t += C::NT) {
+    const int e = t % nev, c = t / nev;
+    p[e][c >> 2][c & 3] = a.mom[(int64_t)c * a.nevt + e0 + e];
+  }
+  __syncthreads();
+  build_tables<P, R, L>(smem, a.pp, nev);
 }
 
 template <class P, class L>

@@ -547,6 +547,139 @@ class Emitter:
         raise ValueError("colour-flow coefficient %r outside {+-1, +-i}" % z)
 
 
+GRAD_PROCS = (2, 3)  # processes with a generated adjoint
+
+
+class GradEmitter:
+    """Reverse-mode (adjoint) program for one process: forward diagram program
+    for one helicity, colour sum, then the adjoint of every step in reverse
+    order.  Momentum-table and propagator adjoints are routed directly to the
+    final-state legs' momentum adjoints pb[4 * leg + mu] (beams are constant)."""
+
+    def __init__(self, em: "Emitter"):
+        self.em = em
+        self.p = em.p
+
+    def _route(self, mom_index, kb, lines, sign=1):
+        """pb += d(momentum entry)/d(p_leg) . kb for the final-state legs."""
+        key = self.em.mom[mom_index]
+        spec = self.p.spec
+        if key[0] == "phys":
+            legs = [(key[1], 1)]
+        else:
+            legs = [(l, -1 if spec.legs[l].incoming else 1) for l in key]
+        for leg, sg in legs:
+            if leg < 2:
+                continue
+            sgn = sg * sign
+            for mu in range(4):
+                lines.append("    pb[%d] %s= %s[%d];" % (4 * leg + mu, "+" if sgn > 0 else "-", kb, mu))
+
+    def emit(self) -> str:
+        em, p = self.em, self.p
+        order, need = em.schedule()
+        var, cur_order = {}, []
+        fwd = ["    cx<R> J[NCOLOR];", "    #pragma unroll", "    for (int s = 0; s < NCOLOR; ++s) J[s] = cx<R>(R(0), R(0));",
+               "    cx<R> amp;"]
+        accum = {1: "J[%d] += amp;", -1: "J[%d] -= amp;", 1j: "J[%d] += mul_i(amp);", -1j: "J[%d] -= mul_i(amp);"}
+        for d in order:
+            a = p.amps[d]
+            for i in need[d]:
+                if i not in var:
+                    var[i] = "w%d" % i
+                    fwd.append("  " + em._current_code(p.cur[i], var))
+                    cur_order.append(i)
+            fwd.append("    amp = FFV1_0<R>(%s, %s, %s, cp.gs);" % (var[a.row], var[a.col], var[a.bos]))
+            for s_ in np.nonzero(em.coef[d])[0]:
+                fwd.append("    " + accum[complex(em.coef[d, s_])] % s_)
+        nc = em.coef.shape[1]
+        body = list(fwd)
+        # colour sum and its adjoint Jb = 2 C J / den
+        body.append("    R m2 = R(0);")
+        body.append("    cx<R> Jb[NCOLOR];")
+        for i in range(nc):
+            tr = " + ".join("R(%d) * J[%d].re" % (int(em.cnum[i, j]), j) for j in range(nc) if em.cnum[i, j] != 0)
+            ti = " + ".join("R(%d) * J[%d].im" % (int(em.cnum[i, j]), j) for j in range(nc) if em.cnum[i, j] != 0)
+            body.append("    { const R tr = %s, ti = %s; m2 += J[%d].re * tr + J[%d].im * ti;"
+                        " Jb[%d] = cx<R>(R(2) * tr / R(CDEN), R(2) * ti / R(CDEN)); }" % (tr, ti, i, i, i))
+        body.append("    m2 /= R(CDEN);")
+        for i in cur_order:
+            body.append("    W4<R> %sb = w4_zero<R>();" % var[i])
+        body.append("    cx<R> propb[NPROP];")
+        body.append("    #pragma unroll")
+        body.append("    for (int j = 0; j < NPROP; ++j) propb[j] = cx<R>(R(0), R(0));")
+        conjc = {1: "", -1: "-", 1j: "mul_mi", -1j: "mul_i"}
+        for d in reversed(order):
+            a = p.amps[d]
+            terms = []
+            for s_ in np.nonzero(em.coef[d])[0]:
+                z = complex(em.coef[d, s_])
+                terms.append({1: "Jb[%d]", -1: "-Jb[%d]", 1j: "mul_mi(Jb[%d])", -1j: "mul_i(Jb[%d])"}[z] % s_)
+            body.append("    { const cx<R> ab = %s;" % " + ".join(terms))
+            body.append("      FFV1_0_adj<R>(%s, %s, %s, cp.gs, ab, %sb, %sb, %sb); }"
+                        % (var[a.row], var[a.col], var[a.bos], var[a.row], var[a.col], var[a.bos]))
+        for i in reversed(cur_order):
+            c = p.cur[i]
+            v = var[i]
+            if c.vertex == "ext":
+                continue
+            ch = [var[j] for j in c.children]
+            if c.vertex == "ggg":
+                A, B = p.cur[c.children[0]], p.cur[c.children[1]]
+                k1, k2 = em.momentum(A.legs), em.momentum(B.legs)
+                pr = em.prop(c.legs, "g")
+                body.append("    { R kb1[4] = {R(0), R(0), R(0), R(0)}, kb2[4] = {R(0), R(0), R(0), R(0)};")
+                body.append("      VVV1P0_1_adj<R>(%s, %s, K + %d, K + %d, cp.gs, prop[%d], %sb, %sb, %sb, kb1, kb2, propb[%d]);"
+                            % (ch[0], ch[1], 4 * k1, 4 * k2, pr, v, ch[0], ch[1], pr))
+                self._route(k1, "kb1", body)
+                self._route(k2, "kb2", body)
+                body.append("    }")
+            elif c.vertex.startswith("gggg"):
+                fn = ("VVVV1P0_1_adj", "VVVV3P0_1_adj", "VVVV4P0_1_adj")[int(c.vertex[-1])]
+                pr = em.prop(c.legs, "g")
+                body.append("    %s<R>(%s, %s, %s, cp.gs2, prop[%d], %sb, %sb, %sb, %sb, propb[%d]);"
+                            % (fn, ch[0], ch[1], ch[2], pr, v, ch[0], ch[1], ch[2], pr))
+            elif c.vertex == "qqg_row":
+                k = em.momentum(c.legs)
+                pr = em.prop(c.legs, "t")
+                body.append("    { R kb[4] = {R(0), R(0), R(0), R(0)};")
+                body.append("      FFV1_2_adj<R>(%s, %s, cp.gs, K + %d, cp.mt, prop[%d], %sb, %sb, %sb, kb, propb[%d]);"
+                            % (ch[0], ch[1], 4 * k, pr, v, ch[0], ch[1], pr))
+                self._route(k, "kb", body)
+                body.append("    }")
+            else:
+                raise ValueError("no adjoint for %s" % c.vertex)
+        # propagators
+        kinds = {"g": 0, "t": 1, "A": 2, "Z": 3}
+        for j, (mi, kind) in enumerate(em.props):
+            body.append("    { R kb[4] = {R(0), R(0), R(0), R(0)};")
+            body.append("      prop_adj<R>(prop[%d], %s, K + %d, propb[%d], kb);"
+                        % (j, "true" if kind == "t" else "false", 4 * mi, j))
+            self._route(mi, "kb", body)
+            body.append("    }")
+        # external wavefunctions (final-state legs only: beams are constant)
+        spec = p.spec
+        for i in cur_order:
+            c = p.cur[i]
+            if c.vertex != "ext":
+                continue
+            leg = c.children[0]
+            if leg < 2:
+                continue
+            L = spec.legs[leg]
+            kind = 2 if L.kind == "g" else (0 if _is_col(L.kind) else 1)
+            ns = (1 if L.incoming else -1) if L.kind == "g" else (1 if L.particle else -1)
+            m = "cp.mt" if L.mass == "mt" else "R(0)"
+            pm = em.momentum_phys(leg)
+            body.append("    { R kb[4] = {R(0), R(0), R(0), R(0)};")
+            body.append("      external_adj<R>(%d, K + %d, %s, hel[%d], %d, %sb, kb);"
+                        % (kind, 4 * pm, m, leg, ns, var[i]))
+            self._route(pm, "kb", body)
+            body.append("    }")
+        body.append("    return m2;")
+        return "\n".join(body)
+
+
 def bf16_colour_image(cnum) -> np.ndarray:
     """B operand of the tensor-core colour sum: B[n][k] = cnum[k][n] in BF16,
     laid out in the canonical K-major no-swizzle layout (8-row x 16-byte core
@@ -650,6 +783,15 @@ def generate(pid: int) -> str:
     out.append("    J.zero();")
     out.append(body)
     out.append("  }")
+    out.append("  static constexpr bool HAS_GRAD = %s;" % ("true" if pid in GRAD_PROCS else "false"))
+    if pid in GRAD_PROCS:
+        out.append("  // |M_h|^2 of one helicity (colour summed) and its gradient with respect to the")
+        out.append("  // physical momenta of the final-state legs, accumulated into pb[4 * leg + mu]")
+        out.append("  template <class R>")
+        out.append("  static __device__ __forceinline__ R amplitudes_grad(const R* __restrict__ K,"
+                   " const cx<R>* __restrict__ prop, const int* hel, const Couplings<R>& cp, R* pb) {")
+        out.append(GradEmitter(em).emit())
+        out.append("  }")
     out.append("};")
     out.append("}  // namespace mg")
     return "\n".join(out) + "\n"

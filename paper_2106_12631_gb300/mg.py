@@ -58,6 +58,7 @@ def lib():
             L.mg_rambo.argtypes = [i32, i64, ctypes.c_double, vp, i32, vp, vp, vp]
             L.mg_filter_helicities.argtypes = [i32, i64, vp, vp, vp]
             L.mg_sigmakin.argtypes = [i32, i64, vp, vp, vp, i32, vp]
+            L.mg_sigmakin_grad.argtypes = [i32, i64, ctypes.c_double, vp, i32, vp, vp, vp, vp, i32, vp]
             L.mg_event_sum_scratch_bytes.argtypes = [i64]
             L.mg_event_sum_scratch_bytes.restype = i64
             L.mg_event_sum.argtypes = [i64, vp, vp, vp, vp, i64, vp]
@@ -157,6 +158,52 @@ def sigmakin(proc, mom: torch.Tensor, mask: torch.Tensor, mode="mixed", me=None,
                              _dev(mask, torch.int32, "mask", (info["nhel"],)),
                              _dev(me, torch.float64, "me", (nevt,)), m, _stream(stream)), "mg_sigmakin")
     return me
+
+
+def sigmakin_grad(proc, rnd: torch.Tensor, ecm: float, mask: torch.Tensor, mode="mixed", gout=None, grad=None,
+                  me=None, stream=None):
+    """d me / d rnd (times gout) for every event: (grad (nrows, nevt), me (nevt,))."""
+    p = _proc(proc)
+    nrows, nevt = rnd.shape
+    m = MODES[mode] if isinstance(mode, str) else int(mode)
+    if grad is None:
+        grad = torch.empty((nrows, nevt), dtype=torch.float64, device=rnd.device)
+    if me is None:
+        me = torch.empty((nevt,), dtype=torch.float64, device=rnd.device)
+    g = _dev(gout, torch.float64, "gout", (nevt,)) if gout is not None else None
+    _check(lib().mg_sigmakin_grad(p, nevt, float(ecm), _dev(rnd, torch.float64, "rnd"), nrows,
+                                  _dev(mask, torch.int32, "mask"), g,
+                                  _dev(grad, torch.float64, "grad", (nrows, nevt)),
+                                  _dev(me, torch.float64, "me", (nevt,)), m, _stream(stream)), "mg_sigmakin_grad")
+    return grad, me
+
+
+class MatrixElement(torch.autograd.Function):
+    """me = SIGMAKIN(RAMBO(rnd)) with a backward pass through the adjoint kernel.
+
+    forward(rnd (nrows, nevt) float64 CUDA, proc, ecm, mask, mode) -> me (nevt,)
+    backward: grad_rnd = grad_me * d me / d rnd (mg_sigmakin_grad)."""
+
+    @staticmethod
+    def forward(ctx, rnd, proc, ecm, mask, mode="mixed"):
+        mom, _ = rambo(proc, rnd.contiguous(), ecm)
+        me = sigmakin(proc, mom, mask, mode=mode)
+        ctx.save_for_backward(rnd, mask)
+        ctx.args = (proc, ecm, mode)
+        return me
+
+    @staticmethod
+    def backward(ctx, grad_me):
+        rnd, mask = ctx.saved_tensors
+        proc, ecm, mode = ctx.args
+        grad, _ = sigmakin_grad(proc, rnd.contiguous(), ecm, mask, mode=mode,
+                                gout=grad_me.contiguous().to(torch.float64))
+        return grad, None, None, None, None
+
+
+def matrix_element(rnd: torch.Tensor, proc, ecm: float, mask: torch.Tensor, mode="mixed") -> torch.Tensor:
+    """Differentiable me(rnd) (see MatrixElement)."""
+    return MatrixElement.apply(rnd, proc, ecm, mask, mode)
 
 
 def event_sum_scratch_bytes(nevt: int) -> int:
