@@ -89,7 +89,8 @@ def test_me_matches_sigmakin_and_gout_scaling(mg):
     g2, _ = mg.sigmakin_grad(proc, rnd, 1500.0, mask, mode="fp64", gout=gout)
     torch.cuda.synchronize()
     np.testing.assert_allclose(me1.cpu().numpy(), me_s.cpu().numpy(), rtol=1e-13)
-    np.testing.assert_allclose(g2.cpu().numpy(), (g1 * gout).cpu().numpy(), rtol=1e-14, atol=0)
+    # gout is applied before the (linear) RAMBO adjoint: equal up to rounding
+    np.testing.assert_allclose(g2.cpu().numpy(), (g1 * gout).cpu().numpy(), rtol=1e-12, atol=0)
 
 
 def test_autograd_function(mg):
