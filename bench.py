@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--nevt", type=int, default=1 << 20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-others", action="store_true")
     return ap.parse_args()
 
 
@@ -120,6 +121,46 @@ class ClockSampler:
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def measure_other_workloads(mg, I, dev, stream, reps: int = 3) -> dict:
+    """ME/s of SIGMAKIN (FP64 and mixed) for e+e- -> mu+mu-, gg -> t t~, gg -> t t~ g,
+    and of the adjoint gradient of gg -> t t~ g (2^18 events, 16 random rows)."""
+    import torch
+
+    def time_it(fn):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 1e3 / reps
+
+    out = {}
+    for name in ("ee_mumu", "gg_tt", "gg_ttg", "gg_ttg_grad"):
+        w = I.WORKLOADS[name]
+        proc, nevt, nr, ecm = w["proc"], w["nevt"], w["nrows"], w["ecm"]
+        rnd = torch.from_numpy(I.uniforms(I.seed_of(name), nr, nevt)).to(dev)
+        frnd = torch.from_numpy(I.uniforms(I.filter_seed_of(name), nr, 16)).to(dev)
+        mask = mg.filter_helicities(proc, mg.rambo(proc, frnd, ecm)[0])
+        mom, _ = mg.rambo(proc, rnd, ecm)
+        me = torch.empty(nevt, dtype=torch.float64, device=dev)
+        res = {"events": nevt, "good_helicities": int(mask.sum().item())}
+        if name == "gg_ttg_grad":
+            grad = torch.empty((nr, nevt), dtype=torch.float64, device=dev)
+            for mode in ("mixed", "fp64"):
+                t = time_it(lambda: mg.sigmakin_grad(proc, rnd, ecm, mask, mode=mode, grad=grad, me=me,
+                                                     stream=stream))
+                res[mode] = {"value": nevt / t, "unit": "gradients/s", "ms": 1e3 * t}
+        else:
+            for mode in ("mixed", "fp64"):
+                t = time_it(lambda: mg.sigmakin(proc, mom, mask, mode=mode, me=me, stream=stream))
+                res[mode] = {"value": nevt / t, "unit": UNIT, "sigmakin_ms": 1e3 * t}
+        out[name] = res
+    return out
 
 
 def cpu_oracle_rate(nevt_sample: int, seed: int, threads: int):
@@ -261,6 +302,9 @@ def main():
                                           "nonfinite": int((~torch.isfinite(me_main)).sum().item()),
                                           "events": nevt}}
 
+    # the other workloads (SIGMAKIN or the adjoint alone, inputs resident, CUDA events)
+    others = {} if args.no_others else measure_other_workloads(mg, I, dev, stream)
+
     # end to end through the C ABI with host buffers (H2D of the random numbers,
     # D2H of the matrix elements inside the timed region)
     rnd_h = torch.from_numpy(I.uniforms(seed, 16, nevt, first_event=rank * nevt)).pin_memory()
@@ -308,6 +352,7 @@ def main():
                    "parallelism": "dp%d (independent event batches)" % world},
         "sigmakin_ms": 1e3 * ksec,
         "fp64": fp64,
+        "other_workloads": others,
         "event_sum": [float(x) for x in sums.cpu().numpy()],
         "roofline": roofline,
         "clocks": clk,
@@ -316,9 +361,9 @@ def main():
     }
     if rank == 0 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
-        rate, dt = cpu_oracle_rate(2048, seed, cores)
+        rate, dt = cpu_oracle_rate(8192, seed, cores)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": "2048 gg->ttgg events (RAMBO + |M|^2 over all 64 helicities, "
+                                "sample": "8192 gg->ttgg events (RAMBO + |M|^2 over all 64 helicities, "
                                           "explicit colour), FP64, %.1f s wall" % dt}
     if rank == 0:
         print(json.dumps(line))
