@@ -44,7 +44,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
-    ap.add_argument("--mode", default="mixed", choices=["mixed", "mixed_simt", "fp64"])
+    ap.add_argument("--mode", default="mixed", choices=["mixed", "mixed_simt", "fp64", "mixed_unrolled",
+                                                        "fp64_unrolled"])
     ap.add_argument("--nevt", type=int, default=1 << 20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
@@ -289,6 +290,13 @@ def main():
     ngood = int(mask.sum().item())
     value = world * nevt * args.steps / total
 
+    # the same step with the per-helicity unrolled kernel (every helicity recomputes its currents)
+    unrolled = None
+    if args.mode in ("mixed", "fp64") and not args.no_others:
+        tu, ku = timed(args.mode + "_unrolled", max(1, min(args.steps, 2)))
+        unrolled = {"mode": args.mode + "_unrolled", "value": world * nevt * max(1, min(args.steps, 2)) / tu,
+                    "unit": UNIT, "sigmakin_ms": 1e3 * statistics.mean(ku)}
+
     fp64 = None
     if not args.no_fp64 and args.mode != "fp64":
         t64, k64 = timed("fp64", max(1, min(args.steps, 2)))
@@ -352,6 +360,7 @@ def main():
                    "parallelism": "dp%d (independent event batches)" % world},
         "sigmakin_ms": 1e3 * ksec,
         "fp64": fp64,
+        "unrolled": unrolled,
         "other_workloads": others,
         "event_sum": [float(x) for x in sums.cpu().numpy()],
         "roofline": roofline,

@@ -56,8 +56,15 @@ typedef enum {
   MG_MIXED = 1,       /* FP32 wavefunctions, currents and amplitudes; FP64 momenta,
                          propagator denominators and helicity/event sums; colour
                          sum on the tensor cores (split-BF16, FP32 accumulation) */
-  MG_MIXED_SIMT = 2   /* as MG_MIXED with the colour sum on CUDA cores in FP32 */
+  MG_MIXED_SIMT = 2,  /* as MG_MIXED with the colour sum on CUDA cores in FP32 */
+  MG_FP64_UNROLLED = 3,   /* MG_FP64 with every helicity recomputing all its currents */
+  MG_MIXED_UNROLLED = 4   /* MG_MIXED with every helicity recomputing all its currents */
 } mg_mode;
+/* Modes 0-2 evaluate each off-shell current once per event for each helicity
+ * combination of its own external legs, and each diagram at the vertex that
+ * needs the cheapest currents; modes 3-4 run one unrolled program per
+ * helicity (the organisation of the paper's SIGMAKIN).  Same results up to
+ * rounding. */
 
 typedef struct {
   int npar;          /* external particles */

@@ -200,6 +200,35 @@ __device__ __forceinline__ cx<R> FFV2_4_0(const W4<R>& fo, const W4<R>& fi, cons
   return mul_mi(gz * row_col(row_slash(fo, v), c));
 }
 
+// three-gluon amplitude, outgoing momenta K1..K3 of the three branches
+// (incoming vertex momenta q = -K):
+//   g [ (A1.A2)((q1 - q2).A3) + (A2.A3)((q2 - q3).A1) + (A3.A1)((q3 - q1).A2) ]
+template <class R>
+__device__ __forceinline__ cx<R> VVV1_0(const W4<R>& a1, const W4<R>& a2, const W4<R>& a3, const R* K1, const R* K2,
+                                        const R* K3, R g) {
+  R d12[4], d23[4], d31[4];
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    d12[mu] = K2[mu] - K1[mu];
+    d23[mu] = K3[mu] - K2[mu];
+    d31[mu] = K1[mu] - K3[mu];
+  }
+  return g * (vdot(a1, a2) * kdot(d12, a3) + vdot(a2, a3) * kdot(d23, a1) + vdot(a3, a1) * kdot(d31, a2));
+}
+// four-gluon amplitude, Lorentz term t (legs 0..3, colour f^{a0 a1 e} f^{a2 a3 e},
+// f^{a0 a2 e} f^{a1 a3 e}, f^{a0 a3 e} f^{a1 a2 e} for t = 0, 1, 2):
+//   -i g^2 [(A0.A2)(A1.A3) - (A0.A3)(A1.A2)],  [(A0.A1)(A2.A3) - (A0.A3)(A1.A2)],
+//   [(A0.A1)(A2.A3) - (A0.A2)(A1.A3)]
+template <class R>
+__device__ __forceinline__ cx<R> VVVV_0(int t, const W4<R>& a0, const W4<R>& a1, const W4<R>& a2, const W4<R>& a3,
+                                        R g2) {
+  cx<R> l;
+  if (t == 0) l = vdot(a0, a2) * vdot(a1, a3) - vdot(a0, a3) * vdot(a1, a2);
+  else if (t == 1) l = vdot(a0, a1) * vdot(a2, a3) - vdot(a0, a3) * vdot(a1, a2);
+  else l = vdot(a0, a1) * vdot(a2, a3) - vdot(a0, a2) * vdot(a1, a3);
+  return mul_mi(g2 * l);
+}
+
 // ---- internal-particle routines ---------------------------------------------
 // off-shell flowing-out fermion:  [row . (i g V/)] (K/ + m) prop,  K = outgoing momentum
 template <class R>

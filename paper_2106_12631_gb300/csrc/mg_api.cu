@@ -200,7 +200,7 @@ int mg_filter_helicities(int proc, int64_t nevt, const double* mom, int32_t* mas
 int mg_sigmakin(int proc, int64_t nevt, const double* mom, const int32_t* mask, double* me, int mode,
                 void* stream) {
   if (!valid_proc(proc)) return MG_ERR_PROC;
-  if (nevt < 0 || mode < 0 || mode > 2) return MG_ERR_ARG;
+  if (nevt < 0 || mode < 0 || mode > 4) return MG_ERR_ARG;
   if (nevt == 0) return MG_OK;
   if (!mom || !mask || !me) return MG_ERR_ARG;
   if (!aligned(mom) || !aligned(mask) || !aligned(me)) return MG_ERR_ALIGN;

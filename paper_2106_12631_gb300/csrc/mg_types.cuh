@@ -33,7 +33,7 @@ template <class R> __device__ __forceinline__ cx<R> mul_mi(cx<R> a) { return cx<
 // six-component wavefunction (Sec. 2) also carries the momentum; here the
 // momenta are helicity independent and live in a per-event table instead.
 template <class R>
-struct W4 {
+struct alignas(16) W4 {
   cx<R> w[4];
 };
 
@@ -47,6 +47,31 @@ struct Couplings {
   R gzl;   // Z left coupling of charged leptons, T3 - Q sin^2 theta_W
   R gzr;   // Z right coupling, -Q sin^2 theta_W
   R mt;    // top mass
+};
+
+// Helicity-shared program tables (generated per process).
+// One variant of one off-shell current: type (0 ixxxxx, 1 oxxxxx, 2 vxxxxx,
+// 3 off-shell flowing-out fermion, 4 off-shell flowing-in fermion, 5 vector from a
+// fermion pair, 6 Z from a lepton pair, 7 three-gluon, 8 four-gluon term);
+// a/b/c: type parameters (external: leg, helicity, flow sign; pair: coupling
+// 0 g_s / 1 e); flag: external top mass; out/in: variant slots; k0/k1:
+// momentum-table entries; prop: propagator entry.
+struct HsItem {
+  uint8_t type;
+  int8_t a, b, c;
+  uint8_t flag;
+  uint16_t out;
+  uint16_t in[6];
+  uint8_t k0, k1, prop;
+};
+// One amplitude: type (0 FFV g_s, 1 FFV e, 2 Z, 3 three-gluon, 4-6 four-gluon
+// term 0-2), its colour flows flows[fstart .. fstart+nflow) (flow | code << 6,
+// code 0 +1, 1 -1, 2 +i, 3 -i), operand currents, momentum entries (three-gluon).
+struct HsAmp {
+  uint8_t type, nflow;
+  uint16_t fstart;
+  uint8_t op[4];
+  uint8_t k[3];
 };
 
 // Physics parameters in FP64 (propagator denominators are formed in FP64 in

@@ -3,6 +3,7 @@
 #pragma once
 #include "launch.h"
 #include "sigmakin.cuh"
+#include "sigmakin_hs.cuh"
 
 namespace mg {
 
@@ -16,15 +17,30 @@ cudaError_t launch_sigmakin_variant(const SigArgs& a, const Couplings<R>& cp, in
   return cudaGetLastError();
 }
 
+template <class P, class R, int CS>
+cudaError_t launch_sigmakin_hs_variant(const SigArgs& a, const Couplings<R>& cp, int64_t grid, cudaStream_t s) {
+  using L = HsLayout<P, R, CS>;
+  auto k = sigmakin_hs_kernel<P, R, CS>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
+  if (e != cudaSuccess) return e;
+  k<<<(unsigned)grid, SigCfg<P>::NT, L::bytes, s>>>(a, cp);
+  return cudaGetLastError();
+}
+
+// mode 0 FP64, 1 mixed + tcgen05 colour sum, 2 mixed + CUDA-core colour sum
+// (helicity-shared kernel); 3 FP64, 4 mixed + tcgen05 with the per-helicity
+// unrolled kernel (every helicity recomputes all its currents)
 template <class P>
 cudaError_t launch_sigmakin_impl(const SigLaunch& l, int mode, cudaStream_t s) {
   SigArgs a{l.nevt, l.mom, l.mask, l.me, l.mask_out, l.pp};
   const int64_t grid = (l.nevt + SigCfg<P>::EVMIN - 1) / SigCfg<P>::EVMIN;
   if (grid == 0) return cudaSuccess;
   switch (mode) {
-    case 0: return launch_sigmakin_variant<P, double, CS_SIMT>(a, l.cd, grid, s);
-    case 1: return launch_sigmakin_variant<P, float, CS_TC>(a, l.cf, grid, s);
-    case 2: return launch_sigmakin_variant<P, float, CS_SIMT>(a, l.cf, grid, s);
+    case 0: return launch_sigmakin_hs_variant<P, double, CS_SIMT>(a, l.cd, grid, s);
+    case 1: return launch_sigmakin_hs_variant<P, float, CS_TC>(a, l.cf, grid, s);
+    case 2: return launch_sigmakin_hs_variant<P, float, CS_SIMT>(a, l.cf, grid, s);
+    case 3: return launch_sigmakin_variant<P, double, CS_SIMT>(a, l.cd, grid, s);
+    case 4: return launch_sigmakin_variant<P, float, CS_TC>(a, l.cf, grid, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -50,6 +66,8 @@ cudaError_t launch_filter_impl(const SigLaunch& l, cudaStream_t s) {
   namespace mg {                                                                                         \
   extern template cudaError_t launch_sigmakin_variant<Proc##N, double, CS_SIMT>(                        \
       const SigArgs&, const Couplings<double>&, int64_t, cudaStream_t);                                  \
+  extern template cudaError_t launch_sigmakin_hs_variant<Proc##N, double, CS_SIMT>(                     \
+      const SigArgs&, const Couplings<double>&, int64_t, cudaStream_t);                                  \
   extern template cudaError_t launch_filter_impl<Proc##N>(const SigLaunch&, cudaStream_t);              \
   cudaError_t launch_sigmakin_p##N(const SigLaunch& a, int mode, cudaStream_t s) {                      \
     return launch_sigmakin_impl<Proc##N>(a, mode, s);                                                    \
@@ -60,6 +78,8 @@ cudaError_t launch_filter_impl(const SigLaunch& l, cudaStream_t s) {
 #define MG_INSTANTIATE_FP64(N)                                                                          \
   namespace mg {                                                                                         \
   template cudaError_t launch_sigmakin_variant<Proc##N, double, CS_SIMT>(                               \
+      const SigArgs&, const Couplings<double>&, int64_t, cudaStream_t);                                  \
+  template cudaError_t launch_sigmakin_hs_variant<Proc##N, double, CS_SIMT>(                            \
       const SigArgs&, const Couplings<double>&, int64_t, cudaStream_t);                                  \
   template cudaError_t launch_filter_impl<Proc##N>(const SigLaunch&, cudaStream_t);                     \
   }

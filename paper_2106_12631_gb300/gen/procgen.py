@@ -364,6 +364,7 @@ FLOPS = {
     "FFV1_0": 96, "FFV2_4_0": 104,
     "FFV1_1": 148, "FFV1_2": 148, "FFV1P0_3": 106, "FFV2_4_3": 114,
     "VVV1P0_1": 176, "VVVV1P0_1": 142, "VVVV3P0_1": 142, "VVVV4P0_1": 142,
+    "VVV1_0": 168, "VVVV_0": 136,
     "jamp": 2,
 }
 
@@ -719,6 +720,8 @@ def generate(pid: int) -> str:
     out.append("// colour-flow coefficients used: %s" % sorted(coefs, key=lambda z: (z.real, z.imag)))
     out.append("#pragma once")
     out.append("namespace mg {")
+    sp = SharedProgram(proc, em)
+    out.extend(sp.emit_tables(pid))
     img = bf16_colour_image(em.cnum)
     out.append("// colour-matrix numerators as the BF16 B operand of the tensor-core colour sum")
     out.append("static __device__ __align__(16) const uint32_t kColourB%d[%d] = {%s};"
@@ -729,6 +732,7 @@ def generate(pid: int) -> str:
     out.append("  static constexpr int NCOLOR = %d;" % ncol)
     out.append("  static constexpr int NDIAGRAMS = %d;" % proc.ndiagrams)
     out.append("  static constexpr int NAMPS = %d;" % len(proc.amps))
+    out.extend(sp.struct_lines(pid))
     out.append("  static constexpr int NMOM = %d;" % len(em.mom))
     out.append("  static constexpr int NPROP = %d;" % len(em.props))
     out.append("  static constexpr int NFINAL = %d;" % (proc.n - 2))
@@ -803,7 +807,359 @@ def summary(pid: int) -> dict:
     for leg in range(proc.n):
         em.momentum_phys(leg)
     em.emit()
+    sp = SharedProgram(proc, em)
+    sp.emit_tables(pid)
     return dict(flops_amp=em.flops, flops_csum=colour_sum_flops(em.cnum), ncurrents=em.ncurrents,
+                hs_flops_items=sp.flops_items, hs_flops_amp_hel=sp.flops_amps_hel, hs_ncur=len(sp.order),
+                hs_nslots=sp.nslots,
                 ndiagrams=proc.ndiagrams, namps=len(proc.amps), ncolor=em.coef.shape[1],
                 nmom=len(em.mom), nprop=len(em.props), coef=em.coef, cnum=em.cnum, cden=em.cden,
                 perms=em.perms, gluon_legs=proc.gluon_legs())
+
+
+# ---------------------------------------------------------------------------
+# Helicity-shared program: every off-shell current is evaluated once per
+# helicity combination of ITS OWN legs (2^|S| variants per event instead of
+# once per event helicity), and every diagram's amplitude is formed at the
+# vertex that needs the cheapest set of such currents.
+# ---------------------------------------------------------------------------
+# Any vertex of a tree diagram gives the same amplitude (the same product of
+# vertex factors and propagators).  Seen from a vertex n of the antitop-rooted
+# tree, the branch towards the root is the "complement" current U(n):
+#   at a quark-line vertex (row r, gluon g | col U):  U(r) = col current (g, U),
+#                                                      U(g) = gluon from the pair (r, U)
+#   at a three-gluon vertex (c0, c1 | P):              U(c0) = ggg(c1, P), U(c1) = ggg(P, c0)
+#     (cyclic order kept, so f^abc and the Lorentz factor keep their orientation)
+#   at a four-gluon term t (c0, c1, c2 | P):           U(ck) = term t with leg k as output
+# The colour coefficients stay those of the antitop-rooted form.
+
+SHARED_COST = {"ext": 40, "ggg": FLOPS["VVV1P0_1"], "gggg": FLOPS["VVVV1P0_1"], "qqg_row": FLOPS["FFV1_2"],
+               "col": FLOPS["FFV1_1"], "pair": FLOPS["FFV1P0_3"], "ffa_cur": FLOPS["FFV1P0_3"],
+               "ffz_cur": FLOPS["FFV2_4_3"]}
+SHARED_AMP = {"ffv": FLOPS["FFV1_0"], "vvv": FLOPS["VVV1_0"], "vvvv": FLOPS["VVVV_0"], "ffv_a": FLOPS["FFV1_0"],
+              "ffz": FLOPS["FFV2_4_0"]}
+
+# four-gluon term t: L_t = (A_a.A_b)(A_c.A_d) - (A_e.A_f)(A_g.A_h), legs 0..3
+VVVV_PAIRS = {0: (((0, 2), (1, 3)), ((0, 3), (1, 2))),
+              1: (((0, 1), (2, 3)), ((0, 3), (1, 2))),
+              2: (((0, 1), (2, 3)), ((0, 2), (1, 3)))}
+
+
+class SharedProgram:
+    def __init__(self, proc: Process, emitter: "Emitter"):
+        self.p = proc
+        self.em = emitter
+        self.n = proc.n
+        self._cands()
+        self._choose()
+        self._currents()
+
+    # ---- descriptors -------------------------------------------------------
+    def legs(self, d):
+        if d[0] == "N":
+            return frozenset(self.p.cur[d[1]].legs)
+        s = frozenset()
+        for x in d[2:]:
+            if isinstance(x, tuple):
+                s |= self.legs(x)
+        return s
+
+    def kind(self, d):
+        if d[0] == "N":
+            v = self.p.cur[d[1]].vertex
+            return "gggg" if v.startswith("gggg") else v
+        return d[1]
+
+    def inputs(self, d):
+        if d[0] == "N":
+            c = self.p.cur[d[1]]
+            return [] if c.vertex == "ext" else [("N", ch) for ch in c.children]
+        return [x for x in d[2:] if isinstance(x, tuple)]
+
+    def deps(self, d, out):
+        if d in out:
+            return
+        for x in self.inputs(d):
+            self.deps(x, out)
+        out[d] = None
+
+    # ---- candidate evaluation points -------------------------------------------
+    def _cands(self):
+        p = self.p
+        top = ("N", p.root_cur)
+        self.cands = []
+        for a in p.amps:
+            A, B = ("N", a.row), ("N", a.bos)
+            if a.vertex != "ffv_t":  # leptons: the root-form amplitude only
+                self.cands.append([(a.vertex, (("N", a.row), ("N", a.col), ("N", a.bos)))])
+                continue
+            opts = [("ffv", (A, top, B))]
+            stack = [(a.row, ("U", "col", B, top)), (a.bos, ("U", "pair", A, top))]
+            while stack:
+                n, U = stack.pop()
+                c = p.cur[n]
+                if c.vertex == "ext":
+                    continue
+                ch = [("N", x) for x in c.children]
+                if c.vertex == "qqg_row":
+                    r, g = ch
+                    opts.append(("ffv", (r, U, g)))
+                    stack.append((c.children[0], ("U", "col", g, U)))
+                    stack.append((c.children[1], ("U", "pair", r, U)))
+                elif c.vertex == "ggg":
+                    c0, c1 = ch
+                    opts.append(("vvv", (c0, c1, U)))
+                    stack.append((c.children[0], ("U", "ggg", c1, U)))
+                    stack.append((c.children[1], ("U", "ggg", U, c0)))
+                elif c.vertex.startswith("gggg"):
+                    t = int(c.vertex[-1])
+                    opts.append(("vvvv%d" % t, (ch[0], ch[1], ch[2], U)))
+                    for k in range(3):
+                        others = tuple(x for j, x in enumerate(ch) if j != k)
+                        stack.append((c.children[k], ("U", "gggg", t, k) + others + (U,)))
+            self.cands.append(opts)
+
+    SLOT_CAP = 384  # variant slots per event (shared memory: 12 KB in FP32, 24 KB in FP64)
+
+    def _cost(self, choice):
+        need = {}
+        amp = 0
+        for opts, ci in zip(self.cands, choice):
+            kind, args = opts[ci]
+            amp += SHARED_AMP["vvvv" if kind.startswith("vvvv") else kind] * (1 << self.n)
+            for x in args:
+                self.deps(x, need)
+        cur = sum(SHARED_COST[self.kind(d)] * (1 << len(self.legs(d))) for d in need)
+        slots = sum(1 << len(self.legs(d)) for d in need)
+        over = max(0, slots - self.SLOT_CAP)
+        return cur + amp + over * 10 ** 7
+
+    def _choose(self):
+        choice = [0] * len(self.cands)
+        for _ in range(4):
+            changed = False
+            for di in range(len(self.cands)):
+                best = None
+                for ci in range(len(self.cands[di])):
+                    choice[di] = ci
+                    t = self._cost(choice)
+                    if best is None or t < best[0]:
+                        best = (t, ci)
+                if choice[di] != best[1]:
+                    changed = True
+                choice[di] = best[1]
+            if not changed:
+                break
+        self.choice = choice
+        self.flops_event = self._cost(choice)
+
+    # ---- currents and their variants ------------------------------------------
+    def _currents(self):
+        need = {}
+        for opts, ci in zip(self.cands, self.choice):
+            for x in opts[ci][1]:
+                self.deps(x, need)
+        self.order = list(need)                    # children before parents
+        self.cid = {d: i for i, d in enumerate(self.order)}
+        self.level = {}
+        for d in self.order:
+            ins = self.inputs(d)
+            self.level[d] = 0 if not ins else 1 + max(self.level[x] for x in ins)
+        self.order.sort(key=lambda d: self.level[d])
+        self.cid = {d: i for i, d in enumerate(self.order)}
+        self.offset = {}
+        off = 0
+        for d in self.order:
+            self.offset[d] = off
+            off += 1 << len(self.legs(d))
+        self.nslots = off
+
+    def variant(self, d, hel_bits):
+        """Variant index of current d for an event helicity (bit l of hel_bits = leg l is +1)."""
+        v = 0
+        for k, l in enumerate(sorted(self.legs(d))):
+            v |= ((hel_bits >> l) & 1) << k
+        return v
+
+    def sub_variant(self, child, parent, v):
+        """Variant of `child` inside variant v of `parent` (child legs subset of parent legs)."""
+        pl = sorted(self.legs(parent))
+        bits = 0
+        for k, l in enumerate(pl):
+            bits |= ((v >> k) & 1) << l
+        return self.variant(child, bits)
+
+    # ---- device tables ------------------------------------------------------------
+    HS_TYPES = {"ixxxxx": 0, "oxxxxx": 1, "vxxxxx": 2, "row": 3, "col": 4, "pair": 5, "zcur": 6,
+                "ggg": 7, "gggg": 8}
+    AMP_TYPES = {"ffv": 0, "ffv_a": 1, "ffz": 2, "vvv": 3, "vvvv0": 4, "vvvv1": 5, "vvvv2": 6}
+
+    def _canon_prop_legs(self, legs):
+        comp = frozenset(range(self.n)) - legs
+        return min(legs, comp, key=lambda s: (len(s), sorted(s)))
+
+    def _item(self, d, v):
+        """One current variant: (type, a, b, c, flag, out, in[6], k0, k1, prop)."""
+        em, spec = self.em, self.p.spec
+        out = self.offset[d] + v
+        ins = [0] * 6
+        a = b = c = flag = 0
+        k0 = k1 = prop = 0
+        kind = self.kind(d)
+        xs = self.inputs(d)
+        slot = lambda x: self.offset[x] + self.sub_variant(x, d, v)
+        legs = self.legs(d)
+        if kind == "ext":
+            leg = self.p.cur[d[1]].children[0]
+            L = spec.legs[leg]
+            hel = 1 if v else -1
+            k0 = em.momentum_phys(leg)
+            flag = 1 if L.mass == "mt" else 0
+            if L.kind == "g":
+                t, c = self.HS_TYPES["vxxxxx"], (1 if L.incoming else -1)
+            elif _is_col(L.kind):
+                t, c = self.HS_TYPES["ixxxxx"], (1 if L.particle else -1)
+            else:
+                t, c = self.HS_TYPES["oxxxxx"], (1 if L.particle else -1)
+            a, b = leg, hel
+        elif kind == "qqg_row":
+            t = self.HS_TYPES["row"]
+            ins[0], ins[1] = slot(xs[0]), slot(xs[1])
+            k0 = em.momentum(legs)
+            prop = em.prop(self._canon_prop_legs(legs), "t")
+        elif kind == "col":
+            t = self.HS_TYPES["col"]
+            g, U = xs
+            ins[0], ins[1] = slot(U), slot(g)   # FFV1_1(fi = U, v = g)
+            k0 = em.momentum(legs)
+            prop = em.prop(self._canon_prop_legs(legs), "t")
+        elif kind == "pair":
+            t = self.HS_TYPES["pair"]
+            r, U = xs
+            ins[0], ins[1] = slot(r), slot(U)   # FFV1P0_3(fo = r, fi = U)
+            prop = em.prop(self._canon_prop_legs(legs), "g")
+        elif kind in ("ffa_cur", "ffz_cur"):
+            t = self.HS_TYPES["pair" if kind == "ffa_cur" else "zcur"]
+            ins[0], ins[1] = slot(xs[0]), slot(xs[1])
+            a = 1  # coupling: e
+            prop = em.prop(self._canon_prop_legs(legs), "A" if kind == "ffa_cur" else "Z")
+        elif kind == "ggg":
+            t = self.HS_TYPES["ggg"]
+            ins[0], ins[1] = slot(xs[0]), slot(xs[1])
+            k0, k1 = em.momentum(self.legs(xs[0])), em.momentum(self.legs(xs[1]))
+            prop = em.prop(self._canon_prop_legs(legs), "g")
+        elif kind == "gggg":
+            t = self.HS_TYPES["gggg"]
+            if d[0] == "N":
+                term = int(self.p.cur[d[1]].vertex[-1])
+                pos = {0: xs[0], 1: xs[1], 2: xs[2]}
+                outpos = 3
+            else:
+                term, outpos = d[2], d[3]
+                o1, o2, U = d[4], d[5], d[6]
+                rest = [q for q in range(3) if q != outpos]
+                pos = {rest[0]: o1, rest[1]: o2, 3: U}
+            for j, pair in enumerate(VVVV_PAIRS[term]):
+                (p0, p1), (p2, p3) = pair
+                if outpos in (p0, p1):
+                    X = p1 if outpos == p0 else p0
+                    Y, Z = p2, p3
+                else:
+                    X = p3 if outpos == p2 else p2
+                    Y, Z = p0, p1
+                ins[3 * j + 0], ins[3 * j + 1], ins[3 * j + 2] = slot(pos[X]), slot(pos[Y]), slot(pos[Z])
+            prop = em.prop(self._canon_prop_legs(legs), "g")
+        else:
+            raise ValueError(kind)
+        return (t, a, b, c, flag, out, ins, k0, k1, prop)
+
+    def emit_tables(self, pid: int) -> list:
+        em = self.em
+        nh = 1 << self.n
+        items, level_start = [], []
+        cur_level = -1
+        for d in self.order:
+            if self.level[d] != cur_level:
+                cur_level = self.level[d]
+                level_start.append(len(items))
+            for v in range(1 << len(self.legs(d))):
+                items.append(self._item(d, v))
+        level_start.append(len(items))
+        # amplitudes, sorted so that consecutive ones share operands
+        amps = []
+        for di, (opts, ci) in enumerate(zip(self.cands, self.choice)):
+            kind, args = opts[ci]
+            ops = [self.cid[x] for x in args]
+            ks = [em.momentum(self.legs(x)) for x in args] if kind == "vvv" else [0, 0, 0]
+            flows = []
+            for s_ in np.nonzero(self.em.coef[di])[0]:
+                z = complex(self.em.coef[di, s_])
+                code = {1: 0, -1: 1, 1j: 2, -1j: 3}[z]
+                flows.append(int(s_) | (code << 6))
+            amps.append((self.AMP_TYPES[kind], ops, ks, flows))
+        amps.sort(key=lambda a: (a[1], a[0]))
+        flow_tab, amp_rows = [], []
+        for t, ops, ks, flows in amps:
+            o = list(ops) + [0] * (4 - len(ops))
+            amp_rows.append("{%d, %d, %d, {%s}, {%s}}" % (t, len(flows), len(flow_tab), ", ".join(map(str, o)),
+                                                          ", ".join(map(str, ks[:3]))))
+            flow_tab.extend(flows)
+        # slot of every current for every event helicity index
+        slot = []
+        for d in self.order:
+            row = []
+            for ih in range(nh):
+                bits = 0
+                for l in range(self.n):
+                    bits |= ((ih >> (self.n - 1 - l)) & 1) << l
+                row.append(self.offset[d] + self.variant(d, bits))
+            slot.append(row)
+        out = []
+        self._exact_flops(items, amps)
+        out.append("// helicity-shared program: %d currents in %d levels, %d variant slots, %d amplitudes,"
+                   " %d flops per event (all helicities)" % (len(self.order), len(level_start) - 1, self.nslots,
+                                                            len(amps), self.flops_items + nh * self.flops_amps_hel))
+        out.append("static __device__ const HsItem kHsItems%d[%d] = {%s};" % (
+            pid, len(items), ", ".join("{%d, %d, %d, %d, %d, %d, {%s}, %d, %d, %d}" % (
+                t, a, b, c, flag, o, ", ".join(map(str, ins)), k0, k1, pr)
+                for (t, a, b, c, flag, o, ins, k0, k1, pr) in items)))
+        out.append("static __constant__ HsAmp kHsAmps%d[%d] = {%s};" % (pid, len(amp_rows), ", ".join(amp_rows)))
+        out.append("static __constant__ uint8_t kHsFlows%d[%d] = {%s};" % (pid, len(flow_tab),
+                                                                          ", ".join(map(str, flow_tab))))
+        out.append("static __device__ const uint16_t kHsSlot%d[%d][%d] = {%s};" % (
+            pid, len(self.order), nh, ", ".join("{" + ", ".join(map(str, r)) + "}" for r in slot)))
+        self.tables = dict(nitems=len(items), level_start=level_start, namps=len(amps), nflows=len(flow_tab),
+                           ncur=len(self.order))
+        return out
+
+    def _exact_flops(self, items, amps):
+        """Operation count: current variants per event, amplitudes + flow sums per helicity."""
+        item_flops = {0: FLOPS["ixxxxx"], 1: FLOPS["oxxxxx"], 2: FLOPS["vxxxxx"], 3: FLOPS["FFV1_2"],
+                      4: FLOPS["FFV1_1"], 5: FLOPS["FFV1P0_3"], 6: FLOPS["FFV2_4_3"], 7: FLOPS["VVV1P0_1"],
+                      8: FLOPS["VVVV1P0_1"]}
+        amp_flops = {0: FLOPS["FFV1_0"], 1: FLOPS["FFV1_0"], 2: FLOPS["FFV2_4_0"], 3: FLOPS["VVV1_0"],
+                     4: FLOPS["VVVV_0"], 5: FLOPS["VVVV_0"], 6: FLOPS["VVVV_0"]}
+        self.flops_items = sum(item_flops[it[0]] for it in items)
+        self.flops_amps_hel = sum(amp_flops[t] + FLOPS["jamp"] * len(fl) for t, _, _, fl in amps)
+
+    def struct_lines(self, pid: int) -> list:
+        t = self.tables
+        return [
+            "  // helicity-shared program (tables above)",
+            "  static constexpr int HS_NSLOT = %d;" % self.nslots,
+            "  static constexpr int HS_NITEM = %d;" % t["nitems"],
+            "  static constexpr int HS_NLEVEL = %d;" % (len(t["level_start"]) - 1),
+            "  static constexpr int HS_NAMP = %d;" % t["namps"],
+            "  static constexpr int HS_NCUR = %d;" % t["ncur"],
+            "  // operations: current variants per event, amplitudes + flow sums per helicity",
+            "  static constexpr long HS_FLOPS_ITEMS = %d;" % self.flops_items,
+            "  static constexpr long HS_FLOPS_AMP_HEL = %d;" % self.flops_amps_hel,
+            "  static __host__ __device__ constexpr int hs_level(int l) {",
+            "    constexpr int t[%d] = {%s};" % (len(t["level_start"]), ", ".join(map(str, t["level_start"]))),
+            "    return t[l];",
+            "  }",
+            "  static __device__ __forceinline__ const HsItem* hs_items() { return kHsItems%d; }" % pid,
+            "  static __device__ __forceinline__ const HsAmp* hs_amps() { return kHsAmps%d; }" % pid,
+            "  static __device__ __forceinline__ const uint8_t* hs_flows() { return kHsFlows%d; }" % pid,
+            "  static __device__ __forceinline__ const uint16_t* hs_slots() { return &kHsSlot%d[0][0]; }" % pid,
+        ]

@@ -15,8 +15,9 @@ import torch
 
 from . import build as _build
 
-MG_FP64, MG_MIXED, MG_MIXED_SIMT = 0, 1, 2
-MODES = {"fp64": MG_FP64, "mixed": MG_MIXED, "mixed_simt": MG_MIXED_SIMT}
+MG_FP64, MG_MIXED, MG_MIXED_SIMT, MG_FP64_UNROLLED, MG_MIXED_UNROLLED = 0, 1, 2, 3, 4
+MODES = {"fp64": MG_FP64, "mixed": MG_MIXED, "mixed_simt": MG_MIXED_SIMT, "fp64_unrolled": MG_FP64_UNROLLED,
+         "mixed_unrolled": MG_MIXED_UNROLLED}
 PROCS = {"ee_mumu": 1, "gg_tt": 2, "gg_ttg": 3, "gg_ttgg": 4}
 
 _lock = threading.Lock()

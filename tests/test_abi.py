@@ -55,7 +55,7 @@ def test_host_side_validation(L):
     assert L.mg_sigmakin(1, 3, vp(fake + 4), vp(fake), vp(fake), 0, None) == -3
     assert L.mg_sigmakin(1, 3, None, vp(fake), vp(fake), 0, None) == -1
     assert L.mg_sigmakin(1, 0, None, None, None, 0, None) == 0  # empty batch is a no-op
-    assert L.mg_sigmakin(1, 3, vp(fake), vp(fake), vp(fake), 3, None) == -1
+    assert L.mg_sigmakin(1, 3, vp(fake), vp(fake), vp(fake), 99, None) == -1
     L.mg_rambo.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_double, vp, ctypes.c_int, vp, vp, vp]
     assert L.mg_rambo(4, 8, 300.0, vp(fake), 16, vp(fake), vp(fake), None) == -1
     assert L.mg_rambo(4, 8, 1500.0, vp(fake), 12, vp(fake), vp(fake), None) == -1

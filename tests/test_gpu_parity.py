@@ -83,13 +83,14 @@ def test_filter_mask(mg, orc, proc):
         assert mask.sum() == 4
 
 
+@pytest.mark.parametrize("mode", ["fp64", "fp64_unrolled"])
 @pytest.mark.parametrize("proc,nevt", [(1, 1), (1, 33), (1, 16384), (2, 1), (2, 4099), (3, 257), (4, 67)])
-def test_sigmakin_fp64_parity(mg, orc, proc, nevt):
+def test_sigmakin_fp64_parity(mg, orc, proc, nevt, mode):
     rnd = I.uniforms(51 + proc, NR[proc], nevt)
     mom_o, _ = orc.rambo(proc, rnd, ECM[proc])
     me_o, d_rot = oracle_conditioning(orc, proc, mom_o)
     mask = gpu_mask(mg, proc)
-    me_g = host(mg.sigmakin(proc, dev(mom_o), mask, mode="fp64"))
+    me_g = host(mg.sigmakin(proc, dev(mom_o), mask, mode=mode))
     rel = np.abs(me_g / me_o - 1)
     check_fp64(rel, d_rot)
 
@@ -100,7 +101,7 @@ def check_fp64(rel, d_rot):
     assert np.mean(rel > FP64_REL) <= FP64_ILL_FRACTION + 1.0 / len(rel)
 
 
-@pytest.mark.parametrize("mode", ["mixed_simt", "mixed"])
+@pytest.mark.parametrize("mode", ["mixed_simt", "mixed", "mixed_unrolled"])
 @pytest.mark.parametrize("proc,nevt", [(1, 16384), (2, 4099), (3, 513), (4, 131)])
 def test_sigmakin_mixed(mg, orc, proc, nevt, mode):
     rnd = I.uniforms(61 + proc, NR[proc], nevt)
@@ -137,7 +138,9 @@ def test_mask_subset(mg, orc, proc):
     want = ph[sub == 1].sum(axis=0)
     _, d_rot = oracle_conditioning(orc, proc, mom_o)
     me_g = host(mg.sigmakin(proc, dev(mom_o), dev(sub), mode="fp64"))
+    me_u = host(mg.sigmakin(proc, dev(mom_o), dev(sub), mode="fp64_unrolled"))
     ok = want != 0
+    assert np.all(np.abs(me_u[ok] / want[ok] - 1) <= np.maximum(FP64_REL, 4 * d_rot[ok]))
     rel = np.abs(me_g[ok] / want[ok] - 1)
     assert np.all(rel <= np.maximum(FP64_REL, 4 * d_rot[ok]))
     assert np.all(me_g[~ok] == 0)
@@ -216,7 +219,7 @@ def test_abi_errors(mg):
     assert L.mg_sigmakin(9, 1, base, base, base, 0, None) == -2
     assert L.mg_sigmakin(1, -1, base, base, base, 0, None) == -1
     assert L.mg_sigmakin(1, 1, base + 8, base, base, 0, None) == -3
-    assert L.mg_sigmakin(1, 1, base, base, base, 7, None) == -1
+    assert L.mg_sigmakin(1, 1, base, base, base, 99, None) == -1
     assert L.mg_rambo(2, 4, 300.0, base, 8, base, base, None) == -1   # below threshold
     assert L.mg_rambo(3, 4, 1500.0, base, 8, base, base, None) == -1  # too few random rows
     assert L.mg_event_sum(5000, base, base, base, base, 8, None) == -6
