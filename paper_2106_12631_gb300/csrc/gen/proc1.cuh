@@ -6,8 +6,7 @@
 namespace mg {
 // helicity-shared program: 6 currents in 2 levels, 16 variant slots, 2 amplitudes, 4504 flops per event (all helicities)
 static __device__ const HsItem kHsItems1[16] = {{1, 3, -1, 1, 0, 0, {0, 0, 0, 0, 0, 0}, 3, 0, 0}, {1, 3, 1, 1, 0, 1, {0, 0, 0, 0, 0, 0}, 3, 0, 0}, {0, 2, -1, -1, 0, 2, {0, 0, 0, 0, 0, 0}, 2, 0, 0}, {0, 2, 1, -1, 0, 3, {0, 0, 0, 0, 0, 0}, 2, 0, 0}, {1, 0, -1, -1, 0, 4, {0, 0, 0, 0, 0, 0}, 0, 0, 0}, {1, 0, 1, -1, 0, 5, {0, 0, 0, 0, 0, 0}, 0, 0, 0}, {0, 1, -1, 1, 0, 6, {0, 0, 0, 0, 0, 0}, 1, 0, 0}, {0, 1, 1, 1, 0, 7, {0, 0, 0, 0, 0, 0}, 1, 0, 0}, {5, 1, 0, 0, 0, 8, {4, 6, 0, 0, 0, 0}, 0, 0, 0}, {5, 1, 0, 0, 0, 9, {5, 6, 0, 0, 0, 0}, 0, 0, 0}, {5, 1, 0, 0, 0, 10, {4, 7, 0, 0, 0, 0}, 0, 0, 0}, {5, 1, 0, 0, 0, 11, {5, 7, 0, 0, 0, 0}, 0, 0, 0}, {6, 1, 0, 0, 0, 12, {4, 6, 0, 0, 0, 0}, 0, 0, 1}, {6, 1, 0, 0, 0, 13, {5, 6, 0, 0, 0, 0}, 0, 0, 1}, {6, 1, 0, 0, 0, 14, {4, 7, 0, 0, 0, 0}, 0, 0, 1}, {6, 1, 0, 0, 0, 15, {5, 7, 0, 0, 0, 0}, 0, 0, 1}};
-static __constant__ HsAmp kHsAmps1[2] = {{1, 1, 0, {0, 1, 4, 0}, {0, 0, 0}}, {2, 1, 1, {0, 1, 5, 0}, {0, 0, 0}}};
-static __constant__ uint8_t kHsFlows1[2] = {0, 0};
+static __constant__ HsAmp kHsAmps1[2] = {{1, 0, {0, 1, 4, 0}, {0, 0, 0}}, {2, 0, {0, 1, 5, 0}, {0, 0, 0}}};
 static __device__ const uint16_t kHsSlot1[6][16] = {{0, 1, 0, 1, 0, 1, 0, 1, 0, 1, 0, 1, 0, 1, 0, 1}, {2, 2, 3, 3, 2, 2, 3, 3, 2, 2, 3, 3, 2, 2, 3, 3}, {4, 4, 4, 4, 4, 4, 4, 4, 5, 5, 5, 5, 5, 5, 5, 5}, {6, 6, 6, 6, 7, 7, 7, 7, 6, 6, 6, 6, 7, 7, 7, 7}, {8, 8, 8, 8, 10, 10, 10, 10, 9, 9, 9, 9, 11, 11, 11, 11}, {12, 12, 12, 12, 14, 14, 14, 14, 13, 13, 13, 13, 15, 15, 15, 15}};
 // colour-matrix numerators as the BF16 B operand of the tensor-core colour sum
 static __device__ __align__(16) const uint32_t kColourB1[128] = {0x00003f80, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000};
@@ -32,8 +31,16 @@ struct Proc1 {
   }
   static __device__ __forceinline__ const HsItem* hs_items() { return kHsItems1; }
   static __device__ __forceinline__ const HsAmp* hs_amps() { return kHsAmps1; }
-  static __device__ __forceinline__ const uint8_t* hs_flows() { return kHsFlows1; }
   static __device__ __forceinline__ const uint16_t* hs_slots() { return &kHsSlot1[0][0]; }
+  static constexpr int HS_NPAT = 1;
+  // colour-flow updates of each amplitude pattern: J_s += amp, -amp, i amp, -i amp
+  template <class R>
+  static __device__ __forceinline__ void hs_flows(int pat, cx<R> amp, cx<R>* J) {
+    switch (pat) {
+      case 0: J[0] += amp; break;
+      default: break;
+    }
+  }
   static constexpr int NMOM = 5;
   static constexpr int NPROP = 2;
   static constexpr int NFINAL = 2;

@@ -5,9 +5,8 @@
 #pragma once
 namespace mg {
 // helicity-shared program: 7 currents in 2 levels, 20 variant slots, 3 amplitudes, 6884 flops per event (all helicities)
-static __device__ const HsItem kHsItems2[20] = {{1, 2, -1, 1, 1, 0, {0, 0, 0, 0, 0, 0}, 2, 0, 0}, {1, 2, 1, 1, 1, 1, {0, 0, 0, 0, 0, 0}, 2, 0, 0}, {0, 3, -1, -1, 1, 2, {0, 0, 0, 0, 0, 0}, 3, 0, 0}, {0, 3, 1, -1, 1, 3, {0, 0, 0, 0, 0, 0}, 3, 0, 0}, {2, 0, -1, 1, 0, 4, {0, 0, 0, 0, 0, 0}, 0, 0, 0}, {2, 0, 1, 1, 0, 5, {0, 0, 0, 0, 0, 0}, 0, 0, 0}, {2, 1, -1, 1, 0, 6, {0, 0, 0, 0, 0, 0}, 1, 0, 0}, {2, 1, 1, 1, 0, 7, {0, 0, 0, 0, 0, 0}, 1, 0, 0}, {7, 0, 0, 0, 0, 8, {4, 6, 0, 0, 0, 0}, 4, 5, 0}, {7, 0, 0, 0, 0, 9, {5, 6, 0, 0, 0, 0}, 4, 5, 0}, {7, 0, 0, 0, 0, 10, {4, 7, 0, 0, 0, 0}, 4, 5, 0}, {7, 0, 0, 0, 0, 11, {5, 7, 0, 0, 0, 0}, 4, 5, 0}, {3, 0, 0, 0, 0, 12, {0, 4, 0, 0, 0, 0}, 7, 0, 1}, {3, 0, 0, 0, 0, 13, {0, 5, 0, 0, 0, 0}, 7, 0, 1}, {3, 0, 0, 0, 0, 14, {1, 4, 0, 0, 0, 0}, 7, 0, 1}, {3, 0, 0, 0, 0, 15, {1, 5, 0, 0, 0, 0}, 7, 0, 1}, {3, 0, 0, 0, 0, 16, {0, 6, 0, 0, 0, 0}, 8, 0, 3}, {3, 0, 0, 0, 0, 17, {0, 7, 0, 0, 0, 0}, 8, 0, 3}, {3, 0, 0, 0, 0, 18, {1, 6, 0, 0, 0, 0}, 8, 0, 3}, {3, 0, 0, 0, 0, 19, {1, 7, 0, 0, 0, 0}, 8, 0, 3}};
-static __constant__ HsAmp kHsAmps2[3] = {{0, 2, 0, {0, 1, 4, 0}, {0, 0, 0}}, {0, 1, 2, {5, 1, 3, 0}, {0, 0, 0}}, {0, 1, 3, {6, 1, 2, 0}, {0, 0, 0}}};
-static __constant__ uint8_t kHsFlows2[4] = {192, 129, 0, 1};
+static __device__ const HsItem kHsItems2[20] = {{1, 2, -1, 1, 1, 0, {0, 0, 0, 0, 0, 0}, 2, 0, 0}, {1, 2, 1, 1, 1, 1, {0, 0, 0, 0, 0, 0}, 2, 0, 0}, {0, 3, -1, -1, 1, 2, {0, 0, 0, 0, 0, 0}, 3, 0, 0}, {0, 3, 1, -1, 1, 3, {0, 0, 0, 0, 0, 0}, 3, 0, 0}, {2, 0, -1, 1, 0, 4, {0, 0, 0, 0, 0, 0}, 0, 0, 0}, {2, 0, 1, 1, 0, 5, {0, 0, 0, 0, 0, 0}, 0, 0, 0}, {2, 1, -1, 1, 0, 6, {0, 0, 0, 0, 0, 0}, 1, 0, 0}, {2, 1, 1, 1, 0, 7, {0, 0, 0, 0, 0, 0}, 1, 0, 0}, {7, 0, 0, 0, 0, 8, {4, 6, 0, 0, 0, 0}, 4, 5, 0}, {7, 0, 0, 0, 0, 9, {5, 6, 0, 0, 0, 0}, 4, 5, 0}, {7, 0, 0, 0, 0, 10, {4, 7, 0, 0, 0, 0}, 4, 5, 0}, {7, 0, 0, 0, 0, 11, {5, 7, 0, 0, 0, 0}, 4, 5, 0}, {3, 0, 0, 0, 0, 12, {0, 4, 0, 0, 0, 0}, 7, 0, 1}, {3, 0, 0, 0, 0, 13, {0, 5, 0, 0, 0, 0}, 7, 0, 1}, {3, 0, 0, 0, 0, 14, {1, 4, 0, 0, 0, 0}, 7, 0, 1}, {3, 0, 0, 0, 0, 15, {1, 5, 0, 0, 0, 0}, 7, 0, 1}, {3, 0, 0, 0, 0, 16, {0, 6, 0, 0, 0, 0}, 8, 0, 2}, {3, 0, 0, 0, 0, 17, {0, 7, 0, 0, 0, 0}, 8, 0, 2}, {3, 0, 0, 0, 0, 18, {1, 6, 0, 0, 0, 0}, 8, 0, 2}, {3, 0, 0, 0, 0, 19, {1, 7, 0, 0, 0, 0}, 8, 0, 2}};
+static __constant__ HsAmp kHsAmps2[3] = {{0, 0, {0, 1, 4, 0}, {0, 0, 0}}, {0, 1, {5, 1, 3, 0}, {0, 0, 0}}, {0, 2, {6, 1, 2, 0}, {0, 0, 0}}};
 static __device__ const uint16_t kHsSlot2[7][16] = {{0, 0, 1, 1, 0, 0, 1, 1, 0, 0, 1, 1, 0, 0, 1, 1}, {2, 3, 2, 3, 2, 3, 2, 3, 2, 3, 2, 3, 2, 3, 2, 3}, {4, 4, 4, 4, 4, 4, 4, 4, 5, 5, 5, 5, 5, 5, 5, 5}, {6, 6, 6, 6, 7, 7, 7, 7, 6, 6, 6, 6, 7, 7, 7, 7}, {8, 8, 8, 8, 10, 10, 10, 10, 9, 9, 9, 9, 11, 11, 11, 11}, {12, 12, 14, 14, 12, 12, 14, 14, 13, 13, 15, 15, 13, 13, 15, 15}, {16, 16, 18, 18, 17, 17, 19, 19, 16, 16, 18, 18, 17, 17, 19, 19}};
 // colour-matrix numerators as the BF16 B operand of the tensor-core colour sum
 static __device__ __align__(16) const uint32_t kColourB2[128] = {0xc0004180, 0x00000000, 0x00000000, 0x00000000, 0x4180c000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000};
@@ -32,10 +31,20 @@ struct Proc2 {
   }
   static __device__ __forceinline__ const HsItem* hs_items() { return kHsItems2; }
   static __device__ __forceinline__ const HsAmp* hs_amps() { return kHsAmps2; }
-  static __device__ __forceinline__ const uint8_t* hs_flows() { return kHsFlows2; }
   static __device__ __forceinline__ const uint16_t* hs_slots() { return &kHsSlot2[0][0]; }
-  static constexpr int NMOM = 10;
-  static constexpr int NPROP = 4;
+  static constexpr int HS_NPAT = 3;
+  // colour-flow updates of each amplitude pattern: J_s += amp, -amp, i amp, -i amp
+  template <class R>
+  static __device__ __forceinline__ void hs_flows(int pat, cx<R> amp, cx<R>* J) {
+    switch (pat) {
+      case 0: J[0] -= mul_i(amp); J[1] += mul_i(amp); break;
+      case 1: J[0] += amp; break;
+      case 2: J[1] += amp; break;
+      default: break;
+    }
+  }
+  static constexpr int NMOM = 9;
+  static constexpr int NPROP = 3;
   static constexpr int NFINAL = 2;
   // floating-point operations per helicity: diagram program, CUDA-core colour sum
   static constexpr long FLOPS_AMP = 898;
@@ -43,12 +52,12 @@ struct Proc2 {
   static constexpr double NORM = 1.0 / 256.0;  // 1/(helicity avg x colour avg x symmetry)
   // momentum table: {0 physical / 1 all-outgoing sum, leg mask, mask of legs entering as -p}
   static __host__ __device__ constexpr int mom(int j, int k) {
-    constexpr int t[NMOM][3] = {{0, 1, 0}, {0, 2, 0}, {0, 4, 0}, {0, 8, 0}, {1, 1, 1}, {1, 2, 2}, {1, 3, 3}, {1, 5, 1}, {1, 6, 2}, {1, 9, 1}};
+    constexpr int t[NMOM][3] = {{0, 1, 0}, {0, 2, 0}, {0, 4, 0}, {0, 8, 0}, {1, 1, 1}, {1, 2, 2}, {1, 3, 3}, {1, 5, 1}, {1, 6, 2}};
     return t[j][k];
   }
   // propagators: {momentum entry, 0 gluon / 1 top / 2 photon / 3 Z}
   static __host__ __device__ constexpr int prop(int j, int k) {
-    constexpr int t[NPROP][2] = {{6, 0}, {7, 1}, {8, 1}, {9, 1}};
+    constexpr int t[NPROP][2] = {{6, 0}, {7, 1}, {8, 1}};
     return t[j][k];
   }
   static __device__ __forceinline__ const uint32_t* colour_bf16_image() { return kColourB2; }
@@ -158,13 +167,6 @@ struct Proc2 {
     pb[9] += kb[1];
     pb[10] += kb[2];
     pb[11] += kb[3];
-    }
-    { R kb[4] = {R(0), R(0), R(0), R(0)};
-      prop_adj<R>(prop[3], true, K + 36, propb[3], kb);
-    pb[12] += kb[0];
-    pb[13] += kb[1];
-    pb[14] += kb[2];
-    pb[15] += kb[3];
     }
     { R kb[4] = {R(0), R(0), R(0), R(0)};
       external_adj<R>(0, K + 12, cp.mt, hel[3], -1, w9b, kb);

@@ -5,9 +5,8 @@
 #pragma once
 namespace mg {
 // helicity-shared program: 20 currents in 3 levels, 94 variant slots, 18 amplitudes, 71580 flops per event (all helicities)
-static __device__ const HsItem kHsItems3[94] = {{1, 2, -1, 1, 1, 0, {0, 0, 0, 0, 0, 0}, 2, 0, 0}, {1, 2, 1, 1, 1, 1, {0, 0, 0, 0, 0, 0}, 2, 0, 0}, {0, 3, -1, -1, 1, 2, {0, 0, 0, 0, 0, 0}, 3, 0, 0}, {0, 3, 1, -1, 1, 3, {0, 0, 0, 0, 0, 0}, 3, 0, 0}, {2, 0, -1, 1, 0, 4, {0, 0, 0, 0, 0, 0}, 0, 0, 0}, {2, 0, 1, 1, 0, 5, {0, 0, 0, 0, 0, 0}, 0, 0, 0}, {2, 1, -1, 1, 0, 6, {0, 0, 0, 0, 0, 0}, 1, 0, 0}, {2, 1, 1, 1, 0, 7, {0, 0, 0, 0, 0, 0}, 1, 0, 0}, {2, 4, -1, -1, 0, 8, {0, 0, 0, 0, 0, 0}, 4, 0, 0}, {2, 4, 1, -1, 0, 9, {0, 0, 0, 0, 0, 0}, 4, 0, 0}, {7, 0, 0, 0, 0, 10, {6, 8, 0, 0, 0, 0}, 6, 7, 1}, {7, 0, 0, 0, 0, 11, {7, 8, 0, 0, 0, 0}, 6, 7, 1}, {7, 0, 0, 0, 0, 12, {6, 9, 0, 0, 0, 0}, 6, 7, 1}, {7, 0, 0, 0, 0, 13, {7, 9, 0, 0, 0, 0}, 6, 7, 1}, {7, 0, 0, 0, 0, 14, {4, 6, 0, 0, 0, 0}, 9, 6, 6}, {7, 0, 0, 0, 0, 15, {5, 6, 0, 0, 0, 0}, 9, 6, 6}, {7, 0, 0, 0, 0, 16, {4, 7, 0, 0, 0, 0}, 9, 6, 6}, {7, 0, 0, 0, 0, 17, {5, 7, 0, 0, 0, 0}, 9, 6, 6}, {7, 0, 0, 0, 0, 18, {4, 8, 0, 0, 0, 0}, 9, 7, 8}, {7, 0, 0, 0, 0, 19, {5, 8, 0, 0, 0, 0}, 9, 7, 8}, {7, 0, 0, 0, 0, 20, {4, 9, 0, 0, 0, 0}, 9, 7, 8}, {7, 0, 0, 0, 0, 21, {5, 9, 0, 0, 0, 0}, 9, 7, 8}, {8, 0, 0, 0, 0, 22, {6, 4, 8, 4, 6, 8}, 0, 0, 10}, {8, 0, 0, 0, 0, 23, {6, 5, 8, 5, 6, 8}, 0, 0, 10}, {8, 0, 0, 0, 0, 24, {7, 4, 8, 4, 7, 8}, 0, 0, 10}, {8, 0, 0, 0, 0, 25, {7, 5, 8, 5, 7, 8}, 0, 0, 10}, {8, 0, 0, 0, 0, 26, {6, 4, 9, 4, 6, 9}, 0, 0, 10}, {8, 0, 0, 0, 0, 27, {6, 5, 9, 5, 6, 9}, 0, 0, 10}, {8, 0, 0, 0, 0, 28, {7, 4, 9, 4, 7, 9}, 0, 0, 10}, {8, 0, 0, 0, 0, 29, {7, 5, 9, 5, 7, 9}, 0, 0, 10}, {8, 0, 0, 0, 0, 30, {8, 4, 6, 4, 6, 8}, 0, 0, 10}, {8, 0, 0, 0, 0, 31, {8, 5, 6, 5, 6, 8}, 0, 0, 10}, {8, 0, 0, 0, 0, 32, {8, 4, 7, 4, 7, 8}, 0, 0, 10}, {8, 0, 0, 0, 0, 33, {8, 5, 7, 5, 7, 8}, 0, 0, 10}, {8, 0, 0, 0, 0, 34, {9, 4, 6, 4, 6, 9}, 0, 0, 10}, {8, 0, 0, 0, 0, 35, {9, 5, 6, 5, 6, 9}, 0, 0, 10}, {8, 0, 0, 0, 0, 36, {9, 4, 7, 4, 7, 9}, 0, 0, 10}, {8, 0, 0, 0, 0, 37, {9, 5, 7, 5, 7, 9}, 0, 0, 10}, {8, 0, 0, 0, 0, 38, {8, 4, 6, 6, 4, 8}, 0, 0, 10}, {8, 0, 0, 0, 0, 39, {8, 5, 6, 6, 5, 8}, 0, 0, 10}, {8, 0, 0, 0, 0, 40, {8, 4, 7, 7, 4, 8}, 0, 0, 10}, {8, 0, 0, 0, 0, 41, {8, 5, 7, 7, 5, 8}, 0, 0, 10}, {8, 0, 0, 0, 0, 42, {9, 4, 6, 6, 4, 9}, 0, 0, 10}, {8, 0, 0, 0, 0, 43, {9, 5, 6, 6, 5, 9}, 0, 0, 10}, {8, 0, 0, 0, 0, 44, {9, 4, 7, 7, 4, 9}, 0, 0, 10}, {8, 0, 0, 0, 0, 45, {9, 5, 7, 7, 5, 9}, 0, 0, 10}, {3, 0, 0, 0, 0, 46, {0, 4, 0, 0, 0, 0}, 10, 0, 2}, {3, 0, 0, 0, 0, 47, {0, 5, 0, 0, 0, 0}, 10, 0, 2}, {3, 0, 0, 0, 0, 48, {1, 4, 0, 0, 0, 0}, 10, 0, 2}, {3, 0, 0, 0, 0, 49, {1, 5, 0, 0, 0, 0}, 10, 0, 2}, {3, 0, 0, 0, 0, 50, {0, 6, 0, 0, 0, 0}, 17, 0, 9}, {3, 0, 0, 0, 0, 51, {0, 7, 0, 0, 0, 0}, 17, 0, 9}, {3, 0, 0, 0, 0, 52, {1, 6, 0, 0, 0, 0}, 17, 0, 9}, {3, 0, 0, 0, 0, 53, {1, 7, 0, 0, 0, 0}, 17, 0, 9}, {3, 0, 0, 0, 0, 54, {0, 8, 0, 0, 0, 0}, 15, 0, 7}, {3, 0, 0, 0, 0, 55, {1, 8, 0, 0, 0, 0}, 15, 0, 7}, {3, 0, 0, 0, 0, 56, {0, 9, 0, 0, 0, 0}, 15, 0, 7}, {3, 0, 0, 0, 0, 57, {1, 9, 0, 0, 0, 0}, 15, 0, 7}, {4, 0, 0, 0, 0, 58, {2, 8, 0, 0, 0, 0}, 19, 0, 11}, {4, 0, 0, 0, 0, 59, {3, 8, 0, 0, 0, 0}, 19, 0, 11}, {4, 0, 0, 0, 0, 60, {2, 9, 0, 0, 0, 0}, 19, 0, 11}, {4, 0, 0, 0, 0, 61, {3, 9, 0, 0, 0, 0}, 19, 0, 11}, {4, 0, 0, 0, 0, 62, {2, 6, 0, 0, 0, 0}, 20, 0, 12}, {4, 0, 0, 0, 0, 63, {2, 7, 0, 0, 0, 0}, 20, 0, 12}, {4, 0, 0, 0, 0, 64, {3, 6, 0, 0, 0, 0}, 20, 0, 12}, {4, 0, 0, 0, 0, 65, {3, 7, 0, 0, 0, 0}, 20, 0, 12}, {4, 0, 0, 0, 0, 66, {2, 4, 0, 0, 0, 0}, 21, 0, 13}, {4, 0, 0, 0, 0, 67, {2, 5, 0, 0, 0, 0}, 21, 0, 13}, {4, 0, 0, 0, 0, 68, {3, 4, 0, 0, 0, 0}, 21, 0, 13}, {4, 0, 0, 0, 0, 69, {3, 5, 0, 0, 0, 0}, 21, 0, 13}, {7, 0, 0, 0, 0, 70, {4, 10, 0, 0, 0, 0}, 9, 8, 10}, {7, 0, 0, 0, 0, 71, {5, 10, 0, 0, 0, 0}, 9, 8, 10}, {7, 0, 0, 0, 0, 72, {4, 11, 0, 0, 0, 0}, 9, 8, 10}, {7, 0, 0, 0, 0, 73, {5, 11, 0, 0, 0, 0}, 9, 8, 10}, {7, 0, 0, 0, 0, 74, {4, 12, 0, 0, 0, 0}, 9, 8, 10}, {7, 0, 0, 0, 0, 75, {5, 12, 0, 0, 0, 0}, 9, 8, 10}, {7, 0, 0, 0, 0, 76, {4, 13, 0, 0, 0, 0}, 9, 8, 10}, {7, 0, 0, 0, 0, 77, {5, 13, 0, 0, 0, 0}, 9, 8, 10}, {7, 0, 0, 0, 0, 78, {14, 8, 0, 0, 0, 0}, 14, 7, 10}, {7, 0, 0, 0, 0, 79, {15, 8, 0, 0, 0, 0}, 14, 7, 10}, {7, 0, 0, 0, 0, 80, {16, 8, 0, 0, 0, 0}, 14, 7, 10}, {7, 0, 0, 0, 0, 81, {17, 8, 0, 0, 0, 0}, 14, 7, 10}, {7, 0, 0, 0, 0, 82, {14, 9, 0, 0, 0, 0}, 14, 7, 10}, {7, 0, 0, 0, 0, 83, {15, 9, 0, 0, 0, 0}, 14, 7, 10}, {7, 0, 0, 0, 0, 84, {16, 9, 0, 0, 0, 0}, 14, 7, 10}, {7, 0, 0, 0, 0, 85, {17, 9, 0, 0, 0, 0}, 14, 7, 10}, {7, 0, 0, 0, 0, 86, {18, 6, 0, 0, 0, 0}, 16, 6, 10}, {7, 0, 0, 0, 0, 87, {19, 6, 0, 0, 0, 0}, 16, 6, 10}, {7, 0, 0, 0, 0, 88, {18, 7, 0, 0, 0, 0}, 16, 6, 10}, {7, 0, 0, 0, 0, 89, {19, 7, 0, 0, 0, 0}, 16, 6, 10}, {7, 0, 0, 0, 0, 90, {20, 6, 0, 0, 0, 0}, 16, 6, 10}, {7, 0, 0, 0, 0, 91, {21, 6, 0, 0, 0, 0}, 16, 6, 10}, {7, 0, 0, 0, 0, 92, {20, 7, 0, 0, 0, 0}, 16, 6, 10}, {7, 0, 0, 0, 0, 93, {21, 7, 0, 0, 0, 0}, 16, 6, 10}};
-static __constant__ HsAmp kHsAmps3[18] = {{0, 4, 0, {0, 1, 8, 0}, {0, 0, 0}}, {0, 4, 4, {0, 1, 9, 0}, {0, 0, 0}}, {0, 4, 8, {0, 1, 10, 0}, {0, 0, 0}}, {0, 4, 12, {0, 1, 17, 0}, {0, 0, 0}}, {0, 4, 16, {0, 1, 18, 0}, {0, 0, 0}}, {0, 4, 20, {0, 1, 19, 0}, {0, 0, 0}}, {0, 2, 24, {0, 14, 6, 0}, {0, 0, 0}}, {0, 2, 26, {0, 15, 7, 0}, {0, 0, 0}}, {0, 2, 28, {0, 16, 5, 0}, {0, 0, 0}}, {0, 2, 30, {11, 1, 5, 0}, {0, 0, 0}}, {0, 1, 32, {11, 14, 3, 0}, {0, 0, 0}}, {0, 1, 33, {11, 15, 4, 0}, {0, 0, 0}}, {0, 2, 34, {12, 1, 7, 0}, {0, 0, 0}}, {0, 1, 36, {12, 14, 2, 0}, {0, 0, 0}}, {0, 1, 37, {12, 16, 4, 0}, {0, 0, 0}}, {0, 2, 38, {13, 1, 6, 0}, {0, 0, 0}}, {0, 1, 40, {13, 15, 2, 0}, {0, 0, 0}}, {0, 1, 41, {13, 16, 3, 0}, {0, 0, 0}}};
-static __constant__ uint8_t kHsFlows3[42] = {64, 2, 4, 69, 65, 2, 67, 4, 0, 65, 67, 5, 64, 1, 3, 69, 64, 2, 4, 69, 65, 2, 67, 4, 192, 130, 193, 132, 195, 133, 192, 129, 0, 1, 194, 131, 2, 3, 196, 133, 4, 5};
+static __device__ const HsItem kHsItems3[94] = {{1, 2, -1, 1, 1, 0, {0, 0, 0, 0, 0, 0}, 2, 0, 0}, {1, 2, 1, 1, 1, 1, {0, 0, 0, 0, 0, 0}, 2, 0, 0}, {0, 3, -1, -1, 1, 2, {0, 0, 0, 0, 0, 0}, 3, 0, 0}, {0, 3, 1, -1, 1, 3, {0, 0, 0, 0, 0, 0}, 3, 0, 0}, {2, 0, -1, 1, 0, 4, {0, 0, 0, 0, 0, 0}, 0, 0, 0}, {2, 0, 1, 1, 0, 5, {0, 0, 0, 0, 0, 0}, 0, 0, 0}, {2, 1, -1, 1, 0, 6, {0, 0, 0, 0, 0, 0}, 1, 0, 0}, {2, 1, 1, 1, 0, 7, {0, 0, 0, 0, 0, 0}, 1, 0, 0}, {2, 4, -1, -1, 0, 8, {0, 0, 0, 0, 0, 0}, 4, 0, 0}, {2, 4, 1, -1, 0, 9, {0, 0, 0, 0, 0, 0}, 4, 0, 0}, {7, 0, 0, 0, 0, 10, {6, 8, 0, 0, 0, 0}, 6, 7, 1}, {7, 0, 0, 0, 0, 11, {7, 8, 0, 0, 0, 0}, 6, 7, 1}, {7, 0, 0, 0, 0, 12, {6, 9, 0, 0, 0, 0}, 6, 7, 1}, {7, 0, 0, 0, 0, 13, {7, 9, 0, 0, 0, 0}, 6, 7, 1}, {7, 0, 0, 0, 0, 14, {4, 6, 0, 0, 0, 0}, 9, 6, 6}, {7, 0, 0, 0, 0, 15, {5, 6, 0, 0, 0, 0}, 9, 6, 6}, {7, 0, 0, 0, 0, 16, {4, 7, 0, 0, 0, 0}, 9, 6, 6}, {7, 0, 0, 0, 0, 17, {5, 7, 0, 0, 0, 0}, 9, 6, 6}, {7, 0, 0, 0, 0, 18, {4, 8, 0, 0, 0, 0}, 9, 7, 8}, {7, 0, 0, 0, 0, 19, {5, 8, 0, 0, 0, 0}, 9, 7, 8}, {7, 0, 0, 0, 0, 20, {4, 9, 0, 0, 0, 0}, 9, 7, 8}, {7, 0, 0, 0, 0, 21, {5, 9, 0, 0, 0, 0}, 9, 7, 8}, {8, 0, 0, 0, 0, 22, {6, 4, 8, 4, 6, 8}, 0, 0, 0}, {8, 0, 0, 0, 0, 23, {6, 5, 8, 5, 6, 8}, 0, 0, 0}, {8, 0, 0, 0, 0, 24, {7, 4, 8, 4, 7, 8}, 0, 0, 0}, {8, 0, 0, 0, 0, 25, {7, 5, 8, 5, 7, 8}, 0, 0, 0}, {8, 0, 0, 0, 0, 26, {6, 4, 9, 4, 6, 9}, 0, 0, 0}, {8, 0, 0, 0, 0, 27, {6, 5, 9, 5, 6, 9}, 0, 0, 0}, {8, 0, 0, 0, 0, 28, {7, 4, 9, 4, 7, 9}, 0, 0, 0}, {8, 0, 0, 0, 0, 29, {7, 5, 9, 5, 7, 9}, 0, 0, 0}, {8, 0, 0, 0, 0, 30, {8, 4, 6, 4, 6, 8}, 0, 0, 0}, {8, 0, 0, 0, 0, 31, {8, 5, 6, 5, 6, 8}, 0, 0, 0}, {8, 0, 0, 0, 0, 32, {8, 4, 7, 4, 7, 8}, 0, 0, 0}, {8, 0, 0, 0, 0, 33, {8, 5, 7, 5, 7, 8}, 0, 0, 0}, {8, 0, 0, 0, 0, 34, {9, 4, 6, 4, 6, 9}, 0, 0, 0}, {8, 0, 0, 0, 0, 35, {9, 5, 6, 5, 6, 9}, 0, 0, 0}, {8, 0, 0, 0, 0, 36, {9, 4, 7, 4, 7, 9}, 0, 0, 0}, {8, 0, 0, 0, 0, 37, {9, 5, 7, 5, 7, 9}, 0, 0, 0}, {8, 0, 0, 0, 0, 38, {8, 4, 6, 6, 4, 8}, 0, 0, 0}, {8, 0, 0, 0, 0, 39, {8, 5, 6, 6, 5, 8}, 0, 0, 0}, {8, 0, 0, 0, 0, 40, {8, 4, 7, 7, 4, 8}, 0, 0, 0}, {8, 0, 0, 0, 0, 41, {8, 5, 7, 7, 5, 8}, 0, 0, 0}, {8, 0, 0, 0, 0, 42, {9, 4, 6, 6, 4, 9}, 0, 0, 0}, {8, 0, 0, 0, 0, 43, {9, 5, 6, 6, 5, 9}, 0, 0, 0}, {8, 0, 0, 0, 0, 44, {9, 4, 7, 7, 4, 9}, 0, 0, 0}, {8, 0, 0, 0, 0, 45, {9, 5, 7, 7, 5, 9}, 0, 0, 0}, {3, 0, 0, 0, 0, 46, {0, 4, 0, 0, 0, 0}, 10, 0, 2}, {3, 0, 0, 0, 0, 47, {0, 5, 0, 0, 0, 0}, 10, 0, 2}, {3, 0, 0, 0, 0, 48, {1, 4, 0, 0, 0, 0}, 10, 0, 2}, {3, 0, 0, 0, 0, 49, {1, 5, 0, 0, 0, 0}, 10, 0, 2}, {3, 0, 0, 0, 0, 50, {0, 6, 0, 0, 0, 0}, 17, 0, 9}, {3, 0, 0, 0, 0, 51, {0, 7, 0, 0, 0, 0}, 17, 0, 9}, {3, 0, 0, 0, 0, 52, {1, 6, 0, 0, 0, 0}, 17, 0, 9}, {3, 0, 0, 0, 0, 53, {1, 7, 0, 0, 0, 0}, 17, 0, 9}, {3, 0, 0, 0, 0, 54, {0, 8, 0, 0, 0, 0}, 15, 0, 7}, {3, 0, 0, 0, 0, 55, {1, 8, 0, 0, 0, 0}, 15, 0, 7}, {3, 0, 0, 0, 0, 56, {0, 9, 0, 0, 0, 0}, 15, 0, 7}, {3, 0, 0, 0, 0, 57, {1, 9, 0, 0, 0, 0}, 15, 0, 7}, {4, 0, 0, 0, 0, 58, {2, 8, 0, 0, 0, 0}, 18, 0, 4}, {4, 0, 0, 0, 0, 59, {3, 8, 0, 0, 0, 0}, 18, 0, 4}, {4, 0, 0, 0, 0, 60, {2, 9, 0, 0, 0, 0}, 18, 0, 4}, {4, 0, 0, 0, 0, 61, {3, 9, 0, 0, 0, 0}, 18, 0, 4}, {4, 0, 0, 0, 0, 62, {2, 6, 0, 0, 0, 0}, 19, 0, 5}, {4, 0, 0, 0, 0, 63, {2, 7, 0, 0, 0, 0}, 19, 0, 5}, {4, 0, 0, 0, 0, 64, {3, 6, 0, 0, 0, 0}, 19, 0, 5}, {4, 0, 0, 0, 0, 65, {3, 7, 0, 0, 0, 0}, 19, 0, 5}, {4, 0, 0, 0, 0, 66, {2, 4, 0, 0, 0, 0}, 20, 0, 3}, {4, 0, 0, 0, 0, 67, {2, 5, 0, 0, 0, 0}, 20, 0, 3}, {4, 0, 0, 0, 0, 68, {3, 4, 0, 0, 0, 0}, 20, 0, 3}, {4, 0, 0, 0, 0, 69, {3, 5, 0, 0, 0, 0}, 20, 0, 3}, {7, 0, 0, 0, 0, 70, {4, 10, 0, 0, 0, 0}, 9, 8, 0}, {7, 0, 0, 0, 0, 71, {5, 10, 0, 0, 0, 0}, 9, 8, 0}, {7, 0, 0, 0, 0, 72, {4, 11, 0, 0, 0, 0}, 9, 8, 0}, {7, 0, 0, 0, 0, 73, {5, 11, 0, 0, 0, 0}, 9, 8, 0}, {7, 0, 0, 0, 0, 74, {4, 12, 0, 0, 0, 0}, 9, 8, 0}, {7, 0, 0, 0, 0, 75, {5, 12, 0, 0, 0, 0}, 9, 8, 0}, {7, 0, 0, 0, 0, 76, {4, 13, 0, 0, 0, 0}, 9, 8, 0}, {7, 0, 0, 0, 0, 77, {5, 13, 0, 0, 0, 0}, 9, 8, 0}, {7, 0, 0, 0, 0, 78, {14, 8, 0, 0, 0, 0}, 14, 7, 0}, {7, 0, 0, 0, 0, 79, {15, 8, 0, 0, 0, 0}, 14, 7, 0}, {7, 0, 0, 0, 0, 80, {16, 8, 0, 0, 0, 0}, 14, 7, 0}, {7, 0, 0, 0, 0, 81, {17, 8, 0, 0, 0, 0}, 14, 7, 0}, {7, 0, 0, 0, 0, 82, {14, 9, 0, 0, 0, 0}, 14, 7, 0}, {7, 0, 0, 0, 0, 83, {15, 9, 0, 0, 0, 0}, 14, 7, 0}, {7, 0, 0, 0, 0, 84, {16, 9, 0, 0, 0, 0}, 14, 7, 0}, {7, 0, 0, 0, 0, 85, {17, 9, 0, 0, 0, 0}, 14, 7, 0}, {7, 0, 0, 0, 0, 86, {18, 6, 0, 0, 0, 0}, 16, 6, 0}, {7, 0, 0, 0, 0, 87, {19, 6, 0, 0, 0, 0}, 16, 6, 0}, {7, 0, 0, 0, 0, 88, {18, 7, 0, 0, 0, 0}, 16, 6, 0}, {7, 0, 0, 0, 0, 89, {19, 7, 0, 0, 0, 0}, 16, 6, 0}, {7, 0, 0, 0, 0, 90, {20, 6, 0, 0, 0, 0}, 16, 6, 0}, {7, 0, 0, 0, 0, 91, {21, 6, 0, 0, 0, 0}, 16, 6, 0}, {7, 0, 0, 0, 0, 92, {20, 7, 0, 0, 0, 0}, 16, 6, 0}, {7, 0, 0, 0, 0, 93, {21, 7, 0, 0, 0, 0}, 16, 6, 0}};
+static __constant__ HsAmp kHsAmps3[18] = {{0, 0, {0, 1, 8, 0}, {0, 0, 0}}, {0, 1, {0, 1, 9, 0}, {0, 0, 0}}, {0, 2, {0, 1, 10, 0}, {0, 0, 0}}, {0, 3, {0, 1, 17, 0}, {0, 0, 0}}, {0, 0, {0, 1, 18, 0}, {0, 0, 0}}, {0, 1, {0, 1, 19, 0}, {0, 0, 0}}, {0, 4, {0, 14, 6, 0}, {0, 0, 0}}, {0, 5, {0, 15, 7, 0}, {0, 0, 0}}, {0, 6, {0, 16, 5, 0}, {0, 0, 0}}, {0, 7, {11, 1, 5, 0}, {0, 0, 0}}, {0, 8, {11, 14, 3, 0}, {0, 0, 0}}, {0, 9, {11, 15, 4, 0}, {0, 0, 0}}, {0, 10, {12, 1, 7, 0}, {0, 0, 0}}, {0, 11, {12, 14, 2, 0}, {0, 0, 0}}, {0, 12, {12, 16, 4, 0}, {0, 0, 0}}, {0, 13, {13, 1, 6, 0}, {0, 0, 0}}, {0, 14, {13, 15, 2, 0}, {0, 0, 0}}, {0, 15, {13, 16, 3, 0}, {0, 0, 0}}};
 static __device__ const uint16_t kHsSlot3[20][32] = {{0, 0, 0, 0, 1, 1, 1, 1, 0, 0, 0, 0, 1, 1, 1, 1, 0, 0, 0, 0, 1, 1, 1, 1, 0, 0, 0, 0, 1, 1, 1, 1}, {2, 2, 3, 3, 2, 2, 3, 3, 2, 2, 3, 3, 2, 2, 3, 3, 2, 2, 3, 3, 2, 2, 3, 3, 2, 2, 3, 3, 2, 2, 3, 3}, {4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5}, {6, 6, 6, 6, 6, 6, 6, 6, 7, 7, 7, 7, 7, 7, 7, 7, 6, 6, 6, 6, 6, 6, 6, 6, 7, 7, 7, 7, 7, 7, 7, 7}, {8, 9, 8, 9, 8, 9, 8, 9, 8, 9, 8, 9, 8, 9, 8, 9, 8, 9, 8, 9, 8, 9, 8, 9, 8, 9, 8, 9, 8, 9, 8, 9}, {10, 12, 10, 12, 10, 12, 10, 12, 11, 13, 11, 13, 11, 13, 11, 13, 10, 12, 10, 12, 10, 12, 10, 12, 11, 13, 11, 13, 11, 13, 11, 13}, {14, 14, 14, 14, 14, 14, 14, 14, 16, 16, 16, 16, 16, 16, 16, 16, 15, 15, 15, 15, 15, 15, 15, 15, 17, 17, 17, 17, 17, 17, 17, 17}, {18, 20, 18, 20, 18, 20, 18, 20, 18, 20, 18, 20, 18, 20, 18, 20, 19, 21, 19, 21, 19, 21, 19, 21, 19, 21, 19, 21, 19, 21, 19, 21}, {22, 26, 22, 26, 22, 26, 22, 26, 24, 28, 24, 28, 24, 28, 24, 28, 23, 27, 23, 27, 23, 27, 23, 27, 25, 29, 25, 29, 25, 29, 25, 29}, {30, 34, 30, 34, 30, 34, 30, 34, 32, 36, 32, 36, 32, 36, 32, 36, 31, 35, 31, 35, 31, 35, 31, 35, 33, 37, 33, 37, 33, 37, 33, 37}, {38, 42, 38, 42, 38, 42, 38, 42, 40, 44, 40, 44, 40, 44, 40, 44, 39, 43, 39, 43, 39, 43, 39, 43, 41, 45, 41, 45, 41, 45, 41, 45}, {46, 46, 46, 46, 48, 48, 48, 48, 46, 46, 46, 46, 48, 48, 48, 48, 47, 47, 47, 47, 49, 49, 49, 49, 47, 47, 47, 47, 49, 49, 49, 49}, {50, 50, 50, 50, 52, 52, 52, 52, 51, 51, 51, 51, 53, 53, 53, 53, 50, 50, 50, 50, 52, 52, 52, 52, 51, 51, 51, 51, 53, 53, 53, 53}, {54, 56, 54, 56, 55, 57, 55, 57, 54, 56, 54, 56, 55, 57, 55, 57, 54, 56, 54, 56, 55, 57, 55, 57, 54, 56, 54, 56, 55, 57, 55, 57}, {58, 60, 59, 61, 58, 60, 59, 61, 58, 60, 59, 61, 58, 60, 59, 61, 58, 60, 59, 61, 58, 60, 59, 61, 58, 60, 59, 61, 58, 60, 59, 61}, {62, 62, 64, 64, 62, 62, 64, 64, 63, 63, 65, 65, 63, 63, 65, 65, 62, 62, 64, 64, 62, 62, 64, 64, 63, 63, 65, 65, 63, 63, 65, 65}, {66, 66, 68, 68, 66, 66, 68, 68, 66, 66, 68, 68, 66, 66, 68, 68, 67, 67, 69, 69, 67, 67, 69, 69, 67, 67, 69, 69, 67, 67, 69, 69}, {70, 74, 70, 74, 70, 74, 70, 74, 72, 76, 72, 76, 72, 76, 72, 76, 71, 75, 71, 75, 71, 75, 71, 75, 73, 77, 73, 77, 73, 77, 73, 77}, {78, 82, 78, 82, 78, 82, 78, 82, 80, 84, 80, 84, 80, 84, 80, 84, 79, 83, 79, 83, 79, 83, 79, 83, 81, 85, 81, 85, 81, 85, 81, 85}, {86, 90, 86, 90, 86, 90, 86, 90, 88, 92, 88, 92, 88, 92, 88, 92, 87, 91, 87, 91, 87, 91, 87, 91, 89, 93, 89, 93, 89, 93, 89, 93}};
 // colour-matrix numerators as the BF16 B operand of the tensor-core colour sum
 static __device__ __align__(16) const uint32_t kColourB3[128] = {0xc1004280, 0x3f80c100, 0x41203f80, 0x00000000, 0x4280c100, 0x41203f80, 0x3f80c100, 0x00000000, 0x3f80c100, 0xc1004280, 0x3f804120, 0x00000000, 0x41203f80, 0x4280c100, 0xc1003f80, 0x00000000, 0xc1003f80, 0x3f804120, 0xc1004280, 0x00000000, 0x3f804120, 0xc1003f80, 0x4280c100, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000};
@@ -32,10 +31,33 @@ struct Proc3 {
   }
   static __device__ __forceinline__ const HsItem* hs_items() { return kHsItems3; }
   static __device__ __forceinline__ const HsAmp* hs_amps() { return kHsAmps3; }
-  static __device__ __forceinline__ const uint8_t* hs_flows() { return kHsFlows3; }
   static __device__ __forceinline__ const uint16_t* hs_slots() { return &kHsSlot3[0][0]; }
-  static constexpr int NMOM = 22;
-  static constexpr int NPROP = 14;
+  static constexpr int HS_NPAT = 16;
+  // colour-flow updates of each amplitude pattern: J_s += amp, -amp, i amp, -i amp
+  template <class R>
+  static __device__ __forceinline__ void hs_flows(int pat, cx<R> amp, cx<R>* J) {
+    switch (pat) {
+      case 0: J[0] -= amp; J[2] += amp; J[4] += amp; J[5] -= amp; break;
+      case 1: J[1] -= amp; J[2] += amp; J[3] -= amp; J[4] += amp; break;
+      case 2: J[0] += amp; J[1] -= amp; J[3] -= amp; J[5] += amp; break;
+      case 3: J[0] -= amp; J[1] += amp; J[3] += amp; J[5] -= amp; break;
+      case 4: J[0] -= mul_i(amp); J[2] += mul_i(amp); break;
+      case 5: J[1] -= mul_i(amp); J[4] += mul_i(amp); break;
+      case 6: J[3] -= mul_i(amp); J[5] += mul_i(amp); break;
+      case 7: J[0] -= mul_i(amp); J[1] += mul_i(amp); break;
+      case 8: J[0] += amp; break;
+      case 9: J[1] += amp; break;
+      case 10: J[2] -= mul_i(amp); J[3] += mul_i(amp); break;
+      case 11: J[2] += amp; break;
+      case 12: J[3] += amp; break;
+      case 13: J[4] -= mul_i(amp); J[5] += mul_i(amp); break;
+      case 14: J[4] += amp; break;
+      case 15: J[5] += amp; break;
+      default: break;
+    }
+  }
+  static constexpr int NMOM = 21;
+  static constexpr int NPROP = 10;
   static constexpr int NFINAL = 3;
   // floating-point operations per helicity: diagram program, CUDA-core colour sum
   static constexpr long FLOPS_AMP = 5220;
@@ -43,12 +65,12 @@ struct Proc3 {
   static constexpr double NORM = 1.0 / 256.0;  // 1/(helicity avg x colour avg x symmetry)
   // momentum table: {0 physical / 1 all-outgoing sum, leg mask, mask of legs entering as -p}
   static __host__ __device__ constexpr int mom(int j, int k) {
-    constexpr int t[NMOM][3] = {{0, 1, 0}, {0, 2, 0}, {0, 4, 0}, {0, 8, 0}, {0, 16, 0}, {1, 19, 3}, {1, 2, 2}, {1, 16, 0}, {1, 18, 2}, {1, 1, 1}, {1, 5, 1}, {1, 22, 2}, {1, 7, 3}, {1, 21, 1}, {1, 3, 3}, {1, 20, 0}, {1, 17, 1}, {1, 6, 2}, {1, 12, 0}, {1, 24, 0}, {1, 10, 2}, {1, 9, 1}};
+    constexpr int t[NMOM][3] = {{0, 1, 0}, {0, 2, 0}, {0, 4, 0}, {0, 8, 0}, {0, 16, 0}, {1, 19, 3}, {1, 2, 2}, {1, 16, 0}, {1, 18, 2}, {1, 1, 1}, {1, 5, 1}, {1, 22, 2}, {1, 7, 3}, {1, 21, 1}, {1, 3, 3}, {1, 20, 0}, {1, 17, 1}, {1, 6, 2}, {1, 7, 4}, {1, 21, 20}, {1, 22, 20}};
     return t[j][k];
   }
   // propagators: {momentum entry, 0 gluon / 1 top / 2 photon / 3 Z}
   static __host__ __device__ constexpr int prop(int j, int k) {
-    constexpr int t[NPROP][2] = {{5, 0}, {8, 0}, {10, 1}, {11, 1}, {12, 1}, {13, 1}, {14, 0}, {15, 1}, {16, 0}, {17, 1}, {18, 0}, {19, 1}, {20, 1}, {21, 1}};
+    constexpr int t[NPROP][2] = {{5, 0}, {8, 0}, {10, 1}, {11, 1}, {12, 1}, {13, 1}, {14, 0}, {15, 1}, {16, 0}, {17, 1}};
     return t[j][k];
   }
   static __device__ __forceinline__ const uint32_t* colour_bf16_image() { return kColourB3; }
@@ -556,42 +578,6 @@ struct Proc3 {
     pb[9] += kb[1];
     pb[10] += kb[2];
     pb[11] += kb[3];
-    }
-    { R kb[4] = {R(0), R(0), R(0), R(0)};
-      prop_adj<R>(prop[10], false, K + 72, propb[10], kb);
-    pb[8] += kb[0];
-    pb[9] += kb[1];
-    pb[10] += kb[2];
-    pb[11] += kb[3];
-    pb[12] += kb[0];
-    pb[13] += kb[1];
-    pb[14] += kb[2];
-    pb[15] += kb[3];
-    }
-    { R kb[4] = {R(0), R(0), R(0), R(0)};
-      prop_adj<R>(prop[11], true, K + 76, propb[11], kb);
-    pb[12] += kb[0];
-    pb[13] += kb[1];
-    pb[14] += kb[2];
-    pb[15] += kb[3];
-    pb[16] += kb[0];
-    pb[17] += kb[1];
-    pb[18] += kb[2];
-    pb[19] += kb[3];
-    }
-    { R kb[4] = {R(0), R(0), R(0), R(0)};
-      prop_adj<R>(prop[12], true, K + 80, propb[12], kb);
-    pb[12] += kb[0];
-    pb[13] += kb[1];
-    pb[14] += kb[2];
-    pb[15] += kb[3];
-    }
-    { R kb[4] = {R(0), R(0), R(0), R(0)};
-      prop_adj<R>(prop[13], true, K + 84, propb[13], kb);
-    pb[12] += kb[0];
-    pb[13] += kb[1];
-    pb[14] += kb[2];
-    pb[15] += kb[3];
     }
     { R kb[4] = {R(0), R(0), R(0), R(0)};
       external_adj<R>(0, K + 12, cp.mt, hel[3], -1, w43b, kb);

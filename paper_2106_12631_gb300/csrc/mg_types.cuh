@@ -65,11 +65,11 @@ struct HsItem {
   uint8_t k0, k1, prop;
 };
 // One amplitude: type (0 FFV g_s, 1 FFV e, 2 Z, 3 three-gluon, 4-6 four-gluon
-// term 0-2), its colour flows flows[fstart .. fstart+nflow) (flow | code << 6,
-// code 0 +1, 1 -1, 2 +i, 3 -i), operand currents, momentum entries (three-gluon).
+// term 0-2), colour-flow pattern (generated hs_flows), operand currents,
+// momentum entries (three-gluon).
 struct HsAmp {
-  uint8_t type, nflow;
-  uint16_t fstart;
+  uint8_t type;
+  uint8_t pat;
   uint8_t op[4];
   uint8_t k[3];
 };

@@ -397,7 +397,16 @@ class Emitter:
         self.prop_index = {}
 
     def momentum(self, legs):
-        key = tuple(sorted(legs))
+        """Momentum-table entry of the outgoing sum over `legs`.  A leg set that
+        contains the root leg is expressed through its complement, K_S = -K_S',
+        so that every momentum and invariant is formed from the same legs as in
+        the root-form program (momenta conserve only up to rounding)."""
+        root = self.p.spec.root
+        if root in legs:
+            comp = tuple(sorted(set(range(self.p.n)) - set(legs)))
+            key = ("neg", comp)
+        else:
+            key = tuple(sorted(legs))
         if key not in self.mom_index:
             self.mom_index[key] = len(self.mom)
             self.mom.append(key)
@@ -567,6 +576,8 @@ class GradEmitter:
         spec = self.p.spec
         if key[0] == "phys":
             legs = [(key[1], 1)]
+        elif key[0] == "neg":
+            legs = [(l, 1 if spec.legs[l].incoming else -1) for l in key[1]]
         else:
             legs = [(l, -1 if spec.legs[l].incoming else 1) for l in key]
         for leg, sg in legs:
@@ -750,6 +761,12 @@ def generate(pid: int) -> str:
             mask = 1 << key[1]
             sgn_mask = 0
             kind = 0
+        elif key[0] == "neg":
+            # -(sum of outgoing momenta of the complement): incoming legs enter as +p
+            for leg in key[1]:
+                mask |= 1 << leg
+            sgn_mask = sum(1 << leg for leg in key[1] if not spec.legs[leg].incoming)
+            kind = 1
         else:
             for leg in key:
                 mask |= 1 << leg
@@ -995,8 +1012,10 @@ class SharedProgram:
     AMP_TYPES = {"ffv": 0, "ffv_a": 1, "ffz": 2, "vvv": 3, "vvvv0": 4, "vvvv1": 5, "vvvv2": 6}
 
     def _canon_prop_legs(self, legs):
-        comp = frozenset(range(self.n)) - legs
-        return min(legs, comp, key=lambda s: (len(s), sorted(s)))
+        """The invariant of an internal line, formed from the side without the
+        root leg (as in the root-form program)."""
+        root = self.p.spec.root
+        return frozenset(range(self.n)) - legs if root in legs else legs
 
     def _item(self, d, v):
         """One current variant: (type, a, b, c, flag, out, in[6], k0, k1, prop)."""
@@ -1098,12 +1117,16 @@ class SharedProgram:
                 flows.append(int(s_) | (code << 6))
             amps.append((self.AMP_TYPES[kind], ops, ks, flows))
         amps.sort(key=lambda a: (a[1], a[0]))
-        flow_tab, amp_rows = [], []
+        patterns = {}
+        amp_rows = []
         for t, ops, ks, flows in amps:
+            key = tuple(flows)
+            if key not in patterns:
+                patterns[key] = len(patterns)
             o = list(ops) + [0] * (4 - len(ops))
-            amp_rows.append("{%d, %d, %d, {%s}, {%s}}" % (t, len(flows), len(flow_tab), ", ".join(map(str, o)),
-                                                          ", ".join(map(str, ks[:3]))))
-            flow_tab.extend(flows)
+            amp_rows.append("{%d, %d, {%s}, {%s}}" % (t, patterns[key], ", ".join(map(str, o)),
+                                                     ", ".join(map(str, ks[:3]))))
+        self.patterns = patterns
         # slot of every current for every event helicity index
         slot = []
         for d in self.order:
@@ -1124,12 +1147,9 @@ class SharedProgram:
                 t, a, b, c, flag, o, ", ".join(map(str, ins)), k0, k1, pr)
                 for (t, a, b, c, flag, o, ins, k0, k1, pr) in items)))
         out.append("static __constant__ HsAmp kHsAmps%d[%d] = {%s};" % (pid, len(amp_rows), ", ".join(amp_rows)))
-        out.append("static __constant__ uint8_t kHsFlows%d[%d] = {%s};" % (pid, len(flow_tab),
-                                                                          ", ".join(map(str, flow_tab))))
         out.append("static __device__ const uint16_t kHsSlot%d[%d][%d] = {%s};" % (
             pid, len(self.order), nh, ", ".join("{" + ", ".join(map(str, r)) + "}" for r in slot)))
-        self.tables = dict(nitems=len(items), level_start=level_start, namps=len(amps), nflows=len(flow_tab),
-                           ncur=len(self.order))
+        self.tables = dict(nitems=len(items), level_start=level_start, namps=len(amps), ncur=len(self.order))
         return out
 
     def _exact_flops(self, items, amps):
@@ -1160,6 +1180,19 @@ class SharedProgram:
             "  }",
             "  static __device__ __forceinline__ const HsItem* hs_items() { return kHsItems%d; }" % pid,
             "  static __device__ __forceinline__ const HsAmp* hs_amps() { return kHsAmps%d; }" % pid,
-            "  static __device__ __forceinline__ const uint8_t* hs_flows() { return kHsFlows%d; }" % pid,
             "  static __device__ __forceinline__ const uint16_t* hs_slots() { return &kHsSlot%d[0][0]; }" % pid,
-        ]
+        ] + self._flow_switch()
+
+    def _flow_switch(self) -> list:
+        """J_s +=, -=, += i, -= i amp for the colour flows of amplitude pattern `pat`."""
+        ops = {0: "J[%d] += amp;", 1: "J[%d] -= amp;", 2: "J[%d] += mul_i(amp);", 3: "J[%d] -= mul_i(amp);"}
+        lines = ["  static constexpr int HS_NPAT = %d;" % len(self.patterns),
+                 "  // colour-flow updates of each amplitude pattern: J_s += amp, -amp, i amp, -i amp",
+                 "  template <class R>",
+                 "  static __device__ __forceinline__ void hs_flows(int pat, cx<R> amp, cx<R>* J) {",
+                 "    switch (pat) {"]
+        for key, pat in sorted(self.patterns.items(), key=lambda kv: kv[1]):
+            lines.append("      case %d: %s break;" % (pat, " ".join(ops[f >> 6] % (f & 63) for f in key)))
+        lines += ["      default: break;", "    }", "  }"]
+        return lines
+
