@@ -6,7 +6,7 @@
 namespace mg {
 // helicity-shared program: 6 currents in 2 levels, 16 variant slots, 2 amplitudes, 4504 flops per event (all helicities)
 static __device__ const HsItem kHsItems1[16] = {{1, 3, -1, 1, 0, 0, {0, 0, 0, 0, 0, 0}, 3, 0, 0}, {1, 3, 1, 1, 0, 1, {0, 0, 0, 0, 0, 0}, 3, 0, 0}, {0, 2, -1, -1, 0, 2, {0, 0, 0, 0, 0, 0}, 2, 0, 0}, {0, 2, 1, -1, 0, 3, {0, 0, 0, 0, 0, 0}, 2, 0, 0}, {1, 0, -1, -1, 0, 4, {0, 0, 0, 0, 0, 0}, 0, 0, 0}, {1, 0, 1, -1, 0, 5, {0, 0, 0, 0, 0, 0}, 0, 0, 0}, {0, 1, -1, 1, 0, 6, {0, 0, 0, 0, 0, 0}, 1, 0, 0}, {0, 1, 1, 1, 0, 7, {0, 0, 0, 0, 0, 0}, 1, 0, 0}, {5, 1, 0, 0, 0, 8, {4, 6, 0, 0, 0, 0}, 0, 0, 0}, {5, 1, 0, 0, 0, 9, {5, 6, 0, 0, 0, 0}, 0, 0, 0}, {5, 1, 0, 0, 0, 10, {4, 7, 0, 0, 0, 0}, 0, 0, 0}, {5, 1, 0, 0, 0, 11, {5, 7, 0, 0, 0, 0}, 0, 0, 0}, {6, 1, 0, 0, 0, 12, {4, 6, 0, 0, 0, 0}, 0, 0, 1}, {6, 1, 0, 0, 0, 13, {5, 6, 0, 0, 0, 0}, 0, 0, 1}, {6, 1, 0, 0, 0, 14, {4, 7, 0, 0, 0, 0}, 0, 0, 1}, {6, 1, 0, 0, 0, 15, {5, 7, 0, 0, 0, 0}, 0, 0, 1}};
-static __constant__ HsAmp kHsAmps1[2] = {{1, 0, {0, 1, 4, 0}, {0, 0, 0}}, {2, 0, {0, 1, 5, 0}, {0, 0, 0}}};
+static __constant__ HsAmp kHsAmps1[2] = {{1, 0, {0, 1, 4, 0}, {0, 0, 0}}, {2, 0, {0, 1, 5, 0}, {0, 0, 0}}};  // grouped by type
 static __device__ const uint16_t kHsSlot1[6][16] = {{0, 1, 0, 1, 0, 1, 0, 1, 0, 1, 0, 1, 0, 1, 0, 1}, {2, 2, 3, 3, 2, 2, 3, 3, 2, 2, 3, 3, 2, 2, 3, 3}, {4, 4, 4, 4, 4, 4, 4, 4, 5, 5, 5, 5, 5, 5, 5, 5}, {6, 6, 6, 6, 7, 7, 7, 7, 6, 6, 6, 6, 7, 7, 7, 7}, {8, 8, 8, 8, 10, 10, 10, 10, 9, 9, 9, 9, 11, 11, 11, 11}, {12, 12, 12, 12, 14, 14, 14, 14, 13, 13, 13, 13, 15, 15, 15, 15}};
 // colour-matrix numerators as the BF16 B operand of the tensor-core colour sum
 static __device__ __align__(16) const uint32_t kColourB1[128] = {0x00003f80, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000};
@@ -39,6 +39,31 @@ struct Proc1 {
     switch (pat) {
       case 0: J[0] += amp; break;
       default: break;
+    }
+  }
+  // amplitudes of one (event, helicity): operands cur[sl[c * NHEL]], flows into J
+  template <class R>
+  static __device__ __forceinline__ void hs_amplitudes(const W4<R>* __restrict__ cur, const uint16_t* __restrict__ sl, const R* __restrict__ K, const Couplings<R>& cp, cx<R>* J) {
+    W4<R> o0, o1, o2, o3;
+    {  // type 1: 1 amplitudes
+      int l0 = -1, l1 = -1;
+      for (int d = 0; d < 1; ++d) {
+        const HsAmp a = kHsAmps1[d];
+        if (a.op[0] != l0) { o0 = cur[sl[a.op[0] * NHEL]]; l0 = a.op[0]; }
+        if (a.op[1] != l1) { o1 = cur[sl[a.op[1] * NHEL]]; l1 = a.op[1]; }
+        o2 = cur[sl[a.op[2] * NHEL]];
+        hs_flows<R>(a.pat, FFV1_0<R>(o0, o1, o2, cp.ee), J);
+      }
+    }
+    {  // type 2: 1 amplitudes
+      int l0 = -1, l1 = -1;
+      for (int d = 1; d < 2; ++d) {
+        const HsAmp a = kHsAmps1[d];
+        if (a.op[0] != l0) { o0 = cur[sl[a.op[0] * NHEL]]; l0 = a.op[0]; }
+        if (a.op[1] != l1) { o1 = cur[sl[a.op[1] * NHEL]]; l1 = a.op[1]; }
+        o2 = cur[sl[a.op[2] * NHEL]];
+        hs_flows<R>(a.pat, FFV2_4_0<R>(o0, o1, o2, cp.gz, cp.gzl, cp.gzr), J);
+      }
     }
   }
   static constexpr int NMOM = 5;

@@ -6,7 +6,7 @@
 namespace mg {
 // helicity-shared program: 20 currents in 3 levels, 94 variant slots, 18 amplitudes, 71580 flops per event (all helicities)
 static __device__ const HsItem kHsItems3[94] = {{1, 2, -1, 1, 1, 0, {0, 0, 0, 0, 0, 0}, 2, 0, 0}, {1, 2, 1, 1, 1, 1, {0, 0, 0, 0, 0, 0}, 2, 0, 0}, {0, 3, -1, -1, 1, 2, {0, 0, 0, 0, 0, 0}, 3, 0, 0}, {0, 3, 1, -1, 1, 3, {0, 0, 0, 0, 0, 0}, 3, 0, 0}, {2, 0, -1, 1, 0, 4, {0, 0, 0, 0, 0, 0}, 0, 0, 0}, {2, 0, 1, 1, 0, 5, {0, 0, 0, 0, 0, 0}, 0, 0, 0}, {2, 1, -1, 1, 0, 6, {0, 0, 0, 0, 0, 0}, 1, 0, 0}, {2, 1, 1, 1, 0, 7, {0, 0, 0, 0, 0, 0}, 1, 0, 0}, {2, 4, -1, -1, 0, 8, {0, 0, 0, 0, 0, 0}, 4, 0, 0}, {2, 4, 1, -1, 0, 9, {0, 0, 0, 0, 0, 0}, 4, 0, 0}, {7, 0, 0, 0, 0, 10, {6, 8, 0, 0, 0, 0}, 6, 7, 1}, {7, 0, 0, 0, 0, 11, {7, 8, 0, 0, 0, 0}, 6, 7, 1}, {7, 0, 0, 0, 0, 12, {6, 9, 0, 0, 0, 0}, 6, 7, 1}, {7, 0, 0, 0, 0, 13, {7, 9, 0, 0, 0, 0}, 6, 7, 1}, {7, 0, 0, 0, 0, 14, {4, 6, 0, 0, 0, 0}, 9, 6, 6}, {7, 0, 0, 0, 0, 15, {5, 6, 0, 0, 0, 0}, 9, 6, 6}, {7, 0, 0, 0, 0, 16, {4, 7, 0, 0, 0, 0}, 9, 6, 6}, {7, 0, 0, 0, 0, 17, {5, 7, 0, 0, 0, 0}, 9, 6, 6}, {7, 0, 0, 0, 0, 18, {4, 8, 0, 0, 0, 0}, 9, 7, 8}, {7, 0, 0, 0, 0, 19, {5, 8, 0, 0, 0, 0}, 9, 7, 8}, {7, 0, 0, 0, 0, 20, {4, 9, 0, 0, 0, 0}, 9, 7, 8}, {7, 0, 0, 0, 0, 21, {5, 9, 0, 0, 0, 0}, 9, 7, 8}, {8, 0, 0, 0, 0, 22, {6, 4, 8, 4, 6, 8}, 0, 0, 0}, {8, 0, 0, 0, 0, 23, {6, 5, 8, 5, 6, 8}, 0, 0, 0}, {8, 0, 0, 0, 0, 24, {7, 4, 8, 4, 7, 8}, 0, 0, 0}, {8, 0, 0, 0, 0, 25, {7, 5, 8, 5, 7, 8}, 0, 0, 0}, {8, 0, 0, 0, 0, 26, {6, 4, 9, 4, 6, 9}, 0, 0, 0}, {8, 0, 0, 0, 0, 27, {6, 5, 9, 5, 6, 9}, 0, 0, 0}, {8, 0, 0, 0, 0, 28, {7, 4, 9, 4, 7, 9}, 0, 0, 0}, {8, 0, 0, 0, 0, 29, {7, 5, 9, 5, 7, 9}, 0, 0, 0}, {8, 0, 0, 0, 0, 30, {8, 4, 6, 4, 6, 8}, 0, 0, 0}, {8, 0, 0, 0, 0, 31, {8, 5, 6, 5, 6, 8}, 0, 0, 0}, {8, 0, 0, 0, 0, 32, {8, 4, 7, 4, 7, 8}, 0, 0, 0}, {8, 0, 0, 0, 0, 33, {8, 5, 7, 5, 7, 8}, 0, 0, 0}, {8, 0, 0, 0, 0, 34, {9, 4, 6, 4, 6, 9}, 0, 0, 0}, {8, 0, 0, 0, 0, 35, {9, 5, 6, 5, 6, 9}, 0, 0, 0}, {8, 0, 0, 0, 0, 36, {9, 4, 7, 4, 7, 9}, 0, 0, 0}, {8, 0, 0, 0, 0, 37, {9, 5, 7, 5, 7, 9}, 0, 0, 0}, {8, 0, 0, 0, 0, 38, {8, 4, 6, 6, 4, 8}, 0, 0, 0}, {8, 0, 0, 0, 0, 39, {8, 5, 6, 6, 5, 8}, 0, 0, 0}, {8, 0, 0, 0, 0, 40, {8, 4, 7, 7, 4, 8}, 0, 0, 0}, {8, 0, 0, 0, 0, 41, {8, 5, 7, 7, 5, 8}, 0, 0, 0}, {8, 0, 0, 0, 0, 42, {9, 4, 6, 6, 4, 9}, 0, 0, 0}, {8, 0, 0, 0, 0, 43, {9, 5, 6, 6, 5, 9}, 0, 0, 0}, {8, 0, 0, 0, 0, 44, {9, 4, 7, 7, 4, 9}, 0, 0, 0}, {8, 0, 0, 0, 0, 45, {9, 5, 7, 7, 5, 9}, 0, 0, 0}, {3, 0, 0, 0, 0, 46, {0, 4, 0, 0, 0, 0}, 10, 0, 2}, {3, 0, 0, 0, 0, 47, {0, 5, 0, 0, 0, 0}, 10, 0, 2}, {3, 0, 0, 0, 0, 48, {1, 4, 0, 0, 0, 0}, 10, 0, 2}, {3, 0, 0, 0, 0, 49, {1, 5, 0, 0, 0, 0}, 10, 0, 2}, {3, 0, 0, 0, 0, 50, {0, 6, 0, 0, 0, 0}, 17, 0, 9}, {3, 0, 0, 0, 0, 51, {0, 7, 0, 0, 0, 0}, 17, 0, 9}, {3, 0, 0, 0, 0, 52, {1, 6, 0, 0, 0, 0}, 17, 0, 9}, {3, 0, 0, 0, 0, 53, {1, 7, 0, 0, 0, 0}, 17, 0, 9}, {3, 0, 0, 0, 0, 54, {0, 8, 0, 0, 0, 0}, 15, 0, 7}, {3, 0, 0, 0, 0, 55, {1, 8, 0, 0, 0, 0}, 15, 0, 7}, {3, 0, 0, 0, 0, 56, {0, 9, 0, 0, 0, 0}, 15, 0, 7}, {3, 0, 0, 0, 0, 57, {1, 9, 0, 0, 0, 0}, 15, 0, 7}, {4, 0, 0, 0, 0, 58, {2, 8, 0, 0, 0, 0}, 18, 0, 4}, {4, 0, 0, 0, 0, 59, {3, 8, 0, 0, 0, 0}, 18, 0, 4}, {4, 0, 0, 0, 0, 60, {2, 9, 0, 0, 0, 0}, 18, 0, 4}, {4, 0, 0, 0, 0, 61, {3, 9, 0, 0, 0, 0}, 18, 0, 4}, {4, 0, 0, 0, 0, 62, {2, 6, 0, 0, 0, 0}, 19, 0, 5}, {4, 0, 0, 0, 0, 63, {2, 7, 0, 0, 0, 0}, 19, 0, 5}, {4, 0, 0, 0, 0, 64, {3, 6, 0, 0, 0, 0}, 19, 0, 5}, {4, 0, 0, 0, 0, 65, {3, 7, 0, 0, 0, 0}, 19, 0, 5}, {4, 0, 0, 0, 0, 66, {2, 4, 0, 0, 0, 0}, 20, 0, 3}, {4, 0, 0, 0, 0, 67, {2, 5, 0, 0, 0, 0}, 20, 0, 3}, {4, 0, 0, 0, 0, 68, {3, 4, 0, 0, 0, 0}, 20, 0, 3}, {4, 0, 0, 0, 0, 69, {3, 5, 0, 0, 0, 0}, 20, 0, 3}, {7, 0, 0, 0, 0, 70, {4, 10, 0, 0, 0, 0}, 9, 8, 0}, {7, 0, 0, 0, 0, 71, {5, 10, 0, 0, 0, 0}, 9, 8, 0}, {7, 0, 0, 0, 0, 72, {4, 11, 0, 0, 0, 0}, 9, 8, 0}, {7, 0, 0, 0, 0, 73, {5, 11, 0, 0, 0, 0}, 9, 8, 0}, {7, 0, 0, 0, 0, 74, {4, 12, 0, 0, 0, 0}, 9, 8, 0}, {7, 0, 0, 0, 0, 75, {5, 12, 0, 0, 0, 0}, 9, 8, 0}, {7, 0, 0, 0, 0, 76, {4, 13, 0, 0, 0, 0}, 9, 8, 0}, {7, 0, 0, 0, 0, 77, {5, 13, 0, 0, 0, 0}, 9, 8, 0}, {7, 0, 0, 0, 0, 78, {14, 8, 0, 0, 0, 0}, 14, 7, 0}, {7, 0, 0, 0, 0, 79, {15, 8, 0, 0, 0, 0}, 14, 7, 0}, {7, 0, 0, 0, 0, 80, {16, 8, 0, 0, 0, 0}, 14, 7, 0}, {7, 0, 0, 0, 0, 81, {17, 8, 0, 0, 0, 0}, 14, 7, 0}, {7, 0, 0, 0, 0, 82, {14, 9, 0, 0, 0, 0}, 14, 7, 0}, {7, 0, 0, 0, 0, 83, {15, 9, 0, 0, 0, 0}, 14, 7, 0}, {7, 0, 0, 0, 0, 84, {16, 9, 0, 0, 0, 0}, 14, 7, 0}, {7, 0, 0, 0, 0, 85, {17, 9, 0, 0, 0, 0}, 14, 7, 0}, {7, 0, 0, 0, 0, 86, {18, 6, 0, 0, 0, 0}, 16, 6, 0}, {7, 0, 0, 0, 0, 87, {19, 6, 0, 0, 0, 0}, 16, 6, 0}, {7, 0, 0, 0, 0, 88, {18, 7, 0, 0, 0, 0}, 16, 6, 0}, {7, 0, 0, 0, 0, 89, {19, 7, 0, 0, 0, 0}, 16, 6, 0}, {7, 0, 0, 0, 0, 90, {20, 6, 0, 0, 0, 0}, 16, 6, 0}, {7, 0, 0, 0, 0, 91, {21, 6, 0, 0, 0, 0}, 16, 6, 0}, {7, 0, 0, 0, 0, 92, {20, 7, 0, 0, 0, 0}, 16, 6, 0}, {7, 0, 0, 0, 0, 93, {21, 7, 0, 0, 0, 0}, 16, 6, 0}};
-static __constant__ HsAmp kHsAmps3[18] = {{0, 0, {0, 1, 8, 0}, {0, 0, 0}}, {0, 1, {0, 1, 9, 0}, {0, 0, 0}}, {0, 2, {0, 1, 10, 0}, {0, 0, 0}}, {0, 3, {0, 1, 17, 0}, {0, 0, 0}}, {0, 0, {0, 1, 18, 0}, {0, 0, 0}}, {0, 1, {0, 1, 19, 0}, {0, 0, 0}}, {0, 4, {0, 14, 6, 0}, {0, 0, 0}}, {0, 5, {0, 15, 7, 0}, {0, 0, 0}}, {0, 6, {0, 16, 5, 0}, {0, 0, 0}}, {0, 7, {11, 1, 5, 0}, {0, 0, 0}}, {0, 8, {11, 14, 3, 0}, {0, 0, 0}}, {0, 9, {11, 15, 4, 0}, {0, 0, 0}}, {0, 10, {12, 1, 7, 0}, {0, 0, 0}}, {0, 11, {12, 14, 2, 0}, {0, 0, 0}}, {0, 12, {12, 16, 4, 0}, {0, 0, 0}}, {0, 13, {13, 1, 6, 0}, {0, 0, 0}}, {0, 14, {13, 15, 2, 0}, {0, 0, 0}}, {0, 15, {13, 16, 3, 0}, {0, 0, 0}}};
+static __constant__ HsAmp kHsAmps3[18] = {{0, 0, {0, 1, 8, 0}, {0, 0, 0}}, {0, 1, {0, 1, 9, 0}, {0, 0, 0}}, {0, 2, {0, 1, 10, 0}, {0, 0, 0}}, {0, 3, {0, 1, 17, 0}, {0, 0, 0}}, {0, 0, {0, 1, 18, 0}, {0, 0, 0}}, {0, 1, {0, 1, 19, 0}, {0, 0, 0}}, {0, 4, {0, 14, 6, 0}, {0, 0, 0}}, {0, 5, {0, 15, 7, 0}, {0, 0, 0}}, {0, 6, {0, 16, 5, 0}, {0, 0, 0}}, {0, 7, {11, 1, 5, 0}, {0, 0, 0}}, {0, 8, {11, 14, 3, 0}, {0, 0, 0}}, {0, 9, {11, 15, 4, 0}, {0, 0, 0}}, {0, 10, {12, 1, 7, 0}, {0, 0, 0}}, {0, 11, {12, 14, 2, 0}, {0, 0, 0}}, {0, 12, {12, 16, 4, 0}, {0, 0, 0}}, {0, 13, {13, 1, 6, 0}, {0, 0, 0}}, {0, 14, {13, 15, 2, 0}, {0, 0, 0}}, {0, 15, {13, 16, 3, 0}, {0, 0, 0}}};  // grouped by type
 static __device__ const uint16_t kHsSlot3[20][32] = {{0, 0, 0, 0, 1, 1, 1, 1, 0, 0, 0, 0, 1, 1, 1, 1, 0, 0, 0, 0, 1, 1, 1, 1, 0, 0, 0, 0, 1, 1, 1, 1}, {2, 2, 3, 3, 2, 2, 3, 3, 2, 2, 3, 3, 2, 2, 3, 3, 2, 2, 3, 3, 2, 2, 3, 3, 2, 2, 3, 3, 2, 2, 3, 3}, {4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5}, {6, 6, 6, 6, 6, 6, 6, 6, 7, 7, 7, 7, 7, 7, 7, 7, 6, 6, 6, 6, 6, 6, 6, 6, 7, 7, 7, 7, 7, 7, 7, 7}, {8, 9, 8, 9, 8, 9, 8, 9, 8, 9, 8, 9, 8, 9, 8, 9, 8, 9, 8, 9, 8, 9, 8, 9, 8, 9, 8, 9, 8, 9, 8, 9}, {10, 12, 10, 12, 10, 12, 10, 12, 11, 13, 11, 13, 11, 13, 11, 13, 10, 12, 10, 12, 10, 12, 10, 12, 11, 13, 11, 13, 11, 13, 11, 13}, {14, 14, 14, 14, 14, 14, 14, 14, 16, 16, 16, 16, 16, 16, 16, 16, 15, 15, 15, 15, 15, 15, 15, 15, 17, 17, 17, 17, 17, 17, 17, 17}, {18, 20, 18, 20, 18, 20, 18, 20, 18, 20, 18, 20, 18, 20, 18, 20, 19, 21, 19, 21, 19, 21, 19, 21, 19, 21, 19, 21, 19, 21, 19, 21}, {22, 26, 22, 26, 22, 26, 22, 26, 24, 28, 24, 28, 24, 28, 24, 28, 23, 27, 23, 27, 23, 27, 23, 27, 25, 29, 25, 29, 25, 29, 25, 29}, {30, 34, 30, 34, 30, 34, 30, 34, 32, 36, 32, 36, 32, 36, 32, 36, 31, 35, 31, 35, 31, 35, 31, 35, 33, 37, 33, 37, 33, 37, 33, 37}, {38, 42, 38, 42, 38, 42, 38, 42, 40, 44, 40, 44, 40, 44, 40, 44, 39, 43, 39, 43, 39, 43, 39, 43, 41, 45, 41, 45, 41, 45, 41, 45}, {46, 46, 46, 46, 48, 48, 48, 48, 46, 46, 46, 46, 48, 48, 48, 48, 47, 47, 47, 47, 49, 49, 49, 49, 47, 47, 47, 47, 49, 49, 49, 49}, {50, 50, 50, 50, 52, 52, 52, 52, 51, 51, 51, 51, 53, 53, 53, 53, 50, 50, 50, 50, 52, 52, 52, 52, 51, 51, 51, 51, 53, 53, 53, 53}, {54, 56, 54, 56, 55, 57, 55, 57, 54, 56, 54, 56, 55, 57, 55, 57, 54, 56, 54, 56, 55, 57, 55, 57, 54, 56, 54, 56, 55, 57, 55, 57}, {58, 60, 59, 61, 58, 60, 59, 61, 58, 60, 59, 61, 58, 60, 59, 61, 58, 60, 59, 61, 58, 60, 59, 61, 58, 60, 59, 61, 58, 60, 59, 61}, {62, 62, 64, 64, 62, 62, 64, 64, 63, 63, 65, 65, 63, 63, 65, 65, 62, 62, 64, 64, 62, 62, 64, 64, 63, 63, 65, 65, 63, 63, 65, 65}, {66, 66, 68, 68, 66, 66, 68, 68, 66, 66, 68, 68, 66, 66, 68, 68, 67, 67, 69, 69, 67, 67, 69, 69, 67, 67, 69, 69, 67, 67, 69, 69}, {70, 74, 70, 74, 70, 74, 70, 74, 72, 76, 72, 76, 72, 76, 72, 76, 71, 75, 71, 75, 71, 75, 71, 75, 73, 77, 73, 77, 73, 77, 73, 77}, {78, 82, 78, 82, 78, 82, 78, 82, 80, 84, 80, 84, 80, 84, 80, 84, 79, 83, 79, 83, 79, 83, 79, 83, 81, 85, 81, 85, 81, 85, 81, 85}, {86, 90, 86, 90, 86, 90, 86, 90, 88, 92, 88, 92, 88, 92, 88, 92, 87, 91, 87, 91, 87, 91, 87, 91, 89, 93, 89, 93, 89, 93, 89, 93}};
 // colour-matrix numerators as the BF16 B operand of the tensor-core colour sum
 static __device__ __align__(16) const uint32_t kColourB3[128] = {0xc1004280, 0x3f80c100, 0x41203f80, 0x00000000, 0x4280c100, 0x41203f80, 0x3f80c100, 0x00000000, 0x3f80c100, 0xc1004280, 0x3f804120, 0x00000000, 0x41203f80, 0x4280c100, 0xc1003f80, 0x00000000, 0xc1003f80, 0x3f804120, 0xc1004280, 0x00000000, 0x3f804120, 0xc1003f80, 0x4280c100, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000};
@@ -54,6 +54,21 @@ struct Proc3 {
       case 14: J[4] += amp; break;
       case 15: J[5] += amp; break;
       default: break;
+    }
+  }
+  // amplitudes of one (event, helicity): operands cur[sl[c * NHEL]], flows into J
+  template <class R>
+  static __device__ __forceinline__ void hs_amplitudes(const W4<R>* __restrict__ cur, const uint16_t* __restrict__ sl, const R* __restrict__ K, const Couplings<R>& cp, cx<R>* J) {
+    W4<R> o0, o1, o2, o3;
+    {  // type 0: 18 amplitudes
+      int l0 = -1, l1 = -1;
+      for (int d = 0; d < 18; ++d) {
+        const HsAmp a = kHsAmps3[d];
+        if (a.op[0] != l0) { o0 = cur[sl[a.op[0] * NHEL]]; l0 = a.op[0]; }
+        if (a.op[1] != l1) { o1 = cur[sl[a.op[1] * NHEL]]; l1 = a.op[1]; }
+        o2 = cur[sl[a.op[2] * NHEL]];
+        hs_flows<R>(a.pat, FFV1_0<R>(o0, o1, o2, cp.gs), J);
+      }
     }
   }
   static constexpr int NMOM = 21;

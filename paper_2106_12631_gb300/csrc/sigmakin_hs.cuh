@@ -145,8 +145,7 @@ __global__ void __launch_bounds__(SigCfg<P>::NT, 1) sigmakin_hs_kernel(SigArgs a
     }
     __syncthreads();
   }
-  // 3. amplitudes of this thread's (event, helicity); J in registers, the next
-  //    amplitude's operands loaded while the current one is computed
+  // 3. amplitudes of this thread's (event, helicity), J in registers
   const bool active = tid < nev * ng;
   const int e = active ? tid / ng : 0;
   const int ih = good[active ? tid - e * ng : 0];
@@ -156,28 +155,7 @@ __global__ void __launch_bounds__(SigCfg<P>::NT, 1) sigmakin_hs_kernel(SigArgs a
   cx<R> J[NC];
 #pragma unroll
   for (int s = 0; s < NC; ++s) J[s] = cx<R>(R(0), R(0));
-  const HsAmp* amps = P::hs_amps();
-  HsAmp op = amps[0];
-  W4<R> o0 = cur[sl[op.op[0] * P::NHEL]], o1 = cur[sl[op.op[1] * P::NHEL]];
-  W4<R> o2 = cur[sl[op.op[2] * P::NHEL]], o3 = cur[sl[op.op[3] * P::NHEL]];
-  for (int d = 0; d < P::HS_NAMP; ++d) {
-    const HsAmp nx = amps[d + 1 < P::HS_NAMP ? d + 1 : d];
-    const W4<R> n0 = nx.op[0] == op.op[0] ? o0 : cur[sl[nx.op[0] * P::NHEL]];
-    const W4<R> n1 = nx.op[1] == op.op[1] ? o1 : cur[sl[nx.op[1] * P::NHEL]];
-    const W4<R> n2 = cur[sl[nx.op[2] * P::NHEL]];
-    const W4<R> n3 = cur[sl[nx.op[3] * P::NHEL]];
-    cx<R> amp;
-    switch (op.type) {
-      case 0: amp = FFV1_0<R>(o0, o1, o2, cp.gs); break;
-      case 1: amp = FFV1_0<R>(o0, o1, o2, cp.ee); break;
-      case 2: amp = FFV2_4_0<R>(o0, o1, o2, cp.gz, cp.gzl, cp.gzr); break;
-      case 3: amp = VVV1_0<R>(o0, o1, o2, K + 4 * op.k[0], K + 4 * op.k[1], K + 4 * op.k[2], cp.gs); break;
-      default: amp = VVVV_0<R>(op.type - 4, o0, o1, o2, o3, cp.gs2);
-    }
-    P::template hs_flows<R>(op.pat, amp, J);
-    op = nx;
-    o0 = n0; o1 = n1; o2 = n2; o3 = n3;
-  }
+  P::template hs_amplitudes<R>(cur, sl, K, cp, J);
   R* Jr = Js + tid;
   R* Ji = Js + NC * NT + tid;
 #pragma unroll

@@ -1118,15 +1118,20 @@ class SharedProgram:
             amps.append((self.AMP_TYPES[kind], ops, ks, flows))
         amps.sort(key=lambda a: (a[1], a[0]))
         patterns = {}
-        amp_rows = []
+        groups = {}
         for t, ops, ks, flows in amps:
             key = tuple(flows)
             if key not in patterns:
                 patterns[key] = len(patterns)
             o = list(ops) + [0] * (4 - len(ops))
-            amp_rows.append("{%d, %d, {%s}, {%s}}" % (t, patterns[key], ", ".join(map(str, o)),
-                                                     ", ".join(map(str, ks[:3]))))
+            groups.setdefault(t, []).append("{%d, %d, {%s}, {%s}}" % (
+                t, patterns[key], ", ".join(map(str, o)), ", ".join(map(str, ks[:3]))))
         self.patterns = patterns
+        self.groups = {t: len(rows) for t, rows in groups.items()}
+        self.amp_list = [(t, list(ops), ks, flows) for t, ops, ks, flows in amps]
+        amp_rows = []
+        for t in sorted(groups):
+            amp_rows.extend(groups[t])
         # slot of every current for every event helicity index
         slot = []
         for d in self.order:
@@ -1146,7 +1151,8 @@ class SharedProgram:
             pid, len(items), ", ".join("{%d, %d, %d, %d, %d, %d, {%s}, %d, %d, %d}" % (
                 t, a, b, c, flag, o, ", ".join(map(str, ins)), k0, k1, pr)
                 for (t, a, b, c, flag, o, ins, k0, k1, pr) in items)))
-        out.append("static __constant__ HsAmp kHsAmps%d[%d] = {%s};" % (pid, len(amp_rows), ", ".join(amp_rows)))
+        out.append("static __constant__ HsAmp kHsAmps%d[%d] = {%s};  // grouped by type"
+                   % (pid, len(amp_rows), ", ".join(amp_rows)))
         out.append("static __device__ const uint16_t kHsSlot%d[%d][%d] = {%s};" % (
             pid, len(self.order), nh, ", ".join("{" + ", ".join(map(str, r)) + "}" for r in slot)))
         self.tables = dict(nitems=len(items), level_start=level_start, namps=len(amps), ncur=len(self.order))
@@ -1181,7 +1187,69 @@ class SharedProgram:
             "  static __device__ __forceinline__ const HsItem* hs_items() { return kHsItems%d; }" % pid,
             "  static __device__ __forceinline__ const HsAmp* hs_amps() { return kHsAmps%d; }" % pid,
             "  static __device__ __forceinline__ const uint16_t* hs_slots() { return &kHsSlot%d[0][0]; }" % pid,
-        ] + self._flow_switch()
+        ] + self._flow_switch() + (self._amp_unrolled(pid) if self.AMP_UNROLL else self._amp_loops(pid))
+
+    AMP_UNROLL = False  # straight-line amplitude phase instead of per-type loops
+
+    def _amp_unrolled(self, pid: int) -> list:
+        calls = {0: "FFV1_0<R>(%s, %s, %s, cp.gs)", 1: "FFV1_0<R>(%s, %s, %s, cp.ee)",
+                 2: "FFV2_4_0<R>(%s, %s, %s, cp.gz, cp.gzl, cp.gzr)"}
+        lines = ["  template <class R>",
+                 "  static __device__ __forceinline__ void hs_amplitudes(const W4<R>* __restrict__ cur,"
+                 " const uint16_t* __restrict__ sl, const R* __restrict__ K, const Couplings<R>& cp, cx<R>* J) {",
+                 "    cx<R> amp;"]
+        ops = {0: "J[%d] += amp;", 1: "J[%d] -= amp;", 2: "J[%d] += mul_i(amp);", 3: "J[%d] -= mul_i(amp);"}
+        loaded = {}
+        for t, o, ks, flows in self.amp_list:
+            names = []
+            for c in o:
+                if c not in loaded:
+                    loaded[c] = "c%d" % c
+                    lines.append("    const W4<R> c%d = cur[sl[%d * NHEL]];" % (c, c))
+                names.append(loaded[c])
+            if t in calls:
+                lines.append("    amp = " + calls[t] % tuple(names[:3]) + ";")
+            elif t == 3:
+                lines.append("    amp = VVV1_0<R>(%s, %s, %s, K + %d, K + %d, K + %d, cp.gs);" % (
+                    names[0], names[1], names[2], 4 * ks[0], 4 * ks[1], 4 * ks[2]))
+            else:
+                lines.append("    amp = VVVV_0<R>(%d, %s, %s, %s, %s, cp.gs2);" % (t - 4, *names[:4]))
+            lines.append("    " + " ".join(ops[f >> 6] % (f & 63) for f in flows))
+        lines.append("  }")
+        return lines
+
+    def _amp_loops(self, pid: int) -> list:
+        """Amplitude phase: one loop per amplitude type over its (constant-memory)
+        table; an operand is reloaded only when it changes (uniform branch)."""
+        calls = {0: "FFV1_0<R>(o0, o1, o2, cp.gs)", 1: "FFV1_0<R>(o0, o1, o2, cp.ee)",
+                 2: "FFV2_4_0<R>(o0, o1, o2, cp.gz, cp.gzl, cp.gzr)",
+                 3: "VVV1_0<R>(o0, o1, o2, K + 4 * a.k[0], K + 4 * a.k[1], K + 4 * a.k[2], cp.gs)",
+                 4: "VVVV_0<R>(0, o0, o1, o2, o3, cp.gs2)", 5: "VVVV_0<R>(1, o0, o1, o2, o3, cp.gs2)",
+                 6: "VVVV_0<R>(2, o0, o1, o2, o3, cp.gs2)"}
+        lines = ["  // amplitudes of one (event, helicity): operands cur[sl[c * NHEL]], flows into J",
+                 "  template <class R>",
+                 "  static __device__ __forceinline__ void hs_amplitudes(const W4<R>* __restrict__ cur,"
+                 " const uint16_t* __restrict__ sl, const R* __restrict__ K, const Couplings<R>& cp, cx<R>* J) {",
+                 "    W4<R> o0, o1, o2, o3;"]
+        start = 0
+        for t in sorted(self.groups):
+            n = self.groups[t]
+            nops = 4 if t >= 4 else 3
+            lines.append("    {  // type %d: %d amplitudes" % (t, n))
+            lines.append("      int l0 = -1, l1 = -1;")
+            lines.append("      for (int d = %d; d < %d; ++d) {" % (start, start + n))
+            lines.append("        const HsAmp a = kHsAmps%d[d];" % pid)
+            lines.append("        if (a.op[0] != l0) { o0 = cur[sl[a.op[0] * NHEL]]; l0 = a.op[0]; }")
+            lines.append("        if (a.op[1] != l1) { o1 = cur[sl[a.op[1] * NHEL]]; l1 = a.op[1]; }")
+            lines.append("        o2 = cur[sl[a.op[2] * NHEL]];")
+            if nops == 4:
+                lines.append("        o3 = cur[sl[a.op[3] * NHEL]];")
+            lines.append("        hs_flows<R>(a.pat, %s, J);" % calls[t])
+            lines.append("      }")
+            lines.append("    }")
+            start += n
+        lines.append("  }")
+        return lines
 
     def _flow_switch(self) -> list:
         """J_s +=, -=, += i, -= i amp for the colour flows of amplitude pattern `pat`."""
