@@ -1199,22 +1199,23 @@ class SharedProgram:
                  " const uint16_t* __restrict__ sl, const R* __restrict__ K, const Couplings<R>& cp, cx<R>* J) {",
                  "    cx<R> amp;"]
         ops = {0: "J[%d] += amp;", 1: "J[%d] -= amp;", 2: "J[%d] += mul_i(amp);", 3: "J[%d] -= mul_i(amp);"}
-        loaded = {}
-        for t, o, ks, flows in self.amp_list:
+        for ia, (t, o, ks, flows) in enumerate(self.amp_list):
+            if ia % 4 == 0 and ia:
+                lines.append("    __syncwarp();  // bounds load hoisting (live ranges)")
+            lines.append("    {")
             names = []
-            for c in o:
-                if c not in loaded:
-                    loaded[c] = "c%d" % c
-                    lines.append("    const W4<R> c%d = cur[sl[%d * NHEL]];" % (c, c))
-                names.append(loaded[c])
+            for j, c in enumerate(o):
+                lines.append("      const W4<R> x%d = cur[sl[%d * NHEL]];" % (j, c))
+                names.append("x%d" % j)
             if t in calls:
-                lines.append("    amp = " + calls[t] % tuple(names[:3]) + ";")
+                lines.append("      amp = " + calls[t] % tuple(names[:3]) + ";")
             elif t == 3:
-                lines.append("    amp = VVV1_0<R>(%s, %s, %s, K + %d, K + %d, K + %d, cp.gs);" % (
+                lines.append("      amp = VVV1_0<R>(%s, %s, %s, K + %d, K + %d, K + %d, cp.gs);" % (
                     names[0], names[1], names[2], 4 * ks[0], 4 * ks[1], 4 * ks[2]))
             else:
-                lines.append("    amp = VVVV_0<R>(%d, %s, %s, %s, %s, cp.gs2);" % (t - 4, *names[:4]))
-            lines.append("    " + " ".join(ops[f >> 6] % (f & 63) for f in flows))
+                lines.append("      amp = VVVV_0<R>(%d, %s, %s, %s, %s, cp.gs2);" % (t - 4, *names[:4]))
+            lines.append("      " + " ".join(ops[f >> 6] % (f & 63) for f in flows))
+            lines.append("    }")
         lines.append("  }")
         return lines
 
