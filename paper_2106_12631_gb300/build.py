@@ -2,7 +2,9 @@
 
 One nvcc invocation per translation unit, run in parallel, then a shared-
 library link.  Rebuilds only when a source or header is newer than the
-library.  ``MG_PTXAS_VERBOSE=1`` adds ``-Xptxas -v`` (registers, spills).
+library.  ``MG_PTXAS_VERBOSE=1`` adds ``-Xptxas -v`` (registers, spills);
+``MG_NVCC_DEFINES`` adds preprocessor definitions (tuning knobs such as
+``-DMG_HS_NT=256``).
 """
 from __future__ import annotations
 
@@ -51,6 +53,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     extra = ["-Xptxas", "-v"] if os.environ.get("MG_PTXAS_VERBOSE") else []
+    extra += os.environ.get("MG_NVCC_DEFINES", "").split()  # e.g. -DMG_HS_NT=256 (tuning)
     cc = nvcc()
 
     def compile_one(src):

@@ -123,7 +123,8 @@ struct SigLayout {
   static constexpr size_t tileA = 128 * C::KP * 2;  // one 128-row BF16 tile
   static constexpr size_t o_B = o_A + (TC ? 3 * 2 * C::MBLK * tileA : 0);
   static constexpr size_t bytes = o_B + (TC ? C::NP * C::KP * 2 : 0);
-  static constexpr uint32_t TMEM_COLS = C::MBLK * 2 * C::NP;
+  static constexpr uint32_t TMEM_COLS = tc::tmem_cols(C::MBLK * 2 * C::NP);
+  static_assert(TMEM_COLS <= 512, "TMEM holds 512 columns");
 };
 
 // Phase 1b: per-event tables from the FP64 momenta already in shared memory.

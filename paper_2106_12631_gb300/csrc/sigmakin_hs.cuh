@@ -24,20 +24,32 @@
 
 namespace mg {
 
+#ifndef MG_HS_NT
+#define MG_HS_NT 512
+#endif
+
+// One large CTA per SM for the many-colour processes: its warps walk the same
+// amplitude table in near lockstep, so they share instruction fetches (the
+// amplitude phase is several thousand instructions long; independent small
+// CTAs at different points of it thrash the instruction cache).  FP64 needs
+// more registers per thread, hence fewer threads.
 template <class P, class R>
 struct HsCfg {
-  using C = SigCfg<P>;
-  static constexpr int NT = C::NT;
-  static constexpr size_t CUR_BUDGET = 48 * 1024 * (sizeof(R) / 4);  // shared memory for current variants
+  static constexpr int NT = P::NCOLOR >= 6 ? (sizeof(R) == 4 ? MG_HS_NT : 256) : 128;
+  static constexpr int EVMIN = (NT / P::NHEL) > 0 ? (NT / P::NHEL) : 1;
+  static constexpr int EVWANT = (4 * EVMIN) < 32 ? 4 * EVMIN : 32;
+  static constexpr size_t CUR_BUDGET = 110 * 1024;  // shared memory for current variants
   static constexpr int FIT = (int)(CUR_BUDGET / (P::HS_NSLOT * sizeof(W4<R>)));
-  static constexpr int EVCAP = (FIT < C::EVCAP ? (FIT > C::EVMIN ? FIT : C::EVMIN) : C::EVCAP);
+  static constexpr int EVCAP = FIT < EVWANT ? (FIT > EVMIN ? FIT : EVMIN) : EVWANT;
+  static constexpr int KP = ((P::NCOLOR + 15) / 16) * 16;
+  static constexpr int NP = KP;
+  static constexpr int MBLK = NT / 128;
 };
 
 template <class P, class R, int CS>
 struct HsLayout {
-  using C = SigCfg<P>;
   using H = HsCfg<P, R>;
-  static constexpr int EVCAP = H::EVCAP;
+  static constexpr int NT = H::NT, EVCAP = H::EVCAP, KP = H::KP, NP = H::NP, MBLK = H::MBLK;
   static constexpr bool TC = CS == CS_TC;
   static constexpr size_t o_momtab = 0;
   static constexpr size_t o_proptab = align_up(o_momtab + 12 * P::NMOM, 16);
@@ -47,16 +59,150 @@ struct HsLayout {
   static constexpr size_t o_K = align_up(o_p + 8 * EVCAP * P::NPAR * 4, 16);
   static constexpr size_t o_pr = align_up(o_K + sizeof(R) * EVCAP * P::NMOM * 4, 16);
   static constexpr size_t o_m2 = align_up(o_pr + 2 * sizeof(R) * EVCAP * P::NPROP, 16);
-  static constexpr size_t o_slot = align_up(o_m2 + 8 * C::NT, 16);
-  static constexpr size_t o_cur = align_up(o_slot + 2 * P::HS_NCUR * P::NHEL, 128);
-  static constexpr size_t o_J = align_up(o_cur + sizeof(W4<R>) * EVCAP * P::HS_NSLOT, 128);
-  static constexpr size_t o_A = align_up(o_J + 2 * sizeof(R) * P::NCOLOR * C::NT, 1024);
-  static constexpr size_t tileA = 128 * C::KP * 2;
-  static constexpr size_t o_B = o_A + (TC ? 3 * 2 * C::MBLK * tileA : 0);
-  static constexpr size_t bytes = o_B + (TC ? C::NP * C::KP * 2 : 0);
-  static constexpr uint32_t TMEM_COLS = C::MBLK * 2 * C::NP;
+  static constexpr size_t o_slot = align_up(o_m2 + 8 * NT, 16);
+  static constexpr size_t o_B = align_up(o_slot + 2 * P::HS_NCUR * P::NHEL, 1024);
+  static constexpr size_t o_U = align_up(o_B + (TC ? NP * KP * 2 : 0), 1024);
+  // union: current variants (phases 2-3), then the tensor-core A tiles (phase 4)
+  static constexpr size_t o_cur = o_U, o_A = o_U;
+  static constexpr size_t tileA = 128 * KP * 2;
+  static constexpr size_t cur_bytes = sizeof(W4<R>) * EVCAP * P::HS_NSLOT;
+  static constexpr size_t a_bytes = TC ? 3 * MBLK * tileA : 0;  // one component's three splits
+  static constexpr size_t bytes = o_U + (cur_bytes > a_bytes ? cur_bytes : a_bytes);
+  static constexpr uint32_t TMEM_COLS = tc::tmem_cols(MBLK * 2 * NP);
+  static_assert(!TC || NT % 128 == 0, "CTA rows must fill 128-row MMA blocks");
+  static_assert(TMEM_COLS <= 512, "TMEM holds 512 columns");
   static_assert(bytes <= 232448, "shared memory per CTA above the 227 KB limit");
 };
+
+// Tensor-core colour sum of the CTA's NT rows with J in registers (layout and
+// three-term BF16 split as in colour_tc.cuh).  Two passes, real then imaginary
+// part, so that one component's A tiles fit in the dead current-variant
+// storage: Y_c = A_c B lands in TMEM columns [c NP, (c+1) NP).
+template <class P, class L>
+__device__ __forceinline__ float colour_sum_tc_regs(unsigned char* smem, const cx<float>* J, uint32_t tmem,
+                                                    uint32_t mbar) {
+  constexpr int NC = P::NCOLOR, KP = L::KP;
+  const int tid = threadIdx.x;
+  const int b = tid >> 7, r = tid & 127;
+  bool ok = true;
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    if (c == 1) {
+      // pass 0's MMAs have read its tiles once every thread saw the barrier
+      // complete; a timed-out wait ends both passes for the whole CTA
+      if (__syncthreads_or(!ok)) {
+        tc::mbar_wait(mbar, 0);
+        return __int_as_float(0x7fc00000);
+      }
+    }
+#pragma unroll
+    for (int k0 = 0; k0 < KP; k0 += 8) {
+      uint32_t w[3][4];
+#pragma unroll
+      for (int q = 0; q < 8; q += 2) {
+        uint16_t hb[3][2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int k = k0 + q + u;
+          const float x = k < NC ? (c == 0 ? J[k].re : J[k].im) : 0.0f;
+          const uint16_t h = tc::bf16_bits(x);
+          const float r1 = x - tc::bf16_value(h);
+          const uint16_t m = tc::bf16_bits(r1);
+          const uint16_t l = tc::bf16_bits(r1 - tc::bf16_value(m));
+          hb[0][u] = h; hb[1][u] = m; hb[2][u] = l;
+        }
+#pragma unroll
+        for (int sp = 0; sp < 3; ++sp) w[sp][q >> 1] = (uint32_t)hb[sp][0] | ((uint32_t)hb[sp][1] << 16);
+      }
+#pragma unroll
+      for (int sp = 0; sp < 3; ++sp) {
+        unsigned char* tile = smem + L::o_A + (sp * L::MBLK + b) * L::tileA;
+        *reinterpret_cast<uint4*>(tile + tc::kmajor_offset<KP>(r, k0)) =
+            make_uint4(w[sp][0], w[sp][1], w[sp][2], w[sp][3]);
+      }
+    }
+    tc::fence_async_shared();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+      constexpr uint32_t idesc = tc::idesc_bf16(128, L::NP);
+      constexpr uint32_t LBO = 128, SBO = (KP / 8) * 128;
+      const uint32_t bbase = tc::smem_addr(smem + L::o_B);
+#pragma unroll
+      for (int bb = 0; bb < L::MBLK; ++bb) {
+        const uint32_t d = tmem + (uint32_t)((bb * 2 + c) * L::NP);
+#pragma unroll
+        for (int sp = 0; sp < 3; ++sp) {
+          const uint32_t abase = tc::smem_addr(smem + L::o_A + (sp * L::MBLK + bb) * L::tileA);
+#pragma unroll
+          for (int j = 0; j < KP / 16; ++j)
+            tc::mma_bf16(d, tc::smem_desc(abase + j * 256, LBO, SBO), tc::smem_desc(bbase + j * 256, LBO, SBO),
+                         idesc, (sp | j) != 0);
+        }
+      }
+      tc::mma_commit(mbar);
+    }
+    ok = tc::mbar_wait(mbar, (uint32_t)c);
+  }
+  tc::fence_after_sync();
+  const int warp = tid >> 5;
+  const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+  float yr[L::NP], yi[L::NP];
+#pragma unroll
+  for (int c0 = 0; c0 < L::NP; c0 += 16) {
+    tc::tmem_ld16(tmem + lane_base + (uint32_t)((b * 2 + 0) * L::NP + c0), yr + c0);
+    tc::tmem_ld16(tmem + lane_base + (uint32_t)((b * 2 + 1) * L::NP + c0), yi + c0);
+  }
+  tc::tmem_wait_ld();
+  float s = 0.0f;
+#pragma unroll
+  for (int k = 0; k < NC; ++k) s += J[k].re * yr[k] + J[k].im * yi[k];
+  s *= 1.0f / (float)P::CDEN;
+  if (!ok) {
+    tc::mbar_wait(mbar, 1);  // second bounded wait for the MMAs still in flight
+    s = __int_as_float(0x7fc00000);
+  }
+  return s;
+}
+
+// Phase 1 with this kernel's thread count (same arithmetic as event_tables).
+template <class P, class R, class L>
+__device__ __forceinline__ void hs_event_tables(unsigned char* smem, const SigArgs& a, int64_t e0, int nev) {
+  constexpr int NT = L::NT;
+  const int tid = threadIdx.x;
+  auto p = reinterpret_cast<double(*)[P::NPAR][4]>(smem + L::o_p);
+  auto K = reinterpret_cast<R(*)[P::NMOM][4]>(smem + L::o_K);
+  auto pr = reinterpret_cast<cx<R>(*)[P::NPROP]>(smem + L::o_pr);
+  const int(*mom_tab)[3] = reinterpret_cast<const int(*)[3]>(smem + L::o_momtab);
+  const int(*prop_tab)[2] = reinterpret_cast<const int(*)[2]>(smem + L::o_proptab);
+  for (int t = tid; t < nev * P::NPAR * 4; t += NT) {
+    const int e = t % nev, c = t / nev;
+    p[e][c >> 2][c & 3] = a.mom[(int64_t)c * a.nevt + e0 + e];
+  }
+  __syncthreads();
+  for (int t = tid; t < nev * (P::NMOM + P::NPROP); t += NT) {
+    const int e = t % nev, j = t / nev;
+    const int mj = j < P::NMOM ? j : prop_tab[j - P::NMOM][0];
+    const int kind = mom_tab[mj][0], lmask = mom_tab[mj][1], smask = mom_tab[mj][2];
+    double k[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int l = 0; l < P::NPAR; ++l) {
+      if (!(lmask >> l & 1)) continue;
+      const double sg = (kind == 1 && (smask >> l & 1)) ? -1.0 : 1.0;
+#pragma unroll
+      for (int mu = 0; mu < 4; ++mu) k[mu] += sg * p[e][l][mu];
+    }
+    if (j < P::NMOM) {
+#pragma unroll
+      for (int mu = 0; mu < 4; ++mu) K[e][j][mu] = R(k[mu]);
+    } else {
+      double re, im;
+      propagator_fp64(k, prop_tab[j - P::NMOM][1], a.pp, re, im);
+      pr[e][j - P::NMOM] = cx<R>(R(re), R(im));
+    }
+  }
+  __syncthreads();
+}
 
 // one current variant
 template <class P, class R>
@@ -80,8 +226,8 @@ __device__ __forceinline__ void hs_item(const HsItem& it, W4<R>* cur, const R* K
 }
 
 template <class P, class R, int CS>
-__global__ void __launch_bounds__(SigCfg<P>::NT, 1) sigmakin_hs_kernel(SigArgs a, Couplings<R> cp) {
-  using C = SigCfg<P>;
+__global__ void __launch_bounds__(HsCfg<P, R>::NT, 1) sigmakin_hs_kernel(SigArgs a, Couplings<R> cp) {
+  using C = HsCfg<P, R>;
   using L = HsLayout<P, R, CS>;
   constexpr int NT = C::NT, NC = P::NCOLOR;
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -90,7 +236,6 @@ __global__ void __launch_bounds__(SigCfg<P>::NT, 1) sigmakin_hs_kernel(SigArgs a
   double* sm2 = reinterpret_cast<double*>(smem + L::o_m2);
   uint16_t* slots = reinterpret_cast<uint16_t*>(smem + L::o_slot);
   W4<R>* curs = reinterpret_cast<W4<R>*>(smem + L::o_cur);
-  R* Js = reinterpret_cast<R*>(smem + L::o_J);
   const int tid = threadIdx.x;
   load_tables<P, L>(smem);
   if (tid == 0) {
@@ -125,7 +270,7 @@ __global__ void __launch_bounds__(SigCfg<P>::NT, 1) sigmakin_hs_kernel(SigArgs a
     tc::fence_before_sync();
   }
   // 1. momenta and per-event tables
-  event_tables<P, R, L>(smem, a, e0, nev);
+  hs_event_tables<P, R, L>(smem, a, e0, nev);
   if constexpr (L::TC) {
     tc::fence_after_sync();
     tmem = static_cast<uint32_t>(misc[1]);
@@ -156,15 +301,11 @@ __global__ void __launch_bounds__(SigCfg<P>::NT, 1) sigmakin_hs_kernel(SigArgs a
 #pragma unroll
   for (int s = 0; s < NC; ++s) J[s] = cx<R>(R(0), R(0));
   P::template hs_amplitudes<R>(cur, sl, K, cp, J);
-  R* Jr = Js + tid;
-  R* Ji = Js + NC * NT + tid;
-#pragma unroll
-  for (int s = 0; s < NC; ++s) { Jr[s * NT] = J[s].re; Ji[s * NT] = J[s].im; }
   // 4. colour sum and helicity sum
   double m2;
   if constexpr (L::TC) {
-    __syncthreads();
-    m2 = (double)colour_sum_tc<P, L>(smem, Js, tmem, mbar);
+    __syncthreads();  // the A tiles overwrite the current variants
+    m2 = (double)colour_sum_tc_regs<P, L>(smem, J, tmem, mbar);
   } else {
     m2 = (double)colour_sum_simt<P, R>([&](int s) { return J[s].re; }, [&](int s) { return J[s].im; });
   }

@@ -23,7 +23,8 @@ cudaError_t launch_sigmakin_hs_variant(const SigArgs& a, const Couplings<R>& cp,
   auto k = sigmakin_hs_kernel<P, R, CS>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
   if (e != cudaSuccess) return e;
-  k<<<(unsigned)grid, SigCfg<P>::NT, L::bytes, s>>>(a, cp);
+  grid = (a.nevt + HsCfg<P, R>::EVMIN - 1) / HsCfg<P, R>::EVMIN;
+  k<<<(unsigned)grid, HsCfg<P, R>::NT, L::bytes, s>>>(a, cp);
   return cudaGetLastError();
 }
 
