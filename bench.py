@@ -37,6 +37,24 @@ FP32_LANES_PER_SM = 128
 SMS = 152
 SM_MAX_MHZ = 2070.0
 
+# DRAM traffic of the mixed gg -> t t~ g g SIGMAKIN kernel from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum of one launch over 2^18 events,
+# scaled by events; it reads the momenta once and writes |M|^2), valid only
+# while the kernel sources are the ones captured.
+SIGMAKIN_TRAFFIC = {"bytes_per_event": None, "sources_sha1": None}
+SIGMAKIN_SOURCES = ["paper_2106_12631_gb300/csrc/" + f for f in
+                    ("sigmakin_hs.cuh", "sigmakin.cuh", "helas.cuh", "colour_tc.cuh", "mg_types.cuh",
+                     "process.cuh", "gen/proc4.cuh")]
+
+
+def sources_sha1() -> str:
+    import hashlib
+    h = hashlib.sha1()
+    for f in SIGMAKIN_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -337,15 +355,23 @@ def main():
     e2e = {"value": world * nevt * args.steps / te2e, "unit": UNIT, "h2d_bytes_per_step": 16 * 8 * nevt,
            "d2h_bytes_per_step": 8 * nevt}
 
-    # roofline of the dominant kernel (SIGMAKIN): FP32 CUDA-core arithmetic
+    # roofline of the dominant kernel (SIGMAKIN): FP32 CUDA-core arithmetic.
+    # Algorithmic flops per event of the helicity-shared kernel: every current
+    # variant once per event, then per good helicity its amplitudes and colour sum.
     s = procgen.summary(proc)
-    flops_per_me = ngood * (s["flops_amp"] + s["flops_csum"])
+    flops_per_me = s["hs_flops_items"] + ngood * (s["hs_flops_amp_hel"] + s["flops_csum"])
     ksec = statistics.mean(kern)
     achieved = flops_per_me * nevt / ksec / 1e12
     peak32 = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    traffic = None
+    if args.mode == "mixed" and SIGMAKIN_TRAFFIC["bytes_per_event"] and \
+            SIGMAKIN_TRAFFIC["sources_sha1"] == sources_sha1():
+        traffic = SIGMAKIN_TRAFFIC["bytes_per_event"] * nevt
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak32, "unit": "TFLOP/s",
-                "frac": achieved / peak32, "traffic": None,
-                "kernel": "sigmakin_kernel<Proc4,float>", "flops_per_me": flops_per_me,
+                "frac": achieved / peak32, "traffic": traffic,
+                "kernel": "sigmakin_hs_kernel<Proc4,%s>" % ("float,TC" if args.mode == "mixed" else args.mode),
+                "flops_per_me": flops_per_me,
+                "flops_per_me_per_helicity_unshared": s["flops_amp"] + s["flops_csum"],
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
 
     line = {

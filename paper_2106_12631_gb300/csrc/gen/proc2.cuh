@@ -4,10 +4,9 @@
 // colour-flow coefficients used: [-1j, 1j, (1+0j)]
 #pragma once
 namespace mg {
-// helicity-shared program: 7 currents in 2 levels, 20 variant slots, 3 amplitudes, 6884 flops per event (all helicities)
-static __device__ const HsItem kHsItems2[20] = {{1, 2, -1, 1, 1, 0, {0, 0, 0, 0, 0, 0}, 2, 0, 0}, {1, 2, 1, 1, 1, 1, {0, 0, 0, 0, 0, 0}, 2, 0, 0}, {0, 3, -1, -1, 1, 2, {0, 0, 0, 0, 0, 0}, 3, 0, 0}, {0, 3, 1, -1, 1, 3, {0, 0, 0, 0, 0, 0}, 3, 0, 0}, {2, 0, -1, 1, 0, 4, {0, 0, 0, 0, 0, 0}, 0, 0, 0}, {2, 0, 1, 1, 0, 5, {0, 0, 0, 0, 0, 0}, 0, 0, 0}, {2, 1, -1, 1, 0, 6, {0, 0, 0, 0, 0, 0}, 1, 0, 0}, {2, 1, 1, 1, 0, 7, {0, 0, 0, 0, 0, 0}, 1, 0, 0}, {7, 0, 0, 0, 0, 8, {4, 6, 0, 0, 0, 0}, 4, 5, 0}, {7, 0, 0, 0, 0, 9, {5, 6, 0, 0, 0, 0}, 4, 5, 0}, {7, 0, 0, 0, 0, 10, {4, 7, 0, 0, 0, 0}, 4, 5, 0}, {7, 0, 0, 0, 0, 11, {5, 7, 0, 0, 0, 0}, 4, 5, 0}, {3, 0, 0, 0, 0, 12, {0, 4, 0, 0, 0, 0}, 7, 0, 1}, {3, 0, 0, 0, 0, 13, {0, 5, 0, 0, 0, 0}, 7, 0, 1}, {3, 0, 0, 0, 0, 14, {1, 4, 0, 0, 0, 0}, 7, 0, 1}, {3, 0, 0, 0, 0, 15, {1, 5, 0, 0, 0, 0}, 7, 0, 1}, {3, 0, 0, 0, 0, 16, {0, 6, 0, 0, 0, 0}, 8, 0, 2}, {3, 0, 0, 0, 0, 17, {0, 7, 0, 0, 0, 0}, 8, 0, 2}, {3, 0, 0, 0, 0, 18, {1, 6, 0, 0, 0, 0}, 8, 0, 2}, {3, 0, 0, 0, 0, 19, {1, 7, 0, 0, 0, 0}, 8, 0, 2}};
-static __constant__ HsAmp kHsAmps2[3] = {{0, 0, {0, 1, 4, 0}, {0, 0, 0}}, {0, 1, {5, 1, 3, 0}, {0, 0, 0}}, {0, 2, {6, 1, 2, 0}, {0, 0, 0}}};  // grouped by type
-static __device__ const uint16_t kHsSlot2[7][16] = {{0, 0, 1, 1, 0, 0, 1, 1, 0, 0, 1, 1, 0, 0, 1, 1}, {2, 3, 2, 3, 2, 3, 2, 3, 2, 3, 2, 3, 2, 3, 2, 3}, {4, 4, 4, 4, 4, 4, 4, 4, 5, 5, 5, 5, 5, 5, 5, 5}, {6, 6, 6, 6, 7, 7, 7, 7, 6, 6, 6, 6, 7, 7, 7, 7}, {8, 8, 8, 8, 10, 10, 10, 10, 9, 9, 9, 9, 11, 11, 11, 11}, {12, 12, 14, 14, 12, 12, 14, 14, 13, 13, 15, 15, 13, 13, 15, 15}, {16, 16, 18, 18, 17, 17, 19, 19, 16, 16, 18, 18, 17, 17, 19, 19}};
+// helicity-shared program: 7 currents in 2 levels (20 variant slots), 3 amputated currents in 1 chunk(s) of <= 12 slots, 3 amplitudes; 4612 flops per event (all helicities)
+static __device__ const HsItem kHsItems2[32] = {{2, 0, -1, 1, 0, 0, {0, 0, 0, 0, 0, 0}, 0, 0, 0}, {2, 0, 1, 1, 0, 1, {0, 0, 0, 0, 0, 0}, 0, 0, 0}, {2, 1, -1, 1, 0, 2, {0, 0, 0, 0, 0, 0}, 1, 0, 0}, {2, 1, 1, 1, 0, 3, {0, 0, 0, 0, 0, 0}, 1, 0, 0}, {1, 2, -1, 1, 1, 4, {0, 0, 0, 0, 0, 0}, 2, 0, 0}, {1, 2, 1, 1, 1, 5, {0, 0, 0, 0, 0, 0}, 2, 0, 0}, {0, 3, -1, -1, 1, 6, {0, 0, 0, 0, 0, 0}, 3, 0, 0}, {0, 3, 1, -1, 1, 7, {0, 0, 0, 0, 0, 0}, 3, 0, 0}, {7, 0, 0, 0, 0, 8, {0, 2, 0, 0, 0, 0}, 4, 5, 0}, {7, 0, 0, 0, 0, 9, {1, 2, 0, 0, 0, 0}, 4, 5, 0}, {7, 0, 0, 0, 0, 10, {0, 3, 0, 0, 0, 0}, 4, 5, 0}, {7, 0, 0, 0, 0, 11, {1, 3, 0, 0, 0, 0}, 4, 5, 0}, {3, 0, 0, 0, 0, 12, {4, 0, 0, 0, 0, 0}, 7, 0, 1}, {3, 0, 0, 0, 0, 13, {4, 1, 0, 0, 0, 0}, 7, 0, 1}, {3, 0, 0, 0, 0, 14, {5, 0, 0, 0, 0, 0}, 7, 0, 1}, {3, 0, 0, 0, 0, 15, {5, 1, 0, 0, 0, 0}, 7, 0, 1}, {3, 0, 0, 0, 0, 16, {4, 2, 0, 0, 0, 0}, 8, 0, 2}, {3, 0, 0, 0, 0, 17, {4, 3, 0, 0, 0, 0}, 8, 0, 2}, {3, 0, 0, 0, 0, 18, {5, 2, 0, 0, 0, 0}, 8, 0, 2}, {3, 0, 0, 0, 0, 19, {5, 3, 0, 0, 0, 0}, 8, 0, 2}, {10, 0, 0, 0, 0, 0, {6, 0, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 1, {6, 1, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 2, {7, 0, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 3, {7, 1, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 4, {6, 2, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 5, {6, 3, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 6, {7, 2, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 7, {7, 3, 0, 0, 0, 0}, 0, 0, 0}, {11, 0, 0, 0, 0, 8, {4, 6, 0, 0, 0, 0}, 0, 0, 0}, {11, 0, 0, 0, 0, 9, {5, 6, 0, 0, 0, 0}, 0, 0, 0}, {11, 0, 0, 0, 0, 10, {4, 7, 0, 0, 0, 0}, 0, 0, 0}, {11, 0, 0, 0, 0, 11, {5, 7, 0, 0, 0, 0}, 0, 0, 0}};
+static __constant__ int kHsXItem2[2] = {20, 32};  // item ranges of the amputated chunks
 // colour-matrix numerators as the BF16 B operand of the tensor-core colour sum
 static __device__ __align__(16) const uint32_t kColourB2[128] = {0xc0004180, 0x00000000, 0x00000000, 0x00000000, 0x4180c000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000};
 struct Proc2 {
@@ -17,45 +16,44 @@ struct Proc2 {
   static constexpr int NDIAGRAMS = 3;
   static constexpr int NAMPS = 3;
   // helicity-shared program (tables above)
-  static constexpr int HS_NSLOT = 20;
-  static constexpr int HS_NITEM = 20;
+  static constexpr int HS_NSLOT = 20;   // current variant slots per event
+  static constexpr int HS_XCAP = 12;    // amputated-current slots per event and chunk
+  static constexpr int HS_NXCHUNK = 1;
+  static constexpr int HS_NITEM = 32;
   static constexpr int HS_NLEVEL = 2;
   static constexpr int HS_NAMP = 3;
   static constexpr int HS_NCUR = 7;
-  // operations: current variants per event, amplitudes + flow sums per helicity
-  static constexpr long HS_FLOPS_ITEMS = 2148;
-  static constexpr long HS_FLOPS_AMP_HEL = 296;
-  static __host__ __device__ constexpr int hs_level(int l) {
+  static constexpr int HS_NX = 3;
+  // operations: current variants per event, contractions + flow sums per helicity
+  static constexpr long HS_FLOPS_ITEMS = 3044;
+  static constexpr long HS_FLOPS_AMP_HEL = 98;
+  // item ranges of the current levels and of the amputated chunks; amplitude ranges of the chunks
+  static __host__ __device__ constexpr int hs_level(int i) {
     constexpr int t[3] = {0, 8, 20};
-    return t[l];
+    return t[i];
   }
+  static __device__ __forceinline__ int hs_xitem(int c) { return kHsXItem2[c]; }
   static __device__ __forceinline__ const HsItem* hs_items() { return kHsItems2; }
-  static __device__ __forceinline__ const HsAmp* hs_amps() { return kHsAmps2; }
-  static __device__ __forceinline__ const uint16_t* hs_slots() { return &kHsSlot2[0][0]; }
-  static constexpr int HS_NPAT = 3;
-  // colour-flow updates of each amplitude pattern: J_s += amp, -amp, i amp, -i amp
+  // A = sum_i X_i Y_i for the amplitudes of chunk c: X = xb[X slot + variant],
+  // Y = cur[Y slot + variant], variant of a leg set S for this helicity = vt[S * NHEL]
   template <class R>
-  static __device__ __forceinline__ void hs_flows(int pat, cx<R> amp, cx<R>* J) {
-    switch (pat) {
-      case 0: J[0] -= mul_i(amp); J[1] += mul_i(amp); break;
-      case 1: J[0] += amp; break;
-      case 2: J[1] += amp; break;
+  static __device__ __forceinline__ void hs_contract(int c, const W4<R>* __restrict__ cur, const W4<R>* __restrict__ xb, const uint8_t* __restrict__ vt, cx<R>* J) {
+    switch (c) {
+      case 0: {
+        {
+          const W4<R> X = xb[0 + vt[144]];
+          { const cx<R> a = dot4(X, cur[16 + vt[96]]); J[1] += a; }
+        }
+        {
+          const W4<R> X = xb[4 + vt[160]];
+          { const cx<R> a = dot4(X, cur[12 + vt[80]]); J[0] += a; }
+        }
+        {
+          const W4<R> X = xb[8 + vt[192]];
+          { const cx<R> a = dot4(X, cur[8 + vt[48]]); J[0] -= mul_i(a); J[1] += mul_i(a); }
+        }
+      } break;
       default: break;
-    }
-  }
-  // amplitudes of one (event, helicity): operands cur[sl[c * NHEL]], flows into J
-  template <class R>
-  static __device__ __forceinline__ void hs_amplitudes(const W4<R>* __restrict__ cur, const uint16_t* __restrict__ sl, const R* __restrict__ K, const Couplings<R>& cp, cx<R>* J) {
-    W4<R> o0, o1, o2, o3;
-    {  // type 0: 3 amplitudes
-      int l0 = -1, l1 = -1;
-      for (int d = 0; d < 3; ++d) {
-        const HsAmp a = kHsAmps2[d];
-        if (a.op[0] != l0) { o0 = cur[sl[a.op[0] * NHEL]]; l0 = a.op[0]; }
-        if (a.op[1] != l1) { o1 = cur[sl[a.op[1] * NHEL]]; l1 = a.op[1]; }
-        o2 = cur[sl[a.op[2] * NHEL]];
-        hs_flows<R>(a.pat, FFV1_0<R>(o0, o1, o2, cp.gs), J);
-      }
     }
   }
   static constexpr int NMOM = 9;

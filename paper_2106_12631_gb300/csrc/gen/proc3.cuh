@@ -4,10 +4,9 @@
 // colour-flow coefficients used: [(-1+0j), -1j, 1j, (1+0j)]
 #pragma once
 namespace mg {
-// helicity-shared program: 20 currents in 3 levels, 94 variant slots, 18 amplitudes, 71580 flops per event (all helicities)
-static __device__ const HsItem kHsItems3[94] = {{1, 2, -1, 1, 1, 0, {0, 0, 0, 0, 0, 0}, 2, 0, 0}, {1, 2, 1, 1, 1, 1, {0, 0, 0, 0, 0, 0}, 2, 0, 0}, {0, 3, -1, -1, 1, 2, {0, 0, 0, 0, 0, 0}, 3, 0, 0}, {0, 3, 1, -1, 1, 3, {0, 0, 0, 0, 0, 0}, 3, 0, 0}, {2, 0, -1, 1, 0, 4, {0, 0, 0, 0, 0, 0}, 0, 0, 0}, {2, 0, 1, 1, 0, 5, {0, 0, 0, 0, 0, 0}, 0, 0, 0}, {2, 1, -1, 1, 0, 6, {0, 0, 0, 0, 0, 0}, 1, 0, 0}, {2, 1, 1, 1, 0, 7, {0, 0, 0, 0, 0, 0}, 1, 0, 0}, {2, 4, -1, -1, 0, 8, {0, 0, 0, 0, 0, 0}, 4, 0, 0}, {2, 4, 1, -1, 0, 9, {0, 0, 0, 0, 0, 0}, 4, 0, 0}, {7, 0, 0, 0, 0, 10, {6, 8, 0, 0, 0, 0}, 6, 7, 1}, {7, 0, 0, 0, 0, 11, {7, 8, 0, 0, 0, 0}, 6, 7, 1}, {7, 0, 0, 0, 0, 12, {6, 9, 0, 0, 0, 0}, 6, 7, 1}, {7, 0, 0, 0, 0, 13, {7, 9, 0, 0, 0, 0}, 6, 7, 1}, {7, 0, 0, 0, 0, 14, {4, 6, 0, 0, 0, 0}, 9, 6, 6}, {7, 0, 0, 0, 0, 15, {5, 6, 0, 0, 0, 0}, 9, 6, 6}, {7, 0, 0, 0, 0, 16, {4, 7, 0, 0, 0, 0}, 9, 6, 6}, {7, 0, 0, 0, 0, 17, {5, 7, 0, 0, 0, 0}, 9, 6, 6}, {7, 0, 0, 0, 0, 18, {4, 8, 0, 0, 0, 0}, 9, 7, 8}, {7, 0, 0, 0, 0, 19, {5, 8, 0, 0, 0, 0}, 9, 7, 8}, {7, 0, 0, 0, 0, 20, {4, 9, 0, 0, 0, 0}, 9, 7, 8}, {7, 0, 0, 0, 0, 21, {5, 9, 0, 0, 0, 0}, 9, 7, 8}, {8, 0, 0, 0, 0, 22, {6, 4, 8, 4, 6, 8}, 0, 0, 0}, {8, 0, 0, 0, 0, 23, {6, 5, 8, 5, 6, 8}, 0, 0, 0}, {8, 0, 0, 0, 0, 24, {7, 4, 8, 4, 7, 8}, 0, 0, 0}, {8, 0, 0, 0, 0, 25, {7, 5, 8, 5, 7, 8}, 0, 0, 0}, {8, 0, 0, 0, 0, 26, {6, 4, 9, 4, 6, 9}, 0, 0, 0}, {8, 0, 0, 0, 0, 27, {6, 5, 9, 5, 6, 9}, 0, 0, 0}, {8, 0, 0, 0, 0, 28, {7, 4, 9, 4, 7, 9}, 0, 0, 0}, {8, 0, 0, 0, 0, 29, {7, 5, 9, 5, 7, 9}, 0, 0, 0}, {8, 0, 0, 0, 0, 30, {8, 4, 6, 4, 6, 8}, 0, 0, 0}, {8, 0, 0, 0, 0, 31, {8, 5, 6, 5, 6, 8}, 0, 0, 0}, {8, 0, 0, 0, 0, 32, {8, 4, 7, 4, 7, 8}, 0, 0, 0}, {8, 0, 0, 0, 0, 33, {8, 5, 7, 5, 7, 8}, 0, 0, 0}, {8, 0, 0, 0, 0, 34, {9, 4, 6, 4, 6, 9}, 0, 0, 0}, {8, 0, 0, 0, 0, 35, {9, 5, 6, 5, 6, 9}, 0, 0, 0}, {8, 0, 0, 0, 0, 36, {9, 4, 7, 4, 7, 9}, 0, 0, 0}, {8, 0, 0, 0, 0, 37, {9, 5, 7, 5, 7, 9}, 0, 0, 0}, {8, 0, 0, 0, 0, 38, {8, 4, 6, 6, 4, 8}, 0, 0, 0}, {8, 0, 0, 0, 0, 39, {8, 5, 6, 6, 5, 8}, 0, 0, 0}, {8, 0, 0, 0, 0, 40, {8, 4, 7, 7, 4, 8}, 0, 0, 0}, {8, 0, 0, 0, 0, 41, {8, 5, 7, 7, 5, 8}, 0, 0, 0}, {8, 0, 0, 0, 0, 42, {9, 4, 6, 6, 4, 9}, 0, 0, 0}, {8, 0, 0, 0, 0, 43, {9, 5, 6, 6, 5, 9}, 0, 0, 0}, {8, 0, 0, 0, 0, 44, {9, 4, 7, 7, 4, 9}, 0, 0, 0}, {8, 0, 0, 0, 0, 45, {9, 5, 7, 7, 5, 9}, 0, 0, 0}, {3, 0, 0, 0, 0, 46, {0, 4, 0, 0, 0, 0}, 10, 0, 2}, {3, 0, 0, 0, 0, 47, {0, 5, 0, 0, 0, 0}, 10, 0, 2}, {3, 0, 0, 0, 0, 48, {1, 4, 0, 0, 0, 0}, 10, 0, 2}, {3, 0, 0, 0, 0, 49, {1, 5, 0, 0, 0, 0}, 10, 0, 2}, {3, 0, 0, 0, 0, 50, {0, 6, 0, 0, 0, 0}, 17, 0, 9}, {3, 0, 0, 0, 0, 51, {0, 7, 0, 0, 0, 0}, 17, 0, 9}, {3, 0, 0, 0, 0, 52, {1, 6, 0, 0, 0, 0}, 17, 0, 9}, {3, 0, 0, 0, 0, 53, {1, 7, 0, 0, 0, 0}, 17, 0, 9}, {3, 0, 0, 0, 0, 54, {0, 8, 0, 0, 0, 0}, 15, 0, 7}, {3, 0, 0, 0, 0, 55, {1, 8, 0, 0, 0, 0}, 15, 0, 7}, {3, 0, 0, 0, 0, 56, {0, 9, 0, 0, 0, 0}, 15, 0, 7}, {3, 0, 0, 0, 0, 57, {1, 9, 0, 0, 0, 0}, 15, 0, 7}, {4, 0, 0, 0, 0, 58, {2, 8, 0, 0, 0, 0}, 18, 0, 4}, {4, 0, 0, 0, 0, 59, {3, 8, 0, 0, 0, 0}, 18, 0, 4}, {4, 0, 0, 0, 0, 60, {2, 9, 0, 0, 0, 0}, 18, 0, 4}, {4, 0, 0, 0, 0, 61, {3, 9, 0, 0, 0, 0}, 18, 0, 4}, {4, 0, 0, 0, 0, 62, {2, 6, 0, 0, 0, 0}, 19, 0, 5}, {4, 0, 0, 0, 0, 63, {2, 7, 0, 0, 0, 0}, 19, 0, 5}, {4, 0, 0, 0, 0, 64, {3, 6, 0, 0, 0, 0}, 19, 0, 5}, {4, 0, 0, 0, 0, 65, {3, 7, 0, 0, 0, 0}, 19, 0, 5}, {4, 0, 0, 0, 0, 66, {2, 4, 0, 0, 0, 0}, 20, 0, 3}, {4, 0, 0, 0, 0, 67, {2, 5, 0, 0, 0, 0}, 20, 0, 3}, {4, 0, 0, 0, 0, 68, {3, 4, 0, 0, 0, 0}, 20, 0, 3}, {4, 0, 0, 0, 0, 69, {3, 5, 0, 0, 0, 0}, 20, 0, 3}, {7, 0, 0, 0, 0, 70, {4, 10, 0, 0, 0, 0}, 9, 8, 0}, {7, 0, 0, 0, 0, 71, {5, 10, 0, 0, 0, 0}, 9, 8, 0}, {7, 0, 0, 0, 0, 72, {4, 11, 0, 0, 0, 0}, 9, 8, 0}, {7, 0, 0, 0, 0, 73, {5, 11, 0, 0, 0, 0}, 9, 8, 0}, {7, 0, 0, 0, 0, 74, {4, 12, 0, 0, 0, 0}, 9, 8, 0}, {7, 0, 0, 0, 0, 75, {5, 12, 0, 0, 0, 0}, 9, 8, 0}, {7, 0, 0, 0, 0, 76, {4, 13, 0, 0, 0, 0}, 9, 8, 0}, {7, 0, 0, 0, 0, 77, {5, 13, 0, 0, 0, 0}, 9, 8, 0}, {7, 0, 0, 0, 0, 78, {14, 8, 0, 0, 0, 0}, 14, 7, 0}, {7, 0, 0, 0, 0, 79, {15, 8, 0, 0, 0, 0}, 14, 7, 0}, {7, 0, 0, 0, 0, 80, {16, 8, 0, 0, 0, 0}, 14, 7, 0}, {7, 0, 0, 0, 0, 81, {17, 8, 0, 0, 0, 0}, 14, 7, 0}, {7, 0, 0, 0, 0, 82, {14, 9, 0, 0, 0, 0}, 14, 7, 0}, {7, 0, 0, 0, 0, 83, {15, 9, 0, 0, 0, 0}, 14, 7, 0}, {7, 0, 0, 0, 0, 84, {16, 9, 0, 0, 0, 0}, 14, 7, 0}, {7, 0, 0, 0, 0, 85, {17, 9, 0, 0, 0, 0}, 14, 7, 0}, {7, 0, 0, 0, 0, 86, {18, 6, 0, 0, 0, 0}, 16, 6, 0}, {7, 0, 0, 0, 0, 87, {19, 6, 0, 0, 0, 0}, 16, 6, 0}, {7, 0, 0, 0, 0, 88, {18, 7, 0, 0, 0, 0}, 16, 6, 0}, {7, 0, 0, 0, 0, 89, {19, 7, 0, 0, 0, 0}, 16, 6, 0}, {7, 0, 0, 0, 0, 90, {20, 6, 0, 0, 0, 0}, 16, 6, 0}, {7, 0, 0, 0, 0, 91, {21, 6, 0, 0, 0, 0}, 16, 6, 0}, {7, 0, 0, 0, 0, 92, {20, 7, 0, 0, 0, 0}, 16, 6, 0}, {7, 0, 0, 0, 0, 93, {21, 7, 0, 0, 0, 0}, 16, 6, 0}};
-static __constant__ HsAmp kHsAmps3[18] = {{0, 0, {0, 1, 8, 0}, {0, 0, 0}}, {0, 1, {0, 1, 9, 0}, {0, 0, 0}}, {0, 2, {0, 1, 10, 0}, {0, 0, 0}}, {0, 3, {0, 1, 17, 0}, {0, 0, 0}}, {0, 0, {0, 1, 18, 0}, {0, 0, 0}}, {0, 1, {0, 1, 19, 0}, {0, 0, 0}}, {0, 4, {0, 14, 6, 0}, {0, 0, 0}}, {0, 5, {0, 15, 7, 0}, {0, 0, 0}}, {0, 6, {0, 16, 5, 0}, {0, 0, 0}}, {0, 7, {11, 1, 5, 0}, {0, 0, 0}}, {0, 8, {11, 14, 3, 0}, {0, 0, 0}}, {0, 9, {11, 15, 4, 0}, {0, 0, 0}}, {0, 10, {12, 1, 7, 0}, {0, 0, 0}}, {0, 11, {12, 14, 2, 0}, {0, 0, 0}}, {0, 12, {12, 16, 4, 0}, {0, 0, 0}}, {0, 13, {13, 1, 6, 0}, {0, 0, 0}}, {0, 14, {13, 15, 2, 0}, {0, 0, 0}}, {0, 15, {13, 16, 3, 0}, {0, 0, 0}}};  // grouped by type
-static __device__ const uint16_t kHsSlot3[20][32] = {{0, 0, 0, 0, 1, 1, 1, 1, 0, 0, 0, 0, 1, 1, 1, 1, 0, 0, 0, 0, 1, 1, 1, 1, 0, 0, 0, 0, 1, 1, 1, 1}, {2, 2, 3, 3, 2, 2, 3, 3, 2, 2, 3, 3, 2, 2, 3, 3, 2, 2, 3, 3, 2, 2, 3, 3, 2, 2, 3, 3, 2, 2, 3, 3}, {4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5}, {6, 6, 6, 6, 6, 6, 6, 6, 7, 7, 7, 7, 7, 7, 7, 7, 6, 6, 6, 6, 6, 6, 6, 6, 7, 7, 7, 7, 7, 7, 7, 7}, {8, 9, 8, 9, 8, 9, 8, 9, 8, 9, 8, 9, 8, 9, 8, 9, 8, 9, 8, 9, 8, 9, 8, 9, 8, 9, 8, 9, 8, 9, 8, 9}, {10, 12, 10, 12, 10, 12, 10, 12, 11, 13, 11, 13, 11, 13, 11, 13, 10, 12, 10, 12, 10, 12, 10, 12, 11, 13, 11, 13, 11, 13, 11, 13}, {14, 14, 14, 14, 14, 14, 14, 14, 16, 16, 16, 16, 16, 16, 16, 16, 15, 15, 15, 15, 15, 15, 15, 15, 17, 17, 17, 17, 17, 17, 17, 17}, {18, 20, 18, 20, 18, 20, 18, 20, 18, 20, 18, 20, 18, 20, 18, 20, 19, 21, 19, 21, 19, 21, 19, 21, 19, 21, 19, 21, 19, 21, 19, 21}, {22, 26, 22, 26, 22, 26, 22, 26, 24, 28, 24, 28, 24, 28, 24, 28, 23, 27, 23, 27, 23, 27, 23, 27, 25, 29, 25, 29, 25, 29, 25, 29}, {30, 34, 30, 34, 30, 34, 30, 34, 32, 36, 32, 36, 32, 36, 32, 36, 31, 35, 31, 35, 31, 35, 31, 35, 33, 37, 33, 37, 33, 37, 33, 37}, {38, 42, 38, 42, 38, 42, 38, 42, 40, 44, 40, 44, 40, 44, 40, 44, 39, 43, 39, 43, 39, 43, 39, 43, 41, 45, 41, 45, 41, 45, 41, 45}, {46, 46, 46, 46, 48, 48, 48, 48, 46, 46, 46, 46, 48, 48, 48, 48, 47, 47, 47, 47, 49, 49, 49, 49, 47, 47, 47, 47, 49, 49, 49, 49}, {50, 50, 50, 50, 52, 52, 52, 52, 51, 51, 51, 51, 53, 53, 53, 53, 50, 50, 50, 50, 52, 52, 52, 52, 51, 51, 51, 51, 53, 53, 53, 53}, {54, 56, 54, 56, 55, 57, 55, 57, 54, 56, 54, 56, 55, 57, 55, 57, 54, 56, 54, 56, 55, 57, 55, 57, 54, 56, 54, 56, 55, 57, 55, 57}, {58, 60, 59, 61, 58, 60, 59, 61, 58, 60, 59, 61, 58, 60, 59, 61, 58, 60, 59, 61, 58, 60, 59, 61, 58, 60, 59, 61, 58, 60, 59, 61}, {62, 62, 64, 64, 62, 62, 64, 64, 63, 63, 65, 65, 63, 63, 65, 65, 62, 62, 64, 64, 62, 62, 64, 64, 63, 63, 65, 65, 63, 63, 65, 65}, {66, 66, 68, 68, 66, 66, 68, 68, 66, 66, 68, 68, 66, 66, 68, 68, 67, 67, 69, 69, 67, 67, 69, 69, 67, 67, 69, 69, 67, 67, 69, 69}, {70, 74, 70, 74, 70, 74, 70, 74, 72, 76, 72, 76, 72, 76, 72, 76, 71, 75, 71, 75, 71, 75, 71, 75, 73, 77, 73, 77, 73, 77, 73, 77}, {78, 82, 78, 82, 78, 82, 78, 82, 80, 84, 80, 84, 80, 84, 80, 84, 79, 83, 79, 83, 79, 83, 79, 83, 81, 85, 81, 85, 81, 85, 81, 85}, {86, 90, 86, 90, 86, 90, 86, 90, 88, 92, 88, 92, 88, 92, 88, 92, 87, 91, 87, 91, 87, 91, 87, 91, 89, 93, 89, 93, 89, 93, 89, 93}};
+// helicity-shared program: 20 currents in 3 levels (94 variant slots), 13 amputated currents in 1 chunk(s) of <= 100 slots, 18 amplitudes; 40796 flops per event (all helicities)
+static __device__ const HsItem kHsItems3[194] = {{2, 0, -1, 1, 0, 0, {0, 0, 0, 0, 0, 0}, 0, 0, 0}, {2, 0, 1, 1, 0, 1, {0, 0, 0, 0, 0, 0}, 0, 0, 0}, {2, 1, -1, 1, 0, 2, {0, 0, 0, 0, 0, 0}, 1, 0, 0}, {2, 1, 1, 1, 0, 3, {0, 0, 0, 0, 0, 0}, 1, 0, 0}, {1, 2, -1, 1, 1, 4, {0, 0, 0, 0, 0, 0}, 2, 0, 0}, {1, 2, 1, 1, 1, 5, {0, 0, 0, 0, 0, 0}, 2, 0, 0}, {0, 3, -1, -1, 1, 6, {0, 0, 0, 0, 0, 0}, 3, 0, 0}, {0, 3, 1, -1, 1, 7, {0, 0, 0, 0, 0, 0}, 3, 0, 0}, {2, 4, -1, -1, 0, 8, {0, 0, 0, 0, 0, 0}, 4, 0, 0}, {2, 4, 1, -1, 0, 9, {0, 0, 0, 0, 0, 0}, 4, 0, 0}, {4, 0, 0, 0, 0, 10, {6, 0, 0, 0, 0, 0}, 18, 0, 3}, {4, 0, 0, 0, 0, 11, {6, 1, 0, 0, 0, 0}, 18, 0, 3}, {4, 0, 0, 0, 0, 12, {7, 0, 0, 0, 0, 0}, 18, 0, 3}, {4, 0, 0, 0, 0, 13, {7, 1, 0, 0, 0, 0}, 18, 0, 3}, {4, 0, 0, 0, 0, 14, {6, 2, 0, 0, 0, 0}, 19, 0, 5}, {4, 0, 0, 0, 0, 15, {6, 3, 0, 0, 0, 0}, 19, 0, 5}, {4, 0, 0, 0, 0, 16, {7, 2, 0, 0, 0, 0}, 19, 0, 5}, {4, 0, 0, 0, 0, 17, {7, 3, 0, 0, 0, 0}, 19, 0, 5}, {4, 0, 0, 0, 0, 18, {6, 8, 0, 0, 0, 0}, 20, 0, 4}, {4, 0, 0, 0, 0, 19, {7, 8, 0, 0, 0, 0}, 20, 0, 4}, {4, 0, 0, 0, 0, 20, {6, 9, 0, 0, 0, 0}, 20, 0, 4}, {4, 0, 0, 0, 0, 21, {7, 9, 0, 0, 0, 0}, 20, 0, 4}, {7, 0, 0, 0, 0, 22, {0, 2, 0, 0, 0, 0}, 9, 6, 6}, {7, 0, 0, 0, 0, 23, {1, 2, 0, 0, 0, 0}, 9, 6, 6}, {7, 0, 0, 0, 0, 24, {0, 3, 0, 0, 0, 0}, 9, 6, 6}, {7, 0, 0, 0, 0, 25, {1, 3, 0, 0, 0, 0}, 9, 6, 6}, {7, 0, 0, 0, 0, 26, {0, 8, 0, 0, 0, 0}, 9, 7, 8}, {7, 0, 0, 0, 0, 27, {1, 8, 0, 0, 0, 0}, 9, 7, 8}, {7, 0, 0, 0, 0, 28, {0, 9, 0, 0, 0, 0}, 9, 7, 8}, {7, 0, 0, 0, 0, 29, {1, 9, 0, 0, 0, 0}, 9, 7, 8}, {7, 0, 0, 0, 0, 30, {2, 8, 0, 0, 0, 0}, 6, 7, 1}, {7, 0, 0, 0, 0, 31, {3, 8, 0, 0, 0, 0}, 6, 7, 1}, {7, 0, 0, 0, 0, 32, {2, 9, 0, 0, 0, 0}, 6, 7, 1}, {7, 0, 0, 0, 0, 33, {3, 9, 0, 0, 0, 0}, 6, 7, 1}, {8, 0, 0, 0, 0, 34, {2, 0, 8, 0, 2, 8}, 0, 0, 0}, {8, 0, 0, 0, 0, 35, {2, 1, 8, 1, 2, 8}, 0, 0, 0}, {8, 0, 0, 0, 0, 36, {3, 0, 8, 0, 3, 8}, 0, 0, 0}, {8, 0, 0, 0, 0, 37, {3, 1, 8, 1, 3, 8}, 0, 0, 0}, {8, 0, 0, 0, 0, 38, {2, 0, 9, 0, 2, 9}, 0, 0, 0}, {8, 0, 0, 0, 0, 39, {2, 1, 9, 1, 2, 9}, 0, 0, 0}, {8, 0, 0, 0, 0, 40, {3, 0, 9, 0, 3, 9}, 0, 0, 0}, {8, 0, 0, 0, 0, 41, {3, 1, 9, 1, 3, 9}, 0, 0, 0}, {8, 0, 0, 0, 0, 42, {8, 0, 2, 0, 2, 8}, 0, 0, 0}, {8, 0, 0, 0, 0, 43, {8, 1, 2, 1, 2, 8}, 0, 0, 0}, {8, 0, 0, 0, 0, 44, {8, 0, 3, 0, 3, 8}, 0, 0, 0}, {8, 0, 0, 0, 0, 45, {8, 1, 3, 1, 3, 8}, 0, 0, 0}, {8, 0, 0, 0, 0, 46, {9, 0, 2, 0, 2, 9}, 0, 0, 0}, {8, 0, 0, 0, 0, 47, {9, 1, 2, 1, 2, 9}, 0, 0, 0}, {8, 0, 0, 0, 0, 48, {9, 0, 3, 0, 3, 9}, 0, 0, 0}, {8, 0, 0, 0, 0, 49, {9, 1, 3, 1, 3, 9}, 0, 0, 0}, {8, 0, 0, 0, 0, 50, {8, 0, 2, 2, 0, 8}, 0, 0, 0}, {8, 0, 0, 0, 0, 51, {8, 1, 2, 2, 1, 8}, 0, 0, 0}, {8, 0, 0, 0, 0, 52, {8, 0, 3, 3, 0, 8}, 0, 0, 0}, {8, 0, 0, 0, 0, 53, {8, 1, 3, 3, 1, 8}, 0, 0, 0}, {8, 0, 0, 0, 0, 54, {9, 0, 2, 2, 0, 9}, 0, 0, 0}, {8, 0, 0, 0, 0, 55, {9, 1, 2, 2, 1, 9}, 0, 0, 0}, {8, 0, 0, 0, 0, 56, {9, 0, 3, 3, 0, 9}, 0, 0, 0}, {8, 0, 0, 0, 0, 57, {9, 1, 3, 3, 1, 9}, 0, 0, 0}, {3, 0, 0, 0, 0, 58, {4, 0, 0, 0, 0, 0}, 10, 0, 2}, {3, 0, 0, 0, 0, 59, {4, 1, 0, 0, 0, 0}, 10, 0, 2}, {3, 0, 0, 0, 0, 60, {5, 0, 0, 0, 0, 0}, 10, 0, 2}, {3, 0, 0, 0, 0, 61, {5, 1, 0, 0, 0, 0}, 10, 0, 2}, {3, 0, 0, 0, 0, 62, {4, 2, 0, 0, 0, 0}, 17, 0, 9}, {3, 0, 0, 0, 0, 63, {4, 3, 0, 0, 0, 0}, 17, 0, 9}, {3, 0, 0, 0, 0, 64, {5, 2, 0, 0, 0, 0}, 17, 0, 9}, {3, 0, 0, 0, 0, 65, {5, 3, 0, 0, 0, 0}, 17, 0, 9}, {3, 0, 0, 0, 0, 66, {4, 8, 0, 0, 0, 0}, 15, 0, 7}, {3, 0, 0, 0, 0, 67, {5, 8, 0, 0, 0, 0}, 15, 0, 7}, {3, 0, 0, 0, 0, 68, {4, 9, 0, 0, 0, 0}, 15, 0, 7}, {3, 0, 0, 0, 0, 69, {5, 9, 0, 0, 0, 0}, 15, 0, 7}, {7, 0, 0, 0, 0, 70, {0, 30, 0, 0, 0, 0}, 9, 8, 0}, {7, 0, 0, 0, 0, 71, {1, 30, 0, 0, 0, 0}, 9, 8, 0}, {7, 0, 0, 0, 0, 72, {0, 31, 0, 0, 0, 0}, 9, 8, 0}, {7, 0, 0, 0, 0, 73, {1, 31, 0, 0, 0, 0}, 9, 8, 0}, {7, 0, 0, 0, 0, 74, {0, 32, 0, 0, 0, 0}, 9, 8, 0}, {7, 0, 0, 0, 0, 75, {1, 32, 0, 0, 0, 0}, 9, 8, 0}, {7, 0, 0, 0, 0, 76, {0, 33, 0, 0, 0, 0}, 9, 8, 0}, {7, 0, 0, 0, 0, 77, {1, 33, 0, 0, 0, 0}, 9, 8, 0}, {7, 0, 0, 0, 0, 78, {22, 8, 0, 0, 0, 0}, 14, 7, 0}, {7, 0, 0, 0, 0, 79, {23, 8, 0, 0, 0, 0}, 14, 7, 0}, {7, 0, 0, 0, 0, 80, {24, 8, 0, 0, 0, 0}, 14, 7, 0}, {7, 0, 0, 0, 0, 81, {25, 8, 0, 0, 0, 0}, 14, 7, 0}, {7, 0, 0, 0, 0, 82, {22, 9, 0, 0, 0, 0}, 14, 7, 0}, {7, 0, 0, 0, 0, 83, {23, 9, 0, 0, 0, 0}, 14, 7, 0}, {7, 0, 0, 0, 0, 84, {24, 9, 0, 0, 0, 0}, 14, 7, 0}, {7, 0, 0, 0, 0, 85, {25, 9, 0, 0, 0, 0}, 14, 7, 0}, {7, 0, 0, 0, 0, 86, {26, 2, 0, 0, 0, 0}, 16, 6, 0}, {7, 0, 0, 0, 0, 87, {27, 2, 0, 0, 0, 0}, 16, 6, 0}, {7, 0, 0, 0, 0, 88, {26, 3, 0, 0, 0, 0}, 16, 6, 0}, {7, 0, 0, 0, 0, 89, {27, 3, 0, 0, 0, 0}, 16, 6, 0}, {7, 0, 0, 0, 0, 90, {28, 2, 0, 0, 0, 0}, 16, 6, 0}, {7, 0, 0, 0, 0, 91, {29, 2, 0, 0, 0, 0}, 16, 6, 0}, {7, 0, 0, 0, 0, 92, {28, 3, 0, 0, 0, 0}, 16, 6, 0}, {7, 0, 0, 0, 0, 93, {29, 3, 0, 0, 0, 0}, 16, 6, 0}, {10, 0, 0, 0, 0, 0, {14, 0, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 1, {14, 1, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 2, {15, 0, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 3, {15, 1, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 4, {16, 0, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 5, {16, 1, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 6, {17, 0, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 7, {17, 1, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 8, {10, 2, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 9, {11, 2, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 10, {10, 3, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 11, {11, 3, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 12, {12, 2, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 13, {13, 2, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 14, {12, 3, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 15, {13, 3, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 16, {6, 22, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 17, {6, 23, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 18, {6, 24, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 19, {6, 25, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 20, {7, 22, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 21, {7, 23, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 22, {7, 24, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 23, {7, 25, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 24, {18, 0, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 25, {18, 1, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 26, {19, 0, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 27, {19, 1, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 28, {20, 0, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 29, {20, 1, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 30, {21, 0, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 31, {21, 1, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 32, {6, 26, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 33, {6, 27, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 34, {7, 26, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 35, {7, 27, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 36, {6, 28, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 37, {6, 29, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 38, {7, 28, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 39, {7, 29, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 40, {10, 8, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 41, {11, 8, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 42, {12, 8, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 43, {13, 8, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 44, {10, 9, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 45, {11, 9, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 46, {12, 9, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 47, {13, 9, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 48, {18, 2, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 49, {18, 3, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 50, {19, 2, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 51, {19, 3, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 52, {20, 2, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 53, {20, 3, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 54, {21, 2, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 55, {21, 3, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 56, {14, 8, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 57, {15, 8, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 58, {16, 8, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 59, {17, 8, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 60, {14, 9, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 61, {15, 9, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 62, {16, 9, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 63, {17, 9, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 64, {6, 30, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 65, {6, 31, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 66, {7, 30, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 67, {7, 31, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 68, {6, 32, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 69, {6, 33, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 70, {7, 32, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 71, {7, 33, 0, 0, 0, 0}, 0, 0, 0}, {11, 0, 0, 0, 0, 72, {4, 6, 0, 0, 0, 0}, 0, 0, 0}, {11, 0, 0, 0, 0, 73, {5, 6, 0, 0, 0, 0}, 0, 0, 0}, {11, 0, 0, 0, 0, 74, {4, 7, 0, 0, 0, 0}, 0, 0, 0}, {11, 0, 0, 0, 0, 75, {5, 7, 0, 0, 0, 0}, 0, 0, 0}, {9, 0, 0, 0, 0, 76, {4, 22, 0, 0, 0, 0}, 0, 0, 0}, {9, 0, 0, 0, 0, 77, {4, 23, 0, 0, 0, 0}, 0, 0, 0}, {9, 0, 0, 0, 0, 78, {4, 24, 0, 0, 0, 0}, 0, 0, 0}, {9, 0, 0, 0, 0, 79, {4, 25, 0, 0, 0, 0}, 0, 0, 0}, {9, 0, 0, 0, 0, 80, {5, 22, 0, 0, 0, 0}, 0, 0, 0}, {9, 0, 0, 0, 0, 81, {5, 23, 0, 0, 0, 0}, 0, 0, 0}, {9, 0, 0, 0, 0, 82, {5, 24, 0, 0, 0, 0}, 0, 0, 0}, {9, 0, 0, 0, 0, 83, {5, 25, 0, 0, 0, 0}, 0, 0, 0}, {9, 0, 0, 0, 0, 84, {4, 26, 0, 0, 0, 0}, 0, 0, 0}, {9, 0, 0, 0, 0, 85, {4, 27, 0, 0, 0, 0}, 0, 0, 0}, {9, 0, 0, 0, 0, 86, {5, 26, 0, 0, 0, 0}, 0, 0, 0}, {9, 0, 0, 0, 0, 87, {5, 27, 0, 0, 0, 0}, 0, 0, 0}, {9, 0, 0, 0, 0, 88, {4, 28, 0, 0, 0, 0}, 0, 0, 0}, {9, 0, 0, 0, 0, 89, {4, 29, 0, 0, 0, 0}, 0, 0, 0}, {9, 0, 0, 0, 0, 90, {5, 28, 0, 0, 0, 0}, 0, 0, 0}, {9, 0, 0, 0, 0, 91, {5, 29, 0, 0, 0, 0}, 0, 0, 0}, {9, 0, 0, 0, 0, 92, {4, 30, 0, 0, 0, 0}, 0, 0, 0}, {9, 0, 0, 0, 0, 93, {4, 31, 0, 0, 0, 0}, 0, 0, 0}, {9, 0, 0, 0, 0, 94, {5, 30, 0, 0, 0, 0}, 0, 0, 0}, {9, 0, 0, 0, 0, 95, {5, 31, 0, 0, 0, 0}, 0, 0, 0}, {9, 0, 0, 0, 0, 96, {4, 32, 0, 0, 0, 0}, 0, 0, 0}, {9, 0, 0, 0, 0, 97, {4, 33, 0, 0, 0, 0}, 0, 0, 0}, {9, 0, 0, 0, 0, 98, {5, 32, 0, 0, 0, 0}, 0, 0, 0}, {9, 0, 0, 0, 0, 99, {5, 33, 0, 0, 0, 0}, 0, 0, 0}};
+static __constant__ int kHsXItem3[2] = {94, 194};  // item ranges of the amputated chunks
 // colour-matrix numerators as the BF16 B operand of the tensor-core colour sum
 static __device__ __align__(16) const uint32_t kColourB3[128] = {0xc1004280, 0x3f80c100, 0x41203f80, 0x00000000, 0x4280c100, 0x41203f80, 0x3f80c100, 0x00000000, 0x3f80c100, 0xc1004280, 0x3f804120, 0x00000000, 0x41203f80, 0x4280c100, 0xc1003f80, 0x00000000, 0xc1003f80, 0x3f804120, 0xc1004280, 0x00000000, 0x3f804120, 0xc1003f80, 0x4280c100, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000, 0x00000000};
 struct Proc3 {
@@ -17,58 +16,89 @@ struct Proc3 {
   static constexpr int NDIAGRAMS = 16;
   static constexpr int NAMPS = 18;
   // helicity-shared program (tables above)
-  static constexpr int HS_NSLOT = 94;
-  static constexpr int HS_NITEM = 94;
+  static constexpr int HS_NSLOT = 94;   // current variant slots per event
+  static constexpr int HS_XCAP = 100;    // amputated-current slots per event and chunk
+  static constexpr int HS_NXCHUNK = 1;
+  static constexpr int HS_NITEM = 194;
   static constexpr int HS_NLEVEL = 3;
   static constexpr int HS_NAMP = 18;
   static constexpr int HS_NCUR = 20;
-  // operations: current variants per event, amplitudes + flow sums per helicity
-  static constexpr long HS_FLOPS_ITEMS = 13596;
-  static constexpr long HS_FLOPS_AMP_HEL = 1812;
-  static __host__ __device__ constexpr int hs_level(int l) {
+  static constexpr int HS_NX = 13;
+  // operations: current variants per event, contractions + flow sums per helicity
+  static constexpr long HS_FLOPS_ITEMS = 20828;
+  static constexpr long HS_FLOPS_AMP_HEL = 624;
+  // item ranges of the current levels and of the amputated chunks; amplitude ranges of the chunks
+  static __host__ __device__ constexpr int hs_level(int i) {
     constexpr int t[4] = {0, 10, 70, 94};
-    return t[l];
+    return t[i];
   }
+  static __device__ __forceinline__ int hs_xitem(int c) { return kHsXItem3[c]; }
   static __device__ __forceinline__ const HsItem* hs_items() { return kHsItems3; }
-  static __device__ __forceinline__ const HsAmp* hs_amps() { return kHsAmps3; }
-  static __device__ __forceinline__ const uint16_t* hs_slots() { return &kHsSlot3[0][0]; }
-  static constexpr int HS_NPAT = 16;
-  // colour-flow updates of each amplitude pattern: J_s += amp, -amp, i amp, -i amp
+  // A = sum_i X_i Y_i for the amplitudes of chunk c: X = xb[X slot + variant],
+  // Y = cur[Y slot + variant], variant of a leg set S for this helicity = vt[S * NHEL]
   template <class R>
-  static __device__ __forceinline__ void hs_flows(int pat, cx<R> amp, cx<R>* J) {
-    switch (pat) {
-      case 0: J[0] -= amp; J[2] += amp; J[4] += amp; J[5] -= amp; break;
-      case 1: J[1] -= amp; J[2] += amp; J[3] -= amp; J[4] += amp; break;
-      case 2: J[0] += amp; J[1] -= amp; J[3] -= amp; J[5] += amp; break;
-      case 3: J[0] -= amp; J[1] += amp; J[3] += amp; J[5] -= amp; break;
-      case 4: J[0] -= mul_i(amp); J[2] += mul_i(amp); break;
-      case 5: J[1] -= mul_i(amp); J[4] += mul_i(amp); break;
-      case 6: J[3] -= mul_i(amp); J[5] += mul_i(amp); break;
-      case 7: J[0] -= mul_i(amp); J[1] += mul_i(amp); break;
-      case 8: J[0] += amp; break;
-      case 9: J[1] += amp; break;
-      case 10: J[2] -= mul_i(amp); J[3] += mul_i(amp); break;
-      case 11: J[2] += amp; break;
-      case 12: J[3] += amp; break;
-      case 13: J[4] -= mul_i(amp); J[5] += mul_i(amp); break;
-      case 14: J[4] += amp; break;
-      case 15: J[5] += amp; break;
+  static __device__ __forceinline__ void hs_contract(int c, const W4<R>* __restrict__ cur, const W4<R>* __restrict__ xb, const uint8_t* __restrict__ vt, cx<R>* J) {
+    switch (c) {
+      case 0: {
+        {
+          const W4<R> X = xb[0 + vt[352]];
+          { const cx<R> a = dot4(X, cur[66 + vt[640]]); J[4] += a; }
+        }
+        {
+          const W4<R> X = xb[8 + vt[352]];
+          { const cx<R> a = dot4(X, cur[66 + vt[640]]); J[5] += a; }
+        }
+        {
+          const W4<R> X = xb[16 + vt[352]];
+          { const cx<R> a = dot4(X, cur[66 + vt[640]]); J[4] -= mul_i(a); J[5] += mul_i(a); }
+        }
+        {
+          const W4<R> X = xb[24 + vt[800]];
+          { const cx<R> a = dot4(X, cur[62 + vt[192]]); J[2] += a; }
+        }
+        {
+          const W4<R> X = xb[32 + vt[800]];
+          { const cx<R> a = dot4(X, cur[62 + vt[192]]); J[2] -= mul_i(a); J[3] += mul_i(a); }
+        }
+        {
+          const W4<R> X = xb[40 + vt[800]];
+          { const cx<R> a = dot4(X, cur[62 + vt[192]]); J[3] += a; }
+        }
+        {
+          const W4<R> X = xb[48 + vt[832]];
+          { const cx<R> a = dot4(X, cur[58 + vt[160]]); J[0] += a; }
+        }
+        {
+          const W4<R> X = xb[56 + vt[832]];
+          { const cx<R> a = dot4(X, cur[58 + vt[160]]); J[1] += a; }
+        }
+        {
+          const W4<R> X = xb[64 + vt[832]];
+          { const cx<R> a = dot4(X, cur[58 + vt[160]]); J[0] -= mul_i(a); J[1] += mul_i(a); }
+        }
+        {
+          const W4<R> X = xb[72 + vt[384]];
+          { const cx<R> a = dot4(X, cur[34 + vt[608]]); J[0] -= a; J[2] += a; J[4] += a; J[5] -= a; }
+          { const cx<R> a = dot4(X, cur[42 + vt[608]]); J[1] -= a; J[2] += a; J[3] -= a; J[4] += a; }
+          { const cx<R> a = dot4(X, cur[50 + vt[608]]); J[0] += a; J[1] -= a; J[3] -= a; J[5] += a; }
+          { const cx<R> a = dot4(X, cur[70 + vt[608]]); J[0] -= a; J[1] += a; J[3] += a; J[5] -= a; }
+          { const cx<R> a = dot4(X, cur[78 + vt[608]]); J[0] -= a; J[2] += a; J[4] += a; J[5] -= a; }
+          { const cx<R> a = dot4(X, cur[86 + vt[608]]); J[1] -= a; J[2] += a; J[3] -= a; J[4] += a; }
+        }
+        {
+          const W4<R> X = xb[76 + vt[224]];
+          { const cx<R> a = dot4(X, cur[18 + vt[768]]); J[0] -= mul_i(a); J[2] += mul_i(a); }
+        }
+        {
+          const W4<R> X = xb[84 + vt[672]];
+          { const cx<R> a = dot4(X, cur[14 + vt[320]]); J[1] -= mul_i(a); J[4] += mul_i(a); }
+        }
+        {
+          const W4<R> X = xb[92 + vt[704]];
+          { const cx<R> a = dot4(X, cur[10 + vt[288]]); J[3] -= mul_i(a); J[5] += mul_i(a); }
+        }
+      } break;
       default: break;
-    }
-  }
-  // amplitudes of one (event, helicity): operands cur[sl[c * NHEL]], flows into J
-  template <class R>
-  static __device__ __forceinline__ void hs_amplitudes(const W4<R>* __restrict__ cur, const uint16_t* __restrict__ sl, const R* __restrict__ K, const Couplings<R>& cp, cx<R>* J) {
-    W4<R> o0, o1, o2, o3;
-    {  // type 0: 18 amplitudes
-      int l0 = -1, l1 = -1;
-      for (int d = 0; d < 18; ++d) {
-        const HsAmp a = kHsAmps3[d];
-        if (a.op[0] != l0) { o0 = cur[sl[a.op[0] * NHEL]]; l0 = a.op[0]; }
-        if (a.op[1] != l1) { o1 = cur[sl[a.op[1] * NHEL]]; l1 = a.op[1]; }
-        o2 = cur[sl[a.op[2] * NHEL]];
-        hs_flows<R>(a.pat, FFV1_0<R>(o0, o1, o2, cp.gs), J);
-      }
     }
   }
   static constexpr int NMOM = 21;
@@ -80,7 +110,7 @@ struct Proc3 {
   static constexpr double NORM = 1.0 / 256.0;  // 1/(helicity avg x colour avg x symmetry)
   // momentum table: {0 physical / 1 all-outgoing sum, leg mask, mask of legs entering as -p}
   static __host__ __device__ constexpr int mom(int j, int k) {
-    constexpr int t[NMOM][3] = {{0, 1, 0}, {0, 2, 0}, {0, 4, 0}, {0, 8, 0}, {0, 16, 0}, {1, 19, 3}, {1, 2, 2}, {1, 16, 0}, {1, 18, 2}, {1, 1, 1}, {1, 5, 1}, {1, 22, 2}, {1, 7, 3}, {1, 21, 1}, {1, 3, 3}, {1, 20, 0}, {1, 17, 1}, {1, 6, 2}, {1, 7, 4}, {1, 21, 20}, {1, 22, 20}};
+    constexpr int t[NMOM][3] = {{0, 1, 0}, {0, 2, 0}, {0, 4, 0}, {0, 8, 0}, {0, 16, 0}, {1, 19, 3}, {1, 2, 2}, {1, 16, 0}, {1, 18, 2}, {1, 1, 1}, {1, 5, 1}, {1, 22, 2}, {1, 7, 3}, {1, 21, 1}, {1, 3, 3}, {1, 20, 0}, {1, 17, 1}, {1, 6, 2}, {1, 22, 20}, {1, 21, 20}, {1, 7, 4}};
     return t[j][k];
   }
   // propagators: {momentum entry, 0 gluon / 1 top / 2 photon / 3 Z}

@@ -296,4 +296,83 @@ __device__ __forceinline__ W4<R> VVVV4P0_1(const W4<R>& a1, const W4<R>& a2, con
   return vvvv_comb(a3, vdot(a1, a2), a2, vdot(a1, a3), mul_mi(g2 * prop));
 }
 
+// ---- amputated currents ------------------------------------------------------
+// The vertex of an amplitude with one operand Y left out and no propagator, so
+// that the amplitude is the plain contraction sum_i X_i Y_i (dot4).  Spinors:
+// the row / column spinor of the vertex; vectors: LOWER index (metric applied).
+// i g row . V/   (pairs with a column spinor)
+template <class R>
+__device__ __forceinline__ W4<R> FFV1_2A(const W4<R>& fo, const W4<R>& v, R g) {
+  W4<R> o = row_slash(fo, v);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) o.w[k] = mul_i(g * o.w[k]);
+  return o;
+}
+// i g V/ . col   (pairs with a row spinor)
+template <class R>
+__device__ __forceinline__ W4<R> FFV1_1A(const W4<R>& fi, const W4<R>& v, R g) {
+  W4<R> o = slash_col(v, fi);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) o.w[k] = mul_i(g * o.w[k]);
+  return o;
+}
+// i g (row . gamma_mu . col)
+template <class R>
+__device__ __forceinline__ W4<R> FFV1P0_3A(const W4<R>& fo, const W4<R>& fi, R g) {
+  const W4<R> j = bilinear(fo, fi, R(1), R(1));
+  W4<R> o;
+  o.w[0] = mul_i(g * j.w[0]);
+#pragma unroll
+  for (int k = 1; k < 4; ++k) o.w[k] = mul_mi(g * j.w[k]);
+  return o;
+}
+// -i gz (row . gamma_mu (gl PL + gr PR) . col)
+template <class R>
+__device__ __forceinline__ W4<R> FFV2_4_3A(const W4<R>& fo, const W4<R>& fi, R gz, R gl, R gr) {
+  const W4<R> j = bilinear(fo, fi, gl, gr);
+  W4<R> o;
+  o.w[0] = mul_mi(gz * j.w[0]);
+#pragma unroll
+  for (int k = 1; k < 4; ++k) o.w[k] = mul_i(gz * j.w[k]);
+  return o;
+}
+// g [ (A1.A2)(q1 - q2)_mu + A2_mu ((q2 - q3).A1) + A1_mu ((q3 - q1).A2) ],
+// q1 = -K1, q2 = -K2, q3 = K1 + K2 (as VVV1P0_1)
+template <class R>
+__device__ __forceinline__ W4<R> VVV1P0_1A(const W4<R>& a1, const W4<R>& a2, const R* K1, const R* K2, R g) {
+  R d12[4], d23[4], d31[4];
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    d12[mu] = K2[mu] - K1[mu];
+    d23[mu] = -(K1[mu] + R(2) * K2[mu]);
+    d31[mu] = R(2) * K1[mu] + K2[mu];
+  }
+  const cx<R> a12 = vdot(a1, a2);
+  const cx<R> c1 = kdot(d23, a1);
+  const cx<R> c2 = kdot(d31, a2);
+  W4<R> o;
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    const cx<R> n = d12[mu] * a12 + a2.w[mu] * c1 + a1.w[mu] * c2;
+    o.w[mu] = (mu == 0 ? g : -g) * n;
+  }
+  return o;
+}
+// -i g^2 [ (x . (..)) - (y . (..)) ] of one four-gluon term (see vvvv_comb)
+template <class R>
+__device__ __forceinline__ W4<R> vvvv_comb_a(const W4<R>& x, cx<R> cx_, const W4<R>& y, cx<R> cy, R g2) {
+  W4<R> o;
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    const cx<R> t = cx_ * x.w[mu] - cy * y.w[mu];
+    o.w[mu] = mu == 0 ? mul_mi(g2 * t) : mul_i(g2 * t);
+  }
+  return o;
+}
+// contraction of an amputated current with the left-out operand
+template <class R>
+__device__ __forceinline__ cx<R> dot4(const W4<R>& x, const W4<R>& y) {
+  return x.w[0] * y.w[0] + x.w[1] * y.w[1] + x.w[2] * y.w[2] + x.w[3] * y.w[3];
+}
+
 }  // namespace mg

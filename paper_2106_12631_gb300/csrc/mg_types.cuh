@@ -50,12 +50,14 @@ struct Couplings {
 };
 
 // Helicity-shared program tables (generated per process).
-// One variant of one off-shell current: type (0 ixxxxx, 1 oxxxxx, 2 vxxxxx,
-// 3 off-shell flowing-out fermion, 4 off-shell flowing-in fermion, 5 vector from a
-// fermion pair, 6 Z from a lepton pair, 7 three-gluon, 8 four-gluon term);
-// a/b/c: type parameters (external: leg, helicity, flow sign; pair: coupling
-// 0 g_s / 1 e); flag: external top mass; out/in: variant slots; k0/k1:
-// momentum-table entries; prop: propagator entry.
+// One variant of one off-shell current or amputated current: type (0 ixxxxx,
+// 1 oxxxxx, 2 vxxxxx, 3 off-shell flowing-out fermion, 4 off-shell flowing-in
+// fermion, 5 vector from a fermion pair, 6 Z from a lepton pair, 7 three-gluon,
+// 8 four-gluon term; amputated: 9 row, 10 column, 11 fermion pair, 12 lepton
+// pair to Z, 13 three-gluon, 14 four-gluon term); a/b/c: type parameters
+// (external: leg, helicity, flow sign; pair: coupling 0 g_s / 1 e); flag:
+// external top mass; out/in: variant slots; k0/k1: momentum-table entries;
+// prop: propagator entry.
 struct HsItem {
   uint8_t type;
   int8_t a, b, c;
@@ -64,16 +66,6 @@ struct HsItem {
   uint16_t in[6];
   uint8_t k0, k1, prop;
 };
-// One amplitude: type (0 FFV g_s, 1 FFV e, 2 Z, 3 three-gluon, 4-6 four-gluon
-// term 0-2), colour-flow pattern (generated hs_flows), operand currents,
-// momentum entries (three-gluon).
-struct HsAmp {
-  uint8_t type;
-  uint8_t pat;
-  uint8_t op[4];
-  uint8_t k[3];
-};
-
 // Physics parameters in FP64 (propagator denominators are formed in FP64 in
 // both precision modes).
 struct PhysParams {

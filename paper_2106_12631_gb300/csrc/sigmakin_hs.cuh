@@ -5,18 +5,17 @@
 //   * an off-shell current over legs S depends only on the helicities of S,
 //     so each current is computed once per event for each of its 2^|S|
 //     helicity variants (not once per event helicity), into shared memory;
-//   * every diagram's amplitude is formed at the vertex (chosen by the
-//     generator) that needs the cheapest set of such currents;
-//   * both the current items and the amplitude list are tables walked by
-//     short loops, so the program is a few hundred instructions that stay in
-//     the instruction cache (the unrolled gg -> t t~ g g program streams
-//     ~30k instructions per helicity from L2).
+//   * every diagram's amplitude is formed at a vertex chosen by the generator,
+//     with one operand Y left out: A = sum_i X_i Y_i, where the amputated
+//     current X of the other operands is again shared across helicities;
+//   * currents, amputated currents and amplitudes are tables walked by short
+//     loops, so the program stays in the instruction cache.
 // CTA of NT threads = EV events x ngood helicities.  Phases:
 //   1. per-event momenta, momentum sums and FP64 propagator factors (as SIGMAKIN);
 //   2. current variants, level by level (a level only reads earlier levels);
-//   3. one thread per (event, helicity): loop over the amplitudes, operands from
-//      shared memory (re-used while consecutive amplitudes share them), each
-//      amplitude added into its colour flows J (shared memory);
+//   3. per chunk of amputated currents: their variants (all threads), then one
+//      thread per (event, helicity) contracts the chunk's amplitudes and adds
+//      each into its colour flows J (registers);
 //   4. colour sum (CUDA cores, or tcgen05 as in sigmakin.cuh) and the
 //      fixed-order FP64 helicity sum.
 #pragma once
@@ -29,17 +28,17 @@ namespace mg {
 #endif
 
 // One large CTA per SM for the many-colour processes: its warps walk the same
-// amplitude table in near lockstep, so they share instruction fetches (the
-// amplitude phase is several thousand instructions long; independent small
-// CTAs at different points of it thrash the instruction cache).  FP64 needs
+// amplitude table in near lockstep and share instruction fetches.  FP64 needs
 // more registers per thread, hence fewer threads.
 template <class P, class R>
 struct HsCfg {
   static constexpr int NT = P::NCOLOR >= 6 ? (sizeof(R) == 4 ? MG_HS_NT : 256) : 128;
   static constexpr int EVMIN = (NT / P::NHEL) > 0 ? (NT / P::NHEL) : 1;
   static constexpr int EVWANT = (4 * EVMIN) < 32 ? 4 * EVMIN : 32;
-  static constexpr size_t CUR_BUDGET = 110 * 1024;  // shared memory for current variants
-  static constexpr int FIT = (int)(CUR_BUDGET / (P::HS_NSLOT * sizeof(W4<R>)));
+  // shared memory for the current variants and one chunk of amputated currents
+  static constexpr size_t CUR_BUDGET = 192 * 1024;
+  static constexpr size_t EV_BYTES = (size_t)(P::HS_NSLOT + P::HS_XCAP) * sizeof(W4<R>);
+  static constexpr int FIT = (int)(CUR_BUDGET / EV_BYTES);
   static constexpr int EVCAP = FIT < EVWANT ? (FIT > EVMIN ? FIT : EVMIN) : EVWANT;
   static constexpr int KP = ((P::NCOLOR + 15) / 16) * 16;
   static constexpr int NP = KP;
@@ -59,15 +58,18 @@ struct HsLayout {
   static constexpr size_t o_K = align_up(o_p + 8 * EVCAP * P::NPAR * 4, 16);
   static constexpr size_t o_pr = align_up(o_K + sizeof(R) * EVCAP * P::NMOM * 4, 16);
   static constexpr size_t o_m2 = align_up(o_pr + 2 * sizeof(R) * EVCAP * P::NPROP, 16);
-  static constexpr size_t o_slot = align_up(o_m2 + 8 * NT, 16);
-  static constexpr size_t o_B = align_up(o_slot + 2 * P::HS_NCUR * P::NHEL, 1024);
+  // variant of a leg set for a helicity: vt[S * NHEL + ihel]
+  static constexpr size_t o_vt = align_up(o_m2 + 8 * NT, 16);
+  static constexpr size_t o_B = align_up(o_vt + (size_t(1) << P::NPAR) * P::NHEL, 1024);
   static constexpr size_t o_U = align_up(o_B + (TC ? NP * KP * 2 : 0), 1024);
-  // union: current variants (phases 2-3), then the tensor-core A tiles (phase 4)
-  static constexpr size_t o_cur = o_U, o_A = o_U;
+  // union: current variants + amputated chunk (phases 2-3), then the tensor-core A tiles (phase 4)
+  static constexpr size_t o_cur = o_U;
+  static constexpr size_t o_x = o_U + sizeof(W4<R>) * EVCAP * P::HS_NSLOT;
+  static constexpr size_t o_A = o_U;
   static constexpr size_t tileA = 128 * KP * 2;
-  static constexpr size_t cur_bytes = sizeof(W4<R>) * EVCAP * P::HS_NSLOT;
+  static constexpr size_t u_bytes = sizeof(W4<R>) * EVCAP * (P::HS_NSLOT + P::HS_XCAP);
   static constexpr size_t a_bytes = TC ? 3 * MBLK * tileA : 0;  // one component's three splits
-  static constexpr size_t bytes = o_U + (cur_bytes > a_bytes ? cur_bytes : a_bytes);
+  static constexpr size_t bytes = o_U + (u_bytes > a_bytes ? u_bytes : a_bytes);
   static constexpr uint32_t TMEM_COLS = tc::tmem_cols(MBLK * 2 * NP);
   static_assert(!TC || NT % 128 == 0, "CTA rows must fill 128-row MMA blocks");
   static_assert(TMEM_COLS <= 512, "TMEM holds 512 columns");
@@ -225,6 +227,24 @@ __device__ __forceinline__ void hs_item(const HsItem& it, W4<R>* cur, const R* K
   cur[it.out] = o;
 }
 
+// one amputated-current variant (reads the currents, writes the chunk buffer)
+template <class P, class R>
+__device__ __forceinline__ void hs_xitem(const HsItem& it, const W4<R>* cur, W4<R>* xb, const R* K,
+                                         const Couplings<R>& cp) {
+  W4<R> o;
+  switch (it.type) {
+    case 9: o = FFV1_2A<R>(cur[it.in[0]], cur[it.in[1]], cp.gs); break;
+    case 10: o = FFV1_1A<R>(cur[it.in[0]], cur[it.in[1]], cp.gs); break;
+    case 11: o = FFV1P0_3A<R>(cur[it.in[0]], cur[it.in[1]], it.a ? cp.ee : cp.gs); break;
+    case 12: o = FFV2_4_3A<R>(cur[it.in[0]], cur[it.in[1]], cp.gz, cp.gzl, cp.gzr); break;
+    case 13: o = VVV1P0_1A<R>(cur[it.in[0]], cur[it.in[1]], K + 4 * it.k0, K + 4 * it.k1, cp.gs); break;
+    default:
+      o = vvvv_comb_a(cur[it.in[0]], vdot(cur[it.in[1]], cur[it.in[2]]), cur[it.in[3]],
+                      vdot(cur[it.in[4]], cur[it.in[5]]), cp.gs2);
+  }
+  xb[it.out] = o;
+}
+
 template <class P, class R, int CS>
 __global__ void __launch_bounds__(HsCfg<P, R>::NT, 1) sigmakin_hs_kernel(SigArgs a, Couplings<R> cp) {
   using C = HsCfg<P, R>;
@@ -234,8 +254,9 @@ __global__ void __launch_bounds__(HsCfg<P, R>::NT, 1) sigmakin_hs_kernel(SigArgs
   int* good = reinterpret_cast<int*>(smem + L::o_good);
   int* misc = reinterpret_cast<int*>(smem + L::o_misc);
   double* sm2 = reinterpret_cast<double*>(smem + L::o_m2);
-  uint16_t* slots = reinterpret_cast<uint16_t*>(smem + L::o_slot);
+  uint8_t* vtab = reinterpret_cast<uint8_t*>(smem + L::o_vt);
   W4<R>* curs = reinterpret_cast<W4<R>*>(smem + L::o_cur);
+  W4<R>* xbufs = reinterpret_cast<W4<R>*>(smem + L::o_x);
   const int tid = threadIdx.x;
   load_tables<P, L>(smem);
   if (tid == 0) {
@@ -244,9 +265,15 @@ __global__ void __launch_bounds__(HsCfg<P, R>::NT, 1) sigmakin_hs_kernel(SigArgs
       if (a.mask[h]) good[n++] = h;
     misc[0] = n;
   }
-  {
-    const uint16_t* src = P::hs_slots();
-    for (int i = tid; i < P::HS_NCUR * P::NHEL; i += NT) slots[i] = src[i];
+  // vt[S][ihel]: bits of the legs in S (ascending) of helicity ihel, where
+  // leg l is +1 when bit NPAR-1-l of ihel is set
+  for (int i = tid; i < (1 << P::NPAR) * P::NHEL; i += NT) {
+    const int S = i / P::NHEL, ih = i % P::NHEL;
+    int v = 0, k = 0;
+#pragma unroll
+    for (int l = 0; l < P::NPAR; ++l)
+      if (S >> l & 1) v |= ((ih >> (P::NPAR - 1 - l)) & 1) << k++;
+    vtab[i] = (uint8_t)v;
   }
   __syncthreads();
   const int ng = misc[0];
@@ -290,17 +317,26 @@ __global__ void __launch_bounds__(HsCfg<P, R>::NT, 1) sigmakin_hs_kernel(SigArgs
     }
     __syncthreads();
   }
-  // 3. amplitudes of this thread's (event, helicity), J in registers
+  // 3. amputated currents chunk by chunk, each followed by the contractions of
+  //    this thread's (event, helicity); J in registers
   const bool active = tid < nev * ng;
   const int e = active ? tid / ng : 0;
   const int ih = good[active ? tid - e * ng : 0];
-  const W4<R>* cur = curs + e * P::HS_NSLOT;
-  const R* K = Kall + e * P::NMOM * 4;
-  const uint16_t* sl = slots + ih;
   cx<R> J[NC];
 #pragma unroll
   for (int s = 0; s < NC; ++s) J[s] = cx<R>(R(0), R(0));
-  P::template hs_amplitudes<R>(cur, sl, K, cp, J);
+#pragma unroll 1
+  for (int c = 0; c < P::HS_NXCHUNK; ++c) {
+    if (c > 0) __syncthreads();  // the previous chunk's contractions are done with the buffer
+    const int i0 = P::hs_xitem(c), n = (P::hs_xitem(c + 1) - i0) * nev;
+    for (int t = tid; t < n; t += NT) {
+      const int ex = t % nev;
+      const HsItem it = items[i0 + t / nev];
+      hs_xitem<P, R>(it, curs + ex * P::HS_NSLOT, xbufs + ex * P::HS_XCAP, Kall + ex * P::NMOM * 4, cp);
+    }
+    __syncthreads();
+    P::template hs_contract<R>(c, curs + e * P::HS_NSLOT, xbufs + e * P::HS_XCAP, vtab + ih, J);
+  }
   // 4. colour sum and helicity sum
   double m2;
   if constexpr (L::TC) {

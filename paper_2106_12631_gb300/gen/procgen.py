@@ -365,6 +365,9 @@ FLOPS = {
     "FFV1_1": 148, "FFV1_2": 148, "FFV1P0_3": 106, "FFV2_4_3": 114,
     "VVV1P0_1": 176, "VVVV1P0_1": 142, "VVVV3P0_1": 142, "VVVV4P0_1": 142,
     "VVV1_0": 168, "VVVV_0": 136,
+    # amputated currents (no propagator) and the contraction sum_i X_i Y_i
+    "FFV1_2A": 72, "FFV1_1A": 72, "FFV1P0_3A": 80, "FFV2_4_3A": 96, "VVV1P0_1A": 158, "VVVV_A": 124,
+    "DOT4": 30,
     "jamp": 2,
 }
 
@@ -828,7 +831,7 @@ def summary(pid: int) -> dict:
     sp.emit_tables(pid)
     return dict(flops_amp=em.flops, flops_csum=colour_sum_flops(em.cnum), ncurrents=em.ncurrents,
                 hs_flops_items=sp.flops_items, hs_flops_amp_hel=sp.flops_amps_hel, hs_ncur=len(sp.order),
-                hs_nslots=sp.nslots,
+                hs_nslots=sp.nslots, hs_nx=len(sp.xoff), hs_xcap=sp.xcap, hs_nxchunk=len(sp.chunks),
                 ndiagrams=proc.ndiagrams, namps=len(proc.amps), ncolor=em.coef.shape[1],
                 nmom=len(em.mom), nprop=len(em.props), coef=em.coef, cnum=em.cnum, cden=em.cden,
                 perms=em.perms, gluon_legs=proc.gluon_legs())
@@ -849,12 +852,27 @@ def summary(pid: int) -> dict:
 #     (cyclic order kept, so f^abc and the Lorentz factor keep their orientation)
 #   at a four-gluon term t (c0, c1, c2 | P):           U(ck) = term t with leg k as output
 # The colour coefficients stay those of the antitop-rooted form.
+#
+# The amplitude at a vertex is multilinear in its operands, so with operand k
+# left out it is a plain contraction  A = sum_i X_i Y_i  of Y = operand k with
+# the AMPUTATED current X of the other operands (the same vertex without its
+# propagator; vectors stored with a lower index).  X depends only on the
+# helicities of its own legs: it is built once per event and helicity variant,
+# like the currents, and each event helicity pays only the contraction
+# (30 flops) instead of a full vertex (96 to 168 flops).  The generator picks
+# the vertex and the left-out operand of every amplitude together.
 
 SHARED_COST = {"ext": 40, "ggg": FLOPS["VVV1P0_1"], "gggg": FLOPS["VVVV1P0_1"], "qqg_row": FLOPS["FFV1_2"],
                "col": FLOPS["FFV1_1"], "pair": FLOPS["FFV1P0_3"], "ffa_cur": FLOPS["FFV1P0_3"],
-               "ffz_cur": FLOPS["FFV2_4_3"]}
-SHARED_AMP = {"ffv": FLOPS["FFV1_0"], "vvv": FLOPS["VVV1_0"], "vvvv": FLOPS["VVVV_0"], "ffv_a": FLOPS["FFV1_0"],
-              "ffz": FLOPS["FFV2_4_0"]}
+               "ffz_cur": FLOPS["FFV2_4_3"],
+               "arow": FLOPS["FFV1_2A"], "acol": FLOPS["FFV1_1A"], "apair": FLOPS["FFV1P0_3A"],
+               "apair_e": FLOPS["FFV1P0_3A"], "azpair": FLOPS["FFV2_4_3A"], "aggg": FLOPS["VVV1P0_1A"],
+               "agggg": FLOPS["VVVV_A"]}
+
+# operands that may be left out of each amplitude form (lepton amplitudes:
+# the boson only, so that the couplings stay in one amputated pair current)
+EXCLUDE = {"ffv": (0, 1, 2), "ffv_a": (2,), "ffz": (2,), "vvv": (0, 1, 2),
+           "vvvv0": (0, 1, 2, 3), "vvvv1": (0, 1, 2, 3), "vvvv2": (0, 1, 2, 3)}
 
 # four-gluon term t: L_t = (A_a.A_b)(A_c.A_d) - (A_e.A_f)(A_g.A_h), legs 0..3
 VVVV_PAIRS = {0: (((0, 2), (1, 3)), ((0, 3), (1, 2))),
@@ -863,22 +881,32 @@ VVVV_PAIRS = {0: (((0, 2), (1, 3)), ((0, 3), (1, 2))),
 
 
 class SharedProgram:
+    SLOT_BUDGET = 768  # current + amputated-chunk variant slots per event (FP32: 8 events in 192 KB)
+    CUR_CAP = 416      # current variant slots per event
+
     def __init__(self, proc: Process, emitter: "Emitter"):
         self.p = proc
         self.em = emitter
         self.n = proc.n
+        self._legs = {}
+        self._closure = {}
         self._cands()
         self._choose()
-        self._currents()
+        self._layout()
 
     # ---- descriptors -------------------------------------------------------
     def legs(self, d):
+        s = self._legs.get(d)
+        if s is not None:
+            return s
         if d[0] == "N":
-            return frozenset(self.p.cur[d[1]].legs)
-        s = frozenset()
-        for x in d[2:]:
-            if isinstance(x, tuple):
-                s |= self.legs(x)
+            s = frozenset(self.p.cur[d[1]].legs)
+        else:
+            s = frozenset()
+            for x in d[2:]:
+                if isinstance(x, tuple):
+                    s |= self.legs(x)
+        self._legs[d] = s
         return s
 
     def kind(self, d):
@@ -893,12 +921,32 @@ class SharedProgram:
             return [] if c.vertex == "ext" else [("N", ch) for ch in c.children]
         return [x for x in d[2:] if isinstance(x, tuple)]
 
-    def deps(self, d, out):
-        if d in out:
-            return
-        for x in self.inputs(d):
-            self.deps(x, out)
-        out[d] = None
+    def closure(self, d):
+        """d and every current it is built from."""
+        c = self._closure.get(d)
+        if c is None:
+            c = frozenset([d]).union(*[self.closure(x) for x in self.inputs(d)])
+            self._closure[d] = c
+        return c
+
+    def nvar(self, d):
+        return 1 << len(self.legs(d))
+
+    @staticmethod
+    def xdesc(kind, args, k):
+        """Amputated current of the operands of amplitude (kind, args) other than k."""
+        if kind == "ffv":
+            r, c, b = args
+            return {0: ("X", "acol", b, c), 1: ("X", "arow", r, b), 2: ("X", "apair", r, c)}[k]
+        if kind == "ffv_a":
+            return ("X", "apair_e", args[0], args[1])
+        if kind == "ffz":
+            return ("X", "azpair", args[0], args[1])
+        if kind == "vvv":
+            c0, c1, u = args
+            return {2: ("X", "aggg", c0, c1), 0: ("X", "aggg", c1, u), 1: ("X", "aggg", u, c0)}[k]
+        t = int(kind[-1])
+        return ("X", "agggg", t, k) + tuple(None if i == k else a for i, a in enumerate(args))
 
     # ---- candidate evaluation points -------------------------------------------
     def _cands(self):
@@ -908,88 +956,131 @@ class SharedProgram:
         for a in p.amps:
             A, B = ("N", a.row), ("N", a.bos)
             if a.vertex != "ffv_t":  # leptons: the root-form amplitude only
-                self.cands.append([(a.vertex, (("N", a.row), ("N", a.col), ("N", a.bos)))])
-                continue
-            opts = [("ffv", (A, top, B))]
-            stack = [(a.row, ("U", "col", B, top)), (a.bos, ("U", "pair", A, top))]
-            while stack:
-                n, U = stack.pop()
-                c = p.cur[n]
-                if c.vertex == "ext":
-                    continue
-                ch = [("N", x) for x in c.children]
-                if c.vertex == "qqg_row":
-                    r, g = ch
-                    opts.append(("ffv", (r, U, g)))
-                    stack.append((c.children[0], ("U", "col", g, U)))
-                    stack.append((c.children[1], ("U", "pair", r, U)))
-                elif c.vertex == "ggg":
-                    c0, c1 = ch
-                    opts.append(("vvv", (c0, c1, U)))
-                    stack.append((c.children[0], ("U", "ggg", c1, U)))
-                    stack.append((c.children[1], ("U", "ggg", U, c0)))
-                elif c.vertex.startswith("gggg"):
-                    t = int(c.vertex[-1])
-                    opts.append(("vvvv%d" % t, (ch[0], ch[1], ch[2], U)))
-                    for k in range(3):
-                        others = tuple(x for j, x in enumerate(ch) if j != k)
-                        stack.append((c.children[k], ("U", "gggg", t, k) + others + (U,)))
-            self.cands.append(opts)
-
-    SLOT_CAP = 384  # variant slots per event (shared memory: 12 KB in FP32, 24 KB in FP64)
-
-    def _cost(self, choice):
-        need = {}
-        amp = 0
-        for opts, ci in zip(self.cands, choice):
-            kind, args = opts[ci]
-            amp += SHARED_AMP["vvvv" if kind.startswith("vvvv") else kind] * (1 << self.n)
-            for x in args:
-                self.deps(x, need)
-        cur = sum(SHARED_COST[self.kind(d)] * (1 << len(self.legs(d))) for d in need)
-        slots = sum(1 << len(self.legs(d)) for d in need)
-        over = max(0, slots - self.SLOT_CAP)
-        return cur + amp + over * 10 ** 7
+                opts = [(a.vertex, (("N", a.row), ("N", a.col), ("N", a.bos)))]
+            else:
+                opts = [("ffv", (A, top, B))]
+                stack = [(a.row, ("U", "col", B, top)), (a.bos, ("U", "pair", A, top))]
+                while stack:
+                    n, U = stack.pop()
+                    c = p.cur[n]
+                    if c.vertex == "ext":
+                        continue
+                    ch = [("N", x) for x in c.children]
+                    if c.vertex == "qqg_row":
+                        r, g = ch
+                        opts.append(("ffv", (r, U, g)))
+                        stack.append((c.children[0], ("U", "col", g, U)))
+                        stack.append((c.children[1], ("U", "pair", r, U)))
+                    elif c.vertex == "ggg":
+                        c0, c1 = ch
+                        opts.append(("vvv", (c0, c1, U)))
+                        stack.append((c.children[0], ("U", "ggg", c1, U)))
+                        stack.append((c.children[1], ("U", "ggg", U, c0)))
+                    elif c.vertex.startswith("gggg"):
+                        t = int(c.vertex[-1])
+                        opts.append(("vvvv%d" % t, (ch[0], ch[1], ch[2], U)))
+                        for k in range(3):
+                            others = tuple(x for j, x in enumerate(ch) if j != k)
+                            stack.append((c.children[k], ("U", "gggg", t, k) + others + (U,)))
+            # every vertex form with every operand that may be left out
+            full = []
+            for kind, args in opts:
+                for k in EXCLUDE[kind]:
+                    X = self.xdesc(kind, args, k)
+                    cl = frozenset().union(*[self.closure(x) for x in self.inputs(X)], self.closure(args[k]))
+                    full.append((kind, args, k, X, cl))
+            self.cands.append(full)
 
     def _choose(self):
-        choice = [0] * len(self.cands)
-        for _ in range(4):
+        """Greedy choice of (vertex, left-out operand) per amplitude minimising the
+        per-event cost of the shared currents and amputated currents (the per-helicity
+        contraction costs the same for every choice), with current slots capped."""
+        refc, xref = {}, {}
+        state = {"cost": 0, "slots": 0}
+
+        def cost_cur(d):
+            return SHARED_COST[self.kind(d)] * self.nvar(d)
+
+        def apply(opt, s):
+            _, _, _, X, cl = opt
+            for d in cl:
+                r = refc.get(d, 0)
+                if (r == 0 and s > 0) or (r == 1 and s < 0):
+                    state["cost"] += s * cost_cur(d)
+                    state["slots"] += s * self.nvar(d)
+                refc[d] = r + s
+            r = xref.get(X, 0)
+            if (r == 0 and s > 0) or (r == 1 and s < 0):
+                state["cost"] += s * SHARED_COST[X[1]] * self.nvar(X)
+            xref[X] = r + s
+
+        def added(opt):
+            _, _, _, X, cl = opt
+            c = sl = 0
+            for d in cl:
+                if refc.get(d, 0) == 0:
+                    c += cost_cur(d)
+                    sl += self.nvar(d)
+            if xref.get(X, 0) == 0:
+                c += SHARED_COST[X[1]] * self.nvar(X)
+            over = max(0, state["slots"] + sl - self.CUR_CAP)
+            return c + over * 10 ** 7
+
+        choice = []
+        for opts in self.cands:  # start: root form, the largest operand left out
+            best = max(range(len(opts)), key=lambda i: (opts[i][0] == opts[0][0] and opts[i][1] == opts[0][1],
+                                                       len(self.legs(opts[i][1][opts[i][2]]))))
+            choice.append(best)
+            apply(opts[best], +1)
+        for _ in range(8):
             changed = False
-            for di in range(len(self.cands)):
-                best = None
-                for ci in range(len(self.cands[di])):
-                    choice[di] = ci
-                    t = self._cost(choice)
-                    if best is None or t < best[0]:
-                        best = (t, ci)
-                if choice[di] != best[1]:
+            for di, opts in enumerate(self.cands):
+                apply(opts[choice[di]], -1)
+                best = min(range(len(opts)), key=lambda i: (added(opts[i]), i))
+                if best != choice[di]:
                     changed = True
-                choice[di] = best[1]
+                choice[di] = best
+                apply(opts[best], +1)
             if not changed:
                 break
         self.choice = choice
-        self.flops_event = self._cost(choice)
+        self.flops_event = state["cost"]
 
-    # ---- currents and their variants ------------------------------------------
-    def _currents(self):
-        need = {}
+    # ---- currents, amputated currents, chunks --------------------------------------
+    def _layout(self):
+        need = set()
+        xs = []
         for opts, ci in zip(self.cands, self.choice):
-            for x in opts[ci][1]:
-                self.deps(x, need)
-        self.order = list(need)                    # children before parents
-        self.cid = {d: i for i, d in enumerate(self.order)}
+            need |= opts[ci][4]
+            if opts[ci][3] not in xs:
+                xs.append(opts[ci][3])
         self.level = {}
-        for d in self.order:
+        for d in sorted(need, key=lambda d: len(self.closure(d))):
             ins = self.inputs(d)
             self.level[d] = 0 if not ins else 1 + max(self.level[x] for x in ins)
-        self.order.sort(key=lambda d: self.level[d])
+        self.order = sorted(need, key=lambda d: (self.level[d], self.kind(d), sorted(self.legs(d)), repr(d)))
         self.cid = {d: i for i, d in enumerate(self.order)}
         self.offset = {}
         off = 0
         for d in self.order:
             self.offset[d] = off
-            off += 1 << len(self.legs(d))
+            off += self.nvar(d)
         self.nslots = off
+        # amputated currents, packed into chunks that share one buffer
+        xs.sort(key=lambda X: (X[1], sorted(self.legs(X)), repr(X)))
+        total = sum(self.nvar(X) for X in xs)
+        self.xcap = min(total, self.SLOT_BUDGET - self.nslots)
+        assert self.xcap >= max(self.nvar(X) for X in xs), "no room for an amputated current"
+        self.xchunk, self.xoff, self.chunks = {}, {}, [[]]
+        used = 0
+        for X in xs:
+            if used + self.nvar(X) > self.xcap:
+                self.chunks.append([])
+                used = 0
+            self.xchunk[X] = len(self.chunks) - 1
+            self.xoff[X] = used
+            self.chunks[-1].append(X)
+            used += self.nvar(X)
 
     def variant(self, d, hel_bits):
         """Variant index of current d for an event helicity (bit l of hel_bits = leg l is +1)."""
@@ -1008,8 +1099,7 @@ class SharedProgram:
 
     # ---- device tables ------------------------------------------------------------
     HS_TYPES = {"ixxxxx": 0, "oxxxxx": 1, "vxxxxx": 2, "row": 3, "col": 4, "pair": 5, "zcur": 6,
-                "ggg": 7, "gggg": 8}
-    AMP_TYPES = {"ffv": 0, "ffv_a": 1, "ffz": 2, "vvv": 3, "vvvv0": 4, "vvvv1": 5, "vvvv2": 6}
+                "ggg": 7, "gggg": 8, "arow": 9, "acol": 10, "apair": 11, "azpair": 12, "aggg": 13, "agggg": 14}
 
     def _canon_prop_legs(self, legs):
         """The invariant of an internal line, formed from the side without the
@@ -1017,10 +1107,24 @@ class SharedProgram:
         root = self.p.spec.root
         return frozenset(range(self.n)) - legs if root in legs else legs
 
+    def _gggg_positions(self, d):
+        """(term, output position, {position: operand}) of a four-gluon current."""
+        xs = self.inputs(d)
+        if d[0] == "N":
+            return int(self.p.cur[d[1]].vertex[-1]), 3, {0: xs[0], 1: xs[1], 2: xs[2]}
+        if d[0] == "U":
+            term, outpos = d[2], d[3]
+            o1, o2, U = d[4], d[5], d[6]
+            rest = [q for q in range(3) if q != outpos]
+            return term, outpos, {rest[0]: o1, rest[1]: o2, 3: U}
+        term, outpos = d[2], d[3]
+        return term, outpos, {q: d[4 + q] for q in range(4) if q != outpos}
+
     def _item(self, d, v):
-        """One current variant: (type, a, b, c, flag, out, in[6], k0, k1, prop)."""
+        """One variant of a current or amputated current:
+        (type, a, b, c, flag, out, in[6], k0, k1, prop)."""
         em, spec = self.em, self.p.spec
-        out = self.offset[d] + v
+        out = (self.xoff[d] if d[0] == "X" else self.offset[d]) + v
         ins = [0] * 6
         a = b = c = flag = 0
         k0 = k1 = prop = 0
@@ -1041,43 +1145,43 @@ class SharedProgram:
             else:
                 t, c = self.HS_TYPES["oxxxxx"], (1 if L.particle else -1)
             a, b = leg, hel
-        elif kind == "qqg_row":
-            t = self.HS_TYPES["row"]
-            ins[0], ins[1] = slot(xs[0]), slot(xs[1])
-            k0 = em.momentum(legs)
-            prop = em.prop(self._canon_prop_legs(legs), "t")
-        elif kind == "col":
-            t = self.HS_TYPES["col"]
+        elif kind in ("qqg_row", "arow"):
+            t = self.HS_TYPES["row" if kind == "qqg_row" else "arow"]
+            ins[0], ins[1] = slot(xs[0]), slot(xs[1])   # (row, gluon)
+            if kind == "qqg_row":
+                k0 = em.momentum(legs)
+                prop = em.prop(self._canon_prop_legs(legs), "t")
+        elif kind in ("col", "acol"):
+            t = self.HS_TYPES[kind]
             g, U = xs
             ins[0], ins[1] = slot(U), slot(g)   # FFV1_1(fi = U, v = g)
-            k0 = em.momentum(legs)
-            prop = em.prop(self._canon_prop_legs(legs), "t")
-        elif kind == "pair":
-            t = self.HS_TYPES["pair"]
+            if kind == "col":
+                k0 = em.momentum(legs)
+                prop = em.prop(self._canon_prop_legs(legs), "t")
+        elif kind in ("pair", "apair", "apair_e"):
+            t = self.HS_TYPES["pair" if kind == "pair" else "apair"]
             r, U = xs
             ins[0], ins[1] = slot(r), slot(U)   # FFV1P0_3(fo = r, fi = U)
-            prop = em.prop(self._canon_prop_legs(legs), "g")
+            a = 1 if kind == "apair_e" else 0
+            if kind == "pair":
+                prop = em.prop(self._canon_prop_legs(legs), "g")
+        elif kind == "azpair":
+            t = self.HS_TYPES["azpair"]
+            ins[0], ins[1] = slot(xs[0]), slot(xs[1])
         elif kind in ("ffa_cur", "ffz_cur"):
             t = self.HS_TYPES["pair" if kind == "ffa_cur" else "zcur"]
             ins[0], ins[1] = slot(xs[0]), slot(xs[1])
             a = 1  # coupling: e
             prop = em.prop(self._canon_prop_legs(legs), "A" if kind == "ffa_cur" else "Z")
-        elif kind == "ggg":
-            t = self.HS_TYPES["ggg"]
+        elif kind in ("ggg", "aggg"):
+            t = self.HS_TYPES[kind]
             ins[0], ins[1] = slot(xs[0]), slot(xs[1])
             k0, k1 = em.momentum(self.legs(xs[0])), em.momentum(self.legs(xs[1]))
-            prop = em.prop(self._canon_prop_legs(legs), "g")
-        elif kind == "gggg":
-            t = self.HS_TYPES["gggg"]
-            if d[0] == "N":
-                term = int(self.p.cur[d[1]].vertex[-1])
-                pos = {0: xs[0], 1: xs[1], 2: xs[2]}
-                outpos = 3
-            else:
-                term, outpos = d[2], d[3]
-                o1, o2, U = d[4], d[5], d[6]
-                rest = [q for q in range(3) if q != outpos]
-                pos = {rest[0]: o1, rest[1]: o2, 3: U}
+            if kind == "ggg":
+                prop = em.prop(self._canon_prop_legs(legs), "g")
+        elif kind in ("gggg", "agggg"):
+            t = self.HS_TYPES[kind]
+            term, outpos, pos = self._gggg_positions(d)
             for j, pair in enumerate(VVVV_PAIRS[term]):
                 (p0, p1), (p2, p3) = pair
                 if outpos in (p0, p1):
@@ -1087,13 +1191,13 @@ class SharedProgram:
                     X = p3 if outpos == p2 else p2
                     Y, Z = p0, p1
                 ins[3 * j + 0], ins[3 * j + 1], ins[3 * j + 2] = slot(pos[X]), slot(pos[Y]), slot(pos[Z])
-            prop = em.prop(self._canon_prop_legs(legs), "g")
+            if kind == "gggg":
+                prop = em.prop(self._canon_prop_legs(legs), "g")
         else:
             raise ValueError(kind)
         return (t, a, b, c, flag, out, ins, k0, k1, prop)
 
     def emit_tables(self, pid: int) -> list:
-        em = self.em
         nh = 1 << self.n
         items, level_start = [], []
         cur_level = -1
@@ -1101,167 +1205,123 @@ class SharedProgram:
             if self.level[d] != cur_level:
                 cur_level = self.level[d]
                 level_start.append(len(items))
-            for v in range(1 << len(self.legs(d))):
+            for v in range(self.nvar(d)):
                 items.append(self._item(d, v))
         level_start.append(len(items))
-        # amplitudes, sorted so that consecutive ones share operands
+        xitem_start = []
+        for chunk in self.chunks:
+            xitem_start.append(len(items))
+            for X in chunk:
+                for v in range(self.nvar(X)):
+                    items.append(self._item(X, v))
+        xitem_start.append(len(items))
+        # amplitudes by chunk, then by amputated current (loaded once per run) and operand
+        patterns = {}
         amps = []
         for di, (opts, ci) in enumerate(zip(self.cands, self.choice)):
-            kind, args = opts[ci]
-            ops = [self.cid[x] for x in args]
-            ks = [em.momentum(self.legs(x)) for x in args] if kind == "vvv" else [0, 0, 0]
+            kind, args, k, X, _ = opts[ci]
+            Y = args[k]
+            assert self.legs(X) | self.legs(Y) == frozenset(range(self.n)) and not self.legs(X) & self.legs(Y)
             flows = []
             for s_ in np.nonzero(self.em.coef[di])[0]:
                 z = complex(self.em.coef[di, s_])
                 code = {1: 0, -1: 1, 1j: 2, -1j: 3}[z]
                 flows.append(int(s_) | (code << 6))
-            amps.append((self.AMP_TYPES[kind], ops, ks, flows))
-        amps.sort(key=lambda a: (a[1], a[0]))
-        patterns = {}
-        groups = {}
-        for t, ops, ks, flows in amps:
             key = tuple(flows)
             if key not in patterns:
                 patterns[key] = len(patterns)
-            o = list(ops) + [0] * (4 - len(ops))
-            groups.setdefault(t, []).append("{%d, %d, {%s}, {%s}}" % (
-                t, patterns[key], ", ".join(map(str, o)), ", ".join(map(str, ks[:3]))))
+            xset = sum(1 << l for l in self.legs(X))
+            amps.append((self.xchunk[X], self.xoff[X], self.offset[Y], patterns[key], xset, flows))
+        amps.sort()
+        assert len(patterns) < 256 and self.nslots < 65536 and self.xcap < 65536
         self.patterns = patterns
-        self.groups = {t: len(rows) for t, rows in groups.items()}
-        self.amp_list = [(t, list(ops), ks, flows) for t, ops, ks, flows in amps]
-        amp_rows = []
-        for t in sorted(groups):
-            amp_rows.extend(groups[t])
-        # slot of every current for every event helicity index
-        slot = []
-        for d in self.order:
-            row = []
-            for ih in range(nh):
-                bits = 0
-                for l in range(self.n):
-                    bits |= ((ih >> (self.n - 1 - l)) & 1) << l
-                row.append(self.offset[d] + self.variant(d, bits))
-            slot.append(row)
+        self.amp_list = amps
+        xamp_start = [0] * (len(self.chunks) + 1)
+        for c in range(len(self.chunks)):
+            xamp_start[c + 1] = xamp_start[c] + sum(1 for a in amps if a[0] == c)
         out = []
         self._exact_flops(items, amps)
-        out.append("// helicity-shared program: %d currents in %d levels, %d variant slots, %d amplitudes,"
-                   " %d flops per event (all helicities)" % (len(self.order), len(level_start) - 1, self.nslots,
-                                                            len(amps), self.flops_items + nh * self.flops_amps_hel))
+        self.tables = dict(nitems=len(items), level_start=level_start, xitem_start=xitem_start,
+                           xamp_start=xamp_start, namps=len(amps), ncur=len(self.order), nx=len(self.xoff))
+        out.append("// helicity-shared program: %d currents in %d levels (%d variant slots), %d amputated"
+                   " currents in %d chunk(s) of <= %d slots, %d amplitudes; %d flops per event (all helicities)"
+                   % (len(self.order), len(level_start) - 1, self.nslots, len(self.xoff), len(self.chunks),
+                      self.xcap, len(amps), self.flops_items + nh * self.flops_amps_hel))
         out.append("static __device__ const HsItem kHsItems%d[%d] = {%s};" % (
             pid, len(items), ", ".join("{%d, %d, %d, %d, %d, %d, {%s}, %d, %d, %d}" % (
                 t, a, b, c, flag, o, ", ".join(map(str, ins)), k0, k1, pr)
                 for (t, a, b, c, flag, o, ins, k0, k1, pr) in items)))
-        out.append("static __constant__ HsAmp kHsAmps%d[%d] = {%s};  // grouped by type"
-                   % (pid, len(amp_rows), ", ".join(amp_rows)))
-        out.append("static __device__ const uint16_t kHsSlot%d[%d][%d] = {%s};" % (
-            pid, len(self.order), nh, ", ".join("{" + ", ".join(map(str, r)) + "}" for r in slot)))
-        self.tables = dict(nitems=len(items), level_start=level_start, namps=len(amps), ncur=len(self.order))
+        out.append("static __constant__ int kHsXItem%d[%d] = {%s};  // item ranges of the amputated chunks"
+                   % (pid, len(xitem_start), ", ".join(map(str, xitem_start))))
         return out
 
     def _exact_flops(self, items, amps):
-        """Operation count: current variants per event, amplitudes + flow sums per helicity."""
+        """Operation count: current and amputated-current variants per event,
+        contractions + flow sums per helicity."""
         item_flops = {0: FLOPS["ixxxxx"], 1: FLOPS["oxxxxx"], 2: FLOPS["vxxxxx"], 3: FLOPS["FFV1_2"],
                       4: FLOPS["FFV1_1"], 5: FLOPS["FFV1P0_3"], 6: FLOPS["FFV2_4_3"], 7: FLOPS["VVV1P0_1"],
-                      8: FLOPS["VVVV1P0_1"]}
-        amp_flops = {0: FLOPS["FFV1_0"], 1: FLOPS["FFV1_0"], 2: FLOPS["FFV2_4_0"], 3: FLOPS["VVV1_0"],
-                     4: FLOPS["VVVV_0"], 5: FLOPS["VVVV_0"], 6: FLOPS["VVVV_0"]}
+                      8: FLOPS["VVVV1P0_1"], 9: FLOPS["FFV1_2A"], 10: FLOPS["FFV1_1A"], 11: FLOPS["FFV1P0_3A"],
+                      12: FLOPS["FFV2_4_3A"], 13: FLOPS["VVV1P0_1A"], 14: FLOPS["VVVV_A"]}
         self.flops_items = sum(item_flops[it[0]] for it in items)
-        self.flops_amps_hel = sum(amp_flops[t] + FLOPS["jamp"] * len(fl) for t, _, _, fl in amps)
+        self.flops_amps_hel = sum(FLOPS["DOT4"] + FLOPS["jamp"] * len(a[5]) for a in amps)
 
     def struct_lines(self, pid: int) -> list:
         t = self.tables
+
+        def table_fn(name, vals):
+            return ["  static __host__ __device__ constexpr int %s(int i) {" % name,
+                    "    constexpr int t[%d] = {%s};" % (len(vals), ", ".join(map(str, vals))),
+                    "    return t[i];",
+                    "  }"]
         return [
             "  // helicity-shared program (tables above)",
-            "  static constexpr int HS_NSLOT = %d;" % self.nslots,
+            "  static constexpr int HS_NSLOT = %d;   // current variant slots per event" % self.nslots,
+            "  static constexpr int HS_XCAP = %d;    // amputated-current slots per event and chunk" % self.xcap,
+            "  static constexpr int HS_NXCHUNK = %d;" % len(self.chunks),
             "  static constexpr int HS_NITEM = %d;" % t["nitems"],
             "  static constexpr int HS_NLEVEL = %d;" % (len(t["level_start"]) - 1),
             "  static constexpr int HS_NAMP = %d;" % t["namps"],
             "  static constexpr int HS_NCUR = %d;" % t["ncur"],
-            "  // operations: current variants per event, amplitudes + flow sums per helicity",
+            "  static constexpr int HS_NX = %d;" % t["nx"],
+            "  // operations: current variants per event, contractions + flow sums per helicity",
             "  static constexpr long HS_FLOPS_ITEMS = %d;" % self.flops_items,
             "  static constexpr long HS_FLOPS_AMP_HEL = %d;" % self.flops_amps_hel,
-            "  static __host__ __device__ constexpr int hs_level(int l) {",
-            "    constexpr int t[%d] = {%s};" % (len(t["level_start"]), ", ".join(map(str, t["level_start"]))),
-            "    return t[l];",
-            "  }",
+            "  // item ranges of the current levels and of the amputated chunks; amplitude ranges of the chunks",
+        ] + table_fn("hs_level", t["level_start"]) + [
+            "  static __device__ __forceinline__ int hs_xitem(int c) { return kHsXItem%d[c]; }" % pid,
             "  static __device__ __forceinline__ const HsItem* hs_items() { return kHsItems%d; }" % pid,
-            "  static __device__ __forceinline__ const HsAmp* hs_amps() { return kHsAmps%d; }" % pid,
-            "  static __device__ __forceinline__ const uint16_t* hs_slots() { return &kHsSlot%d[0][0]; }" % pid,
-        ] + self._flow_switch() + (self._amp_unrolled(pid) if self.AMP_UNROLL else self._amp_loops(pid))
+        ] + self._contract_code()
 
-    AMP_UNROLL = False  # straight-line amplitude phase instead of per-type loops
-
-    def _amp_unrolled(self, pid: int) -> list:
-        calls = {0: "FFV1_0<R>(%s, %s, %s, cp.gs)", 1: "FFV1_0<R>(%s, %s, %s, cp.ee)",
-                 2: "FFV2_4_0<R>(%s, %s, %s, cp.gz, cp.gzl, cp.gzr)"}
-        lines = ["  template <class R>",
-                 "  static __device__ __forceinline__ void hs_amplitudes(const W4<R>* __restrict__ cur,"
-                 " const uint16_t* __restrict__ sl, const R* __restrict__ K, const Couplings<R>& cp, cx<R>* J) {",
-                 "    cx<R> amp;"]
-        ops = {0: "J[%d] += amp;", 1: "J[%d] -= amp;", 2: "J[%d] += mul_i(amp);", 3: "J[%d] -= mul_i(amp);"}
-        for ia, (t, o, ks, flows) in enumerate(self.amp_list):
-            if ia % 4 == 0 and ia:
-                lines.append("    __syncwarp();  // bounds load hoisting (live ranges)")
-            lines.append("    {")
-            names = []
-            for j, c in enumerate(o):
-                lines.append("      const W4<R> x%d = cur[sl[%d * NHEL]];" % (j, c))
-                names.append("x%d" % j)
-            if t in calls:
-                lines.append("      amp = " + calls[t] % tuple(names[:3]) + ";")
-            elif t == 3:
-                lines.append("      amp = VVV1_0<R>(%s, %s, %s, K + %d, K + %d, K + %d, cp.gs);" % (
-                    names[0], names[1], names[2], 4 * ks[0], 4 * ks[1], 4 * ks[2]))
-            else:
-                lines.append("      amp = VVVV_0<R>(%d, %s, %s, %s, %s, cp.gs2);" % (t - 4, *names[:4]))
-            lines.append("      " + " ".join(ops[f >> 6] % (f & 63) for f in flows))
-            lines.append("    }")
-        lines.append("  }")
-        return lines
-
-    def _amp_loops(self, pid: int) -> list:
-        """Amplitude phase: one loop per amplitude type over its (constant-memory)
-        table; an operand is reloaded only when it changes (uniform branch)."""
-        calls = {0: "FFV1_0<R>(o0, o1, o2, cp.gs)", 1: "FFV1_0<R>(o0, o1, o2, cp.ee)",
-                 2: "FFV2_4_0<R>(o0, o1, o2, cp.gz, cp.gzl, cp.gzr)",
-                 3: "VVV1_0<R>(o0, o1, o2, K + 4 * a.k[0], K + 4 * a.k[1], K + 4 * a.k[2], cp.gs)",
-                 4: "VVVV_0<R>(0, o0, o1, o2, o3, cp.gs2)", 5: "VVVV_0<R>(1, o0, o1, o2, o3, cp.gs2)",
-                 6: "VVVV_0<R>(2, o0, o1, o2, o3, cp.gs2)"}
-        lines = ["  // amplitudes of one (event, helicity): operands cur[sl[c * NHEL]], flows into J",
+    def _contract_code(self) -> list:
+        """Contractions of one chunk for one (event, helicity), straight-line: every
+        operand offset and variant-table entry is a constant, so the loads of
+        successive amplitudes are independent; each amplitude goes straight into
+        its colour flows J_s (+amp, -amp, +i amp, -i amp)."""
+        nh = 1 << self.n
+        ALL = (1 << self.n) - 1
+        ops = {0: "J[%d] += a;", 1: "J[%d] -= a;", 2: "J[%d] += mul_i(a);", 3: "J[%d] -= mul_i(a);"}
+        lines = ["  // A = sum_i X_i Y_i for the amplitudes of chunk c: X = xb[X slot + variant],",
+                 "  // Y = cur[Y slot + variant], variant of a leg set S for this helicity = vt[S * NHEL]",
                  "  template <class R>",
-                 "  static __device__ __forceinline__ void hs_amplitudes(const W4<R>* __restrict__ cur,"
-                 " const uint16_t* __restrict__ sl, const R* __restrict__ K, const Couplings<R>& cp, cx<R>* J) {",
-                 "    W4<R> o0, o1, o2, o3;"]
-        start = 0
-        for t in sorted(self.groups):
-            n = self.groups[t]
-            nops = 4 if t >= 4 else 3
-            lines.append("    {  // type %d: %d amplitudes" % (t, n))
-            lines.append("      int l0 = -1, l1 = -1;")
-            lines.append("      for (int d = %d; d < %d; ++d) {" % (start, start + n))
-            lines.append("        const HsAmp a = kHsAmps%d[d];" % pid)
-            lines.append("        if (a.op[0] != l0) { o0 = cur[sl[a.op[0] * NHEL]]; l0 = a.op[0]; }")
-            lines.append("        if (a.op[1] != l1) { o1 = cur[sl[a.op[1] * NHEL]]; l1 = a.op[1]; }")
-            lines.append("        o2 = cur[sl[a.op[2] * NHEL]];")
-            if nops == 4:
-                lines.append("        o3 = cur[sl[a.op[3] * NHEL]];")
-            lines.append("        hs_flows<R>(a.pat, %s, J);" % calls[t])
-            lines.append("      }")
-            lines.append("    }")
-            start += n
-        lines.append("  }")
-        return lines
-
-    def _flow_switch(self) -> list:
-        """J_s +=, -=, += i, -= i amp for the colour flows of amplitude pattern `pat`."""
-        ops = {0: "J[%d] += amp;", 1: "J[%d] -= amp;", 2: "J[%d] += mul_i(amp);", 3: "J[%d] -= mul_i(amp);"}
-        lines = ["  static constexpr int HS_NPAT = %d;" % len(self.patterns),
-                 "  // colour-flow updates of each amplitude pattern: J_s += amp, -amp, i amp, -i amp",
-                 "  template <class R>",
-                 "  static __device__ __forceinline__ void hs_flows(int pat, cx<R> amp, cx<R>* J) {",
-                 "    switch (pat) {"]
-        for key, pat in sorted(self.patterns.items(), key=lambda kv: kv[1]):
-            lines.append("      case %d: %s break;" % (pat, " ".join(ops[f >> 6] % (f & 63) for f in key)))
+                 "  static __device__ __forceinline__ void hs_contract(int c, const W4<R>* __restrict__ cur,"
+                 " const W4<R>* __restrict__ xb, const uint8_t* __restrict__ vt, cx<R>* J) {",
+                 "    switch (c) {"]
+        for c in range(len(self.chunks)):
+            lines.append("      case %d: {" % c)
+            last_x = None
+            for (ch, xo, yo, pat, xset, flows) in self.amp_list:
+                if ch != c:
+                    continue
+                if xo != last_x:
+                    if last_x is not None:
+                        lines.append("        }")
+                    lines.append("        {")
+                    lines.append("          const W4<R> X = xb[%d + vt[%d]];" % (xo, xset * nh))
+                    last_x = xo
+                lines.append("          { const cx<R> a = dot4(X, cur[%d + vt[%d]]); %s }"
+                             % (yo, (ALL ^ xset) * nh, " ".join(ops[f >> 6] % (f & 63) for f in flows)))
+            if last_x is not None:
+                lines.append("        }")
+            lines.append("      } break;")
         lines += ["      default: break;", "    }", "  }"]
         return lines
-
