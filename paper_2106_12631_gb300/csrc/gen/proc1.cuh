@@ -36,8 +36,8 @@ struct Proc1 {
   static __device__ __forceinline__ const HsItem* hs_items() { return kHsItems1; }
   // A = sum_i X_i Y_i for the amplitudes of chunk c: X = xb[X slot + variant],
   // Y = cur[Y slot + variant], variant of a leg set S for this helicity = vt[S * NHEL]
-  template <class R>
-  static __device__ __forceinline__ void hs_contract(int c, const W4<R>* __restrict__ cur, const W4<R>* __restrict__ xb, const uint8_t* __restrict__ vt, cx<R>* J) {
+  template <class R, class CUR, class XB>
+  static __device__ __forceinline__ void hs_contract(int c, const CUR& cur, const XB& xb, const uint8_t* __restrict__ vt, cx<R>* J) {
     switch (c) {
       case 0: {
         {

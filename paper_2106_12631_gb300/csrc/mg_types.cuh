@@ -37,6 +37,28 @@ struct alignas(16) W4 {
   cx<R> w[4];
 };
 
+// An array of N wavefunction slots stored as 16-byte planes: plane k holds
+// bytes [16k, 16k + 16) of every slot.  Threads that read consecutive slots
+// then touch consecutive 16-byte words of shared memory (no bank conflicts),
+// and threads that read the same slot share one access.
+template <class R, int N>
+struct Slots {
+  static constexpr int NPL = (int)(sizeof(W4<R>) / 16);
+  uint4* p;
+  __device__ __forceinline__ W4<R> operator[](int i) const {
+    W4<R> w;
+    uint4* d = reinterpret_cast<uint4*>(&w);
+#pragma unroll
+    for (int k = 0; k < NPL; ++k) d[k] = p[i + k * N];
+    return w;
+  }
+  __device__ __forceinline__ void set(int i, const W4<R>& w) const {
+    const uint4* s = reinterpret_cast<const uint4*>(&w);
+#pragma unroll
+    for (int k = 0; k < NPL; ++k) p[i + k * N] = s[k];
+  }
+};
+
 // Couplings and masses in the working precision.
 template <class R>
 struct Couplings {

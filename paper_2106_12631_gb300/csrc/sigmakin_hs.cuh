@@ -208,8 +208,8 @@ __device__ __forceinline__ void hs_event_tables(unsigned char* smem, const SigAr
 
 // one current variant
 template <class P, class R>
-__device__ __forceinline__ void hs_item(const HsItem& it, W4<R>* cur, const R* K, const cx<R>* pr,
-                                        const Couplings<R>& cp) {
+__device__ __forceinline__ void hs_item(const HsItem& it, const Slots<R, P::HS_NSLOT>& cur, const R* K,
+                                        const cx<R>* pr, const Couplings<R>& cp) {
   W4<R> o;
   switch (it.type) {
     case 0: o = ixxxxx<R>(K + 4 * it.k0, it.flag ? cp.mt : R(0), it.b, it.c); break;
@@ -224,13 +224,13 @@ __device__ __forceinline__ void hs_item(const HsItem& it, W4<R>* cur, const R* K
       o = vvvv_comb(cur[it.in[0]], vdot(cur[it.in[1]], cur[it.in[2]]), cur[it.in[3]],
                     vdot(cur[it.in[4]], cur[it.in[5]]), mul_mi(cp.gs2 * pr[it.prop]));
   }
-  cur[it.out] = o;
+  cur.set(it.out, o);
 }
 
 // one amputated-current variant (reads the currents, writes the chunk buffer)
 template <class P, class R>
-__device__ __forceinline__ void hs_xitem(const HsItem& it, const W4<R>* cur, W4<R>* xb, const R* K,
-                                         const Couplings<R>& cp) {
+__device__ __forceinline__ void hs_xitem(const HsItem& it, const Slots<R, P::HS_NSLOT>& cur,
+                                         const Slots<R, P::HS_XCAP>& xb, const R* K, const Couplings<R>& cp) {
   W4<R> o;
   switch (it.type) {
     case 9: o = FFV1_2A<R>(cur[it.in[0]], cur[it.in[1]], cp.gs); break;
@@ -242,7 +242,7 @@ __device__ __forceinline__ void hs_xitem(const HsItem& it, const W4<R>* cur, W4<
       o = vvvv_comb_a(cur[it.in[0]], vdot(cur[it.in[1]], cur[it.in[2]]), cur[it.in[3]],
                       vdot(cur[it.in[4]], cur[it.in[5]]), cp.gs2);
   }
-  xb[it.out] = o;
+  xb.set(it.out, o);
 }
 
 template <class P, class R, int CS>
@@ -255,8 +255,10 @@ __global__ void __launch_bounds__(HsCfg<P, R>::NT, 1) sigmakin_hs_kernel(SigArgs
   int* misc = reinterpret_cast<int*>(smem + L::o_misc);
   double* sm2 = reinterpret_cast<double*>(smem + L::o_m2);
   uint8_t* vtab = reinterpret_cast<uint8_t*>(smem + L::o_vt);
-  W4<R>* curs = reinterpret_cast<W4<R>*>(smem + L::o_cur);
-  W4<R>* xbufs = reinterpret_cast<W4<R>*>(smem + L::o_x);
+  // per event: HS_NSLOT current slots, HS_XCAP amputated slots (16-byte planes)
+  uint4* curs = reinterpret_cast<uint4*>(smem + L::o_cur);
+  uint4* xbufs = reinterpret_cast<uint4*>(smem + L::o_x);
+  constexpr int CUR_EV = P::HS_NSLOT * Slots<R, 1>::NPL, X_EV = P::HS_XCAP * Slots<R, 1>::NPL;
   const int tid = threadIdx.x;
   load_tables<P, L>(smem);
   if (tid == 0) {
@@ -304,16 +306,17 @@ __global__ void __launch_bounds__(HsCfg<P, R>::NT, 1) sigmakin_hs_kernel(SigArgs
   }
   const R* Kall = reinterpret_cast<const R*>(smem + L::o_K);
   const cx<R>* prall = reinterpret_cast<const cx<R>*>(smem + L::o_pr);
-  // 2. current variants, level by level; consecutive threads take the same
-  //    item for consecutive events
+  // 2. current variants, level by level; consecutive threads take consecutive
+  //    items (variants) of one event
   const HsItem* items = P::hs_items();
 #pragma unroll
   for (int l = 0; l < P::HS_NLEVEL; ++l) {
-    const int i0 = P::hs_level(l), n = (P::hs_level(l + 1) - i0) * nev;
+    const int i0 = P::hs_level(l), ni = P::hs_level(l + 1) - i0, n = ni * nev;
     for (int t = tid; t < n; t += NT) {
-      const int e = t % nev;
-      const HsItem it = items[i0 + t / nev];
-      hs_item<P, R>(it, curs + e * P::HS_NSLOT, Kall + e * P::NMOM * 4, prall + e * P::NPROP, cp);
+      const int e = t / ni;
+      const HsItem it = items[i0 + t - e * ni];
+      hs_item<P, R>(it, Slots<R, P::HS_NSLOT>{curs + e * CUR_EV}, Kall + e * P::NMOM * 4, prall + e * P::NPROP,
+                    cp);
     }
     __syncthreads();
   }
@@ -328,14 +331,16 @@ __global__ void __launch_bounds__(HsCfg<P, R>::NT, 1) sigmakin_hs_kernel(SigArgs
 #pragma unroll 1
   for (int c = 0; c < P::HS_NXCHUNK; ++c) {
     if (c > 0) __syncthreads();  // the previous chunk's contractions are done with the buffer
-    const int i0 = P::hs_xitem(c), n = (P::hs_xitem(c + 1) - i0) * nev;
+    const int i0 = P::hs_xitem(c), ni = P::hs_xitem(c + 1) - i0, n = ni * nev;
     for (int t = tid; t < n; t += NT) {
-      const int ex = t % nev;
-      const HsItem it = items[i0 + t / nev];
-      hs_xitem<P, R>(it, curs + ex * P::HS_NSLOT, xbufs + ex * P::HS_XCAP, Kall + ex * P::NMOM * 4, cp);
+      const int ex = t / ni;
+      const HsItem it = items[i0 + t - ex * ni];
+      hs_xitem<P, R>(it, Slots<R, P::HS_NSLOT>{curs + ex * CUR_EV}, Slots<R, P::HS_XCAP>{xbufs + ex * X_EV},
+                     Kall + ex * P::NMOM * 4, cp);
     }
     __syncthreads();
-    P::template hs_contract<R>(c, curs + e * P::HS_NSLOT, xbufs + e * P::HS_XCAP, vtab + ih, J);
+    P::template hs_contract<R>(c, Slots<R, P::HS_NSLOT>{curs + e * CUR_EV}, Slots<R, P::HS_XCAP>{xbufs + e * X_EV},
+                               vtab + ih, J);
   }
   // 4. colour sum and helicity sum
   double m2;
