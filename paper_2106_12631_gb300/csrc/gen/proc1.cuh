@@ -69,6 +69,11 @@ struct Proc1 {
     constexpr int t[NPROP][2] = {{4, 2}, {4, 3}};
     return t[j][k];
   }
+  // propagator entries formed from each momentum entry (-1: none)
+  static __host__ __device__ constexpr int mom_prop(int j, int k) {
+    constexpr int t[NMOM][2] = {{-1, -1}, {-1, -1}, {-1, -1}, {-1, -1}, {0, 1}};
+    return t[j][k];
+  }
   static __device__ __forceinline__ const uint32_t* colour_bf16_image() { return kColourB1; }
   // colour matrix = CNUM / CDEN (real symmetric)
   static constexpr int CDEN = 1;

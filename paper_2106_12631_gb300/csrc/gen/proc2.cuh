@@ -73,6 +73,11 @@ struct Proc2 {
     constexpr int t[NPROP][2] = {{6, 0}, {7, 1}, {8, 1}};
     return t[j][k];
   }
+  // propagator entries formed from each momentum entry (-1: none)
+  static __host__ __device__ constexpr int mom_prop(int j, int k) {
+    constexpr int t[NMOM][2] = {{-1, -1}, {-1, -1}, {-1, -1}, {-1, -1}, {-1, -1}, {-1, -1}, {0, -1}, {1, -1}, {2, -1}};
+    return t[j][k];
+  }
   static __device__ __forceinline__ const uint32_t* colour_bf16_image() { return kColourB2; }
   // colour matrix = CNUM / CDEN (real symmetric)
   static constexpr int CDEN = 3;

@@ -118,6 +118,11 @@ struct Proc3 {
     constexpr int t[NPROP][2] = {{5, 0}, {8, 0}, {10, 1}, {11, 1}, {12, 1}, {13, 1}, {14, 0}, {15, 1}, {16, 0}, {17, 1}};
     return t[j][k];
   }
+  // propagator entries formed from each momentum entry (-1: none)
+  static __host__ __device__ constexpr int mom_prop(int j, int k) {
+    constexpr int t[NMOM][2] = {{-1, -1}, {-1, -1}, {-1, -1}, {-1, -1}, {-1, -1}, {0, -1}, {-1, -1}, {-1, -1}, {1, -1}, {-1, -1}, {2, -1}, {3, -1}, {4, -1}, {5, -1}, {6, -1}, {7, -1}, {8, -1}, {9, -1}, {-1, -1}, {-1, -1}, {-1, -1}};
+    return t[j][k];
+  }
   static __device__ __forceinline__ const uint32_t* colour_bf16_image() { return kColourB3; }
   // colour matrix = CNUM / CDEN (real symmetric)
   static constexpr int CDEN = 9;

@@ -26,6 +26,9 @@ namespace mg {
 #ifndef MG_HS_NT
 #define MG_HS_NT 512
 #endif
+#ifndef MG_HS_CTAS
+#define MG_HS_CTAS 1  // resident CTAs per SM the shared-memory budget is split for
+#endif
 
 // One large CTA per SM for the many-colour processes: its warps walk the same
 // amplitude table in near lockstep and share instruction fetches.  FP64 needs
@@ -36,7 +39,8 @@ struct HsCfg {
   static constexpr int EVMIN = (NT / P::NHEL) > 0 ? (NT / P::NHEL) : 1;
   static constexpr int EVWANT = (4 * EVMIN) < 32 ? 4 * EVMIN : 32;
   // shared memory for the current variants and one chunk of amputated currents
-  static constexpr size_t CUR_BUDGET = 192 * 1024;
+  static constexpr int CTAS = P::NCOLOR >= 6 && sizeof(R) == 4 ? MG_HS_CTAS : 1;
+  static constexpr size_t CUR_BUDGET = 192 * 1024 / CTAS;
   static constexpr size_t EV_BYTES = (size_t)(P::HS_NSLOT + P::HS_XCAP) * sizeof(W4<R>);
   static constexpr int FIT = (int)(CUR_BUDGET / EV_BYTES);
   static constexpr int EVCAP = FIT < EVWANT ? (FIT > EVMIN ? FIT : EVMIN) : EVWANT;
@@ -50,8 +54,7 @@ struct HsLayout {
   using H = HsCfg<P, R>;
   static constexpr int NT = H::NT, EVCAP = H::EVCAP, KP = H::KP, NP = H::NP, MBLK = H::MBLK;
   static constexpr bool TC = CS == CS_TC;
-  static constexpr size_t o_momtab = 0;
-  static constexpr size_t o_proptab = align_up(o_momtab + 12 * P::NMOM, 16);
+  static constexpr size_t o_proptab = 0;  // {momentum entry, line kind} per propagator
   static constexpr size_t o_good = align_up(o_proptab + 8 * P::NPROP, 16);
   static constexpr size_t o_misc = align_up(o_good + 4 * P::NHEL, 16);
   static constexpr size_t o_p = align_up(o_misc + 32, 16);
@@ -66,6 +69,9 @@ struct HsLayout {
   static constexpr size_t o_cur = o_U;
   static constexpr size_t o_x = o_U + sizeof(W4<R>) * EVCAP * P::HS_NSLOT;
   static constexpr size_t o_A = o_U;
+  // FP64 momentum sums of phase 1 (the amputated buffer is free then)
+  static constexpr size_t o_Kd = o_x;
+  static_assert(8 * EVCAP * P::NMOM * 4 <= sizeof(W4<R>) * EVCAP * P::HS_XCAP, "FP64 sums overflow their scratch");
   static constexpr size_t tileA = 128 * KP * 2;
   static constexpr size_t u_bytes = sizeof(W4<R>) * EVCAP * (P::HS_NSLOT + P::HS_XCAP);
   static constexpr size_t a_bytes = TC ? 3 * MBLK * tileA : 0;  // one component's three splits
@@ -167,41 +173,112 @@ __device__ __forceinline__ float colour_sum_tc_regs(unsigned char* smem, const c
   return s;
 }
 
-// Phase 1 with this kernel's thread count (same arithmetic as event_tables).
+// |M_h|^2 = J^dagger C J / CDEN on CUDA cores with C real symmetric:
+//   sum_i J_i^* (C_ii J_i + 2 sum_{j>i} C_ij J_j)  (real part; the imaginary parts cancel)
+// — each off-diagonal entry once, half the multiply-adds of the row-wise form.
+template <class P>
+__host__ __device__ constexpr bool colour_matrix_symmetric() {
+  for (int i = 0; i < P::NCOLOR; ++i)
+    for (int j = 0; j < i; ++j)
+      if (P::cnum(i, j) != P::cnum(j, i)) return false;
+  return true;
+}
+template <class P, class R>
+__device__ __forceinline__ R colour_sum_sym(const cx<R>* J) {
+  static_assert(colour_matrix_symmetric<P>(), "colour matrix must be symmetric");
+  constexpr int NC = P::NCOLOR;
+  R sum = R(0);
+#pragma unroll
+  for (int i = 0; i < NC; ++i) {
+    R ur = R(P::cnum(i, i)) * J[i].re, ui = R(P::cnum(i, i)) * J[i].im;
+#pragma unroll
+    for (int j = i + 1; j < NC; ++j) {
+      if (P::cnum(i, j) == 0) continue;
+      ur += R(2 * P::cnum(i, j)) * J[j].re;
+      ui += R(2 * P::cnum(i, j)) * J[j].im;
+    }
+    sum += J[i].re * ur + J[i].im * ui;
+  }
+  return sum / R(P::CDEN);
+}
+
+// Propagator factor of one line from its FP64 momentum: the invariant
+// k^2 - m^2 is formed in FP64 (it cancels near the pole and for collinear
+// pairs); the reciprocal 1/(k^2 - m^2 + i m w) times i (fermion) or -i (vector)
+// is taken in the working precision.
+template <class R>
+__device__ __forceinline__ cx<R> propagator_hs(const double* k, int kind, const PhysParams& pp) {
+  const double k2 = k[0] * k[0] - k[1] * k[1] - k[2] * k[2] - k[3] * k[3];
+  double dr = k2, di = 0.0;
+  if (kind == 1) { dr = k2 - pp.mt * pp.mt; di = pp.mt * pp.wt; }
+  else if (kind == 3) { dr = k2 - pp.mz * pp.mz; di = pp.mz * pp.wz; }
+  const R r = R(dr), i = R(di);
+  const R inv = R(1) / (r * r + i * i);
+  const R ar = r * inv, ai = -i * inv;
+  return kind == 1 ? cx<R>(-ai, ar) : cx<R>(ai, -ar);
+}
+
+// Phase 1: momenta; momentum-table entries as FP64 signed sums of the external
+// momenta (one thread per (event, component) walks all entries with the leg
+// masks known at compile time: |S| - 1 additions per entry, no wasted FP64
+// work), rounded to R and kept in FP64 for the propagators; the external
+// wavefunctions (level 0 of the current program) straight from the momenta;
+// then the propagator of every line (one thread per (event, propagator)).
 template <class P, class R, class L>
-__device__ __forceinline__ void hs_event_tables(unsigned char* smem, const SigArgs& a, int64_t e0, int nev) {
+__device__ __forceinline__ void hs_event_tables(unsigned char* smem, const SigArgs& a, int64_t e0, int nev,
+                                                uint4* curs, const Couplings<R>& cp) {
   constexpr int NT = L::NT;
+  constexpr int NEXT = P::hs_level(1);  // external variants
+  constexpr int CUR_EV = P::HS_NSLOT * Slots<R, 1>::NPL;
   const int tid = threadIdx.x;
   auto p = reinterpret_cast<double(*)[P::NPAR][4]>(smem + L::o_p);
   auto K = reinterpret_cast<R(*)[P::NMOM][4]>(smem + L::o_K);
+  auto Kd = reinterpret_cast<double(*)[P::NMOM][4]>(smem + L::o_Kd);
   auto pr = reinterpret_cast<cx<R>(*)[P::NPROP]>(smem + L::o_pr);
-  const int(*mom_tab)[3] = reinterpret_cast<const int(*)[3]>(smem + L::o_momtab);
-  const int(*prop_tab)[2] = reinterpret_cast<const int(*)[2]>(smem + L::o_proptab);
+  const int2* prop_tab = reinterpret_cast<const int2*>(smem + L::o_proptab);
   for (int t = tid; t < nev * P::NPAR * 4; t += NT) {
     const int e = t % nev, c = t / nev;
     p[e][c >> 2][c & 3] = a.mom[(int64_t)c * a.nevt + e0 + e];
   }
   __syncthreads();
-  for (int t = tid; t < nev * (P::NMOM + P::NPROP); t += NT) {
-    const int e = t % nev, j = t / nev;
-    const int mj = j < P::NMOM ? j : prop_tab[j - P::NMOM][0];
-    const int kind = mom_tab[mj][0], lmask = mom_tab[mj][1], smask = mom_tab[mj][2];
-    double k[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int t = tid; t < nev * (4 + NEXT); t += NT) {
+    if (t < nev * 4) {
+      const int e = t >> 2, mu = t & 3;
+      double q[P::NPAR];
 #pragma unroll
-    for (int l = 0; l < P::NPAR; ++l) {
-      if (!(lmask >> l & 1)) continue;
-      const double sg = (kind == 1 && (smask >> l & 1)) ? -1.0 : 1.0;
+      for (int l = 0; l < P::NPAR; ++l) q[l] = p[e][l][mu];
 #pragma unroll
-      for (int mu = 0; mu < 4; ++mu) k[mu] += sg * p[e][l][mu];
-    }
-    if (j < P::NMOM) {
+      for (int j = 0; j < P::NMOM; ++j) {
+        double k = 0.0;
+        bool first = true;
 #pragma unroll
-      for (int mu = 0; mu < 4; ++mu) K[e][j][mu] = R(k[mu]);
+        for (int l = 0; l < P::NPAR; ++l) {
+          if (!(P::mom(j, 1) >> l & 1)) continue;
+          const bool neg = P::mom(j, 0) == 1 && (P::mom(j, 2) >> l & 1);
+          k = first ? (neg ? -q[l] : q[l]) : (neg ? k - q[l] : k + q[l]);
+          first = false;
+        }
+        K[e][j][mu] = R(k);
+        Kd[e][j][mu] = k;
+      }
     } else {
-      double re, im;
-      propagator_fp64(k, prop_tab[j - P::NMOM][1], a.pp, re, im);
-      pr[e][j - P::NMOM] = cx<R>(R(re), R(im));
+      const int t2 = t - nev * 4, e = t2 / NEXT;
+      const HsItem it = P::hs_items()[t2 - e * NEXT];
+      R k[4];
+#pragma unroll
+      for (int mu = 0; mu < 4; ++mu) k[mu] = R(p[e][it.a][mu]);
+      W4<R> o;
+      if (it.type == 0) o = ixxxxx<R>(k, it.flag ? cp.mt : R(0), it.b, it.c);
+      else if (it.type == 1) o = oxxxxx<R>(k, it.flag ? cp.mt : R(0), it.b, it.c);
+      else o = vxxxxx<R>(k, it.b, it.c);
+      Slots<R, P::HS_NSLOT>{curs + e * CUR_EV}.set(it.out, o);
     }
+  }
+  __syncthreads();
+  for (int t = tid; t < nev * P::NPROP; t += NT) {
+    const int e = t / P::NPROP, j = t - e * P::NPROP;
+    const int2 m = prop_tab[j];  // momentum entry, line kind
+    pr[e][j] = propagator_hs<R>(Kd[e][m.x], m.y, a.pp);
   }
   __syncthreads();
 }
@@ -246,7 +323,7 @@ __device__ __forceinline__ void hs_xitem(const HsItem& it, const Slots<R, P::HS_
 }
 
 template <class P, class R, int CS>
-__global__ void __launch_bounds__(HsCfg<P, R>::NT, 1) sigmakin_hs_kernel(SigArgs a, Couplings<R> cp) {
+__global__ void __launch_bounds__(HsCfg<P, R>::NT, HsCfg<P, R>::CTAS) sigmakin_hs_kernel(SigArgs a, Couplings<R> cp) {
   using C = HsCfg<P, R>;
   using L = HsLayout<P, R, CS>;
   constexpr int NT = C::NT, NC = P::NCOLOR;
@@ -260,13 +337,18 @@ __global__ void __launch_bounds__(HsCfg<P, R>::NT, 1) sigmakin_hs_kernel(SigArgs
   uint4* xbufs = reinterpret_cast<uint4*>(smem + L::o_x);
   constexpr int CUR_EV = P::HS_NSLOT * Slots<R, 1>::NPL, X_EV = P::HS_XCAP * Slots<R, 1>::NPL;
   const int tid = threadIdx.x;
-  load_tables<P, L>(smem);
-  if (tid == 0) {
-    int n = 0;
-    for (int h = 0; h < P::NHEL; ++h)
-      if (a.mask[h]) good[n++] = h;
-    misc[0] = n;
+  if (tid < P::NPROP) {
+    int2 v = make_int2(0, 0);
+#pragma unroll
+    for (int j = 0; j < P::NPROP; ++j)
+      if (tid == j) v = make_int2(P::prop(j, 0), P::prop(j, 1));
+    reinterpret_cast<int2*>(smem + L::o_proptab)[tid] = v;
   }
+  // good helicities: one ballot word per 32 helicities in misc[2..3]
+  static_assert(P::NHEL <= 64 && NT >= P::NHEL, "helicity ballot layout");
+  const bool hgood = tid < P::NHEL && a.mask[tid] != 0;
+  const unsigned hb = __ballot_sync(0xffffffffu, hgood);
+  if (tid < P::NHEL && (tid & 31) == 0) misc[2 + (tid >> 5)] = (int)hb;
   // vt[S][ihel]: bits of the legs in S (ascending) of helicity ihel, where
   // leg l is +1 when bit NPAR-1-l of ihel is set
   for (int i = tid; i < (1 << P::NPAR) * P::NHEL; i += NT) {
@@ -278,7 +360,10 @@ __global__ void __launch_bounds__(HsCfg<P, R>::NT, 1) sigmakin_hs_kernel(SigArgs
     vtab[i] = (uint8_t)v;
   }
   __syncthreads();
-  const int ng = misc[0];
+  // good[] in helicity order (read only after later barriers)
+  const unsigned w0 = (unsigned)misc[2], w1 = P::NHEL > 32 ? (unsigned)misc[3] : 0u;
+  if (hgood) good[__popc(hb & ((1u << (tid & 31)) - 1u)) + (tid >= 32 ? __popc(w0) : 0)] = tid;
+  const int ng = __popc(w0) + __popc(w1);
   const int ev = ng > 0 ? min(L::EVCAP, NT / ng) : C::EVMIN;
   const int64_t e0 = (int64_t)blockIdx.x * ev;
   if (e0 >= a.nevt) return;
@@ -299,18 +384,18 @@ __global__ void __launch_bounds__(HsCfg<P, R>::NT, 1) sigmakin_hs_kernel(SigArgs
     tc::fence_before_sync();
   }
   // 1. momenta and per-event tables
-  hs_event_tables<P, R, L>(smem, a, e0, nev);
+  hs_event_tables<P, R, L>(smem, a, e0, nev, curs, cp);
   if constexpr (L::TC) {
     tc::fence_after_sync();
     tmem = static_cast<uint32_t>(misc[1]);
   }
   const R* Kall = reinterpret_cast<const R*>(smem + L::o_K);
   const cx<R>* prall = reinterpret_cast<const cx<R>*>(smem + L::o_pr);
-  // 2. current variants, level by level; consecutive threads take consecutive
-  //    items (variants) of one event
+  // 2. current variants, level by level (level 0, the external wavefunctions,
+  //    came with phase 1); consecutive threads take consecutive items of one event
   const HsItem* items = P::hs_items();
 #pragma unroll
-  for (int l = 0; l < P::HS_NLEVEL; ++l) {
+  for (int l = 1; l < P::HS_NLEVEL; ++l) {
     const int i0 = P::hs_level(l), ni = P::hs_level(l + 1) - i0, n = ni * nev;
     for (int t = tid; t < n; t += NT) {
       const int e = t / ni;
@@ -348,7 +433,7 @@ __global__ void __launch_bounds__(HsCfg<P, R>::NT, 1) sigmakin_hs_kernel(SigArgs
     __syncthreads();  // the A tiles overwrite the current variants
     m2 = (double)colour_sum_tc_regs<P, L>(smem, J, tmem, mbar);
   } else {
-    m2 = (double)colour_sum_simt<P, R>([&](int s) { return J[s].re; }, [&](int s) { return J[s].im; });
+    m2 = (double)colour_sum_sym<P, R>(J);
   }
   sm2[tid] = active ? m2 : 0.0;
   if constexpr (L::TC) tc::fence_before_sync();

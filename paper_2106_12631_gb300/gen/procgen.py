@@ -372,6 +372,15 @@ FLOPS = {
 }
 
 
+def colour_sum_sym_flops(cnum) -> int:
+    """J^dagger C J / CDEN with the symmetric form: per row the diagonal term
+    (2 multiplies), two multiply-adds per non-zero upper entry, the row's
+    re/im products into the sum (4), and the final scale."""
+    nc = cnum.shape[0]
+    upper = sum(1 for i in range(nc) for j in range(i + 1, nc) if cnum[i, j] != 0)
+    return 2 * nc + 4 * upper + 4 * nc + 1
+
+
 def colour_sum_flops(cnum) -> int:
     """Real colour sum J^dagger C J with C = CNUM / CDEN on CUDA cores: per row
     two FMAs per non-zero entry, then re/im products, the row sum and the scale."""
@@ -790,6 +799,15 @@ def generate(pid: int) -> str:
     out.append("    constexpr int t[NPROP][2] = {%s};" % ", ".join(prows))
     out.append("    return t[j][k];")
     out.append("  }")
+    pof = [[-1, -1] for _ in em.mom]
+    for pi, (mi, _) in enumerate(em.props):
+        slot = pof[mi].index(-1)  # at most two lines (photon and Z) share one momentum
+        pof[mi][slot] = pi
+    out.append("  // propagator entries formed from each momentum entry (-1: none)")
+    out.append("  static __host__ __device__ constexpr int mom_prop(int j, int k) {")
+    out.append("    constexpr int t[NMOM][2] = {%s};" % ", ".join("{%d, %d}" % tuple(r) for r in pof))
+    out.append("    return t[j][k];")
+    out.append("  }")
     out.append("  static __device__ __forceinline__ const uint32_t* colour_bf16_image() { return kColourB%d; }" % pid)
     out.append("  // colour matrix = CNUM / CDEN (real symmetric)")
     out.append("  static constexpr int CDEN = %d;" % em.cden)
@@ -829,7 +847,8 @@ def summary(pid: int) -> dict:
     em.emit()
     sp = SharedProgram(proc, em)
     sp.emit_tables(pid)
-    return dict(flops_amp=em.flops, flops_csum=colour_sum_flops(em.cnum), ncurrents=em.ncurrents,
+    return dict(flops_amp=em.flops, flops_csum=colour_sum_flops(em.cnum),
+                flops_csum_sym=colour_sum_sym_flops(em.cnum), ncurrents=em.ncurrents,
                 hs_flops_items=sp.flops_items, hs_flops_amp_hel=sp.flops_amps_hel, hs_ncur=len(sp.order),
                 hs_nslots=sp.nslots, hs_nx=len(sp.xoff), hs_xcap=sp.xcap, hs_nxchunk=len(sp.chunks),
                 ndiagrams=proc.ndiagrams, namps=len(proc.amps), ncolor=em.coef.shape[1],
