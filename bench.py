@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
-    ap.add_argument("--mode", default="mixed", choices=["mixed", "mixed_simt", "fp64", "mixed_unrolled",
+    ap.add_argument("--mode", default="mixed", choices=["mixed", "mixed_simt", "mixed_tc", "fp64", "mixed_unrolled",
                                                         "fp64_unrolled"])
     ap.add_argument("--nevt", type=int, default=1 << 20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -81,6 +81,31 @@ def dist_init(args):
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
     return rank, world, local
+
+
+def shard_first_event(rank: int, nevt: int) -> int:
+    """First event index of a rank's batch: ranks take disjoint, contiguous
+    ranges of the counter-based random stream (weak scaling)."""
+    return rank * nevt
+
+
+def max_over_ranks(seconds: float, world: int, dev) -> float:
+    """The job's time: the slowest rank's."""
+    if world == 1:
+        return seconds
+    import torch
+    t = torch.tensor([seconds], dtype=torch.float64, device=dev)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(sums, world: int):
+    """The path's one exchange: the event sums (sum w me, sum (w me)^2, N) of
+    all ranks, added in place."""
+    if world > 1:
+        import torch
+        torch.distributed.all_reduce(sums, op=torch.distributed.ReduceOp.SUM)
+    return sums
 
 
 def measured_peaks():
@@ -247,7 +272,7 @@ def main():
     proc, ecm, nevt = 4, 1500.0, args.nevt
     seed = I.seed_of(WORKLOAD)
     # inputs resident in HBM: this rank's own event range
-    rnd = torch.from_numpy(I.uniforms(seed, 16, nevt, first_event=rank * nevt)).to(dev)
+    rnd = torch.from_numpy(I.uniforms(seed, 16, nevt, first_event=shard_first_event(rank, nevt))).to(dev)
     frnd = torch.from_numpy(I.uniforms(I.filter_seed_of(WORKLOAD), 16, 16)).to(dev)
     info = mg.process_info(proc)
     mom = torch.empty((info["npar"], 4, nevt), dtype=torch.float64, device=dev)
@@ -261,10 +286,16 @@ def main():
     stream = torch.cuda.current_stream()
     kernel_launches_per_step = 6  # rambo(filter), filter, rambo, sigmakin, event_sum x2
 
+    side = torch.cuda.Stream()
+
     def step(mode, ev=None):
+        # the batch's RAMBO (side stream) overlaps the helicity filter (main stream);
+        # it may overwrite mom only after the previous step's SIGMAKIN
+        side.wait_stream(stream)
         mg.rambo(proc, frnd, ecm, mom=fmom, wgt=fwgt, stream=stream)
         mg.filter_helicities(proc, fmom, mask=mask, stream=stream)
-        mg.rambo(proc, rnd, ecm, mom=mom, wgt=wgt, stream=stream)
+        mg.rambo(proc, rnd, ecm, mom=mom, wgt=wgt, stream=side)
+        stream.wait_stream(side)
         if ev is not None:
             ev[0].record(stream)
         mg.sigmakin(proc, mom, mask, mode=mode, me=me, stream=stream)
@@ -293,11 +324,7 @@ def main():
         barrier()
         total = t0.elapsed_time(t1) / 1e3
         kern = [a.elapsed_time(b) / 1e3 for a, b in kev]
-        if world > 1:
-            t = torch.tensor([total], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            total = float(t.item())
-        return total, kern
+        return max_over_ranks(total, world, dev), kern
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -315,6 +342,13 @@ def main():
         unrolled = {"mode": args.mode + "_unrolled", "value": world * nevt * max(1, min(args.steps, 2)) / tu,
                     "unit": UNIT, "sigmakin_ms": 1e3 * statistics.mean(ku)}
 
+    # the same step with the colour sum on the tensor cores (split-BF16 tcgen05)
+    tensor_core = None
+    if args.mode == "mixed" and not args.no_others:
+        tt, kt = timed("mixed_tc", max(1, min(args.steps, 2)))
+        tensor_core = {"mode": "mixed_tc", "value": world * nevt * max(1, min(args.steps, 2)) / tt, "unit": UNIT,
+                       "sigmakin_ms": 1e3 * statistics.mean(kt)}
+
     fp64 = None
     if not args.no_fp64 and args.mode != "fp64":
         t64, k64 = timed("fp64", max(1, min(args.steps, 2)))
@@ -331,35 +365,45 @@ def main():
     # the other workloads (SIGMAKIN or the adjoint alone, inputs resident, CUDA events)
     others = {} if args.no_others else measure_other_workloads(mg, I, dev, stream)
 
-    # end to end through the C ABI with host buffers (H2D of the random numbers,
-    # D2H of the matrix elements inside the timed region)
-    rnd_h = torch.from_numpy(I.uniforms(seed, 16, nevt, first_event=rank * nevt)).pin_memory()
+    # end to end through the C ABI with host buffers: every step copies the
+    # filter events' and the batch's random numbers from pinned host memory,
+    # filters the helicities, runs RAMBO + SIGMAKIN + the event sum, and reads
+    # me and the event sum back
+    rnd_h = torch.from_numpy(I.uniforms(seed, 16, nevt, first_event=shard_first_event(rank, nevt))).pin_memory()
+    frnd_h = torch.from_numpy(I.uniforms(I.filter_seed_of(WORKLOAD), 16, 16)).pin_memory()
     me_h = torch.empty(nevt, dtype=torch.float64).pin_memory()
+    sums_h = torch.empty(3, dtype=torch.float64).pin_memory()
     ws = torch.empty(mg.pipeline_workspace_bytes(proc, nevt, 16) // 8 + 1, dtype=torch.float64, device=dev)
+
+    def step_e2e():
+        frnd.copy_(frnd_h, non_blocking=True)
+        mg.rambo(proc, frnd, ecm, mom=fmom, wgt=fwgt, stream=stream)
+        mg.filter_helicities(proc, fmom, mask=mask, stream=stream)
+        mg.pipeline_host(proc, rnd_h, ecm, mask, mode=args.mode, me_host=me_h, sums_host=sums_h, workspace=ws,
+                         stream=stream)
+
     for _ in range(args.warmup):
-        mg.pipeline_host(proc, rnd_h, ecm, mask, mode=args.mode, me_host=me_h, workspace=ws, stream=stream)
+        step_e2e()
     torch.cuda.synchronize()
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        mg.pipeline_host(proc, rnd_h, ecm, mask, mode=args.mode, me_host=me_h, workspace=ws, stream=stream)
+        step_e2e()
     e1.record(stream)
     torch.cuda.synchronize()
     te2e = e0.elapsed_time(e1) / 1e3
-    if world > 1:
-        t = torch.tensor([te2e], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        te2e = float(t.item())
-        torch.distributed.all_reduce(sums)  # the path's one exchange: sum over all events
-    e2e = {"value": world * nevt * args.steps / te2e, "unit": UNIT, "h2d_bytes_per_step": 16 * 8 * nevt,
-           "d2h_bytes_per_step": 8 * nevt}
+    te2e = max_over_ranks(te2e, world, dev)
+    sum_over_ranks(sums, world)
+    e2e = {"value": world * nevt * args.steps / te2e, "unit": UNIT,
+           "h2d_bytes_per_step": 8 * frnd_h.numel() + 8 * rnd_h.numel(),
+           "d2h_bytes_per_step": 8 * nevt + 8 * 3}
 
     # roofline of the dominant kernel (SIGMAKIN): FP32 CUDA-core arithmetic.
     # Algorithmic flops per event of the helicity-shared kernel: every current
     # variant once per event, then per good helicity its amplitudes and colour sum.
     s = procgen.summary(proc)
-    flops_per_me = s["hs_flops_items"] + ngood * (s["hs_flops_amp_hel"] + s["flops_csum"])
+    flops_per_me = s["hs_flops_items"] + ngood * (s["hs_flops_amp_hel"] + s["flops_csum_sym"])
     ksec = statistics.mean(kern)
     achieved = flops_per_me * nevt / ksec / 1e12
     peak32 = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
@@ -369,7 +413,9 @@ def main():
         traffic = SIGMAKIN_TRAFFIC["bytes_per_event"] * nevt
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak32, "unit": "TFLOP/s",
                 "frac": achieved / peak32, "traffic": traffic,
-                "kernel": "sigmakin_hs_kernel<Proc4,%s>" % ("float,TC" if args.mode == "mixed" else args.mode),
+                "kernel": "sigmakin_hs_kernel<Proc4,%s>" % {"mixed": "float,SIMT", "mixed_simt": "float,SIMT",
+                                                            "mixed_tc": "float,TC", "fp64": "double,SIMT"}.get(
+                                                                args.mode, args.mode),
                 "flops_per_me": flops_per_me,
                 "flops_per_me_per_helicity_unshared": s["flops_amp"] + s["flops_csum"],
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
@@ -387,6 +433,7 @@ def main():
         "sigmakin_ms": 1e3 * ksec,
         "fp64": fp64,
         "unrolled": unrolled,
+        "tensor_core_colour_sum": tensor_core,
         "other_workloads": others,
         "event_sum": [float(x) for x in sums.cpu().numpy()],
         "roofline": roofline,

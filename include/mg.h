@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define MG_ABI_VERSION 1
+#define MG_ABI_VERSION 2
 
 typedef enum {
   MG_OK = 0,
@@ -54,15 +54,19 @@ typedef enum {
 typedef enum {
   MG_FP64 = 0,        /* everything in FP64 */
   MG_MIXED = 1,       /* FP32 wavefunctions, currents and amplitudes; FP64 momenta,
-                         propagator denominators and helicity/event sums; colour
-                         sum on the tensor cores (split-BF16, FP32 accumulation) */
-  MG_MIXED_SIMT = 2,  /* as MG_MIXED with the colour sum on CUDA cores in FP32 */
+                         momentum sums, propagator invariants and helicity/event
+                         sums; colour sum on CUDA cores in FP32 below 48 colour
+                         flows, on the tensor cores from 48 flows on */
+  MG_MIXED_SIMT = 2,  /* MG_MIXED with the colour sum on CUDA cores in FP32 */
   MG_FP64_UNROLLED = 3,   /* MG_FP64 with every helicity recomputing all its currents */
-  MG_MIXED_UNROLLED = 4   /* MG_MIXED with every helicity recomputing all its currents */
+  MG_MIXED_UNROLLED = 4,  /* MG_MIXED_TC with every helicity recomputing all its currents */
+  MG_MIXED_TC = 5     /* MG_MIXED with the colour sum on the tensor cores
+                         (split-BF16 operands, FP32 accumulation) */
 } mg_mode;
-/* Modes 0-2 evaluate each off-shell current once per event for each helicity
- * combination of its own external legs, and each diagram at the vertex that
- * needs the cheapest currents; modes 3-4 run one unrolled program per
+/* Modes 0-2 and 5 evaluate each off-shell current once per event for each
+ * helicity combination of its own external legs, and each diagram as the
+ * contraction of one of its currents with the amputated current of the others
+ * (also shared across helicities); modes 3-4 run one unrolled program per
  * helicity (the organisation of the paper's SIGMAKIN).  Same results up to
  * rounding. */
 
@@ -129,8 +133,9 @@ int mg_sigmakin(int proc, int64_t nevt, const double* mom, const int32_t* mask, 
  * Newton step enters through its implicit-function derivative).  rnd: [nrows]
  * [nevt] as for mg_rambo; rows beyond 4*nfinal get exactly 0.  gout: [nevt]
  * dL/dme or NULL for 1.  me: [nevt] receives the matrix elements (or NULL).
- * mode: MG_FP64 (FP64 forward and adjoint) or MG_MIXED / MG_MIXED_SIMT (FP32
- * forward and adjoint; FP64 RAMBO, propagator denominators and sums).
+ * mode: MG_FP64 (FP64 forward and adjoint) or MG_MIXED / MG_MIXED_SIMT /
+ * MG_MIXED_TC (FP32 forward and adjoint on CUDA cores; FP64 RAMBO, propagator
+ * denominators and sums).
  * Available for proc 2 (g g -> t t~) and 3 (g g -> t t~ g); MG_ERR_PROC
  * otherwise. */
 int mg_sigmakin_grad(int proc, int64_t nevt, double ecm, const double* rnd, int nrows, const int32_t* mask,
@@ -165,15 +170,16 @@ int mg_event_sum_noalloc(int64_t nevt, const double* me, const double* wgt, doub
 
 /* End-to-end pipeline from HOST buffers (copies inside): h_rnd [nrows][nevt]
  * -> host-to-device copy -> RAMBO -> SIGMAKIN (mask from mg_filter_helicities,
- * on the device) -> device-to-host copy of me (and wgt if h_wgt != NULL).
- * Host buffers should be pinned for asynchronous copies.  workspace: device
- * buffer of at least mg_pipeline_workspace_bytes(proc, nevt, nrows) bytes.
- * Enqueued on stream; the host buffers are valid after the stream
- * synchronises. */
+ * on the device) -> device-to-host copy of me (and wgt if h_wgt != NULL) and,
+ * if h_sums != NULL, of the FP64 event sum {sum w me, sum (w me)^2, nevt} of
+ * mg_event_sum (3 doubles).  Host buffers should be pinned for asynchronous
+ * copies.  workspace: device buffer of at least
+ * mg_pipeline_workspace_bytes(proc, nevt, nrows) bytes.  Enqueued on stream;
+ * the host buffers are valid after the stream synchronises. */
 int64_t mg_pipeline_workspace_bytes(int proc, int64_t nevt, int nrows);
 int mg_pipeline_host(int proc, int64_t nevt, double ecm, const double* h_rnd, int nrows, const int32_t* mask,
-                     int mode, double* h_me, double* h_wgt, void* workspace, int64_t workspace_bytes,
-                     void* stream);
+                     int mode, double* h_me, double* h_wgt, double* h_sums, void* workspace,
+                     int64_t workspace_bytes, void* stream);
 
 /* Human-readable status; the CUDA error code of the last MG_ERR_CUDA. */
 const char* mg_status_string(int status);

@@ -35,7 +35,10 @@ struct Proc2 {
   static __device__ __forceinline__ int hs_xitem(int c) { return kHsXItem2[c]; }
   static __device__ __forceinline__ const HsItem* hs_items() { return kHsItems2; }
   // A = sum_i X_i Y_i for the amplitudes of chunk c: X = xb[X slot + variant],
-  // Y = cur[Y slot + variant], variant of a leg set S for this helicity = vt[S * NHEL]
+  // Y = cur[Y slot + variant], variant of a leg set S for this helicity = vt[S * NHEL];
+  // HS_LOCKSTEP(m, n) between amputated currents (amplitudes m and n of the chunk
+  // start the previous and the next one)
+  // lets the kernel re-align its warps
   template <class R, class CUR, class XB>
   static __device__ __forceinline__ void hs_contract(int c, const CUR& cur, const XB& xb, const uint8_t* __restrict__ vt, cx<R>* J) {
     switch (c) {
@@ -44,10 +47,12 @@ struct Proc2 {
           const W4<R> X = xb[0 + vt[144]];
           { const cx<R> a = dot4(X, cur[16 + vt[96]]); J[1] += a; }
         }
+        HS_LOCKSTEP(0, 1);
         {
           const W4<R> X = xb[4 + vt[160]];
           { const cx<R> a = dot4(X, cur[12 + vt[80]]); J[0] += a; }
         }
+        HS_LOCKSTEP(1, 2);
         {
           const W4<R> X = xb[8 + vt[192]];
           { const cx<R> a = dot4(X, cur[8 + vt[48]]); J[0] -= mul_i(a); J[1] += mul_i(a); }

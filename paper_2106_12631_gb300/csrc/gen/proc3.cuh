@@ -35,7 +35,10 @@ struct Proc3 {
   static __device__ __forceinline__ int hs_xitem(int c) { return kHsXItem3[c]; }
   static __device__ __forceinline__ const HsItem* hs_items() { return kHsItems3; }
   // A = sum_i X_i Y_i for the amplitudes of chunk c: X = xb[X slot + variant],
-  // Y = cur[Y slot + variant], variant of a leg set S for this helicity = vt[S * NHEL]
+  // Y = cur[Y slot + variant], variant of a leg set S for this helicity = vt[S * NHEL];
+  // HS_LOCKSTEP(m, n) between amputated currents (amplitudes m and n of the chunk
+  // start the previous and the next one)
+  // lets the kernel re-align its warps
   template <class R, class CUR, class XB>
   static __device__ __forceinline__ void hs_contract(int c, const CUR& cur, const XB& xb, const uint8_t* __restrict__ vt, cx<R>* J) {
     switch (c) {
@@ -44,38 +47,47 @@ struct Proc3 {
           const W4<R> X = xb[0 + vt[352]];
           { const cx<R> a = dot4(X, cur[66 + vt[640]]); J[4] += a; }
         }
+        HS_LOCKSTEP(0, 1);
         {
           const W4<R> X = xb[8 + vt[352]];
           { const cx<R> a = dot4(X, cur[66 + vt[640]]); J[5] += a; }
         }
+        HS_LOCKSTEP(1, 2);
         {
           const W4<R> X = xb[16 + vt[352]];
           { const cx<R> a = dot4(X, cur[66 + vt[640]]); J[4] -= mul_i(a); J[5] += mul_i(a); }
         }
+        HS_LOCKSTEP(2, 3);
         {
           const W4<R> X = xb[24 + vt[800]];
           { const cx<R> a = dot4(X, cur[62 + vt[192]]); J[2] += a; }
         }
+        HS_LOCKSTEP(3, 4);
         {
           const W4<R> X = xb[32 + vt[800]];
           { const cx<R> a = dot4(X, cur[62 + vt[192]]); J[2] -= mul_i(a); J[3] += mul_i(a); }
         }
+        HS_LOCKSTEP(4, 5);
         {
           const W4<R> X = xb[40 + vt[800]];
           { const cx<R> a = dot4(X, cur[62 + vt[192]]); J[3] += a; }
         }
+        HS_LOCKSTEP(5, 6);
         {
           const W4<R> X = xb[48 + vt[832]];
           { const cx<R> a = dot4(X, cur[58 + vt[160]]); J[0] += a; }
         }
+        HS_LOCKSTEP(6, 7);
         {
           const W4<R> X = xb[56 + vt[832]];
           { const cx<R> a = dot4(X, cur[58 + vt[160]]); J[1] += a; }
         }
+        HS_LOCKSTEP(7, 8);
         {
           const W4<R> X = xb[64 + vt[832]];
           { const cx<R> a = dot4(X, cur[58 + vt[160]]); J[0] -= mul_i(a); J[1] += mul_i(a); }
         }
+        HS_LOCKSTEP(8, 9);
         {
           const W4<R> X = xb[72 + vt[384]];
           { const cx<R> a = dot4(X, cur[34 + vt[608]]); J[0] -= a; J[2] += a; J[4] += a; J[5] -= a; }
@@ -85,14 +97,17 @@ struct Proc3 {
           { const cx<R> a = dot4(X, cur[78 + vt[608]]); J[0] -= a; J[2] += a; J[4] += a; J[5] -= a; }
           { const cx<R> a = dot4(X, cur[86 + vt[608]]); J[1] -= a; J[2] += a; J[3] -= a; J[4] += a; }
         }
+        HS_LOCKSTEP(9, 15);
         {
           const W4<R> X = xb[76 + vt[224]];
           { const cx<R> a = dot4(X, cur[18 + vt[768]]); J[0] -= mul_i(a); J[2] += mul_i(a); }
         }
+        HS_LOCKSTEP(15, 16);
         {
           const W4<R> X = xb[84 + vt[672]];
           { const cx<R> a = dot4(X, cur[14 + vt[320]]); J[1] -= mul_i(a); J[4] += mul_i(a); }
         }
+        HS_LOCKSTEP(16, 17);
         {
           const W4<R> X = xb[92 + vt[704]];
           { const cx<R> a = dot4(X, cur[10 + vt[288]]); J[3] -= mul_i(a); J[5] += mul_i(a); }

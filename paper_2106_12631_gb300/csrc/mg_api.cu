@@ -200,7 +200,7 @@ int mg_filter_helicities(int proc, int64_t nevt, const double* mom, int32_t* mas
 int mg_sigmakin(int proc, int64_t nevt, const double* mom, const int32_t* mask, double* me, int mode,
                 void* stream) {
   if (!valid_proc(proc)) return MG_ERR_PROC;
-  if (nevt < 0 || mode < 0 || mode > 4) return MG_ERR_ARG;
+  if (nevt < 0 || mode < 0 || mode > 5) return MG_ERR_ARG;
   if (nevt == 0) return MG_OK;
   if (!mom || !mask || !me) return MG_ERR_ARG;
   if (!aligned(mom) || !aligned(mask) || !aligned(me)) return MG_ERR_ALIGN;
@@ -214,7 +214,7 @@ int mg_sigmakin_grad(int proc, int64_t nevt, double ecm, const double* rnd, int 
   if (!valid_proc(proc)) return MG_ERR_PROC;
   if (proc != 2 && proc != 3) return MG_ERR_PROC;
   const ProcDesc& d = kProcs[proc];
-  if (nevt < 0 || mode < 0 || mode > 2 || !(ecm > 0) || !std::isfinite(ecm) || nrows < 4 * (d.npar - 2))
+  if (nevt < 0 || mode < 0 || (mode > 2 && mode != 5) || !(ecm > 0) || !std::isfinite(ecm) || nrows < 4 * (d.npar - 2))
     return MG_ERR_ARG;
   mg::RamboSetup st;
   if (int r = rambo_setup(proc, ecm, st)) return r;
@@ -269,14 +269,15 @@ int mg_event_sum_noalloc(int64_t nevt, const double* me, const double* wgt, doub
 int64_t mg_pipeline_workspace_bytes(int proc, int64_t nevt, int nrows) {
   if (!valid_proc(proc) || nevt < 0 || nrows < 0) return -1;
   const int64_t n = nevt;
-  return align256(8 * n * nrows) + align256(8 * n * 4 * kProcs[proc].npar) + 2 * align256(8 * n);
+  return align256(8 * n * nrows) + align256(8 * n * 4 * kProcs[proc].npar) + 2 * align256(8 * n) + align256(8 * 3) +
+         align256(mg_event_sum_scratch_bytes(n));
 }
 
 int mg_pipeline_host(int proc, int64_t nevt, double ecm, const double* h_rnd, int nrows, const int32_t* mask,
-                     int mode, double* h_me, double* h_wgt, void* workspace, int64_t workspace_bytes,
-                     void* stream) {
+                     int mode, double* h_me, double* h_wgt, double* h_sums, void* workspace,
+                     int64_t workspace_bytes, void* stream) {
   if (!valid_proc(proc)) return MG_ERR_PROC;
-  if (nevt < 0 || mode < 0 || mode > 2 || nrows < 4 * (kProcs[proc].npar - 2)) return MG_ERR_ARG;
+  if (nevt < 0 || mode < 0 || mode > 5 || nrows < 4 * (kProcs[proc].npar - 2)) return MG_ERR_ARG;
   if (nevt == 0) return MG_OK;
   if (!h_rnd || !mask || !h_me || !workspace) return MG_ERR_ARG;
   if (workspace_bytes < mg_pipeline_workspace_bytes(proc, nevt, nrows)) return MG_ERR_SPACE;
@@ -289,6 +290,10 @@ int mg_pipeline_host(int proc, int64_t nevt, double ecm, const double* h_rnd, in
   double* d_wgt = (double*)ws;
   ws += align256(8 * nevt);
   double* d_me = (double*)ws;
+  ws += align256(8 * nevt);
+  double* d_sums = (double*)ws;
+  ws += align256(8 * 3);
+  double* d_scratch = (double*)ws;
   cudaStream_t s = (cudaStream_t)stream;
   if (int r = cuda_status(cudaMemcpyAsync(d_rnd, h_rnd, 8 * nevt * nrows, cudaMemcpyHostToDevice, s))) return r;
   if (int r = mg_rambo(proc, nevt, ecm, d_rnd, nrows, d_mom, d_wgt, stream)) return r;
@@ -296,6 +301,11 @@ int mg_pipeline_host(int proc, int64_t nevt, double ecm, const double* h_rnd, in
   if (int r = cuda_status(cudaMemcpyAsync(h_me, d_me, 8 * nevt, cudaMemcpyDeviceToHost, s))) return r;
   if (h_wgt)
     if (int r = cuda_status(cudaMemcpyAsync(h_wgt, d_wgt, 8 * nevt, cudaMemcpyDeviceToHost, s))) return r;
+  if (h_sums) {
+    if (int r = mg_event_sum(nevt, d_me, d_wgt, d_sums, d_scratch, mg_event_sum_scratch_bytes(nevt), stream))
+      return r;
+    if (int r = cuda_status(cudaMemcpyAsync(h_sums, d_sums, 8 * 3, cudaMemcpyDeviceToHost, s))) return r;
+  }
   return MG_OK;
 }
 

@@ -3,6 +3,17 @@
 #pragma once
 #include "helas_adj.cuh"
 
+// CTA barrier inside the straight-line contraction code every MG_HS_LOCK_EVERY
+// amplitudes (at the next change of amputated current), so that the warps
+// stay close together in the program and share instruction fetches (0: none)
+#ifndef MG_HS_LOCK_EVERY
+#define MG_HS_LOCK_EVERY 0
+#endif
+#define HS_LOCKSTEP(m, n)                                                             \
+  do {                                                                                \
+    constexpr int lock_every_ = MG_HS_LOCK_EVERY > 0 ? MG_HS_LOCK_EVERY : 1 << 30;    \
+    if constexpr ((m) / lock_every_ != (n) / lock_every_) __syncthreads();            \
+  } while (0)
 #include "gen/proc1.cuh"
 #include "gen/proc2.cuh"
 #include "gen/proc3.cuh"

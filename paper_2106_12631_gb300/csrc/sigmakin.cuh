@@ -128,16 +128,15 @@ struct SigLayout {
 };
 
 // Phase 1b: per-event tables from the FP64 momenta already in shared memory.
-template <class P, class R, class L>
+template <class P, class R, class L, int NTS = SigCfg<P>::NT>
 __device__ __forceinline__ void build_tables(unsigned char* smem, const PhysParams& pp, int nev) {
-  using C = SigCfg<P>;
   const int tid = threadIdx.x;
   auto p = reinterpret_cast<double(*)[P::NPAR][4]>(smem + L::o_p);
   auto K = reinterpret_cast<R(*)[P::NMOM][4]>(smem + L::o_K);
   auto pr = reinterpret_cast<cx<R>(*)[P::NPROP]>(smem + L::o_pr);
   const int(*mom_tab)[3] = reinterpret_cast<const int(*)[3]>(smem + L::o_momtab);
   const int(*prop_tab)[2] = reinterpret_cast<const int(*)[2]>(smem + L::o_proptab);
-  for (int t = tid; t < nev * (P::NMOM + P::NPROP); t += C::NT) {
+  for (int t = tid; t < nev * (P::NMOM + P::NPROP); t += NTS) {
     const int e = t % nev, j = t / nev;
     const int mj = j < P::NMOM ? j : prop_tab[j - P::NMOM][0];
     const int kind = mom_tab[mj][0], lmask = mom_tab[mj][1], smask = mom_tab[mj][2];
@@ -161,18 +160,18 @@ __device__ __forceinline__ void build_tables(unsigned char* smem, const PhysPara
   __syncthreads();
 }
 
-// Phase 1: external momenta (global -> shared) and the per-event tables.
-template <class P, class R, class L>
+// Phase 1: external momenta (global -> shared) and the per-event tables
+// (NTS threads).
+template <class P, class R, class L, int NTS = SigCfg<P>::NT>
 __device__ __forceinline__ void event_tables(unsigned char* smem, const SigArgs& a, int64_t e0, int nev) {
-  using C = SigCfg<P>;
   const int tid = threadIdx.x;
   auto p = reinterpret_cast<double(*)[P::NPAR][4]>(smem + L::o_p);
-  for (int t = tid; t < nev * P::NPAR * 4; t += C::NT) {
+  for (int t = tid; t < nev * P::NPAR * 4; t += NTS) {
     const int e = t % nev, c = t / nev;
     p[e][c >> 2][c & 3] = a.mom[(int64_t)c * a.nevt + e0 + e];
   }
   __syncthreads();
-  build_tables<P, R, L>(smem, a.pp, nev);
+  build_tables<P, R, L, NTS>(smem, a.pp, nev);
 }
 
 template <class P, class L>
@@ -368,25 +367,28 @@ __global__ void __launch_bounds__(SigCfg<P>::NT, 1) sigmakin_kernel(SigArgs a, C
 
 // Helicity filtering (FP64): every helicity of the first nevt events; a
 // helicity is kept if any event gives a non-zero |M_h|^2.
+// Helicity filter: helicity h is kept if |M_h|^2 != 0 for any of the filter
+// events (FP64, the straight-line program of each helicity).  One thread per
+// (event, helicity) in CTAs of FILTER_NT threads, so that the few filter
+// events spread over many SMs (each thread's FP64 program is long).
+constexpr int FILTER_NT = 16;
 template <class P>
-__global__ void __launch_bounds__(SigCfg<P>::NT, 1) filter_kernel(SigArgs a, Couplings<double> cp) {
-  using C = SigCfg<P>;
+__global__ void __launch_bounds__(FILTER_NT) filter_kernel(SigArgs a, Couplings<double> cp) {
   using L = SigLayout<P, double, CS_SIMT>;
+  constexpr int HB = (P::NHEL + FILTER_NT - 1) / FILTER_NT;  // helicity blocks per event
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x;
+  const int64_t e0 = (int64_t)(blockIdx.x / HB);
+  const int h = (int)(blockIdx.x % HB) * FILTER_NT + tid;
+  if (e0 >= a.nevt) return;
   load_tables<P, L>(smem);
   __syncthreads();
-  constexpr int ev = C::EVMIN;
-  const int64_t e0 = (int64_t)blockIdx.x * ev;
-  if (e0 >= a.nevt) return;
-  const int nev = (int)min((int64_t)ev, a.nevt - e0);
-  event_tables<P, double, L>(smem, a, e0, nev);
-  const int e = tid / P::NHEL, h = tid % P::NHEL;
-  if (e < nev) {
+  event_tables<P, double, L, FILTER_NT>(smem, a, e0, 1);
+  if (h < P::NHEL) {
     int hel[P::NPAR];
     decode_helicity<P>(h, hel);
-    const double* K = reinterpret_cast<const double*>(smem + L::o_K) + e * P::NMOM * 4;
-    const cx<double>* pr = reinterpret_cast<const cx<double>*>(smem + L::o_pr) + e * P::NPROP;
+    const double* K = reinterpret_cast<const double*>(smem + L::o_K);
+    const cx<double>* pr = reinterpret_cast<const cx<double>*>(smem + L::o_pr);
     RegAcc<double, P::NCOLOR> J;
     P::template amplitudes<double, RegAcc<double, P::NCOLOR>, NoSync>(K, pr, hel, cp, J);
     const double m2 =

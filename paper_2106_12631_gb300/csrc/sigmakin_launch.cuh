@@ -28,18 +28,23 @@ cudaError_t launch_sigmakin_hs_variant(const SigArgs& a, const Couplings<R>& cp,
   return cudaGetLastError();
 }
 
-// mode 0 FP64, 1 mixed + tcgen05 colour sum, 2 mixed + CUDA-core colour sum
-// (helicity-shared kernel); 3 FP64, 4 mixed + tcgen05 with the per-helicity
-// unrolled kernel (every helicity recomputes all its currents)
+// mode 0 FP64; 1 mixed, colour sum on CUDA cores below 48 colour flows and on
+// the tensor cores from 48 on; 2 mixed + CUDA-core colour sum; 5 mixed +
+// tcgen05 colour sum (helicity-shared kernel); 3 FP64, 4 mixed + tcgen05 with
+// the per-helicity unrolled kernel (every helicity recomputes all its currents)
 template <class P>
 cudaError_t launch_sigmakin_impl(const SigLaunch& l, int mode, cudaStream_t s) {
   SigArgs a{l.nevt, l.mom, l.mask, l.me, l.mask_out, l.pp};
   const int64_t grid = (l.nevt + SigCfg<P>::EVMIN - 1) / SigCfg<P>::EVMIN;
   if (grid == 0) return cudaSuccess;
+  constexpr bool tc_default = P::NCOLOR >= 48;
   switch (mode) {
     case 0: return launch_sigmakin_hs_variant<P, double, CS_SIMT>(a, l.cd, grid, s);
-    case 1: return launch_sigmakin_hs_variant<P, float, CS_TC>(a, l.cf, grid, s);
+    case 1:
+      return tc_default ? launch_sigmakin_hs_variant<P, float, CS_TC>(a, l.cf, grid, s)
+                        : launch_sigmakin_hs_variant<P, float, CS_SIMT>(a, l.cf, grid, s);
     case 2: return launch_sigmakin_hs_variant<P, float, CS_SIMT>(a, l.cf, grid, s);
+    case 5: return launch_sigmakin_hs_variant<P, float, CS_TC>(a, l.cf, grid, s);
     case 3: return launch_sigmakin_variant<P, double, CS_SIMT>(a, l.cd, grid, s);
     case 4: return launch_sigmakin_variant<P, float, CS_TC>(a, l.cf, grid, s);
   }
@@ -50,12 +55,12 @@ template <class P>
 cudaError_t launch_filter_impl(const SigLaunch& l, cudaStream_t s) {
   using L = SigLayout<P, double, CS_SIMT>;
   SigArgs a{l.nevt, l.mom, l.mask, l.me, l.mask_out, l.pp};
-  const int64_t grid = (l.nevt + SigCfg<P>::EVMIN - 1) / SigCfg<P>::EVMIN;
+  const int64_t grid = l.nevt * ((P::NHEL + FILTER_NT - 1) / FILTER_NT);
   if (grid == 0) return cudaSuccess;
   auto k = filter_kernel<P>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
   if (e != cudaSuccess) return e;
-  k<<<(unsigned)grid, SigCfg<P>::NT, L::bytes, s>>>(a, l.cd);
+  k<<<(unsigned)grid, FILTER_NT, L::bytes, s>>>(a, l.cd);
   return cudaGetLastError();
 }
 

@@ -1320,7 +1320,10 @@ class SharedProgram:
         ALL = (1 << self.n) - 1
         ops = {0: "J[%d] += a;", 1: "J[%d] -= a;", 2: "J[%d] += mul_i(a);", 3: "J[%d] -= mul_i(a);"}
         lines = ["  // A = sum_i X_i Y_i for the amplitudes of chunk c: X = xb[X slot + variant],",
-                 "  // Y = cur[Y slot + variant], variant of a leg set S for this helicity = vt[S * NHEL]",
+                 "  // Y = cur[Y slot + variant], variant of a leg set S for this helicity = vt[S * NHEL];",
+                 "  // HS_LOCKSTEP(m, n) between amputated currents (amplitudes m and n of the chunk",
+                 "  // start the previous and the next one)",
+                 "  // lets the kernel re-align its warps",
                  "  template <class R, class CUR, class XB>",
                  "  static __device__ __forceinline__ void hs_contract(int c, const CUR& cur, const XB& xb,"
                  " const uint8_t* __restrict__ vt, cx<R>* J) {",
@@ -1328,12 +1331,17 @@ class SharedProgram:
         for c in range(len(self.chunks)):
             lines.append("      case %d: {" % c)
             last_x = None
+            n = prev = 0
             for (ch, xo, yo, pat, xset, flows) in self.amp_list:
                 if ch != c:
                     continue
+                if xo != last_x and n > 0:
+                    lines.append("        }")
+                    lines.append("        HS_LOCKSTEP(%d, %d);" % (prev, n))
+                    prev = n
+                    last_x = None
+                n += 1
                 if xo != last_x:
-                    if last_x is not None:
-                        lines.append("        }")
                     lines.append("        {")
                     lines.append("          const W4<R> X = xb[%d + vt[%d]];" % (xo, xset * nh))
                     last_x = xo

@@ -15,9 +15,9 @@ import torch
 
 from . import build as _build
 
-MG_FP64, MG_MIXED, MG_MIXED_SIMT, MG_FP64_UNROLLED, MG_MIXED_UNROLLED = 0, 1, 2, 3, 4
+MG_FP64, MG_MIXED, MG_MIXED_SIMT, MG_FP64_UNROLLED, MG_MIXED_UNROLLED, MG_MIXED_TC = 0, 1, 2, 3, 4, 5
 MODES = {"fp64": MG_FP64, "mixed": MG_MIXED, "mixed_simt": MG_MIXED_SIMT, "fp64_unrolled": MG_FP64_UNROLLED,
-         "mixed_unrolled": MG_MIXED_UNROLLED}
+         "mixed_unrolled": MG_MIXED_UNROLLED, "mixed_tc": MG_MIXED_TC}
 PROCS = {"ee_mumu": 1, "gg_tt": 2, "gg_ttg": 3, "gg_ttgg": 4}
 
 _lock = threading.Lock()
@@ -68,7 +68,7 @@ def lib():
             L.mg_event_sum_noalloc.argtypes = [i64, vp, vp, vp, vp]
             L.mg_pipeline_workspace_bytes.argtypes = [i32, i64, i32]
             L.mg_pipeline_workspace_bytes.restype = i64
-            L.mg_pipeline_host.argtypes = [i32, i64, ctypes.c_double, vp, i32, vp, i32, vp, vp, vp, i64, vp]
+            L.mg_pipeline_host.argtypes = [i32, i64, ctypes.c_double, vp, i32, vp, i32, vp, vp, vp, vp, i64, vp]
             L.mg_status_string.argtypes = [i32]
             L.mg_status_string.restype = ctypes.c_char_p
             _lib = L
@@ -242,9 +242,10 @@ def pipeline_workspace_bytes(proc, nevt: int, nrows: int) -> int:
 
 
 def pipeline_host(proc, rnd_host: torch.Tensor, ecm: float, mask: torch.Tensor, mode="mixed", me_host=None,
-                  wgt_host=None, workspace=None, stream=None):
-    """Host random numbers -> (H2D) RAMBO -> SIGMAKIN -> (D2H) host me.  Async on the stream;
-    synchronise before reading me_host.  rnd_host should be pinned."""
+                  wgt_host=None, sums_host=None, workspace=None, stream=None):
+    """Host random numbers -> (H2D) RAMBO -> SIGMAKIN -> (D2H) host me (and wgt, and the
+    event sum into sums_host[3] if given).  Async on the stream; synchronise before reading
+    the host buffers.  rnd_host should be pinned."""
     p = _proc(proc)
     if rnd_host.is_cuda or rnd_host.dtype != torch.float64 or not rnd_host.is_contiguous():
         raise ValueError("rnd_host must be a contiguous float64 CPU tensor")
@@ -258,6 +259,7 @@ def pipeline_host(proc, rnd_host: torch.Tensor, ecm: float, mask: torch.Tensor, 
     _check(lib().mg_pipeline_host(p, nevt, float(ecm), rnd_host.data_ptr(), nrows,
                                   _dev(mask, torch.int32, "mask"), m, me_host.data_ptr(),
                                   wgt_host.data_ptr() if wgt_host is not None else None,
+                                  sums_host.data_ptr() if sums_host is not None else None,
                                   workspace.data_ptr(), workspace.numel() * workspace.element_size(),
                                   _stream(stream)), "mg_pipeline_host")
     return me_host

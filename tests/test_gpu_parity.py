@@ -101,7 +101,7 @@ def check_fp64(rel, d_rot):
     assert np.mean(rel > FP64_REL) <= FP64_ILL_FRACTION + 1.0 / len(rel)
 
 
-@pytest.mark.parametrize("mode", ["mixed_simt", "mixed", "mixed_unrolled"])
+@pytest.mark.parametrize("mode", ["mixed_simt", "mixed", "mixed_tc", "mixed_unrolled"])
 @pytest.mark.parametrize("proc,nevt", [(1, 16384), (2, 4099), (3, 513), (4, 131)])
 def test_sigmakin_mixed(mg, orc, proc, nevt, mode):
     rnd = I.uniforms(61 + proc, NR[proc], nevt)
@@ -178,9 +178,16 @@ def test_pipeline_host_matches_device_path(mg):
     mom, _ = mg.rambo(proc, dev(rnd), 1500.0)
     me_dev = host(mg.sigmakin(proc, mom, mask, mode="mixed"))
     rnd_h = torch.from_numpy(rnd).pin_memory()
-    me_h = mg.pipeline_host(proc, rnd_h, 1500.0, mask, mode="mixed")
+    sums_h = torch.zeros(3, dtype=torch.float64).pin_memory()
+    wgt_h = torch.zeros(nevt, dtype=torch.float64).pin_memory()
+    me_h = mg.pipeline_host(proc, rnd_h, 1500.0, mask, mode="mixed", wgt_host=wgt_h, sums_host=sums_h)
     torch.cuda.synchronize()
     np.testing.assert_array_equal(me_h.numpy(), me_dev)
+    # the event sum of the pipeline is the device event sum of the same me and weights
+    _, wgt = mg.rambo(proc, dev(rnd), 1500.0)
+    np.testing.assert_array_equal(wgt_h.numpy(), host(wgt))
+    ref = host(mg.event_sum(torch.from_numpy(me_dev).cuda(), wgt))
+    np.testing.assert_array_equal(sums_h.numpy(), ref)
 
 
 @pytest.mark.parametrize("mode", ["fp64", "mixed"])
