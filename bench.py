@@ -41,7 +41,7 @@ SM_MAX_MHZ = 2070.0
 # (dram__bytes_read.sum + dram__bytes_write.sum of one launch over 2^18 events,
 # scaled by events; it reads the momenta once and writes |M|^2), valid only
 # while the kernel sources are the ones captured.
-SIGMAKIN_TRAFFIC = {"bytes_per_event": None, "sources_sha1": None}
+SIGMAKIN_TRAFFIC = {"bytes_per_event": 193.13, "sources_sha1": "9dbfde6eba6b4894b8abb0651414f31a0b2a2d7b"}
 SIGMAKIN_SOURCES = ["paper_2106_12631_gb300/csrc/" + f for f in
                     ("sigmakin_hs.cuh", "sigmakin.cuh", "helas.cuh", "colour_tc.cuh", "mg_types.cuh",
                      "process.cuh", "gen/proc4.cuh")]
