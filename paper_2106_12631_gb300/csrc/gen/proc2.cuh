@@ -19,6 +19,7 @@ struct Proc2 {
   static constexpr int HS_NSLOT = 20;   // current variant slots per event
   static constexpr int HS_XCAP = 12;    // amputated-current slots per event and chunk
   static constexpr int HS_NXCHUNK = 1;
+  static constexpr int HS_XBUFS = 1;   // chunk buffers
   static constexpr int HS_NITEM = 32;
   static constexpr int HS_NLEVEL = 2;
   static constexpr int HS_NAMP = 3;
@@ -36,9 +37,10 @@ struct Proc2 {
   static __device__ __forceinline__ const HsItem* hs_items() { return kHsItems2; }
   // A = sum_i X_i Y_i for the amplitudes of chunk c: X = xb[X slot + variant],
   // Y = cur[Y slot + variant], variant of a leg set S for this helicity = vt[S * NHEL];
+  // amplitudes with the same X and colour flows equal up to a phase share one
+  // contraction with the phase-weighted sum of their Y;
   // HS_LOCKSTEP(m, n) between amputated currents (amplitudes m and n of the chunk
   // start the previous and the next one)
-  // lets the kernel re-align its warps
   template <class R, class CUR, class XB>
   static __device__ __forceinline__ void hs_contract(int c, const CUR& cur, const XB& xb, const uint8_t* __restrict__ vt, cx<R>* J) {
     switch (c) {

@@ -369,6 +369,35 @@ __device__ __forceinline__ W4<R> vvvv_comb_a(const W4<R>& x, cx<R> cx_, const W4
   }
   return o;
 }
+// s + y, s - y, s + i y, s - i y (sums of left-out operands with a common phase)
+template <class R>
+__device__ __forceinline__ W4<R> w4_add(const W4<R>& s, const W4<R>& y) {
+  W4<R> o;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) o.w[k] = s.w[k] + y.w[k];
+  return o;
+}
+template <class R>
+__device__ __forceinline__ W4<R> w4_sub(const W4<R>& s, const W4<R>& y) {
+  W4<R> o;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) o.w[k] = s.w[k] - y.w[k];
+  return o;
+}
+template <class R>
+__device__ __forceinline__ W4<R> w4_addi(const W4<R>& s, const W4<R>& y) {
+  W4<R> o;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) o.w[k] = s.w[k] + mul_i(y.w[k]);
+  return o;
+}
+template <class R>
+__device__ __forceinline__ W4<R> w4_subi(const W4<R>& s, const W4<R>& y) {
+  W4<R> o;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) o.w[k] = s.w[k] - mul_i(y.w[k]);
+  return o;
+}
 // contraction of an amputated current with the left-out operand
 template <class R>
 __device__ __forceinline__ cx<R> dot4(const W4<R>& x, const W4<R>& y) {

@@ -41,7 +41,7 @@ struct HsCfg {
   // shared memory for the current variants and one chunk of amputated currents
   static constexpr int CTAS = P::NCOLOR >= 6 && sizeof(R) == 4 ? MG_HS_CTAS : 1;
   static constexpr size_t CUR_BUDGET = 192 * 1024 / CTAS;
-  static constexpr size_t EV_BYTES = (size_t)(P::HS_NSLOT + P::HS_XCAP) * sizeof(W4<R>);
+  static constexpr size_t EV_BYTES = (size_t)(P::HS_NSLOT + P::HS_XBUFS * P::HS_XCAP) * sizeof(W4<R>);
   static constexpr int FIT = (int)(CUR_BUDGET / EV_BYTES);
   static constexpr int EVCAP = FIT < EVWANT ? (FIT > EVMIN ? FIT : EVMIN) : EVWANT;
   static constexpr int KP = ((P::NCOLOR + 15) / 16) * 16;
@@ -71,9 +71,10 @@ struct HsLayout {
   static constexpr size_t o_A = o_U;
   // FP64 momentum sums of phase 1 (the amputated buffer is free then)
   static constexpr size_t o_Kd = o_x;
-  static_assert(8 * EVCAP * P::NMOM * 4 <= sizeof(W4<R>) * EVCAP * P::HS_XCAP, "FP64 sums overflow their scratch");
+  static_assert(8 * EVCAP * P::NMOM * 4 <= sizeof(W4<R>) * EVCAP * P::HS_XBUFS * P::HS_XCAP,
+                "FP64 sums overflow their scratch");
   static constexpr size_t tileA = 128 * KP * 2;
-  static constexpr size_t u_bytes = sizeof(W4<R>) * EVCAP * (P::HS_NSLOT + P::HS_XCAP);
+  static constexpr size_t u_bytes = sizeof(W4<R>) * EVCAP * (P::HS_NSLOT + P::HS_XBUFS * P::HS_XCAP);
   static constexpr size_t a_bytes = TC ? 3 * MBLK * tileA : 0;  // one component's three splits
   static constexpr size_t bytes = o_U + (u_bytes > a_bytes ? u_bytes : a_bytes);
   static constexpr uint32_t TMEM_COLS = tc::tmem_cols(MBLK * 2 * NP);
@@ -405,27 +406,35 @@ __global__ void __launch_bounds__(HsCfg<P, R>::NT, HsCfg<P, R>::CTAS) sigmakin_h
     }
     __syncthreads();
   }
-  // 3. amputated currents chunk by chunk, each followed by the contractions of
-  //    this thread's (event, helicity); J in registers
+  // 3. amputated currents chunk by chunk into two alternating buffers: in
+  //    interval c every thread first builds its share of chunk c, then
+  //    contracts chunk c - 1 for its (event, helicity) (J in registers), so the
+  //    latency of the item work hides behind other warps' contractions
   const bool active = tid < nev * ng;
   const int e = active ? tid / ng : 0;
   const int ih = good[active ? tid - e * ng : 0];
+  constexpr int XBUF = L::EVCAP * X_EV;  // one chunk buffer, all events
   cx<R> J[NC];
 #pragma unroll
   for (int s = 0; s < NC; ++s) J[s] = cx<R>(R(0), R(0));
 #pragma unroll 1
-  for (int c = 0; c < P::HS_NXCHUNK; ++c) {
-    if (c > 0) __syncthreads();  // the previous chunk's contractions are done with the buffer
-    const int i0 = P::hs_xitem(c), ni = P::hs_xitem(c + 1) - i0, n = ni * nev;
-    for (int t = tid; t < n; t += NT) {
-      const int ex = t / ni;
-      const HsItem it = items[i0 + t - ex * ni];
-      hs_xitem<P, R>(it, Slots<R, P::HS_NSLOT>{curs + ex * CUR_EV}, Slots<R, P::HS_XCAP>{xbufs + ex * X_EV},
-                     Kall + ex * P::NMOM * 4, cp);
+  for (int c = 0; c <= P::HS_NXCHUNK; ++c) {
+    if (c < P::HS_NXCHUNK) {
+      uint4* xb = xbufs + (P::HS_XBUFS == 2 ? (c & 1) * XBUF : 0);
+      const int i0 = P::hs_xitem(c), ni = P::hs_xitem(c + 1) - i0, n = ni * nev;
+      for (int t = tid; t < n; t += NT) {
+        const int ex = t / ni;
+        const HsItem it = items[i0 + t - ex * ni];
+        hs_xitem<P, R>(it, Slots<R, P::HS_NSLOT>{curs + ex * CUR_EV}, Slots<R, P::HS_XCAP>{xb + ex * X_EV},
+                       Kall + ex * P::NMOM * 4, cp);
+      }
     }
-    __syncthreads();
-    P::template hs_contract<R>(c, Slots<R, P::HS_NSLOT>{curs + e * CUR_EV}, Slots<R, P::HS_XCAP>{xbufs + e * X_EV},
-                               vtab + ih, J);
+    if (c > 0) {
+      const uint4* xb = xbufs + (P::HS_XBUFS == 2 ? ((c - 1) & 1) * XBUF : 0);
+      P::template hs_contract<R>(c - 1, Slots<R, P::HS_NSLOT>{curs + e * CUR_EV},
+                                 Slots<R, P::HS_XCAP>{const_cast<uint4*>(xb) + e * X_EV}, vtab + ih, J);
+    }
+    if (c < P::HS_NXCHUNK) __syncthreads();
   }
   // 4. colour sum and helicity sum
   double m2;

@@ -367,7 +367,7 @@ FLOPS = {
     "VVV1_0": 168, "VVVV_0": 136,
     # amputated currents (no propagator) and the contraction sum_i X_i Y_i
     "FFV1_2A": 72, "FFV1_1A": 72, "FFV1P0_3A": 80, "FFV2_4_3A": 96, "VVV1P0_1A": 158, "VVVV_A": 124,
-    "DOT4": 30,
+    "DOT4": 30, "W4ADD": 8,
     "jamp": 2,
 }
 
@@ -1088,7 +1088,9 @@ class SharedProgram:
         # amputated currents, packed into chunks that share one buffer
         xs.sort(key=lambda X: (X[1], sorted(self.legs(X)), repr(X)))
         total = sum(self.nvar(X) for X in xs)
-        self.xcap = min(total, self.SLOT_BUDGET - self.nslots)
+        # two chunk buffers when it takes more than one chunk (the kernel builds
+        # chunk c + 1 while it contracts chunk c)
+        self.xcap = total if total <= self.SLOT_BUDGET - self.nslots else (self.SLOT_BUDGET - self.nslots) // 2
         assert self.xcap >= max(self.nvar(X) for X in xs), "no room for an amputated current"
         self.xchunk, self.xoff, self.chunks = {}, {}, [[]]
         used = 0
@@ -1255,6 +1257,7 @@ class SharedProgram:
         assert len(patterns) < 256 and self.nslots < 65536 and self.xcap < 65536
         self.patterns = patterns
         self.amp_list = amps
+        self.groups = self._merge_groups(amps)
         xamp_start = [0] * (len(self.chunks) + 1)
         for c in range(len(self.chunks)):
             xamp_start[c + 1] = xamp_start[c] + sum(1 for a in amps if a[0] == c)
@@ -1282,7 +1285,9 @@ class SharedProgram:
                       8: FLOPS["VVVV1P0_1"], 9: FLOPS["FFV1_2A"], 10: FLOPS["FFV1_1A"], 11: FLOPS["FFV1P0_3A"],
                       12: FLOPS["FFV2_4_3A"], 13: FLOPS["VVV1P0_1A"], 14: FLOPS["VVVV_A"]}
         self.flops_items = sum(item_flops[it[0]] for it in items)
-        self.flops_amps_hel = sum(FLOPS["DOT4"] + FLOPS["jamp"] * len(a[5]) for a in amps)
+        groups = self._merge_groups(amps)
+        self.flops_amps_hel = sum(FLOPS["DOT4"] + FLOPS["jamp"] * len(g["flows"]) + FLOPS["W4ADD"] * (len(g["ys"]) - 1)
+                                  for g in groups)
 
     def struct_lines(self, pid: int) -> list:
         t = self.tables
@@ -1297,6 +1302,7 @@ class SharedProgram:
             "  static constexpr int HS_NSLOT = %d;   // current variant slots per event" % self.nslots,
             "  static constexpr int HS_XCAP = %d;    // amputated-current slots per event and chunk" % self.xcap,
             "  static constexpr int HS_NXCHUNK = %d;" % len(self.chunks),
+            "  static constexpr int HS_XBUFS = %d;   // chunk buffers" % (1 if len(self.chunks) == 1 else 2),
             "  static constexpr int HS_NITEM = %d;" % t["nitems"],
             "  static constexpr int HS_NLEVEL = %d;" % (len(t["level_start"]) - 1),
             "  static constexpr int HS_NAMP = %d;" % t["namps"],
@@ -1311,19 +1317,53 @@ class SharedProgram:
             "  static __device__ __forceinline__ const HsItem* hs_items() { return kHsItems%d; }" % pid,
         ] + self._contract_code()
 
+    @staticmethod
+    def _rotate(flows, r):
+        """Colour-flow coefficients times i^r (codes: 0 +1, 1 -1, 2 +i, 3 -i)."""
+        times_i = {0: 2, 2: 1, 1: 3, 3: 0}
+        out = []
+        for f in flows:
+            c = f >> 6
+            for _ in range(r):
+                c = times_i[c]
+            out.append((f & 63) | (c << 6))
+        return tuple(sorted(out))
+
+    def _merge_groups(self, amps):
+        """Amplitudes of one chunk with the same amputated current X whose colour
+        flows agree up to a phase i^r contract once:
+            sum_k (X . Y_k) i^{r_k} P = X . (sum_k i^{r_k} Y_k) P."""
+        groups = []
+        index = {}
+        for (ch, xo, yo, pat, xset, flows) in amps:
+            base = None
+            for r in range(4):
+                key = (ch, xo, self._rotate(flows, r))
+                if key in index:
+                    base = index[key], (4 - r) % 4  # flows = i^{-r} P
+                    break
+            if base is None:
+                index[(ch, xo, tuple(sorted(flows)))] = len(groups)
+                groups.append(dict(ch=ch, xo=xo, xset=xset, flows=list(flows), ys=[(yo, 0)]))
+            else:
+                groups[base[0]]["ys"].append((yo, base[1]))
+        return groups
+
     def _contract_code(self) -> list:
         """Contractions of one chunk for one (event, helicity), straight-line: every
         operand offset and variant-table entry is a constant, so the loads of
-        successive amplitudes are independent; each amplitude goes straight into
-        its colour flows J_s (+amp, -amp, +i amp, -i amp)."""
+        successive amplitudes are independent; each (merged) amplitude goes
+        straight into its colour flows J_s (+amp, -amp, +i amp, -i amp)."""
         nh = 1 << self.n
         ALL = (1 << self.n) - 1
         ops = {0: "J[%d] += a;", 1: "J[%d] -= a;", 2: "J[%d] += mul_i(a);", 3: "J[%d] -= mul_i(a);"}
+        acc = {0: "w4_add", 1: "w4_addi", 2: "w4_sub", 3: "w4_subi"}  # Y_sum += i^r Y
         lines = ["  // A = sum_i X_i Y_i for the amplitudes of chunk c: X = xb[X slot + variant],",
                  "  // Y = cur[Y slot + variant], variant of a leg set S for this helicity = vt[S * NHEL];",
+                 "  // amplitudes with the same X and colour flows equal up to a phase share one",
+                 "  // contraction with the phase-weighted sum of their Y;",
                  "  // HS_LOCKSTEP(m, n) between amputated currents (amplitudes m and n of the chunk",
                  "  // start the previous and the next one)",
-                 "  // lets the kernel re-align its warps",
                  "  template <class R, class CUR, class XB>",
                  "  static __device__ __forceinline__ void hs_contract(int c, const CUR& cur, const XB& xb,"
                  " const uint8_t* __restrict__ vt, cx<R>* J) {",
@@ -1332,21 +1372,31 @@ class SharedProgram:
             lines.append("      case %d: {" % c)
             last_x = None
             n = prev = 0
-            for (ch, xo, yo, pat, xset, flows) in self.amp_list:
-                if ch != c:
+            for g in self.groups:
+                if g["ch"] != c:
                     continue
-                if xo != last_x and n > 0:
+                if g["xo"] != last_x and n > 0:
                     lines.append("        }")
                     lines.append("        HS_LOCKSTEP(%d, %d);" % (prev, n))
                     prev = n
                     last_x = None
-                n += 1
-                if xo != last_x:
+                n += len(g["ys"])
+                if g["xo"] != last_x:
                     lines.append("        {")
-                    lines.append("          const W4<R> X = xb[%d + vt[%d]];" % (xo, xset * nh))
-                    last_x = xo
-                lines.append("          { const cx<R> a = dot4(X, cur[%d + vt[%d]]); %s }"
-                             % (yo, (ALL ^ xset) * nh, " ".join(ops[f >> 6] % (f & 63) for f in flows)))
+                    lines.append("          const W4<R> X = xb[%d + vt[%d]];" % (g["xo"], g["xset"] * nh))
+                    last_x = g["xo"]
+                yv = (ALL ^ g["xset"]) * nh
+                flows = " ".join(ops[f >> 6] % (f & 63) for f in g["flows"])
+                if len(g["ys"]) == 1:
+                    lines.append("          { const cx<R> a = dot4(X, cur[%d + vt[%d]]); %s }" % (g["ys"][0][0], yv, flows))
+                else:
+                    y0 = g["ys"][0][0]
+                    lines.append("          {")
+                    lines.append("            W4<R> Y = cur[%d + vt[%d]];" % (y0, yv))
+                    for (yo, r) in g["ys"][1:]:
+                        lines.append("            Y = %s(Y, cur[%d + vt[%d]]);" % (acc[r], yo, yv))
+                    lines.append("            const cx<R> a = dot4(X, Y); %s" % flows)
+                    lines.append("          }")
             if last_x is not None:
                 lines.append("        }")
             lines.append("      } break;")

@@ -101,3 +101,23 @@ def test_generator_colour_matrix_matches_oracle(orc, ng):
     C = orc.chain_colour_matrix(ng).real
     np.testing.assert_allclose(num / den, C, rtol=0, atol=1e-12)
     assert np.all(np.diag(num) * 3 ** ng == den * 3 * 4 ** ng)
+
+
+@pytest.mark.parametrize("pid", [1, 2, 3, 4])
+def test_generator_merged_contractions_keep_every_amplitude(pid):
+    """Amplitudes merged into one contraction (same amputated current X, colour
+    flows equal up to a phase i^r) each keep their own flows: i^r times the
+    group's pattern, and every amplitude appears in exactly one group."""
+    from paper_2106_12631_gb300.gen import procgen
+    proc = procgen.Process(procgen.PROCS[pid])
+    em = procgen.Emitter(proc)
+    for leg in range(proc.n):
+        em.momentum_phys(leg)
+    em.emit()
+    sp = procgen.SharedProgram(proc, em)
+    sp.emit_tables(pid)
+    remaining = [(a[0], a[1], a[2], tuple(sorted(a[5]))) for a in sp.amp_list]
+    for g in sp.groups:
+        for yo, r in g["ys"]:
+            remaining.remove((g["ch"], g["xo"], yo, sp._rotate(g["flows"], r)))
+    assert remaining == []
