@@ -57,7 +57,9 @@ struct HsLayout {
   static constexpr size_t o_proptab = 0;  // {momentum entry, line kind} per propagator
   static constexpr size_t o_good = align_up(o_proptab + 8 * P::NPROP, 16);
   static constexpr size_t o_misc = align_up(o_good + 4 * P::NHEL, 16);
-  static constexpr size_t o_p = align_up(o_misc + 32, 16);
+  // mixed mode: {m^2 hi, m^2 lo, m w, 0} of the top and of the Z
+  static constexpr size_t o_mconst = align_up(o_misc + 32, 16);
+  static constexpr size_t o_p = align_up(o_mconst + 32, 16);
   static constexpr size_t o_K = align_up(o_p + 8 * EVCAP * P::NPAR * 4, 16);
   static constexpr size_t o_pr = align_up(o_K + sizeof(R) * EVCAP * P::NMOM * 4, 16);
   static constexpr size_t o_m2 = align_up(o_pr + 2 * sizeof(R) * EVCAP * P::NPROP, 16);
@@ -219,22 +221,82 @@ __device__ __forceinline__ cx<R> propagator_hs(const double* k, int kind, const 
   return kind == 1 ? cx<R>(-ai, ar) : cx<R>(ai, -ar);
 }
 
-// Phase 1: momenta; momentum-table entries as FP64 signed sums of the external
+// ---- double-float arithmetic for the mixed mode ---------------------------------
+// A value as an unevaluated sum hi + lo of two FP32 numbers.  Sums use Knuth's
+// error-free TwoSum (the rounding error of a + b is exactly representable and
+// recovered with six additions) accumulated as in the cascaded summation of
+// Ogita, Rump and Oishi (SIAM J. Sci. Comput. 26, 2005); squares use the
+// FMA-based exact product.  The result is as accurate as a sum evaluated in
+// twice the FP32 precision and then rounded — ample for momentum sums rounded
+// to FP32 and for k^2 - m^2 near a pole — while GB300 runs FP32 at 64 times its
+// FP64 rate.
+struct dfl {
+  float hi, lo;
+};
+__device__ __forceinline__ dfl two_sum(float a, float b) {
+  const float s = a + b, bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ dfl dfl_split(double x) {
+  const float h = (float)x;
+  return {h, (float)(x - (double)h)};
+}
+// sum of signed terms t_k = hi_k + lo_k, k = 0..n-1
+struct DflSum {
+  float s, err;
+  __device__ __forceinline__ void first(float hi, float lo) { s = hi; err = lo; }
+  __device__ __forceinline__ void add(float hi, float lo) {
+    const dfl t = two_sum(s, hi);
+    s = t.hi;
+    err += t.lo + lo;
+  }
+  __device__ __forceinline__ float value() const { return s + err; }
+};
+
+// Propagator factor from a double-float momentum: k^2 - m^2 summed error-free
+// from the exact squares of the components, then the reciprocal in FP32.
+// m2 = m^2 as double-float, mw = m w.
+__device__ __forceinline__ cx<float> propagator_dfl(const float2* k, int kind, dfl m2, float mw) {
+  DflSum d;
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    const float h = k[mu].x, l = k[mu].y;
+    const float p = h * h;
+    float e = fmaf(h, h, -p);
+    e = fmaf(2.0f * h, l, e);
+    if (mu == 0) d.first(p, e);
+    else d.add(-p, -e);
+  }
+  float di = 0.0f;
+  if (kind == 1 || kind == 3) {
+    d.add(-m2.hi, -m2.lo);
+    di = mw;
+  }
+  const float r = d.value();
+  const float inv = 1.0f / (r * r + di * di);
+  const float ar = r * inv, ai = -di * inv;
+  return kind == 1 ? cx<float>(-ai, ar) : cx<float>(ai, -ar);
+}
+
+// Phase 1: momenta; momentum-table entries as signed sums of the external
 // momenta (one thread per (event, component) walks all entries with the leg
-// masks known at compile time: |S| - 1 additions per entry, no wasted FP64
-// work), rounded to R and kept in FP64 for the propagators; the external
-// wavefunctions (level 0 of the current program) straight from the momenta;
-// then the propagator of every line (one thread per (event, propagator)).
+// masks known at compile time: |S| - 1 additions per entry), in FP64 (FP64
+// mode) or double-float (mixed mode), rounded to R and kept unrounded for the
+// propagators; the external wavefunctions (level 0 of the current program)
+// straight from the momenta; then the propagator of every line (one thread
+// per (event, propagator)).
 template <class P, class R, class L>
 __device__ __forceinline__ void hs_event_tables(unsigned char* smem, const SigArgs& a, int64_t e0, int nev,
                                                 uint4* curs, const Couplings<R>& cp) {
   constexpr int NT = L::NT;
   constexpr int NEXT = P::hs_level(1);  // external variants
   constexpr int CUR_EV = P::HS_NSLOT * Slots<R, 1>::NPL;
+  constexpr bool DF = sizeof(R) == 4;
   const int tid = threadIdx.x;
   auto p = reinterpret_cast<double(*)[P::NPAR][4]>(smem + L::o_p);
   auto K = reinterpret_cast<R(*)[P::NMOM][4]>(smem + L::o_K);
   auto Kd = reinterpret_cast<double(*)[P::NMOM][4]>(smem + L::o_Kd);
+  auto Kf = reinterpret_cast<float2(*)[P::NMOM][4]>(smem + L::o_Kd);
   auto pr = reinterpret_cast<cx<R>(*)[P::NPROP]>(smem + L::o_pr);
   const int2* prop_tab = reinterpret_cast<const int2*>(smem + L::o_proptab);
   for (int t = tid; t < nev * P::NPAR * 4; t += NT) {
@@ -245,22 +307,48 @@ __device__ __forceinline__ void hs_event_tables(unsigned char* smem, const SigAr
   for (int t = tid; t < nev * (4 + NEXT); t += NT) {
     if (t < nev * 4) {
       const int e = t >> 2, mu = t & 3;
-      double q[P::NPAR];
-#pragma unroll
-      for (int l = 0; l < P::NPAR; ++l) q[l] = p[e][l][mu];
-#pragma unroll
-      for (int j = 0; j < P::NMOM; ++j) {
-        double k = 0.0;
-        bool first = true;
+      if constexpr (DF) {
+        float qh[P::NPAR], ql[P::NPAR];
 #pragma unroll
         for (int l = 0; l < P::NPAR; ++l) {
-          if (!(P::mom(j, 1) >> l & 1)) continue;
-          const bool neg = P::mom(j, 0) == 1 && (P::mom(j, 2) >> l & 1);
-          k = first ? (neg ? -q[l] : q[l]) : (neg ? k - q[l] : k + q[l]);
-          first = false;
+          const dfl q = dfl_split(p[e][l][mu]);
+          qh[l] = q.hi;
+          ql[l] = q.lo;
         }
-        K[e][j][mu] = R(k);
-        Kd[e][j][mu] = k;
+#pragma unroll
+        for (int j = 0; j < P::NMOM; ++j) {
+          DflSum k;
+          bool first = true;
+#pragma unroll
+          for (int l = 0; l < P::NPAR; ++l) {
+            if (!(P::mom(j, 1) >> l & 1)) continue;
+            const bool neg = P::mom(j, 0) == 1 && (P::mom(j, 2) >> l & 1);
+            const float h = neg ? -qh[l] : qh[l], lo = neg ? -ql[l] : ql[l];
+            if (first) k.first(h, lo);
+            else k.add(h, lo);
+            first = false;
+          }
+          K[e][j][mu] = k.value();
+          Kf[e][j][mu] = make_float2(k.s, k.err);
+        }
+      } else {
+        double q[P::NPAR];
+#pragma unroll
+        for (int l = 0; l < P::NPAR; ++l) q[l] = p[e][l][mu];
+#pragma unroll
+        for (int j = 0; j < P::NMOM; ++j) {
+          double k = 0.0;
+          bool first = true;
+#pragma unroll
+          for (int l = 0; l < P::NPAR; ++l) {
+            if (!(P::mom(j, 1) >> l & 1)) continue;
+            const bool neg = P::mom(j, 0) == 1 && (P::mom(j, 2) >> l & 1);
+            k = first ? (neg ? -q[l] : q[l]) : (neg ? k - q[l] : k + q[l]);
+            first = false;
+          }
+          K[e][j][mu] = R(k);
+          Kd[e][j][mu] = k;
+        }
       }
     } else {
       const int t2 = t - nev * 4, e = t2 / NEXT;
@@ -276,10 +364,20 @@ __device__ __forceinline__ void hs_event_tables(unsigned char* smem, const SigAr
     }
   }
   __syncthreads();
-  for (int t = tid; t < nev * P::NPROP; t += NT) {
-    const int e = t / P::NPROP, j = t - e * P::NPROP;
-    const int2 m = prop_tab[j];  // momentum entry, line kind
-    pr[e][j] = propagator_hs<R>(Kd[e][m.x], m.y, a.pp);
+  if constexpr (DF) {
+    const float4* mc = reinterpret_cast<const float4*>(smem + L::o_mconst);
+    for (int t = tid; t < nev * P::NPROP; t += NT) {
+      const int e = t / P::NPROP, j = t - e * P::NPROP;
+      const int2 m = prop_tab[j];  // momentum entry, line kind
+      const float4 c = mc[m.y == 3 ? 1 : 0];  // {m^2 hi, m^2 lo, m w, 0} of the top / the Z
+      pr[e][j] = propagator_dfl(Kf[e][m.x], m.y, dfl{c.x, c.y}, c.z);
+    }
+  } else {
+    for (int t = tid; t < nev * P::NPROP; t += NT) {
+      const int e = t / P::NPROP, j = t - e * P::NPROP;
+      const int2 m = prop_tab[j];  // momentum entry, line kind
+      pr[e][j] = propagator_hs<R>(Kd[e][m.x], m.y, a.pp);
+    }
   }
   __syncthreads();
 }
@@ -344,6 +442,13 @@ __global__ void __launch_bounds__(HsCfg<P, R>::NT, HsCfg<P, R>::CTAS) sigmakin_h
     for (int j = 0; j < P::NPROP; ++j)
       if (tid == j) v = make_int2(P::prop(j, 0), P::prop(j, 1));
     reinterpret_cast<int2*>(smem + L::o_proptab)[tid] = v;
+  }
+  if constexpr (sizeof(R) == 4) {
+    if (tid < 2) {
+      const double m = tid == 0 ? a.pp.mt : a.pp.mz, w = tid == 0 ? a.pp.wt : a.pp.wz;
+      const dfl m2 = dfl_split(m * m);
+      reinterpret_cast<float4*>(smem + L::o_mconst)[tid] = make_float4(m2.hi, m2.lo, (float)(m * w), 0.0f);
+    }
   }
   // good helicities: one ballot word per 32 helicities in misc[2..3]
   static_assert(P::NHEL <= 64 && NT >= P::NHEL, "helicity ballot layout");
