@@ -455,16 +455,10 @@ __global__ void __launch_bounds__(HsCfg<P, R>::NT, HsCfg<P, R>::CTAS) sigmakin_h
   const bool hgood = tid < P::NHEL && a.mask[tid] != 0;
   const unsigned hb = __ballot_sync(0xffffffffu, hgood);
   if (tid < P::NHEL && (tid & 31) == 0) misc[2 + (tid >> 5)] = (int)hb;
-  // vt[S][ihel]: bits of the legs in S (ascending) of helicity ihel, where
-  // leg l is +1 when bit NPAR-1-l of ihel is set
-  for (int i = tid; i < (1 << P::NPAR) * P::NHEL; i += NT) {
-    const int S = i / P::NHEL, ih = i % P::NHEL;
-    int v = 0, k = 0;
-#pragma unroll
-    for (int l = 0; l < P::NPAR; ++l)
-      if (S >> l & 1) v |= ((ih >> (P::NPAR - 1 - l)) & 1) << k++;
-    vtab[i] = (uint8_t)v;
-  }
+  // vt[S][ihel]: variant index of leg set S for helicity ihel (generated table)
+  static_assert(((1 << P::NPAR) * P::NHEL) % 16 == 0, "variant table copied in 16-byte words");
+  for (int i = tid; i < (1 << P::NPAR) * P::NHEL / 16; i += NT)
+    reinterpret_cast<uint4*>(vtab)[i] = reinterpret_cast<const uint4*>(P::hs_variants())[i];
   __syncthreads();
   // good[] in helicity order (read only after later barriers)
   const unsigned w0 = (unsigned)misc[2], w1 = P::NHEL > 32 ? (unsigned)misc[3] : 0u;

@@ -1275,6 +1275,19 @@ class SharedProgram:
                 for (t, a, b, c, flag, o, ins, k0, k1, pr) in items)))
         out.append("static __constant__ int kHsXItem%d[%d] = {%s};  // item ranges of the amputated chunks"
                    % (pid, len(xitem_start), ", ".join(map(str, xitem_start))))
+        # variant of every leg set S for every event helicity h: the bits of the
+        # legs of S in ascending order, leg l being +1 when bit n-1-l of h is set
+        var = []
+        for S in range(1 << self.n):
+            for ih in range(nh):
+                v = k = 0
+                for l in range(self.n):
+                    if S >> l & 1:
+                        v |= ((ih >> (self.n - 1 - l)) & 1) << k
+                        k += 1
+                var.append(v)
+        out.append("static __device__ __align__(16) const uint8_t kHsVar%d[%d] = {%s};  // [leg set][helicity]"
+                   % (pid, len(var), ", ".join(map(str, var))))
         return out
 
     def _exact_flops(self, items, amps):
@@ -1314,6 +1327,7 @@ class SharedProgram:
             "  // item ranges of the current levels and of the amputated chunks; amplitude ranges of the chunks",
         ] + table_fn("hs_level", t["level_start"]) + [
             "  static __device__ __forceinline__ int hs_xitem(int c) { return kHsXItem%d[c]; }" % pid,
+            "  static __device__ __forceinline__ const uint8_t* hs_variants() { return kHsVar%d; }" % pid,
             "  static __device__ __forceinline__ const HsItem* hs_items() { return kHsItems%d; }" % pid,
         ] + self._contract_code()
 
