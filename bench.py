@@ -207,6 +207,40 @@ def measure_other_workloads(mg, I, dev, stream, reps: int = 3) -> dict:
     return out
 
 
+def measure_generation(mg, proc, ecm, nevt, seed, mom, wgt, me, sums, stream, hbm_gbs, reps=3):
+    import torch
+
+    def time_it(fn):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 1e3 / reps
+
+    from paper_2106_12631_gb300 import inputs as I
+    rnd = torch.from_numpy(I.uniforms(seed, 16, nevt)).to(mom.device)
+    mom2, wgt2 = torch.empty_like(mom), torch.empty_like(wgt)
+    t_buf = time_it(lambda: mg.rambo(proc, rnd, ecm, mom=mom2, wgt=wgt2, stream=stream))
+    t_seed = time_it(lambda: mg.rambo_seeded(proc, nevt, ecm, seed, 0, mom=mom2, wgt=wgt2, stream=stream))
+    idx = torch.empty(nevt, dtype=torch.int64, device=mom.device)
+    cnt = torch.empty(1, dtype=torch.int64, device=mom.device)
+    scratch = torch.empty(mg.unweight_scratch_bytes(nevt) // 8 + 2, dtype=torch.float64, device=mom.device)
+    t_uw = time_it(lambda: mg.unweight(me, wgt, seed, 0, idx=idx, count=cnt, scratch=scratch, stream=stream))
+    kept = int(cnt.item())
+    xs = mg.cross_section(proc, ecm, sums, stream=stream).cpu().numpy()
+    uw_bytes = 3 * 16 * nevt + 8 * kept  # (w, me) read by three passes, kept indices written
+    return {"events": nevt,
+            "rambo_device_rng_ms": 1e3 * t_seed, "rambo_buffered_ms": 1e3 * t_buf,
+            "unweight_ms": 1e3 * t_uw, "unweight_kept": kept,
+            "unweight_gbs": uw_bytes / t_uw / 1e9,
+            "unweight_hbm_frac": (uw_bytes / t_uw / 1e9) / hbm_gbs if hbm_gbs else None,
+            "cross_section_pb": float(xs[0]), "cross_section_err_pb": float(xs[1])}
+
+
 def cpu_oracle_rate(nevt_sample: int, seed: int, threads: int):
     """Oracle ME/s on the host cores for a bounded sample (RAMBO + |M|^2, FP64)."""
     import numpy as np
@@ -362,6 +396,13 @@ def main():
                                           "nonfinite": int((~torch.isfinite(me_main)).sum().item()),
                                           "events": nevt}}
 
+    # event generation from the step's weighted events: device-RNG RAMBO (vs the
+    # buffered one), cross section, hit-or-miss unweighting (CUDA events)
+    generation = None
+    if not args.no_others:
+        generation = measure_generation(mg, proc, ecm, nevt, seed, mom, wgt, me, out, stream,
+                                        measured_peaks().get("hbm_gbs"))
+
     # the other workloads (SIGMAKIN or the adjoint alone, inputs resident, CUDA events)
     others = {} if args.no_others else measure_other_workloads(mg, I, dev, stream)
 
@@ -435,6 +476,7 @@ def main():
         "unrolled": unrolled,
         "tensor_core_colour_sum": tensor_core,
         "other_workloads": others,
+        "event_generation": generation,
         "event_sum": [float(x) for x in sums.cpu().numpy()],
         "roofline": roofline,
         "clocks": clk,

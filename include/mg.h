@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define MG_ABI_VERSION 2
+#define MG_ABI_VERSION 3
 
 typedef enum {
   MG_OK = 0,
@@ -167,6 +167,37 @@ int mg_event_sum(int64_t nevt, const double* me, const double* wgt, double* out3
  * them.  Results are identical to mg_event_sum's. */
 int64_t mg_event_sum_noalloc_max_events(void);
 int mg_event_sum_noalloc(int64_t nevt, const double* me, const double* wgt, double* out3, void* stream);
+
+/* RAMBO with the uniforms drawn on the device (Sec. 3's random numbers fused
+ * into the phase-space kernel; no random-number buffer): the uniform of event
+ * i, row k is SplitMix64 used as a counter-based generator,
+ *   key = mix(seed), z = mix(key + (64 (first_event + i) + k + 1) * 0x9E3779B97F4A7C15),
+ *   u = ((z >> 11) + 0.5) 2^-53,
+ * mix = SplitMix64's finaliser (Steele, Lea, Flood, OOPSLA 2014); rows
+ * 0 .. 4 nfinal - 1 feed RAMBO as in mg_rambo, whose results these equal for
+ * the same uniforms.  mom, wgt: device, as for mg_rambo.  first_event >= 0 and
+ * first_event + nevt <= 2^57, else MG_ERR_ARG. */
+int mg_rambo_seeded(int proc, int64_t nevt, double ecm, uint64_t seed, int64_t first_event, double* mom,
+                    double* wgt, void* stream);
+
+/* Cross section from the event sums (Sec. 3: the average of the weighted
+ * matrix elements of a run gives the cross section): sums3 = {sum w me,
+ * sum (w me)^2, N} from mg_event_sum (device); xsec2 (device) receives
+ * sigma = (hbar c)^2 (2 pi)^(4 - 3 nfinal) / (2 s) * (sum w me) / N  in pb and
+ * its Monte Carlo error from the sample variance (0 for N <= 1).  The flux
+ * 1/(2 s) is that of massless beams; w is mg_rambo's flat weight. */
+int mg_cross_section(int proc, double ecm, const double* sums3, double* xsec2, void* stream);
+
+/* Hit-or-miss unweighting (the toy workflow's unweighted events): with
+ * x_i = wgt_i me_i and u_i the generator's uniform for (seed, first_event + i,
+ * row 63), event i is kept iff u_i * max_j x_j < x_i.  The kept event indices
+ * (0-based within this batch) are written to idx in increasing order and their
+ * number to *count (device int64).  idx must hold nevt entries (the worst case).
+ * scratch: device, >= mg_unweight_scratch_bytes(nevt) bytes, else MG_ERR_SPACE.
+ * Deterministic: the same inputs give the same indices.  nevt <= 2^41. */
+int64_t mg_unweight_scratch_bytes(int64_t nevt);
+int mg_unweight(int64_t nevt, const double* me, const double* wgt, uint64_t seed, int64_t first_event,
+                int64_t* idx, int64_t* count, void* scratch, int64_t scratch_bytes, void* stream);
 
 /* End-to-end pipeline from HOST buffers (copies inside): h_rnd [nrows][nevt]
  * -> host-to-device copy -> RAMBO -> SIGMAKIN (mask from mg_filter_helicities,

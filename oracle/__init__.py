@@ -207,3 +207,31 @@ def event_sum(me_: np.ndarray, wgt: np.ndarray) -> np.ndarray:
     out = np.zeros(3)
     _chk(lib().oracle_event_sum(me_.shape[0], _p(me_), _p(wgt), _p(out)), "event_sum")
     return out
+
+
+# ---- cross section and unweighting (Sec. 3: the run's weighted events give the
+# cross section; unweighting keeps events with probability x / max x) ----------
+HBARC2_PB = 0.3893793721e9  # (hbar c)^2 in pb GeV^2
+
+
+def cross_section(proc: int, ecm: float, me_: np.ndarray, wgt: np.ndarray) -> np.ndarray:
+    """(sigma, error) in pb: sigma = (hbar c)^2 (2 pi)^(4 - 3 n) / (2 s) mean(w me),
+    the Monte Carlo error from the sample variance (flux of massless beams,
+    w = RAMBO's flat phase-space weight without (2 pi) factors)."""
+    nf = NPAR[proc] - 2
+    sums = event_sum(me_, wgt)
+    n = sums[2]
+    mean = sums[0] / n
+    var = (sums[1] / n - mean * mean) * n / (n - 1) if n > 1 else 0.0
+    norm = HBARC2_PB * (2 * np.pi) ** (4 - 3 * nf) / (2 * ecm * ecm)
+    return np.array([norm * mean, norm * np.sqrt(max(var, 0.0) / n)])
+
+
+def unweight(me_: np.ndarray, wgt: np.ndarray, u: np.ndarray) -> np.ndarray:
+    """Hit-or-miss: indices i (increasing) with u_i * max_j x_j < x_i, x = w me."""
+    x = np.asarray(wgt, dtype=np.float64) * np.asarray(me_, dtype=np.float64)
+    if x.size == 0:
+        return np.zeros(0, dtype=np.int64)
+    xmax = x.max()
+    return np.nonzero(np.asarray(u, dtype=np.float64) * xmax < x)[0].astype(np.int64)
+

@@ -21,8 +21,13 @@ struct SigLaunch {
   Couplings<float> cf;
 };
 
+// rnd == nullptr: uniforms drawn on the device from (seed, first_event + i, row)
 cudaError_t launch_rambo(int nfinal, int64_t nevt, double ecm, const double* rnd, double* mom, double* wgt,
-                         const RamboSetup& st, cudaStream_t s);
+                         const RamboSetup& st, cudaStream_t s, uint64_t seed = 0, int64_t first_event = 0);
+int64_t unweight_blocks(int64_t n);
+cudaError_t launch_unweight(int64_t n, const double* me, const double* w, uint64_t seed, int64_t first_event,
+                            int64_t* idx, int64_t* count, double* scratch, cudaStream_t s);
+cudaError_t launch_cross_section(const double* sums, double norm, double* out, cudaStream_t s);
 int64_t event_sum_blocks(int64_t n);
 cudaError_t launch_event_sum(int64_t n, const double* me, const double* w, double* out3, double* partial,
                              cudaStream_t s);

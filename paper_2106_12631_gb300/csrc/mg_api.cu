@@ -177,6 +177,53 @@ int mg_rambo(int proc, int64_t nevt, double ecm, const double* rnd, int nrows, d
   return cuda_status(mg::launch_rambo(d.npar - 2, nevt, ecm, rnd, mom, wgt, st, (cudaStream_t)stream));
 }
 
+int mg_rambo_seeded(int proc, int64_t nevt, double ecm, uint64_t seed, int64_t first_event, double* mom,
+                    double* wgt, void* stream) {
+  if (!valid_proc(proc)) return MG_ERR_PROC;
+  const ProcDesc& d = kProcs[proc];
+  if (nevt < 0 || first_event < 0 || !(ecm > 0) || !std::isfinite(ecm)) return MG_ERR_ARG;
+  if (first_event > ((int64_t)1 << 57) - nevt) return MG_ERR_ARG;  // event counters stay below 2^57
+  mg::RamboSetup st;
+  if (int r = rambo_setup(proc, ecm, st)) return r;
+  if (nevt == 0) return MG_OK;
+  if (!mom || !wgt) return MG_ERR_ARG;
+  if (!aligned(mom) || !aligned(wgt)) return MG_ERR_ALIGN;
+  if (nevt > (int64_t)INT32_MAX * 64) return MG_ERR_ARG;
+  return cuda_status(
+      mg::launch_rambo(d.npar - 2, nevt, ecm, nullptr, mom, wgt, st, (cudaStream_t)stream, seed, first_event));
+}
+
+int mg_cross_section(int proc, double ecm, const double* sums3, double* xsec2, void* stream) {
+  if (!valid_proc(proc)) return MG_ERR_PROC;
+  if (!(ecm > 0) || !std::isfinite(ecm) || !sums3 || !xsec2) return MG_ERR_ARG;
+  if (!aligned(sums3) || !aligned(xsec2)) return MG_ERR_ALIGN;
+  // sigma = (hbar c)^2 (2 pi)^(4 - 3 n) / (2 s) * mean(w |M|^2); (hbar c)^2 = 0.3893793721 mb GeV^2
+  const int nf = kProcs[proc].npar - 2;
+  const double hbarc2_pb = 0.3893793721e9;
+  const double norm = hbarc2_pb * std::pow(2.0 * M_PI, 4.0 - 3.0 * nf) / (2.0 * ecm * ecm);
+  return cuda_status(mg::launch_cross_section(sums3, norm, xsec2, (cudaStream_t)stream));
+}
+
+int64_t mg_unweight_scratch_bytes(int64_t nevt) {
+  if (nevt < 0) return -1;
+  return 8 * (1 + 2 * mg::unweight_blocks(nevt));
+}
+
+int mg_unweight(int64_t nevt, const double* me, const double* wgt, uint64_t seed, int64_t first_event,
+                int64_t* idx, int64_t* count, void* scratch, int64_t scratch_bytes, void* stream) {
+  if (nevt < 0 || first_event < 0 || !count) return MG_ERR_ARG;
+  if (first_event > ((int64_t)1 << 57) - nevt) return MG_ERR_ARG;
+  if (!aligned(count) || (me && !aligned(me)) || (wgt && !aligned(wgt)) || (idx && !aligned(idx)) ||
+      (scratch && !aligned(scratch)))
+    return MG_ERR_ALIGN;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (nevt == 0) return cuda_status(cudaMemsetAsync(count, 0, sizeof(int64_t), s));
+  if (!me || !wgt || !idx || !scratch) return MG_ERR_ARG;
+  if (nevt > (int64_t)INT32_MAX * 1024) return MG_ERR_ARG;
+  if (scratch_bytes < mg_unweight_scratch_bytes(nevt)) return MG_ERR_SPACE;
+  return cuda_status(mg::launch_unweight(nevt, me, wgt, seed, first_event, idx, count, (double*)scratch, s));
+}
+
 int mg_filter_helicities(int proc, int64_t nevt, const double* mom, int32_t* mask, void* stream) {
   if (!valid_proc(proc)) return MG_ERR_PROC;
   if (nevt < 0) return MG_ERR_ARG;

@@ -15,18 +15,26 @@
 
 #include "launch.h"
 #include "rambo.cuh"
+#include "rng.cuh"
 
 namespace mg {
 
+// Uniforms of one event: from a buffer rnd[k][nevt], or (rnd == nullptr)
+// drawn on the device from the counter-based generator (key, event index).
 template <int NF>
 __global__ void __launch_bounds__(128) rambo_kernel(int64_t nevt, double ecm, const double* __restrict__ rnd,
                                                     double* __restrict__ mom, double* __restrict__ wgt,
-                                                    RamboSetup st) {
+                                                    RamboSetup st, uint64_t key, int64_t first_event) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nevt) return;
   double r[4 * NF];
+  if (rnd) {
 #pragma unroll
-  for (int k = 0; k < 4 * NF; ++k) r[k] = rnd[(int64_t)k * nevt + i];
+    for (int k = 0; k < 4 * NF; ++k) r[k] = rnd[(int64_t)k * nevt + i];
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4 * NF; ++k) r[k] = sm64_uniform(key, first_event + i, k);
+  }
   RamboState<NF> z;
   rambo_forward<NF>(r, ecm, st, z);
   const double h = 0.5 * ecm;
@@ -41,13 +49,14 @@ __global__ void __launch_bounds__(128) rambo_kernel(int64_t nevt, double ecm, co
 }
 
 cudaError_t launch_rambo(int nfinal, int64_t nevt, double ecm, const double* rnd, double* mom, double* wgt,
-                         const RamboSetup& st, cudaStream_t s) {
+                         const RamboSetup& st, cudaStream_t s, uint64_t seed, int64_t first_event) {
   const int nt = 128;
   const int64_t grid = (nevt + nt - 1) / nt;
+  const uint64_t key = sm64_mix(seed);
   switch (nfinal) {
-    case 2: rambo_kernel<2><<<(unsigned)grid, nt, 0, s>>>(nevt, ecm, rnd, mom, wgt, st); break;
-    case 3: rambo_kernel<3><<<(unsigned)grid, nt, 0, s>>>(nevt, ecm, rnd, mom, wgt, st); break;
-    case 4: rambo_kernel<4><<<(unsigned)grid, nt, 0, s>>>(nevt, ecm, rnd, mom, wgt, st); break;
+    case 2: rambo_kernel<2><<<(unsigned)grid, nt, 0, s>>>(nevt, ecm, rnd, mom, wgt, st, key, first_event); break;
+    case 3: rambo_kernel<3><<<(unsigned)grid, nt, 0, s>>>(nevt, ecm, rnd, mom, wgt, st, key, first_event); break;
+    case 4: rambo_kernel<4><<<(unsigned)grid, nt, 0, s>>>(nevt, ecm, rnd, mom, wgt, st, key, first_event); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

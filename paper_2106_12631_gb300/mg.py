@@ -63,6 +63,12 @@ def lib():
             L.mg_event_sum_scratch_bytes.argtypes = [i64]
             L.mg_event_sum_scratch_bytes.restype = i64
             L.mg_event_sum.argtypes = [i64, vp, vp, vp, vp, i64, vp]
+            u64 = ctypes.c_uint64
+            L.mg_rambo_seeded.argtypes = [i32, i64, ctypes.c_double, u64, i64, vp, vp, vp]
+            L.mg_cross_section.argtypes = [i32, ctypes.c_double, vp, vp, vp]
+            L.mg_unweight_scratch_bytes.argtypes = [i64]
+            L.mg_unweight_scratch_bytes.restype = i64
+            L.mg_unweight.argtypes = [i64, vp, vp, u64, i64, vp, vp, vp, i64, vp]
             L.mg_event_sum_noalloc_max_events.argtypes = []
             L.mg_event_sum_noalloc_max_events.restype = i64
             L.mg_event_sum_noalloc.argtypes = [i64, vp, vp, vp, vp]
@@ -134,6 +140,55 @@ def rambo(proc, rnd: torch.Tensor, ecm: float, mom=None, wgt=None, stream=None):
                           _dev(mom, torch.float64, "mom", (npar, 4, nevt)),
                           _dev(wgt, torch.float64, "wgt", (nevt,)), _stream(stream)), "mg_rambo")
     return mom, wgt
+
+
+def rambo_seeded(proc, nevt: int, ecm: float, seed: int, first_event: int = 0, mom=None, wgt=None, device=None,
+                 stream=None):
+    """RAMBO with the uniforms drawn on the device (counter-based, as inputs.uniforms)."""
+    p = _proc(proc)
+    npar = process_info(p)["npar"]
+    dev = device if device is not None else (mom.device if mom is not None else torch.device("cuda"))
+    if mom is None:
+        mom = torch.empty((npar, 4, nevt), dtype=torch.float64, device=dev)
+    if wgt is None:
+        wgt = torch.empty((nevt,), dtype=torch.float64, device=dev)
+    _check(lib().mg_rambo_seeded(p, nevt, float(ecm), seed & 0xFFFFFFFFFFFFFFFF, first_event,
+                                 _dev(mom, torch.float64, "mom", (npar, 4, nevt)),
+                                 _dev(wgt, torch.float64, "wgt", (nevt,)), _stream(stream)), "mg_rambo_seeded")
+    return mom, wgt
+
+
+def cross_section(proc, ecm: float, sums: torch.Tensor, out=None, stream=None) -> torch.Tensor:
+    """(sigma, error) in pb on the device from the event sums of mg_event_sum."""
+    if out is None:
+        out = torch.empty((2,), dtype=torch.float64, device=sums.device)
+    _check(lib().mg_cross_section(_proc(proc), float(ecm), _dev(sums, torch.float64, "sums", (3,)),
+                                  _dev(out, torch.float64, "out", (2,)), _stream(stream)), "mg_cross_section")
+    return out
+
+
+def unweight_scratch_bytes(nevt: int) -> int:
+    return int(lib().mg_unweight_scratch_bytes(nevt))
+
+
+def unweight(me: torch.Tensor, wgt: torch.Tensor, seed: int, first_event: int = 0, idx=None, count=None,
+             scratch=None, stream=None):
+    """Hit-or-miss unweighting: (idx (nevt,) int64 with the kept indices first, count (1,) int64)."""
+    nevt = me.shape[0]
+    if idx is None:
+        idx = torch.empty((max(nevt, 1),), dtype=torch.int64, device=me.device)
+    if idx.numel() < nevt:
+        raise ValueError("idx must hold nevt entries")
+    if count is None:
+        count = torch.empty((1,), dtype=torch.int64, device=me.device)
+    nb = unweight_scratch_bytes(nevt)
+    if scratch is None:
+        scratch = torch.empty((max(nb, 16) + 7) // 8, dtype=torch.float64, device=me.device)
+    _check(lib().mg_unweight(nevt, _dev(me, torch.float64, "me", (nevt,)), _dev(wgt, torch.float64, "wgt", (nevt,)),
+                             seed & 0xFFFFFFFFFFFFFFFF, first_event, _dev(idx, torch.int64, "idx"),
+                             _dev(count, torch.int64, "count", (1,)), scratch.data_ptr(),
+                             scratch.numel() * scratch.element_size(), _stream(stream)), "mg_unweight")
+    return idx, count
 
 
 def filter_helicities(proc, mom: torch.Tensor, mask=None, stream=None) -> torch.Tensor:
