@@ -24,15 +24,16 @@
 namespace mg {
 
 #ifndef MG_HS_NT
-#define MG_HS_NT 512
+#define MG_HS_NT 256
 #endif
 #ifndef MG_HS_CTAS
-#define MG_HS_CTAS 1  // resident CTAs per SM the shared-memory budget is split for
+#define MG_HS_CTAS 2  // resident CTAs per SM the shared-memory budget is split for
 #endif
 
-// One large CTA per SM for the many-colour processes: its warps walk the same
-// amplitude table in near lockstep and share instruction fetches.  FP64 needs
-// more registers per thread, hence fewer threads.
+// Many-colour processes in FP32: two 256-thread CTAs per SM (4 events x 64
+// helicities each for gg -> t t~ g g), so that one CTA's short barrier-bound
+// phases overlap the other's contractions.  FP64 needs more registers per
+// thread: one 256-thread CTA per SM.
 template <class P, class R>
 struct HsCfg {
   static constexpr int NT = P::NCOLOR >= 6 ? (sizeof(R) == 4 ? MG_HS_NT : 256) : 128;
