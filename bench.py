@@ -232,13 +232,23 @@ def measure_generation(mg, proc, ecm, nevt, seed, mom, wgt, me, sums, stream, hb
     t_uw = time_it(lambda: mg.unweight(me, wgt, seed, 0, idx=idx, count=cnt, scratch=scratch, stream=stream))
     kept = int(cnt.item())
     xs = mg.cross_section(proc, ecm, sums, stream=stream).cpu().numpy()
+    scr = torch.empty(mg.event_sum_scratch_bytes(nevt) // 8 + 2, dtype=torch.float64, device=mom.device)
+    out3 = torch.empty(3, dtype=torch.float64, device=mom.device)
+    t_sum = time_it(lambda: mg.event_sum(me, wgt, out=out3, scratch=scr, stream=stream))
     uw_bytes = 3 * 16 * nevt + 8 * kept  # (w, me) read by three passes, kept indices written
     return {"events": nevt,
             "rambo_device_rng_ms": 1e3 * t_seed, "rambo_buffered_ms": 1e3 * t_buf,
             "unweight_ms": 1e3 * t_uw, "unweight_kept": kept,
             "unweight_gbs": uw_bytes / t_uw / 1e9,
             "unweight_hbm_frac": (uw_bytes / t_uw / 1e9) / hbm_gbs if hbm_gbs else None,
-            "cross_section_pb": float(xs[0]), "cross_section_err_pb": float(xs[1])}
+            "cross_section_pb": float(xs[0]), "cross_section_err_pb": float(xs[1]),
+            "rooflines": {
+                "event_sum": {"bound": "hbm", "achieved": 16 * nevt / t_sum / 1e9, "peak": hbm_gbs,
+                              "unit": "GB/s", "frac": (16 * nevt / t_sum / 1e9) / hbm_gbs if hbm_gbs else None,
+                              "ms": 1e3 * t_sum, "bytes_per_event": 16},
+                "unweight": {"bound": "hbm", "achieved": uw_bytes / t_uw / 1e9, "peak": hbm_gbs, "unit": "GB/s",
+                             "frac": (uw_bytes / t_uw / 1e9) / hbm_gbs if hbm_gbs else None,
+                             "ms": 1e3 * t_uw, "bytes_per_event": 48}}}
 
 
 def cpu_oracle_rate(nevt_sample: int, seed: int, threads: int):

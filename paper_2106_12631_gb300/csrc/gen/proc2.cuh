@@ -65,6 +65,94 @@ struct Proc2 {
       default: break;
     }
   }
+  // adjoint of hs_contract: Jb -> atomic adds into curb (operands) and xbb (amputated);
+  // full = the warp's lanes are consecutive helicities of its event(s), all good
+  template <class R, class CUR, class XB>
+  static __device__ __forceinline__ void hs_contract_adj(int c, const CUR& cur, const XB& xb, const uint8_t* __restrict__ vt, const cx<R>* Jb, const CUR& curb, const XB& xbb, bool full, int lane) {
+    switch (c) {
+      case 0: {
+        {
+          const int vx = vt[144];
+          const W4<R> X = xb[0 + vx];
+          W4<R> Xb = w4_zero<R>();
+          {
+            const int vy = vt[96];
+            W4<R> Y = cur[16 + vy];
+            const cx<R> ab = Jb[1];
+            w4_acc_conj(Xb, Y, ab);
+            const W4<R> Yb = w4_conj_scale(X, ab);
+            if (full) {
+              W4<R> s = Yb;
+              w4_warp_sum<9u>(s);
+              if ((lane & 9u) == 0) curb.atomic_add(16 + vy, s);
+            } else {
+              curb.atomic_add(16 + vy, Yb);
+            }
+          }
+          if (full) {
+            W4<R> s = Xb;
+            w4_warp_sum<6u>(s);
+            if ((lane & 6u) == 0) xbb.atomic_add(0 + vx, s);
+          } else {
+            xbb.atomic_add(0 + vx, Xb);
+          }
+        }
+        {
+          const int vx = vt[160];
+          const W4<R> X = xb[4 + vx];
+          W4<R> Xb = w4_zero<R>();
+          {
+            const int vy = vt[80];
+            W4<R> Y = cur[12 + vy];
+            const cx<R> ab = Jb[0];
+            w4_acc_conj(Xb, Y, ab);
+            const W4<R> Yb = w4_conj_scale(X, ab);
+            if (full) {
+              W4<R> s = Yb;
+              w4_warp_sum<5u>(s);
+              if ((lane & 5u) == 0) curb.atomic_add(12 + vy, s);
+            } else {
+              curb.atomic_add(12 + vy, Yb);
+            }
+          }
+          if (full) {
+            W4<R> s = Xb;
+            w4_warp_sum<10u>(s);
+            if ((lane & 10u) == 0) xbb.atomic_add(4 + vx, s);
+          } else {
+            xbb.atomic_add(4 + vx, Xb);
+          }
+        }
+        {
+          const int vx = vt[192];
+          const W4<R> X = xb[8 + vx];
+          W4<R> Xb = w4_zero<R>();
+          {
+            const int vy = vt[48];
+            W4<R> Y = cur[8 + vy];
+            const cx<R> ab = mul_i(Jb[0]) + mul_mi(Jb[1]);
+            w4_acc_conj(Xb, Y, ab);
+            const W4<R> Yb = w4_conj_scale(X, ab);
+            if (full) {
+              W4<R> s = Yb;
+              w4_warp_sum<3u>(s);
+              if ((lane & 3u) == 0) curb.atomic_add(8 + vy, s);
+            } else {
+              curb.atomic_add(8 + vy, Yb);
+            }
+          }
+          if (full) {
+            W4<R> s = Xb;
+            w4_warp_sum<12u>(s);
+            if ((lane & 12u) == 0) xbb.atomic_add(8 + vx, s);
+          } else {
+            xbb.atomic_add(8 + vx, Xb);
+          }
+        }
+      } break;
+      default: break;
+    }
+  }
   static constexpr int NMOM = 9;
   static constexpr int NPROP = 3;
   static constexpr int NFINAL = 2;

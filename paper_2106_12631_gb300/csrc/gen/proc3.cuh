@@ -129,6 +129,406 @@ struct Proc3 {
       default: break;
     }
   }
+  // adjoint of hs_contract: Jb -> atomic adds into curb (operands) and xbb (amputated);
+  // full = the warp's lanes are consecutive helicities of its event(s), all good
+  template <class R, class CUR, class XB>
+  static __device__ __forceinline__ void hs_contract_adj(int c, const CUR& cur, const XB& xb, const uint8_t* __restrict__ vt, const cx<R>* Jb, const CUR& curb, const XB& xbb, bool full, int lane) {
+    switch (c) {
+      case 0: {
+        {
+          const int vx = vt[352];
+          const W4<R> X = xb[0 + vx];
+          W4<R> Xb = w4_zero<R>();
+          {
+            const int vy = vt[640];
+            W4<R> Y = cur[66 + vy];
+            const cx<R> ab = Jb[4];
+            w4_acc_conj(Xb, Y, ab);
+            const W4<R> Yb = w4_conj_scale(X, ab);
+            if (full) {
+              W4<R> s = Yb;
+              w4_warp_sum<26u>(s);
+              if ((lane & 26u) == 0) curb.atomic_add(66 + vy, s);
+            } else {
+              curb.atomic_add(66 + vy, Yb);
+            }
+          }
+          if (full) {
+            W4<R> s = Xb;
+            w4_warp_sum<5u>(s);
+            if ((lane & 5u) == 0) xbb.atomic_add(0 + vx, s);
+          } else {
+            xbb.atomic_add(0 + vx, Xb);
+          }
+        }
+        {
+          const int vx = vt[352];
+          const W4<R> X = xb[8 + vx];
+          W4<R> Xb = w4_zero<R>();
+          {
+            const int vy = vt[640];
+            W4<R> Y = cur[66 + vy];
+            const cx<R> ab = Jb[5];
+            w4_acc_conj(Xb, Y, ab);
+            const W4<R> Yb = w4_conj_scale(X, ab);
+            if (full) {
+              W4<R> s = Yb;
+              w4_warp_sum<26u>(s);
+              if ((lane & 26u) == 0) curb.atomic_add(66 + vy, s);
+            } else {
+              curb.atomic_add(66 + vy, Yb);
+            }
+          }
+          if (full) {
+            W4<R> s = Xb;
+            w4_warp_sum<5u>(s);
+            if ((lane & 5u) == 0) xbb.atomic_add(8 + vx, s);
+          } else {
+            xbb.atomic_add(8 + vx, Xb);
+          }
+        }
+        {
+          const int vx = vt[352];
+          const W4<R> X = xb[16 + vx];
+          W4<R> Xb = w4_zero<R>();
+          {
+            const int vy = vt[640];
+            W4<R> Y = cur[66 + vy];
+            const cx<R> ab = mul_i(Jb[4]) + mul_mi(Jb[5]);
+            w4_acc_conj(Xb, Y, ab);
+            const W4<R> Yb = w4_conj_scale(X, ab);
+            if (full) {
+              W4<R> s = Yb;
+              w4_warp_sum<26u>(s);
+              if ((lane & 26u) == 0) curb.atomic_add(66 + vy, s);
+            } else {
+              curb.atomic_add(66 + vy, Yb);
+            }
+          }
+          if (full) {
+            W4<R> s = Xb;
+            w4_warp_sum<5u>(s);
+            if ((lane & 5u) == 0) xbb.atomic_add(16 + vx, s);
+          } else {
+            xbb.atomic_add(16 + vx, Xb);
+          }
+        }
+        {
+          const int vx = vt[800];
+          const W4<R> X = xb[24 + vx];
+          W4<R> Xb = w4_zero<R>();
+          {
+            const int vy = vt[192];
+            W4<R> Y = cur[62 + vy];
+            const cx<R> ab = Jb[2];
+            w4_acc_conj(Xb, Y, ab);
+            const W4<R> Yb = w4_conj_scale(X, ab);
+            if (full) {
+              W4<R> s = Yb;
+              w4_warp_sum<19u>(s);
+              if ((lane & 19u) == 0) curb.atomic_add(62 + vy, s);
+            } else {
+              curb.atomic_add(62 + vy, Yb);
+            }
+          }
+          if (full) {
+            W4<R> s = Xb;
+            w4_warp_sum<12u>(s);
+            if ((lane & 12u) == 0) xbb.atomic_add(24 + vx, s);
+          } else {
+            xbb.atomic_add(24 + vx, Xb);
+          }
+        }
+        {
+          const int vx = vt[800];
+          const W4<R> X = xb[32 + vx];
+          W4<R> Xb = w4_zero<R>();
+          {
+            const int vy = vt[192];
+            W4<R> Y = cur[62 + vy];
+            const cx<R> ab = mul_i(Jb[2]) + mul_mi(Jb[3]);
+            w4_acc_conj(Xb, Y, ab);
+            const W4<R> Yb = w4_conj_scale(X, ab);
+            if (full) {
+              W4<R> s = Yb;
+              w4_warp_sum<19u>(s);
+              if ((lane & 19u) == 0) curb.atomic_add(62 + vy, s);
+            } else {
+              curb.atomic_add(62 + vy, Yb);
+            }
+          }
+          if (full) {
+            W4<R> s = Xb;
+            w4_warp_sum<12u>(s);
+            if ((lane & 12u) == 0) xbb.atomic_add(32 + vx, s);
+          } else {
+            xbb.atomic_add(32 + vx, Xb);
+          }
+        }
+        {
+          const int vx = vt[800];
+          const W4<R> X = xb[40 + vx];
+          W4<R> Xb = w4_zero<R>();
+          {
+            const int vy = vt[192];
+            W4<R> Y = cur[62 + vy];
+            const cx<R> ab = Jb[3];
+            w4_acc_conj(Xb, Y, ab);
+            const W4<R> Yb = w4_conj_scale(X, ab);
+            if (full) {
+              W4<R> s = Yb;
+              w4_warp_sum<19u>(s);
+              if ((lane & 19u) == 0) curb.atomic_add(62 + vy, s);
+            } else {
+              curb.atomic_add(62 + vy, Yb);
+            }
+          }
+          if (full) {
+            W4<R> s = Xb;
+            w4_warp_sum<12u>(s);
+            if ((lane & 12u) == 0) xbb.atomic_add(40 + vx, s);
+          } else {
+            xbb.atomic_add(40 + vx, Xb);
+          }
+        }
+        {
+          const int vx = vt[832];
+          const W4<R> X = xb[48 + vx];
+          W4<R> Xb = w4_zero<R>();
+          {
+            const int vy = vt[160];
+            W4<R> Y = cur[58 + vy];
+            const cx<R> ab = Jb[0];
+            w4_acc_conj(Xb, Y, ab);
+            const W4<R> Yb = w4_conj_scale(X, ab);
+            if (full) {
+              W4<R> s = Yb;
+              w4_warp_sum<11u>(s);
+              if ((lane & 11u) == 0) curb.atomic_add(58 + vy, s);
+            } else {
+              curb.atomic_add(58 + vy, Yb);
+            }
+          }
+          if (full) {
+            W4<R> s = Xb;
+            w4_warp_sum<20u>(s);
+            if ((lane & 20u) == 0) xbb.atomic_add(48 + vx, s);
+          } else {
+            xbb.atomic_add(48 + vx, Xb);
+          }
+        }
+        {
+          const int vx = vt[832];
+          const W4<R> X = xb[56 + vx];
+          W4<R> Xb = w4_zero<R>();
+          {
+            const int vy = vt[160];
+            W4<R> Y = cur[58 + vy];
+            const cx<R> ab = Jb[1];
+            w4_acc_conj(Xb, Y, ab);
+            const W4<R> Yb = w4_conj_scale(X, ab);
+            if (full) {
+              W4<R> s = Yb;
+              w4_warp_sum<11u>(s);
+              if ((lane & 11u) == 0) curb.atomic_add(58 + vy, s);
+            } else {
+              curb.atomic_add(58 + vy, Yb);
+            }
+          }
+          if (full) {
+            W4<R> s = Xb;
+            w4_warp_sum<20u>(s);
+            if ((lane & 20u) == 0) xbb.atomic_add(56 + vx, s);
+          } else {
+            xbb.atomic_add(56 + vx, Xb);
+          }
+        }
+        {
+          const int vx = vt[832];
+          const W4<R> X = xb[64 + vx];
+          W4<R> Xb = w4_zero<R>();
+          {
+            const int vy = vt[160];
+            W4<R> Y = cur[58 + vy];
+            const cx<R> ab = mul_i(Jb[0]) + mul_mi(Jb[1]);
+            w4_acc_conj(Xb, Y, ab);
+            const W4<R> Yb = w4_conj_scale(X, ab);
+            if (full) {
+              W4<R> s = Yb;
+              w4_warp_sum<11u>(s);
+              if ((lane & 11u) == 0) curb.atomic_add(58 + vy, s);
+            } else {
+              curb.atomic_add(58 + vy, Yb);
+            }
+          }
+          if (full) {
+            W4<R> s = Xb;
+            w4_warp_sum<20u>(s);
+            if ((lane & 20u) == 0) xbb.atomic_add(64 + vx, s);
+          } else {
+            xbb.atomic_add(64 + vx, Xb);
+          }
+        }
+        {
+          const int vx = vt[384];
+          const W4<R> X = xb[72 + vx];
+          W4<R> Xb = w4_zero<R>();
+          {
+            const int vy = vt[608];
+            W4<R> Y = cur[34 + vy];
+            Y = w4_add(Y, cur[78 + vy]);
+            const cx<R> ab = -Jb[0] + Jb[2] + Jb[4] + -Jb[5];
+            w4_acc_conj(Xb, Y, ab);
+            const W4<R> Yb = w4_conj_scale(X, ab);
+            if (full) {
+              W4<R> s = Yb;
+              w4_warp_sum<6u>(s);
+              if ((lane & 6u) == 0) curb.atomic_add(34 + vy, s);
+            } else {
+              curb.atomic_add(34 + vy, Yb);
+            }
+            if (full) {
+              W4<R> s = Yb;
+              w4_warp_sum<6u>(s);
+              if ((lane & 6u) == 0) curb.atomic_add(78 + vy, s);
+            } else {
+              curb.atomic_add(78 + vy, Yb);
+            }
+          }
+          {
+            const int vy = vt[608];
+            W4<R> Y = cur[42 + vy];
+            Y = w4_add(Y, cur[86 + vy]);
+            const cx<R> ab = -Jb[1] + Jb[2] + -Jb[3] + Jb[4];
+            w4_acc_conj(Xb, Y, ab);
+            const W4<R> Yb = w4_conj_scale(X, ab);
+            if (full) {
+              W4<R> s = Yb;
+              w4_warp_sum<6u>(s);
+              if ((lane & 6u) == 0) curb.atomic_add(42 + vy, s);
+            } else {
+              curb.atomic_add(42 + vy, Yb);
+            }
+            if (full) {
+              W4<R> s = Yb;
+              w4_warp_sum<6u>(s);
+              if ((lane & 6u) == 0) curb.atomic_add(86 + vy, s);
+            } else {
+              curb.atomic_add(86 + vy, Yb);
+            }
+          }
+          {
+            const int vy = vt[608];
+            W4<R> Y = cur[50 + vy];
+            Y = w4_sub(Y, cur[70 + vy]);
+            const cx<R> ab = Jb[0] + -Jb[1] + -Jb[3] + Jb[5];
+            w4_acc_conj(Xb, Y, ab);
+            const W4<R> Yb = w4_conj_scale(X, ab);
+            if (full) {
+              W4<R> s = Yb;
+              w4_warp_sum<6u>(s);
+              if ((lane & 6u) == 0) curb.atomic_add(50 + vy, s);
+            } else {
+              curb.atomic_add(50 + vy, Yb);
+            }
+            if (full) {
+              W4<R> s = w4_neg(Yb);
+              w4_warp_sum<6u>(s);
+              if ((lane & 6u) == 0) curb.atomic_add(70 + vy, s);
+            } else {
+              curb.atomic_add(70 + vy, w4_neg(Yb));
+            }
+          }
+          if (full) {
+            W4<R> s = Xb;
+            w4_warp_sum<25u>(s);
+            if ((lane & 25u) == 0) xbb.atomic_add(72 + vx, s);
+          } else {
+            xbb.atomic_add(72 + vx, Xb);
+          }
+        }
+        {
+          const int vx = vt[224];
+          const W4<R> X = xb[76 + vx];
+          W4<R> Xb = w4_zero<R>();
+          {
+            const int vy = vt[768];
+            W4<R> Y = cur[18 + vy];
+            const cx<R> ab = mul_i(Jb[0]) + mul_mi(Jb[2]);
+            w4_acc_conj(Xb, Y, ab);
+            const W4<R> Yb = w4_conj_scale(X, ab);
+            if (full) {
+              W4<R> s = Yb;
+              w4_warp_sum<28u>(s);
+              if ((lane & 28u) == 0) curb.atomic_add(18 + vy, s);
+            } else {
+              curb.atomic_add(18 + vy, Yb);
+            }
+          }
+          if (full) {
+            W4<R> s = Xb;
+            w4_warp_sum<3u>(s);
+            if ((lane & 3u) == 0) xbb.atomic_add(76 + vx, s);
+          } else {
+            xbb.atomic_add(76 + vx, Xb);
+          }
+        }
+        {
+          const int vx = vt[672];
+          const W4<R> X = xb[84 + vx];
+          W4<R> Xb = w4_zero<R>();
+          {
+            const int vy = vt[320];
+            W4<R> Y = cur[14 + vy];
+            const cx<R> ab = mul_i(Jb[1]) + mul_mi(Jb[4]);
+            w4_acc_conj(Xb, Y, ab);
+            const W4<R> Yb = w4_conj_scale(X, ab);
+            if (full) {
+              W4<R> s = Yb;
+              w4_warp_sum<21u>(s);
+              if ((lane & 21u) == 0) curb.atomic_add(14 + vy, s);
+            } else {
+              curb.atomic_add(14 + vy, Yb);
+            }
+          }
+          if (full) {
+            W4<R> s = Xb;
+            w4_warp_sum<10u>(s);
+            if ((lane & 10u) == 0) xbb.atomic_add(84 + vx, s);
+          } else {
+            xbb.atomic_add(84 + vx, Xb);
+          }
+        }
+        {
+          const int vx = vt[704];
+          const W4<R> X = xb[92 + vx];
+          W4<R> Xb = w4_zero<R>();
+          {
+            const int vy = vt[288];
+            W4<R> Y = cur[10 + vy];
+            const cx<R> ab = mul_i(Jb[3]) + mul_mi(Jb[5]);
+            w4_acc_conj(Xb, Y, ab);
+            const W4<R> Yb = w4_conj_scale(X, ab);
+            if (full) {
+              W4<R> s = Yb;
+              w4_warp_sum<13u>(s);
+              if ((lane & 13u) == 0) curb.atomic_add(10 + vy, s);
+            } else {
+              curb.atomic_add(10 + vy, Yb);
+            }
+          }
+          if (full) {
+            W4<R> s = Xb;
+            w4_warp_sum<18u>(s);
+            if ((lane & 18u) == 0) xbb.atomic_add(92 + vx, s);
+          } else {
+            xbb.atomic_add(92 + vx, Xb);
+          }
+        }
+      } break;
+      default: break;
+    }
+  }
   static constexpr int NMOM = 21;
   static constexpr int NPROP = 10;
   static constexpr int NFINAL = 3;

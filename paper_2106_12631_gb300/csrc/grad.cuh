@@ -154,12 +154,4 @@ cudaError_t launch_grad_variant(const GradArgs& a, const Couplings<R>& cp, cudaS
   return cudaGetLastError();
 }
 
-template <class P>
-cudaError_t launch_grad_impl(const GradLaunch& l, int mode, cudaStream_t s) {
-  GradArgs a{l.nevt, l.ecm, l.rnd, l.nrows, l.mask, l.gout, l.grad, l.me, l.pp, l.st};
-  if (mode == 0) return launch_grad_variant<P, double>(a, l.cd, s);
-  if (mode == 1 || mode == 2 || mode == 5) return launch_grad_variant<P, float>(a, l.cf, s);
-  return cudaErrorInvalidValue;
-}
-
 }  // namespace mg

@@ -1,5 +1,5 @@
-// Adjoint gradient d me / d rnd for process 2 (see grad.cuh, gen/proc2.cuh).
-#include "grad.cuh"
+// Adjoint gradient d me / d rnd for process 2 (see grad_hs.cuh, grad.cuh, gen/proc2.cuh).
+#include "grad_hs.cuh"
 #include "launch.h"
 namespace mg {
 cudaError_t launch_grad_p2(const GradLaunch& a, int mode, cudaStream_t s) { return launch_grad_impl<Proc2>(a, mode, s); }

@@ -199,6 +199,202 @@ __device__ __forceinline__ void VVVV4P0_1_adj(const W4<R>& a1, const W4<R>& a2, 
   vvvv_adj(a3, a1, a2, a2, a1, a3, g2, prop, ob, a3b, a1b, a2b, a2b, a1b, a3b, propb);
 }
 
+// slash_col: o0 = vm f2 - xm f3, o1 = vp f3 - xp f2, o2 = vp f0 + xm f1, o3 = xp f0 + vm f1
+template <class R>
+__device__ __forceinline__ void slash_col_adj(const W4<R>& V, const W4<R>& f, const W4<R>& ob, W4<R>& Vb, W4<R>& fb) {
+  const cx<R> vp = V.w[0] + V.w[3], vm = V.w[0] - V.w[3];
+  const cx<R> xp = V.w[1] + mul_i(V.w[2]), xm = V.w[1] - mul_i(V.w[2]);
+  fb.w[2] += conj(vm) * ob.w[0] - conj(xp) * ob.w[1];
+  fb.w[3] += conj(vp) * ob.w[1] - conj(xm) * ob.w[0];
+  fb.w[0] += conj(vp) * ob.w[2] + conj(xp) * ob.w[3];
+  fb.w[1] += conj(xm) * ob.w[2] + conj(vm) * ob.w[3];
+  const cx<R> bp = conj(f.w[3]) * ob.w[1] + conj(f.w[0]) * ob.w[2];
+  const cx<R> bm = conj(f.w[2]) * ob.w[0] + conj(f.w[1]) * ob.w[3];
+  const cx<R> bxp = conj(f.w[0]) * ob.w[3] - conj(f.w[2]) * ob.w[1];
+  const cx<R> bxm = conj(f.w[1]) * ob.w[2] - conj(f.w[3]) * ob.w[0];
+  slash_parts_adj(bp, bm, bxp, bxm, Vb);
+}
+
+// mkslash_m_col: o0 = m f0 - (km f2 - kxm f3), o1 = m f1 - (kp f3 - kxp f2),
+//                o2 = m f2 - (kp f0 + kxm f1), o3 = m f3 - (kxp f0 + km f1)
+template <class R>
+__device__ __forceinline__ void mkslash_m_col_adj(const R* K, R m, const W4<R>& f, const W4<R>& ob, W4<R>& fb, R* Kb) {
+  const R kp = K[0] + K[3], km = K[0] - K[3];
+  const cx<R> kxp(K[1], K[2]), kxm(K[1], -K[2]);
+  fb.w[0] += m * ob.w[0] - kp * ob.w[2] - conj(kxp) * ob.w[3];
+  fb.w[1] += m * ob.w[1] - conj(kxm) * ob.w[2] - km * ob.w[3];
+  fb.w[2] += m * ob.w[2] - km * ob.w[0] + conj(kxp) * ob.w[1];
+  fb.w[3] += m * ob.w[3] + conj(kxm) * ob.w[0] - kp * ob.w[1];
+  const R bkp = -re_dot(f.w[3], ob.w[1]) - re_dot(f.w[0], ob.w[2]);
+  const R bkm = -re_dot(f.w[2], ob.w[0]) - re_dot(f.w[1], ob.w[3]);
+  Kb[0] += bkp + bkm;
+  Kb[3] += bkp - bkm;
+  // d o / d K1: o0 += f3, o1 += f2, o2 -= f1, o3 -= f0; d o / d K2: i times (-f3, f2, f1, -f0)
+  Kb[1] += re_dot(f.w[3], ob.w[0]) + re_dot(f.w[2], ob.w[1]) - re_dot(f.w[1], ob.w[2]) - re_dot(f.w[0], ob.w[3]);
+  Kb[2] += re_dot(mul_mi(f.w[3]), ob.w[0]) + re_dot(mul_i(f.w[2]), ob.w[1]) + re_dot(mul_i(f.w[1]), ob.w[2]) +
+           re_dot(mul_mi(f.w[0]), ob.w[3]);
+}
+
+// FFV1_1 = [mkslash_m_col(K, m, slash_col(v, fi))] (i g prop)
+template <class R>
+__device__ __forceinline__ void FFV1_1_adj(const W4<R>& fi, const W4<R>& v, R g, const R* K, R m, cx<R> prop,
+                                           const W4<R>& ob, W4<R>& fib, W4<R>& vb, R* Kb, cx<R>& propb) {
+  const W4<R> u = slash_col(v, fi);
+  const W4<R> w = mkslash_m_col(K, m, u);
+  const cx<R> s = mul_i(g * prop);
+  W4<R> wb;
+  cx<R> sb(R(0), R(0));
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    wb.w[k] = conj(s) * ob.w[k];
+    sb += conj(w.w[k]) * ob.w[k];
+  }
+  propb += mul_mi(g * sb);
+  W4<R> ub = w4_zero<R>();
+  mkslash_m_col_adj(K, m, u, wb, ub, Kb);
+  slash_col_adj(v, fi, ub, vb, fib);
+}
+
+// bilinear (row f, column g, couplings gl, gr): see helas.cuh
+template <class R>
+__device__ __forceinline__ void bilinear_adj(const W4<R>& f, const W4<R>& g, R gl, R gr, const W4<R>& jb, W4<R>& fb,
+                                             W4<R>& gb) {
+  const cx<R> a02b = gr * (jb.w[0] + jb.w[3]), a13b = gr * (jb.w[0] - jb.w[3]);
+  const cx<R> a03b = gr * (jb.w[1] + mul_i(jb.w[2])), a12b = gr * (jb.w[1] - mul_i(jb.w[2]));
+  const cx<R> b20b = gl * (jb.w[0] - jb.w[3]), b31b = gl * (jb.w[0] + jb.w[3]);
+  const cx<R> b21b = gl * (-jb.w[1] - mul_i(jb.w[2])), b30b = gl * (mul_i(jb.w[2]) - jb.w[1]);
+  fb.w[0] += conj(g.w[2]) * a02b + conj(g.w[3]) * a03b;
+  fb.w[1] += conj(g.w[3]) * a13b + conj(g.w[2]) * a12b;
+  fb.w[2] += conj(g.w[0]) * b20b + conj(g.w[1]) * b21b;
+  fb.w[3] += conj(g.w[1]) * b31b + conj(g.w[0]) * b30b;
+  gb.w[2] += conj(f.w[0]) * a02b + conj(f.w[1]) * a12b;
+  gb.w[3] += conj(f.w[1]) * a13b + conj(f.w[0]) * a03b;
+  gb.w[0] += conj(f.w[2]) * b20b + conj(f.w[3]) * b30b;
+  gb.w[1] += conj(f.w[3]) * b31b + conj(f.w[2]) * b21b;
+}
+
+// FFV1P0_3 = bilinear(fo, fi, 1, 1) (i g prop)
+template <class R>
+__device__ __forceinline__ void FFV1P0_3_adj(const W4<R>& fo, const W4<R>& fi, R g, cx<R> prop, const W4<R>& ob,
+                                             W4<R>& fob, W4<R>& fib, cx<R>& propb) {
+  const W4<R> j = bilinear(fo, fi, R(1), R(1));
+  const cx<R> s = mul_i(g * prop);
+  W4<R> jb;
+  cx<R> sb(R(0), R(0));
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    jb.w[k] = conj(s) * ob.w[k];
+    sb += conj(j.w[k]) * ob.w[k];
+  }
+  propb += mul_mi(g * sb);
+  bilinear_adj(fo, fi, R(1), R(1), jb, fob, fib);
+}
+
+// ---- amputated currents (helas.cuh): same maps without the propagator,
+// vector outputs with a lower index (o_mu = eta_mu t_mu)
+template <class R>
+__device__ __forceinline__ W4<R> lower_adj(const W4<R>& ob) {  // adjoint seen by the upper-index vector
+  W4<R> t;
+  t.w[0] = ob.w[0];
+#pragma unroll
+  for (int k = 1; k < 4; ++k) t.w[k] = -ob.w[k];
+  return t;
+}
+// FFV1_2A = i g row_slash(fo, v)
+template <class R>
+__device__ __forceinline__ void FFV1_2A_adj(const W4<R>& fo, const W4<R>& v, R g, const W4<R>& ob, W4<R>& fob,
+                                            W4<R>& vb) {
+  W4<R> ub;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) ub.w[k] = mul_mi(g * ob.w[k]);
+  row_slash_adj(fo, v, ub, fob, vb);
+}
+// FFV1_1A = i g slash_col(v, fi)
+template <class R>
+__device__ __forceinline__ void FFV1_1A_adj(const W4<R>& fi, const W4<R>& v, R g, const W4<R>& ob, W4<R>& fib,
+                                            W4<R>& vb) {
+  W4<R> ub;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) ub.w[k] = mul_mi(g * ob.w[k]);
+  slash_col_adj(v, fi, ub, vb, fib);
+}
+// FFV1P0_3A = lower(i g bilinear(fo, fi, 1, 1))
+template <class R>
+__device__ __forceinline__ void FFV1P0_3A_adj(const W4<R>& fo, const W4<R>& fi, R g, const W4<R>& ob, W4<R>& fob,
+                                              W4<R>& fib) {
+  const W4<R> t = lower_adj(ob);
+  W4<R> jb;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) jb.w[k] = mul_mi(g * t.w[k]);
+  bilinear_adj(fo, fi, R(1), R(1), jb, fob, fib);
+}
+// VVV1P0_1A = lower(g n): VVV1P0_1 with a unit propagator
+template <class R>
+__device__ __forceinline__ void VVV1P0_1A_adj(const W4<R>& a1, const W4<R>& a2, const R* K1, const R* K2, R g,
+                                              const W4<R>& ob, W4<R>& a1b, W4<R>& a2b, R* K1b, R* K2b) {
+  cx<R> unused(R(0), R(0));
+  VVV1P0_1_adj(a1, a2, K1, K2, g, cx<R>(R(1), R(0)), lower_adj(ob), a1b, a2b, K1b, K2b, unused);
+}
+// vvvv_comb_a = lower(-i g2 ((A.B) X - (C.D) Y)): vvvv_adj with a unit propagator
+template <class R>
+__device__ __forceinline__ void vvvv_comb_a_adj(const W4<R>& X, const W4<R>& A, const W4<R>& B, const W4<R>& Y,
+                                                const W4<R>& C, const W4<R>& D, R g2, const W4<R>& ob, W4<R>& Xb,
+                                                W4<R>& Ab, W4<R>& Bb, W4<R>& Yb, W4<R>& Cb, W4<R>& Db) {
+  cx<R> unused(R(0), R(0));
+  vvvv_adj(X, A, B, Y, C, D, g2, cx<R>(R(1), R(0)), lower_adj(ob), Xb, Ab, Bb, Yb, Cb, Db, unused);
+}
+
+// contraction A = sum_i X_i Y_i: Xb_i += conj(Y_i) Ab (and symmetrically)
+template <class R>
+__device__ __forceinline__ void w4_acc_conj(W4<R>& acc, const W4<R>& y, cx<R> ab) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) acc.w[k] += conj(y.w[k]) * ab;
+}
+template <class R>
+__device__ __forceinline__ W4<R> w4_conj_scale(const W4<R>& x, cx<R> ab) {
+  W4<R> o;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) o.w[k] = conj(x.w[k]) * ab;
+  return o;
+}
+// sum of v over the lanes that differ only in the lane bits of MASK (butterfly);
+// every lane of the warp must take part
+template <unsigned MASK, class R>
+__device__ __forceinline__ void w4_warp_sum(W4<R>& v) {
+#pragma unroll
+  for (int b = 0; b < 5; ++b) {
+    if (!(MASK >> b & 1u)) continue;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      v.w[k].re += __shfl_xor_sync(0xffffffffu, v.w[k].re, 1 << b);
+      v.w[k].im += __shfl_xor_sync(0xffffffffu, v.w[k].im, 1 << b);
+    }
+  }
+}
+
+// y times i, -1, -i
+template <class R>
+__device__ __forceinline__ W4<R> w4_mul_i(const W4<R>& y) {
+  W4<R> o;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) o.w[k] = mul_i(y.w[k]);
+  return o;
+}
+template <class R>
+__device__ __forceinline__ W4<R> w4_neg(const W4<R>& y) {
+  W4<R> o;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) o.w[k] = -y.w[k];
+  return o;
+}
+template <class R>
+__device__ __forceinline__ W4<R> w4_mul_mi(const W4<R>& y) {
+  W4<R> o;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) o.w[k] = mul_mi(y.w[k]);
+  return o;
+}
+
 // Propagator factor prop = c / (K^2 - M^2 + i M W), c = i (fermion) or -i (vector):
 // d prop / d K_mu = kappa 2 eta_mu K_mu with kappa = i prop^2 (fermion), -i prop^2 (vector)
 template <class R>

@@ -24,6 +24,12 @@ struct SigLaunch {
 // rnd == nullptr: uniforms drawn on the device from (seed, first_event + i, row)
 cudaError_t launch_rambo(int nfinal, int64_t nevt, double ecm, const double* rnd, double* mom, double* wgt,
                          const RamboSetup& st, cudaStream_t s, uint64_t seed = 0, int64_t first_event = 0);
+// gradient passes: final momenta out[4 f + mu][nevt]; adjoint from grad rows
+// 0 .. 4 nfinal - 1 (dL/dk) to dL/d rnd in place
+cudaError_t launch_rambo_final(int nfinal, int64_t nevt, double ecm, const double* rnd, double* out,
+                               const RamboSetup& st, cudaStream_t s);
+cudaError_t launch_rambo_adjoint(int nfinal, int64_t nevt, double ecm, const double* rnd, int nrows, double* grad,
+                                 const RamboSetup& st, cudaStream_t s);
 int64_t unweight_blocks(int64_t n);
 cudaError_t launch_unweight(int64_t n, const double* me, const double* w, uint64_t seed, int64_t first_event,
                             int64_t* idx, int64_t* count, double* scratch, cudaStream_t s);

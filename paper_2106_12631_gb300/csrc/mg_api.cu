@@ -261,7 +261,7 @@ int mg_sigmakin_grad(int proc, int64_t nevt, double ecm, const double* rnd, int 
   if (!valid_proc(proc)) return MG_ERR_PROC;
   if (proc != 2 && proc != 3) return MG_ERR_PROC;
   const ProcDesc& d = kProcs[proc];
-  if (nevt < 0 || mode < 0 || (mode > 2 && mode != 5) || !(ecm > 0) || !std::isfinite(ecm) || nrows < 4 * (d.npar - 2))
+  if (nevt < 0 || mode < 0 || mode > 5 || !(ecm > 0) || !std::isfinite(ecm) || nrows < 4 * (d.npar - 2))
     return MG_ERR_ARG;
   mg::RamboSetup st;
   if (int r = rambo_setup(proc, ecm, st)) return r;

@@ -57,6 +57,18 @@ struct Slots {
 #pragma unroll
     for (int k = 0; k < NPL; ++k) p[i + k * N] = s[k];
   }
+  // slot i += w, component by component with shared-memory atomics (adjoint
+  // accumulation from many threads)
+  __device__ __forceinline__ void atomic_add(int i, const W4<R>& w) const {
+    constexpr int PER = (int)(16 / sizeof(R));  // values per 16-byte plane word
+    const R* s = reinterpret_cast<const R*>(&w);
+#pragma unroll
+    for (int k = 0; k < NPL; ++k) {
+      R* d = reinterpret_cast<R*>(p + i + k * N);
+#pragma unroll
+      for (int q = 0; q < PER; ++q) atomicAdd(d + q, s[k * PER + q]);
+    }
+  }
 };
 
 // Couplings and masses in the working precision.

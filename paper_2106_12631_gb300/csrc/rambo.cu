@@ -48,6 +48,70 @@ __global__ void __launch_bounds__(128) rambo_kernel(int64_t nevt, double ecm, co
   wgt[i] = z.w;
 }
 
+// Final-state momenta only, out[4 f + mu][nevt] (the gradient's first pass;
+// the beams are fixed), from rnd[k][nevt].
+template <int NF>
+__global__ void __launch_bounds__(128) rambo_final_kernel(int64_t nevt, double ecm, const double* __restrict__ rnd,
+                                                          double* __restrict__ out, RamboSetup st) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nevt) return;
+  double r[4 * NF];
+#pragma unroll
+  for (int k = 0; k < 4 * NF; ++k) r[k] = rnd[(int64_t)k * nevt + i];
+  RamboState<NF> z;
+  rambo_forward<NF>(r, ecm, st, z);
+#pragma unroll
+  for (int f = 0; f < NF; ++f)
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) out[(int64_t)(4 * f + mu) * nevt + i] = z.k[f][mu];
+}
+
+// RAMBO adjoint: grad[4 f + mu][i] holds dL/dk_f^mu of the final momenta on
+// entry; on exit grad[k][i] = dL/d rnd[k][i] (0 for rows RAMBO does not use).
+template <int NF>
+__global__ void __launch_bounds__(128) rambo_adjoint_kernel(int64_t nevt, double ecm, const double* __restrict__ rnd,
+                                                            int nrows, double* __restrict__ grad, RamboSetup st) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nevt) return;
+  double r[4 * NF], kb[NF][4], rb[4 * NF];
+#pragma unroll
+  for (int k = 0; k < 4 * NF; ++k) r[k] = rnd[(int64_t)k * nevt + i];
+#pragma unroll
+  for (int f = 0; f < NF; ++f)
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) kb[f][mu] = grad[(int64_t)(4 * f + mu) * nevt + i];
+  RamboState<NF> z;
+  rambo_forward<NF>(r, ecm, st, z);
+  rambo_adjoint<NF>(r, ecm, st, z, kb, rb);
+  for (int k = 0; k < nrows; ++k) grad[(int64_t)k * nevt + i] = k < 4 * NF ? rb[k] : 0.0;
+}
+
+cudaError_t launch_rambo_final(int nfinal, int64_t nevt, double ecm, const double* rnd, double* out,
+                               const RamboSetup& st, cudaStream_t s) {
+  const int nt = 128;
+  const int64_t grid = (nevt + nt - 1) / nt;
+  switch (nfinal) {
+    case 2: rambo_final_kernel<2><<<(unsigned)grid, nt, 0, s>>>(nevt, ecm, rnd, out, st); break;
+    case 3: rambo_final_kernel<3><<<(unsigned)grid, nt, 0, s>>>(nevt, ecm, rnd, out, st); break;
+    case 4: rambo_final_kernel<4><<<(unsigned)grid, nt, 0, s>>>(nevt, ecm, rnd, out, st); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rambo_adjoint(int nfinal, int64_t nevt, double ecm, const double* rnd, int nrows, double* grad,
+                                 const RamboSetup& st, cudaStream_t s) {
+  const int nt = 128;
+  const int64_t grid = (nevt + nt - 1) / nt;
+  switch (nfinal) {
+    case 2: rambo_adjoint_kernel<2><<<(unsigned)grid, nt, 0, s>>>(nevt, ecm, rnd, nrows, grad, st); break;
+    case 3: rambo_adjoint_kernel<3><<<(unsigned)grid, nt, 0, s>>>(nevt, ecm, rnd, nrows, grad, st); break;
+    case 4: rambo_adjoint_kernel<4><<<(unsigned)grid, nt, 0, s>>>(nevt, ecm, rnd, nrows, grad, st); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_rambo(int nfinal, int64_t nevt, double ecm, const double* rnd, double* mom, double* wgt,
                          const RamboSetup& st, cudaStream_t s, uint64_t seed, int64_t first_event) {
   const int nt = 128;

@@ -287,8 +287,25 @@ __device__ __forceinline__ cx<float> propagator_dfl(const float2* k, int kind, d
 // straight from the momenta; then the propagator of every line (one thread
 // per (event, propagator)).
 template <class P, class R, class L>
+__device__ __forceinline__ void hs_build_tables(unsigned char* smem, const PhysParams& pp, int nev, uint4* curs,
+                                                const Couplings<R>& cp);
+
+template <class P, class R, class L>
 __device__ __forceinline__ void hs_event_tables(unsigned char* smem, const SigArgs& a, int64_t e0, int nev,
                                                 uint4* curs, const Couplings<R>& cp) {
+  auto p = reinterpret_cast<double(*)[P::NPAR][4]>(smem + L::o_p);
+  for (int t = threadIdx.x; t < nev * P::NPAR * 4; t += L::NT) {
+    const int e = t % nev, c = t / nev;
+    p[e][c >> 2][c & 3] = a.mom[(int64_t)c * a.nevt + e0 + e];
+  }
+  __syncthreads();
+  hs_build_tables<P, R, L>(smem, a.pp, nev, curs, cp);
+}
+
+// the tables from the momenta already in shared memory
+template <class P, class R, class L>
+__device__ __forceinline__ void hs_build_tables(unsigned char* smem, const PhysParams& pp, int nev, uint4* curs,
+                                                const Couplings<R>& cp) {
   constexpr int NT = L::NT;
   constexpr int NEXT = P::hs_level(1);  // external variants
   constexpr int CUR_EV = P::HS_NSLOT * Slots<R, 1>::NPL;
@@ -300,11 +317,6 @@ __device__ __forceinline__ void hs_event_tables(unsigned char* smem, const SigAr
   auto Kf = reinterpret_cast<float2(*)[P::NMOM][4]>(smem + L::o_Kd);
   auto pr = reinterpret_cast<cx<R>(*)[P::NPROP]>(smem + L::o_pr);
   const int2* prop_tab = reinterpret_cast<const int2*>(smem + L::o_proptab);
-  for (int t = tid; t < nev * P::NPAR * 4; t += NT) {
-    const int e = t % nev, c = t / nev;
-    p[e][c >> 2][c & 3] = a.mom[(int64_t)c * a.nevt + e0 + e];
-  }
-  __syncthreads();
   for (int t = tid; t < nev * (4 + NEXT); t += NT) {
     if (t < nev * 4) {
       const int e = t >> 2, mu = t & 3;
@@ -377,7 +389,7 @@ __device__ __forceinline__ void hs_event_tables(unsigned char* smem, const SigAr
     for (int t = tid; t < nev * P::NPROP; t += NT) {
       const int e = t / P::NPROP, j = t - e * P::NPROP;
       const int2 m = prop_tab[j];  // momentum entry, line kind
-      pr[e][j] = propagator_hs<R>(Kd[e][m.x], m.y, a.pp);
+      pr[e][j] = propagator_hs<R>(Kd[e][m.x], m.y, pp);
     }
   }
   __syncthreads();

@@ -1329,7 +1329,7 @@ class SharedProgram:
             "  static __device__ __forceinline__ int hs_xitem(int c) { return kHsXItem%d[c]; }" % pid,
             "  static __device__ __forceinline__ const uint8_t* hs_variants() { return kHsVar%d; }" % pid,
             "  static __device__ __forceinline__ const HsItem* hs_items() { return kHsItems%d; }" % pid,
-        ] + self._contract_code()
+        ] + self._contract_code() + self._contract_adj_code()
 
     @staticmethod
     def _rotate(flows, r):
@@ -1362,6 +1362,81 @@ class SharedProgram:
             else:
                 groups[base[0]]["ys"].append((yo, base[1]))
         return groups
+
+    def _contract_adj_code(self) -> list:
+        """Adjoint of hs_contract for one (event, helicity): from Jb_s = dL/dJ_s
+        (Wirtinger: dL/dRe + i dL/dIm) each group's Ab = sum_s conj(c_s) Jb_s;
+        Xb += conj(Y) Ab (registers, one atomic add per amputated current) and
+        Yb_k = conj(phase_k) conj(X) Ab added atomically into the operands' slots."""
+        nh = 1 << self.n
+        ALL = (1 << self.n) - 1
+        cj = {0: "Jb[%d]", 1: "-Jb[%d]", 2: "mul_mi(Jb[%d])", 3: "mul_i(Jb[%d])"}  # conj(c) Jb
+        ph = {0: "Yb", 1: "w4_mul_mi(Yb)", 2: "w4_neg(Yb)", 3: "w4_mul_i(Yb)"}      # conj(i^r) Yb
+        def lane_mask(legs):
+            """lane bits of a warp whose helicity bits are those of `legs` (lane
+            bit b = helicity bit b = leg n-1-b; a warp spans helicity bits 0..4)"""
+            m = 0
+            for b in range(min(5, self.n)):
+                if (self.n - 1 - b) in legs:
+                    m |= 1 << b
+            return m
+
+        def add(target, slot, value, mask):
+            # full: lanes = consecutive helicities of one event, all good: sum the
+            # lanes sharing the slot first, one atomic add per slot and warp
+            return ["          if (full) {",
+                    "            W4<R> s = %s;" % value,
+                    "            w4_warp_sum<%du>(s);" % mask,
+                    "            if ((lane & %du) == 0) %s.atomic_add(%s, s);" % (mask, target, slot),
+                    "          } else {",
+                    "            %s.atomic_add(%s, %s);" % (target, slot, value),
+                    "          }"]
+
+        lines = ["  // adjoint of hs_contract: Jb -> atomic adds into curb (operands) and xbb (amputated);",
+                 "  // full = the warp's lanes are consecutive helicities of its event(s), all good",
+                 "  template <class R, class CUR, class XB>",
+                 "  static __device__ __forceinline__ void hs_contract_adj(int c, const CUR& cur, const XB& xb,"
+                 " const uint8_t* __restrict__ vt, const cx<R>* Jb, const CUR& curb, const XB& xbb, bool full,"
+                 " int lane) {",
+                 "    switch (c) {"]
+        for c in range(len(self.chunks)):
+            lines.append("      case %d: {" % c)
+            last_x = None
+            last_mask = 0
+            for g in self.groups:
+                if g["ch"] != c:
+                    continue
+                xlegs = set(l for l in range(self.n) if g["xset"] >> l & 1)
+                if g["xo"] != last_x:
+                    if last_x is not None:
+                        lines += add("xbb", "%d + vx" % last_x, "Xb", last_mask)
+                        lines.append("        }")
+                    lines.append("        {")
+                    lines.append("          const int vx = vt[%d];" % (g["xset"] * nh))
+                    lines.append("          const W4<R> X = xb[%d + vx];" % g["xo"])
+                    lines.append("          W4<R> Xb = w4_zero<R>();")
+                    last_x = g["xo"]
+                    last_mask = lane_mask(set(range(self.n)) - xlegs)
+                yv = (ALL ^ g["xset"]) * nh
+                ab = " + ".join(cj[f >> 6] % (f & 63) for f in g["flows"])
+                lines.append("          {")
+                lines.append("            const int vy = vt[%d];" % yv)
+                lines.append("            W4<R> Y = cur[%d + vy];" % g["ys"][0][0])
+                acc = {0: "w4_add", 1: "w4_addi", 2: "w4_sub", 3: "w4_subi"}
+                for (yo, r) in g["ys"][1:]:
+                    lines.append("            Y = %s(Y, cur[%d + vy]);" % (acc[r], yo))
+                lines.append("            const cx<R> ab = %s;" % ab)
+                lines.append("            w4_acc_conj(Xb, Y, ab);")
+                lines.append("            const W4<R> Yb = w4_conj_scale(X, ab);")
+                for (yo, r) in g["ys"]:
+                    lines += ["  " + ln for ln in add("curb", "%d + vy" % yo, ph[r], lane_mask(xlegs))]
+                lines.append("          }")
+            if last_x is not None:
+                lines += add("xbb", "%d + vx" % last_x, "Xb", last_mask)
+                lines.append("        }")
+            lines.append("      } break;")
+        lines += ["      default: break;", "    }", "  }"]
+        return lines
 
     def _contract_code(self) -> list:
         """Contractions of one chunk for one (event, helicity), straight-line: every

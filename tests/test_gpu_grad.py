@@ -1,6 +1,7 @@
 """Adjoint gradient d me / d rnd (gg -> t t~ and gg -> t t~ g) against the oracle.
 
-Bars (per event, normwise over the random rows k):
+The default modes run the helicity-shared adjoint, modes *_unrolled the
+per-helicity one.  Bars (per event, normwise over the random rows k):
   |g - g_ref|_inf / |g_ref|_inf <= 1e-4 for the FP32 forward + adjoint
   (tested against the oracle's forward-mode dual-number gradient and against
   central finite differences h = 1e-6 of the FP64 oracle), <= 1e-9 for the
@@ -41,7 +42,8 @@ def normwise(g, ref):
 
 
 @pytest.mark.parametrize("proc,nevt", [(2, 33), (3, 37)])
-@pytest.mark.parametrize("mode,bar", [("fp64", 1e-9), ("mixed", 1e-4)])
+@pytest.mark.parametrize("mode,bar", [("fp64", 1e-9), ("mixed", 1e-4), ("fp64_unrolled", 1e-9),
+                                      ("mixed_unrolled", 1e-4)])
 def test_adjoint_vs_dual(mg, orc, proc, nevt, mode, bar):
     nrows = 16
     rnd = I.uniforms(I.seed_of("gg_ttg_grad") + proc, nrows, nevt)
@@ -55,7 +57,7 @@ def test_adjoint_vs_dual(mg, orc, proc, nevt, mode, bar):
     err = normwise(g[:used], g_o[:used])
     print("proc %d %s: max normwise err %.3g median %.3g" % (proc, mode, err.max(), np.median(err)))
     assert np.all(err <= bar), (err.max(), int(err.argmax()))
-    np.testing.assert_allclose(me, me_o, rtol=1e-9 if mode == "fp64" else 1e-4)
+    np.testing.assert_allclose(me, me_o, rtol=1e-9 if mode.startswith("fp64") else 1e-4)
 
 
 def test_adjoint_vs_finite_differences(mg, orc):
@@ -90,9 +92,10 @@ def test_me_matches_sigmakin_and_gout_scaling(mg):
     torch.cuda.synchronize()
     np.testing.assert_allclose(me1.cpu().numpy(), me_s.cpu().numpy(), rtol=1e-13)
     # gout is applied before the (linear) RAMBO adjoint: equal up to rounding,
-    # normwise per event (the adjoint sums terms that cancel)
+    # normwise per event (the adjoint sums terms that cancel, and its shared
+    # atomics may add in a different order in the two calls)
     a, b = g2.cpu().numpy(), (g1 * gout).cpu().numpy()
-    assert np.all(np.max(np.abs(a - b), axis=0) <= 1e-12 * np.max(np.abs(b), axis=0))
+    assert np.all(np.max(np.abs(a - b), axis=0) <= 1e-9 * np.max(np.abs(b), axis=0))
 
 
 def test_autograd_function(mg):
@@ -104,7 +107,10 @@ def test_autograd_function(mg):
     (me * w).sum().backward()
     g_ref, _ = mg.sigmakin_grad(proc, rnd.detach(), 1500.0, mask, mode="mixed", gout=w)
     torch.cuda.synchronize()
-    np.testing.assert_allclose(rnd.grad.cpu().numpy(), g_ref.cpu().numpy(), rtol=0, atol=0)
+    # the adjoint accumulates shared variants with atomics: two calls agree to
+    # FP32 rounding (normwise per event), not bit for bit
+    a, b = rnd.grad.cpu().numpy(), g_ref.cpu().numpy()
+    assert np.all(np.max(np.abs(a - b), axis=0) <= 1e-5 * np.max(np.abs(b), axis=0))
 
 
 def test_grad_unsupported_process(mg):
