@@ -24,9 +24,20 @@
 
 namespace mg {
 
+// events per CTA: small FP32 CTAs, several per SM, overlap each other's
+// latency-bound phases; the FP64 kernel prefers larger ones (measured)
+#ifndef MG_HSG_EV
+#define MG_HSG_EV 2
+#endif
+#ifndef MG_HSG_EV64
+#define MG_HSG_EV64 8
+#endif
+
 template <class P, class R>
 struct HsGradCfg {
-  static constexpr int NT = (sizeof(R) == 4 ? 8 : 4) * P::NHEL;  // 8 (FP32) or 4 (FP64) events x all helicities
+  static constexpr int EVW = sizeof(R) == 4 ? MG_HSG_EV : MG_HSG_EV64;
+  // at least one whole warp (the adjoint's warp sums shuffle across all 32 lanes)
+  static constexpr int NT = EVW * P::NHEL >= 32 ? EVW * P::NHEL : 32;
   static constexpr int EVMIN = NT / P::NHEL;
   static constexpr int EVCAP = EVMIN;
   static_assert(P::HS_NXCHUNK == 1, "the adjoint keeps every amputated current: one chunk");
@@ -146,7 +157,7 @@ __device__ __forceinline__ void hs_xitem_adj(const HsItem& it, const Slots<R, P:
 }
 
 template <class P, class R>
-__global__ void __launch_bounds__(HsGradCfg<P, R>::NT, 1) sigmakin_hs_grad_kernel(GradArgs a, Couplings<R> cp) {
+__global__ void __launch_bounds__(HsGradCfg<P, R>::NT) sigmakin_hs_grad_kernel(GradArgs a, Couplings<R> cp) {
   using L = HsGradLayout<P, R>;
   constexpr int NT = L::NT, NC = P::NCOLOR, NF = P::NFINAL;
   constexpr int CUR_EV = P::HS_NSLOT * Slots<R, 1>::NPL, X_EV = P::HS_XCAP * Slots<R, 1>::NPL;
