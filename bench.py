@@ -330,16 +330,16 @@ def main():
     stream = torch.cuda.current_stream()
     kernel_launches_per_step = 6  # rambo(filter), filter, rambo, sigmakin, event_sum x2
 
-    side = torch.cuda.Stream()
+    # the helicity filter runs on a high-priority stream next to the batch's
+    # RAMBO: its few long CTAs take SMs as RAMBO's short CTAs retire
+    filt = torch.cuda.Stream(priority=-1)
 
     def step(mode, ev=None):
-        # the batch's RAMBO (side stream) overlaps the helicity filter (main stream);
-        # it may overwrite mom only after the previous step's SIGMAKIN
-        side.wait_stream(stream)
-        mg.rambo(proc, frnd, ecm, mom=fmom, wgt=fwgt, stream=stream)
-        mg.filter_helicities(proc, fmom, mask=mask, stream=stream)
-        mg.rambo(proc, rnd, ecm, mom=mom, wgt=wgt, stream=side)
-        stream.wait_stream(side)
+        filt.wait_stream(stream)  # the previous step's SIGMAKIN has read mask
+        mg.rambo(proc, frnd, ecm, mom=fmom, wgt=fwgt, stream=filt)
+        mg.filter_helicities(proc, fmom, mask=mask, stream=filt)
+        mg.rambo(proc, rnd, ecm, mom=mom, wgt=wgt, stream=stream)
+        stream.wait_stream(filt)
         if ev is not None:
             ev[0].record(stream)
         mg.sigmakin(proc, mom, mask, mode=mode, me=me, stream=stream)

@@ -76,7 +76,24 @@ __device__ __forceinline__ void rambo_forward(const double* r, double ecm, const
       for (int mu = 0; mu < 4; ++mu) z.k[f][mu] = z.p[f][mu];
     return;
   }
-  double xi = st.xi0;
+  // Newton for sum_f sqrt(m_f^2 + xi^2 E_f^2) = ecm: first in FP32 to ~1e-6
+  // (cheap; GB300 runs FP64 at 1/64 of the FP32 rate), then FP64 steps until
+  // the residual is below 1e-15 ecm, plus one (quadratic convergence: the
+  // same root as iterating in FP64 from the start)
+  float xf = (float)st.xi0;
+  for (int it = 0; it < 12; ++it) {
+    float fv = -(float)ecm, df = 0.0f;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      const float e0 = (float)z.p[f][0];
+      const float en = sqrtf((float)st.m2[f] + xf * xf * e0 * e0);
+      fv += en;
+      df += xf * e0 * e0 / en;
+    }
+    xf -= fv / df;
+    if (fabsf(fv) <= 1e-6f * (float)ecm) break;
+  }
+  double xi = (isfinite(xf) && xf > 0.0f && xf <= 1.0f) ? (double)xf : st.xi0;  // else from the start
   int extra = 0;
   for (int it = 0; it < 50; ++it) {
     double fv = -ecm, df = 0.0;
@@ -87,7 +104,7 @@ __device__ __forceinline__ void rambo_forward(const double* r, double ecm, const
       df += xi * z.p[f][0] * z.p[f][0] / en;
     }
     xi -= fv / df;
-    if (fabs(fv) <= 1e-15 * ecm && ++extra >= 2) break;
+    if (fabs(fv) <= 1e-15 * ecm && ++extra >= 1) break;
   }
   z.xi = xi;
   double w2 = 1.0, w3 = 0.0;
