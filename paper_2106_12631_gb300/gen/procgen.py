@@ -1012,10 +1012,28 @@ class SharedProgram:
 
     def _choose(self):
         """Greedy choice of (vertex, left-out operand) per amplitude minimising the
-        per-event cost of the shared currents and amputated currents (the per-helicity
-        contraction costs the same for every choice), with current slots capped."""
-        refc, xref = {}, {}
+        per-event cost: the shared currents and amputated currents once per event,
+        plus, per event helicity, the contractions — an amplitude whose amputated
+        current and colour flows (up to a phase) match another's joins its
+        contraction (8 flops instead of 30 + 2 per flow) — with current slots capped."""
+        refc, xref, kref = {}, {}, {}
         state = {"cost": 0, "slots": 0}
+        nhel = 1 << self.n
+        pats, nflows = [], []
+        for di in range(len(self.cands)):
+            flows = []
+            for s_ in np.nonzero(self.em.coef[di])[0]:
+                z = complex(self.em.coef[di, s_])
+                flows.append(int(s_) | ({1: 0, -1: 1, 1j: 2, -1j: 3}[z] << 6))
+            pats.append(min(self._rotate(flows, r) for r in range(4)))
+            nflows.append(len(flows))
+        di_of = {}
+        for di, opts in enumerate(self.cands):
+            for o in opts:
+                di_of[id(o)] = di
+
+        def hel_cost(di, first):
+            return FLOPS["W4ADD"] + (FLOPS["DOT4"] - FLOPS["W4ADD"] + FLOPS["jamp"] * nflows[di] if first else 0)
 
         def cost_cur(d):
             return SHARED_COST[self.kind(d)] * self.nvar(d)
@@ -1032,6 +1050,11 @@ class SharedProgram:
             if (r == 0 and s > 0) or (r == 1 and s < 0):
                 state["cost"] += s * SHARED_COST[X[1]] * self.nvar(X)
             xref[X] = r + s
+            di = di_of[id(opt)]
+            key = (X, pats[di])
+            r = kref.get(key, 0)
+            state["cost"] += s * nhel * hel_cost(di, (r == 0 and s > 0) or (r == 1 and s < 0))
+            kref[key] = r + s
 
         def added(opt):
             _, _, _, X, cl = opt
@@ -1042,26 +1065,43 @@ class SharedProgram:
                     sl += self.nvar(d)
             if xref.get(X, 0) == 0:
                 c += SHARED_COST[X[1]] * self.nvar(X)
+            di = di_of[id(opt)]
+            c += nhel * hel_cost(di, kref.get((X, pats[di]), 0) == 0)
             over = max(0, state["slots"] + sl - self.CUR_CAP)
             return c + over * 10 ** 7
 
-        choice = []
-        for opts in self.cands:  # start: root form, the largest operand left out
-            best = max(range(len(opts)), key=lambda i: (opts[i][0] == opts[0][0] and opts[i][1] == opts[0][1],
-                                                       len(self.legs(opts[i][1][opts[i][2]]))))
-            choice.append(best)
-            apply(opts[best], +1)
-        for _ in range(8):
-            changed = False
+        def run(start):
+            for k in list(refc):
+                refc[k] = 0
+            for k in list(xref):
+                xref[k] = 0
+            for k in list(kref):
+                kref[k] = 0
+            state["cost"] = state["slots"] = 0
+            choice = list(start)
             for di, opts in enumerate(self.cands):
-                apply(opts[choice[di]], -1)
-                best = min(range(len(opts)), key=lambda i: (added(opts[i]), i))
-                if best != choice[di]:
-                    changed = True
-                choice[di] = best
-                apply(opts[best], +1)
-            if not changed:
-                break
+                apply(opts[choice[di]], +1)
+            for _ in range(8):
+                changed = False
+                for di, opts in enumerate(self.cands):
+                    apply(opts[choice[di]], -1)
+                    best = min(range(len(opts)), key=lambda i: (added(opts[i]), i))
+                    if best != choice[di]:
+                        changed = True
+                    choice[di] = best
+                    apply(opts[best], +1)
+                if not changed:
+                    break
+            return state["cost"], choice
+
+        # start: root form, the largest operand left out (a start from a greedy
+        # cover of the amplitudes by (amputated current, flow pattern) keys, i.e.
+        # the most merged contractions, converges to the same choice)
+        start = []
+        for opts in self.cands:
+            start.append(max(range(len(opts)), key=lambda i: (opts[i][0] == opts[0][0] and opts[i][1] == opts[0][1],
+                                                             len(self.legs(opts[i][1][opts[i][2]])))))
+        choice = run(start)[1]
         self.choice = choice
         self.flops_event = state["cost"]
 
