@@ -41,7 +41,7 @@ SM_MAX_MHZ = 2070.0
 # (dram__bytes_read.sum + dram__bytes_write.sum of one launch over 2^18 events,
 # scaled by events; it reads the momenta once and writes |M|^2), valid only
 # while the kernel sources are the ones captured.
-SIGMAKIN_TRAFFIC = {"bytes_per_event": 193.13, "sources_sha1": "9dbfde6eba6b4894b8abb0651414f31a0b2a2d7b"}
+SIGMAKIN_TRAFFIC = {"bytes_per_event": 192.79, "sources_sha1": "77fd800010d4d1818d0549fb2234ce20547cff64"}
 SIGMAKIN_SOURCES = ["paper_2106_12631_gb300/csrc/" + f for f in
                     ("sigmakin_hs.cuh", "sigmakin.cuh", "helas.cuh", "colour_tc.cuh", "mg_types.cuh",
                      "process.cuh", "gen/proc4.cuh")]
@@ -416,22 +416,29 @@ def main():
     # the other workloads (SIGMAKIN or the adjoint alone, inputs resident, CUDA events)
     others = {} if args.no_others else measure_other_workloads(mg, I, dev, stream)
 
-    # end to end through the C ABI with host buffers: every step copies the
+    # end to end through the public API with host buffers: every step copies the
     # filter events' and the batch's random numbers from pinned host memory,
-    # filters the helicities, runs RAMBO + SIGMAKIN + the event sum, and reads
-    # me and the event sum back
+    # filters the helicities (high-priority stream, beside the copy and RAMBO),
+    # runs RAMBO + SIGMAKIN + the event sum, and reads me and the event sum back
     rnd_h = torch.from_numpy(I.uniforms(seed, 16, nevt, first_event=shard_first_event(rank, nevt))).pin_memory()
     frnd_h = torch.from_numpy(I.uniforms(I.filter_seed_of(WORKLOAD), 16, 16)).pin_memory()
     me_h = torch.empty(nevt, dtype=torch.float64).pin_memory()
     sums_h = torch.empty(3, dtype=torch.float64).pin_memory()
-    ws = torch.empty(mg.pipeline_workspace_bytes(proc, nevt, 16) // 8 + 1, dtype=torch.float64, device=dev)
+    rnd_d = torch.empty_like(rnd)
 
     def step_e2e():
-        frnd.copy_(frnd_h, non_blocking=True)
-        mg.rambo(proc, frnd, ecm, mom=fmom, wgt=fwgt, stream=stream)
-        mg.filter_helicities(proc, fmom, mask=mask, stream=stream)
-        mg.pipeline_host(proc, rnd_h, ecm, mask, mode=args.mode, me_host=me_h, sums_host=sums_h, workspace=ws,
-                         stream=stream)
+        filt.wait_stream(stream)
+        with torch.cuda.stream(filt):
+            frnd.copy_(frnd_h, non_blocking=True)
+        mg.rambo(proc, frnd, ecm, mom=fmom, wgt=fwgt, stream=filt)
+        mg.filter_helicities(proc, fmom, mask=mask, stream=filt)
+        rnd_d.copy_(rnd_h, non_blocking=True)
+        mg.rambo(proc, rnd_d, ecm, mom=mom, wgt=wgt, stream=stream)
+        stream.wait_stream(filt)
+        mg.sigmakin(proc, mom, mask, mode=args.mode, me=me, stream=stream)
+        mg.event_sum(me, wgt, out=out, scratch=scratch, stream=stream)
+        me_h.copy_(me, non_blocking=True)
+        sums_h.copy_(out, non_blocking=True)
 
     for _ in range(args.warmup):
         step_e2e()
