@@ -118,3 +118,26 @@ def test_grad_unsupported_process(mg):
     p = torch.zeros(64, dtype=torch.float64, device="cuda").data_ptr()
     assert L.mg_sigmakin_grad(4, 1, 1500.0, p, 16, p, None, p, None, 1, None) == -2
     assert L.mg_sigmakin_grad(1, 1, 500.0, p, 16, p, None, p, None, 1, None) == -2
+
+
+@pytest.mark.parametrize("proc,mode", [(2, "fp64"), (3, "fp64"), (3, "mixed")])
+def test_helicity_subsets_add_up(mg, proc, mode):
+    """The gradient is linear in the helicity sum: the gradients for two
+    complementary helicity masks add up to the full one (the masked runs take
+    the adjoint's path for incomplete helicity sets, the full one its warp-sum
+    path, which the oracle comparisons pin)."""
+    nevt, nrows = 301, 16
+    rnd = torch.from_numpy(I.uniforms(I.seed_of("gg_ttg_grad") + 10 * proc, nrows, nevt)).cuda()
+    full = mask_for(mg, proc, nrows)
+    nhel = full.numel()
+    a = full.clone()
+    a[torch.arange(nhel, device="cuda") % 3 == 0] = 0
+    b = full - a
+    g, me = mg.sigmakin_grad(proc, rnd, 1500.0, full, mode=mode)
+    ga, mea = mg.sigmakin_grad(proc, rnd, 1500.0, a, mode=mode)
+    gb, meb = mg.sigmakin_grad(proc, rnd, 1500.0, b, mode=mode)
+    torch.cuda.synchronize()
+    bar = 1e-12 if mode == "fp64" else 1e-5
+    np.testing.assert_allclose((mea + meb).cpu().numpy(), me.cpu().numpy(), rtol=bar)
+    s, ref = (ga + gb).cpu().numpy(), g.cpu().numpy()
+    assert np.all(np.max(np.abs(s - ref), axis=0) <= bar * np.max(np.abs(ref), axis=0))
