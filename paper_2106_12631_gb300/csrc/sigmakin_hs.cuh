@@ -27,20 +27,25 @@ namespace mg {
 #define MG_HS_NT 256
 #endif
 #ifndef MG_HS_CTAS
-#define MG_HS_CTAS 2  // resident CTAs per SM the shared-memory budget is split for
+#define MG_HS_CTAS 2  // resident CTAs per SM the shared-memory budget is split for (24+ colour flows)
+#endif
+#ifndef MG_HS_CTAS_SMALL
+#define MG_HS_CTAS_SMALL 3  // the same below 24 colour flows (smaller variant sets per event)
 #endif
 
-// Many-colour processes in FP32: two 256-thread CTAs per SM (4 events x 64
-// helicities each for gg -> t t~ g g), so that one CTA's short barrier-bound
-// phases overlap the other's contractions.  FP64 needs more registers per
-// thread: one 256-thread CTA per SM.
+// Many-colour processes in FP32: several 256-thread CTAs per SM (two of
+// 4 events x 64 helicities for gg -> t t~ g g, three of 8 x 32 for
+// gg -> t t~ g), so that one CTA's short barrier-bound phases overlap the
+// others' contractions (measured).  FP64 needs more registers per thread:
+// one 256-thread CTA per SM.
 template <class P, class R>
 struct HsCfg {
   static constexpr int NT = P::NCOLOR >= 6 ? (sizeof(R) == 4 ? MG_HS_NT : 256) : 128;
   static constexpr int EVMIN = (NT / P::NHEL) > 0 ? (NT / P::NHEL) : 1;
   static constexpr int EVWANT = (4 * EVMIN) < 32 ? 4 * EVMIN : 32;
   // shared memory for the current variants and one chunk of amputated currents
-  static constexpr int CTAS = P::NCOLOR >= 6 && sizeof(R) == 4 ? MG_HS_CTAS : 1;
+  static constexpr int CTAS =
+      P::NCOLOR >= 6 && sizeof(R) == 4 ? (P::NCOLOR >= 24 ? MG_HS_CTAS : MG_HS_CTAS_SMALL) : 1;
   static constexpr size_t CUR_BUDGET = 192 * 1024 / CTAS;
   static constexpr size_t EV_BYTES = (size_t)(P::HS_NSLOT + P::HS_XBUFS * P::HS_XCAP) * sizeof(W4<R>);
   static constexpr int FIT = (int)(CUR_BUDGET / EV_BYTES);
