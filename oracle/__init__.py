@@ -87,6 +87,8 @@ def lib():
             L.oracle_me_grad.argtypes = [ctypes.c_int, ctypes.c_long, ctypes.c_double, dp,
                                          ctypes.c_int, pp, dp, dp, ctypes.c_int]
             L.oracle_event_sum.argtypes = [ctypes.c_long, dp, dp, dp]
+            L.oracle_colour_flow_info.argtypes = [ctypes.c_int, ip, dp]
+            L.oracle_colour_flows.argtypes = [ctypes.c_int, ctypes.c_long, dp, pp, dp, ctypes.c_int]
             _lib = L
     return _lib
 
@@ -209,6 +211,49 @@ def event_sum(me_: np.ndarray, wgt: np.ndarray) -> np.ndarray:
     return out
 
 
+def colour_flow_info(proc: int):
+    """(number of colour flows, residual of the projection of the diagrams'
+    colour tensors onto the colour chains)."""
+    n, r = ctypes.c_int(), ctypes.c_double()
+    _chk(lib().oracle_colour_flow_info(proc, n, ctypes.byref(r)), "colour_flow_info")
+    return n.value, r.value
+
+
+def colour_flows(proc: int, mom: np.ndarray, prm: Params | None = None, nthreads: int = 1) -> np.ndarray:
+    """Colour-flow amplitudes J_s of every helicity: complex (nhel, nflow, nevt); the
+    full-colour amplitude is sum_s J_s (T^{a_s1} .. T^{a_sk})_{i_top j_antitop}."""
+    mom = np.ascontiguousarray(mom, dtype=np.float64)
+    nevt = mom.shape[2]
+    nf, _ = colour_flow_info(proc)
+    prm = prm or params()
+    out = np.zeros((1 << NPAR[proc], nf, nevt, 2))
+    _chk(lib().oracle_colour_flows(proc, nevt, _p(mom), ctypes.byref(prm), _p(out), nthreads), "colour_flows")
+    return out[..., 0] + 1j * out[..., 1]
+
+
+def choose_colour(jf: np.ndarray, mask: np.ndarray, u: np.ndarray) -> np.ndarray:
+    """One colour flow per event with probability w_s / sum_t w_t, w_s = sum over the
+    good helicities of |J_s|^2: the first flow whose running sum exceeds u * sum
+    (the last flow if rounding leaves none); -1 where the sum is zero."""
+    good = np.nonzero(np.asarray(mask))[0]
+    w = np.zeros(jf.shape[1:])
+    for h in good:
+        w += np.abs(jf[h]) ** 2
+    out = np.full(jf.shape[2], -1, dtype=np.int32)
+    for e in range(jf.shape[2]):
+        tot = sum(w[s, e] for s in range(w.shape[0]))
+        if tot <= 0.0:
+            continue
+        target, run = u[e] * tot, 0.0
+        out[e] = w.shape[0] - 1
+        for s in range(w.shape[0]):
+            run += w[s, e]
+            if run > target:
+                out[e] = s
+                break
+    return out
+
+
 # ---- cross section and unweighting (Sec. 3: the run's weighted events give the
 # cross section; unweighting keeps events with probability x / max x) ----------
 HBARC2_PB = 0.3893793721e9  # (hbar c)^2 in pb GeV^2
@@ -235,3 +280,27 @@ def unweight(me_: np.ndarray, wgt: np.ndarray, u: np.ndarray) -> np.ndarray:
     xmax = x.max()
     return np.nonzero(np.asarray(u, dtype=np.float64) * xmax < x)[0].astype(np.int64)
 
+
+
+def choose_helicity(ph: np.ndarray, mask: np.ndarray, u: np.ndarray) -> np.ndarray:
+    """One helicity per event with probability |M_h|^2 / sum over the good h.
+
+    Inverse-CDF sampling over the good helicities (mask != 0) in increasing
+    index order: the first h whose running sum exceeds u * sum (the last good
+    one if rounding leaves none); -1 where the sum is zero.  ph: (nhel, nevt).
+    """
+    ph = np.asarray(ph, dtype=np.float64)
+    good = np.nonzero(np.asarray(mask))[0]
+    out = np.full(ph.shape[1], -1, dtype=np.int32)
+    for e in range(ph.shape[1]):
+        tot = sum(ph[h, e] for h in good)
+        if tot <= 0.0:
+            continue
+        target, run = u[e] * tot, 0.0
+        out[e] = good[-1]
+        for h in good:
+            run += ph[h, e]
+            if run > target:
+                out[e] = h
+                break
+    return out

@@ -880,6 +880,126 @@ static void parallel_for(long n, int nthreads, const std::function<void(long, lo
 }  // namespace orc
 
 // ----------------------------------------------------------------------------
+// Colour flows (Sec. 2, colour-flow method).  The full-colour amplitude of one
+// helicity, M(c) = sum_d a_d x_d(c) over the explicit colour assignments c of
+// all legs, is written in the basis of the colour chains
+//   chi_s(c) = (T^{a_{g(s_1)}} ... T^{a_{g(s_k)}})_{i_top j_antitop},
+// g = the gluon legs in leg order, s the k! permutations in lexicographic
+// order (one flow, chi = 1, without colour): M = sum_s J_s chi_s.  The
+// coefficient of each amplitude on each chain is the projection
+// P = G^{-1} B^dagger X with B[c][s] = chi_s(c), G = B^dagger B and
+// X[c][d] = x_d(c); the residual max |B P - X| shows that every diagram's
+// colour tensor lies in the span of the chains.
+// ----------------------------------------------------------------------------
+namespace orc {
+
+struct FlowProjection {
+  int nflow = 0;
+  std::vector<C> P;  // [s][d]
+  double residual = 0.0;
+};
+
+static FlowProjection* build_flow_projection(const Topology& tp) {
+  const auto& legs = tp.proc.legs;
+  const int nl = (int)legs.size();
+  std::vector<int> g;
+  int top = -1, atop = -1;
+  for (int l = 0; l < nl; ++l) {
+    if (legs[l].line == GLU) g.push_back(l);
+    if (legs[l].line == ROW_T) top = l;
+    if (legs[l].line == COL_T) atop = l;
+  }
+  const int ng = (int)g.size();
+  std::vector<std::vector<int>> perms;
+  std::vector<int> pm(ng);
+  for (int i = 0; i < ng; ++i) pm[i] = i;
+  do perms.push_back(pm); while (std::next_permutation(pm.begin(), pm.end()));
+  const int nf = top >= 0 ? (int)perms.size() : 1;
+  size_t ncol = 1;
+  for (int l = 0; l < nl; ++l) ncol *= colour_dim(legs[l].line);
+  const SU3& G3 = su3();
+  // B[c][s]
+  std::vector<C> B(ncol * nf, C(0));
+  std::vector<int> col(nl);
+  for (size_t A = 0; A < ncol; ++A) {
+    size_t rem = A;
+    for (int l = nl - 1; l >= 0; --l) { int d = colour_dim(legs[l].line); col[l] = (int)(rem % d); rem /= d; }
+    if (top < 0) { B[A] = 1.0; continue; }
+    for (int s = 0; s < nf; ++s) {
+      C M[3][3];
+      for (int i = 0; i < 3; ++i) for (int j = 0; j < 3; ++j) M[i][j] = i == j ? 1.0 : 0.0;
+      for (int k = 0; k < ng; ++k) {
+        const int a = col[g[perms[s][k]]];
+        C R[3][3];
+        for (int i = 0; i < 3; ++i)
+          for (int j = 0; j < 3; ++j) {
+            R[i][j] = 0;
+            for (int m = 0; m < 3; ++m) R[i][j] += M[i][m] * G3.T[a][m][j];
+          }
+        for (int i = 0; i < 3; ++i) for (int j = 0; j < 3; ++j) M[i][j] = R[i][j];
+      }
+      B[A * nf + s] = M[col[top]][col[atop]];
+    }
+  }
+  const int na = (int)tp.amps.size();
+  // normal equations G P = H, H = B^dagger X
+  std::vector<C> Gm(nf * nf, C(0)), H((size_t)nf * na, C(0));
+  for (size_t A = 0; A < ncol; ++A)
+    for (int s = 0; s < nf; ++s) {
+      const C b = std::conj(B[A * nf + s]);
+      if (b == C(0)) continue;
+      for (int t = 0; t < nf; ++t) Gm[s * nf + t] += b * B[A * nf + t];
+      for (int d = 0; d < na; ++d) {
+        const C x = tp.ctensor[tp.amps[d]][A];
+        if (x != C(0)) H[(size_t)s * na + d] += b * x;
+      }
+    }
+  // Gauss-Jordan elimination with partial pivoting on [G | H]
+  for (int k = 0; k < nf; ++k) {
+    int piv = k;
+    for (int r = k + 1; r < nf; ++r) if (std::abs(Gm[r * nf + k]) > std::abs(Gm[piv * nf + k])) piv = r;
+    if (piv != k) {
+      for (int t = 0; t < nf; ++t) std::swap(Gm[k * nf + t], Gm[piv * nf + t]);
+      for (int d = 0; d < na; ++d) std::swap(H[(size_t)k * na + d], H[(size_t)piv * na + d]);
+    }
+    const C inv = 1.0 / Gm[k * nf + k];
+    for (int t = 0; t < nf; ++t) Gm[k * nf + t] *= inv;
+    for (int d = 0; d < na; ++d) H[(size_t)k * na + d] *= inv;
+    for (int r = 0; r < nf; ++r) {
+      if (r == k) continue;
+      const C f = Gm[r * nf + k];
+      if (f == C(0)) continue;
+      for (int t = 0; t < nf; ++t) Gm[r * nf + t] -= f * Gm[k * nf + t];
+      for (int d = 0; d < na; ++d) H[(size_t)r * na + d] -= f * H[(size_t)k * na + d];
+    }
+  }
+  auto* fp = new FlowProjection();
+  fp->nflow = nf;
+  fp->P = H;
+  double res = 0.0;
+  for (size_t A = 0; A < ncol; ++A)
+    for (int d = 0; d < na; ++d) {
+      C v = -tp.ctensor[tp.amps[d]][A];
+      for (int s = 0; s < nf; ++s) v += B[A * nf + s] * H[(size_t)s * na + d];
+      res = std::max(res, std::abs(v));
+    }
+  fp->residual = res;
+  return fp;
+}
+
+static const FlowProjection* flow_projection(int proc) {
+  static std::mutex mu;
+  static FlowProjection* cache[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  Topology* tp = topology(proc);
+  if (!tp) return nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!cache[proc]) cache[proc] = build_flow_projection(*tp);
+  return cache[proc];
+}
+
+}  // namespace orc
+
+// ----------------------------------------------------------------------------
 // C entry points (ctypes).  Arrays are structure-of-arrays with the event
 // index fastest: rnd[k*nevt + i], mom[((p*4)+mu)*nevt + i].
 // Return 0 on success, a negative number on a bad argument.
@@ -1088,6 +1208,48 @@ int oracle_event_sum(long nevt, const double* me, const double* w, double* out3)
   double s1 = 0, s2 = 0;
   if (nevt > 0) pairwise(me, w, 0, nevt, s1, s2);
   out3[0] = s1; out3[1] = s2; out3[2] = (double)nevt;
+  return 0;
+}
+
+// Colour-flow decomposition: number of flows and the projection residual
+int oracle_colour_flow_info(int proc, int* nflow, double* residual) {
+  const FlowProjection* fp = flow_projection(proc);
+  if (!fp) return -2;
+  *nflow = fp->nflow;
+  *residual = fp->residual;
+  return 0;
+}
+
+// Colour-flow amplitudes J_s of every helicity h (index as in oracle_me):
+// jf[((h*nflow + s)*nevt + i)*2 + {0: re, 1: im}], without the average factors
+int oracle_colour_flows(int proc, long nevt, const double* mom, const oracle_params* prm, double* jf, int nthreads) {
+  Topology* tp = topology(proc);
+  const FlowProjection* fp = flow_projection(proc);
+  if (!tp || !fp) return -2;
+  if (nevt < 0) return -1;
+  Couplings cp = couplings(*prm);
+  const int nl = (int)tp->proc.legs.size(), nh = 1 << nl, nf = fp->nflow, na = (int)tp->amps.size();
+  parallel_for(nevt, nthreads, [&](long a, long b) {
+    Eval<double> ev(*tp, cp);
+    std::vector<int> hel(nl);
+    std::vector<Cx<double>> amp(na);
+    for (long i = a; i < b; ++i) {
+      std::vector<Mom<double>> p(nl);
+      for (int l = 0; l < nl; ++l) for (int mu = 0; mu < 4; ++mu) p[l][mu] = mom[(l * 4 + mu) * nevt + i];
+      for (int h = 0; h < nh; ++h) {
+        for (int k = 0; k < nl; ++k) hel[k] = ((h >> (nl - 1 - k)) & 1) ? +1 : -1;
+        ev.run(p, hel);
+        for (int d = 0; d < na; ++d) amp[d] = ev.close(tp->amps[d], p, hel);
+        for (int s = 0; s < nf; ++s) {
+          C j = 0;
+          for (int d = 0; d < na; ++d) j += fp->P[(size_t)s * na + d] * C(amp[d].re, amp[d].im);
+          const size_t o = (((size_t)h * nf + s) * nevt + i) * 2;
+          jf[o] = j.real();
+          jf[o + 1] = j.imag();
+        }
+      }
+    }
+  });
   return 0;
 }
 

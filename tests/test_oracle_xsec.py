@@ -96,3 +96,29 @@ def test_unweight_distribution(orc):
     c = mom[2, 3, kept] / mom[2, 0, kept]  # cos theta of the mu+
     c2 = np.mean(c ** 2)  # 1 + cos^2 theta: <cos^2> = 2/5, variance of cos^2 = 9/35 - 4/25
     assert abs(c2 - 0.4) < 5 * math.sqrt((9 / 35 - 4 / 25) / kept.size), c2
+
+
+def test_choose_helicity_hand_example():
+    ph = np.array([[1.0, 0.0, 2.0], [0.0, 0.0, 2.0], [3.0, 0.0, 0.0], [4.0, 0.0, 4.0]])  # (nhel=4, nevt=3)
+    mask = np.array([1, 0, 1, 1])  # helicity 1 is not good
+    # event 0: good sums 1, 4, 8 -> u=0.5 -> target 4 -> first run > 4 is h=3
+    # event 1: all zero -> -1; event 2: runs 2, 2, 6 (h=1 skipped) -> u=0.2 -> 1.2 -> h=0
+    np.testing.assert_array_equal(oracle.choose_helicity(ph, mask, np.array([0.5, 0.3, 0.2])), [3, -1, 0])
+    # u = 0 picks the first good helicity with |M_h|^2 > 0; u -> 1 the last one
+    np.testing.assert_array_equal(oracle.choose_helicity(ph, mask, np.array([0.0, 0.0, 0.0])), [0, -1, 0])
+    np.testing.assert_array_equal(oracle.choose_helicity(ph, mask, np.full(3, 1 - 2 ** -53)), [3, -1, 3])
+
+
+def test_choose_helicity_frequencies(orc):
+    # one gg -> t tbar point, many uniforms: the chosen helicities follow |M_h|^2 / |M|^2
+    rnd = I.uniforms(9105, 4 * 2, 1)
+    mom, _ = orc.rambo(2, rnd, 1500.0)
+    me, ph = orc.me(2, mom, per_helicity=True)
+    n = 1 << 14
+    u = I.uniforms(9106, 1, n)[0]
+    mask = (ph[:, 0] > 0).astype(np.int32)
+    h = oracle.choose_helicity(np.repeat(ph, n, axis=1), mask, u)
+    p = ph[:, 0] / ph[:, 0].sum()
+    for k in range(ph.shape[0]):
+        f = np.mean(h == k)
+        assert abs(f - p[k]) < 5 * math.sqrt(p[k] * (1 - p[k]) / n) + 1e-12, (k, f, p[k])
