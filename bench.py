@@ -207,7 +207,7 @@ def measure_other_workloads(mg, I, dev, stream, reps: int = 3) -> dict:
     return out
 
 
-def measure_generation(mg, proc, ecm, nevt, seed, mom, wgt, me, sums, stream, hbm_gbs, reps=3):
+def measure_generation(mg, proc, ecm, nevt, seed, mom, wgt, me, sums, stream, hbm_gbs, mask, mode, reps=3):
     import torch
 
     def time_it(fn):
@@ -236,12 +236,29 @@ def measure_generation(mg, proc, ecm, nevt, seed, mom, wgt, me, sums, stream, hb
     out3 = torch.empty(3, dtype=torch.float64, device=mom.device)
     t_sum = time_it(lambda: mg.event_sum(me, wgt, out=out3, scratch=scr, stream=stream))
     uw_bytes = 3 * 16 * nevt + 8 * kept  # (w, me) read by three passes, kept indices written
+    # the batched entry point for an external integrator: the same events as an
+    # array of structures, alone and with a helicity and a colour flow chosen per event
+    mom_aos = mom.permute(2, 0, 1).contiguous()
+    me_b = torch.empty_like(me)
+    hel_b = torch.empty(nevt, dtype=torch.int32, device=mom.device)
+    col_b = torch.empty(nevt, dtype=torch.int32, device=mom.device)
+    ws = torch.empty(mg.batch_workspace_bytes(proc, nevt) // 8 + 2, dtype=torch.float64, device=mom.device)
+    t_batch = time_it(lambda: mg.matrix_elements_batch(proc, mom_aos, mask, mode=mode, me=me_b, workspace=ws,
+                                                       stream=stream))
+    choose = "unrolled" not in mode  # the choices come with the helicity-shared kernels
+    t_choice = time_it(lambda: mg.matrix_elements_batch(proc, mom_aos, mask, mode=mode, hel_rnd=rnd[0], col_rnd=rnd[1],
+                                                        me=me_b, hel=hel_b, col=col_b, workspace=ws,
+                                                        stream=stream)) if choose else None
+    t_sig = time_it(lambda: mg.sigmakin(proc, mom, mask, mode=mode, me=me_b, stream=stream))
+    del mom_aos, ws
     return {"events": nevt,
             "rambo_device_rng_ms": 1e3 * t_seed, "rambo_buffered_ms": 1e3 * t_buf,
             "unweight_ms": 1e3 * t_uw, "unweight_kept": kept,
             "unweight_gbs": uw_bytes / t_uw / 1e9,
             "unweight_hbm_frac": (uw_bytes / t_uw / 1e9) / hbm_gbs if hbm_gbs else None,
             "cross_section_pb": float(xs[0]), "cross_section_err_pb": float(xs[1]),
+            "batch_aos_ms": 1e3 * t_batch,
+            "batch_aos_with_choices_ms": 1e3 * t_choice if t_choice is not None else None, "sigmakin_soa_ms": 1e3 * t_sig,
             "rooflines": {
                 "event_sum": {"bound": "hbm", "achieved": 16 * nevt / t_sum / 1e9, "peak": hbm_gbs,
                               "unit": "GB/s", "frac": (16 * nevt / t_sum / 1e9) / hbm_gbs if hbm_gbs else None,
@@ -411,7 +428,7 @@ def main():
     generation = None
     if not args.no_others:
         generation = measure_generation(mg, proc, ecm, nevt, seed, mom, wgt, me, out, stream,
-                                        measured_peaks().get("hbm_gbs"))
+                                        measured_peaks().get("hbm_gbs"), mask, args.mode)
 
     # the other workloads (SIGMAKIN or the adjoint alone, inputs resident, CUDA events)
     others = {} if args.no_others else measure_other_workloads(mg, I, dev, stream)

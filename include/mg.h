@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define MG_ABI_VERSION 3
+#define MG_ABI_VERSION 4
 
 typedef enum {
   MG_OK = 0,
@@ -198,6 +198,32 @@ int mg_cross_section(int proc, double ecm, const double* sums3, double* xsec2, v
 int64_t mg_unweight_scratch_bytes(int64_t nevt);
 int mg_unweight(int64_t nevt, const double* me, const double* wgt, uint64_t seed, int64_t first_event,
                 int64_t* idx, int64_t* count, void* scratch, int64_t scratch_bytes, void* stream);
+
+/* Batched matrix elements for an external integrator (Sec. 6: the MadEvent
+ * bridge, where an existing event generator hands over a set of phase-space
+ * points it prepared and receives their matrix elements, its 4-momenta passed
+ * in its own layout): momenta as an array of structures
+ * mom_aos[nevt][npar][4] (device; E, px, py, pz of every particle in the
+ * process's leg order, incoming legs first, as mg_rambo returns them but event
+ * by event) -> me[nevt] as mg_sigmakin (mask from mg_filter_helicities, mode as
+ * mg_sigmakin).  Optional choices (modes 0-2 and 5; NULL outputs skip them,
+ * a non-NULL output needs its uniforms, device [nevt] in [0, 1)), made per
+ * event in FP64 by inverse-CDF sampling: the first index, in order, whose
+ * running sum of weights exceeds u * (sum of the weights):
+ *   hel_out (int32 [nevt], from hel_rnd): a good helicity, weights |M_h|^2
+ *     (colour summed) in helicity-index order;
+ *   col_out (int32 [nevt], from col_rnd): a colour flow s, weights
+ *     sum over the good helicities of |J_s|^2 (Sec. 2, colour-flow method:
+ *     J_s the coefficient of the chain (T^{a_s1} ... T^{a_sk})_{i_top j_antitop},
+ *     s the k! orderings of the gluon legs, in leg order, in lexicographic
+ *     order; one flow without colour).
+ * Both are -1 for an event with me = 0.  workspace: device, >=
+ * mg_batch_workspace_bytes(proc, nevt) bytes (the structure-of-arrays copy),
+ * else MG_ERR_SPACE. */
+int64_t mg_batch_workspace_bytes(int proc, int64_t nevt);
+int mg_matrix_elements_batch(int proc, int64_t nevt, const double* mom_aos, const int32_t* mask, int mode,
+                             const double* hel_rnd, const double* col_rnd, double* me, int32_t* hel_out,
+                             int32_t* col_out, void* workspace, int64_t workspace_bytes, void* stream);
 
 /* End-to-end pipeline from HOST buffers (copies inside): h_rnd [nrows][nevt]
  * -> host-to-device copy -> RAMBO -> SIGMAKIN (mask from mg_filter_helicities,

@@ -19,6 +19,10 @@ struct SigLaunch {
   PhysParams pp;
   Couplings<double> cd;
   Couplings<float> cf;
+  const double* hel_rnd = nullptr;  // helicity and colour-flow choices (helicity-shared kernel only)
+  int32_t* hel_out = nullptr;
+  const double* col_rnd = nullptr;
+  int32_t* col_out = nullptr;
 };
 
 // rnd == nullptr: uniforms drawn on the device from (seed, first_event + i, row)
@@ -30,6 +34,8 @@ cudaError_t launch_rambo_final(int nfinal, int64_t nevt, double ecm, const doubl
                                const RamboSetup& st, cudaStream_t s);
 cudaError_t launch_rambo_adjoint(int nfinal, int64_t nevt, double ecm, const double* rnd, int nrows, double* grad,
                                  const RamboSetup& st, cudaStream_t s);
+// [nevt][npar][4] -> [npar][4][nevt]
+cudaError_t launch_aos_to_soa(int64_t nevt, int npar, const double* aos, double* soa, cudaStream_t s);
 int64_t unweight_blocks(int64_t n);
 cudaError_t launch_unweight(int64_t n, const double* me, const double* w, uint64_t seed, int64_t first_event,
                             int64_t* idx, int64_t* count, double* scratch, cudaStream_t s);

@@ -224,6 +224,36 @@ int mg_unweight(int64_t nevt, const double* me, const double* wgt, uint64_t seed
   return cuda_status(mg::launch_unweight(nevt, me, wgt, seed, first_event, idx, count, (double*)scratch, s));
 }
 
+int64_t mg_batch_workspace_bytes(int proc, int64_t nevt) {
+  if (!valid_proc(proc) || nevt < 0) return -1;
+  return align256(8 * nevt * 4 * kProcs[proc].npar);
+}
+
+int mg_matrix_elements_batch(int proc, int64_t nevt, const double* mom_aos, const int32_t* mask, int mode,
+                             const double* hel_rnd, const double* col_rnd, double* me, int32_t* hel_out,
+                             int32_t* col_out, void* workspace, int64_t workspace_bytes, void* stream) {
+  if (!valid_proc(proc)) return MG_ERR_PROC;
+  if (nevt < 0 || mode < 0 || mode > 5) return MG_ERR_ARG;
+  if ((hel_out || col_out) && (mode == 3 || mode == 4)) return MG_ERR_ARG;  // choices: helicity-shared modes
+  if ((hel_out && !hel_rnd) || (col_out && !col_rnd)) return MG_ERR_ARG;
+  if (nevt == 0) return MG_OK;
+  if (!mom_aos || !mask || !me || !workspace) return MG_ERR_ARG;
+  if (!aligned(mom_aos) || !aligned(mask) || !aligned(me) || !aligned(workspace) || (hel_out && !aligned(hel_out)) ||
+      (col_out && !aligned(col_out)) || (hel_out && !aligned(hel_rnd)) || (col_out && !aligned(col_rnd)))
+    return MG_ERR_ALIGN;
+  if (workspace_bytes < mg_batch_workspace_bytes(proc, nevt)) return MG_ERR_SPACE;
+  if (nevt > (int64_t)INT32_MAX * 16) return MG_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  double* soa = (double*)workspace;
+  if (int r = cuda_status(mg::launch_aos_to_soa(nevt, kProcs[proc].npar, mom_aos, soa, s))) return r;
+  mg::SigLaunch l = sig_launch(nevt, soa, mask, me, nullptr);
+  l.hel_rnd = hel_out ? hel_rnd : nullptr;
+  l.hel_out = hel_out;
+  l.col_rnd = col_out ? col_rnd : nullptr;
+  l.col_out = col_out;
+  return cuda_status(dispatch_sigmakin(proc, l, mode, s));
+}
+
 int mg_filter_helicities(int proc, int64_t nevt, const double* mom, int32_t* mask, void* stream) {
   if (!valid_proc(proc)) return MG_ERR_PROC;
   if (nevt < 0) return MG_ERR_ARG;

@@ -46,6 +46,10 @@ struct SigArgs {
   double* __restrict__ me;            // [nevt] (sum mode)
   int32_t* __restrict__ mask_out;     // [nhel] (filter mode, pre-zeroed)
   PhysParams pp;
+  const double* __restrict__ hel_rnd;  // [nevt] uniforms for the helicity choice, or null
+  int32_t* __restrict__ hel_out;       // [nevt] chosen helicity (-1 if me = 0), or null
+  const double* __restrict__ col_rnd;  // [nevt] uniforms for the colour-flow choice, or null
+  int32_t* __restrict__ col_out;       // [nevt] chosen colour flow (-1 if me = 0), or null
 };
 
 // ---- dual-amplitude accumulators ------------------------------------------------

@@ -439,6 +439,76 @@ __device__ __forceinline__ void hs_xitem(const HsItem& it, const Slots<R, P::HS_
   xb.set(it.out, o);
 }
 
+// Inverse-CDF sampling by one warp: the first k < n, in order, whose running
+// sum of the weights get(k) exceeds u * (their total), the last one if
+// rounding leaves none, -1 if the total is not positive (FP64; n <= 32 RND,
+// lanes take consecutive k, running sums by warp scans 32 weights at a time,
+// the total is the last running sum).
+template <int RND, class F>
+__device__ __forceinline__ int warp_inverse_cdf(int n, double u, int lane, F get) {
+  double run[RND];
+  double carry = 0.0;
+#pragma unroll
+  for (int r = 0; r < RND; ++r) {
+    run[r] = 0.0;
+    if (32 * r < n) {
+      double x = 32 * r + lane < n ? get(32 * r + lane) : 0.0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const double y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      run[r] = carry + x;
+      carry = __shfl_sync(0xffffffffu, run[r], 31);
+    }
+  }
+  if (!(carry > 0.0)) return -1;
+  const double target = u * carry;
+#pragma unroll
+  for (int r = 0; r < RND; ++r) {
+    const unsigned hit = __ballot_sync(0xffffffffu, 32 * r + lane < n && run[r] > target);
+    if (hit) return 32 * r + __ffs(hit) - 1;
+  }
+  return n - 1;
+}
+
+// Per event: a good helicity with probability |M_h|^2 / sum (weights sm2 of
+// the event's threads, helicity order) and a colour flow s with probability
+// w_s / sum, w_s = sum over the good helicities of |J_s|^2; one warp per event.
+// The |J_s|^2 of every thread are staged in the dead union region, thread-major
+// with an odd row stride (lane s of the event's warp sums row entries s over
+// the event's helicities, in helicity order, in the working precision; the
+// running sums that decide are FP64).
+template <class P, class R>
+struct HsChoice {
+  static constexpr int NCP = P::NCOLOR | 1;
+};
+
+template <class P, class R, class L>
+__device__ __forceinline__ void hs_choices(const unsigned char* smem, const SigArgs& a, int64_t e0, int nev, int ng,
+                                           const int* good, const double* sm2) {
+  constexpr int NT = L::NT, NC = P::NCOLOR, NCP = HsChoice<P, R>::NCP;
+  static_assert(NC <= 32, "one lane per colour flow");
+  static_assert(sizeof(R) * NCP * NT <= L::u_bytes, "colour weights overflow their scratch");
+  const int tid = threadIdx.x, lane = tid & 31;
+  const R* wj = reinterpret_cast<const R*>(smem + L::o_U);
+  for (int e = tid >> 5; e < nev; e += NT / 32) {
+    if (a.hel_out) {
+      const int k = warp_inverse_cdf<(P::NHEL + 31) / 32>(ng, a.hel_rnd[e0 + e], lane,
+                                                          [&](int i) { return sm2[e * ng + i]; });
+      if (lane == 0) a.hel_out[e0 + e] = k < 0 ? -1 : good[k];
+    }
+    if (a.col_out) {
+      R x = R(0);
+      if (lane < NC)
+        for (int k = 0; k < ng; ++k) x += wj[(e * ng + k) * NCP + lane];
+      const double w = (double)x;
+      const int c = warp_inverse_cdf<1>(NC, a.col_rnd[e0 + e], lane, [&](int) { return w; });
+      if (lane == 0) a.col_out[e0 + e] = c;
+    }
+  }
+}
+
 template <class P, class R, int CS>
 __global__ void __launch_bounds__(HsCfg<P, R>::NT, HsCfg<P, R>::CTAS) sigmakin_hs_kernel(SigArgs a, Couplings<R> cp) {
   using C = HsCfg<P, R>;
@@ -487,7 +557,11 @@ __global__ void __launch_bounds__(HsCfg<P, R>::NT, HsCfg<P, R>::CTAS) sigmakin_h
   if (e0 >= a.nevt) return;
   const int nev = (int)min((int64_t)ev, a.nevt - e0);
   if (ng == 0) {
-    if (tid < nev) a.me[e0 + tid] = 0.0;
+    if (tid < nev) {
+      a.me[e0 + tid] = 0.0;
+      if (a.hel_out) a.hel_out[e0 + tid] = -1;
+      if (a.col_out) a.col_out[e0 + tid] = -1;
+    }
     return;
   }
   uint32_t tmem = 0, mbar = 0;
@@ -574,6 +648,16 @@ __global__ void __launch_bounds__(HsCfg<P, R>::NT, HsCfg<P, R>::CTAS) sigmakin_h
     double sum = 0.0;
     for (int k = 0; k < ng; ++k) sum += sm2[tid * ng + k];
     a.me[e0 + tid] = sum * P::NORM;
+  }
+  // 5. helicity and colour-flow choices (batched entry point)
+  if (a.hel_out || a.col_out) {
+    if (a.col_out) {
+      R* wj = reinterpret_cast<R*>(smem + L::o_U) + tid * HsChoice<P, R>::NCP;  // the union is dead here
+#pragma unroll
+      for (int s = 0; s < NC; ++s) wj[s] = active ? J[s].re * J[s].re + J[s].im * J[s].im : R(0);
+      __syncthreads();
+    }
+    hs_choices<P, R, L>(smem, a, e0, nev, ng, good, sm2);
   }
 }
 

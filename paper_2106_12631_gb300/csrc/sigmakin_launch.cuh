@@ -34,7 +34,7 @@ cudaError_t launch_sigmakin_hs_variant(const SigArgs& a, const Couplings<R>& cp,
 // the per-helicity unrolled kernel (every helicity recomputes all its currents)
 template <class P>
 cudaError_t launch_sigmakin_impl(const SigLaunch& l, int mode, cudaStream_t s) {
-  SigArgs a{l.nevt, l.mom, l.mask, l.me, l.mask_out, l.pp};
+  SigArgs a{l.nevt, l.mom, l.mask, l.me, l.mask_out, l.pp, l.hel_rnd, l.hel_out, l.col_rnd, l.col_out};
   const int64_t grid = (l.nevt + SigCfg<P>::EVMIN - 1) / SigCfg<P>::EVMIN;
   if (grid == 0) return cudaSuccess;
   constexpr bool tc_default = P::NCOLOR >= 48;
@@ -54,7 +54,7 @@ cudaError_t launch_sigmakin_impl(const SigLaunch& l, int mode, cudaStream_t s) {
 template <class P>
 cudaError_t launch_filter_impl(const SigLaunch& l, cudaStream_t s) {
   using L = SigLayout<P, double, CS_SIMT>;
-  SigArgs a{l.nevt, l.mom, l.mask, l.me, l.mask_out, l.pp};
+  SigArgs a{l.nevt, l.mom, l.mask, l.me, l.mask_out, l.pp, nullptr, nullptr};
   const int64_t grid = l.nevt * ((P::NHEL + FILTER_NT - 1) / FILTER_NT);
   if (grid == 0) return cudaSuccess;
   auto k = filter_kernel<P>;

@@ -69,6 +69,9 @@ def lib():
             L.mg_unweight_scratch_bytes.argtypes = [i64]
             L.mg_unweight_scratch_bytes.restype = i64
             L.mg_unweight.argtypes = [i64, vp, vp, u64, i64, vp, vp, vp, i64, vp]
+            L.mg_batch_workspace_bytes.argtypes = [i32, i64]
+            L.mg_batch_workspace_bytes.restype = i64
+            L.mg_matrix_elements_batch.argtypes = [i32, i64, vp, vp, i32, vp, vp, vp, vp, vp, vp, i64, vp]
             L.mg_event_sum_noalloc_max_events.argtypes = []
             L.mg_event_sum_noalloc_max_events.restype = i64
             L.mg_event_sum_noalloc.argtypes = [i64, vp, vp, vp, vp]
@@ -189,6 +192,38 @@ def unweight(me: torch.Tensor, wgt: torch.Tensor, seed: int, first_event: int = 
                              _dev(count, torch.int64, "count", (1,)), scratch.data_ptr(),
                              scratch.numel() * scratch.element_size(), _stream(stream)), "mg_unweight")
     return idx, count
+
+
+def batch_workspace_bytes(proc, nevt: int) -> int:
+    return int(lib().mg_batch_workspace_bytes(_proc(proc), nevt))
+
+
+def matrix_elements_batch(proc, mom_aos: torch.Tensor, mask: torch.Tensor, mode="mixed", hel_rnd=None, col_rnd=None,
+                          me=None, hel=None, col=None, workspace=None, stream=None):
+    """mom_aos (nevt, npar, 4) float64 CUDA -> me (nevt,), or (me, hel, col) when hel_rnd or
+    col_rnd (nevt,) uniforms are given (a choice not asked for is None)."""
+    p = _proc(proc)
+    nevt, npar = mom_aos.shape[0], process_info(p)["npar"]
+    if me is None:
+        me = torch.empty((nevt,), dtype=torch.float64, device=mom_aos.device)
+    if hel_rnd is not None and hel is None:
+        hel = torch.empty((nevt,), dtype=torch.int32, device=mom_aos.device)
+    if col_rnd is not None and col is None:
+        col = torch.empty((nevt,), dtype=torch.int32, device=mom_aos.device)
+    nb = batch_workspace_bytes(p, nevt)
+    if workspace is None:
+        workspace = torch.empty(((max(nb, 16) + 7) // 8,), dtype=torch.float64, device=mom_aos.device)
+    m = MODES[mode] if isinstance(mode, str) else int(mode)
+    opt = lambda t, dt, name: _dev(t, dt, name, (nevt,)) if t is not None else None
+    _check(lib().mg_matrix_elements_batch(
+        p, nevt, _dev(mom_aos, torch.float64, "mom_aos", (nevt, npar, 4)), _dev(mask, torch.int32, "mask"), m,
+        opt(hel_rnd, torch.float64, "hel_rnd"), opt(col_rnd, torch.float64, "col_rnd"),
+        _dev(me, torch.float64, "me", (nevt,)), opt(hel, torch.int32, "hel"), opt(col, torch.int32, "col"),
+        workspace.data_ptr(), workspace.numel() * workspace.element_size(), _stream(stream)),
+        "mg_matrix_elements_batch")
+    if hel_rnd is None and col_rnd is None:
+        return me
+    return me, hel, col
 
 
 def filter_helicities(proc, mom: torch.Tensor, mask=None, stream=None) -> torch.Tensor:
