@@ -41,7 +41,7 @@ SM_MAX_MHZ = 2070.0
 # (dram__bytes_read.sum + dram__bytes_write.sum of one launch over 2^18 events,
 # scaled by events; it reads the momenta once and writes |M|^2), valid only
 # while the kernel sources are the ones captured.
-SIGMAKIN_TRAFFIC = {"bytes_per_event": 192.79, "sources_sha1": "77fd800010d4d1818d0549fb2234ce20547cff64"}
+SIGMAKIN_TRAFFIC = {"bytes_per_event": 192.81, "sources_sha1": "469fe696f946d64aced4490028e5c95d484e42d5"}
 SIGMAKIN_SOURCES = ["paper_2106_12631_gb300/csrc/" + f for f in
                     ("sigmakin_hs.cuh", "sigmakin.cuh", "helas.cuh", "colour_tc.cuh", "mg_types.cuh",
                      "process.cuh", "gen/proc4.cuh")]
