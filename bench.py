@@ -410,6 +410,29 @@ def main():
         tensor_core = {"mode": "mixed_tc", "value": world * nevt * max(1, min(args.steps, 2)) / tt, "unit": UNIT,
                        "sigmakin_ms": 1e3 * statistics.mean(kt)}
 
+    # SIGMAKIN split in two kernels per chunk (currents, then amplitudes), the
+    # chunks' launches replayed from a CUDA graph; same momenta and mask
+    kernel_split = None
+    if args.mode in ("mixed", "fp64") and not args.no_others:
+        smode = "mixed_simt" if args.mode == "mixed" else "fp64"  # gg -> t t~ g g: CUDA-core colour sum
+        ws = torch.empty(mg.sigmakin_split_workspace_bytes(proc, smode, nevt) // 8 + 2, dtype=torch.float64,
+                         device=dev)
+        me_s = torch.empty_like(me)
+        mg.sigmakin_split(proc, mom, mask, mode=smode, me=me_s, workspace=ws, stream=stream)  # graph capture
+        torch.cuda.synchronize()
+        ns = max(1, min(args.steps, 3))
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(ns):
+            mg.sigmakin_split(proc, mom, mask, mode=smode, me=me_s, workspace=ws, stream=stream)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        ts = a0.elapsed_time(a1) / 1e3 / ns
+        kernel_split = {"mode": smode, "value": world * nevt / ts, "unit": UNIT, "sigmakin_ms": 1e3 * ts,
+                        "workspace_mib": ws.numel() * 8 / 2 ** 20,
+                        "identical_to_single_kernel": bool(torch.equal(me_s, me_main))}
+        del ws, me_s
+
     fp64 = None
     if not args.no_fp64 and args.mode != "fp64":
         t64, k64 = timed("fp64", max(1, min(args.steps, 2)))
@@ -509,6 +532,7 @@ def main():
         "fp64": fp64,
         "unrolled": unrolled,
         "tensor_core_colour_sum": tensor_core,
+        "kernel_split": kernel_split,
         "other_workloads": others,
         "event_generation": generation,
         "event_sum": [float(x) for x in sums.cpu().numpy()],

@@ -225,6 +225,24 @@ int mg_matrix_elements_batch(int proc, int64_t nevt, const double* mom_aos, cons
                              const double* hel_rnd, const double* col_rnd, double* me, int32_t* hel_out,
                              int32_t* col_out, void* workspace, int64_t workspace_bytes, void* stream);
 
+/* Kernel-split variant of mg_sigmakin (Sec. 5, outlook: the single large
+ * SIGMAKIN kernel split into smaller kernels orchestrated with CUDA Graphs),
+ * kept for comparison with the single kernel.  Same inputs and result as
+ * mg_sigmakin (mom [npar][4][nevt], mask, me [nevt]; mode MG_FP64 = 0 or
+ * MG_MIXED_SIMT = 2 only, else MG_ERR_ARG): the events go through in chunks;
+ * for each chunk one kernel computes every current variant and writes them to
+ * workspace, a second reads them back and computes amplitudes, colour and
+ * helicity sums.  workspace: device, two chunk buffers; chunk = workspace /
+ * (2 x per-event record), so at least 8 records (MG_ERR_SPACE otherwise);
+ * mg_sigmakin_split_workspace_bytes returns the size whose two buffers
+ * together hold at most 96 MiB (they stay in L2).  The launches of one call are
+ * captured into a CUDA graph, instantiated once and replayed while the
+ * arguments, buffers and parameters are unchanged (one cached graph per
+ * library, calls serialised by a mutex). */
+int64_t mg_sigmakin_split_workspace_bytes(int proc, int mode, int64_t nevt);
+int mg_sigmakin_split(int proc, int64_t nevt, const double* mom, const int32_t* mask, int mode, double* me,
+                      void* workspace, int64_t workspace_bytes, void* stream);
+
 /* End-to-end pipeline from HOST buffers (copies inside): h_rnd [nrows][nevt]
  * -> host-to-device copy -> RAMBO -> SIGMAKIN (mask from mg_filter_helicities,
  * on the device) -> device-to-host copy of me (and wgt if h_wgt != NULL) and,

@@ -51,7 +51,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and not is_stale():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
-    srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+    # the largest translation units (the many-leg processes) first, so the
+    # parallel compile ends with the small ones
+    srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")),
+                  key=lambda f: (-max([int(c) for c in os.path.basename(f) if c.isdigit()] or [0]), f))
     extra = ["-Xptxas", "-v"] if os.environ.get("MG_PTXAS_VERBOSE") else []
     extra += os.environ.get("MG_NVCC_DEFINES", "").split()  # e.g. -DMG_HS_NT=256 (tuning)
     cc = nvcc()

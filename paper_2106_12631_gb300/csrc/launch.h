@@ -2,6 +2,7 @@
 // translation units.  Not part of the public header.
 #pragma once
 #include <cstdint>
+#include <functional>
 #include <cuda_runtime.h>
 
 #include "mg_types.cuh"
@@ -45,6 +46,26 @@ cudaError_t launch_event_sum(int64_t n, const double* me, const double* w, doubl
                              cudaStream_t s);
 int64_t event_sum_noalloc_max_events();
 cudaError_t launch_event_sum_noalloc(int64_t n, const double* me, const double* w, double* out3, cudaStream_t s);
+
+// Kernel-split variant (sigmakin_split.cuh): the launches of one batch, chunk
+// by chunk, captured into a CUDA graph and replayed while the key (launch
+// arguments and buffers) is unchanged.
+struct SplitOps {
+  std::function<cudaError_t()> prepare;  // function attributes, before any capture
+  std::function<cudaError_t(int64_t first, int64_t last, void* rec, cudaStream_t)> currents;
+  std::function<cudaError_t(int64_t first, int64_t last, const void* rec, cudaStream_t)> amplitudes;
+};
+cudaError_t run_split_graph(const void* key, size_t key_bytes, int64_t nevt, int64_t chunk, void* buf0, void* buf1,
+                            const SplitOps& ops, cudaStream_t s);
+// per process: record bytes per event (mode 0 FP64, 2 mixed) and the launch
+int64_t split_record_bytes_p1(int mode);
+int64_t split_record_bytes_p2(int mode);
+int64_t split_record_bytes_p3(int mode);
+int64_t split_record_bytes_p4(int mode);
+cudaError_t launch_sigmakin_split_p1(const SigLaunch& a, int mode, void* ws, int64_t ws_bytes, cudaStream_t s);
+cudaError_t launch_sigmakin_split_p2(const SigLaunch& a, int mode, void* ws, int64_t ws_bytes, cudaStream_t s);
+cudaError_t launch_sigmakin_split_p3(const SigLaunch& a, int mode, void* ws, int64_t ws_bytes, cudaStream_t s);
+cudaError_t launch_sigmakin_split_p4(const SigLaunch& a, int mode, void* ws, int64_t ws_bytes, cudaStream_t s);
 
 // mode: 0 FP64, 1 mixed (tensor-core colour sum), 2 mixed (CUDA-core colour sum)
 cudaError_t launch_sigmakin_p1(const SigLaunch& a, int mode, cudaStream_t s);

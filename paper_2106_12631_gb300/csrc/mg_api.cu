@@ -85,6 +85,15 @@ cudaError_t dispatch_sigmakin(int proc, const mg::SigLaunch& l, int mode, cudaSt
   return cudaErrorInvalidValue;
 }
 
+int64_t split_record_bytes(int proc, int mode) {
+  switch (proc) {
+    case 1: return mg::split_record_bytes_p1(mode);
+    case 2: return mg::split_record_bytes_p2(mode);
+    case 3: return mg::split_record_bytes_p3(mode);
+    default: return mg::split_record_bytes_p4(mode);
+  }
+}
+
 int rambo_setup(int proc, double ecm, mg::RamboSetup& st) {
   const ProcDesc& d = kProcs[proc];
   const mg_params p = params_snapshot();
@@ -252,6 +261,36 @@ int mg_matrix_elements_batch(int proc, int64_t nevt, const double* mom_aos, cons
   l.col_rnd = col_out ? col_rnd : nullptr;
   l.col_out = col_out;
   return cuda_status(dispatch_sigmakin(proc, l, mode, s));
+}
+
+int64_t mg_sigmakin_split_workspace_bytes(int proc, int mode, int64_t nevt) {
+  if (!valid_proc(proc) || nevt < 0 || (mode != 0 && mode != 2)) return -1;
+  const int64_t rec = split_record_bytes(proc, mode);
+  // two chunk buffers of together at most 96 MiB (they stay in L2), 4 events at least
+  int64_t chunk = ((int64_t)48 << 20) / rec;
+  chunk -= chunk % 4;
+  if (chunk < 4) chunk = 4;
+  const int64_t need = (nevt + 3) / 4 * 4;
+  return 2 * (need < chunk ? need : chunk) * rec;
+}
+
+int mg_sigmakin_split(int proc, int64_t nevt, const double* mom, const int32_t* mask, int mode, double* me,
+                      void* workspace, int64_t workspace_bytes, void* stream) {
+  if (!valid_proc(proc)) return MG_ERR_PROC;
+  if (nevt < 0 || (mode != 0 && mode != 2)) return MG_ERR_ARG;
+  if (nevt == 0) return MG_OK;
+  if (!mom || !mask || !me || !workspace) return MG_ERR_ARG;
+  if (!aligned(mom) || !aligned(mask) || !aligned(me) || !aligned(workspace)) return MG_ERR_ALIGN;
+  if (workspace_bytes < 8 * split_record_bytes(proc, mode)) return MG_ERR_SPACE;
+  if (nevt > (int64_t)INT32_MAX * 16) return MG_ERR_ARG;
+  mg::SigLaunch l = sig_launch(nevt, mom, mask, me, nullptr);
+  cudaStream_t s = (cudaStream_t)stream;
+  switch (proc) {
+    case 1: return cuda_status(mg::launch_sigmakin_split_p1(l, mode, workspace, workspace_bytes, s));
+    case 2: return cuda_status(mg::launch_sigmakin_split_p2(l, mode, workspace, workspace_bytes, s));
+    case 3: return cuda_status(mg::launch_sigmakin_split_p3(l, mode, workspace, workspace_bytes, s));
+    default: return cuda_status(mg::launch_sigmakin_split_p4(l, mode, workspace, workspace_bytes, s));
+  }
 }
 
 int mg_filter_helicities(int proc, int64_t nevt, const double* mom, int32_t* mask, void* stream) {

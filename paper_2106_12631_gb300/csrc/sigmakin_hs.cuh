@@ -509,10 +509,28 @@ __device__ __forceinline__ void hs_choices(const unsigned char* smem, const SigA
   }
 }
 
-template <class P, class R, int CS>
-__global__ void __launch_bounds__(HsCfg<P, R>::NT, HsCfg<P, R>::CTAS) sigmakin_hs_kernel(SigArgs a, Couplings<R> cp) {
+// Record of one event's current variants and momentum table in global memory
+// (the kernel-split variant: the first kernel writes them, the second reads
+// them back into shared memory): HS_NSLOT slots of 16-byte planes, then the
+// momentum table K[NMOM][4] in the working precision.
+template <class P, class R>
+struct HsRecord {
+  static constexpr int CUR = P::HS_NSLOT * Slots<R, 1>::NPL;
+  static_assert((P::NMOM * 4 * sizeof(R)) % 16 == 0, "momentum table in 16-byte words");
+  static constexpr int KW = (int)(P::NMOM * 4 * sizeof(R) / 16);
+  static constexpr int WORDS = CUR + KW;
+};
+
+// The helicity-shared program for the events [first, last) of the batch.
+// FROM_RECORDS: phases 1-2 (momenta, tables, current variants) are replaced
+// by a copy of the events' records from `rec` (one record per event, event
+// first - first at rec[0]).
+template <class P, class R, int CS, bool FROM_RECORDS>
+__device__ __forceinline__ void hs_sigmakin_body(const SigArgs& a, const Couplings<R>& cp, int64_t first, int64_t last,
+                                                 const uint4* __restrict__ rec) {
   using C = HsCfg<P, R>;
   using L = HsLayout<P, R, CS>;
+  static_assert(!(FROM_RECORDS && L::TC), "the kernel-split variant sums colours on CUDA cores");
   constexpr int NT = C::NT, NC = P::NCOLOR;
   extern __shared__ __align__(1024) unsigned char smem[];
   int* good = reinterpret_cast<int*>(smem + L::o_good);
@@ -553,9 +571,9 @@ __global__ void __launch_bounds__(HsCfg<P, R>::NT, HsCfg<P, R>::CTAS) sigmakin_h
   if (hgood) good[__popc(hb & ((1u << (tid & 31)) - 1u)) + (tid >= 32 ? __popc(w0) : 0)] = tid;
   const int ng = __popc(w0) + __popc(w1);
   const int ev = ng > 0 ? min(L::EVCAP, NT / ng) : C::EVMIN;
-  const int64_t e0 = (int64_t)blockIdx.x * ev;
-  if (e0 >= a.nevt) return;
-  const int nev = (int)min((int64_t)ev, a.nevt - e0);
+  const int64_t e0 = first + (int64_t)blockIdx.x * ev;
+  if (e0 >= last) return;
+  const int nev = (int)min((int64_t)ev, last - e0);
   if (ng == 0) {
     if (tid < nev) {
       a.me[e0 + tid] = 0.0;
@@ -575,27 +593,41 @@ __global__ void __launch_bounds__(HsCfg<P, R>::NT, HsCfg<P, R>::CTAS) sigmakin_h
     tc::fence_async_shared();
     tc::fence_before_sync();
   }
-  // 1. momenta and per-event tables
-  hs_event_tables<P, R, L>(smem, a, e0, nev, curs, cp);
-  if constexpr (L::TC) {
-    tc::fence_after_sync();
-    tmem = static_cast<uint32_t>(misc[1]);
-  }
   const R* Kall = reinterpret_cast<const R*>(smem + L::o_K);
-  const cx<R>* prall = reinterpret_cast<const cx<R>*>(smem + L::o_pr);
-  // 2. current variants, level by level (level 0, the external wavefunctions,
-  //    came with phase 1); consecutive threads take consecutive items of one event
   const HsItem* items = P::hs_items();
-#pragma unroll
-  for (int l = 1; l < P::HS_NLEVEL; ++l) {
-    const int i0 = P::hs_level(l), ni = P::hs_level(l + 1) - i0, n = ni * nev;
-    for (int t = tid; t < n; t += NT) {
-      const int e = t / ni;
-      const HsItem it = items[i0 + t - e * ni];
-      hs_item<P, R>(it, Slots<R, P::HS_NSLOT>{curs + e * CUR_EV}, Kall + e * P::NMOM * 4, prall + e * P::NPROP,
-                    cp);
+  if constexpr (FROM_RECORDS) {
+    // 1-2. the events' current variants and momentum tables from their records
+    using RC = HsRecord<P, R>;
+    const uint4* in = rec + (e0 - first) * RC::WORDS;
+    uint4* ks = reinterpret_cast<uint4*>(smem + L::o_K);
+    for (int t = tid; t < nev * RC::WORDS; t += NT) {
+      const int e = t / RC::WORDS, w = t - e * RC::WORDS;
+      const uint4 v = __ldcs(in + t);  // read once: streaming
+      if (w < RC::CUR) curs[e * CUR_EV + w] = v;
+      else ks[e * RC::KW + (w - RC::CUR)] = v;
     }
     __syncthreads();
+  } else {
+    // 1. momenta and per-event tables
+    hs_event_tables<P, R, L>(smem, a, e0, nev, curs, cp);
+    if constexpr (L::TC) {
+      tc::fence_after_sync();
+      tmem = static_cast<uint32_t>(misc[1]);
+    }
+    const cx<R>* prall = reinterpret_cast<const cx<R>*>(smem + L::o_pr);
+    // 2. current variants, level by level (level 0, the external wavefunctions,
+    //    came with phase 1); consecutive threads take consecutive items of one event
+#pragma unroll
+    for (int l = 1; l < P::HS_NLEVEL; ++l) {
+      const int i0 = P::hs_level(l), ni = P::hs_level(l + 1) - i0, n = ni * nev;
+      for (int t = tid; t < n; t += NT) {
+        const int e = t / ni;
+        const HsItem it = items[i0 + t - e * ni];
+        hs_item<P, R>(it, Slots<R, P::HS_NSLOT>{curs + e * CUR_EV}, Kall + e * P::NMOM * 4, prall + e * P::NPROP,
+                      cp);
+      }
+      __syncthreads();
+    }
   }
   // 3. amputated currents chunk by chunk into two alternating buffers: in
   //    interval c every thread first builds its share of chunk c, then
@@ -659,6 +691,11 @@ __global__ void __launch_bounds__(HsCfg<P, R>::NT, HsCfg<P, R>::CTAS) sigmakin_h
     }
     hs_choices<P, R, L>(smem, a, e0, nev, ng, good, sm2);
   }
+}
+
+template <class P, class R, int CS>
+__global__ void __launch_bounds__(HsCfg<P, R>::NT, HsCfg<P, R>::CTAS) sigmakin_hs_kernel(SigArgs a, Couplings<R> cp) {
+  hs_sigmakin_body<P, R, CS, false>(a, cp, 0, a.nevt, nullptr);
 }
 
 }  // namespace mg

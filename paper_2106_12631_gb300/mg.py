@@ -69,6 +69,9 @@ def lib():
             L.mg_unweight_scratch_bytes.argtypes = [i64]
             L.mg_unweight_scratch_bytes.restype = i64
             L.mg_unweight.argtypes = [i64, vp, vp, u64, i64, vp, vp, vp, i64, vp]
+            L.mg_sigmakin_split_workspace_bytes.argtypes = [i32, i32, i64]
+            L.mg_sigmakin_split_workspace_bytes.restype = i64
+            L.mg_sigmakin_split.argtypes = [i32, i64, vp, vp, i32, vp, vp, i64, vp]
             L.mg_batch_workspace_bytes.argtypes = [i32, i64]
             L.mg_batch_workspace_bytes.restype = i64
             L.mg_matrix_elements_batch.argtypes = [i32, i64, vp, vp, i32, vp, vp, vp, vp, vp, vp, i64, vp]
@@ -224,6 +227,29 @@ def matrix_elements_batch(proc, mom_aos: torch.Tensor, mask: torch.Tensor, mode=
     if hel_rnd is None and col_rnd is None:
         return me
     return me, hel, col
+
+
+def sigmakin_split_workspace_bytes(proc, mode, nevt: int) -> int:
+    m = MODES[mode] if isinstance(mode, str) else int(mode)
+    return int(lib().mg_sigmakin_split_workspace_bytes(_proc(proc), m, nevt))
+
+
+def sigmakin_split(proc, mom: torch.Tensor, mask: torch.Tensor, mode="mixed_simt", me=None, workspace=None,
+                   stream=None) -> torch.Tensor:
+    """The kernel-split variant of sigmakin (currents, then amplitudes, per chunk, in a CUDA graph)."""
+    p = _proc(proc)
+    nevt = mom.shape[2]
+    if me is None:
+        me = torch.empty((nevt,), dtype=torch.float64, device=mom.device)
+    m = MODES[mode] if isinstance(mode, str) else int(mode)
+    if workspace is None:
+        nb = max(sigmakin_split_workspace_bytes(p, m, nevt), 16)
+        workspace = torch.empty(((nb + 7) // 8,), dtype=torch.float64, device=mom.device)
+    _check(lib().mg_sigmakin_split(p, nevt, _dev(mom, torch.float64, "mom"), _dev(mask, torch.int32, "mask"), m,
+                                   _dev(me, torch.float64, "me", (nevt,)), workspace.data_ptr(),
+                                   workspace.numel() * workspace.element_size(), _stream(stream)),
+           "mg_sigmakin_split")
+    return me
 
 
 def filter_helicities(proc, mom: torch.Tensor, mask=None, stream=None) -> torch.Tensor:
