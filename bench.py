@@ -41,7 +41,7 @@ SM_MAX_MHZ = 2070.0
 # (dram__bytes_read.sum + dram__bytes_write.sum of one launch over 2^18 events,
 # scaled by events; it reads the momenta once and writes |M|^2), valid only
 # while the kernel sources are the ones captured.
-SIGMAKIN_TRAFFIC = {"bytes_per_event": 192.81, "sources_sha1": "469fe696f946d64aced4490028e5c95d484e42d5"}
+SIGMAKIN_TRAFFIC = {"bytes_per_event": 192.81, "sources_sha1": "8746b9e21ec371255594df98cac6b98b6a7cedaa"}
 SIGMAKIN_SOURCES = ["paper_2106_12631_gb300/csrc/" + f for f in
                     ("sigmakin_hs.cuh", "sigmakin.cuh", "helas.cuh", "colour_tc.cuh", "mg_types.cuh",
                      "process.cuh", "gen/proc4.cuh")]
@@ -203,6 +203,18 @@ def measure_other_workloads(mg, I, dev, stream, reps: int = 3) -> dict:
             for mode in ("mixed", "fp64"):
                 t = time_it(lambda: mg.sigmakin(proc, mom, mask, mode=mode, me=me, stream=stream))
                 res[mode] = {"value": nevt / t, "unit": UNIT, "sigmakin_ms": 1e3 * t}
+        if name == "ee_mumu":
+            # the paper's own e+e- -> mu+mu- point: 2^19 events per launch, past the
+            # plateau in events in flight (16384 events leave the GPU mostly idle)
+            big = 1 << 19
+            rnd_b = torch.from_numpy(I.uniforms(I.seed_of(name), nr, big)).to(dev)
+            mom_b, _ = mg.rambo(proc, rnd_b, ecm)
+            me_b = torch.empty(big, dtype=torch.float64, device=dev)
+            res["events_2^19"] = {}
+            for mode in ("mixed", "fp64"):
+                t = time_it(lambda: mg.sigmakin(proc, mom_b, mask, mode=mode, me=me_b, stream=stream))
+                res["events_2^19"][mode] = {"value": big / t, "unit": UNIT, "sigmakin_ms": 1e3 * t}
+            del rnd_b, mom_b, me_b
         out[name] = res
     return out
 
@@ -266,6 +278,21 @@ def measure_generation(mg, proc, ecm, nevt, seed, mom, wgt, me, sums, stream, hb
                 "unweight": {"bound": "hbm", "achieved": uw_bytes / t_uw / 1e9, "peak": hbm_gbs, "unit": "GB/s",
                              "frac": (uw_bytes / t_uw / 1e9) / hbm_gbs if hbm_gbs else None,
                              "ms": 1e3 * t_uw, "bytes_per_event": 48}}}
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (/proc/cpuinfo; Arm hosts name the part by its ids)."""
+    import platform
+    try:
+        with open("/proc/cpuinfo") as f:
+            info = f.read()
+    except OSError:
+        return platform.machine()
+    for key in ("model name", "Hardware", "CPU part"):
+        for ln in info.splitlines():
+            if ln.startswith(key):
+                return "%s %s: %s" % (platform.machine(), key, ln.split(":", 1)[1].strip())
+    return platform.machine()
 
 
 def cpu_oracle_rate(nevt_sample: int, seed: int, threads: int):
@@ -544,9 +571,13 @@ def main():
     if rank == 0 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
         rate, dt = cpu_oracle_rate(8192, seed, cores)
+        rate1, dt1 = cpu_oracle_rate(512, seed, 1)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": "8192 gg->ttgg events (RAMBO + |M|^2 over all 64 helicities, "
-                                          "explicit colour), FP64, %.1f s wall" % dt}
+                                          "explicit colour), FP64, %.1f s wall" % dt,
+                                "single_thread": {"value": rate1, "unit": UNIT,
+                                                  "sample": "512 events, %.1f s wall" % dt1},
+                                "cpu": cpu_model()}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
