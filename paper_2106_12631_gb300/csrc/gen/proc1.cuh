@@ -49,12 +49,12 @@ struct Proc1 {
       case 0: {
         {
           const W4<R> X = xb[0 + vt[192]];
-          { const cx<R> a = dot4(X, cur[8 + vt[48]]); J[0] += a; }
+          dot4_acc<0>(J[0], X, cur[8 + vt[48]]);
         }
         HS_LOCKSTEP(0, 1);
         {
           const W4<R> X = xb[4 + vt[192]];
-          { const cx<R> a = dot4(X, cur[12 + vt[48]]); J[0] += a; }
+          dot4_acc<0>(J[0], X, cur[12 + vt[48]]);
         }
       } break;
       default: break;

@@ -49,12 +49,12 @@ struct Proc2 {
       case 0: {
         {
           const W4<R> X = xb[0 + vt[144]];
-          { const cx<R> a = dot4(X, cur[16 + vt[96]]); J[1] += a; }
+          dot4_acc<0>(J[1], X, cur[16 + vt[96]]);
         }
         HS_LOCKSTEP(0, 1);
         {
           const W4<R> X = xb[4 + vt[160]];
-          { const cx<R> a = dot4(X, cur[12 + vt[80]]); J[0] += a; }
+          dot4_acc<0>(J[0], X, cur[12 + vt[80]]);
         }
         HS_LOCKSTEP(1, 2);
         {

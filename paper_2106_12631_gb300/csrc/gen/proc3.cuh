@@ -49,12 +49,12 @@ struct Proc3 {
       case 0: {
         {
           const W4<R> X = xb[0 + vt[352]];
-          { const cx<R> a = dot4(X, cur[66 + vt[640]]); J[4] += a; }
+          dot4_acc<0>(J[4], X, cur[66 + vt[640]]);
         }
         HS_LOCKSTEP(0, 1);
         {
           const W4<R> X = xb[8 + vt[352]];
-          { const cx<R> a = dot4(X, cur[66 + vt[640]]); J[5] += a; }
+          dot4_acc<0>(J[5], X, cur[66 + vt[640]]);
         }
         HS_LOCKSTEP(1, 2);
         {
@@ -64,7 +64,7 @@ struct Proc3 {
         HS_LOCKSTEP(2, 3);
         {
           const W4<R> X = xb[24 + vt[800]];
-          { const cx<R> a = dot4(X, cur[62 + vt[192]]); J[2] += a; }
+          dot4_acc<0>(J[2], X, cur[62 + vt[192]]);
         }
         HS_LOCKSTEP(3, 4);
         {
@@ -74,17 +74,17 @@ struct Proc3 {
         HS_LOCKSTEP(4, 5);
         {
           const W4<R> X = xb[40 + vt[800]];
-          { const cx<R> a = dot4(X, cur[62 + vt[192]]); J[3] += a; }
+          dot4_acc<0>(J[3], X, cur[62 + vt[192]]);
         }
         HS_LOCKSTEP(5, 6);
         {
           const W4<R> X = xb[48 + vt[832]];
-          { const cx<R> a = dot4(X, cur[58 + vt[160]]); J[0] += a; }
+          dot4_acc<0>(J[0], X, cur[58 + vt[160]]);
         }
         HS_LOCKSTEP(6, 7);
         {
           const W4<R> X = xb[56 + vt[832]];
-          { const cx<R> a = dot4(X, cur[58 + vt[160]]); J[1] += a; }
+          dot4_acc<0>(J[1], X, cur[58 + vt[160]]);
         }
         HS_LOCKSTEP(7, 8);
         {

@@ -110,10 +110,10 @@ __device__ __forceinline__ W4<R> row_slash(const W4<R>& f, const W4<R>& V) {
   const cx<R> vp = V.w[0] + V.w[3], vm = V.w[0] - V.w[3];
   const cx<R> vxpy = V.w[1] + mul_i(V.w[2]), vxmy = V.w[1] - mul_i(V.w[2]);
   W4<R> o;
-  o.w[0] = f.w[2] * vp + f.w[3] * vxpy;
-  o.w[1] = f.w[2] * vxmy + f.w[3] * vm;
-  o.w[2] = f.w[0] * vm - f.w[1] * vxpy;
-  o.w[3] = f.w[1] * vp - f.w[0] * vxmy;
+  o.w[0] = cfma(f.w[3], vxpy, f.w[2] * vp);
+  o.w[1] = cfma(f.w[3], vm, f.w[2] * vxmy);
+  o.w[2] = cfma(-f.w[1], vxpy, f.w[0] * vm);
+  o.w[3] = cfma(-f.w[0], vxmy, f.w[1] * vp);
   return o;
 }
 // V/ . col
@@ -122,10 +122,10 @@ __device__ __forceinline__ W4<R> slash_col(const W4<R>& V, const W4<R>& f) {
   const cx<R> vp = V.w[0] + V.w[3], vm = V.w[0] - V.w[3];
   const cx<R> vxpy = V.w[1] + mul_i(V.w[2]), vxmy = V.w[1] - mul_i(V.w[2]);
   W4<R> o;
-  o.w[0] = vm * f.w[2] - vxmy * f.w[3];
-  o.w[1] = vp * f.w[3] - vxpy * f.w[2];
-  o.w[2] = vp * f.w[0] + vxmy * f.w[1];
-  o.w[3] = vxpy * f.w[0] + vm * f.w[1];
+  o.w[0] = cfma(-vxmy, f.w[3], vm * f.w[2]);
+  o.w[1] = cfma(-vxpy, f.w[2], vp * f.w[3]);
+  o.w[2] = cfma(vxmy, f.w[1], vp * f.w[0]);
+  o.w[3] = cfma(vm, f.w[1], vxpy * f.w[0]);
   return o;
 }
 // row . (K/ + m)  for a real momentum K
@@ -134,10 +134,10 @@ __device__ __forceinline__ W4<R> row_kslash_m(const W4<R>& f, const R* K, R m) {
   const R kp = K[0] + K[3], km = K[0] - K[3];
   const cx<R> kxpy(K[1], K[2]), kxmy(K[1], -K[2]);
   W4<R> o;
-  o.w[0] = kp * f.w[2] + f.w[3] * kxpy + m * f.w[0];
-  o.w[1] = f.w[2] * kxmy + km * f.w[3] + m * f.w[1];
-  o.w[2] = km * f.w[0] - f.w[1] * kxpy + m * f.w[2];
-  o.w[3] = kp * f.w[1] - f.w[0] * kxmy + m * f.w[3];
+  o.w[0] = rfma(m, f.w[0], cfma(f.w[3], kxpy, kp * f.w[2]));
+  o.w[1] = rfma(m, f.w[1], cfma(f.w[2], kxmy, km * f.w[3]));
+  o.w[2] = rfma(m, f.w[2], cfma(-f.w[1], kxpy, km * f.w[0]));
+  o.w[3] = rfma(m, f.w[3], cfma(-f.w[0], kxmy, kp * f.w[1]));
   return o;
 }
 // (-K/ + m) . col
@@ -146,24 +146,24 @@ __device__ __forceinline__ W4<R> mkslash_m_col(const R* K, R m, const W4<R>& f) 
   const R kp = K[0] + K[3], km = K[0] - K[3];
   const cx<R> kxpy(K[1], K[2]), kxmy(K[1], -K[2]);
   W4<R> o;
-  o.w[0] = m * f.w[0] - (km * f.w[2] - kxmy * f.w[3]);
-  o.w[1] = m * f.w[1] - (kp * f.w[3] - kxpy * f.w[2]);
-  o.w[2] = m * f.w[2] - (kp * f.w[0] + kxmy * f.w[1]);
-  o.w[3] = m * f.w[3] - (kxpy * f.w[0] + km * f.w[1]);
+  o.w[0] = rfma(m, f.w[0], cfma(kxmy, f.w[3], -km * f.w[2]));
+  o.w[1] = rfma(m, f.w[1], cfma(kxpy, f.w[2], -kp * f.w[3]));
+  o.w[2] = rfma(m, f.w[2], cfma(-kxmy, f.w[1], -kp * f.w[0]));
+  o.w[3] = rfma(m, f.w[3], cfma(-kxpy, f.w[0], -km * f.w[1]));
   return o;
 }
 template <class R>
 __device__ __forceinline__ cx<R> row_col(const W4<R>& a, const W4<R>& b) {
-  return a.w[0] * b.w[0] + a.w[1] * b.w[1] + a.w[2] * b.w[2] + a.w[3] * b.w[3];
+  return cfma(a.w[3], b.w[3], cfma(a.w[2], b.w[2], cfma(a.w[1], b.w[1], a.w[0] * b.w[0])));
 }
 // Minkowski product of two complex vectors (no conjugation)
 template <class R>
 __device__ __forceinline__ cx<R> vdot(const W4<R>& a, const W4<R>& b) {
-  return a.w[0] * b.w[0] - a.w[1] * b.w[1] - a.w[2] * b.w[2] - a.w[3] * b.w[3];
+  return cfma(-a.w[3], b.w[3], cfma(-a.w[2], b.w[2], cfma(-a.w[1], b.w[1], a.w[0] * b.w[0])));
 }
 template <class R>
 __device__ __forceinline__ cx<R> kdot(const R* k, const W4<R>& a) {
-  return k[0] * a.w[0] - k[1] * a.w[1] - k[2] * a.w[2] - k[3] * a.w[3];
+  return rfma(-k[3], a.w[3], rfma(-k[2], a.w[2], rfma(-k[1], a.w[1], k[0] * a.w[0])));
 }
 template <class R>
 __device__ __forceinline__ W4<R> scale(const W4<R>& a, cx<R> s) {
@@ -268,7 +268,7 @@ __device__ __forceinline__ W4<R> VVV1P0_1(const W4<R>& a1, const W4<R>& a2, cons
   const cx<R> s = g * prop;
   W4<R> o;
 #pragma unroll
-  for (int mu = 0; mu < 4; ++mu) o.w[mu] = (d12[mu] * a12 + a2.w[mu] * c1 + a1.w[mu] * c2) * s;
+  for (int mu = 0; mu < 4; ++mu) o.w[mu] = cfma(a1.w[mu], c2, cfma(a2.w[mu], c1, d12[mu] * a12)) * s;
   return o;
 }
 // four-gluon vertex, the three colour-stripped Lorentz terms (legs A1, A2, A3, new):
@@ -280,7 +280,7 @@ template <class R>
 __device__ __forceinline__ W4<R> vvvv_comb(const W4<R>& x, cx<R> cx_, const W4<R>& y, cx<R> cy, cx<R> s) {
   W4<R> o;
 #pragma unroll
-  for (int mu = 0; mu < 4; ++mu) o.w[mu] = (cx_ * x.w[mu] - cy * y.w[mu]) * s;
+  for (int mu = 0; mu < 4; ++mu) o.w[mu] = cfma(-cy, y.w[mu], cx_ * x.w[mu]) * s;
   return o;
 }
 template <class R>
@@ -353,7 +353,7 @@ __device__ __forceinline__ W4<R> VVV1P0_1A(const W4<R>& a1, const W4<R>& a2, con
   W4<R> o;
 #pragma unroll
   for (int mu = 0; mu < 4; ++mu) {
-    const cx<R> n = d12[mu] * a12 + a2.w[mu] * c1 + a1.w[mu] * c2;
+    const cx<R> n = cfma(a1.w[mu], c2, cfma(a2.w[mu], c1, d12[mu] * a12));
     o.w[mu] = (mu == 0 ? g : -g) * n;
   }
   return o;
@@ -364,7 +364,7 @@ __device__ __forceinline__ W4<R> vvvv_comb_a(const W4<R>& x, cx<R> cx_, const W4
   W4<R> o;
 #pragma unroll
   for (int mu = 0; mu < 4; ++mu) {
-    const cx<R> t = cx_ * x.w[mu] - cy * y.w[mu];
+    const cx<R> t = cfma(-cy, y.w[mu], cx_ * x.w[mu]);
     o.w[mu] = mu == 0 ? mul_mi(g2 * t) : mul_i(g2 * t);
   }
   return o;
@@ -398,10 +398,43 @@ __device__ __forceinline__ W4<R> w4_subi(const W4<R>& s, const W4<R>& y) {
   for (int k = 0; k < 4; ++k) o.w[k] = s.w[k] - mul_i(y.w[k]);
   return o;
 }
-// contraction of an amputated current with the left-out operand
+// contraction of an amputated current with the left-out operand, the real and
+// imaginary parts each one chain of fused multiply-adds (16 operations)
 template <class R>
 __device__ __forceinline__ cx<R> dot4(const W4<R>& x, const W4<R>& y) {
-  return x.w[0] * y.w[0] + x.w[1] * y.w[1] + x.w[2] * y.w[2] + x.w[3] * y.w[3];
+  R re = x.w[0].re * y.w[0].re, im = x.w[0].re * y.w[0].im;
+  re = fmac(-x.w[0].im, y.w[0].im, re);
+  im = fmac(x.w[0].im, y.w[0].re, im);
+#pragma unroll
+  for (int k = 1; k < 4; ++k) {
+    re = fmac(x.w[k].re, y.w[k].re, re);
+    re = fmac(-x.w[k].im, y.w[k].im, re);
+    im = fmac(x.w[k].re, y.w[k].im, im);
+    im = fmac(x.w[k].im, y.w[k].re, im);
+  }
+  return cx<R>(re, im);
+}
+
+// J += i^PH sum_i X_i Y_i straight into one colour flow (PH 0: +1, 1: -1,
+// 2: +i, 3: -i): the chains start from the flow's value, no separate add
+template <int PH, class R>
+__device__ __forceinline__ void dot4_acc(cx<R>& J, const W4<R>& x, const W4<R>& y) {
+  R tr, ti;  // the flow's parts that Re(XY) and Im(XY) add to, signed so both are +
+  if constexpr (PH == 0) { tr = J.re; ti = J.im; }
+  else if constexpr (PH == 1) { tr = -J.re; ti = -J.im; }
+  else if constexpr (PH == 2) { tr = J.im; ti = -J.re; }   // J += i a: J.im += Re a, J.re -= Im a
+  else { tr = -J.im; ti = J.re; }                          // J -= i a: J.im -= Re a, J.re += Im a
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    tr = fmac(x.w[k].re, y.w[k].re, tr);
+    tr = fmac(-x.w[k].im, y.w[k].im, tr);
+    ti = fmac(x.w[k].re, y.w[k].im, ti);
+    ti = fmac(x.w[k].im, y.w[k].re, ti);
+  }
+  if constexpr (PH == 0) { J.re = tr; J.im = ti; }
+  else if constexpr (PH == 1) { J.re = -tr; J.im = -ti; }
+  else if constexpr (PH == 2) { J.im = tr; J.re = -ti; }
+  else { J.im = -tr; J.re = ti; }
 }
 
 }  // namespace mg

@@ -26,6 +26,19 @@ template <class R> __device__ __forceinline__ cx<R>& operator-=(cx<R>& a, cx<R> 
 template <class R> __device__ __forceinline__ cx<R> conj(cx<R> a) { return cx<R>(a.re, -a.im); }
 template <class R> __device__ __forceinline__ cx<R> mul_i(cx<R> a) { return cx<R>(-a.im, a.re); }   // i * a
 template <class R> __device__ __forceinline__ cx<R> mul_mi(cx<R> a) { return cx<R>(a.im, -a.re); }  // -i * a
+// fused multiply-add in the working precision (one rounding)
+template <class R> __device__ __forceinline__ R fmac(R a, R b, R c) {
+  if constexpr (sizeof(R) == 4) return __fmaf_rn(a, b, c);
+  else return __fma_rn(a, b, c);
+}
+// a b + c and s a + c as chains of fused multiply-adds (four and two
+// operations; a product followed by a separate sum takes six and four)
+template <class R> __device__ __forceinline__ cx<R> cfma(cx<R> a, cx<R> b, cx<R> c) {
+  return cx<R>(fmac(a.re, b.re, fmac(-a.im, b.im, c.re)), fmac(a.re, b.im, fmac(a.im, b.re, c.im)));
+}
+template <class R> __device__ __forceinline__ cx<R> rfma(R s, cx<R> a, cx<R> c) {
+  return cx<R>(fmac(s, a.re, c.re), fmac(s, a.im, c.im));
+}
 
 // Four complex components: a Dirac spinor (chiral basis, upper pair
 // left-handed; a row spinor for flowing-out fermions, a column spinor for

@@ -206,7 +206,7 @@ __device__ __forceinline__ R colour_sum_sym(const cx<R>* J) {
       ur += R(2 * P::cnum(i, j)) * J[j].re;
       ui += R(2 * P::cnum(i, j)) * J[j].im;
     }
-    sum += J[i].re * ur + J[i].im * ui;
+    sum = fmac(J[i].re, ur, fmac(J[i].im, ui, sum));
   }
   return sum / R(P::CDEN);
 }

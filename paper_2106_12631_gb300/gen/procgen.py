@@ -1482,7 +1482,8 @@ class SharedProgram:
         """Contractions of one chunk for one (event, helicity), straight-line: every
         operand offset and variant-table entry is a constant, so the loads of
         successive amplitudes are independent; each (merged) amplitude goes
-        straight into its colour flows J_s (+amp, -amp, +i amp, -i amp)."""
+        straight into its colour flows J_s (+amp, -amp, +i amp, -i amp); the
+        contraction of an amplitude with a single flow accumulates into it."""
         nh = 1 << self.n
         ALL = (1 << self.n) - 1
         ops = {0: "J[%d] += a;", 1: "J[%d] -= a;", 2: "J[%d] += mul_i(a);", 3: "J[%d] -= mul_i(a);"}
@@ -1516,15 +1517,26 @@ class SharedProgram:
                     last_x = g["xo"]
                 yv = (ALL ^ g["xset"]) * nh
                 flows = " ".join(ops[f >> 6] % (f & 63) for f in g["flows"])
+                one = len(g["flows"]) == 1  # a single flow: the contraction accumulates into it
+                if one:
+                    f = g["flows"][0]
+                    into = "dot4_acc<%d>(J[%d], X, %%s);" % (f >> 6, f & 63)
                 if len(g["ys"]) == 1:
-                    lines.append("          { const cx<R> a = dot4(X, cur[%d + vt[%d]]); %s }" % (g["ys"][0][0], yv, flows))
+                    y = "cur[%d + vt[%d]]" % (g["ys"][0][0], yv)
+                    if one:
+                        lines.append("          " + into % y)
+                    else:
+                        lines.append("          { const cx<R> a = dot4(X, %s); %s }" % (y, flows))
                 else:
                     y0 = g["ys"][0][0]
                     lines.append("          {")
                     lines.append("            W4<R> Y = cur[%d + vt[%d]];" % (y0, yv))
                     for (yo, r) in g["ys"][1:]:
                         lines.append("            Y = %s(Y, cur[%d + vt[%d]]);" % (acc[r], yo, yv))
-                    lines.append("            const cx<R> a = dot4(X, Y); %s" % flows)
+                    if one:
+                        lines.append("            " + into % "Y")
+                    else:
+                        lines.append("            const cx<R> a = dot4(X, Y); %s" % flows)
                     lines.append("          }")
             if last_x is not None:
                 lines.append("        }")
