@@ -196,6 +196,24 @@ template <class P, class R>
 __device__ __forceinline__ R colour_sum_sym(const cx<R>* J) {
   static_assert(colour_matrix_symmetric<P>(), "colour matrix must be symmetric");
   constexpr int NC = P::NCOLOR;
+  if constexpr (sizeof(R) == 4) {
+    // FP32: the real and imaginary parts side by side in the paired FP32
+    // instructions (one FFMA2 per matrix entry instead of two FFMAs)
+    float2 tot = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int i = 0; i < NC; ++i) {
+      const float cii = (float)P::cnum(i, i);
+      float2 u = __fmul2_rn(make_float2(cii, cii), make_float2(J[i].re, J[i].im));
+#pragma unroll
+      for (int j = i + 1; j < NC; ++j) {
+        if (P::cnum(i, j) == 0) continue;
+        const float c = (float)(2 * P::cnum(i, j));
+        u = __ffma2_rn(make_float2(c, c), make_float2(J[j].re, J[j].im), u);
+      }
+      tot = __ffma2_rn(make_float2(J[i].re, J[i].im), u, tot);
+    }
+    return (tot.x + tot.y) / R(P::CDEN);
+  }
   R sum = R(0);
 #pragma unroll
   for (int i = 0; i < NC; ++i) {
