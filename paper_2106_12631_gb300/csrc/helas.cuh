@@ -400,8 +400,31 @@ __device__ __forceinline__ W4<R> w4_subi(const W4<R>& s, const W4<R>& y) {
 }
 // contraction of an amputated current with the left-out operand, the real and
 // imaginary parts each one chain of fused multiply-adds (16 operations)
+#ifndef MG_DOT4_PAIRS
+// FP32 contractions in paired FP32 instructions: bit 0 those accumulated
+// straight into one colour flow, bit 1 the others (their extra registers made
+// the gg -> t t~ g g kernel spill)
+#define MG_DOT4_PAIRS 1
+#endif
+// FP32 form: P = sum (xr yr, xi yi) and Q = sum (xi yr, xr yi) side by side in
+// the paired FP32 instructions (8 FFMA2), Re = P.x - P.y, Im = Q.x + Q.y; the
+// initial pairs carry a value the result is added to
+__device__ __forceinline__ void dot4_pairs(const W4<float>& x, const W4<float>& y, float2& p, float2& q) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float2 yk = make_float2(y.w[k].re, y.w[k].im);
+    p = __ffma2_rn(make_float2(x.w[k].re, x.w[k].im), yk, p);
+    q = __ffma2_rn(make_float2(x.w[k].im, x.w[k].re), yk, q);
+  }
+}
+
 template <class R>
 __device__ __forceinline__ cx<R> dot4(const W4<R>& x, const W4<R>& y) {
+  if constexpr (sizeof(R) == 4 && (MG_DOT4_PAIRS & 2)) {
+    float2 p = make_float2(0.0f, 0.0f), q = make_float2(0.0f, 0.0f);
+    dot4_pairs(x, y, p, q);
+    return cx<R>(p.x - p.y, q.x + q.y);
+  }
   R re = x.w[0].re * y.w[0].re, im = x.w[0].re * y.w[0].im;
   re = fmac(-x.w[0].im, y.w[0].im, re);
   im = fmac(x.w[0].im, y.w[0].re, im);
@@ -419,6 +442,20 @@ __device__ __forceinline__ cx<R> dot4(const W4<R>& x, const W4<R>& y) {
 // 2: +i, 3: -i): the chains start from the flow's value, no separate add
 template <int PH, class R>
 __device__ __forceinline__ void dot4_acc(cx<R>& J, const W4<R>& x, const W4<R>& y) {
+  if constexpr (sizeof(R) == 4 && (MG_DOT4_PAIRS & 1)) {
+    // Re(XY) = P.x - P.y, Im(XY) = Q.x + Q.y, each started from the flow's part
+    float2 p, q;
+    if constexpr (PH == 0) { p = make_float2(J.re, 0.0f); q = make_float2(J.im, 0.0f); }
+    else if constexpr (PH == 1) { p = make_float2(0.0f, J.re); q = make_float2(-J.im, 0.0f); }
+    else if constexpr (PH == 2) { p = make_float2(J.im, 0.0f); q = make_float2(-J.re, 0.0f); }
+    else { p = make_float2(0.0f, J.im); q = make_float2(J.re, 0.0f); }
+    dot4_pairs(x, y, p, q);
+    if constexpr (PH == 0) { J.re = p.x - p.y; J.im = q.x + q.y; }
+    else if constexpr (PH == 1) { J.re = p.y - p.x; J.im = -(q.x + q.y); }
+    else if constexpr (PH == 2) { J.im = p.x - p.y; J.re = -(q.x + q.y); }
+    else { J.im = p.y - p.x; J.re = q.x + q.y; }
+    return;
+  }
   R tr, ti;  // the flow's parts that Re(XY) and Im(XY) add to, signed so both are +
   if constexpr (PH == 0) { tr = J.re; ti = J.im; }
   else if constexpr (PH == 1) { tr = -J.re; ti = -J.im; }
