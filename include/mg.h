@@ -49,7 +49,7 @@ typedef enum {
   MG_ERR_SPACE = -6    /* workspace or scratch smaller than required */
 } mg_status;
 
-/* Precision modes of mg_sigmakin (the paper's precision switch, Sec. 5,
+/* Precision modes of mg_sigmakin (the paper's build-time precision switch, Sec. 4,
  * extended to a mixed mode). */
 typedef enum {
   MG_FP64 = 0,        /* everything in FP64 */
@@ -199,7 +199,7 @@ int64_t mg_unweight_scratch_bytes(int64_t nevt);
 int mg_unweight(int64_t nevt, const double* me, const double* wgt, uint64_t seed, int64_t first_event,
                 int64_t* idx, int64_t* count, void* scratch, int64_t scratch_bytes, void* stream);
 
-/* Batched matrix elements for an external integrator (Sec. 6: the MadEvent
+/* Batched matrix elements for an external integrator (Sec. 5: the MadEvent
  * bridge, where an existing event generator hands over a set of phase-space
  * points it prepared and receives their matrix elements, its 4-momenta passed
  * in its own layout): momenta as an array of structures
@@ -225,7 +225,7 @@ int mg_matrix_elements_batch(int proc, int64_t nevt, const double* mom_aos, cons
                              const double* hel_rnd, const double* col_rnd, double* me, int32_t* hel_out,
                              int32_t* col_out, void* workspace, int64_t workspace_bytes, void* stream);
 
-/* Kernel-split variant of mg_sigmakin (Sec. 5, outlook: the single large
+/* Kernel-split variant of mg_sigmakin (Sec. 4, future work: the single large
  * SIGMAKIN kernel split into smaller kernels orchestrated with CUDA Graphs),
  * kept for comparison with the single kernel.  Same inputs and result as
  * mg_sigmakin (mom [npar][4][nevt], mask, me [nevt]; mode MG_FP64 = 0 or

@@ -1,5 +1,5 @@
 // Kernel-split variant of the helicity-shared program (the outlook of
-// Sec. 5: SIGMAKIN split into smaller kernels orchestrated with CUDA Graphs,
+// Sec. 4: SIGMAKIN split into smaller kernels orchestrated with CUDA Graphs,
 // to relieve the one large kernel).  Two kernels per chunk of events:
 //   currents:   momenta -> tables -> external wavefunctions -> every current
 //               variant (phases 1-2 of the helicity-shared kernel), written

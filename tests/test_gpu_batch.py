@@ -1,4 +1,4 @@
-"""The batched entry point for an external integrator (Sec. 6: an existing
+"""The batched entry point for an external integrator (Sec. 5: an existing
 event generator hands its own phase-space points over, event by event, and
 gets their matrix elements back), through the C ABI.
 
