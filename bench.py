@@ -295,6 +295,29 @@ def cpu_model() -> str:
     return platform.machine()
 
 
+def cpu_simd_rates(seed: int, threads: int) -> dict:
+    """The SIMD CPU build of the same program (libmg_cpu.so) on the host cores,
+    gg -> t t~ g g on a bounded sample: ME/s per precision."""
+    import oracle
+    from paper_2106_12631_gb300 import cpu_simd
+    from paper_2106_12631_gb300 import inputs as I
+    frnd = I.uniforms(I.filter_seed_of(WORKLOAD), 16, 16)
+    fmom, _ = oracle.rambo(4, frnd, 1500.0)
+    _, ph = oracle.me(4, fmom, per_helicity=True, nthreads=threads)
+    mask = (abs(ph).max(axis=1) > 0).astype("int32")
+    out = {"kind": "SIMD CPU build of the helicity-shared program", "cores": threads}
+    for prec, n in (("fp32", 16384), ("fp64", 8192)):
+        rnd = I.uniforms(seed, 16, n)
+        mom, _ = oracle.rambo(4, rnd, 1500.0)
+        cpu_simd.sigmakin(4, mom[:, :, :256].copy(), mask, prec, nthreads=threads)  # warm-up
+        t0 = time.perf_counter()
+        cpu_simd.sigmakin(4, mom, mask, prec, nthreads=threads)
+        dt = time.perf_counter() - t0
+        out[prec] = {"value": n / dt, "unit": UNIT, "lanes": cpu_simd.lanes(prec),
+                     "sample": "%d gg->ttgg events, %.2f s wall" % (n, dt)}
+    return out
+
+
 def cpu_oracle_rate(nevt_sample: int, seed: int, threads: int):
     """Oracle ME/s on the host cores for a bounded sample (RAMBO + |M|^2, FP64)."""
     import numpy as np
@@ -578,6 +601,7 @@ def main():
                                 "single_thread": {"value": rate1, "unit": UNIT,
                                                   "sample": "512 events, %.1f s wall" % dt1},
                                 "cpu": cpu_model()}
+        line["cpu_simd"] = cpu_simd_rates(seed, cores)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

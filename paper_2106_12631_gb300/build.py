@@ -1,4 +1,5 @@
-"""Build libmg.so (CUDA kernels + C ABI) in-tree for sm_103a.
+"""Build libmg.so (CUDA kernels + C ABI) in-tree for sm_103a, and beside it
+libmg_cpu.so (the SIMD CPU build of the same program, host compiler).
 
 One nvcc invocation per translation unit, run in parallel, then a shared-
 library link.  Rebuilds only when a source or header is newer than the
@@ -40,6 +41,32 @@ def _deps():
     return files
 
 
+CPU_SRC = os.path.join(HERE, "cpu", "mg_cpu.cpp")
+CPU_LIB = os.path.join(BUILD, "libmg_cpu.so")
+
+
+def cuda_include() -> str:
+    return os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc()))), "include")
+
+
+def build_cpu(force: bool = False) -> str:
+    """The SIMD CPU build (cpu/mg_cpu.cpp) with the host C++ compiler: no
+    target-specific flags, FMA contraction where the target has it."""
+    deps = _deps() + [CPU_SRC]
+    if not force and os.path.exists(CPU_LIB) and all(os.path.getmtime(f) <= os.path.getmtime(CPU_LIB) for f in deps):
+        return CPU_LIB
+    os.makedirs(BUILD, exist_ok=True)
+    cxx = os.environ.get("CXX") or shutil.which("g++") or "c++"
+    tmp = CPU_LIB + ".%d.tmp" % os.getpid()
+    cmd = [cxx, "-std=c++17", "-O3", "-ffp-contract=fast", "-fPIC", "-shared", "-pthread", "-I", CSRC, "-I",
+           INCLUDE, "-I", cuda_include(), CPU_SRC, "-o", tmp]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("host compiler failed for %s:\n%s" % (CPU_SRC, r.stderr))
+    os.replace(tmp, CPU_LIB)
+    return CPU_LIB
+
+
 def is_stale() -> bool:
     if not os.path.exists(LIB):
         return True
@@ -49,6 +76,7 @@ def is_stale() -> bool:
 
 def build(force: bool = False, verbose: bool = False) -> str:
     if not force and not is_stale():
+        build_cpu()
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     # the largest translation units (the many-leg processes) first, so the
@@ -67,9 +95,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
             raise RuntimeError("nvcc failed for %s:\n%s" % (src, r.stderr))
         return obj, r.stderr
 
-    jobs = min(len(srcs), os.cpu_count() or 4)
+    jobs = min(len(srcs) + 1, os.cpu_count() or 4)
     with cf.ThreadPoolExecutor(jobs) as ex:
+        cpu = ex.submit(build_cpu, True)  # the host build alongside the CUDA translation units
         results = list(ex.map(compile_one, srcs))
+        cpu.result()
     if verbose or extra:
         for obj, err in results:
             if err.strip():

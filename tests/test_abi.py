@@ -1,6 +1,7 @@
 """Host-side checks of the C ABI and of the process generator (no GPU needed).
 
-* libmg.so loads and exports every function include/mg.h declares.
+* libmg.so loads and exports every function include/mg.h declares; so does
+  libmg_cpu.so for include/mg_cpu.h.
 * Process descriptions and host-side argument validation (these return before
   any CUDA call).
 * The generated CUDA headers are up to date with the generator.
@@ -35,6 +36,19 @@ def test_exports_every_declared_symbol(L):
     assert len(names) >= 12
     for n in names:
         assert hasattr(L, n), n
+
+
+def test_cpu_build_exports_its_header():
+    from paper_2106_12631_gb300 import cpu_simd
+    text = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "mg_cpu.h")).read(), flags=re.S)
+    names = sorted(set(re.findall(r"^\s*int\s+(mgc_\w+)\s*\(", text, flags=re.M)))
+    assert names == ["mgc_lanes", "mgc_sigmakin"]
+    L = cpu_simd.lib()
+    for n in names:
+        assert hasattr(L, n), n
+    assert L.mgc_sigmakin(0, 1, None, None, 0, None, None, 1) == -2
+    assert L.mgc_sigmakin(1, 1, None, None, 0, None, None, 1) == -1
+    assert L.mgc_sigmakin(1, 0, None, None, 1, None, None, 1) == 0
 
 
 def test_process_info():
