@@ -134,6 +134,7 @@ cudaError_t launch_split_impl(int proc, const SigLaunch& l, const Couplings<R>& 
   if (chunk > l.nevt) chunk = (l.nevt + HsSplitA<P, R>::EV - 1) / HsSplitA<P, R>::EV * HsSplitA<P, R>::EV;
   struct Key {
     int proc_mode;
+    int device;  // a graph belongs to the device it was captured on
     SigArgs a;
     Couplings<R> cp;
     void* ws;
@@ -141,6 +142,7 @@ cudaError_t launch_split_impl(int proc, const SigLaunch& l, const Couplings<R>& 
   } key;
   std::memset(&key, 0, sizeof key);  // padding compared too
   key.proc_mode = proc * 16 + mode;
+  key.device = dev;
   key.a = SigArgs{l.nevt, l.mom, l.mask, l.me, nullptr, l.pp, l.hel_rnd, l.hel_out, l.col_rnd, l.col_out};
   key.cp = cp;
   key.ws = ws;
