@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-others", action="store_true")
+    ap.add_argument("--sweep", action="store_true",
+                    help="SIGMAKIN throughput against the number of events per launch (no step, one JSON line)")
     return ap.parse_args()
 
 
@@ -295,6 +297,44 @@ def cpu_model() -> str:
     return platform.machine()
 
 
+def sweep_events_per_launch() -> dict:
+    """ME/s of SIGMAKIN against the events of one launch (the paper's throughput
+    against the grid size): e+e- -> mu+mu- and gg -> t t~ g g, mixed and FP64,
+    inputs resident, CUDA events, three launches after one warm-up."""
+    import torch
+
+    from paper_2106_12631_gb300 import inputs as I
+    from paper_2106_12631_gb300 import mg
+    dev = torch.device("cuda", 0)
+    out = {"metric": "SIGMAKIN ME/s against events per launch", "unit": UNIT, "points": {}}
+    plan = {("ee_mumu", "mixed"): range(10, 23, 2), ("ee_mumu", "fp64"): range(10, 23, 2),
+            ("gg_ttgg", "mixed"): range(8, 22, 1), ("gg_ttgg", "fp64"): range(8, 19, 2)}
+    for (name, mode), ks in plan.items():
+        w = I.WORKLOADS[name]
+        proc, nr, ecm = w["proc"], w["nrows"], w["ecm"]
+        frnd = torch.from_numpy(I.uniforms(I.filter_seed_of(name), nr, 16)).to(dev)
+        mask = mg.filter_helicities(proc, mg.rambo(proc, frnd, ecm)[0])
+        nmax = 1 << max(ks)
+        mom, _ = mg.rambo(proc, torch.from_numpy(I.uniforms(I.seed_of(name), nr, nmax)).to(dev), ecm)
+        me = torch.empty(nmax, dtype=torch.float64, device=dev)
+        pts = []
+        for k in ks:
+            n = 1 << k
+            m = mom[:, :, :n].contiguous()
+            mg.sigmakin(proc, m, mask, mode=mode, me=me[:n])
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(3):
+                mg.sigmakin(proc, m, mask, mode=mode, me=me[:n])
+            b.record()
+            torch.cuda.synchronize()
+            t = a.elapsed_time(b) / 1e3 / 3
+            pts.append({"events": n, "ms": 1e3 * t, "value": n / t})
+        out["points"]["%s_%s" % (name, mode)] = pts
+    return out
+
+
 def cpu_simd_rates(seed: int, threads: int) -> dict:
     """The SIMD CPU build of the same program (libmg_cpu.so) on the host cores,
     gg -> t t~ g g on a bounded sample: ME/s per precision."""
@@ -370,6 +410,10 @@ def main():
     rank, world, local = dist_init(args)
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.sweep:
+        if rank == 0:
+            print(json.dumps(sweep_events_per_launch()))
         return
     import numpy as np
     import torch
