@@ -110,6 +110,13 @@ def _dev(t: torch.Tensor, dtype, name: str, shape=None):
     return t.data_ptr()
 
 
+def _ws(t: torch.Tensor):
+    """(device pointer, bytes) of a caller workspace tensor."""
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous():
+        raise ValueError("workspace must be a contiguous CUDA tensor")
+    return t.data_ptr(), t.numel() * t.element_size()
+
+
 def _proc(proc) -> int:
     return PROCS[proc] if isinstance(proc, str) else int(proc)
 
@@ -219,10 +226,11 @@ def matrix_elements_batch(proc, mom_aos: torch.Tensor, mask: torch.Tensor, mode=
     m = MODES[mode] if isinstance(mode, str) else int(mode)
     opt = lambda t, dt, name: _dev(t, dt, name, (nevt,)) if t is not None else None
     _check(lib().mg_matrix_elements_batch(
-        p, nevt, _dev(mom_aos, torch.float64, "mom_aos", (nevt, npar, 4)), _dev(mask, torch.int32, "mask"), m,
+        p, nevt, _dev(mom_aos, torch.float64, "mom_aos", (nevt, npar, 4)),
+        _dev(mask, torch.int32, "mask", (process_info(p)["nhel"],)), m,
         opt(hel_rnd, torch.float64, "hel_rnd"), opt(col_rnd, torch.float64, "col_rnd"),
         _dev(me, torch.float64, "me", (nevt,)), opt(hel, torch.int32, "hel"), opt(col, torch.int32, "col"),
-        workspace.data_ptr(), workspace.numel() * workspace.element_size(), _stream(stream)),
+        *_ws(workspace), _stream(stream)),
         "mg_matrix_elements_batch")
     if hel_rnd is None and col_rnd is None:
         return me
@@ -245,9 +253,10 @@ def sigmakin_split(proc, mom: torch.Tensor, mask: torch.Tensor, mode="mixed_simt
     if workspace is None:
         nb = max(sigmakin_split_workspace_bytes(p, m, nevt), 16)
         workspace = torch.empty(((nb + 7) // 8,), dtype=torch.float64, device=mom.device)
-    _check(lib().mg_sigmakin_split(p, nevt, _dev(mom, torch.float64, "mom"), _dev(mask, torch.int32, "mask"), m,
-                                   _dev(me, torch.float64, "me", (nevt,)), workspace.data_ptr(),
-                                   workspace.numel() * workspace.element_size(), _stream(stream)),
+    info = process_info(p)
+    _check(lib().mg_sigmakin_split(p, nevt, _dev(mom, torch.float64, "mom", (info["npar"], 4, nevt)),
+                                   _dev(mask, torch.int32, "mask", (info["nhel"],)), m,
+                                   _dev(me, torch.float64, "me", (nevt,)), *_ws(workspace), _stream(stream)),
            "mg_sigmakin_split")
     return me
 
@@ -289,7 +298,7 @@ def sigmakin_grad(proc, rnd: torch.Tensor, ecm: float, mask: torch.Tensor, mode=
         me = torch.empty((nevt,), dtype=torch.float64, device=rnd.device)
     g = _dev(gout, torch.float64, "gout", (nevt,)) if gout is not None else None
     _check(lib().mg_sigmakin_grad(p, nevt, float(ecm), _dev(rnd, torch.float64, "rnd"), nrows,
-                                  _dev(mask, torch.int32, "mask"), g,
+                                  _dev(mask, torch.int32, "mask", (process_info(p)["nhel"],)), g,
                                   _dev(grad, torch.float64, "grad", (nrows, nevt)),
                                   _dev(me, torch.float64, "me", (nevt,)), m, _stream(stream)), "mg_sigmakin_grad")
     return grad, me
@@ -369,14 +378,18 @@ def pipeline_host(proc, rnd_host: torch.Tensor, ecm: float, mask: torch.Tensor, 
     m = MODES[mode] if isinstance(mode, str) else int(mode)
     if me_host is None:
         me_host = torch.empty((nevt,), dtype=torch.float64, pin_memory=True)
+    for t, name, n in ((me_host, "me_host", nevt), (wgt_host, "wgt_host", nevt), (sums_host, "sums_host", 3)):
+        if t is not None and (t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous() or t.numel() != n):
+            raise ValueError("%s must be a contiguous float64 CPU tensor of %d values" % (name, n))
     nb = pipeline_workspace_bytes(p, nevt, nrows)
     if workspace is None:
         workspace = torch.empty(((nb + 7) // 8,), dtype=torch.float64, device=mask.device)
     _check(lib().mg_pipeline_host(p, nevt, float(ecm), rnd_host.data_ptr(), nrows,
-                                  _dev(mask, torch.int32, "mask"), m, me_host.data_ptr(),
+                                  _dev(mask, torch.int32, "mask", (process_info(p)["nhel"],)), m,
+                                  me_host.data_ptr(),
                                   wgt_host.data_ptr() if wgt_host is not None else None,
                                   sums_host.data_ptr() if sums_host is not None else None,
-                                  workspace.data_ptr(), workspace.numel() * workspace.element_size(),
+                                  *_ws(workspace),
                                   _stream(stream)), "mg_pipeline_host")
     return me_host
 
