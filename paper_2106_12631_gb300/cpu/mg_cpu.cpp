@@ -31,6 +31,7 @@ static inline float2 __ffma2_rn(float2 a, float2 b, float2 c) {
   return make_float2(std::fma(a.x, b.x, c.x), std::fma(a.y, b.y, c.y));
 }
 static inline float2 __fmul2_rn(float2 a, float2 b) { return make_float2(a.x * b.x, a.y * b.y); }
+static inline float2 __fadd2_rn(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 
 #include "mg_cpu.h"
 #include "process.cuh"

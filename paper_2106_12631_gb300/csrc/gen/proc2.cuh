@@ -59,7 +59,7 @@ struct Proc2 {
         HS_LOCKSTEP(1, 2);
         {
           const W4<R> X = xb[8 + vt[192]];
-          { const cx<R> a = dot4(X, cur[8 + vt[48]]); J[0] -= mul_i(a); J[1] += mul_i(a); }
+          { const cx<R> a = dot4(X, cur[8 + vt[48]]); flow_add<3>(J[0], a); flow_add<2>(J[1], a); }
         }
       } break;
       default: break;

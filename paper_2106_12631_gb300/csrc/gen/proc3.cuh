@@ -59,7 +59,7 @@ struct Proc3 {
         HS_LOCKSTEP(1, 2);
         {
           const W4<R> X = xb[16 + vt[352]];
-          { const cx<R> a = dot4(X, cur[66 + vt[640]]); J[4] -= mul_i(a); J[5] += mul_i(a); }
+          { const cx<R> a = dot4(X, cur[66 + vt[640]]); flow_add<3>(J[4], a); flow_add<2>(J[5], a); }
         }
         HS_LOCKSTEP(2, 3);
         {
@@ -69,7 +69,7 @@ struct Proc3 {
         HS_LOCKSTEP(3, 4);
         {
           const W4<R> X = xb[32 + vt[800]];
-          { const cx<R> a = dot4(X, cur[62 + vt[192]]); J[2] -= mul_i(a); J[3] += mul_i(a); }
+          { const cx<R> a = dot4(X, cur[62 + vt[192]]); flow_add<3>(J[2], a); flow_add<2>(J[3], a); }
         }
         HS_LOCKSTEP(4, 5);
         {
@@ -89,7 +89,7 @@ struct Proc3 {
         HS_LOCKSTEP(7, 8);
         {
           const W4<R> X = xb[64 + vt[832]];
-          { const cx<R> a = dot4(X, cur[58 + vt[160]]); J[0] -= mul_i(a); J[1] += mul_i(a); }
+          { const cx<R> a = dot4(X, cur[58 + vt[160]]); flow_add<3>(J[0], a); flow_add<2>(J[1], a); }
         }
         HS_LOCKSTEP(8, 9);
         {
@@ -97,33 +97,33 @@ struct Proc3 {
           {
             W4<R> Y = cur[34 + vt[608]];
             Y = w4_add(Y, cur[78 + vt[608]]);
-            const cx<R> a = dot4(X, Y); J[0] -= a; J[2] += a; J[4] += a; J[5] -= a;
+            const cx<R> a = dot4(X, Y); flow_add<1>(J[0], a); flow_add<0>(J[2], a); flow_add<0>(J[4], a); flow_add<1>(J[5], a);
           }
           {
             W4<R> Y = cur[42 + vt[608]];
             Y = w4_add(Y, cur[86 + vt[608]]);
-            const cx<R> a = dot4(X, Y); J[1] -= a; J[2] += a; J[3] -= a; J[4] += a;
+            const cx<R> a = dot4(X, Y); flow_add<1>(J[1], a); flow_add<0>(J[2], a); flow_add<1>(J[3], a); flow_add<0>(J[4], a);
           }
           {
             W4<R> Y = cur[50 + vt[608]];
             Y = w4_sub(Y, cur[70 + vt[608]]);
-            const cx<R> a = dot4(X, Y); J[0] += a; J[1] -= a; J[3] -= a; J[5] += a;
+            const cx<R> a = dot4(X, Y); flow_add<0>(J[0], a); flow_add<1>(J[1], a); flow_add<1>(J[3], a); flow_add<0>(J[5], a);
           }
         }
         HS_LOCKSTEP(9, 15);
         {
           const W4<R> X = xb[76 + vt[224]];
-          { const cx<R> a = dot4(X, cur[18 + vt[768]]); J[0] -= mul_i(a); J[2] += mul_i(a); }
+          { const cx<R> a = dot4(X, cur[18 + vt[768]]); flow_add<3>(J[0], a); flow_add<2>(J[2], a); }
         }
         HS_LOCKSTEP(15, 16);
         {
           const W4<R> X = xb[84 + vt[672]];
-          { const cx<R> a = dot4(X, cur[14 + vt[320]]); J[1] -= mul_i(a); J[4] += mul_i(a); }
+          { const cx<R> a = dot4(X, cur[14 + vt[320]]); flow_add<3>(J[1], a); flow_add<2>(J[4], a); }
         }
         HS_LOCKSTEP(16, 17);
         {
           const W4<R> X = xb[92 + vt[704]];
-          { const cx<R> a = dot4(X, cur[10 + vt[288]]); J[3] -= mul_i(a); J[5] += mul_i(a); }
+          { const cx<R> a = dot4(X, cur[10 + vt[288]]); flow_add<3>(J[3], a); flow_add<2>(J[5], a); }
         }
       } break;
       default: break;

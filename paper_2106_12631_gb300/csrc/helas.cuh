@@ -403,8 +403,9 @@ __device__ __forceinline__ W4<R> w4_subi(const W4<R>& s, const W4<R>& y) {
 #ifndef MG_DOT4_PAIRS
 // FP32 contractions in paired FP32 instructions: bit 0 those accumulated
 // straight into one colour flow, bit 1 the others (their extra registers made
-// the gg -> t t~ g g kernel spill)
-#define MG_DOT4_PAIRS 1
+// the gg -> t t~ g g kernel spill), bit 2 the additions of an amplitude into
+// its several colour flows
+#define MG_DOT4_PAIRS 5
 #endif
 // FP32 form: P = sum (xr yr, xi yi) and Q = sum (xi yr, xr yi) side by side in
 // the paired FP32 instructions (8 FFMA2), Re = P.x - P.y, Im = Q.x + Q.y; the
@@ -436,6 +437,27 @@ __device__ __forceinline__ cx<R> dot4(const W4<R>& x, const W4<R>& y) {
     im = fmac(x.w[k].im, y.w[k].re, im);
   }
   return cx<R>(re, im);
+}
+
+// J += i^PH a (PH 0: +1, 1: -1, 2: +i, 3: -i) for an amplitude that feeds
+// several flows; FP32 with bit 2 of MG_DOT4_PAIRS: one paired FP32 add or FMA
+// with a constant phase pair
+template <int PH, class R>
+__device__ __forceinline__ void flow_add(cx<R>& J, cx<R> a) {
+  if constexpr (sizeof(R) == 4 && (MG_DOT4_PAIRS & 4)) {
+    float2 j = make_float2(J.re, J.im);
+    if constexpr (PH == 0) j = __fadd2_rn(j, make_float2(a.re, a.im));
+    else if constexpr (PH == 1) j = __ffma2_rn(make_float2(-1.0f, -1.0f), make_float2(a.re, a.im), j);
+    else if constexpr (PH == 2) j = __ffma2_rn(make_float2(-1.0f, 1.0f), make_float2(a.im, a.re), j);
+    else j = __ffma2_rn(make_float2(1.0f, -1.0f), make_float2(a.im, a.re), j);
+    J.re = j.x;
+    J.im = j.y;
+    return;
+  }
+  if constexpr (PH == 0) J += a;
+  else if constexpr (PH == 1) J -= a;
+  else if constexpr (PH == 2) J += mul_i(a);
+  else J -= mul_i(a);
 }
 
 // J += i^PH sum_i X_i Y_i straight into one colour flow (PH 0: +1, 1: -1,

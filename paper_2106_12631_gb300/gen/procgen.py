@@ -1486,7 +1486,7 @@ class SharedProgram:
         contraction of an amplitude with a single flow accumulates into it."""
         nh = 1 << self.n
         ALL = (1 << self.n) - 1
-        ops = {0: "J[%d] += a;", 1: "J[%d] -= a;", 2: "J[%d] += mul_i(a);", 3: "J[%d] -= mul_i(a);"}
+        ops = {r: "flow_add<%d>(J[%%d], a);" % r for r in range(4)}
         acc = {0: "w4_add", 1: "w4_addi", 2: "w4_sub", 3: "w4_subi"}  # Y_sum += i^r Y
         lines = ["  // A = sum_i X_i Y_i for the amplitudes of chunk c: X = xb[X slot + variant],",
                  "  // Y = cur[Y slot + variant], variant of a leg set S for this helicity = vt[S * NHEL];",
