@@ -80,6 +80,67 @@ __device__ __forceinline__ void atomic_addc(cx<R>* d, cx<R> v) {
   atomicAdd(&d->im, v.im);
 }
 
+// Warp-aggregated adds for the item adjoints: the lanes of a warp that add into
+// the same destination (same key: its shared-memory address) first sum their
+// values with shuffles, and only the lowest lane of each such group adds the
+// sum atomically, so no two lanes of a warp contend for one address.  The
+// lanes taking part are the ones executing together (__activemask), and every
+// collective below runs on all of them.
+template <int NV, class R>
+__device__ __forceinline__ bool warp_group_sum(unsigned key, R* v) {
+  const unsigned act = __activemask();
+  const int lane = threadIdx.x & 31;
+  const unsigned g = __match_any_sync(act, key);
+  const bool leader = lane == __ffs(g) - 1;
+  const int nmax = __reduce_max_sync(act, (unsigned)__popc(g));
+  unsigned others = leader ? g & ~(1u << lane) : 0u;
+  R s[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) s[i] = v[i];
+  for (int j = 1; j < nmax; ++j) {
+    int src = lane;
+    if (others) {
+      src = __ffs(others) - 1;
+      others &= others - 1;
+    }
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      const R x = __shfl_sync(act, v[i], src);
+      if (src != lane) s[i] += x;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < NV; ++i) v[i] = s[i];
+  return leader;
+}
+__device__ __forceinline__ unsigned smem_key(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+template <class R>
+__device__ __forceinline__ void agg_add4(R* d, const R* v) {
+  R t[4] = {v[0], v[1], v[2], v[3]};
+  if (warp_group_sum<4>(smem_key(d), t)) atomic_add4(d, t);
+}
+template <class R>
+__device__ __forceinline__ void agg_addc(cx<R>* d, cx<R> v) {
+  R t[2] = {v.re, v.im};
+  if (warp_group_sum<2>(smem_key(d), t)) atomic_addc(d, cx<R>(t[0], t[1]));
+}
+template <class R, int N>
+__device__ __forceinline__ void agg_slot_add(const Slots<R, N>& s, int i, const W4<R>& w) {
+  R t[8];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    t[2 * k] = w.w[k].re;
+    t[2 * k + 1] = w.w[k].im;
+  }
+  if (warp_group_sum<8>(smem_key(s.p + i), t)) {
+    W4<R> o;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) o.w[k] = cx<R>(t[2 * k], t[2 * k + 1]);
+    s.atomic_add(i, o);
+  }
+}
+
 // adjoint of one current variant (levels >= 1)
 template <class P, class R>
 __device__ __forceinline__ void hs_item_adj(const HsItem& it, const Slots<R, P::HS_NSLOT>& cur,
@@ -116,10 +177,10 @@ __device__ __forceinline__ void hs_item_adj(const HsItem& it, const Slots<R, P::
   }
 #pragma unroll
   for (int k = 0; k < 6; ++k)
-    if (k < nin) curb.atomic_add(it.in[k], b[k]);
-  if (nk >= 1) atomic_add4(Kb + 4 * it.k0, kb0);
-  if (nk >= 2) atomic_add4(Kb + 4 * it.k1, kb1);
-  atomic_addc(prb + it.prop, pb);
+    if (k < nin) agg_slot_add(curb, it.in[k], b[k]);
+  if (nk >= 1) agg_add4(Kb + 4 * it.k0, kb0);
+  if (nk >= 2) agg_add4(Kb + 4 * it.k1, kb1);
+  agg_addc(prb + it.prop, pb);
 }
 
 // adjoint of one amputated-current variant
@@ -149,10 +210,10 @@ __device__ __forceinline__ void hs_xitem_adj(const HsItem& it, const Slots<R, P:
   }
 #pragma unroll
   for (int k = 0; k < 6; ++k)
-    if (k < nin) curb.atomic_add(it.in[k], b[k]);
+    if (k < nin) agg_slot_add(curb, it.in[k], b[k]);
   if (mom) {
-    atomic_add4(Kb + 4 * it.k0, kb0);
-    atomic_add4(Kb + 4 * it.k1, kb1);
+    agg_add4(Kb + 4 * it.k0, kb0);
+    agg_add4(Kb + 4 * it.k1, kb1);
   }
 }
 
