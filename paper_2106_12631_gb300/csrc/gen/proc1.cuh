@@ -61,9 +61,10 @@ struct Proc1 {
     }
   }
   // adjoint of hs_contract: Jb -> atomic adds into curb (operands) and xbb (amputated);
-  // full = the warp's lanes are consecutive helicities of its event(s), all good
+  // full = the warp's lanes are consecutive helicities of its event(s), all good;
+  // act = this lane has an (event, helicity) (lanes without one add zeros)
   template <class R, class CUR, class XB>
-  static __device__ __forceinline__ void hs_contract_adj(int c, const CUR& cur, const XB& xb, const uint8_t* __restrict__ vt, const cx<R>* Jb, const CUR& curb, const XB& xbb, bool full, int lane) {
+  static __device__ __forceinline__ void hs_contract_adj(int c, const CUR& cur, const XB& xb, const uint8_t* __restrict__ vt, const cx<R>* Jb, const CUR& curb, const XB& xbb, bool full, int lane, bool act) {
     switch (c) {
       case 0: {
         {
@@ -79,7 +80,7 @@ struct Proc1 {
             if (full) {
               W4<R> s = Yb;
               w4_warp_sum<3u>(s);
-              if ((lane & 3u) == 0) curb.atomic_add(8 + vy, s);
+              if ((lane & 3u) == 0 && act) slot_add(curb, 8 + vy, s);
             } else {
               curb.atomic_add(8 + vy, Yb);
             }
@@ -87,7 +88,7 @@ struct Proc1 {
           if (full) {
             W4<R> s = Xb;
             w4_warp_sum<12u>(s);
-            if ((lane & 12u) == 0) xbb.atomic_add(0 + vx, s);
+            if ((lane & 12u) == 0 && act) slot_add(xbb, 0 + vx, s);
           } else {
             xbb.atomic_add(0 + vx, Xb);
           }
@@ -105,7 +106,7 @@ struct Proc1 {
             if (full) {
               W4<R> s = Yb;
               w4_warp_sum<3u>(s);
-              if ((lane & 3u) == 0) curb.atomic_add(12 + vy, s);
+              if ((lane & 3u) == 0 && act) slot_add(curb, 12 + vy, s);
             } else {
               curb.atomic_add(12 + vy, Yb);
             }
@@ -113,7 +114,7 @@ struct Proc1 {
           if (full) {
             W4<R> s = Xb;
             w4_warp_sum<12u>(s);
-            if ((lane & 12u) == 0) xbb.atomic_add(4 + vx, s);
+            if ((lane & 12u) == 0 && act) slot_add(xbb, 4 + vx, s);
           } else {
             xbb.atomic_add(4 + vx, Xb);
           }

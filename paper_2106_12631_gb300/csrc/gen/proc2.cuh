@@ -66,9 +66,10 @@ struct Proc2 {
     }
   }
   // adjoint of hs_contract: Jb -> atomic adds into curb (operands) and xbb (amputated);
-  // full = the warp's lanes are consecutive helicities of its event(s), all good
+  // full = the warp's lanes are consecutive helicities of its event(s), all good;
+  // act = this lane has an (event, helicity) (lanes without one add zeros)
   template <class R, class CUR, class XB>
-  static __device__ __forceinline__ void hs_contract_adj(int c, const CUR& cur, const XB& xb, const uint8_t* __restrict__ vt, const cx<R>* Jb, const CUR& curb, const XB& xbb, bool full, int lane) {
+  static __device__ __forceinline__ void hs_contract_adj(int c, const CUR& cur, const XB& xb, const uint8_t* __restrict__ vt, const cx<R>* Jb, const CUR& curb, const XB& xbb, bool full, int lane, bool act) {
     switch (c) {
       case 0: {
         {
@@ -84,7 +85,7 @@ struct Proc2 {
             if (full) {
               W4<R> s = Yb;
               w4_warp_sum<9u>(s);
-              if ((lane & 9u) == 0) curb.atomic_add(16 + vy, s);
+              if ((lane & 9u) == 0 && act) slot_add(curb, 16 + vy, s);
             } else {
               curb.atomic_add(16 + vy, Yb);
             }
@@ -92,7 +93,7 @@ struct Proc2 {
           if (full) {
             W4<R> s = Xb;
             w4_warp_sum<6u>(s);
-            if ((lane & 6u) == 0) xbb.atomic_add(0 + vx, s);
+            if ((lane & 6u) == 0 && act) slot_add(xbb, 0 + vx, s);
           } else {
             xbb.atomic_add(0 + vx, Xb);
           }
@@ -110,7 +111,7 @@ struct Proc2 {
             if (full) {
               W4<R> s = Yb;
               w4_warp_sum<5u>(s);
-              if ((lane & 5u) == 0) curb.atomic_add(12 + vy, s);
+              if ((lane & 5u) == 0 && act) slot_add(curb, 12 + vy, s);
             } else {
               curb.atomic_add(12 + vy, Yb);
             }
@@ -118,7 +119,7 @@ struct Proc2 {
           if (full) {
             W4<R> s = Xb;
             w4_warp_sum<10u>(s);
-            if ((lane & 10u) == 0) xbb.atomic_add(4 + vx, s);
+            if ((lane & 10u) == 0 && act) slot_add(xbb, 4 + vx, s);
           } else {
             xbb.atomic_add(4 + vx, Xb);
           }
@@ -136,7 +137,7 @@ struct Proc2 {
             if (full) {
               W4<R> s = Yb;
               w4_warp_sum<3u>(s);
-              if ((lane & 3u) == 0) curb.atomic_add(8 + vy, s);
+              if ((lane & 3u) == 0 && act) slot_add(curb, 8 + vy, s);
             } else {
               curb.atomic_add(8 + vy, Yb);
             }
@@ -144,7 +145,7 @@ struct Proc2 {
           if (full) {
             W4<R> s = Xb;
             w4_warp_sum<12u>(s);
-            if ((lane & 12u) == 0) xbb.atomic_add(8 + vx, s);
+            if ((lane & 12u) == 0 && act) slot_add(xbb, 8 + vx, s);
           } else {
             xbb.atomic_add(8 + vx, Xb);
           }

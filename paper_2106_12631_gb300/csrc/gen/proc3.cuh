@@ -130,9 +130,10 @@ struct Proc3 {
     }
   }
   // adjoint of hs_contract: Jb -> atomic adds into curb (operands) and xbb (amputated);
-  // full = the warp's lanes are consecutive helicities of its event(s), all good
+  // full = the warp's lanes are consecutive helicities of its event(s), all good;
+  // act = this lane has an (event, helicity) (lanes without one add zeros)
   template <class R, class CUR, class XB>
-  static __device__ __forceinline__ void hs_contract_adj(int c, const CUR& cur, const XB& xb, const uint8_t* __restrict__ vt, const cx<R>* Jb, const CUR& curb, const XB& xbb, bool full, int lane) {
+  static __device__ __forceinline__ void hs_contract_adj(int c, const CUR& cur, const XB& xb, const uint8_t* __restrict__ vt, const cx<R>* Jb, const CUR& curb, const XB& xbb, bool full, int lane, bool act) {
     switch (c) {
       case 0: {
         {
@@ -148,7 +149,7 @@ struct Proc3 {
             if (full) {
               W4<R> s = Yb;
               w4_warp_sum<26u>(s);
-              if ((lane & 26u) == 0) curb.atomic_add(66 + vy, s);
+              if ((lane & 26u) == 0 && act) slot_add(curb, 66 + vy, s);
             } else {
               curb.atomic_add(66 + vy, Yb);
             }
@@ -156,7 +157,7 @@ struct Proc3 {
           if (full) {
             W4<R> s = Xb;
             w4_warp_sum<5u>(s);
-            if ((lane & 5u) == 0) xbb.atomic_add(0 + vx, s);
+            if ((lane & 5u) == 0 && act) slot_add(xbb, 0 + vx, s);
           } else {
             xbb.atomic_add(0 + vx, Xb);
           }
@@ -174,7 +175,7 @@ struct Proc3 {
             if (full) {
               W4<R> s = Yb;
               w4_warp_sum<26u>(s);
-              if ((lane & 26u) == 0) curb.atomic_add(66 + vy, s);
+              if ((lane & 26u) == 0 && act) slot_add(curb, 66 + vy, s);
             } else {
               curb.atomic_add(66 + vy, Yb);
             }
@@ -182,7 +183,7 @@ struct Proc3 {
           if (full) {
             W4<R> s = Xb;
             w4_warp_sum<5u>(s);
-            if ((lane & 5u) == 0) xbb.atomic_add(8 + vx, s);
+            if ((lane & 5u) == 0 && act) slot_add(xbb, 8 + vx, s);
           } else {
             xbb.atomic_add(8 + vx, Xb);
           }
@@ -200,7 +201,7 @@ struct Proc3 {
             if (full) {
               W4<R> s = Yb;
               w4_warp_sum<26u>(s);
-              if ((lane & 26u) == 0) curb.atomic_add(66 + vy, s);
+              if ((lane & 26u) == 0 && act) slot_add(curb, 66 + vy, s);
             } else {
               curb.atomic_add(66 + vy, Yb);
             }
@@ -208,7 +209,7 @@ struct Proc3 {
           if (full) {
             W4<R> s = Xb;
             w4_warp_sum<5u>(s);
-            if ((lane & 5u) == 0) xbb.atomic_add(16 + vx, s);
+            if ((lane & 5u) == 0 && act) slot_add(xbb, 16 + vx, s);
           } else {
             xbb.atomic_add(16 + vx, Xb);
           }
@@ -226,7 +227,7 @@ struct Proc3 {
             if (full) {
               W4<R> s = Yb;
               w4_warp_sum<19u>(s);
-              if ((lane & 19u) == 0) curb.atomic_add(62 + vy, s);
+              if ((lane & 19u) == 0 && act) slot_add(curb, 62 + vy, s);
             } else {
               curb.atomic_add(62 + vy, Yb);
             }
@@ -234,7 +235,7 @@ struct Proc3 {
           if (full) {
             W4<R> s = Xb;
             w4_warp_sum<12u>(s);
-            if ((lane & 12u) == 0) xbb.atomic_add(24 + vx, s);
+            if ((lane & 12u) == 0 && act) slot_add(xbb, 24 + vx, s);
           } else {
             xbb.atomic_add(24 + vx, Xb);
           }
@@ -252,7 +253,7 @@ struct Proc3 {
             if (full) {
               W4<R> s = Yb;
               w4_warp_sum<19u>(s);
-              if ((lane & 19u) == 0) curb.atomic_add(62 + vy, s);
+              if ((lane & 19u) == 0 && act) slot_add(curb, 62 + vy, s);
             } else {
               curb.atomic_add(62 + vy, Yb);
             }
@@ -260,7 +261,7 @@ struct Proc3 {
           if (full) {
             W4<R> s = Xb;
             w4_warp_sum<12u>(s);
-            if ((lane & 12u) == 0) xbb.atomic_add(32 + vx, s);
+            if ((lane & 12u) == 0 && act) slot_add(xbb, 32 + vx, s);
           } else {
             xbb.atomic_add(32 + vx, Xb);
           }
@@ -278,7 +279,7 @@ struct Proc3 {
             if (full) {
               W4<R> s = Yb;
               w4_warp_sum<19u>(s);
-              if ((lane & 19u) == 0) curb.atomic_add(62 + vy, s);
+              if ((lane & 19u) == 0 && act) slot_add(curb, 62 + vy, s);
             } else {
               curb.atomic_add(62 + vy, Yb);
             }
@@ -286,7 +287,7 @@ struct Proc3 {
           if (full) {
             W4<R> s = Xb;
             w4_warp_sum<12u>(s);
-            if ((lane & 12u) == 0) xbb.atomic_add(40 + vx, s);
+            if ((lane & 12u) == 0 && act) slot_add(xbb, 40 + vx, s);
           } else {
             xbb.atomic_add(40 + vx, Xb);
           }
@@ -304,7 +305,7 @@ struct Proc3 {
             if (full) {
               W4<R> s = Yb;
               w4_warp_sum<11u>(s);
-              if ((lane & 11u) == 0) curb.atomic_add(58 + vy, s);
+              if ((lane & 11u) == 0 && act) slot_add(curb, 58 + vy, s);
             } else {
               curb.atomic_add(58 + vy, Yb);
             }
@@ -312,7 +313,7 @@ struct Proc3 {
           if (full) {
             W4<R> s = Xb;
             w4_warp_sum<20u>(s);
-            if ((lane & 20u) == 0) xbb.atomic_add(48 + vx, s);
+            if ((lane & 20u) == 0 && act) slot_add(xbb, 48 + vx, s);
           } else {
             xbb.atomic_add(48 + vx, Xb);
           }
@@ -330,7 +331,7 @@ struct Proc3 {
             if (full) {
               W4<R> s = Yb;
               w4_warp_sum<11u>(s);
-              if ((lane & 11u) == 0) curb.atomic_add(58 + vy, s);
+              if ((lane & 11u) == 0 && act) slot_add(curb, 58 + vy, s);
             } else {
               curb.atomic_add(58 + vy, Yb);
             }
@@ -338,7 +339,7 @@ struct Proc3 {
           if (full) {
             W4<R> s = Xb;
             w4_warp_sum<20u>(s);
-            if ((lane & 20u) == 0) xbb.atomic_add(56 + vx, s);
+            if ((lane & 20u) == 0 && act) slot_add(xbb, 56 + vx, s);
           } else {
             xbb.atomic_add(56 + vx, Xb);
           }
@@ -356,7 +357,7 @@ struct Proc3 {
             if (full) {
               W4<R> s = Yb;
               w4_warp_sum<11u>(s);
-              if ((lane & 11u) == 0) curb.atomic_add(58 + vy, s);
+              if ((lane & 11u) == 0 && act) slot_add(curb, 58 + vy, s);
             } else {
               curb.atomic_add(58 + vy, Yb);
             }
@@ -364,7 +365,7 @@ struct Proc3 {
           if (full) {
             W4<R> s = Xb;
             w4_warp_sum<20u>(s);
-            if ((lane & 20u) == 0) xbb.atomic_add(64 + vx, s);
+            if ((lane & 20u) == 0 && act) slot_add(xbb, 64 + vx, s);
           } else {
             xbb.atomic_add(64 + vx, Xb);
           }
@@ -383,14 +384,14 @@ struct Proc3 {
             if (full) {
               W4<R> s = Yb;
               w4_warp_sum<6u>(s);
-              if ((lane & 6u) == 0) curb.atomic_add(34 + vy, s);
+              if ((lane & 6u) == 0 && act) slot_add(curb, 34 + vy, s);
             } else {
               curb.atomic_add(34 + vy, Yb);
             }
             if (full) {
               W4<R> s = Yb;
               w4_warp_sum<6u>(s);
-              if ((lane & 6u) == 0) curb.atomic_add(78 + vy, s);
+              if ((lane & 6u) == 0 && act) slot_add(curb, 78 + vy, s);
             } else {
               curb.atomic_add(78 + vy, Yb);
             }
@@ -405,14 +406,14 @@ struct Proc3 {
             if (full) {
               W4<R> s = Yb;
               w4_warp_sum<6u>(s);
-              if ((lane & 6u) == 0) curb.atomic_add(42 + vy, s);
+              if ((lane & 6u) == 0 && act) slot_add(curb, 42 + vy, s);
             } else {
               curb.atomic_add(42 + vy, Yb);
             }
             if (full) {
               W4<R> s = Yb;
               w4_warp_sum<6u>(s);
-              if ((lane & 6u) == 0) curb.atomic_add(86 + vy, s);
+              if ((lane & 6u) == 0 && act) slot_add(curb, 86 + vy, s);
             } else {
               curb.atomic_add(86 + vy, Yb);
             }
@@ -427,14 +428,14 @@ struct Proc3 {
             if (full) {
               W4<R> s = Yb;
               w4_warp_sum<6u>(s);
-              if ((lane & 6u) == 0) curb.atomic_add(50 + vy, s);
+              if ((lane & 6u) == 0 && act) slot_add(curb, 50 + vy, s);
             } else {
               curb.atomic_add(50 + vy, Yb);
             }
             if (full) {
               W4<R> s = w4_neg(Yb);
               w4_warp_sum<6u>(s);
-              if ((lane & 6u) == 0) curb.atomic_add(70 + vy, s);
+              if ((lane & 6u) == 0 && act) slot_add(curb, 70 + vy, s);
             } else {
               curb.atomic_add(70 + vy, w4_neg(Yb));
             }
@@ -442,7 +443,7 @@ struct Proc3 {
           if (full) {
             W4<R> s = Xb;
             w4_warp_sum<25u>(s);
-            if ((lane & 25u) == 0) xbb.atomic_add(72 + vx, s);
+            if ((lane & 25u) == 0 && act) slot_add(xbb, 72 + vx, s);
           } else {
             xbb.atomic_add(72 + vx, Xb);
           }
@@ -460,7 +461,7 @@ struct Proc3 {
             if (full) {
               W4<R> s = Yb;
               w4_warp_sum<28u>(s);
-              if ((lane & 28u) == 0) curb.atomic_add(18 + vy, s);
+              if ((lane & 28u) == 0 && act) slot_add(curb, 18 + vy, s);
             } else {
               curb.atomic_add(18 + vy, Yb);
             }
@@ -468,7 +469,7 @@ struct Proc3 {
           if (full) {
             W4<R> s = Xb;
             w4_warp_sum<3u>(s);
-            if ((lane & 3u) == 0) xbb.atomic_add(76 + vx, s);
+            if ((lane & 3u) == 0 && act) slot_add(xbb, 76 + vx, s);
           } else {
             xbb.atomic_add(76 + vx, Xb);
           }
@@ -486,7 +487,7 @@ struct Proc3 {
             if (full) {
               W4<R> s = Yb;
               w4_warp_sum<21u>(s);
-              if ((lane & 21u) == 0) curb.atomic_add(14 + vy, s);
+              if ((lane & 21u) == 0 && act) slot_add(curb, 14 + vy, s);
             } else {
               curb.atomic_add(14 + vy, Yb);
             }
@@ -494,7 +495,7 @@ struct Proc3 {
           if (full) {
             W4<R> s = Xb;
             w4_warp_sum<10u>(s);
-            if ((lane & 10u) == 0) xbb.atomic_add(84 + vx, s);
+            if ((lane & 10u) == 0 && act) slot_add(xbb, 84 + vx, s);
           } else {
             xbb.atomic_add(84 + vx, Xb);
           }
@@ -512,7 +513,7 @@ struct Proc3 {
             if (full) {
               W4<R> s = Yb;
               w4_warp_sum<13u>(s);
-              if ((lane & 13u) == 0) curb.atomic_add(10 + vy, s);
+              if ((lane & 13u) == 0 && act) slot_add(curb, 10 + vy, s);
             } else {
               curb.atomic_add(10 + vy, Yb);
             }
@@ -520,7 +521,7 @@ struct Proc3 {
           if (full) {
             W4<R> s = Xb;
             w4_warp_sum<18u>(s);
-            if ((lane & 18u) == 0) xbb.atomic_add(92 + vx, s);
+            if ((lane & 18u) == 0 && act) slot_add(xbb, 92 + vx, s);
           } else {
             xbb.atomic_add(92 + vx, Xb);
           }

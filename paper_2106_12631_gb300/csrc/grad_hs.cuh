@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(HsGradCfg<P, R>::NT) sigmakin_hs_grad_kernel(G
     }
     // lanes = consecutive helicities of whole events when every helicity is good
     const bool full = ng == P::NHEL && (P::NHEL % 32 == 0 || 32 % P::NHEL == 0);
-    P::template hs_contract_adj<R>(0, cur, xb, vtab + ih, Jb, curb, xbb, full, tid & 31);
+    P::template hs_contract_adj<R>(0, cur, xb, vtab + ih, Jb, curb, xbb, full, tid & 31, active);
   }
   __syncthreads();
   // 4. amputated currents, then the current levels in reverse

@@ -461,4 +461,14 @@ __device__ __forceinline__ void external_adj(int kind, const R* p, R m, int hel,
     for (int nu = 0; nu < 4; ++nu) pb[nu] += w.w[c].re.d[nu] * wb.w[c].re + w.w[c].im.d[nu] * wb.w[c].im;
 }
 
+// slot i += w by its only writer (a plain read, add and write: the adjoint
+// contractions' warp sums leave one lane per slot and event)
+template <class R, int N>
+__device__ __forceinline__ void slot_add(const Slots<R, N>& s, int i, const W4<R>& w) {
+  W4<R> o = s[i];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) o.w[k] += w.w[k];
+  s.set(i, o);
+}
+
 }  // namespace mg

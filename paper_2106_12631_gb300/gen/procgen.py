@@ -1421,23 +1421,30 @@ class SharedProgram:
                     m |= 1 << b
             return m
 
+        # with at most 32 helicities an event's helicities are all in one warp, so
+        # after the warp sum the first lane of the slot's group is its only writer
+        one_warp = self.n <= 5
+
         def add(target, slot, value, mask):
             # full: lanes = consecutive helicities of one event, all good: sum the
-            # lanes sharing the slot first, one atomic add per slot and warp
+            # lanes sharing the slot first, one add per slot and warp (a plain
+            # add when the warp holds every helicity of the event, else atomic)
             return ["          if (full) {",
                     "            W4<R> s = %s;" % value,
                     "            w4_warp_sum<%du>(s);" % mask,
-                    "            if ((lane & %du) == 0) %s.atomic_add(%s, s);" % (mask, target, slot),
+                    ("            if ((lane & %du) == 0 && act) slot_add(%s, %s, s);" % (mask, target, slot)) if one_warp
+                    else ("            if ((lane & %du) == 0) %s.atomic_add(%s, s);" % (mask, target, slot)),
                     "          } else {",
                     "            %s.atomic_add(%s, %s);" % (target, slot, value),
                     "          }"]
 
         lines = ["  // adjoint of hs_contract: Jb -> atomic adds into curb (operands) and xbb (amputated);",
-                 "  // full = the warp's lanes are consecutive helicities of its event(s), all good",
+                 "  // full = the warp's lanes are consecutive helicities of its event(s), all good;",
+                 "  // act = this lane has an (event, helicity) (lanes without one add zeros)",
                  "  template <class R, class CUR, class XB>",
                  "  static __device__ __forceinline__ void hs_contract_adj(int c, const CUR& cur, const XB& xb,"
                  " const uint8_t* __restrict__ vt, const cx<R>* Jb, const CUR& curb, const XB& xbb, bool full,"
-                 " int lane) {",
+                 " int lane, bool act) {",
                  "    switch (c) {"]
         for c in range(len(self.chunks)):
             lines.append("      case %d: {" % c)
