@@ -37,7 +37,7 @@ static inline float2 __fadd2_rn(float2 a, float2 b) { return make_float2(a.x + b
 #include "process.cuh"
 
 #ifndef MGC_LANES_BYTES
-#define MGC_LANES_BYTES 32  // bytes per lane vector (two 128-bit registers: more independent work)
+#define MGC_LANES_BYTES 256  // bytes per lane vector: 64 FP32 or 32 FP64 events (measured best on Grace)
 #endif
 
 namespace mgcpu {
