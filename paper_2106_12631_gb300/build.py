@@ -58,7 +58,7 @@ def build_cpu(force: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     cxx = os.environ.get("CXX") or shutil.which("g++") or "c++"
     tmp = CPU_LIB + ".%d.tmp" % os.getpid()
-    cmd = [cxx, "-std=c++17", "-O3", "-ffp-contract=fast", "-fPIC", "-shared", "-pthread", "-I", CSRC, "-I",
+    cmd = [cxx, "-std=c++17", "-O3", "-ffp-contract=fast", "-Wno-psabi", "-fPIC", "-shared", "-pthread", "-I", CSRC, "-I",
            INCLUDE, "-I", cuda_include(), CPU_SRC, "-o", tmp]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:

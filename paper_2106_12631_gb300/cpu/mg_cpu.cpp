@@ -37,7 +37,7 @@ static inline float2 __fadd2_rn(float2 a, float2 b) { return make_float2(a.x + b
 #include "process.cuh"
 
 #ifndef MGC_LANES_BYTES
-#define MGC_LANES_BYTES 256  // bytes per lane vector: 64 FP32 or 32 FP64 events (measured best on Grace)
+#define MGC_LANES_BYTES 64  // bytes per lane vector: 16 FP32 or 8 FP64 events (wider ran faster on Grace but compiles for minutes)
 #endif
 
 namespace mgcpu {
