@@ -169,6 +169,22 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def rel_err_stats(x, ref) -> dict:
+    """Per-event relative error |x / ref - 1| over all events: max, median,
+    99.99th percentile, non-finite results, and the events above 1e-5 (the
+    stated bound of the mixed path's 99.9th percentile) and above 1e-12 (the FP64
+    bar)."""
+    import numpy as np
+    import torch
+    x = x.cpu().numpy() if isinstance(x, torch.Tensor) else np.asarray(x)
+    ref = ref.cpu().numpy() if isinstance(ref, torch.Tensor) else np.asarray(ref)
+    bad = ~np.isfinite(x)
+    rel = np.where(bad, np.inf, np.abs(x / ref - 1))
+    return {"max": float(rel.max()), "median": float(np.median(rel)), "p99.99": float(np.quantile(rel, 0.9999)),
+            "nonfinite": int(bad.sum()), "above_1e-5": int((rel > 1e-5).sum()),
+            "above_1e-12": int((rel > 1e-12).sum()), "events": int(rel.size)}
+
+
 def measure_other_workloads(mg, I, dev, stream, reps: int = 3) -> dict:
     """ME/s of SIGMAKIN (FP64 and mixed) for e+e- -> mu+mu-, gg -> t t~, gg -> t t~ g,
     and of the adjoint gradient of gg -> t t~ g (2^18 events, 16 random rows)."""
@@ -202,9 +218,12 @@ def measure_other_workloads(mg, I, dev, stream, reps: int = 3) -> dict:
                                                      stream=stream))
                 res[mode] = {"value": nevt / t, "unit": "gradients/s", "ms": 1e3 * t}
         else:
+            me_by_mode = {}
             for mode in ("mixed", "fp64"):
                 t = time_it(lambda: mg.sigmakin(proc, mom, mask, mode=mode, me=me, stream=stream))
                 res[mode] = {"value": nevt / t, "unit": UNIT, "sigmakin_ms": 1e3 * t}
+                me_by_mode[mode] = me.clone()
+            res["mixed_vs_fp64_rel_err"] = rel_err_stats(me_by_mode["mixed"], me_by_mode["fp64"])
         if name == "ee_mumu":
             # the paper's own e+e- -> mu+mu- point: 2^19 events per launch, past the
             # plateau in events in flight (16384 events leave the GPU mostly idle)
@@ -374,6 +393,38 @@ def cpu_oracle_rate(nevt_sample: int, seed: int, threads: int):
     return nevt_sample / dt, dt
 
 
+# seeded sample per workload for the error against the oracle (the workload's
+# first events; about a second of oracle time on the host cores in all)
+ORACLE_ERROR_SAMPLE = (("ee_mumu", 4096), ("gg_tt", 4096), ("gg_ttg", 4096), ("gg_ttgg", 1024))
+
+
+def oracle_error_stats(mg, dev, cores: int) -> dict:
+    """Relative error of the GPU's FP64 and mixed-precision |M|^2 against the
+    FP64 oracle, per workload, on a seeded sample: the oracle's own RAMBO
+    momenta go to both sides, the GPU uses its own helicity filter."""
+    import torch
+
+    import oracle
+    from paper_2106_12631_gb300 import inputs as I
+    oracle.build()
+    out = {}
+    for name, n in ORACLE_ERROR_SAMPLE:
+        w = I.WORKLOADS[name]
+        proc, nr, ecm = w["proc"], w["nrows"], w["ecm"]
+        mom, _ = oracle.rambo(proc, I.uniforms(I.seed_of(name), nr, n), ecm)
+        t0 = time.perf_counter()
+        me_o = oracle.me(proc, mom, nthreads=cores)
+        dt = time.perf_counter() - t0
+        frnd = torch.from_numpy(I.uniforms(I.filter_seed_of(name), nr, 16)).to(dev)
+        mask = mg.filter_helicities(proc, mg.rambo(proc, frnd, ecm)[0])
+        mom_d = torch.from_numpy(mom).to(dev)
+        res = {"events": n, "oracle_s": dt}
+        for mode in ("fp64", "mixed"):
+            res[mode] = rel_err_stats(mg.sigmakin(proc, mom_d, mask, mode=mode), me_o)
+        out[name] = res
+    return out
+
+
 def run_reference(args, rank, world):
     """Reference arm: the FP64 CPU oracle on the host cores, bounded sample per step."""
     if rank != 0:
@@ -531,14 +582,9 @@ def main():
     if not args.no_fp64 and args.mode != "fp64":
         t64, k64 = timed("fp64", max(1, min(args.steps, 2)))
         me64 = me.clone()
-        rel = (me_main - me64).abs() / me64.abs()
-        relh = rel.cpu().numpy()
         fp64 = {"value": world * nevt * max(1, min(args.steps, 2)) / t64, "unit": UNIT,
                 "sigmakin_ms": 1e3 * statistics.mean(k64),
-                "mixed_vs_fp64_rel_err": {"max": float(relh.max()), "median": float(np.median(relh)),
-                                          "p99.99": float(np.quantile(relh, 0.9999)),
-                                          "nonfinite": int((~torch.isfinite(me_main)).sum().item()),
-                                          "events": nevt}}
+                "mixed_vs_fp64_rel_err": rel_err_stats(me_main, me64)}
 
     # event generation from the step's weighted events: device-RNG RAMBO (vs the
     # buffered one), cross section, hit-or-miss unweighting (CUDA events)
@@ -550,46 +596,58 @@ def main():
     # the other workloads (SIGMAKIN or the adjoint alone, inputs resident, CUDA events)
     others = {} if args.no_others else measure_other_workloads(mg, I, dev, stream)
 
-    # end to end through the public API with host buffers: every step copies the
-    # filter events' and the batch's random numbers from pinned host memory,
-    # filters the helicities (high-priority stream, beside the copy and RAMBO),
-    # runs RAMBO + SIGMAKIN + the event sum, and reads me and the event sum back
+    # end to end through the library's host-buffer entry point (mg_pipeline_host):
+    # every step copies the batch's random numbers from pinned host memory, runs
+    # RAMBO + SIGMAKIN + the event sum, and copies me and the event sum back.
+    # Each step's helicity mask comes from its own 16 filter events, drawn and
+    # filtered on the device (mg_rambo_seeded, mg_filter_helicities) on the
+    # high-priority stream one step ahead, into one of two mask buffers, so the
+    # filter runs beside the previous step's pipeline.
     rnd_h = torch.from_numpy(I.uniforms(seed, 16, nevt, first_event=shard_first_event(rank, nevt))).pin_memory()
-    frnd_h = torch.from_numpy(I.uniforms(I.filter_seed_of(WORKLOAD), 16, 16)).pin_memory()
     me_h = torch.empty(nevt, dtype=torch.float64).pin_memory()
     sums_h = torch.empty(3, dtype=torch.float64).pin_memory()
-    rnd_d = torch.empty_like(rnd)
+    ws = torch.empty(mg.pipeline_workspace_bytes(proc, nevt, 16) // 8 + 2, dtype=torch.float64, device=dev)
+    masks = [torch.empty_like(mask) for _ in range(2)]
+    mask_ready = [torch.cuda.Event() for _ in range(2)]
+    mask_free = [torch.cuda.Event() for _ in range(2)]
+    fseed = I.filter_seed_of(WORKLOAD)
 
-    def step_e2e():
+    def filter_e2e(k):
+        b = k & 1
+        filt.wait_event(mask_free[b])  # the pipeline two steps back has read this mask
+        mg.rambo_seeded(proc, 16, ecm, fseed, 0, mom=fmom, wgt=fwgt, stream=filt)
+        mg.filter_helicities(proc, fmom, mask=masks[b], stream=filt)
+        mask_ready[b].record(filt)
+
+    def steps_e2e(n):
         filt.wait_stream(stream)
-        with torch.cuda.stream(filt):
-            frnd.copy_(frnd_h, non_blocking=True)
-        mg.rambo(proc, frnd, ecm, mom=fmom, wgt=fwgt, stream=filt)
-        mg.filter_helicities(proc, fmom, mask=mask, stream=filt)
-        rnd_d.copy_(rnd_h, non_blocking=True)
-        mg.rambo(proc, rnd_d, ecm, mom=mom, wgt=wgt, stream=stream)
-        stream.wait_stream(filt)
-        mg.sigmakin(proc, mom, mask, mode=args.mode, me=me, stream=stream)
-        mg.event_sum(me, wgt, out=out, scratch=scratch, stream=stream)
-        me_h.copy_(me, non_blocking=True)
-        sums_h.copy_(out, non_blocking=True)
+        filter_e2e(0)
+        for k in range(n):
+            if k + 1 < n:
+                filter_e2e(k + 1)
+            stream.wait_event(mask_ready[k & 1])
+            mg.pipeline_host(proc, rnd_h, ecm, masks[k & 1], mode=args.mode, me_host=me_h, sums_host=sums_h,
+                             workspace=ws, stream=stream)
+            mask_free[k & 1].record(stream)
 
-    for _ in range(args.warmup):
-        step_e2e()
+    steps_e2e(args.warmup)
     torch.cuda.synchronize()
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
-        step_e2e()
+    steps_e2e(args.steps)
     e1.record(stream)
     torch.cuda.synchronize()
     te2e = e0.elapsed_time(e1) / 1e3
     te2e = max_over_ranks(te2e, world, dev)
+    e2e_same = bool(torch.equal(me_h, me_main.cpu()))
     sum_over_ranks(sums, world)
     e2e = {"value": world * nevt * args.steps / te2e, "unit": UNIT,
-           "h2d_bytes_per_step": 8 * frnd_h.numel() + 8 * rnd_h.numel(),
-           "d2h_bytes_per_step": 8 * nevt + 8 * 3}
+           "h2d_bytes_per_step": 8 * rnd_h.numel(),
+           "d2h_bytes_per_step": 8 * nevt + 8 * 3,
+           "api": "mg_pipeline_host (host rnd in; host me and event sum out), filter on the device",
+           "me_identical_to_device_step": e2e_same}
+    del ws
 
     # roofline of the dominant kernel (SIGMAKIN): FP32 CUDA-core arithmetic.
     # Algorithmic flops per event of the helicity-shared kernel: every current
@@ -646,6 +704,7 @@ def main():
                                                   "sample": "512 events, %.1f s wall" % dt1},
                                 "cpu": cpu_model()}
         line["cpu_simd"] = cpu_simd_rates(seed, cores)
+        line["rel_err_vs_oracle"] = oracle_error_stats(mg, dev, cores)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

@@ -1,5 +1,20 @@
-"""Small test-only helpers: Minkowski products and Lorentz transformations."""
+"""Small test-only helpers: Minkowski products, Lorentz transformations and
+the parity bars shared by the test files."""
 import numpy as np
+
+# FP64 path: 1e-12 relative per event; on events whose own FP64 conditioning
+# is worse, 4 d_rot (d_rot: oracle_conditioning below), never above 1e-9.
+FP64_REL = 1e-12
+FP64_CAP = 1e-9
+# mixed path (FP32 amplitudes, FP64 propagator invariants and sums): stated bound
+MIXED_MAX_REL = 1e-4
+MIXED_P999_REL = 1e-5
+MIXED_MEDIAN_REL = 1e-6
+
+
+def fp64_tol(d_rot):
+    """Per-event FP64 bar: 1e-12, or 4 d_rot on ill-conditioned events, at most 1e-9."""
+    return np.minimum(np.maximum(FP64_REL, 4 * np.asarray(d_rot)), FP64_CAP)
 
 
 def mdot(a, b):

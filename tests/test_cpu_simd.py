@@ -15,7 +15,7 @@ FP64 oracle.
 import numpy as np
 import pytest
 
-from helpers import oracle_conditioning
+from helpers import fp64_tol, oracle_conditioning
 from paper_2106_12631_gb300 import cpu_simd
 from paper_2106_12631_gb300 import inputs as I
 
@@ -41,7 +41,7 @@ def test_fp64_parity(orc, proc, nevt):
     me_o, d_rot = oracle_conditioning(orc, proc, mom)
     me = cpu_simd.sigmakin(proc, mom, good_mask(orc, proc), "fp64", nthreads=4)
     rel = np.abs(me / me_o - 1)
-    assert np.all(rel <= np.maximum(1e-12, 4 * d_rot)), rel.max()
+    assert np.all(rel <= fp64_tol(d_rot)), rel.max()
 
 
 @pytest.mark.parametrize("proc,nevt", [(1, 1001), (2, 515), (3, 67), (4, 13)])

@@ -8,12 +8,12 @@ gets their matrix elements back), through the C ABI.
 * The helicity chosen per event equals the oracle's inverse-CDF choice over its
   own per-helicity |M_h|^2 with the same uniforms, except where u * |M|^2 falls
   within the mode's error of a boundary of the running sum (FP64: 1e-12 or
-  4 d_rot relative, d_rot the event's own conditioning; mixed: 1e-3).
+  4 d_rot relative up to 1e-9, d_rot the event's own conditioning; mixed: 1e-4).
 * The colour flow chosen per event likewise equals the oracle's choice over its
   own colour-flow weights w_s = sum over the good helicities of |J_s|^2, the
   oracle's J_s projected from explicit colour tensors (Sec. 2, colour-flow
   method), except within the mode's error of a boundary (FP64: 1e-9 or
-  100 d_rot; mixed: 1e-3).
+  100 d_rot; mixed: 1e-4).
 * For one phase-space point and many uniforms the chosen helicities follow
   |M_h|^2 / |M|^2 and the chosen flows w_s / sum w (5 sigma each).
 * Edge cases: only vanishing helicities in the mask (me = 0, choices -1),
@@ -26,7 +26,7 @@ import pytest
 import torch
 
 import oracle
-from helpers import oracle_conditioning
+from helpers import MIXED_MAX_REL, fp64_tol, oracle_conditioning
 from paper_2106_12631_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
@@ -116,10 +116,10 @@ def test_choices(mg, orc, proc, nevt, mode):
     fp64 = mode == "fp64"
     good = (mask_h != 0)[:, None]
     nb = check_choice(hel, oracle.choose_helicity(ph, mask_h, u[0]), np.where(good, ph, 0.0), u[0],
-                      np.maximum(1e-12, 4 * d_rot) if fp64 else 1e-3, 0.0 if fp64 else 0.01)
+                      fp64_tol(d_rot) if fp64 else MIXED_MAX_REL, 0.0 if fp64 else 0.01)
     w = np.sum(np.where(good[:, :, None], np.abs(jf) ** 2, 0.0), axis=0)
     nc = check_choice(col, oracle.choose_colour(jf, mask_h, u[1]), w, u[1],
-                      np.maximum(1e-9, 100 * d_rot) if fp64 else 1e-3, 0.0 if fp64 else 0.01)
+                      np.maximum(1e-9, 100 * d_rot) if fp64 else MIXED_MAX_REL, 0.0 if fp64 else 0.01)
     print("proc %d %s: %d helicity and %d colour choices of %d differ from the oracle's" % (proc, mode, nb, nc, nevt))
 
 

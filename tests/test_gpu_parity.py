@@ -6,9 +6,10 @@ Bars:
 * FP64 matrix elements on identical momenta: 1e-12 relative per event, except
   for events whose own FP64 conditioning is worse: there the bar is 4 d_rot,
   d_rot = the oracle's relative change under exact rotations of the event
-  (rounding-level input changes).  At most 0.1% of events may need that.
+  (rounding-level input changes), and never above 1e-9.  At most 0.1% of
+  events (plus one, for small samples) may need the relaxation.
 * Mixed precision (FP32 amplitudes, FP64 denominators and sums): median <=
-  1e-6, 99.9th percentile <= 1e-5, max <= 1e-3, no NaN/Inf; for events with
+  1e-6, 99.9th percentile <= 1e-5, max <= 1e-4, no NaN/Inf; for events with
   d_rot <= 1e-14 (well conditioned) every event is within 1e-5.
 * Helicity mask: identical to the oracle's set of non-zero helicities.
 * Event sum: 1e-14 relative to the oracle's pairwise sum, bitwise
@@ -18,16 +19,13 @@ import numpy as np
 import pytest
 import torch
 
-from helpers import oracle_conditioning, rambo_gamma
+from helpers import (FP64_REL, MIXED_MAX_REL, MIXED_MEDIAN_REL, MIXED_P999_REL, fp64_tol, oracle_conditioning,
+                     rambo_gamma)
 from paper_2106_12631_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
 
-FP64_REL = 1e-12
 FP64_ILL_FRACTION = 1e-3
-MIXED_MAX_REL = 1e-3
-MIXED_P999_REL = 1e-5
-MIXED_MEDIAN_REL = 1e-6
 WELL_CONDITIONED = 1e-14
 EPS = np.finfo(float).eps
 NR = {1: 8, 2: 8, 3: 12, 4: 16}
@@ -51,6 +49,21 @@ def dev(x):
 def host(t):
     torch.cuda.synchronize()
     return t.cpu().numpy()
+
+
+_ORACLE = {}
+
+
+def oracle_sample(orc, proc, seed, nevt):
+    """Oracle momenta, matrix elements and conditioning of a seeded sample
+    (computed once per module: several modes compare with the same values)."""
+    key = (proc, seed, nevt)
+    if key not in _ORACLE:
+        rnd = I.uniforms(seed, NR[proc], nevt)
+        mom_o, _ = orc.rambo(proc, rnd, ECM[proc])
+        me_o, d_rot = oracle_conditioning(orc, proc, mom_o, nthreads=16)
+        _ORACLE[key] = (mom_o, me_o, d_rot)
+    return _ORACLE[key]
 
 
 def gpu_mask(mg, proc):
@@ -86,9 +99,7 @@ def test_filter_mask(mg, orc, proc):
 @pytest.mark.parametrize("mode", ["fp64", "fp64_unrolled"])
 @pytest.mark.parametrize("proc,nevt", [(1, 1), (1, 33), (1, 16384), (2, 1), (2, 4099), (3, 257), (4, 67)])
 def test_sigmakin_fp64_parity(mg, orc, proc, nevt, mode):
-    rnd = I.uniforms(51 + proc, NR[proc], nevt)
-    mom_o, _ = orc.rambo(proc, rnd, ECM[proc])
-    me_o, d_rot = oracle_conditioning(orc, proc, mom_o)
+    mom_o, me_o, d_rot = oracle_sample(orc, proc, 51 + proc, nevt)
     mask = gpu_mask(mg, proc)
     me_g = host(mg.sigmakin(proc, dev(mom_o), mask, mode=mode))
     rel = np.abs(me_g / me_o - 1)
@@ -96,17 +107,15 @@ def test_sigmakin_fp64_parity(mg, orc, proc, nevt, mode):
 
 
 def check_fp64(rel, d_rot):
-    tol = np.maximum(FP64_REL, 4 * d_rot)
+    tol = fp64_tol(d_rot)
     assert np.all(rel <= tol), (rel.max(), int(np.argmax(rel / tol)))
     assert np.mean(rel > FP64_REL) <= FP64_ILL_FRACTION + 1.0 / len(rel)
 
 
 @pytest.mark.parametrize("mode", ["mixed_simt", "mixed", "mixed_tc", "mixed_unrolled"])
-@pytest.mark.parametrize("proc,nevt", [(1, 16384), (2, 4099), (3, 513), (4, 131)])
+@pytest.mark.parametrize("proc,nevt", [(1, 16384), (2, 4099), (3, 4099), (4, 4099)])
 def test_sigmakin_mixed(mg, orc, proc, nevt, mode):
-    rnd = I.uniforms(61 + proc, NR[proc], nevt)
-    mom_o, _ = orc.rambo(proc, rnd, ECM[proc])
-    me_o, d_rot = oracle_conditioning(orc, proc, mom_o)
+    mom_o, me_o, d_rot = oracle_sample(orc, proc, 61 + proc, nevt)
     mask = gpu_mask(mg, proc)
     me_g = host(mg.sigmakin(proc, dev(mom_o), mask, mode=mode))
     assert np.all(np.isfinite(me_g))
@@ -140,9 +149,9 @@ def test_mask_subset(mg, orc, proc):
     me_g = host(mg.sigmakin(proc, dev(mom_o), dev(sub), mode="fp64"))
     me_u = host(mg.sigmakin(proc, dev(mom_o), dev(sub), mode="fp64_unrolled"))
     ok = want != 0
-    assert np.all(np.abs(me_u[ok] / want[ok] - 1) <= np.maximum(FP64_REL, 4 * d_rot[ok]))
+    assert np.all(np.abs(me_u[ok] / want[ok] - 1) <= fp64_tol(d_rot[ok]))
     rel = np.abs(me_g[ok] / want[ok] - 1)
-    assert np.all(rel <= np.maximum(FP64_REL, 4 * d_rot[ok]))
+    assert np.all(rel <= fp64_tol(d_rot[ok]))
     assert np.all(me_g[~ok] == 0)
 
 
@@ -212,7 +221,7 @@ def test_full_size_sampled(mg, orc, mode):
     me_o, d_rot = oracle_conditioning(orc, 4, np.ascontiguousarray(mom_g))
     rel = np.abs(me_g / me_o - 1)
     if mode == "fp64":
-        assert np.all(rel <= np.maximum(FP64_REL, 4 * d_rot))
+        assert np.all(rel <= fp64_tol(d_rot))
     else:
         assert rel.max() <= MIXED_MAX_REL and np.all(rel[d_rot <= WELL_CONDITIONED] <= MIXED_P999_REL)
     s = host(out)

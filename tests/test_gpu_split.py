@@ -15,7 +15,7 @@ import numpy as np
 import pytest
 import torch
 
-from helpers import oracle_conditioning
+from helpers import MIXED_MAX_REL, MIXED_MEDIAN_REL, fp64_tol, oracle_conditioning
 from paper_2106_12631_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
@@ -90,8 +90,9 @@ def test_graph_replay_and_recapture(mg):
         mg.set_params(alpha_s=0.13)
         got = host(mg.sigmakin_split(proc, mom, mask, mode=mode, me=me, workspace=ws)).copy()
         np.testing.assert_array_equal(got, host(mg.sigmakin(proc, mom, mask, mode=mode)))
-        rel = np.abs(got / a / (0.13 / 0.118) ** 3 - 1)  # |M|^2 ~ alpha_s^3 (FP32 rounding differs)
-        assert np.median(rel) < 1e-6 and rel.max() < 1e-3
+        # |M|^2 ~ alpha_s^3; a ratio of two mixed results, each within the mixed bar
+        rel = np.abs(got / a / (0.13 / 0.118) ** 3 - 1)
+        assert np.median(rel) < 2 * MIXED_MEDIAN_REL and rel.max() < 2 * MIXED_MAX_REL
     finally:
         mg.set_params(**old)
 
@@ -102,7 +103,7 @@ def test_split_fp64_against_oracle(mg, orc):
     mom_o, _ = orc.rambo(proc, rnd, ECM[proc])
     me_o, d_rot = oracle_conditioning(orc, proc, mom_o)
     got = host(mg.sigmakin_split(proc, torch.from_numpy(mom_o).cuda(), gpu_mask(mg, proc), mode="fp64"))
-    assert np.all(np.abs(got / me_o - 1) <= np.maximum(1e-12, 4 * d_rot))
+    assert np.all(np.abs(got / me_o - 1) <= fp64_tol(d_rot))
 
 
 def test_split_errors(mg):
