@@ -61,7 +61,8 @@ struct HsLayout {
   static constexpr int NT = H::NT, EVCAP = H::EVCAP, KP = H::KP, NP = H::NP, MBLK = H::MBLK;
   static constexpr bool TC = CS == CS_TC;
   static constexpr size_t o_proptab = 0;  // {momentum entry, line kind} per propagator
-  static constexpr size_t o_good = align_up(o_proptab + 8 * P::NPROP, 16);
+  static constexpr size_t o_md = align_up(o_proptab + 8 * P::NPROP, 16);  // momentum-entry descriptors (int4)
+  static constexpr size_t o_good = align_up(o_md + 16 * P::NMOM, 16);
   static constexpr size_t o_misc = align_up(o_good + 4 * P::NHEL, 16);
   // mixed mode: {m^2 hi, m^2 lo, m w, 0} of the top and of the Z
   static constexpr size_t o_mconst = align_up(o_misc + 32, 16);
@@ -77,10 +78,6 @@ struct HsLayout {
   static constexpr size_t o_cur = o_U;
   static constexpr size_t o_x = o_U + sizeof(W4<R>) * EVCAP * P::HS_NSLOT;
   static constexpr size_t o_A = o_U;
-  // FP64 momentum sums of phase 1 (the amputated buffer is free then)
-  static constexpr size_t o_Kd = o_x;
-  static_assert(8 * EVCAP * P::NMOM * 4 <= sizeof(W4<R>) * EVCAP * P::HS_XBUFS * P::HS_XCAP,
-                "FP64 sums overflow their scratch");
   static constexpr size_t tileA = 128 * KP * 2;
   static constexpr size_t u_bytes = sizeof(W4<R>) * EVCAP * (P::HS_NSLOT + P::HS_XBUFS * P::HS_XCAP);
   static constexpr size_t a_bytes = TC ? 3 * MBLK * tileA : 0;  // one component's three splits
@@ -302,28 +299,165 @@ __device__ __forceinline__ cx<float> propagator_dfl(const float2* k, int kind, d
   return kind == 1 ? cx<float>(-ai, ar) : cx<float>(ai, -ar);
 }
 
-// Phase 1: momenta; momentum-table entries as signed sums of the external
-// momenta (one thread per (event, component) walks all entries with the leg
-// masks known at compile time: |S| - 1 additions per entry), in FP64 (FP64
-// mode) or double-float (mixed mode), rounded to R and kept unrounded for the
-// propagators; the external wavefunctions (level 0 of the current program)
-// straight from the momenta; then the propagator of every line (one thread
-// per (event, propagator)).
+// Phase 1 of the forward kernels, in three parts:
+//   hs_setup_words   per-CTA constants: {momentum entry, line kind} per
+//                    propagator, a descriptor per momentum-table entry, and in
+//                    the mixed mode {m^2 hi, m^2 lo, m w, 0} of the top and Z;
+//   hs_load_momenta  the CTA's momenta into shared memory: FP64, or in the
+//                    mixed mode each component split into a double-float pair;
+//   hs_tables        (after a barrier) one thread per (event, momentum-table
+//                    entry) sums the entry's signed external momenta — in FP64
+//                    (FP64 mode) or double-float (mixed mode), every leg in leg
+//                    order with coefficient +1, -1 or 0 (adding an exact zero
+//                    changes neither an FP64 sum nor a double-float pair), rounds
+//                    it to R for the currents and forms the propagator factor
+//                    of every line with that momentum from the unrounded sum;
+//                    one thread per (event, external leg variant) builds the
+//                    external wavefunction (level 0 of the current program).
+
+// Descriptor of momentum-table entry j: {legs added, legs subtracted, first
+// propagator on that momentum, second} (-1: none).
+template <class P>
+__device__ __forceinline__ int4 hs_mom_desc(int j) {
+  int4 v = make_int4(0, 0, -1, -1);
+#pragma unroll
+  for (int jj = 0; jj < P::NMOM; ++jj) {
+    if (j != jj) continue;
+    const int legs = P::mom(jj, 1), neg = P::mom(jj, 0) == 1 ? (P::mom(jj, 2) & legs) : 0;
+    v = make_int4(legs & ~neg, neg, P::mom_prop(jj, 0), P::mom_prop(jj, 1));
+  }
+  return v;
+}
+
+template <class P, class R, class L>
+__device__ __forceinline__ void hs_setup_words(unsigned char* smem, const PhysParams& pp) {
+  static_assert(L::NT >= P::NPROP && L::NT >= P::NMOM, "one thread per propagator and per momentum entry");
+  const int tid = threadIdx.x;
+  if (tid < P::NPROP) {
+    int2 v = make_int2(0, 0);
+#pragma unroll
+    for (int j = 0; j < P::NPROP; ++j)
+      if (tid == j) v = make_int2(P::prop(j, 0), P::prop(j, 1));
+    reinterpret_cast<int2*>(smem + L::o_proptab)[tid] = v;
+  }
+  if (tid < P::NMOM) reinterpret_cast<int4*>(smem + L::o_md)[tid] = hs_mom_desc<P>(tid);
+  if constexpr (sizeof(R) == 4) {
+    if (tid < 2) {
+      const double m = tid == 0 ? pp.mt : pp.mz, w = tid == 0 ? pp.wt : pp.wz;
+      const dfl m2 = dfl_split(m * m);
+      reinterpret_cast<float4*>(smem + L::o_mconst)[tid] = make_float4(m2.hi, m2.lo, (float)(m * w), 0.0f);
+    }
+  }
+}
+
+// p[e][leg][mu]: double, or float2 (hi, lo) in the mixed mode (same 8 bytes)
+template <class P, class R, class L>
+__device__ __forceinline__ void hs_load_momenta(unsigned char* smem, const double* __restrict__ mom, int64_t nevt,
+                                                int64_t e0, int nev) {
+  for (int t = threadIdx.x; t < nev * P::NPAR * 4; t += L::NT) {
+    const int e = t % nev, c = t / nev;
+    const double x = mom[(int64_t)c * nevt + e0 + e];
+    if constexpr (sizeof(R) == 4) {
+      const dfl q = dfl_split(x);
+      reinterpret_cast<float2*>(smem + L::o_p)[e * P::NPAR * 4 + c] = make_float2(q.hi, q.lo);
+    } else {
+      reinterpret_cast<double*>(smem + L::o_p)[e * P::NPAR * 4 + c] = x;
+    }
+  }
+}
+
+template <class P, class R, class L>
+__device__ __forceinline__ void hs_tables(unsigned char* smem, const PhysParams& pp, int nev, uint4* curs,
+                                          const Couplings<R>& cp) {
+  constexpr int NT = L::NT, NM = P::NMOM, NPAR = P::NPAR;
+  constexpr int NEXT = P::hs_level(1);  // external variants
+  constexpr int CUR_EV = P::HS_NSLOT * Slots<R, 1>::NPL;
+  constexpr bool DF = sizeof(R) == 4;
+  const int4* md = reinterpret_cast<const int4*>(smem + L::o_md);
+  const int2* prop_tab = reinterpret_cast<const int2*>(smem + L::o_proptab);
+  R* K = reinterpret_cast<R*>(smem + L::o_K);                // [EV][NMOM][4]
+  cx<R>* pr = reinterpret_cast<cx<R>*>(smem + L::o_pr);      // [EV][NPROP]
+  for (int t = threadIdx.x; t < nev * (NM + NEXT); t += NT) {
+    if (t < nev * NM) {
+      const int e = t / NM, j = t - e * NM;
+      const int4 d = md[j];
+      if constexpr (DF) {
+        const float2* q = reinterpret_cast<const float2*>(smem + L::o_p) + e * NPAR * 4;
+        float2 kf[4];
+        float kv[4];
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+          DflSum k;
+          k.first(0.0f, 0.0f);
+#pragma unroll
+          for (int l = 0; l < NPAR; ++l) {
+            const float2 v = q[l * 4 + mu];
+            const float c = (d.x >> l & 1) ? 1.0f : ((d.y >> l & 1) ? -1.0f : 0.0f);
+            k.add(c * v.x, c * v.y);
+          }
+          kf[mu] = make_float2(k.s, k.err);
+          kv[mu] = k.value();
+        }
+        reinterpret_cast<float4*>(K)[e * NM + j] = make_float4(kv[0], kv[1], kv[2], kv[3]);
+        const float4* mc = reinterpret_cast<const float4*>(smem + L::o_mconst);
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int pj = u == 0 ? d.z : d.w;
+          if (pj < 0) continue;
+          const int kind = prop_tab[pj].y;
+          const float4 c = mc[kind == 3 ? 1 : 0];  // {m^2 hi, m^2 lo, m w, 0} of the top / the Z
+          pr[e * P::NPROP + pj] = propagator_dfl(kf, kind, dfl{c.x, c.y}, c.z);
+        }
+      } else {
+        const double* q = reinterpret_cast<const double*>(smem + L::o_p) + e * NPAR * 4;
+        double k[4];
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+          double s = 0.0;
+#pragma unroll
+          for (int l = 0; l < NPAR; ++l) {
+            const double c = (d.x >> l & 1) ? 1.0 : ((d.y >> l & 1) ? -1.0 : 0.0);
+            s += c * q[l * 4 + mu];
+          }
+          k[mu] = s;
+          K[(e * NM + j) * 4 + mu] = R(s);
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int pj = u == 0 ? d.z : d.w;
+          if (pj < 0) continue;
+          pr[e * P::NPROP + pj] = propagator_hs<R>(k, prop_tab[pj].y, pp);
+        }
+      }
+    } else {
+      const int t2 = t - nev * NM, e = t2 / NEXT;
+      const HsItem it = P::hs_items()[t2 - e * NEXT];
+      R k[4];
+#pragma unroll
+      for (int mu = 0; mu < 4; ++mu) {
+        if constexpr (DF) k[mu] = reinterpret_cast<const float2*>(smem + L::o_p)[(e * NPAR + it.a) * 4 + mu].x;
+        else k[mu] = reinterpret_cast<const double*>(smem + L::o_p)[(e * NPAR + it.a) * 4 + mu];
+      }
+      W4<R> o;
+      if (it.type == 0) o = ixxxxx<R>(k, it.flag ? cp.mt : R(0), it.b, it.c);
+      else if (it.type == 1) o = oxxxxx<R>(k, it.flag ? cp.mt : R(0), it.b, it.c);
+      else o = vxxxxx<R>(k, it.b, it.c);
+      Slots<R, P::HS_NSLOT>{curs + e * CUR_EV}.set(it.out, o);
+    }
+  }
+  __syncthreads();
+}
+
+// Phase 1 of the adjoint kernel (grad_hs.cuh): momentum-table entries as signed
+// sums of the external momenta (one thread per (event, component) walks all
+// entries with the leg masks known at compile time: |S| - 1 additions per
+// entry), in FP64 (FP64 mode) or double-float (mixed mode), rounded to R and
+// kept unrounded for the propagators; the external wavefunctions (level 0 of
+// the current program) straight from the momenta; then the propagator of every
+// line (one thread per (event, propagator)).
 template <class P, class R, class L>
 __device__ __forceinline__ void hs_build_tables(unsigned char* smem, const PhysParams& pp, int nev, uint4* curs,
                                                 const Couplings<R>& cp);
-
-template <class P, class R, class L>
-__device__ __forceinline__ void hs_event_tables(unsigned char* smem, const SigArgs& a, int64_t e0, int nev,
-                                                uint4* curs, const Couplings<R>& cp) {
-  auto p = reinterpret_cast<double(*)[P::NPAR][4]>(smem + L::o_p);
-  for (int t = threadIdx.x; t < nev * P::NPAR * 4; t += L::NT) {
-    const int e = t % nev, c = t / nev;
-    p[e][c >> 2][c & 3] = a.mom[(int64_t)c * a.nevt + e0 + e];
-  }
-  __syncthreads();
-  hs_build_tables<P, R, L>(smem, a.pp, nev, curs, cp);
-}
 
 // the tables from the momenta already in shared memory
 template <class P, class R, class L>
@@ -559,34 +693,22 @@ __device__ __forceinline__ void hs_sigmakin_body(const SigArgs& a, const Couplin
   uint4* curs = reinterpret_cast<uint4*>(smem + L::o_cur);
   uint4* xbufs = reinterpret_cast<uint4*>(smem + L::o_x);
   constexpr int CUR_EV = P::HS_NSLOT * Slots<R, 1>::NPL, X_EV = P::HS_XCAP * Slots<R, 1>::NPL;
-  const int tid = threadIdx.x;
-  if (tid < P::NPROP) {
-    int2 v = make_int2(0, 0);
-#pragma unroll
-    for (int j = 0; j < P::NPROP; ++j)
-      if (tid == j) v = make_int2(P::prop(j, 0), P::prop(j, 1));
-    reinterpret_cast<int2*>(smem + L::o_proptab)[tid] = v;
-  }
-  if constexpr (sizeof(R) == 4) {
-    if (tid < 2) {
-      const double m = tid == 0 ? a.pp.mt : a.pp.mz, w = tid == 0 ? a.pp.wt : a.pp.wz;
-      const dfl m2 = dfl_split(m * m);
-      reinterpret_cast<float4*>(smem + L::o_mconst)[tid] = make_float4(m2.hi, m2.lo, (float)(m * w), 0.0f);
-    }
-  }
-  // good helicities: one ballot word per 32 helicities in misc[2..3]
-  static_assert(P::NHEL <= 64 && NT >= P::NHEL, "helicity ballot layout");
-  const bool hgood = tid < P::NHEL && a.mask[tid] != 0;
-  const unsigned hb = __ballot_sync(0xffffffffu, hgood);
-  if (tid < P::NHEL && (tid & 31) == 0) misc[2 + (tid >> 5)] = (int)hb;
+  const int tid = threadIdx.x, lane = tid & 31;
+  hs_setup_words<P, R, L>(smem, a.pp);
   // vt[S][ihel]: variant index of leg set S for helicity ihel (generated table)
   static_assert(((1 << P::NPAR) * P::NHEL) % 16 == 0, "variant table copied in 16-byte words");
   for (int i = tid; i < (1 << P::NPAR) * P::NHEL / 16; i += NT)
     reinterpret_cast<uint4*>(vtab)[i] = reinterpret_cast<const uint4*>(P::hs_variants())[i];
-  __syncthreads();
+  // good helicities: every warp ballots the mask itself (32 helicities per
+  // word), so the events and their momenta are known before any barrier;
   // good[] in helicity order (read only after later barriers)
-  const unsigned w0 = (unsigned)misc[2], w1 = P::NHEL > 32 ? (unsigned)misc[3] : 0u;
-  if (hgood) good[__popc(hb & ((1u << (tid & 31)) - 1u)) + (tid >= 32 ? __popc(w0) : 0)] = tid;
+  static_assert(P::NHEL <= 64 && NT >= P::NHEL, "helicity ballot layout");
+  const unsigned w0 = __ballot_sync(0xffffffffu, lane < P::NHEL && a.mask[lane] != 0);
+  const unsigned w1 = P::NHEL > 32 ? __ballot_sync(0xffffffffu, lane + 32 < P::NHEL && a.mask[lane + 32] != 0) : 0u;
+  if (tid < P::NHEL) {
+    const unsigned w = tid < 32 ? w0 : w1, bit = 1u << (tid & 31);
+    if (w & bit) good[__popc(w & (bit - 1u)) + (tid >= 32 ? __popc(w0) : 0)] = tid;
+  }
   const int ng = __popc(w0) + __popc(w1);
   const int ev = ng > 0 ? min(L::EVCAP, NT / ng) : C::EVMIN;
   const int64_t e0 = first + (int64_t)blockIdx.x * ev;
@@ -627,7 +749,9 @@ __device__ __forceinline__ void hs_sigmakin_body(const SigArgs& a, const Couplin
     __syncthreads();
   } else {
     // 1. momenta and per-event tables
-    hs_event_tables<P, R, L>(smem, a, e0, nev, curs, cp);
+    hs_load_momenta<P, R, L>(smem, a.mom, a.nevt, e0, nev);
+    __syncthreads();
+    hs_tables<P, R, L>(smem, a.pp, nev, curs, cp);
     if constexpr (L::TC) {
       tc::fence_after_sync();
       tmem = static_cast<uint32_t>(misc[1]);
@@ -694,10 +818,21 @@ __device__ __forceinline__ void hs_sigmakin_body(const SigArgs& a, const Couplin
       tc::tmem_dealloc(tmem, L::TMEM_COLS);
     }
   }
-  if (tid < nev) {
+  // fixed-order FP64 helicity sum per event: eight lanes per event each add
+  // every eighth helicity in order, then a butterfly over the eight lanes
+  // (addition commutes, so every lane ends with the same bits)
+  for (int b = 0; b < nev * 8; b += NT) {
+    const int t = b + tid, e = t >> 3, q = t & 7;
     double sum = 0.0;
-    for (int k = 0; k < ng; ++k) sum += sm2[tid * ng + k];
-    a.me[e0 + tid] = sum * P::NORM;
+    if (t < nev * 8) {
+#pragma unroll
+      for (int i = 0; i < (P::NHEL + 7) / 8; ++i)
+        if (q + 8 * i < ng) sum += sm2[e * ng + q + 8 * i];
+    }
+    sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+    sum += __shfl_xor_sync(0xffffffffu, sum, 2);
+    sum += __shfl_xor_sync(0xffffffffu, sum, 4);
+    if (t < nev * 8 && q == 0) a.me[e0 + e] = sum * P::NORM;
   }
   // 5. helicity and colour-flow choices (batched entry point)
   if (a.hel_out || a.col_out) {

@@ -23,13 +23,13 @@ template <class P, class R>
 struct HsSplitA {
   static constexpr int NT = 128, EV = 4, CTAS = 3;
   static constexpr size_t o_proptab = 0;
-  static constexpr size_t o_mconst = align_up(o_proptab + 8 * P::NPROP, 16);
+  static constexpr size_t o_md = align_up(o_proptab + 8 * P::NPROP, 16);
+  static constexpr size_t o_mconst = align_up(o_md + 16 * P::NMOM, 16);
   static constexpr size_t o_p = align_up(o_mconst + 32, 16);
   static constexpr size_t o_K = align_up(o_p + 8 * EV * P::NPAR * 4, 16);
   static constexpr size_t o_pr = align_up(o_K + sizeof(R) * EV * P::NMOM * 4, 16);
   static constexpr size_t o_cur = align_up(o_pr + 2 * sizeof(R) * EV * P::NPROP, 16);
-  static constexpr size_t o_Kd = o_cur + sizeof(W4<R>) * EV * P::HS_NSLOT;  // FP64 / double-float sums
-  static constexpr size_t bytes = o_Kd + 8 * EV * P::NMOM * 4;
+  static constexpr size_t bytes = o_cur + sizeof(W4<R>) * EV * P::HS_NSLOT;
   static_assert(bytes <= 232448, "shared memory per CTA above the 227 KB limit");
 };
 
@@ -44,17 +44,11 @@ __global__ void __launch_bounds__(HsSplitA<P, R>::NT, HsSplitA<P, R>::CTAS)
   const int64_t e0 = first + (int64_t)blockIdx.x * L::EV;
   if (e0 >= last) return;
   const int nev = (int)min((int64_t)L::EV, last - e0);
-  for (int j = tid; j < P::NPROP; j += NT)
-    reinterpret_cast<int2*>(smem + L::o_proptab)[j] = make_int2(P::prop(j, 0), P::prop(j, 1));
-  if constexpr (sizeof(R) == 4) {
-    if (tid < 2) {
-      const double m = tid == 0 ? a.pp.mt : a.pp.mz, w = tid == 0 ? a.pp.wt : a.pp.wz;
-      const dfl m2 = dfl_split(m * m);
-      reinterpret_cast<float4*>(smem + L::o_mconst)[tid] = make_float4(m2.hi, m2.lo, (float)(m * w), 0.0f);
-    }
-  }
   uint4* curs = reinterpret_cast<uint4*>(smem + L::o_cur);
-  hs_event_tables<P, R, L>(smem, a, e0, nev, curs, cp);  // its first barrier covers the writes above
+  hs_setup_words<P, R, L>(smem, a.pp);
+  hs_load_momenta<P, R, L>(smem, a.mom, a.nevt, e0, nev);
+  __syncthreads();
+  hs_tables<P, R, L>(smem, a.pp, nev, curs, cp);
   const R* Kall = reinterpret_cast<const R*>(smem + L::o_K);
   const cx<R>* prall = reinterpret_cast<const cx<R>*>(smem + L::o_pr);
   const HsItem* items = P::hs_items();
