@@ -19,6 +19,8 @@
 //   4. colour sum (CUDA cores, or tcgen05 as in sigmakin.cuh) and the
 //      fixed-order FP64 helicity sum.
 #pragma once
+#include <type_traits>
+
 #include "sigmakin.cuh"
 
 namespace mg {
@@ -28,6 +30,9 @@ namespace mg {
 #endif
 #ifndef MG_HS_CTAS
 #define MG_HS_CTAS 2  // resident CTAs per SM the shared-memory budget is split for (24+ colour flows)
+#endif
+#ifndef MG_HS_EVENT_SYNC
+#define MG_HS_EVENT_SYNC 0  // 1: per-event barrier groups (HsGroup) instead of CTA barriers
 #endif
 #ifndef MG_HS_CTAS_SMALL
 #define MG_HS_CTAS_SMALL 3  // the same below 24 colour flows (smaller variant sets per event)
@@ -67,7 +72,9 @@ struct HsLayout {
   // mixed mode: {m^2 hi, m^2 lo, m w, 0} of the top and of the Z
   static constexpr size_t o_mconst = align_up(o_misc + 32, 16);
   static constexpr size_t o_p = align_up(o_mconst + 32, 16);
-  static constexpr size_t o_K = align_up(o_p + 8 * EVCAP * P::NPAR * 4, 16);
+  // the next group's momenta (FP64), copied asynchronously while this group runs
+  static constexpr size_t o_ps = align_up(o_p + 8 * EVCAP * P::NPAR * 4, 16);
+  static constexpr size_t o_K = align_up(o_ps + 8 * EVCAP * P::NPAR * 4, 16);
   static constexpr size_t o_pr = align_up(o_K + sizeof(R) * EVCAP * P::NMOM * 4, 16);
   static constexpr size_t o_m2 = align_up(o_pr + 2 * sizeof(R) * EVCAP * P::NPROP, 16);
   // variant of a leg set for a helicity: vt[S * NHEL + ihel]
@@ -189,6 +196,17 @@ __host__ __device__ constexpr bool colour_matrix_symmetric() {
       if (P::cnum(i, j) != P::cnum(j, i)) return false;
   return true;
 }
+// f(std::integral_constant<int, i>) for i = B .. E - 1: indices that are
+// compile-time constants by construction (the colour matrix entries below are
+// then immediates, whatever the unroller decides inside a large loop body)
+template <int B, int E, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+  if constexpr (B < E) {
+    f(std::integral_constant<int, B>{});
+    static_for<B + 1, E>(f);
+  }
+}
+
 template <class P, class R>
 __device__ __forceinline__ R colour_sum_sym(const cx<R>* J) {
   static_assert(colour_matrix_symmetric<P>(), "colour matrix must be symmetric");
@@ -197,32 +215,34 @@ __device__ __forceinline__ R colour_sum_sym(const cx<R>* J) {
     // FP32: the real and imaginary parts side by side in the paired FP32
     // instructions (one FFMA2 per matrix entry instead of two FFMAs)
     float2 tot = make_float2(0.0f, 0.0f);
-#pragma unroll
-    for (int i = 0; i < NC; ++i) {
-      const float cii = (float)P::cnum(i, i);
+    static_for<0, NC>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      constexpr float cii = (float)P::cnum(i, i);
       float2 u = __fmul2_rn(make_float2(cii, cii), make_float2(J[i].re, J[i].im));
-#pragma unroll
-      for (int j = i + 1; j < NC; ++j) {
-        if (P::cnum(i, j) == 0) continue;
-        const float c = (float)(2 * P::cnum(i, j));
-        u = __ffma2_rn(make_float2(c, c), make_float2(J[j].re, J[j].im), u);
-      }
+      static_for<i + 1, NC>([&](auto Jc) {
+        constexpr int j = decltype(Jc)::value;
+        if constexpr (P::cnum(i, j) != 0) {
+          constexpr float c = (float)(2 * P::cnum(i, j));
+          u = __ffma2_rn(make_float2(c, c), make_float2(J[j].re, J[j].im), u);
+        }
+      });
       tot = __ffma2_rn(make_float2(J[i].re, J[i].im), u, tot);
-    }
+    });
     return (tot.x + tot.y) / R(P::CDEN);
   }
   R sum = R(0);
-#pragma unroll
-  for (int i = 0; i < NC; ++i) {
+  static_for<0, NC>([&](auto I) {
+    constexpr int i = decltype(I)::value;
     R ur = R(P::cnum(i, i)) * J[i].re, ui = R(P::cnum(i, i)) * J[i].im;
-#pragma unroll
-    for (int j = i + 1; j < NC; ++j) {
-      if (P::cnum(i, j) == 0) continue;
-      ur += R(2 * P::cnum(i, j)) * J[j].re;
-      ui += R(2 * P::cnum(i, j)) * J[j].im;
-    }
+    static_for<i + 1, NC>([&](auto Jc) {
+      constexpr int j = decltype(Jc)::value;
+      if constexpr (P::cnum(i, j) != 0) {
+        ur += R(2 * P::cnum(i, j)) * J[j].re;
+        ui += R(2 * P::cnum(i, j)) * J[j].im;
+      }
+    });
     sum = fmac(J[i].re, ur, fmac(J[i].im, ui, sum));
-  }
+  });
   return sum / R(P::CDEN);
 }
 
@@ -366,10 +386,102 @@ __device__ __forceinline__ void hs_load_momenta(unsigned char* smem, const doubl
   }
 }
 
+// A later group's momenta, copied asynchronously (cp.async, 8 bytes per
+// component) into the staging buffer in the layout of p; the copies of each
+// thread complete at its cp_async_wait_all, and hs_convert_momenta (after a
+// barrier) turns them into p.
+template <class P, class L>
+__device__ __forceinline__ void hs_prefetch_momenta(unsigned char* smem, const double* __restrict__ mom, int64_t nevt,
+                                                    int64_t e0, int nev) {
+  const uint32_t st = tc::smem_addr(smem + L::o_ps);
+  for (int t = threadIdx.x; t < nev * P::NPAR * 4; t += L::NT) {
+    const int e = t % nev, c = t / nev;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(st + 8u * (uint32_t)(e * P::NPAR * 4 + c)),
+                 "l"(mom + (int64_t)c * nevt + e0 + e)
+                 : "memory");
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 template <class P, class R, class L>
-__device__ __forceinline__ void hs_tables(unsigned char* smem, const PhysParams& pp, int nev, uint4* curs,
+__device__ __forceinline__ void hs_convert_momenta(unsigned char* smem, int nev) {
+  const double* st = reinterpret_cast<const double*>(smem + L::o_ps);
+  for (int t = threadIdx.x; t < nev * P::NPAR * 4; t += L::NT) {
+    const double x = st[t];
+    if constexpr (sizeof(R) == 4) {
+      const dfl q = dfl_split(x);
+      reinterpret_cast<float2*>(smem + L::o_p)[t] = make_float2(q.hi, q.lo);
+    } else {
+      reinterpret_cast<double*>(smem + L::o_p)[t] = x;
+    }
+  }
+}
+
+// Barrier domain of the phases after the CTA's first barrier: the threads of
+// one event, or of the events that share one warp, synchronise only among
+// themselves, so the events of a CTA move through their phases independently.
+// With ng good helicities (thread = (event, good helicity)): ng = 64 -> one
+// event per two warps on a named barrier; ng = 32 -> one event per warp; ng a
+// divisor of 32 -> the 32 / ng events of one warp; otherwise, and for the
+// tensor-core colour sum (one MMA spans several events), the whole CTA.
+struct HsGroup {
+  int kind;      // 0 CTA barrier, 1 warp, 2 named barrier
+  int tpg;       // threads per group
+  int j;         // thread index within the group
+  int ev0, nev;  // the group's events (CTA-local)
+  int id;        // named barrier (kind 2)
+  __device__ __forceinline__ void sync() const {
+    if (kind == 0) __syncthreads();
+    else if (kind == 1) __syncwarp();
+    else named_sync();
+  }
+  // barrier ids as immediates, so only the ids in use are reserved
+  __device__ __forceinline__ void named_sync() const {
+    switch (id) {
+      case 1: asm volatile("bar.sync 1, 64;" ::: "memory"); break;
+      case 2: asm volatile("bar.sync 2, 64;" ::: "memory"); break;
+      case 3: asm volatile("bar.sync 3, 64;" ::: "memory"); break;
+      case 4: asm volatile("bar.sync 4, 64;" ::: "memory"); break;
+      case 5: asm volatile("bar.sync 5, 64;" ::: "memory"); break;
+      case 6: asm volatile("bar.sync 6, 64;" ::: "memory"); break;
+      case 7: asm volatile("bar.sync 7, 64;" ::: "memory"); break;
+      default: asm volatile("bar.sync 8, 64;" ::: "memory"); break;
+    }
+  }
+};
+
+template <int NT>
+__device__ __forceinline__ HsGroup hs_group(bool cta_only, int ng, int ev, int nev) {
+  static_assert(NT % 64 == 0 && NT / 64 <= 8, "named barriers 1..8 for the two-warp groups");
+  HsGroup g;
+  int epg;
+  if (cta_only || ng < 1 || !(ng == 64 || 32 % ng == 0)) {
+    g.kind = 0;
+    g.tpg = NT;
+    epg = ev;
+  } else if (ng == 64) {
+    g.kind = 2;
+    g.tpg = 64;
+    epg = 1;
+  } else {
+    g.kind = 1;
+    g.tpg = 32;
+    epg = 32 / ng;
+  }
+  const int grp = (int)threadIdx.x / g.tpg;
+  g.j = (int)threadIdx.x - grp * g.tpg;
+  g.ev0 = grp * epg;
+  g.nev = max(0, min(epg, nev - g.ev0));
+  g.id = 1 + grp;
+  return g;
+}
+
+template <class P, class R, class L>
+__device__ __forceinline__ void hs_tables(unsigned char* smem, const PhysParams& pp, const HsGroup& grp, uint4* curs,
                                           const Couplings<R>& cp) {
-  constexpr int NT = L::NT, NM = P::NMOM, NPAR = P::NPAR;
+  constexpr int NM = P::NMOM, NPAR = P::NPAR;
   constexpr int NEXT = P::hs_level(1);  // external variants
   constexpr int CUR_EV = P::HS_NSLOT * Slots<R, 1>::NPL;
   constexpr bool DF = sizeof(R) == 4;
@@ -377,9 +489,10 @@ __device__ __forceinline__ void hs_tables(unsigned char* smem, const PhysParams&
   const int2* prop_tab = reinterpret_cast<const int2*>(smem + L::o_proptab);
   R* K = reinterpret_cast<R*>(smem + L::o_K);                // [EV][NMOM][4]
   cx<R>* pr = reinterpret_cast<cx<R>*>(smem + L::o_pr);      // [EV][NPROP]
-  for (int t = threadIdx.x; t < nev * (NM + NEXT); t += NT) {
+  const int nev = grp.nev;
+  for (int t = grp.j; t < nev * (NM + NEXT); t += grp.tpg) {
     if (t < nev * NM) {
-      const int e = t / NM, j = t - e * NM;
+      const int el = t / NM, j = t - el * NM, e = grp.ev0 + el;
       const int4 d = md[j];
       if constexpr (DF) {
         const float2* q = reinterpret_cast<const float2*>(smem + L::o_p) + e * NPAR * 4;
@@ -430,8 +543,8 @@ __device__ __forceinline__ void hs_tables(unsigned char* smem, const PhysParams&
         }
       }
     } else {
-      const int t2 = t - nev * NM, e = t2 / NEXT;
-      const HsItem it = P::hs_items()[t2 - e * NEXT];
+      const int t2 = t - nev * NM, el = t2 / NEXT, e = grp.ev0 + el;
+      const HsItem it = P::hs_items()[t2 - el * NEXT];
       R k[4];
 #pragma unroll
       for (int mu = 0; mu < 4; ++mu) {
@@ -445,7 +558,7 @@ __device__ __forceinline__ void hs_tables(unsigned char* smem, const PhysParams&
       Slots<R, P::HS_NSLOT>{curs + e * CUR_EV}.set(it.out, o);
     }
   }
-  __syncthreads();
+  grp.sync();
 }
 
 // Phase 1 of the adjoint kernel (grad_hs.cuh): momentum-table entries as signed
@@ -711,14 +824,18 @@ __device__ __forceinline__ void hs_sigmakin_body(const SigArgs& a, const Couplin
   }
   const int ng = __popc(w0) + __popc(w1);
   const int ev = ng > 0 ? min(L::EVCAP, NT / ng) : C::EVMIN;
-  const int64_t e0 = first + (int64_t)blockIdx.x * ev;
-  if (e0 >= last) return;
-  const int nev = (int)min((int64_t)ev, last - e0);
+  // groups of ev events, g = blockIdx.x, blockIdx.x + gridDim.x, ...: one
+  // group per CTA for a grid of all groups, several for a persistent grid
+  const int ngrp = (int)((last - first + ev - 1) / ev);
+  if ((int)blockIdx.x >= ngrp) return;
   if (ng == 0) {
-    if (tid < nev) {
-      a.me[e0 + tid] = 0.0;
-      if (a.hel_out) a.hel_out[e0 + tid] = -1;
-      if (a.col_out) a.col_out[e0 + tid] = -1;
+    for (int g = blockIdx.x; g < ngrp; g += gridDim.x) {
+      const int64_t e0 = first + (int64_t)g * ev;
+      if (tid < (int)min((int64_t)ev, last - e0)) {
+        a.me[e0 + tid] = 0.0;
+        if (a.hel_out) a.hel_out[e0 + tid] = -1;
+        if (a.col_out) a.col_out[e0 + tid] = -1;
+      }
     }
     return;
   }
@@ -735,114 +852,142 @@ __device__ __forceinline__ void hs_sigmakin_body(const SigArgs& a, const Couplin
   }
   const R* Kall = reinterpret_cast<const R*>(smem + L::o_K);
   const HsItem* items = P::hs_items();
-  if constexpr (FROM_RECORDS) {
-    // 1-2. the events' current variants and momentum tables from their records
-    using RC = HsRecord<P, R>;
-    const uint4* in = rec + (e0 - first) * RC::WORDS;
-    uint4* ks = reinterpret_cast<uint4*>(smem + L::o_K);
-    for (int t = tid; t < nev * RC::WORDS; t += NT) {
-      const int e = t / RC::WORDS, w = t - e * RC::WORDS;
-      const uint4 v = __ldcs(in + t);  // read once: streaming
-      if (w < RC::CUR) curs[e * CUR_EV + w] = v;
-      else ks[e * RC::KW + (w - RC::CUR)] = v;
-    }
-    __syncthreads();
-  } else {
-    // 1. momenta and per-event tables
-    hs_load_momenta<P, R, L>(smem, a.mom, a.nevt, e0, nev);
-    __syncthreads();
-    hs_tables<P, R, L>(smem, a.pp, nev, curs, cp);
-    if constexpr (L::TC) {
-      tc::fence_after_sync();
-      tmem = static_cast<uint32_t>(misc[1]);
-    }
-    const cx<R>* prall = reinterpret_cast<const cx<R>*>(smem + L::o_pr);
-    // 2. current variants, level by level (level 0, the external wavefunctions,
-    //    came with phase 1); consecutive threads take consecutive items of one event
-#pragma unroll
-    for (int l = 1; l < P::HS_NLEVEL; ++l) {
-      const int i0 = P::hs_level(l), ni = P::hs_level(l + 1) - i0, n = ni * nev;
-      for (int t = tid; t < n; t += NT) {
-        const int e = t / ni;
-        const HsItem it = items[i0 + t - e * ni];
-        hs_item<P, R>(it, Slots<R, P::HS_NSLOT>{curs + e * CUR_EV}, Kall + e * P::NMOM * 4, prall + e * P::NPROP,
-                      cp);
+  if constexpr (!FROM_RECORDS) {
+    // the first group's momenta; later groups' arrive by prefetch
+    const int64_t e0 = first + (int64_t)blockIdx.x * ev;
+    hs_load_momenta<P, R, L>(smem, a.mom, a.nevt, e0, (int)min((int64_t)ev, last - e0));
+  }
+  __syncthreads();
+  if constexpr (L::TC) {
+    tc::fence_after_sync();
+    tmem = static_cast<uint32_t>(misc[1]);
+  }
+#pragma unroll 1
+  for (int g = blockIdx.x; g < ngrp; g += gridDim.x) {
+    // e0 and nev are formed again after the contractions (fewer live registers)
+    const int nev = (int)min((int64_t)ev, last - (first + (int64_t)g * ev));
+    const HsGroup grp = hs_group<NT>(L::TC || !MG_HS_EVENT_SYNC, ng, ev, nev);
+    if constexpr (FROM_RECORDS) {
+      // 1-2. the events' current variants and momentum tables from their records
+      using RC = HsRecord<P, R>;
+      const uint4* in = rec + (int64_t)g * ev * RC::WORDS;
+      uint4* ks = reinterpret_cast<uint4*>(smem + L::o_K);
+      for (int t = tid; t < nev * RC::WORDS; t += NT) {
+        const int e = t / RC::WORDS, w = t - e * RC::WORDS;
+        const uint4 v = __ldcs(in + t);  // read once: streaming
+        if (w < RC::CUR) curs[e * CUR_EV + w] = v;
+        else ks[e * RC::KW + (w - RC::CUR)] = v;
       }
+      __syncthreads();
+    } else {
+      // the next group's momenta: copied during this group's phases 1-2 and
+      // converted after the last current level (p is free once the tables are built)
+      const int gn = g + gridDim.x;
+      const int64_t e0n = first + (int64_t)gn * ev;
+      const int nevn = gn < ngrp ? (int)min((int64_t)ev, last - e0n) : 0;
+      if (nevn > 0) hs_prefetch_momenta<P, L>(smem, a.mom, a.nevt, e0n, nevn);
+      // 1. per-event tables (the momenta are in p)
+      hs_tables<P, R, L>(smem, a.pp, grp, curs, cp);
+      const cx<R>* prall = reinterpret_cast<const cx<R>*>(smem + L::o_pr);
+      // 2. current variants, level by level (level 0, the external wavefunctions,
+      //    came with phase 1); consecutive threads take consecutive items of one event
+#pragma unroll
+      for (int l = 1; l < P::HS_NLEVEL; ++l) {
+        const int i0 = P::hs_level(l), ni = P::hs_level(l + 1) - i0, n = ni * grp.nev;
+        for (int t = grp.j; t < n; t += grp.tpg) {
+          const int el = t / ni, e = grp.ev0 + el;
+          const HsItem it = items[i0 + t - el * ni];
+          hs_item<P, R>(it, Slots<R, P::HS_NSLOT>{curs + e * CUR_EV}, Kall + e * P::NMOM * 4, prall + e * P::NPROP,
+                        cp);
+        }
+        if (l == P::HS_NLEVEL - 1) {
+          cp_async_wait_all();
+          __syncthreads();
+          if (nevn > 0) hs_convert_momenta<P, R, L>(smem, nevn);
+        } else {
+          grp.sync();
+        }
+      }
+    }
+    // 3. amputated currents chunk by chunk into two alternating buffers: in
+    //    interval c every thread first builds its share of chunk c, then
+    //    contracts chunk c - 1 for its (event, helicity) (J in registers), so the
+    //    latency of the item work hides behind other warps' contractions
+    const bool active = tid < nev * ng;
+    const int e = active ? tid / ng : 0;
+    const int ih = good[active ? tid - e * ng : 0];
+    constexpr int XBUF = L::EVCAP * X_EV;  // one chunk buffer, all events
+    cx<R> J[NC];
+#pragma unroll
+    for (int s = 0; s < NC; ++s) J[s] = cx<R>(R(0), R(0));
+#pragma unroll 1
+    for (int c = 0; c <= P::HS_NXCHUNK; ++c) {
+      if (c < P::HS_NXCHUNK) {
+        uint4* xb = xbufs + (P::HS_XBUFS == 2 ? (c & 1) * XBUF : 0);
+        const int i0 = P::hs_xitem(c), ni = P::hs_xitem(c + 1) - i0, n = ni * grp.nev;
+        for (int t = grp.j; t < n; t += grp.tpg) {
+          const int exl = t / ni, ex = grp.ev0 + exl;
+          const HsItem it = items[i0 + t - exl * ni];
+          hs_xitem<P, R>(it, Slots<R, P::HS_NSLOT>{curs + ex * CUR_EV}, Slots<R, P::HS_XCAP>{xb + ex * X_EV},
+                         Kall + ex * P::NMOM * 4, cp);
+        }
+      }
+      if (c > 0) {
+        const uint4* xb = xbufs + (P::HS_XBUFS == 2 ? ((c - 1) & 1) * XBUF : 0);
+        P::template hs_contract<R>(c - 1, Slots<R, P::HS_NSLOT>{curs + e * CUR_EV},
+                                   Slots<R, P::HS_XCAP>{const_cast<uint4*>(xb) + e * X_EV}, vtab + ih, J);
+      }
+      if (c < P::HS_NXCHUNK) grp.sync();
+    }
+    // 4. colour sum and helicity sum
+    double m2;
+    if constexpr (L::TC) {
+      __syncthreads();  // the A tiles overwrite the current variants
+      m2 = (double)colour_sum_tc_regs<P, L>(smem, J, tmem, mbar);
+    } else {
+      m2 = (double)colour_sum_sym<P, R>(J);
+    }
+    sm2[tid] = active ? m2 : 0.0;
+    if constexpr (L::TC) tc::fence_before_sync();
+    grp.sync();
+    const int64_t e0 = first + (int64_t)g * ev;
+    // fixed-order FP64 helicity sum per event: eight lanes per event each add
+    // every eighth helicity in order, then a butterfly over the eight lanes
+    // (addition commutes, so every lane ends with the same bits); sm2 is next
+    // written at the end of the next group, after several barriers
+    for (int b = 0; b < grp.nev * 8; b += grp.tpg) {
+      const int t = b + grp.j, eh = grp.ev0 + (t >> 3), q = t & 7;
+      double sum = 0.0;
+      if (t < grp.nev * 8) {
+#pragma unroll
+        for (int i = 0; i < (P::NHEL + 7) / 8; ++i)
+          if (q + 8 * i < ng) sum += sm2[eh * ng + q + 8 * i];
+      }
+      sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+      sum += __shfl_xor_sync(0xffffffffu, sum, 2);
+      sum += __shfl_xor_sync(0xffffffffu, sum, 4);
+      if (t < grp.nev * 8 && q == 0) a.me[e0 + eh] = sum * P::NORM;
+    }
+    // 5. helicity and colour-flow choices (batched entry point), once every
+    //    group of the CTA is done with the union region; the closing barrier
+    //    keeps the next group's currents out of it until the choices are made
+    if (a.hel_out || a.col_out) {
+      __syncthreads();
+      if (a.col_out) {
+        R* wj = reinterpret_cast<R*>(smem + L::o_U) + tid * HsChoice<P, R>::NCP;  // the union is dead here
+#pragma unroll
+        for (int s = 0; s < NC; ++s) wj[s] = active ? J[s].re * J[s].re + J[s].im * J[s].im : R(0);
+        __syncthreads();
+      }
+      hs_choices<P, R, L>(smem, a, e0, nev, ng, good, sm2);
       __syncthreads();
     }
   }
-  // 3. amputated currents chunk by chunk into two alternating buffers: in
-  //    interval c every thread first builds its share of chunk c, then
-  //    contracts chunk c - 1 for its (event, helicity) (J in registers), so the
-  //    latency of the item work hides behind other warps' contractions
-  const bool active = tid < nev * ng;
-  const int e = active ? tid / ng : 0;
-  const int ih = good[active ? tid - e * ng : 0];
-  constexpr int XBUF = L::EVCAP * X_EV;  // one chunk buffer, all events
-  cx<R> J[NC];
-#pragma unroll
-  for (int s = 0; s < NC; ++s) J[s] = cx<R>(R(0), R(0));
-#pragma unroll 1
-  for (int c = 0; c <= P::HS_NXCHUNK; ++c) {
-    if (c < P::HS_NXCHUNK) {
-      uint4* xb = xbufs + (P::HS_XBUFS == 2 ? (c & 1) * XBUF : 0);
-      const int i0 = P::hs_xitem(c), ni = P::hs_xitem(c + 1) - i0, n = ni * nev;
-      for (int t = tid; t < n; t += NT) {
-        const int ex = t / ni;
-        const HsItem it = items[i0 + t - ex * ni];
-        hs_xitem<P, R>(it, Slots<R, P::HS_NSLOT>{curs + ex * CUR_EV}, Slots<R, P::HS_XCAP>{xb + ex * X_EV},
-                       Kall + ex * P::NMOM * 4, cp);
-      }
-    }
-    if (c > 0) {
-      const uint4* xb = xbufs + (P::HS_XBUFS == 2 ? ((c - 1) & 1) * XBUF : 0);
-      P::template hs_contract<R>(c - 1, Slots<R, P::HS_NSLOT>{curs + e * CUR_EV},
-                                 Slots<R, P::HS_XCAP>{const_cast<uint4*>(xb) + e * X_EV}, vtab + ih, J);
-    }
-    if (c < P::HS_NXCHUNK) __syncthreads();
-  }
-  // 4. colour sum and helicity sum
-  double m2;
-  if constexpr (L::TC) {
-    __syncthreads();  // the A tiles overwrite the current variants
-    m2 = (double)colour_sum_tc_regs<P, L>(smem, J, tmem, mbar);
-  } else {
-    m2 = (double)colour_sum_sym<P, R>(J);
-  }
-  sm2[tid] = active ? m2 : 0.0;
-  if constexpr (L::TC) tc::fence_before_sync();
-  __syncthreads();
   if constexpr (L::TC) {
     if (tid < 32) {
       tc::fence_after_sync();
       tc::tmem_dealloc(tmem, L::TMEM_COLS);
     }
-  }
-  // fixed-order FP64 helicity sum per event: eight lanes per event each add
-  // every eighth helicity in order, then a butterfly over the eight lanes
-  // (addition commutes, so every lane ends with the same bits)
-  for (int b = 0; b < nev * 8; b += NT) {
-    const int t = b + tid, e = t >> 3, q = t & 7;
-    double sum = 0.0;
-    if (t < nev * 8) {
-#pragma unroll
-      for (int i = 0; i < (P::NHEL + 7) / 8; ++i)
-        if (q + 8 * i < ng) sum += sm2[e * ng + q + 8 * i];
-    }
-    sum += __shfl_xor_sync(0xffffffffu, sum, 1);
-    sum += __shfl_xor_sync(0xffffffffu, sum, 2);
-    sum += __shfl_xor_sync(0xffffffffu, sum, 4);
-    if (t < nev * 8 && q == 0) a.me[e0 + e] = sum * P::NORM;
-  }
-  // 5. helicity and colour-flow choices (batched entry point)
-  if (a.hel_out || a.col_out) {
-    if (a.col_out) {
-      R* wj = reinterpret_cast<R*>(smem + L::o_U) + tid * HsChoice<P, R>::NCP;  // the union is dead here
-#pragma unroll
-      for (int s = 0; s < NC; ++s) wj[s] = active ? J[s].re * J[s].re + J[s].im * J[s].im : R(0);
-      __syncthreads();
-    }
-    hs_choices<P, R, L>(smem, a, e0, nev, ng, good, sm2);
   }
 }
 

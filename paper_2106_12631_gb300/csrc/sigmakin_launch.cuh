@@ -17,14 +17,31 @@ cudaError_t launch_sigmakin_variant(const SigArgs& a, const Couplings<R>& cp, in
   return cudaGetLastError();
 }
 
+// The helicity-shared kernel runs persistent: at most as many CTAs as are
+// resident at once (SMs x CTAs per SM, cached per device), each looping over
+// groups of events (the CTA's group count follows from the mask on the device).
 template <class P, class R, int CS>
 cudaError_t launch_sigmakin_hs_variant(const SigArgs& a, const Couplings<R>& cp, int64_t grid, cudaStream_t s) {
   using L = HsLayout<P, R, CS>;
+  constexpr int NT = HsCfg<P, R>::NT;
+  constexpr int kMaxDevices = 64;
+  static int resident[kMaxDevices];  // CTAs resident on the whole device; 0 until known
   auto k = sigmakin_hs_kernel<P, R, CS>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
   if (e != cudaSuccess) return e;
   grid = (a.nevt + HsCfg<P, R>::EVMIN - 1) / HsCfg<P, R>::EVMIN;
-  k<<<(unsigned)grid, HsCfg<P, R>::NT, L::bytes, s>>>(a, cp);
+  int dev = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  int cap = dev < kMaxDevices ? resident[dev] : 0;
+  if (cap == 0) {
+    int nsm = 0, per = 0;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, NT, L::bytes)) != cudaSuccess) return e;
+    cap = nsm * (per > 0 ? per : 1);
+    if (dev < kMaxDevices) resident[dev] = cap;
+  }
+  if (grid > cap) grid = cap;
+  k<<<(unsigned)grid, NT, L::bytes, s>>>(a, cp);
   return cudaGetLastError();
 }
 

@@ -48,7 +48,8 @@ __global__ void __launch_bounds__(HsSplitA<P, R>::NT, HsSplitA<P, R>::CTAS)
   hs_setup_words<P, R, L>(smem, a.pp);
   hs_load_momenta<P, R, L>(smem, a.mom, a.nevt, e0, nev);
   __syncthreads();
-  hs_tables<P, R, L>(smem, a.pp, nev, curs, cp);
+  const HsGroup cta{0, NT, tid, 0, nev, 0};
+  hs_tables<P, R, L>(smem, a.pp, cta, curs, cp);
   const R* Kall = reinterpret_cast<const R*>(smem + L::o_K);
   const cx<R>* prall = reinterpret_cast<const cx<R>*>(smem + L::o_pr);
   const HsItem* items = P::hs_items();
