@@ -162,9 +162,12 @@ int mg_event_sum(int64_t nevt, const double* me, const double* wgt, double* out3
  * Larger nevt returns MG_ERR_SPACE and launches nothing.  The call allocates
  * nothing.  Its first call on a device looks up that array's device address
  * (once per device, with the device current), so make the first call before
- * any stream capture.  All calls share the array: calls that overlap on the
- * GPU (two streams, two host threads) race and give wrong sums; serialise
- * them.  Results are identical to mg_event_sum's. */
+ * any stream capture.  That address is kept for the life of the device's
+ * primary context: after cudaDeviceReset, or with another context made
+ * current on the same device, it is stale, so do not call this function
+ * then.  All calls share the array: calls that overlap on the GPU (two
+ * streams, two host threads) race and give wrong sums; serialise them.
+ * Results are identical to mg_event_sum's. */
 int64_t mg_event_sum_noalloc_max_events(void);
 int mg_event_sum_noalloc(int64_t nevt, const double* me, const double* wgt, double* out3, void* stream);
 

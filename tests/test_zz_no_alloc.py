@@ -41,3 +41,27 @@ def test_noalloc_event_sum_matches_scratch_version():
     out = torch.zeros(3, dtype=torch.float64, device="cuda")
     fake = ctypes.c_void_p(out.data_ptr())
     assert L.mg_event_sum_noalloc(nmax + 1, fake, fake, out.data_ptr(), stream) == -6
+
+
+def test_noalloc_edges_and_binding():
+    """No events (pass 2 alone: (0, 0, 0)), exactly the largest batch the
+    fixed array holds (every partial slot in use; 1 GiB of inputs), and the
+    Python binding, each bit for bit against mg_event_sum."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2106_12631_gb300 import mg
+    empty = torch.zeros(0, dtype=torch.float64, device="cuda")
+    out = torch.full((3,), -1.0, dtype=torch.float64, device="cuda")
+    mg.event_sum_noalloc(empty, empty, out=out)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out.cpu().numpy(), [0.0, 0.0, 0.0])
+    nmax = int(mg.lib().mg_event_sum_noalloc_max_events())
+    g = torch.Generator(device="cuda").manual_seed(2106)
+    for nevt in (nmax, 5):
+        me = torch.rand(nevt, dtype=torch.float64, device="cuda", generator=g)
+        w = torch.rand(nevt, dtype=torch.float64, device="cuda", generator=g) + 0.5
+        got = mg.event_sum_noalloc(me, w).cpu().numpy()
+        want = mg.event_sum(me, w).cpu().numpy()
+        np.testing.assert_array_equal(got, want)
+        assert got[2] == nevt
+        del me, w
