@@ -17,9 +17,13 @@ cudaError_t launch_sigmakin_variant(const SigArgs& a, const Couplings<R>& cp, in
   return cudaGetLastError();
 }
 
-// The helicity-shared kernel runs persistent: at most as many CTAs as are
-// resident at once (SMs x CTAs per SM, cached per device), each looping over
-// groups of events (the CTA's group count follows from the mask on the device).
+// The helicity-shared kernel runs persistent: as many CTAs as are resident at
+// once (SMs x CTAs per SM, cached per device), each looping over groups of
+// events (the CTA's group count follows from the mask on the device).  CTAs
+// per SM: the larger of the occupancy query and the count the kernel's shared
+// memory budget and launch bounds are built for (the query has returned 1 for
+// the tcgen05 variant, whose two CTAs per SM fit); should fewer fit, the
+// surplus CTAs start later and take their groups then.
 template <class P, class R, int CS>
 cudaError_t launch_sigmakin_hs_variant(const SigArgs& a, const Couplings<R>& cp, int64_t grid, cudaStream_t s) {
   using L = HsLayout<P, R, CS>;
@@ -37,7 +41,7 @@ cudaError_t launch_sigmakin_hs_variant(const SigArgs& a, const Couplings<R>& cp,
     int nsm = 0, per = 0;
     if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, NT, L::bytes)) != cudaSuccess) return e;
-    cap = nsm * (per > 0 ? per : 1);
+    cap = nsm * (per > HsCfg<P, R>::CTAS ? per : HsCfg<P, R>::CTAS);
     if (dev < kMaxDevices) resident[dev] = cap;
   }
   if (grid > cap) grid = cap;
