@@ -15,9 +15,12 @@
 //      propagators into the momenta; the momentum table into the legs;
 //   6. dL/d(final momenta) back into the buffer;
 // then the RAMBO adjoint (one thread per event, FP64) -> dL/d rnd; rows RAMBO
-// does not consume get 0.  Many helicities share a variant, so adjoints accumulate with shared-memory
-// atomics (their order, hence the last bits of the result, may vary between
-// runs).  Adjoint convention of helas_adj.cuh: zb = dL/dRe z + i dL/dIm z.
+// does not consume get 0.  Many helicities share a variant: the adjoint
+// contractions sum them with warp shuffles (shared-memory atomics when the
+// helicities of an event do not fill whole warps); the item adjoints of an
+// event run on one warp, whose lanes with the same destination sum with
+// shuffles before one lane adds (no atomics); the external and propagator
+// adjoints add atomically, so the last bits of a result may vary between runs.  Adjoint convention of helas_adj.cuh: zb = dL/dRe z + i dL/dIm z.
 #pragma once
 #include "grad.cuh"
 #include "sigmakin_hs.cuh"
@@ -83,7 +86,7 @@ __device__ __forceinline__ void atomic_addc(cx<R>* d, cx<R> v) {
 // Warp-aggregated adds for the item adjoints: the lanes of a warp that add into
 // the same destination (same key: its shared-memory address) first sum their
 // values with shuffles, and only the lowest lane of each such group adds the
-// sum atomically, so no two lanes of a warp contend for one address.  The
+// sum, so no two lanes of a warp write one address.  The
 // lanes taking part are the ones executing together (__activemask), and every
 // collective below runs on all of them.
 template <int NV, class R>
@@ -115,18 +118,25 @@ __device__ __forceinline__ bool warp_group_sum(unsigned key, R* v) {
 }
 __device__ __forceinline__ unsigned smem_key(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
+// Adds into destinations that only the calling warp writes during the phase
+// (each event's item adjoints run on one warp): the group's lowest lane adds
+// the group sum with a plain read-modify-write; the caller separates rounds of
+// items with __syncwarp.
 template <class R>
-__device__ __forceinline__ void agg_add4(R* d, const R* v) {
+__device__ __forceinline__ void own_add4(R* d, const R* v) {
   R t[4] = {v[0], v[1], v[2], v[3]};
-  if (warp_group_sum<4>(smem_key(d), t)) atomic_add4(d, t);
+  if (warp_group_sum<4>(smem_key(d), t)) {
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) d[mu] += t[mu];
+  }
 }
 template <class R>
-__device__ __forceinline__ void agg_addc(cx<R>* d, cx<R> v) {
+__device__ __forceinline__ void own_addc(cx<R>* d, cx<R> v) {
   R t[2] = {v.re, v.im};
-  if (warp_group_sum<2>(smem_key(d), t)) atomic_addc(d, cx<R>(t[0], t[1]));
+  if (warp_group_sum<2>(smem_key(d), t)) *d = cx<R>(d->re + t[0], d->im + t[1]);
 }
 template <class R, int N>
-__device__ __forceinline__ void agg_slot_add(const Slots<R, N>& s, int i, const W4<R>& w) {
+__device__ __forceinline__ void own_slot_add(const Slots<R, N>& s, int i, const W4<R>& w) {
   R t[8];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
@@ -134,10 +144,10 @@ __device__ __forceinline__ void agg_slot_add(const Slots<R, N>& s, int i, const 
     t[2 * k + 1] = w.w[k].im;
   }
   if (warp_group_sum<8>(smem_key(s.p + i), t)) {
-    W4<R> o;
+    W4<R> o = s[i];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) o.w[k] = cx<R>(t[2 * k], t[2 * k + 1]);
-    s.atomic_add(i, o);
+    for (int k = 0; k < 4; ++k) o.w[k] = cx<R>(o.w[k].re + t[2 * k], o.w[k].im + t[2 * k + 1]);
+    s.set(i, o);
   }
 }
 
@@ -177,10 +187,10 @@ __device__ __forceinline__ void hs_item_adj(const HsItem& it, const Slots<R, P::
   }
 #pragma unroll
   for (int k = 0; k < 6; ++k)
-    if (k < nin) agg_slot_add(curb, it.in[k], b[k]);
-  if (nk >= 1) agg_add4(Kb + 4 * it.k0, kb0);
-  if (nk >= 2) agg_add4(Kb + 4 * it.k1, kb1);
-  agg_addc(prb + it.prop, pb);
+    if (k < nin) own_slot_add(curb, it.in[k], b[k]);
+  if (nk >= 1) own_add4(Kb + 4 * it.k0, kb0);
+  if (nk >= 2) own_add4(Kb + 4 * it.k1, kb1);
+  own_addc(prb + it.prop, pb);
 }
 
 // adjoint of one amputated-current variant
@@ -210,10 +220,10 @@ __device__ __forceinline__ void hs_xitem_adj(const HsItem& it, const Slots<R, P:
   }
 #pragma unroll
   for (int k = 0; k < 6; ++k)
-    if (k < nin) agg_slot_add(curb, it.in[k], b[k]);
+    if (k < nin) own_slot_add(curb, it.in[k], b[k]);
   if (mom) {
-    agg_add4(Kb + 4 * it.k0, kb0);
-    agg_add4(Kb + 4 * it.k1, kb1);
+    own_add4(Kb + 4 * it.k0, kb0);
+    own_add4(Kb + 4 * it.k1, kb1);
   }
 }
 
@@ -341,27 +351,39 @@ __global__ void __launch_bounds__(HsGradCfg<P, R>::NT) sigmakin_hs_grad_kernel(G
     P::template hs_contract_adj<R>(0, cur, xb, vtab + ih, Jb, curb, xbb, full, tid & 31, active);
   }
   __syncthreads();
-  // 4. amputated currents, then the current levels in reverse
+  // 4. amputated currents, then the current levels in reverse; the items of
+  //    event ex run on warp ex % (NT / 32), so each event's adjoint slots have
+  //    one writing warp (plain adds, rounds of 32 items separated by __syncwarp)
+  const int warp = tid >> 5, lane = tid & 31;
+  constexpr int NW = NT / 32;
   {
-    const int i0 = P::hs_xitem(0), ni = P::hs_xitem(1) - i0, n = ni * nev;
-    for (int t = tid; t < n; t += NT) {
-      const int ex = t / ni;
-      const HsItem it = items[i0 + t - ex * ni];
-      hs_xitem_adj<P, R>(it, Slots<R, P::HS_NSLOT>{curs + ex * CUR_EV}, Slots<R, P::HS_NSLOT>{cursb + ex * CUR_EV},
-                         Slots<R, P::HS_XCAP>{xbufsb + ex * X_EV}, Kall + ex * P::NMOM * 4,
-                         Kball + ex * P::NMOM * 4, cp);
+    const int i0 = P::hs_xitem(0), ni = P::hs_xitem(1) - i0;
+    for (int ex = warp; ex < nev; ex += NW) {
+      for (int r0 = 0; r0 < ni; r0 += 32) {
+        if (r0 + lane < ni) {
+          const HsItem it = items[i0 + r0 + lane];
+          hs_xitem_adj<P, R>(it, Slots<R, P::HS_NSLOT>{curs + ex * CUR_EV},
+                             Slots<R, P::HS_NSLOT>{cursb + ex * CUR_EV}, Slots<R, P::HS_XCAP>{xbufsb + ex * X_EV},
+                             Kall + ex * P::NMOM * 4, Kball + ex * P::NMOM * 4, cp);
+        }
+        __syncwarp();
+      }
     }
   }
   __syncthreads();
 #pragma unroll
   for (int l = P::HS_NLEVEL - 1; l >= 1; --l) {
-    const int i0 = P::hs_level(l), ni = P::hs_level(l + 1) - i0, n = ni * nev;
-    for (int t = tid; t < n; t += NT) {
-      const int ex = t / ni;
-      const HsItem it = items[i0 + t - ex * ni];
-      hs_item_adj<P, R>(it, Slots<R, P::HS_NSLOT>{curs + ex * CUR_EV}, Slots<R, P::HS_NSLOT>{cursb + ex * CUR_EV},
-                        Kall + ex * P::NMOM * 4, Kball + ex * P::NMOM * 4, prall + ex * P::NPROP,
-                        prball + ex * P::NPROP, cp);
+    const int i0 = P::hs_level(l), ni = P::hs_level(l + 1) - i0;
+    for (int ex = warp; ex < nev; ex += NW) {
+      for (int r0 = 0; r0 < ni; r0 += 32) {
+        if (r0 + lane < ni) {
+          const HsItem it = items[i0 + r0 + lane];
+          hs_item_adj<P, R>(it, Slots<R, P::HS_NSLOT>{curs + ex * CUR_EV}, Slots<R, P::HS_NSLOT>{cursb + ex * CUR_EV},
+                            Kall + ex * P::NMOM * 4, Kball + ex * P::NMOM * 4, prall + ex * P::NPROP,
+                            prball + ex * P::NPROP, cp);
+        }
+        __syncwarp();
+      }
     }
     __syncthreads();
   }
