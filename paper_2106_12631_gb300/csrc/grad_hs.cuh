@@ -20,7 +20,8 @@
 // helicities of an event do not fill whole warps); the item adjoints of an
 // event run on one warp, whose lanes with the same destination sum with
 // shuffles before one lane adds (no atomics); the external and propagator
-// adjoints add atomically, so the last bits of a result may vary between runs.  Adjoint convention of helas_adj.cuh: zb = dL/dRe z + i dL/dIm z.
+// adjoints add atomically, so the last bits of a result may vary between runs.
+// Adjoint convention of helas_adj.cuh: zb = dL/dRe z + i dL/dIm z.
 #pragma once
 #include "grad.cuh"
 #include "sigmakin_hs.cuh"
@@ -412,31 +413,36 @@ __global__ void __launch_bounds__(HsGradCfg<P, R>::NT) sigmakin_hs_grad_kernel(G
     }
   }
   __syncthreads();
-  //    momentum table -> legs (one thread per (event, component), masks at compile time)
-  for (int t = tid; t < nev * 4; t += NT) {
-    const int ex = t >> 2, mu = t & 3;
-    const R* Kb = Kball + ex * P::NMOM * 4;
+  // 6. helicity sum (eight lanes per event in a fixed order, then a butterfly
+  //    over the eight lanes, as the forward kernel); dL/d(final momenta) into
+  //    grad for the RAMBO adjoint pass: one thread per (event, final leg,
+  //    component) adds to the external wavefunctions' part the momentum-table
+  //    entries that contain the leg (sign from the entry, four partial sums)
+  for (int b = 0; b < nev * 8; b += NT) {
+    const int t = b + tid, ex = t >> 3, q = t & 7;
+    double sum = 0.0;
+    if (t < nev * 8) {
 #pragma unroll
-    for (int j = 0; j < P::NMOM; ++j) {
-      const double kb = (double)Kb[4 * j + mu];
-#pragma unroll
-      for (int l = 0; l < P::NPAR; ++l) {
-        if (!(P::mom(j, 1) >> l & 1)) continue;
-        const bool neg = P::mom(j, 0) == 1 && (P::mom(j, 2) >> l & 1);
-        pbs[ex][l][mu] += neg ? -kb : kb;
-      }
+      for (int i = 0; i < (P::NHEL + 7) / 8; ++i)
+        if (q + 8 * i < ng) sum += sm2[ex * ng + q + 8 * i];
     }
-  }
-  __syncthreads();
-  // 6. helicity sum; dL/d(final momenta) into grad for the RAMBO adjoint pass
-  if (tid < nev && a.me) {
-    double me = 0.0;
-    for (int k = 0; k < ng; ++k) me += sm2[tid * ng + k];
-    a.me[e0 + tid] = me * P::NORM;
+    sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+    sum += __shfl_xor_sync(0xffffffffu, sum, 2);
+    sum += __shfl_xor_sync(0xffffffffu, sum, 4);
+    if (t < nev * 8 && q == 0 && a.me) a.me[e0 + ex] = sum * P::NORM;
   }
   for (int t = tid; t < nev * 4 * NF; t += NT) {
-    const int e = t % nev, c = t / nev;
-    a.grad[(int64_t)c * a.nevt + e0 + e] = pbs[e][2 + (c >> 2)][c & 3];
+    const int ex = t % nev, c = t / nev, l = 2 + (c >> 2), mu = c & 3;
+    const R* Kb = Kball + ex * P::NMOM * 4;
+    double acc[4] = {pbs[ex][l][mu], 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int j = 0; j < P::NMOM; ++j) {
+      if (!(P::mom(j, 1) >> l & 1)) continue;
+      const bool neg = P::mom(j, 0) == 1 && (P::mom(j, 2) >> l & 1);
+      const double kb = (double)Kb[4 * j + mu];
+      acc[j & 3] += neg ? -kb : kb;
+    }
+    a.grad[(int64_t)c * a.nevt + e0 + ex] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
   }
 }
 
