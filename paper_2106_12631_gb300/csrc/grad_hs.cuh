@@ -53,15 +53,15 @@ struct HsGradLayout {
   static constexpr int NT = H::NT, EVCAP = H::EVCAP, NF = P::NFINAL;
   static constexpr size_t W = sizeof(W4<R>);
   static constexpr size_t o_proptab = 0;
-  static constexpr size_t o_good = align_up(o_proptab + 8 * P::NPROP, 16);
+  static constexpr size_t o_md = align_up(o_proptab + 8 * P::NPROP, 16);  // momentum-entry descriptors (int4)
+  static constexpr size_t o_good = align_up(o_md + 16 * P::NMOM, 16);
   static constexpr size_t o_misc = align_up(o_good + 4 * P::NHEL, 16);
   static constexpr size_t o_mconst = align_up(o_misc + 32, 16);
-  static constexpr size_t o_p = align_up(o_mconst + 32, 16);                          // double [EV][NPAR][4]
+  static constexpr size_t o_p = align_up(o_mconst + 32, 16);  // [EV][NPAR][4]: double, or float2 (hi, lo) in FP32
   static constexpr size_t o_pb = align_up(o_p + 8 * EVCAP * P::NPAR * 4, 16);          // double [EV][NPAR][4]
   static constexpr size_t o_K = align_up(o_pb + 8 * EVCAP * P::NPAR * 4, 16);          // R [EV][NMOM][4]
   static constexpr size_t o_Kb = align_up(o_K + sizeof(R) * EVCAP * P::NMOM * 4, 16);  // R [EV][NMOM][4]
-  static constexpr size_t o_Kd = align_up(o_Kb + sizeof(R) * EVCAP * P::NMOM * 4, 16); // 8 B [EV][NMOM][4]
-  static constexpr size_t o_pr = align_up(o_Kd + 8 * EVCAP * P::NMOM * 4, 16);         // cx<R> [EV][NPROP]
+  static constexpr size_t o_pr = align_up(o_Kb + sizeof(R) * EVCAP * P::NMOM * 4, 16);  // cx<R> [EV][NPROP]
   static constexpr size_t o_prb = align_up(o_pr + 2 * sizeof(R) * EVCAP * P::NPROP, 16);
   static constexpr size_t o_m2 = align_up(o_prb + 2 * sizeof(R) * EVCAP * P::NPROP, 16);  // double [NT]
   static constexpr size_t o_vt = align_up(o_m2 + 8 * NT, 16);
@@ -238,7 +238,6 @@ __global__ void __launch_bounds__(HsGradCfg<P, R>::NT) sigmakin_hs_grad_kernel(G
   int* misc = reinterpret_cast<int*>(smem + L::o_misc);
   double* sm2 = reinterpret_cast<double*>(smem + L::o_m2);
   uint8_t* vtab = reinterpret_cast<uint8_t*>(smem + L::o_vt);
-  auto p = reinterpret_cast<double(*)[P::NPAR][4]>(smem + L::o_p);
   auto pbs = reinterpret_cast<double(*)[P::NPAR][4]>(smem + L::o_pb);
   R* Kall = reinterpret_cast<R*>(smem + L::o_K);
   R* Kball = reinterpret_cast<R*>(smem + L::o_Kb);
@@ -250,20 +249,7 @@ __global__ void __launch_bounds__(HsGradCfg<P, R>::NT) sigmakin_hs_grad_kernel(G
   uint4* xbufsb = reinterpret_cast<uint4*>(smem + L::o_xb);
   const int tid = threadIdx.x;
   // 0. tables, zeroed adjoints
-  if (tid < P::NPROP) {
-    int2 v = make_int2(0, 0);
-#pragma unroll
-    for (int j = 0; j < P::NPROP; ++j)
-      if (tid == j) v = make_int2(P::prop(j, 0), P::prop(j, 1));
-    reinterpret_cast<int2*>(smem + L::o_proptab)[tid] = v;
-  }
-  if constexpr (sizeof(R) == 4) {
-    if (tid < 2) {
-      const double m = tid == 0 ? a.pp.mt : a.pp.mz, w = tid == 0 ? a.pp.wt : a.pp.wz;
-      const dfl m2 = dfl_split(m * m);
-      reinterpret_cast<float4*>(smem + L::o_mconst)[tid] = make_float4(m2.hi, m2.lo, (float)(m * w), 0.0f);
-    }
-  }
+  hs_setup_words<P, R, L>(smem, a.pp);
   static_assert(P::NHEL <= 64 && NT >= P::NHEL, "helicity ballot layout");
   const bool hgood = tid < P::NHEL && a.mask[tid] != 0;
   const unsigned hbal = __ballot_sync(0xffffffffu, hgood);
@@ -274,7 +260,7 @@ __global__ void __launch_bounds__(HsGradCfg<P, R>::NT) sigmakin_hs_grad_kernel(G
     const uint4 z = make_uint4(0, 0, 0, 0);
     uint4* zb = cursb;  // curb, x (harmless), xb are one contiguous range from o_curb
     for (int i = tid; i < (int)((L::bytes - L::o_curb) / 16); i += NT) zb[i] = z;
-    for (int i = tid; i < (int)((L::o_Kd - L::o_Kb) / 16); i += NT) reinterpret_cast<uint4*>(Kball)[i] = z;
+    for (int i = tid; i < (int)((L::o_pr - L::o_Kb) / 16); i += NT) reinterpret_cast<uint4*>(Kball)[i] = z;
     for (int i = tid; i < (int)((L::o_m2 - L::o_prb) / 16); i += NT) reinterpret_cast<uint4*>(prball)[i] = z;
     for (int i = tid; i < (int)((L::o_K - L::o_pb) / 16); i += NT) reinterpret_cast<uint4*>(&pbs[0][0][0])[i] = z;
   }
@@ -286,12 +272,19 @@ __global__ void __launch_bounds__(HsGradCfg<P, R>::NT) sigmakin_hs_grad_kernel(G
   const int64_t e0 = (int64_t)blockIdx.x * ev;
   if (e0 >= a.nevt) return;
   const int nev = (int)min((int64_t)ev, a.nevt - e0);
-  // 1. momenta: the beams, and the final states the RAMBO pass left in grad
+  // 1. momenta: the beams, and the final states the RAMBO pass left in grad,
+  //    in the layout of the forward kernel's p
   for (int t = tid; t < nev * P::NPAR * 4; t += NT) {
     const int e = t % nev, c = t / nev, l = c >> 2, mu = c & 3;
     const double h = 0.5 * a.ecm;
-    p[e][l][mu] = l >= 2 ? a.grad[(int64_t)(c - 8) * a.nevt + e0 + e]
-                         : (mu == 0 ? h : (mu == 3 ? (l == 0 ? h : -h) : 0.0));
+    const double x = l >= 2 ? a.grad[(int64_t)(c - 8) * a.nevt + e0 + e]
+                            : (mu == 0 ? h : (mu == 3 ? (l == 0 ? h : -h) : 0.0));
+    if constexpr (sizeof(R) == 4) {
+      const dfl q = dfl_split(x);
+      reinterpret_cast<float2*>(smem + L::o_p)[e * P::NPAR * 4 + c] = make_float2(q.hi, q.lo);
+    } else {
+      reinterpret_cast<double*>(smem + L::o_p)[e * P::NPAR * 4 + c] = x;
+    }
   }
   __syncthreads();
   if (ng == 0) {
@@ -300,7 +293,7 @@ __global__ void __launch_bounds__(HsGradCfg<P, R>::NT) sigmakin_hs_grad_kernel(G
     return;
   }
   // 2. forward: tables, currents, amputated currents, contractions, colour sum
-  hs_build_tables<P, R, L>(smem, a.pp, nev, curs, cp);
+  hs_tables<P, R, L>(smem, a.pp, HsGroup{0, NT, tid, 0, nev, 0}, curs, cp);
   const HsItem* items = P::hs_items();
 #pragma unroll
   for (int l = 1; l < P::HS_NLEVEL; ++l) {
@@ -399,7 +392,11 @@ __global__ void __launch_bounds__(HsGradCfg<P, R>::NT) sigmakin_hs_grad_kernel(G
         const W4<R> ob = Slots<R, P::HS_NSLOT>{cursb + ex * CUR_EV}[it.out];
         R pk[4], pbk[4] = {R(0), R(0), R(0), R(0)};
 #pragma unroll
-        for (int mu = 0; mu < 4; ++mu) pk[mu] = R(p[ex][it.a][mu]);
+        for (int mu = 0; mu < 4; ++mu) {
+          const int ip = (ex * P::NPAR + it.a) * 4 + mu;
+          if constexpr (sizeof(R) == 4) pk[mu] = reinterpret_cast<const float2*>(smem + L::o_p)[ip].x;
+          else pk[mu] = reinterpret_cast<const double*>(smem + L::o_p)[ip];
+        }
         external_adj<R>(it.type, pk, it.flag ? cp.mt : R(0), it.b, it.c, ob, pbk);
 #pragma unroll
         for (int mu = 0; mu < 4; ++mu) atomicAdd(&pbs[ex][it.a][mu], (double)pbk[mu]);

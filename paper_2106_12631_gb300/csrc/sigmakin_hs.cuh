@@ -561,110 +561,6 @@ __device__ __forceinline__ void hs_tables(unsigned char* smem, const PhysParams&
   grp.sync();
 }
 
-// Phase 1 of the adjoint kernel (grad_hs.cuh): momentum-table entries as signed
-// sums of the external momenta (one thread per (event, component) walks all
-// entries with the leg masks known at compile time: |S| - 1 additions per
-// entry), in FP64 (FP64 mode) or double-float (mixed mode), rounded to R and
-// kept unrounded for the propagators; the external wavefunctions (level 0 of
-// the current program) straight from the momenta; then the propagator of every
-// line (one thread per (event, propagator)).
-template <class P, class R, class L>
-__device__ __forceinline__ void hs_build_tables(unsigned char* smem, const PhysParams& pp, int nev, uint4* curs,
-                                                const Couplings<R>& cp);
-
-// the tables from the momenta already in shared memory
-template <class P, class R, class L>
-__device__ __forceinline__ void hs_build_tables(unsigned char* smem, const PhysParams& pp, int nev, uint4* curs,
-                                                const Couplings<R>& cp) {
-  constexpr int NT = L::NT;
-  constexpr int NEXT = P::hs_level(1);  // external variants
-  constexpr int CUR_EV = P::HS_NSLOT * Slots<R, 1>::NPL;
-  constexpr bool DF = sizeof(R) == 4;
-  const int tid = threadIdx.x;
-  auto p = reinterpret_cast<double(*)[P::NPAR][4]>(smem + L::o_p);
-  auto K = reinterpret_cast<R(*)[P::NMOM][4]>(smem + L::o_K);
-  auto Kd = reinterpret_cast<double(*)[P::NMOM][4]>(smem + L::o_Kd);
-  auto Kf = reinterpret_cast<float2(*)[P::NMOM][4]>(smem + L::o_Kd);
-  auto pr = reinterpret_cast<cx<R>(*)[P::NPROP]>(smem + L::o_pr);
-  const int2* prop_tab = reinterpret_cast<const int2*>(smem + L::o_proptab);
-  for (int t = tid; t < nev * (4 + NEXT); t += NT) {
-    if (t < nev * 4) {
-      const int e = t >> 2, mu = t & 3;
-      if constexpr (DF) {
-        float qh[P::NPAR], ql[P::NPAR];
-#pragma unroll
-        for (int l = 0; l < P::NPAR; ++l) {
-          const dfl q = dfl_split(p[e][l][mu]);
-          qh[l] = q.hi;
-          ql[l] = q.lo;
-        }
-#pragma unroll
-        for (int j = 0; j < P::NMOM; ++j) {
-          DflSum k;
-          bool first = true;
-#pragma unroll
-          for (int l = 0; l < P::NPAR; ++l) {
-            if (!(P::mom(j, 1) >> l & 1)) continue;
-            const bool neg = P::mom(j, 0) == 1 && (P::mom(j, 2) >> l & 1);
-            const float h = neg ? -qh[l] : qh[l], lo = neg ? -ql[l] : ql[l];
-            if (first) k.first(h, lo);
-            else k.add(h, lo);
-            first = false;
-          }
-          K[e][j][mu] = k.value();
-          Kf[e][j][mu] = make_float2(k.s, k.err);
-        }
-      } else {
-        double q[P::NPAR];
-#pragma unroll
-        for (int l = 0; l < P::NPAR; ++l) q[l] = p[e][l][mu];
-#pragma unroll
-        for (int j = 0; j < P::NMOM; ++j) {
-          double k = 0.0;
-          bool first = true;
-#pragma unroll
-          for (int l = 0; l < P::NPAR; ++l) {
-            if (!(P::mom(j, 1) >> l & 1)) continue;
-            const bool neg = P::mom(j, 0) == 1 && (P::mom(j, 2) >> l & 1);
-            k = first ? (neg ? -q[l] : q[l]) : (neg ? k - q[l] : k + q[l]);
-            first = false;
-          }
-          K[e][j][mu] = R(k);
-          Kd[e][j][mu] = k;
-        }
-      }
-    } else {
-      const int t2 = t - nev * 4, e = t2 / NEXT;
-      const HsItem it = P::hs_items()[t2 - e * NEXT];
-      R k[4];
-#pragma unroll
-      for (int mu = 0; mu < 4; ++mu) k[mu] = R(p[e][it.a][mu]);
-      W4<R> o;
-      if (it.type == 0) o = ixxxxx<R>(k, it.flag ? cp.mt : R(0), it.b, it.c);
-      else if (it.type == 1) o = oxxxxx<R>(k, it.flag ? cp.mt : R(0), it.b, it.c);
-      else o = vxxxxx<R>(k, it.b, it.c);
-      Slots<R, P::HS_NSLOT>{curs + e * CUR_EV}.set(it.out, o);
-    }
-  }
-  __syncthreads();
-  if constexpr (DF) {
-    const float4* mc = reinterpret_cast<const float4*>(smem + L::o_mconst);
-    for (int t = tid; t < nev * P::NPROP; t += NT) {
-      const int e = t / P::NPROP, j = t - e * P::NPROP;
-      const int2 m = prop_tab[j];  // momentum entry, line kind
-      const float4 c = mc[m.y == 3 ? 1 : 0];  // {m^2 hi, m^2 lo, m w, 0} of the top / the Z
-      pr[e][j] = propagator_dfl(Kf[e][m.x], m.y, dfl{c.x, c.y}, c.z);
-    }
-  } else {
-    for (int t = tid; t < nev * P::NPROP; t += NT) {
-      const int e = t / P::NPROP, j = t - e * P::NPROP;
-      const int2 m = prop_tab[j];  // momentum entry, line kind
-      pr[e][j] = propagator_hs<R>(Kd[e][m.x], m.y, pp);
-    }
-  }
-  __syncthreads();
-}
-
 // one current variant
 template <class P, class R>
 __device__ __forceinline__ void hs_item(const HsItem& it, const Slots<R, P::HS_NSLOT>& cur, const R* K,
