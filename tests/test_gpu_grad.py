@@ -141,3 +141,26 @@ def test_helicity_subsets_add_up(mg, proc, mode):
     np.testing.assert_allclose((mea + meb).cpu().numpy(), me.cpu().numpy(), rtol=bar)
     s, ref = (ga + gb).cpu().numpy(), g.cpu().numpy()
     assert np.all(np.max(np.abs(s - ref), axis=0) <= bar * np.max(np.abs(ref), axis=0))
+
+
+@pytest.mark.parametrize("mode,bar", [("mixed", 1e-4), ("fp64", 1e-9)])
+def test_adjoint_full_size_sampled(mg, orc, mode, bar):
+    """The gradient workload at full size (gg -> t t~ g, 2^18 events, 16 random
+    rows) in the benchmark's launch configuration; 32 sampled events, the
+    first and the last among them, recomputed one by one by the oracle's
+    dual numbers from their own uniforms."""
+    proc, nevt, nrows = 3, 1 << 18, 16
+    seed = I.seed_of("gg_ttg_grad")
+    mask = mask_for(mg, proc, nrows)
+    rnd = torch.from_numpy(I.uniforms(seed, nrows, nevt)).cuda()
+    g, me = mg.sigmakin_grad(proc, rnd, 1500.0, mask, mode=mode)
+    idx = np.sort(np.random.default_rng(7).choice(nevt, 32, replace=False))
+    idx[0], idx[-1] = 0, nevt - 1
+    g = g.cpu().numpy()[:, idx]
+    me = me.cpu().numpy()[idx]
+    me_o, g_o = orc.me_grad(proc, I.uniforms_at(seed, nrows, idx), 1500.0, nthreads=8)
+    used = 4 * (orc.NPAR[proc] - 2)
+    assert np.all(g[used:] == 0.0)
+    err = normwise(g[:used], g_o[:used])
+    assert np.all(err <= bar), (err.max(), int(idx[err.argmax()]))
+    np.testing.assert_allclose(me, me_o, rtol=1e-9 if mode == "fp64" else 1e-4)
