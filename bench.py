@@ -283,6 +283,13 @@ def measure_generation(mg, proc, ecm, nevt, seed, mom, wgt, me, sums, stream, hb
                                                         me=me_b, hel=hel_b, col=col_b, workspace=ws,
                                                         stream=stream)) if choose else None
     t_sig = time_it(lambda: mg.sigmakin(proc, mom, mask, mode=mode, me=me_b, stream=stream))
+    # RAMBO and SIGMAKIN in one kernel (no momentum buffer) against the two kernels
+    wgt_b = torch.empty_like(wgt)
+    fusable = "unrolled" not in mode
+    t_two = time_it(lambda: (mg.rambo(proc, rnd, ecm, mom=mom2, wgt=wgt2, stream=stream),
+                             mg.sigmakin(proc, mom2, mask, mode=mode, me=me_b, stream=stream)))
+    t_fused = time_it(lambda: mg.sigmakin_rambo(proc, rnd, ecm, mask, mode=mode, me=me_b, wgt=wgt_b,
+                                                stream=stream)) if fusable else None
     del mom_aos, ws
     return {"events": nevt,
             "rambo_device_rng_ms": 1e3 * t_seed, "rambo_buffered_ms": 1e3 * t_buf,
@@ -292,6 +299,8 @@ def measure_generation(mg, proc, ecm, nevt, seed, mom, wgt, me, sums, stream, hb
             "cross_section_pb": float(xs[0]), "cross_section_err_pb": float(xs[1]),
             "batch_aos_ms": 1e3 * t_batch,
             "batch_aos_with_choices_ms": 1e3 * t_choice if t_choice is not None else None, "sigmakin_soa_ms": 1e3 * t_sig,
+            "rambo_then_sigmakin_ms": 1e3 * t_two,
+            "rambo_sigmakin_fused_ms": 1e3 * t_fused if t_fused is not None else None,
             "rooflines": {
                 "event_sum": {"bound": "hbm", "achieved": 16 * nevt / t_sum / 1e9, "peak": hbm_gbs,
                               "unit": "GB/s", "frac": (16 * nevt / t_sum / 1e9) / hbm_gbs if hbm_gbs else None,

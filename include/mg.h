@@ -171,6 +171,27 @@ int mg_event_sum(int64_t nevt, const double* me, const double* wgt, double* out3
 int64_t mg_event_sum_noalloc_max_events(void);
 int mg_event_sum_noalloc(int64_t nevt, const double* me, const double* wgt, double* out3, void* stream);
 
+/* RAMBO and SIGMAKIN in one kernel (Sec. 3: random numbers -> RAMBO -> matrix
+ * elements), for callers that need only me and the phase-space weight: no
+ * momentum buffer, no momentum round trip through HBM.  Each CTA runs RAMBO
+ * for its next group of events, one lane per event, while it computes the
+ * current group.  me and wgt equal, bit for bit, mg_rambo (or
+ * mg_rambo_seeded) followed by mg_sigmakin with the same mask and mode.  On
+ * GB300 it saves memory, not time: RAMBO's FP64 work on one lane per event
+ * takes longer than a group's matrix elements, so the kernel waits for it
+ * (gg -> t t~ g g, 2^20 events, mixed: 44.5 ms against 22.2 ms for the two
+ * kernels).
+ * mg_sigmakin_rambo: uniforms rnd [nrows][nevt] (device), as mg_rambo.
+ * mg_sigmakin_seeded: uniforms drawn on the device, as mg_rambo_seeded
+ * (seed, first_event >= 0, first_event + nevt <= 2^57).
+ * mask: [nhel] from mg_filter_helicities; mode: MG_FP64, MG_MIXED,
+ * MG_MIXED_SIMT or MG_MIXED_TC (the helicity-shared kernels; the per-helicity
+ * modes give MG_ERR_ARG).  me, wgt: device [nevt]. */
+int mg_sigmakin_rambo(int proc, int64_t nevt, double ecm, const double* rnd, int nrows, const int32_t* mask,
+                      int mode, double* me, double* wgt, void* stream);
+int mg_sigmakin_seeded(int proc, int64_t nevt, double ecm, uint64_t seed, int64_t first_event,
+                       const int32_t* mask, int mode, double* me, double* wgt, void* stream);
+
 /* RAMBO with the uniforms drawn on the device (Sec. 3's random numbers fused
  * into the phase-space kernel; no random-number buffer): the uniform of event
  * i, row k is SplitMix64 used as a counter-based generator,

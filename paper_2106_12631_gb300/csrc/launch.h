@@ -24,6 +24,13 @@ struct SigLaunch {
   int32_t* hel_out = nullptr;
   const double* col_rnd = nullptr;
   int32_t* col_out = nullptr;
+  // RAMBO inside SIGMAKIN (mg_sigmakin_rambo, mg_sigmakin_seeded)
+  const double* rnd = nullptr;  // [nrows][nevt], or nullptr: uniforms from (key, first_event + i, row)
+  double* wgt = nullptr;
+  double ecm = 0.0;
+  uint64_t key = 0;
+  int64_t first_event = 0;
+  RamboSetup st{};
 };
 
 // rnd == nullptr: uniforms drawn on the device from (seed, first_event + i, row)
@@ -72,6 +79,11 @@ cudaError_t launch_sigmakin_p1(const SigLaunch& a, int mode, cudaStream_t s);
 cudaError_t launch_sigmakin_p2(const SigLaunch& a, int mode, cudaStream_t s);
 cudaError_t launch_sigmakin_p3(const SigLaunch& a, int mode, cudaStream_t s);
 cudaError_t launch_sigmakin_p4(const SigLaunch& a, int mode, cudaStream_t s);
+// RAMBO + SIGMAKIN in one kernel (helicity-shared modes 0, 1, 2, 5 only)
+cudaError_t launch_sigmakin_rambo_p1(const SigLaunch& a, int mode, cudaStream_t s);
+cudaError_t launch_sigmakin_rambo_p2(const SigLaunch& a, int mode, cudaStream_t s);
+cudaError_t launch_sigmakin_rambo_p3(const SigLaunch& a, int mode, cudaStream_t s);
+cudaError_t launch_sigmakin_rambo_p4(const SigLaunch& a, int mode, cudaStream_t s);
 struct GradLaunch {
   int64_t nevt;
   double ecm;

@@ -7,6 +7,7 @@
 #include "mg.h"
 #include "launch.h"
 #include "process.cuh"
+#include "rng.cuh"
 
 namespace {
 
@@ -92,6 +93,43 @@ int64_t split_record_bytes(int proc, int mode) {
     case 3: return mg::split_record_bytes_p3(mode);
     default: return mg::split_record_bytes_p4(mode);
   }
+}
+
+cudaError_t dispatch_sigmakin_rambo(int proc, const mg::SigLaunch& l, int mode, cudaStream_t s) {
+  switch (proc) {
+    case 1: return mg::launch_sigmakin_rambo_p1(l, mode, s);
+    case 2: return mg::launch_sigmakin_rambo_p2(l, mode, s);
+    case 3: return mg::launch_sigmakin_rambo_p3(l, mode, s);
+    case 4: return mg::launch_sigmakin_rambo_p4(l, mode, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+int rambo_setup(int proc, double ecm, mg::RamboSetup& st);
+
+// mg_sigmakin_rambo (seeded = false: uniforms from rnd) and mg_sigmakin_seeded
+int sigmakin_rambo(int proc, int64_t nevt, double ecm, const double* rnd, int nrows, bool seeded, uint64_t seed,
+                   int64_t first_event, const int32_t* mask, int mode, double* me, double* wgt, void* stream) {
+  if (!valid_proc(proc)) return MG_ERR_PROC;
+  const ProcDesc& d = kProcs[proc];
+  if (nevt < 0 || !(ecm > 0) || !std::isfinite(ecm)) return MG_ERR_ARG;
+  if (mode != MG_FP64 && mode != MG_MIXED && mode != MG_MIXED_SIMT && mode != MG_MIXED_TC) return MG_ERR_ARG;
+  if (!seeded && nrows < 4 * (d.npar - 2)) return MG_ERR_ARG;
+  if (seeded && (first_event < 0 || first_event > ((int64_t)1 << 57) - nevt)) return MG_ERR_ARG;
+  mg::RamboSetup st;
+  if (int r = rambo_setup(proc, ecm, st)) return r;
+  if (nevt == 0) return MG_OK;
+  if ((!seeded && !rnd) || !mask || !me || !wgt) return MG_ERR_ARG;
+  if ((!seeded && !aligned(rnd)) || !aligned(mask) || !aligned(me) || !aligned(wgt)) return MG_ERR_ALIGN;
+  if (nevt > (int64_t)INT32_MAX) return MG_ERR_ARG;
+  mg::SigLaunch l = sig_launch(nevt, nullptr, mask, me, nullptr);
+  l.rnd = seeded ? nullptr : rnd;
+  l.wgt = wgt;
+  l.ecm = ecm;
+  l.key = seeded ? mg::sm64_mix(seed) : 0;
+  l.first_event = seeded ? first_event : 0;
+  l.st = st;
+  return cuda_status(dispatch_sigmakin_rambo(proc, l, mode, (cudaStream_t)stream));
 }
 
 int rambo_setup(int proc, double ecm, mg::RamboSetup& st) {
@@ -200,6 +238,16 @@ int mg_rambo_seeded(int proc, int64_t nevt, double ecm, uint64_t seed, int64_t f
   if (nevt > (int64_t)INT32_MAX * 64) return MG_ERR_ARG;
   return cuda_status(
       mg::launch_rambo(d.npar - 2, nevt, ecm, nullptr, mom, wgt, st, (cudaStream_t)stream, seed, first_event));
+}
+
+int mg_sigmakin_rambo(int proc, int64_t nevt, double ecm, const double* rnd, int nrows, const int32_t* mask,
+                      int mode, double* me, double* wgt, void* stream) {
+  return sigmakin_rambo(proc, nevt, ecm, rnd, nrows, false, 0, 0, mask, mode, me, wgt, stream);
+}
+
+int mg_sigmakin_seeded(int proc, int64_t nevt, double ecm, uint64_t seed, int64_t first_event,
+                       const int32_t* mask, int mode, double* me, double* wgt, void* stream) {
+  return sigmakin_rambo(proc, nevt, ecm, nullptr, 0, true, seed, first_event, mask, mode, me, wgt, stream);
 }
 
 int mg_cross_section(int proc, double ecm, const double* sums3, double* xsec2, void* stream) {

@@ -21,6 +21,8 @@
 #pragma once
 #include <type_traits>
 
+#include "rambo.cuh"
+#include "rng.cuh"
 #include "sigmakin.cuh"
 
 namespace mg {
@@ -682,15 +684,51 @@ struct HsRecord {
   static constexpr int WORDS = CUR + KW;
 };
 
+// Where a group's momenta come from: the momentum buffer (mg_sigmakin), the
+// kernel-split records (current variants and momentum tables instead), or
+// RAMBO inside the kernel (mg_sigmakin_rambo, mg_sigmakin_seeded).
+constexpr int kSrcMomenta = 0, kSrcRecords = 1, kSrcRambo = 2;
+
+// One event's RAMBO inside a SIGMAKIN kernel: the uniforms as the RAMBO kernel
+// reads or draws them, the same forward code (rambo_forward), the momenta of
+// all legs into out[leg][mu] (shared memory, FP64; the beams as the RAMBO
+// kernel writes them) and the weight into wgt.  Not inlined, so that RAMBO's
+// many FP64 temporaries do not raise the register count of the calling
+// kernel (the call runs on a few lanes, once per event).
+template <int NF>
+__device__ __noinline__ void rambo_event_fused(const double* __restrict__ rnd, int64_t nevt, int64_t i, uint64_t key,
+                                               int64_t first_event, double ecm, const RamboSetup& st, double* out,
+                                               double* __restrict__ wgt) {
+  double r[4 * NF];
+  if (rnd) {
+#pragma unroll
+    for (int k = 0; k < 4 * NF; ++k) r[k] = rnd[(int64_t)k * nevt + i];
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4 * NF; ++k) r[k] = sm64_uniform(key, first_event + i, k);
+  }
+  RamboState<NF> z;
+  rambo_forward<NF>(r, ecm, st, z);
+  const double h = 0.5 * ecm;
+  out[0] = h; out[1] = 0.0; out[2] = 0.0; out[3] = h;
+  out[4] = h; out[5] = 0.0; out[6] = 0.0; out[7] = -h;
+#pragma unroll
+  for (int f = 0; f < NF; ++f)
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) out[(2 + f) * 4 + mu] = z.k[f][mu];
+  wgt[i] = z.w;
+}
+
 // The helicity-shared program for the events [first, last) of the batch.
-// FROM_RECORDS: phases 1-2 (momenta, tables, current variants) are replaced
-// by a copy of the events' records from `rec` (one record per event, event
-// first - first at rec[0]).
-template <class P, class R, int CS, bool FROM_RECORDS>
+// SRC == kSrcRecords: phases 1-2 (momenta, tables, current variants) are
+// replaced by a copy of the events' records from `rec` (one record per event,
+// event first - first at rec[0]).
+template <class P, class R, int CS, int SRC>
 __device__ __forceinline__ void hs_sigmakin_body(const SigArgs& a, const Couplings<R>& cp, int64_t first, int64_t last,
                                                  const uint4* __restrict__ rec) {
   using C = HsCfg<P, R>;
   using L = HsLayout<P, R, CS>;
+  constexpr bool FROM_RECORDS = SRC == kSrcRecords;
   static_assert(!(FROM_RECORDS && L::TC), "the kernel-split variant sums colours on CUDA cores");
   constexpr int NT = C::NT, NC = P::NCOLOR;
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -731,6 +769,9 @@ __device__ __forceinline__ void hs_sigmakin_body(const SigArgs& a, const Couplin
         a.me[e0 + tid] = 0.0;
         if (a.hel_out) a.hel_out[e0 + tid] = -1;
         if (a.col_out) a.col_out[e0 + tid] = -1;
+        if constexpr (SRC == kSrcRambo)  // the weight all the same
+          rambo_event_fused<P::NPAR - 2>(a.rnd, a.nevt, e0 + tid, a.key, a.first_event, a.ecm, a.st,
+                                         reinterpret_cast<double*>(smem + L::o_ps) + tid * P::NPAR * 4, a.wgt);
       }
     }
     return;
@@ -748,10 +789,19 @@ __device__ __forceinline__ void hs_sigmakin_body(const SigArgs& a, const Couplin
   }
   const R* Kall = reinterpret_cast<const R*>(smem + L::o_K);
   const HsItem* items = P::hs_items();
-  if constexpr (!FROM_RECORDS) {
+  if constexpr (SRC == kSrcMomenta) {
     // the first group's momenta; later groups' arrive by prefetch
     const int64_t e0 = first + (int64_t)blockIdx.x * ev;
     hs_load_momenta<P, R, L>(smem, a.mom, a.nevt, e0, (int)min((int64_t)ev, last - e0));
+  } else if constexpr (SRC == kSrcRambo) {
+    // the first group's RAMBO, one lane per event, into the staging buffer
+    const int64_t e0 = first + (int64_t)blockIdx.x * ev;
+    const int nev0 = (int)min((int64_t)ev, last - e0);
+    if (tid < nev0)
+      rambo_event_fused<P::NPAR - 2>(a.rnd, a.nevt, e0 + tid, a.key, a.first_event, a.ecm, a.st,
+                                     reinterpret_cast<double*>(smem + L::o_ps) + tid * P::NPAR * 4, a.wgt);
+    __syncthreads();
+    hs_convert_momenta<P, R, L>(smem, nev0);
   }
   __syncthreads();
   if constexpr (L::TC) {
@@ -781,7 +831,16 @@ __device__ __forceinline__ void hs_sigmakin_body(const SigArgs& a, const Couplin
       const int gn = g + gridDim.x;
       const int64_t e0n = first + (int64_t)gn * ev;
       const int nevn = gn < ngrp ? (int)min((int64_t)ev, last - e0n) : 0;
-      if (nevn > 0) hs_prefetch_momenta<P, L>(smem, a.mom, a.nevt, e0n, nevn);
+      if constexpr (SRC == kSrcRambo) {
+        // the next group's RAMBO on the last lanes, which the tables phase
+        // leaves idle when it has fewer items than threads
+        const int u = NT - 1 - tid;
+        if (u < nevn)
+          rambo_event_fused<P::NPAR - 2>(a.rnd, a.nevt, e0n + u, a.key, a.first_event, a.ecm, a.st,
+                                         reinterpret_cast<double*>(smem + L::o_ps) + u * P::NPAR * 4, a.wgt);
+      } else {
+        if (nevn > 0) hs_prefetch_momenta<P, L>(smem, a.mom, a.nevt, e0n, nevn);
+      }
       // 1. per-event tables (the momenta are in p)
       hs_tables<P, R, L>(smem, a.pp, grp, curs, cp);
       const cx<R>* prall = reinterpret_cast<const cx<R>*>(smem + L::o_pr);
@@ -889,7 +948,14 @@ __device__ __forceinline__ void hs_sigmakin_body(const SigArgs& a, const Couplin
 
 template <class P, class R, int CS>
 __global__ void __launch_bounds__(HsCfg<P, R>::NT, HsCfg<P, R>::CTAS) sigmakin_hs_kernel(SigArgs a, Couplings<R> cp) {
-  hs_sigmakin_body<P, R, CS, false>(a, cp, 0, a.nevt, nullptr);
+  hs_sigmakin_body<P, R, CS, kSrcMomenta>(a, cp, 0, a.nevt, nullptr);
+}
+
+// RAMBO and SIGMAKIN in one kernel: no momentum buffer in HBM
+template <class P, class R, int CS>
+__global__ void __launch_bounds__(HsCfg<P, R>::NT, HsCfg<P, R>::CTAS)
+    sigmakin_hs_rambo_kernel(SigArgs a, Couplings<R> cp) {
+  hs_sigmakin_body<P, R, CS, kSrcRambo>(a, cp, 0, a.nevt, nullptr);
 }
 
 }  // namespace mg

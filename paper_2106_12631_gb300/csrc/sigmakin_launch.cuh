@@ -24,13 +24,14 @@ cudaError_t launch_sigmakin_variant(const SigArgs& a, const Couplings<R>& cp, in
 // memory budget and launch bounds are built for (the query has returned 1 for
 // the tcgen05 variant, whose two CTAs per SM fit); should fewer fit, the
 // surplus CTAs start later and take their groups then.
-template <class P, class R, int CS>
+// FUSED: the kernel that runs RAMBO itself (sigmakin_hs_rambo_kernel).
+template <class P, class R, int CS, bool FUSED = false>
 cudaError_t launch_sigmakin_hs_variant(const SigArgs& a, const Couplings<R>& cp, int64_t grid, cudaStream_t s) {
   using L = HsLayout<P, R, CS>;
   constexpr int NT = HsCfg<P, R>::NT;
   constexpr int kMaxDevices = 64;
   static int resident[kMaxDevices];  // CTAs resident on the whole device; 0 until known
-  auto k = sigmakin_hs_kernel<P, R, CS>;
+  auto k = FUSED ? sigmakin_hs_rambo_kernel<P, R, CS> : sigmakin_hs_kernel<P, R, CS>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
   if (e != cudaSuccess) return e;
   grid = (a.nevt + HsCfg<P, R>::EVMIN - 1) / HsCfg<P, R>::EVMIN;
@@ -53,9 +54,20 @@ cudaError_t launch_sigmakin_hs_variant(const SigArgs& a, const Couplings<R>& cp,
 // the tensor cores from 48 on; 2 mixed + CUDA-core colour sum; 5 mixed +
 // tcgen05 colour sum (helicity-shared kernel); 3 FP64, 4 mixed + tcgen05 with
 // the per-helicity unrolled kernel (every helicity recomputes all its currents)
+inline SigArgs sig_args(const SigLaunch& l) {
+  SigArgs a{l.nevt, l.mom, l.mask, l.me, l.mask_out, l.pp, l.hel_rnd, l.hel_out, l.col_rnd, l.col_out};
+  a.rnd = l.rnd;
+  a.wgt = l.wgt;
+  a.ecm = l.ecm;
+  a.key = l.key;
+  a.first_event = l.first_event;
+  a.st = l.st;
+  return a;
+}
+
 template <class P>
 cudaError_t launch_sigmakin_impl(const SigLaunch& l, int mode, cudaStream_t s) {
-  SigArgs a{l.nevt, l.mom, l.mask, l.me, l.mask_out, l.pp, l.hel_rnd, l.hel_out, l.col_rnd, l.col_out};
+  const SigArgs a = sig_args(l);
   const int64_t grid = (l.nevt + SigCfg<P>::EVMIN - 1) / SigCfg<P>::EVMIN;
   if (grid == 0) return cudaSuccess;
   constexpr bool tc_default = P::NCOLOR >= 48;
@@ -68,6 +80,24 @@ cudaError_t launch_sigmakin_impl(const SigLaunch& l, int mode, cudaStream_t s) {
     case 5: return launch_sigmakin_hs_variant<P, float, CS_TC>(a, l.cf, grid, s);
     case 3: return launch_sigmakin_variant<P, double, CS_SIMT>(a, l.cd, grid, s);
     case 4: return launch_sigmakin_variant<P, float, CS_TC>(a, l.cf, grid, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// RAMBO and SIGMAKIN in one kernel; the helicity-shared modes only (0 FP64,
+// 1 mixed, 2 mixed + CUDA-core colour sum, 5 mixed + tcgen05 colour sum)
+template <class P>
+cudaError_t launch_sigmakin_rambo_impl(const SigLaunch& l, int mode, cudaStream_t s) {
+  const SigArgs a = sig_args(l);
+  if (l.nevt == 0) return cudaSuccess;
+  constexpr bool tc_default = P::NCOLOR >= 48;
+  switch (mode) {
+    case 0: return launch_sigmakin_hs_variant<P, double, CS_SIMT, true>(a, l.cd, 0, s);
+    case 1:
+      return tc_default ? launch_sigmakin_hs_variant<P, float, CS_TC, true>(a, l.cf, 0, s)
+                        : launch_sigmakin_hs_variant<P, float, CS_SIMT, true>(a, l.cf, 0, s);
+    case 2: return launch_sigmakin_hs_variant<P, float, CS_SIMT, true>(a, l.cf, 0, s);
+    case 5: return launch_sigmakin_hs_variant<P, float, CS_TC, true>(a, l.cf, 0, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -95,9 +125,14 @@ cudaError_t launch_filter_impl(const SigLaunch& l, cudaStream_t s) {
       const SigArgs&, const Couplings<double>&, int64_t, cudaStream_t);                                  \
   extern template cudaError_t launch_sigmakin_hs_variant<Proc##N, double, CS_SIMT>(                     \
       const SigArgs&, const Couplings<double>&, int64_t, cudaStream_t);                                  \
+  extern template cudaError_t launch_sigmakin_hs_variant<Proc##N, double, CS_SIMT, true>(               \
+      const SigArgs&, const Couplings<double>&, int64_t, cudaStream_t);                                  \
   extern template cudaError_t launch_filter_impl<Proc##N>(const SigLaunch&, cudaStream_t);              \
   cudaError_t launch_sigmakin_p##N(const SigLaunch& a, int mode, cudaStream_t s) {                      \
     return launch_sigmakin_impl<Proc##N>(a, mode, s);                                                    \
+  }                                                                                                      \
+  cudaError_t launch_sigmakin_rambo_p##N(const SigLaunch& a, int mode, cudaStream_t s) {                \
+    return launch_sigmakin_rambo_impl<Proc##N>(a, mode, s);                                              \
   }                                                                                                      \
   cudaError_t launch_filter_p##N(const SigLaunch& a, cudaStream_t s) { return launch_filter_impl<Proc##N>(a, s); } \
   }
@@ -107,6 +142,8 @@ cudaError_t launch_filter_impl(const SigLaunch& l, cudaStream_t s) {
   template cudaError_t launch_sigmakin_variant<Proc##N, double, CS_SIMT>(                               \
       const SigArgs&, const Couplings<double>&, int64_t, cudaStream_t);                                  \
   template cudaError_t launch_sigmakin_hs_variant<Proc##N, double, CS_SIMT>(                            \
+      const SigArgs&, const Couplings<double>&, int64_t, cudaStream_t);                                  \
+  template cudaError_t launch_sigmakin_hs_variant<Proc##N, double, CS_SIMT, true>(                      \
       const SigArgs&, const Couplings<double>&, int64_t, cudaStream_t);                                  \
   template cudaError_t launch_filter_impl<Proc##N>(const SigLaunch&, cudaStream_t);                     \
   }

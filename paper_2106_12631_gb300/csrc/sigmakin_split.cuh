@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(HsSplitA<P, R>::NT, HsSplitA<P, R>::CTAS)
 template <class P, class R>
 __global__ void __launch_bounds__(HsCfg<P, R>::NT, HsCfg<P, R>::CTAS)
     sigmakin_hs_amplitudes_kernel(SigArgs a, Couplings<R> cp, int64_t first, int64_t last, const uint4* __restrict__ rec) {
-  hs_sigmakin_body<P, R, CS_SIMT, true>(a, cp, first, last, rec);
+  hs_sigmakin_body<P, R, CS_SIMT, kSrcRecords>(a, cp, first, last, rec);
 }
 
 template <class P, class R>

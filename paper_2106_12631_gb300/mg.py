@@ -81,6 +81,8 @@ def lib():
             L.mg_pipeline_workspace_bytes.argtypes = [i32, i64, i32]
             L.mg_pipeline_workspace_bytes.restype = i64
             L.mg_pipeline_host.argtypes = [i32, i64, ctypes.c_double, vp, i32, vp, i32, vp, vp, vp, vp, i64, vp]
+            L.mg_sigmakin_rambo.argtypes = [i32, i64, ctypes.c_double, vp, i32, vp, i32, vp, vp, vp]
+            L.mg_sigmakin_seeded.argtypes = [i32, i64, ctypes.c_double, u64, i64, vp, i32, vp, vp, vp]
             L.mg_status_string.argtypes = [i32]
             L.mg_status_string.restype = ctypes.c_char_p
             _lib = L
@@ -284,6 +286,43 @@ def sigmakin(proc, mom: torch.Tensor, mask: torch.Tensor, mode="mixed", me=None,
                              _dev(mask, torch.int32, "mask", (info["nhel"],)),
                              _dev(me, torch.float64, "me", (nevt,)), m, _stream(stream)), "mg_sigmakin")
     return me
+
+
+def _me_wgt(nevt, device, me, wgt):
+    if me is None:
+        me = torch.empty((nevt,), dtype=torch.float64, device=device)
+    if wgt is None:
+        wgt = torch.empty((nevt,), dtype=torch.float64, device=device)
+    return me, wgt
+
+
+def sigmakin_rambo(proc, rnd: torch.Tensor, ecm: float, mask: torch.Tensor, mode="mixed", me=None, wgt=None,
+                   stream=None):
+    """RAMBO and SIGMAKIN in one kernel: rnd (nrows, nevt) float64 CUDA -> (me, wgt),
+    equal to rambo() followed by sigmakin()."""
+    p = _proc(proc)
+    nrows, nevt = rnd.shape
+    m = MODES[mode] if isinstance(mode, str) else int(mode)
+    me, wgt = _me_wgt(nevt, rnd.device, me, wgt)
+    _check(lib().mg_sigmakin_rambo(p, nevt, float(ecm), _dev(rnd, torch.float64, "rnd"), nrows,
+                                   _dev(mask, torch.int32, "mask", (process_info(p)["nhel"],)), m,
+                                   _dev(me, torch.float64, "me", (nevt,)), _dev(wgt, torch.float64, "wgt", (nevt,)),
+                                   _stream(stream)), "mg_sigmakin_rambo")
+    return me, wgt
+
+
+def sigmakin_seeded(proc, nevt: int, ecm: float, seed: int, mask: torch.Tensor, mode="mixed", first_event: int = 0,
+                    me=None, wgt=None, stream=None):
+    """RAMBO with device-drawn uniforms and SIGMAKIN in one kernel -> (me, wgt),
+    equal to rambo_seeded() followed by sigmakin()."""
+    p = _proc(proc)
+    m = MODES[mode] if isinstance(mode, str) else int(mode)
+    me, wgt = _me_wgt(nevt, mask.device, me, wgt)
+    _check(lib().mg_sigmakin_seeded(p, nevt, float(ecm), seed & 0xFFFFFFFFFFFFFFFF, first_event,
+                                    _dev(mask, torch.int32, "mask", (process_info(p)["nhel"],)), m,
+                                    _dev(me, torch.float64, "me", (nevt,)), _dev(wgt, torch.float64, "wgt", (nevt,)),
+                                    _stream(stream)), "mg_sigmakin_seeded")
+    return me, wgt
 
 
 def sigmakin_grad(proc, rnd: torch.Tensor, ecm: float, mask: torch.Tensor, mode="mixed", gout=None, grad=None,
