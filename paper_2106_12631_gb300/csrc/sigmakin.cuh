@@ -51,15 +51,20 @@ struct SigArgs {
   int32_t* __restrict__ hel_out;       // [nevt] chosen helicity (-1 if me = 0), or null
   const double* __restrict__ col_rnd;  // [nevt] uniforms for the colour-flow choice, or null
   int32_t* __restrict__ col_out;       // [nevt] chosen colour flow (-1 if me = 0), or null
-  // RAMBO inside the kernel (the fused entry points): the uniforms of event i,
-  // row k from rnd[k][nevt], or (rnd == nullptr) from the counter-based
-  // generator at (key, first_event + i, k); wgt[nevt] receives RAMBO's weight
-  const double* __restrict__ rnd = nullptr;
-  double* __restrict__ wgt = nullptr;
-  double ecm = 0.0;
-  uint64_t key = 0;
-  int64_t first_event = 0;
-  RamboSetup st{};
+};
+
+// RAMBO inside the SIGMAKIN kernel (the fused entry points), a kernel argument
+// of its own so that the other kernels' arguments stay as they are: the
+// uniforms of event i, row k from rnd[k][nevt], or (rnd == nullptr) from the
+// counter-based generator at (key, first_event + i, k); wgt[nevt] receives
+// RAMBO's weight.
+struct RamboArgs {
+  const double* __restrict__ rnd;
+  double* __restrict__ wgt;
+  double ecm;
+  uint64_t key;
+  int64_t first_event;
+  RamboSetup st;
 };
 
 // ---- dual-amplitude accumulators ------------------------------------------------

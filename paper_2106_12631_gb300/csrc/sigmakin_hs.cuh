@@ -725,7 +725,7 @@ __device__ __noinline__ void rambo_event_fused(const double* __restrict__ rnd, i
 // event first - first at rec[0]).
 template <class P, class R, int CS, int SRC>
 __device__ __forceinline__ void hs_sigmakin_body(const SigArgs& a, const Couplings<R>& cp, int64_t first, int64_t last,
-                                                 const uint4* __restrict__ rec) {
+                                                 const uint4* __restrict__ rec, const RamboArgs* ra = nullptr) {
   using C = HsCfg<P, R>;
   using L = HsLayout<P, R, CS>;
   constexpr bool FROM_RECORDS = SRC == kSrcRecords;
@@ -770,8 +770,8 @@ __device__ __forceinline__ void hs_sigmakin_body(const SigArgs& a, const Couplin
         if (a.hel_out) a.hel_out[e0 + tid] = -1;
         if (a.col_out) a.col_out[e0 + tid] = -1;
         if constexpr (SRC == kSrcRambo)  // the weight all the same
-          rambo_event_fused<P::NPAR - 2>(a.rnd, a.nevt, e0 + tid, a.key, a.first_event, a.ecm, a.st,
-                                         reinterpret_cast<double*>(smem + L::o_ps) + tid * P::NPAR * 4, a.wgt);
+          rambo_event_fused<P::NPAR - 2>(ra->rnd, a.nevt, e0 + tid, ra->key, ra->first_event, ra->ecm, ra->st,
+                                         reinterpret_cast<double*>(smem + L::o_ps) + tid * P::NPAR * 4, ra->wgt);
       }
     }
     return;
@@ -798,8 +798,8 @@ __device__ __forceinline__ void hs_sigmakin_body(const SigArgs& a, const Couplin
     const int64_t e0 = first + (int64_t)blockIdx.x * ev;
     const int nev0 = (int)min((int64_t)ev, last - e0);
     if (tid < nev0)
-      rambo_event_fused<P::NPAR - 2>(a.rnd, a.nevt, e0 + tid, a.key, a.first_event, a.ecm, a.st,
-                                     reinterpret_cast<double*>(smem + L::o_ps) + tid * P::NPAR * 4, a.wgt);
+      rambo_event_fused<P::NPAR - 2>(ra->rnd, a.nevt, e0 + tid, ra->key, ra->first_event, ra->ecm, ra->st,
+                                     reinterpret_cast<double*>(smem + L::o_ps) + tid * P::NPAR * 4, ra->wgt);
     __syncthreads();
     hs_convert_momenta<P, R, L>(smem, nev0);
   }
@@ -836,8 +836,8 @@ __device__ __forceinline__ void hs_sigmakin_body(const SigArgs& a, const Couplin
         // leaves idle when it has fewer items than threads
         const int u = NT - 1 - tid;
         if (u < nevn)
-          rambo_event_fused<P::NPAR - 2>(a.rnd, a.nevt, e0n + u, a.key, a.first_event, a.ecm, a.st,
-                                         reinterpret_cast<double*>(smem + L::o_ps) + u * P::NPAR * 4, a.wgt);
+          rambo_event_fused<P::NPAR - 2>(ra->rnd, a.nevt, e0n + u, ra->key, ra->first_event, ra->ecm, ra->st,
+                                         reinterpret_cast<double*>(smem + L::o_ps) + u * P::NPAR * 4, ra->wgt);
       } else {
         if (nevn > 0) hs_prefetch_momenta<P, L>(smem, a.mom, a.nevt, e0n, nevn);
       }
@@ -954,8 +954,8 @@ __global__ void __launch_bounds__(HsCfg<P, R>::NT, HsCfg<P, R>::CTAS) sigmakin_h
 // RAMBO and SIGMAKIN in one kernel: no momentum buffer in HBM
 template <class P, class R, int CS>
 __global__ void __launch_bounds__(HsCfg<P, R>::NT, HsCfg<P, R>::CTAS)
-    sigmakin_hs_rambo_kernel(SigArgs a, Couplings<R> cp) {
-  hs_sigmakin_body<P, R, CS, kSrcRambo>(a, cp, 0, a.nevt, nullptr);
+    sigmakin_hs_rambo_kernel(SigArgs a, Couplings<R> cp, RamboArgs ra) {
+  hs_sigmakin_body<P, R, CS, kSrcRambo>(a, cp, 0, a.nevt, nullptr, &ra);
 }
 
 }  // namespace mg

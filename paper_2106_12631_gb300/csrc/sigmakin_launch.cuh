@@ -24,14 +24,15 @@ cudaError_t launch_sigmakin_variant(const SigArgs& a, const Couplings<R>& cp, in
 // memory budget and launch bounds are built for (the query has returned 1 for
 // the tcgen05 variant, whose two CTAs per SM fit); should fewer fit, the
 // surplus CTAs start later and take their groups then.
-// FUSED: the kernel that runs RAMBO itself (sigmakin_hs_rambo_kernel).
+// ra != nullptr: the kernel that runs RAMBO itself (sigmakin_hs_rambo_kernel).
 template <class P, class R, int CS, bool FUSED = false>
-cudaError_t launch_sigmakin_hs_variant(const SigArgs& a, const Couplings<R>& cp, int64_t grid, cudaStream_t s) {
+cudaError_t launch_sigmakin_hs_variant(const SigArgs& a, const Couplings<R>& cp, int64_t grid, cudaStream_t s,
+                                       const RamboArgs* ra = nullptr) {
   using L = HsLayout<P, R, CS>;
   constexpr int NT = HsCfg<P, R>::NT;
   constexpr int kMaxDevices = 64;
   static int resident[kMaxDevices];  // CTAs resident on the whole device; 0 until known
-  auto k = FUSED ? sigmakin_hs_rambo_kernel<P, R, CS> : sigmakin_hs_kernel<P, R, CS>;
+  const void* k = FUSED ? (const void*)sigmakin_hs_rambo_kernel<P, R, CS> : (const void*)sigmakin_hs_kernel<P, R, CS>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
   if (e != cudaSuccess) return e;
   grid = (a.nevt + HsCfg<P, R>::EVMIN - 1) / HsCfg<P, R>::EVMIN;
@@ -46,7 +47,8 @@ cudaError_t launch_sigmakin_hs_variant(const SigArgs& a, const Couplings<R>& cp,
     if (dev < kMaxDevices) resident[dev] = cap;
   }
   if (grid > cap) grid = cap;
-  k<<<(unsigned)grid, NT, L::bytes, s>>>(a, cp);
+  if constexpr (FUSED) sigmakin_hs_rambo_kernel<P, R, CS><<<(unsigned)grid, NT, L::bytes, s>>>(a, cp, *ra);
+  else sigmakin_hs_kernel<P, R, CS><<<(unsigned)grid, NT, L::bytes, s>>>(a, cp);
   return cudaGetLastError();
 }
 
@@ -55,14 +57,7 @@ cudaError_t launch_sigmakin_hs_variant(const SigArgs& a, const Couplings<R>& cp,
 // tcgen05 colour sum (helicity-shared kernel); 3 FP64, 4 mixed + tcgen05 with
 // the per-helicity unrolled kernel (every helicity recomputes all its currents)
 inline SigArgs sig_args(const SigLaunch& l) {
-  SigArgs a{l.nevt, l.mom, l.mask, l.me, l.mask_out, l.pp, l.hel_rnd, l.hel_out, l.col_rnd, l.col_out};
-  a.rnd = l.rnd;
-  a.wgt = l.wgt;
-  a.ecm = l.ecm;
-  a.key = l.key;
-  a.first_event = l.first_event;
-  a.st = l.st;
-  return a;
+  return SigArgs{l.nevt, l.mom, l.mask, l.me, l.mask_out, l.pp, l.hel_rnd, l.hel_out, l.col_rnd, l.col_out};
 }
 
 template <class P>
@@ -89,15 +84,16 @@ cudaError_t launch_sigmakin_impl(const SigLaunch& l, int mode, cudaStream_t s) {
 template <class P>
 cudaError_t launch_sigmakin_rambo_impl(const SigLaunch& l, int mode, cudaStream_t s) {
   const SigArgs a = sig_args(l);
+  const RamboArgs ra{l.rnd, l.wgt, l.ecm, l.key, l.first_event, l.st};
   if (l.nevt == 0) return cudaSuccess;
   constexpr bool tc_default = P::NCOLOR >= 48;
   switch (mode) {
-    case 0: return launch_sigmakin_hs_variant<P, double, CS_SIMT, true>(a, l.cd, 0, s);
+    case 0: return launch_sigmakin_hs_variant<P, double, CS_SIMT, true>(a, l.cd, 0, s, &ra);
     case 1:
-      return tc_default ? launch_sigmakin_hs_variant<P, float, CS_TC, true>(a, l.cf, 0, s)
-                        : launch_sigmakin_hs_variant<P, float, CS_SIMT, true>(a, l.cf, 0, s);
-    case 2: return launch_sigmakin_hs_variant<P, float, CS_SIMT, true>(a, l.cf, 0, s);
-    case 5: return launch_sigmakin_hs_variant<P, float, CS_TC, true>(a, l.cf, 0, s);
+      return tc_default ? launch_sigmakin_hs_variant<P, float, CS_TC, true>(a, l.cf, 0, s, &ra)
+                        : launch_sigmakin_hs_variant<P, float, CS_SIMT, true>(a, l.cf, 0, s, &ra);
+    case 2: return launch_sigmakin_hs_variant<P, float, CS_SIMT, true>(a, l.cf, 0, s, &ra);
+    case 5: return launch_sigmakin_hs_variant<P, float, CS_TC, true>(a, l.cf, 0, s, &ra);
   }
   return cudaErrorInvalidValue;
 }
@@ -124,9 +120,9 @@ cudaError_t launch_filter_impl(const SigLaunch& l, cudaStream_t s) {
   extern template cudaError_t launch_sigmakin_variant<Proc##N, double, CS_SIMT>(                        \
       const SigArgs&, const Couplings<double>&, int64_t, cudaStream_t);                                  \
   extern template cudaError_t launch_sigmakin_hs_variant<Proc##N, double, CS_SIMT>(                     \
-      const SigArgs&, const Couplings<double>&, int64_t, cudaStream_t);                                  \
+      const SigArgs&, const Couplings<double>&, int64_t, cudaStream_t, const RamboArgs*);                \
   extern template cudaError_t launch_sigmakin_hs_variant<Proc##N, double, CS_SIMT, true>(               \
-      const SigArgs&, const Couplings<double>&, int64_t, cudaStream_t);                                  \
+      const SigArgs&, const Couplings<double>&, int64_t, cudaStream_t, const RamboArgs*);                \
   extern template cudaError_t launch_filter_impl<Proc##N>(const SigLaunch&, cudaStream_t);              \
   cudaError_t launch_sigmakin_p##N(const SigLaunch& a, int mode, cudaStream_t s) {                      \
     return launch_sigmakin_impl<Proc##N>(a, mode, s);                                                    \
@@ -142,8 +138,8 @@ cudaError_t launch_filter_impl(const SigLaunch& l, cudaStream_t s) {
   template cudaError_t launch_sigmakin_variant<Proc##N, double, CS_SIMT>(                               \
       const SigArgs&, const Couplings<double>&, int64_t, cudaStream_t);                                  \
   template cudaError_t launch_sigmakin_hs_variant<Proc##N, double, CS_SIMT>(                            \
-      const SigArgs&, const Couplings<double>&, int64_t, cudaStream_t);                                  \
+      const SigArgs&, const Couplings<double>&, int64_t, cudaStream_t, const RamboArgs*);                \
   template cudaError_t launch_sigmakin_hs_variant<Proc##N, double, CS_SIMT, true>(                      \
-      const SigArgs&, const Couplings<double>&, int64_t, cudaStream_t);                                  \
+      const SigArgs&, const Couplings<double>&, int64_t, cudaStream_t, const RamboArgs*);                \
   template cudaError_t launch_filter_impl<Proc##N>(const SigLaunch&, cudaStream_t);                     \
   }
