@@ -1,0 +1,58 @@
+"""Register budget of the default SIGMAKIN kernels (no GPU needed: ptxas only).
+
+The helicity-shared kernels run at a fixed number of CTAs per SM, so the
+register count per thread is capped (126 for gg -> t t~ g g at two 256-thread
+CTAs per SM, 80 for gg -> t t~ g at three), and a change anywhere in their
+code or arguments can push them into spilling to local memory, which cost
+gg -> t t~ g 8 % once.  The default kernels of the four processes, in both
+precisions, must compile without spills or local stack.
+"""
+import concurrent.futures as cf
+import os
+import re
+import shutil
+import subprocess
+import tempfile
+
+import pytest
+
+from paper_2106_12631_gb300 import build as B
+
+pytestmark = pytest.mark.slow
+
+
+def ptxas_report(src: str) -> dict:
+    """ptxas -v report per compiled entry: name -> (stack bytes, spill stores, spill loads)."""
+    with tempfile.TemporaryDirectory() as d:
+        cmd = [B.nvcc(), *B.ARCH, *B.FLAGS, "-Xptxas", "-v", "-c", src, "-o", os.path.join(d, "x.o")]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-2000:]
+    out, name = {}, None
+    for ln in r.stderr.splitlines():
+        m = re.search(r"Compiling entry function '(\w+)'", ln)
+        if m:
+            name = m.group(1)
+            continue
+        m = re.search(r"(\d+) bytes stack frame, (\d+) bytes spill stores, (\d+) bytes spill loads", ln)
+        if m and name:
+            out[name] = tuple(int(x) for x in m.groups())
+            name = None
+    return out
+
+
+@pytest.mark.skipif(shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"),
+                    reason="nvcc not available")
+def test_default_kernels_do_not_spill():
+    srcs = [os.path.join(B.CSRC, f) for f in ("sigmakin_p1.cu", "sigmakin_p2.cu", "sigmakin_p3.cu", "sigmakin_p4.cu",
+                                               "sigmakin_p3_fp64.cu", "sigmakin_p4_fp64.cu")]
+    with cf.ThreadPoolExecutor(len(srcs)) as ex:
+        reports = list(ex.map(ptxas_report, srcs))
+    checked = 0
+    for rep in reports:
+        for name, (stack, st, ld) in rep.items():
+            # the helicity-shared kernel with the CUDA-core colour sum (template
+            # argument CS = 0): the default of MG_MIXED below 48 colour flows and of MG_FP64
+            if "sigmakin_hs_kernel" in name and ("EfLi0E" in name or "EdLi0E" in name):
+                assert (stack, st, ld) == (0, 0, 0), (name, stack, st, ld)
+                checked += 1
+    assert checked >= 6, checked
