@@ -42,6 +42,10 @@ SM_MAX_MHZ = 2070.0
 # scaled by events; it reads the momenta once and writes |M|^2), valid only
 # while the kernel sources are the ones captured.
 SIGMAKIN_TRAFFIC = {"bytes_per_event": 192.70, "sources_sha1": "b05d5b5d027d7253172100ceb89d18b1f9e14c8d"}
+# Tensor-pipe activity of the tcgen05 colour-sum variant from the same kind of
+# capture (sm__pipe_tensor_cycles_active, fraction of its peak), valid while
+# the kernel sources are the ones captured.
+TC_TENSOR_PIPE = {"frac": 0.0149, "sources_sha1": "b05d5b5d027d7253172100ceb89d18b1f9e14c8d"}
 SIGMAKIN_SOURCES = ["paper_2106_12631_gb300/csrc/" + f for f in
                     ("sigmakin_hs.cuh", "sigmakin_launch.cuh", "sigmakin.cuh", "helas.cuh", "colour_tc.cuh",
                      "mg_types.cuh", "process.cuh", "gen/proc4.cuh")]
@@ -562,7 +566,10 @@ def main():
     if args.mode == "mixed" and not args.no_others:
         tt, kt = timed("mixed_tc", max(1, min(args.steps, 2)))
         tensor_core = {"mode": "mixed_tc", "value": world * nevt * max(1, min(args.steps, 2)) / tt, "unit": UNIT,
-                       "sigmakin_ms": 1e3 * statistics.mean(kt)}
+                       "sigmakin_ms": 1e3 * statistics.mean(kt),
+                       "tensor_pipe_active": TC_TENSOR_PIPE["frac"] if TC_TENSOR_PIPE["sources_sha1"] == sources_sha1()
+                       else None,
+                       "tensor_pipe_source": "ncu sm__pipe_tensor_cycles_active of one 2^18-event launch"}
 
     # SIGMAKIN split in two kernels per chunk (currents, then amplitudes), the
     # chunks' launches replayed from a CUDA graph; same momenta and mask
@@ -608,14 +615,17 @@ def main():
     # end to end through the library's host-buffer entry point (mg_pipeline_host):
     # every step copies the batch's random numbers from pinned host memory, runs
     # RAMBO + SIGMAKIN + the event sum, and copies me and the event sum back.
+    # Consecutive steps alternate between two streams, workspaces and host
+    # output buffers, so one step's copies overlap the previous step's kernels.
     # Each step's helicity mask comes from its own 16 filter events, drawn and
     # filtered on the device (mg_rambo_seeded, mg_filter_helicities) on the
-    # high-priority stream one step ahead, into one of two mask buffers, so the
-    # filter runs beside the previous step's pipeline.
+    # high-priority stream one step ahead, into one of two mask buffers.
     rnd_h = torch.from_numpy(I.uniforms(seed, 16, nevt, first_event=shard_first_event(rank, nevt))).pin_memory()
-    me_h = torch.empty(nevt, dtype=torch.float64).pin_memory()
-    sums_h = torch.empty(3, dtype=torch.float64).pin_memory()
-    ws = torch.empty(mg.pipeline_workspace_bytes(proc, nevt, 16) // 8 + 2, dtype=torch.float64, device=dev)
+    me_hs = [torch.empty(nevt, dtype=torch.float64).pin_memory() for _ in range(2)]
+    sums_hs = [torch.empty(3, dtype=torch.float64).pin_memory() for _ in range(2)]
+    wss = [torch.empty(mg.pipeline_workspace_bytes(proc, nevt, 16) // 8 + 2, dtype=torch.float64, device=dev)
+           for _ in range(2)]
+    pipes = [stream, torch.cuda.Stream()]
     masks = [torch.empty_like(mask) for _ in range(2)]
     mask_ready = [torch.cuda.Event() for _ in range(2)]
     mask_free = [torch.cuda.Event() for _ in range(2)]
@@ -629,15 +639,18 @@ def main():
         mask_ready[b].record(filt)
 
     def steps_e2e(n):
+        pipes[1].wait_stream(stream)
         filt.wait_stream(stream)
         filter_e2e(0)
         for k in range(n):
             if k + 1 < n:
                 filter_e2e(k + 1)
-            stream.wait_event(mask_ready[k & 1])
-            mg.pipeline_host(proc, rnd_h, ecm, masks[k & 1], mode=args.mode, me_host=me_h, sums_host=sums_h,
-                             workspace=ws, stream=stream)
-            mask_free[k & 1].record(stream)
+            b = k & 1
+            pipes[b].wait_event(mask_ready[b])
+            mg.pipeline_host(proc, rnd_h, ecm, masks[b], mode=args.mode, me_host=me_hs[b], sums_host=sums_hs[b],
+                             workspace=wss[b], stream=pipes[b])
+            mask_free[b].record(pipes[b])
+        stream.wait_stream(pipes[1])
 
     steps_e2e(args.warmup)
     torch.cuda.synchronize()
@@ -649,14 +662,15 @@ def main():
     torch.cuda.synchronize()
     te2e = e0.elapsed_time(e1) / 1e3
     te2e = max_over_ranks(te2e, world, dev)
-    e2e_same = bool(torch.equal(me_h, me_main.cpu()))
+    e2e_same = bool(torch.equal(me_hs[(args.steps - 1) & 1], me_main.cpu()))
     sum_over_ranks(sums, world)
     e2e = {"value": world * nevt * args.steps / te2e, "unit": UNIT,
            "h2d_bytes_per_step": 8 * rnd_h.numel(),
            "d2h_bytes_per_step": 8 * nevt + 8 * 3,
-           "api": "mg_pipeline_host (host rnd in; host me and event sum out), filter on the device",
+           "api": "mg_pipeline_host (host rnd in; host me and event sum out), filter on the device; "
+                  "steps alternate between two streams",
            "me_identical_to_device_step": e2e_same}
-    del ws
+    del wss
 
     # roofline of the dominant kernel (SIGMAKIN): FP32 CUDA-core arithmetic.
     # Algorithmic flops per event of the helicity-shared kernel: every current
