@@ -506,29 +506,47 @@ def main():
     kernel_launches_per_step = 6  # rambo(filter), filter, rambo, sigmakin, event_sum x2
 
     # the helicity filter runs on a high-priority stream next to the batch's
-    # RAMBO: its few long CTAs take SMs as RAMBO's short CTAs retire
+    # RAMBO: its few long CTAs take SMs as RAMBO's short CTAs retire.
+    # Consecutive steps alternate between two streams, each with its own
+    # momentum, weight, matrix-element, event-sum and mask buffers, so one
+    # step's RAMBO can fill the tail of the previous step's SIGMAKIN; every
+    # step still runs the filter, RAMBO, SIGMAKIN and the event sum of its batch.
     filt = torch.cuda.Stream(priority=-1)
+    pipes = [stream, torch.cuda.Stream()]
+    bufs = [(mom, wgt, me, out, scratch, mask),
+            (torch.empty_like(mom), torch.empty_like(wgt), torch.empty_like(me), torch.empty_like(out),
+             torch.empty_like(scratch), torch.empty_like(mask))]
+    mask_ready = [torch.cuda.Event() for _ in range(2)]
+    mask_free = [torch.cuda.Event() for _ in range(2)]
 
-    def step(mode, ev=None):
-        filt.wait_stream(stream)  # the previous step's SIGMAKIN has read mask
+    def step(k, mode):
+        b = k & 1
+        st = pipes[b]
+        mom_b, wgt_b, me_b, out_b, scr_b, mask_b = bufs[b]
+        filt.wait_event(mask_free[b])  # the SIGMAKIN two steps back has read this mask
         mg.rambo(proc, frnd, ecm, mom=fmom, wgt=fwgt, stream=filt)
-        mg.filter_helicities(proc, fmom, mask=mask, stream=filt)
-        mg.rambo(proc, rnd, ecm, mom=mom, wgt=wgt, stream=stream)
+        mg.filter_helicities(proc, fmom, mask=mask_b, stream=filt)
+        mask_ready[b].record(filt)
+        mg.rambo(proc, rnd, ecm, mom=mom_b, wgt=wgt_b, stream=st)
+        st.wait_event(mask_ready[b])
+        mg.sigmakin(proc, mom_b, mask_b, mode=mode, me=me_b, stream=st)
+        mask_free[b].record(st)
+        mg.event_sum(me_b, wgt_b, out=out_b, scratch=scr_b, stream=st)
+
+    def run_steps(mode, n):
+        pipes[1].wait_stream(stream)
+        filt.wait_stream(stream)
+        for k in range(n):
+            step(k, mode)
+        stream.wait_stream(pipes[1])
         stream.wait_stream(filt)
-        if ev is not None:
-            ev[0].record(stream)
-        mg.sigmakin(proc, mom, mask, mode=mode, me=me, stream=stream)
-        if ev is not None:
-            ev[1].record(stream)
-        mg.event_sum(me, wgt, out=out, scratch=scratch, stream=stream)
 
     def barrier():
         if world > 1:
             torch.distributed.barrier()
 
     def timed(mode, steps):
-        for _ in range(args.warmup):
-            step(mode)
+        run_steps(mode, args.warmup)
         torch.cuda.synchronize()
         barrier()
         kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
@@ -536,12 +554,20 @@ def main():
         torch.cuda.synchronize()
         barrier()
         t0.record(stream)
-        for k in range(steps):
-            step(mode, kev[k])
+        run_steps(mode, steps)
         t1.record(stream)
         torch.cuda.synchronize()
         barrier()
         total = t0.elapsed_time(t1) / 1e3
+        # SIGMAKIN's own launch duration (for the roofline and the comparison
+        # lines): in the pipelined steps a launch's events would also cover the
+        # wait for the previous step's kernel, so the kernel is timed right
+        # after the steps, alone, back to back on one stream, on the same inputs
+        for a, b in kev:
+            a.record(stream)
+            mg.sigmakin(proc, mom, mask, mode=mode, me=me, stream=stream)
+            b.record(stream)
+        torch.cuda.synchronize()
         kern = [a.elapsed_time(b) / 1e3 for a, b in kev]
         return max_over_ranks(total, world, dev), kern
 
@@ -702,6 +728,7 @@ def main():
                                "mt=173 wt=1.491 alpha_s=0.118",
                    "mode": args.mode, "events_per_gpu": nevt, "good_helicities": ngood,
                    "l2": "inputs larger than L2 (336 MiB per step), no flush",
+                   "steps": "filter, RAMBO, SIGMAKIN and event sum per step; consecutive steps on two streams",
                    "parallelism": "dp%d (independent event batches)" % world},
         "sigmakin_ms": 1e3 * ksec,
         "fp64": fp64,

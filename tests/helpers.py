@@ -90,3 +90,4 @@ def oracle_conditioning(orc, proc, mom, prm=None, nthreads=8):
         mr = np.ascontiguousarray(np.stack([rotate(mom[l], axis, ang) for l in range(mom.shape[0])]))
         worst = np.maximum(worst, np.abs(orc.me(proc, mr, prm, nthreads=nthreads) / me0 - 1))
     return me0, worst
+
