@@ -78,17 +78,13 @@ struct Proc1 {
             w4_acc_conj(Xb, Y, ab);
             const W4<R> Yb = w4_conj_scale(X, ab);
             if (full) {
-              W4<R> s = Yb;
-              w4_warp_sum<3u>(s);
-              if ((lane & 3u) == 0 && act) slot_add(curb, 8 + vy, s);
+              w4_warp_reduce_add<3u, false>(Yb, curb, 8 + vy, lane, act);
             } else {
               curb.atomic_add(8 + vy, Yb);
             }
           }
           if (full) {
-            W4<R> s = Xb;
-            w4_warp_sum<12u>(s);
-            if ((lane & 12u) == 0 && act) slot_add(xbb, 0 + vx, s);
+            w4_warp_reduce_add<12u, false>(Xb, xbb, 0 + vx, lane, act);
           } else {
             xbb.atomic_add(0 + vx, Xb);
           }
@@ -104,17 +100,13 @@ struct Proc1 {
             w4_acc_conj(Xb, Y, ab);
             const W4<R> Yb = w4_conj_scale(X, ab);
             if (full) {
-              W4<R> s = Yb;
-              w4_warp_sum<3u>(s);
-              if ((lane & 3u) == 0 && act) slot_add(curb, 12 + vy, s);
+              w4_warp_reduce_add<3u, false>(Yb, curb, 12 + vy, lane, act);
             } else {
               curb.atomic_add(12 + vy, Yb);
             }
           }
           if (full) {
-            W4<R> s = Xb;
-            w4_warp_sum<12u>(s);
-            if ((lane & 12u) == 0 && act) slot_add(xbb, 4 + vx, s);
+            w4_warp_reduce_add<12u, false>(Xb, xbb, 4 + vx, lane, act);
           } else {
             xbb.atomic_add(4 + vx, Xb);
           }

@@ -83,17 +83,13 @@ struct Proc2 {
             w4_acc_conj(Xb, Y, ab);
             const W4<R> Yb = w4_conj_scale(X, ab);
             if (full) {
-              W4<R> s = Yb;
-              w4_warp_sum<9u>(s);
-              if ((lane & 9u) == 0 && act) slot_add(curb, 16 + vy, s);
+              w4_warp_reduce_add<9u, false>(Yb, curb, 16 + vy, lane, act);
             } else {
               curb.atomic_add(16 + vy, Yb);
             }
           }
           if (full) {
-            W4<R> s = Xb;
-            w4_warp_sum<6u>(s);
-            if ((lane & 6u) == 0 && act) slot_add(xbb, 0 + vx, s);
+            w4_warp_reduce_add<6u, false>(Xb, xbb, 0 + vx, lane, act);
           } else {
             xbb.atomic_add(0 + vx, Xb);
           }
@@ -109,17 +105,13 @@ struct Proc2 {
             w4_acc_conj(Xb, Y, ab);
             const W4<R> Yb = w4_conj_scale(X, ab);
             if (full) {
-              W4<R> s = Yb;
-              w4_warp_sum<5u>(s);
-              if ((lane & 5u) == 0 && act) slot_add(curb, 12 + vy, s);
+              w4_warp_reduce_add<5u, false>(Yb, curb, 12 + vy, lane, act);
             } else {
               curb.atomic_add(12 + vy, Yb);
             }
           }
           if (full) {
-            W4<R> s = Xb;
-            w4_warp_sum<10u>(s);
-            if ((lane & 10u) == 0 && act) slot_add(xbb, 4 + vx, s);
+            w4_warp_reduce_add<10u, false>(Xb, xbb, 4 + vx, lane, act);
           } else {
             xbb.atomic_add(4 + vx, Xb);
           }
@@ -135,17 +127,13 @@ struct Proc2 {
             w4_acc_conj(Xb, Y, ab);
             const W4<R> Yb = w4_conj_scale(X, ab);
             if (full) {
-              W4<R> s = Yb;
-              w4_warp_sum<3u>(s);
-              if ((lane & 3u) == 0 && act) slot_add(curb, 8 + vy, s);
+              w4_warp_reduce_add<3u, false>(Yb, curb, 8 + vy, lane, act);
             } else {
               curb.atomic_add(8 + vy, Yb);
             }
           }
           if (full) {
-            W4<R> s = Xb;
-            w4_warp_sum<12u>(s);
-            if ((lane & 12u) == 0 && act) slot_add(xbb, 8 + vx, s);
+            w4_warp_reduce_add<12u, false>(Xb, xbb, 8 + vx, lane, act);
           } else {
             xbb.atomic_add(8 + vx, Xb);
           }

@@ -147,17 +147,13 @@ struct Proc3 {
             w4_acc_conj(Xb, Y, ab);
             const W4<R> Yb = w4_conj_scale(X, ab);
             if (full) {
-              W4<R> s = Yb;
-              w4_warp_sum<26u>(s);
-              if ((lane & 26u) == 0 && act) slot_add(curb, 66 + vy, s);
+              w4_warp_reduce_add<26u, false>(Yb, curb, 66 + vy, lane, act);
             } else {
               curb.atomic_add(66 + vy, Yb);
             }
           }
           if (full) {
-            W4<R> s = Xb;
-            w4_warp_sum<5u>(s);
-            if ((lane & 5u) == 0 && act) slot_add(xbb, 0 + vx, s);
+            w4_warp_reduce_add<5u, false>(Xb, xbb, 0 + vx, lane, act);
           } else {
             xbb.atomic_add(0 + vx, Xb);
           }
@@ -173,17 +169,13 @@ struct Proc3 {
             w4_acc_conj(Xb, Y, ab);
             const W4<R> Yb = w4_conj_scale(X, ab);
             if (full) {
-              W4<R> s = Yb;
-              w4_warp_sum<26u>(s);
-              if ((lane & 26u) == 0 && act) slot_add(curb, 66 + vy, s);
+              w4_warp_reduce_add<26u, false>(Yb, curb, 66 + vy, lane, act);
             } else {
               curb.atomic_add(66 + vy, Yb);
             }
           }
           if (full) {
-            W4<R> s = Xb;
-            w4_warp_sum<5u>(s);
-            if ((lane & 5u) == 0 && act) slot_add(xbb, 8 + vx, s);
+            w4_warp_reduce_add<5u, false>(Xb, xbb, 8 + vx, lane, act);
           } else {
             xbb.atomic_add(8 + vx, Xb);
           }
@@ -199,17 +191,13 @@ struct Proc3 {
             w4_acc_conj(Xb, Y, ab);
             const W4<R> Yb = w4_conj_scale(X, ab);
             if (full) {
-              W4<R> s = Yb;
-              w4_warp_sum<26u>(s);
-              if ((lane & 26u) == 0 && act) slot_add(curb, 66 + vy, s);
+              w4_warp_reduce_add<26u, false>(Yb, curb, 66 + vy, lane, act);
             } else {
               curb.atomic_add(66 + vy, Yb);
             }
           }
           if (full) {
-            W4<R> s = Xb;
-            w4_warp_sum<5u>(s);
-            if ((lane & 5u) == 0 && act) slot_add(xbb, 16 + vx, s);
+            w4_warp_reduce_add<5u, false>(Xb, xbb, 16 + vx, lane, act);
           } else {
             xbb.atomic_add(16 + vx, Xb);
           }
@@ -225,17 +213,13 @@ struct Proc3 {
             w4_acc_conj(Xb, Y, ab);
             const W4<R> Yb = w4_conj_scale(X, ab);
             if (full) {
-              W4<R> s = Yb;
-              w4_warp_sum<19u>(s);
-              if ((lane & 19u) == 0 && act) slot_add(curb, 62 + vy, s);
+              w4_warp_reduce_add<19u, false>(Yb, curb, 62 + vy, lane, act);
             } else {
               curb.atomic_add(62 + vy, Yb);
             }
           }
           if (full) {
-            W4<R> s = Xb;
-            w4_warp_sum<12u>(s);
-            if ((lane & 12u) == 0 && act) slot_add(xbb, 24 + vx, s);
+            w4_warp_reduce_add<12u, false>(Xb, xbb, 24 + vx, lane, act);
           } else {
             xbb.atomic_add(24 + vx, Xb);
           }
@@ -251,17 +235,13 @@ struct Proc3 {
             w4_acc_conj(Xb, Y, ab);
             const W4<R> Yb = w4_conj_scale(X, ab);
             if (full) {
-              W4<R> s = Yb;
-              w4_warp_sum<19u>(s);
-              if ((lane & 19u) == 0 && act) slot_add(curb, 62 + vy, s);
+              w4_warp_reduce_add<19u, false>(Yb, curb, 62 + vy, lane, act);
             } else {
               curb.atomic_add(62 + vy, Yb);
             }
           }
           if (full) {
-            W4<R> s = Xb;
-            w4_warp_sum<12u>(s);
-            if ((lane & 12u) == 0 && act) slot_add(xbb, 32 + vx, s);
+            w4_warp_reduce_add<12u, false>(Xb, xbb, 32 + vx, lane, act);
           } else {
             xbb.atomic_add(32 + vx, Xb);
           }
@@ -277,17 +257,13 @@ struct Proc3 {
             w4_acc_conj(Xb, Y, ab);
             const W4<R> Yb = w4_conj_scale(X, ab);
             if (full) {
-              W4<R> s = Yb;
-              w4_warp_sum<19u>(s);
-              if ((lane & 19u) == 0 && act) slot_add(curb, 62 + vy, s);
+              w4_warp_reduce_add<19u, false>(Yb, curb, 62 + vy, lane, act);
             } else {
               curb.atomic_add(62 + vy, Yb);
             }
           }
           if (full) {
-            W4<R> s = Xb;
-            w4_warp_sum<12u>(s);
-            if ((lane & 12u) == 0 && act) slot_add(xbb, 40 + vx, s);
+            w4_warp_reduce_add<12u, false>(Xb, xbb, 40 + vx, lane, act);
           } else {
             xbb.atomic_add(40 + vx, Xb);
           }
@@ -303,17 +279,13 @@ struct Proc3 {
             w4_acc_conj(Xb, Y, ab);
             const W4<R> Yb = w4_conj_scale(X, ab);
             if (full) {
-              W4<R> s = Yb;
-              w4_warp_sum<11u>(s);
-              if ((lane & 11u) == 0 && act) slot_add(curb, 58 + vy, s);
+              w4_warp_reduce_add<11u, false>(Yb, curb, 58 + vy, lane, act);
             } else {
               curb.atomic_add(58 + vy, Yb);
             }
           }
           if (full) {
-            W4<R> s = Xb;
-            w4_warp_sum<20u>(s);
-            if ((lane & 20u) == 0 && act) slot_add(xbb, 48 + vx, s);
+            w4_warp_reduce_add<20u, false>(Xb, xbb, 48 + vx, lane, act);
           } else {
             xbb.atomic_add(48 + vx, Xb);
           }
@@ -329,17 +301,13 @@ struct Proc3 {
             w4_acc_conj(Xb, Y, ab);
             const W4<R> Yb = w4_conj_scale(X, ab);
             if (full) {
-              W4<R> s = Yb;
-              w4_warp_sum<11u>(s);
-              if ((lane & 11u) == 0 && act) slot_add(curb, 58 + vy, s);
+              w4_warp_reduce_add<11u, false>(Yb, curb, 58 + vy, lane, act);
             } else {
               curb.atomic_add(58 + vy, Yb);
             }
           }
           if (full) {
-            W4<R> s = Xb;
-            w4_warp_sum<20u>(s);
-            if ((lane & 20u) == 0 && act) slot_add(xbb, 56 + vx, s);
+            w4_warp_reduce_add<20u, false>(Xb, xbb, 56 + vx, lane, act);
           } else {
             xbb.atomic_add(56 + vx, Xb);
           }
@@ -355,17 +323,13 @@ struct Proc3 {
             w4_acc_conj(Xb, Y, ab);
             const W4<R> Yb = w4_conj_scale(X, ab);
             if (full) {
-              W4<R> s = Yb;
-              w4_warp_sum<11u>(s);
-              if ((lane & 11u) == 0 && act) slot_add(curb, 58 + vy, s);
+              w4_warp_reduce_add<11u, false>(Yb, curb, 58 + vy, lane, act);
             } else {
               curb.atomic_add(58 + vy, Yb);
             }
           }
           if (full) {
-            W4<R> s = Xb;
-            w4_warp_sum<20u>(s);
-            if ((lane & 20u) == 0 && act) slot_add(xbb, 64 + vx, s);
+            w4_warp_reduce_add<20u, false>(Xb, xbb, 64 + vx, lane, act);
           } else {
             xbb.atomic_add(64 + vx, Xb);
           }
@@ -382,16 +346,12 @@ struct Proc3 {
             w4_acc_conj(Xb, Y, ab);
             const W4<R> Yb = w4_conj_scale(X, ab);
             if (full) {
-              W4<R> s = Yb;
-              w4_warp_sum<6u>(s);
-              if ((lane & 6u) == 0 && act) slot_add(curb, 34 + vy, s);
+              w4_warp_reduce_add<6u, false>(Yb, curb, 34 + vy, lane, act);
             } else {
               curb.atomic_add(34 + vy, Yb);
             }
             if (full) {
-              W4<R> s = Yb;
-              w4_warp_sum<6u>(s);
-              if ((lane & 6u) == 0 && act) slot_add(curb, 78 + vy, s);
+              w4_warp_reduce_add<6u, false>(Yb, curb, 78 + vy, lane, act);
             } else {
               curb.atomic_add(78 + vy, Yb);
             }
@@ -404,16 +364,12 @@ struct Proc3 {
             w4_acc_conj(Xb, Y, ab);
             const W4<R> Yb = w4_conj_scale(X, ab);
             if (full) {
-              W4<R> s = Yb;
-              w4_warp_sum<6u>(s);
-              if ((lane & 6u) == 0 && act) slot_add(curb, 42 + vy, s);
+              w4_warp_reduce_add<6u, false>(Yb, curb, 42 + vy, lane, act);
             } else {
               curb.atomic_add(42 + vy, Yb);
             }
             if (full) {
-              W4<R> s = Yb;
-              w4_warp_sum<6u>(s);
-              if ((lane & 6u) == 0 && act) slot_add(curb, 86 + vy, s);
+              w4_warp_reduce_add<6u, false>(Yb, curb, 86 + vy, lane, act);
             } else {
               curb.atomic_add(86 + vy, Yb);
             }
@@ -426,24 +382,18 @@ struct Proc3 {
             w4_acc_conj(Xb, Y, ab);
             const W4<R> Yb = w4_conj_scale(X, ab);
             if (full) {
-              W4<R> s = Yb;
-              w4_warp_sum<6u>(s);
-              if ((lane & 6u) == 0 && act) slot_add(curb, 50 + vy, s);
+              w4_warp_reduce_add<6u, false>(Yb, curb, 50 + vy, lane, act);
             } else {
               curb.atomic_add(50 + vy, Yb);
             }
             if (full) {
-              W4<R> s = w4_neg(Yb);
-              w4_warp_sum<6u>(s);
-              if ((lane & 6u) == 0 && act) slot_add(curb, 70 + vy, s);
+              w4_warp_reduce_add<6u, false>(w4_neg(Yb), curb, 70 + vy, lane, act);
             } else {
               curb.atomic_add(70 + vy, w4_neg(Yb));
             }
           }
           if (full) {
-            W4<R> s = Xb;
-            w4_warp_sum<25u>(s);
-            if ((lane & 25u) == 0 && act) slot_add(xbb, 72 + vx, s);
+            w4_warp_reduce_add<25u, false>(Xb, xbb, 72 + vx, lane, act);
           } else {
             xbb.atomic_add(72 + vx, Xb);
           }
@@ -459,17 +409,13 @@ struct Proc3 {
             w4_acc_conj(Xb, Y, ab);
             const W4<R> Yb = w4_conj_scale(X, ab);
             if (full) {
-              W4<R> s = Yb;
-              w4_warp_sum<28u>(s);
-              if ((lane & 28u) == 0 && act) slot_add(curb, 18 + vy, s);
+              w4_warp_reduce_add<28u, false>(Yb, curb, 18 + vy, lane, act);
             } else {
               curb.atomic_add(18 + vy, Yb);
             }
           }
           if (full) {
-            W4<R> s = Xb;
-            w4_warp_sum<3u>(s);
-            if ((lane & 3u) == 0 && act) slot_add(xbb, 76 + vx, s);
+            w4_warp_reduce_add<3u, false>(Xb, xbb, 76 + vx, lane, act);
           } else {
             xbb.atomic_add(76 + vx, Xb);
           }
@@ -485,17 +431,13 @@ struct Proc3 {
             w4_acc_conj(Xb, Y, ab);
             const W4<R> Yb = w4_conj_scale(X, ab);
             if (full) {
-              W4<R> s = Yb;
-              w4_warp_sum<21u>(s);
-              if ((lane & 21u) == 0 && act) slot_add(curb, 14 + vy, s);
+              w4_warp_reduce_add<21u, false>(Yb, curb, 14 + vy, lane, act);
             } else {
               curb.atomic_add(14 + vy, Yb);
             }
           }
           if (full) {
-            W4<R> s = Xb;
-            w4_warp_sum<10u>(s);
-            if ((lane & 10u) == 0 && act) slot_add(xbb, 84 + vx, s);
+            w4_warp_reduce_add<10u, false>(Xb, xbb, 84 + vx, lane, act);
           } else {
             xbb.atomic_add(84 + vx, Xb);
           }
@@ -511,17 +453,13 @@ struct Proc3 {
             w4_acc_conj(Xb, Y, ab);
             const W4<R> Yb = w4_conj_scale(X, ab);
             if (full) {
-              W4<R> s = Yb;
-              w4_warp_sum<13u>(s);
-              if ((lane & 13u) == 0 && act) slot_add(curb, 10 + vy, s);
+              w4_warp_reduce_add<13u, false>(Yb, curb, 10 + vy, lane, act);
             } else {
               curb.atomic_add(10 + vy, Yb);
             }
           }
           if (full) {
-            W4<R> s = Xb;
-            w4_warp_sum<18u>(s);
-            if ((lane & 18u) == 0 && act) slot_add(xbb, 92 + vx, s);
+            w4_warp_reduce_add<18u, false>(Xb, xbb, 92 + vx, lane, act);
           } else {
             xbb.atomic_add(92 + vx, Xb);
           }

@@ -463,6 +463,78 @@ __device__ __forceinline__ void external_adj(int kind, const R* p, R m, int hel,
 
 // slot i += w by its only writer (a plain read, add and write: the adjoint
 // contractions' warp sums leave one lane per slot and event)
+// ---- sum of a W4 over a group of lanes, added into a slot -----------------
+// The lanes that differ only in the bits of MASK (at most the five lane bits)
+// hold terms of one slot's adjoint.  Reduce-scatter: at each of the first
+// (up to three) bits of MASK the two partner lanes swap half of the
+// components they still hold and each keeps the sum of the other half (4, 2,
+// then 1 values exchanged instead of all 8 per level); further bits sum the
+// kept components; every lane whose further bits are 0 then adds its
+// components into the slot (each component has one writing lane).
+constexpr int popc5(unsigned m) {
+  return (int)(m & 1u) + (int)(m >> 1 & 1u) + (int)(m >> 2 & 1u) + (int)(m >> 3 & 1u) + (int)(m >> 4 & 1u);
+}
+constexpr int nth_set_bit(unsigned m, int t) {
+  for (int b = 0; b < 32; ++b)
+    if (m >> b & 1u) {
+      if (t == 0) return b;
+      --t;
+    }
+  return -1;
+}
+constexpr unsigned drop_low_set_bits(unsigned m, int k) {
+  for (int i = 0; i < k; ++i) m &= m - 1u;
+  return m;
+}
+
+template <unsigned MASK, int T, int S, class R>
+__device__ __forceinline__ void rs_split(R* v, int lane, int& off) {
+  if constexpr (T < S) {
+    constexpr int b = nth_set_bit(MASK, T), h = (8 >> T) / 2;
+    const bool hi = (lane >> b & 1) != 0;
+#pragma unroll
+    for (int j = 0; j < h; ++j) {
+      const R send = hi ? v[j] : v[h + j];
+      const R keep = hi ? v[h + j] : v[j];
+      v[j] = keep + __shfl_xor_sync(0xffffffffu, send, 1 << b);
+    }
+    off += hi ? h : 0;
+    rs_split<MASK, T + 1, S, R>(v, lane, off);
+  }
+}
+
+template <unsigned MASK, int T, int NB, int K, class R>
+__device__ __forceinline__ void rs_sum(R* v) {
+  if constexpr (T < NB) {
+    constexpr int b = nth_set_bit(MASK, T);
+#pragma unroll
+    for (int j = 0; j < K; ++j) v[j] += __shfl_xor_sync(0xffffffffu, v[j], 1 << b);
+    rs_sum<MASK, T + 1, NB, K, R>(v);
+  }
+}
+
+// ATOMIC: the slot also receives adds from other warps (shared-memory atomics).
+template <unsigned MASK, bool ATOMIC, class R, int N>
+__device__ __forceinline__ void w4_warp_reduce_add(const W4<R>& w, const Slots<R, N>& s, int i, int lane, bool act) {
+  static_assert(MASK < 32u, "lane bits only");
+  constexpr int NB = popc5(MASK), S = NB < 3 ? NB : 3, K = 8 >> S;
+  R v[8] = {w.w[0].re, w.w[0].im, w.w[1].re, w.w[1].im, w.w[2].re, w.w[2].im, w.w[3].re, w.w[3].im};
+  int off = 0;  // first of the K components this lane keeps
+  rs_split<MASK, 0, S, R>(v, lane, off);
+  rs_sum<MASK, S, NB, K, R>(v);
+  constexpr unsigned REST = drop_low_set_bits(MASK, S);
+  if ((lane & (int)REST) == 0 && act) {
+    constexpr int PER = (int)(16 / sizeof(R));  // components per 16-byte plane
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const int c = off + j;
+      R* d = reinterpret_cast<R*>(s.p + i + (c / PER) * N) + (c % PER);
+      if constexpr (ATOMIC) atomicAdd(d, v[j]);
+      else *d += v[j];
+    }
+  }
+}
+
 template <class R, int N>
 __device__ __forceinline__ void slot_add(const Slots<R, N>& s, int i, const W4<R>& w) {
   W4<R> o = s[i];

@@ -1427,13 +1427,12 @@ class SharedProgram:
 
         def add(target, slot, value, mask):
             # full: lanes = consecutive helicities of one event, all good: sum the
-            # lanes sharing the slot first, one add per slot and warp (a plain
-            # add when the warp holds every helicity of the event, else atomic)
+            # lanes sharing the slot first (reduce-scatter), each component added
+            # once per warp (a plain add when the warp holds every helicity of
+            # the event, else atomic)
             return ["          if (full) {",
-                    "            W4<R> s = %s;" % value,
-                    "            w4_warp_sum<%du>(s);" % mask,
-                    ("            if ((lane & %du) == 0 && act) slot_add(%s, %s, s);" % (mask, target, slot)) if one_warp
-                    else ("            if ((lane & %du) == 0) %s.atomic_add(%s, s);" % (mask, target, slot)),
+                    "            w4_warp_reduce_add<%du, %s>(%s, %s, %s, lane, act);"
+                    % (mask, "false" if one_warp else "true", value, target, slot),
                     "          } else {",
                     "            %s.atomic_add(%s, %s);" % (target, slot, value),
                     "          }"]
