@@ -901,6 +901,11 @@ VVVV_PAIRS = {0: (((0, 2), (1, 3)), ((0, 3), (1, 2))),
 
 class SharedProgram:
     SLOT_BUDGET = 768  # current + amputated-chunk variant slots per event (FP32: 8 events in 192 KB)
+    # amputated-chunk slots per event are rounded up to a multiple of this: a
+    # 256-thread CTA of 4 events x 64 helicities then builds a chunk in whole
+    # rounds of one item per thread (gg -> t t~ g g: 4 chunks of 192 slots,
+    # 12 rounds, instead of 176 x 4 + 64 in 13)
+    CHUNK_QUANTUM = 64
     CUR_CAP = 416      # current variant slots per event
 
     def __init__(self, proc: Process, emitter: "Emitter"):
@@ -1130,7 +1135,9 @@ class SharedProgram:
         total = sum(self.nvar(X) for X in xs)
         # two chunk buffers when it takes more than one chunk (the kernel builds
         # chunk c + 1 while it contracts chunk c)
-        self.xcap = total if total <= self.SLOT_BUDGET - self.nslots else (self.SLOT_BUDGET - self.nslots) // 2
+        cap = (self.SLOT_BUDGET - self.nslots) // 2
+        cap = -(-cap // self.CHUNK_QUANTUM) * self.CHUNK_QUANTUM
+        self.xcap = total if total <= self.SLOT_BUDGET - self.nslots else cap
         assert self.xcap >= max(self.nvar(X) for X in xs), "no room for an amputated current"
         self.xchunk, self.xoff, self.chunks = {}, {}, [[]]
         used = 0
