@@ -93,9 +93,9 @@ inline void item(const mg::HsItem& it, mg::W4<R>* cur, const R* K, const mg::cx<
     case 5: o = FFV1P0_3<R>(cur[it.in[0]], cur[it.in[1]], it.a ? cp.ee : cp.gs, pr[it.prop]); break;
     case 6: o = FFV2_4_3<R>(cur[it.in[0]], cur[it.in[1]], cp.gz, cp.gzl, cp.gzr, pr[it.prop]); break;
     case 7: o = VVV1P0_1<R>(cur[it.in[0]], cur[it.in[1]], K + 4 * it.k0, K + 4 * it.k1, cp.gs, pr[it.prop]); break;
-    default:
-      o = vvvv_comb(cur[it.in[0]], vdot(cur[it.in[1]], cur[it.in[2]]), cur[it.in[3]],
-                    vdot(cur[it.in[4]], cur[it.in[5]]), mul_mi(cp.gs2 * pr[it.prop]));
+    default:  // four-gluon term X_0 (X_1 . W) - X_1 (X_0 . W), in = {X_0, X_1, W}
+      o = vvvv_comb(cur[it.in[0]], vdot(cur[it.in[1]], cur[it.in[2]]), cur[it.in[1]],
+                    vdot(cur[it.in[0]], cur[it.in[2]]), mul_mi(cp.gs2 * pr[it.prop]));
   }
   cur[it.out] = o;
 }
@@ -111,9 +111,9 @@ inline void xitem(const mg::HsItem& it, const mg::W4<R>* cur, mg::W4<R>* xb, con
     case 11: o = FFV1P0_3A<R>(cur[it.in[0]], cur[it.in[1]], it.a ? cp.ee : cp.gs); break;
     case 12: o = FFV2_4_3A<R>(cur[it.in[0]], cur[it.in[1]], cp.gz, cp.gzl, cp.gzr); break;
     case 13: o = VVV1P0_1A<R>(cur[it.in[0]], cur[it.in[1]], K + 4 * it.k0, K + 4 * it.k1, cp.gs); break;
-    default:
-      o = vvvv_comb_a(cur[it.in[0]], vdot(cur[it.in[1]], cur[it.in[2]]), cur[it.in[3]],
-                      vdot(cur[it.in[4]], cur[it.in[5]]), cp.gs2);
+    default:  // four-gluon term, as in item
+      o = vvvv_comb_a(cur[it.in[0]], vdot(cur[it.in[1]], cur[it.in[2]]), cur[it.in[1]],
+                      vdot(cur[it.in[0]], cur[it.in[2]]), cp.gs2);
   }
   xb[it.out] = o;
 }

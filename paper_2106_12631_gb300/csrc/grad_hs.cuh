@@ -158,9 +158,9 @@ __device__ __forceinline__ void hs_item_adj(const HsItem& it, const Slots<R, P::
                                             const Slots<R, P::HS_NSLOT>& curb, const R* K, R* Kb, const cx<R>* pr,
                                             cx<R>* prb, const Couplings<R>& cp) {
   const W4<R> ob = curb[it.out];
-  W4<R> b[6];
+  W4<R> b[3];
 #pragma unroll
-  for (int k = 0; k < 6; ++k) b[k] = w4_zero<R>();
+  for (int k = 0; k < 3; ++k) b[k] = w4_zero<R>();
   R kb0[4] = {R(0), R(0), R(0), R(0)}, kb1[4] = {R(0), R(0), R(0), R(0)};
   cx<R> pb(R(0), R(0));
   int nin = 2, nk = 0;
@@ -181,13 +181,14 @@ __device__ __forceinline__ void hs_item_adj(const HsItem& it, const Slots<R, P::
                    kb0, kb1, pb);
       nk = 2;
       break;
-    default:  // four-gluon term
-      vvvv_adj(cur[it.in[0]], cur[it.in[1]], cur[it.in[2]], cur[it.in[3]], cur[it.in[4]], cur[it.in[5]], cp.gs2,
-               pr[it.prop], ob, b[0], b[1], b[2], b[3], b[4], b[5], pb);
-      nin = 6;
+    default: {  // four-gluon term X_0 (X_1 . W) - X_1 (X_0 . W), in = {X_0, X_1, W}
+      const W4<R> x0 = cur[it.in[0]], x1 = cur[it.in[1]], w = cur[it.in[2]];
+      vvvv_adj(x0, x1, w, x1, x0, w, cp.gs2, pr[it.prop], ob, b[0], b[1], b[2], b[1], b[0], b[2], pb);
+      nin = 3;
+    }
   }
 #pragma unroll
-  for (int k = 0; k < 6; ++k)
+  for (int k = 0; k < 3; ++k)
     if (k < nin) own_slot_add(curb, it.in[k], b[k]);
   if (nk >= 1) own_add4(Kb + 4 * it.k0, kb0);
   if (nk >= 2) own_add4(Kb + 4 * it.k1, kb1);
@@ -200,9 +201,9 @@ __device__ __forceinline__ void hs_xitem_adj(const HsItem& it, const Slots<R, P:
                                              const Slots<R, P::HS_NSLOT>& curb, const Slots<R, P::HS_XCAP>& xbb,
                                              const R* K, R* Kb, const Couplings<R>& cp) {
   const W4<R> ob = xbb[it.out];
-  W4<R> b[6];
+  W4<R> b[3];
 #pragma unroll
-  for (int k = 0; k < 6; ++k) b[k] = w4_zero<R>();
+  for (int k = 0; k < 3; ++k) b[k] = w4_zero<R>();
   R kb0[4] = {R(0), R(0), R(0), R(0)}, kb1[4] = {R(0), R(0), R(0), R(0)};
   int nin = 2;
   bool mom = false;
@@ -214,13 +215,14 @@ __device__ __forceinline__ void hs_xitem_adj(const HsItem& it, const Slots<R, P:
       VVV1P0_1A_adj(cur[it.in[0]], cur[it.in[1]], K + 4 * it.k0, K + 4 * it.k1, cp.gs, ob, b[0], b[1], kb0, kb1);
       mom = true;
       break;
-    default:  // four-gluon term
-      vvvv_comb_a_adj(cur[it.in[0]], cur[it.in[1]], cur[it.in[2]], cur[it.in[3]], cur[it.in[4]], cur[it.in[5]],
-                      cp.gs2, ob, b[0], b[1], b[2], b[3], b[4], b[5]);
-      nin = 6;
+    default: {  // four-gluon term, as in hs_item_adj
+      const W4<R> x0 = cur[it.in[0]], x1 = cur[it.in[1]], w = cur[it.in[2]];
+      vvvv_comb_a_adj(x0, x1, w, x1, x0, w, cp.gs2, ob, b[0], b[1], b[2], b[1], b[0], b[2]);
+      nin = 3;
+    }
   }
 #pragma unroll
-  for (int k = 0; k < 6; ++k)
+  for (int k = 0; k < 3; ++k)
     if (k < nin) own_slot_add(curb, it.in[k], b[k]);
   if (mom) {
     own_add4(Kb + 4 * it.k0, kb0);

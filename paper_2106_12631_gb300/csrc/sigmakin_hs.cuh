@@ -577,9 +577,10 @@ __device__ __forceinline__ void hs_item(const HsItem& it, const Slots<R, P::HS_N
     case 5: o = FFV1P0_3<R>(cur[it.in[0]], cur[it.in[1]], it.a ? cp.ee : cp.gs, pr[it.prop]); break;
     case 6: o = FFV2_4_3<R>(cur[it.in[0]], cur[it.in[1]], cp.gz, cp.gzl, cp.gzr, pr[it.prop]); break;
     case 7: o = VVV1P0_1<R>(cur[it.in[0]], cur[it.in[1]], K + 4 * it.k0, K + 4 * it.k1, cp.gs, pr[it.prop]); break;
-    default:
-      o = vvvv_comb(cur[it.in[0]], vdot(cur[it.in[1]], cur[it.in[2]]), cur[it.in[3]],
-                    vdot(cur[it.in[4]], cur[it.in[5]]), mul_mi(cp.gs2 * pr[it.prop]));
+    default: {  // four-gluon term X_0 (X_1 . W) - X_1 (X_0 . W), in = {X_0, X_1, W}
+      const W4<R> x0 = cur[it.in[0]], x1 = cur[it.in[1]], w = cur[it.in[2]];
+      o = vvvv_comb(x0, vdot(x1, w), x1, vdot(x0, w), mul_mi(cp.gs2 * pr[it.prop]));
+    }
   }
   cur.set(it.out, o);
 }
@@ -595,9 +596,10 @@ __device__ __forceinline__ void hs_xitem(const HsItem& it, const Slots<R, P::HS_
     case 11: o = FFV1P0_3A<R>(cur[it.in[0]], cur[it.in[1]], it.a ? cp.ee : cp.gs); break;
     case 12: o = FFV2_4_3A<R>(cur[it.in[0]], cur[it.in[1]], cp.gz, cp.gzl, cp.gzr); break;
     case 13: o = VVV1P0_1A<R>(cur[it.in[0]], cur[it.in[1]], K + 4 * it.k0, K + 4 * it.k1, cp.gs); break;
-    default:
-      o = vvvv_comb_a(cur[it.in[0]], vdot(cur[it.in[1]], cur[it.in[2]]), cur[it.in[3]],
-                      vdot(cur[it.in[4]], cur[it.in[5]]), cp.gs2);
+    default: {  // four-gluon term, as in hs_item
+      const W4<R> x0 = cur[it.in[0]], x1 = cur[it.in[1]], w = cur[it.in[2]];
+      o = vvvv_comb_a(x0, vdot(x1, w), x1, vdot(x0, w), cp.gs2);
+    }
   }
   xb.set(it.out, o);
 }

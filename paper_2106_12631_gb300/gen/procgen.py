@@ -1249,16 +1249,20 @@ class SharedProgram:
                 prop = em.prop(self._canon_prop_legs(legs), "g")
         elif kind in ("gggg", "agggg"):
             t = self.HS_TYPES[kind]
+            # each of the term's two products pairs the output position with an
+            # operand X_j and dots the other two: o = X_0 (X_1 . W) - X_1 (X_0 . W),
+            # W the third operand; in = {X_0, X_1, W}
             term, outpos, pos = self._gggg_positions(d)
-            for j, pair in enumerate(VVVV_PAIRS[term]):
+            xs_ = []
+            for pair in VVVV_PAIRS[term]:
                 (p0, p1), (p2, p3) = pair
                 if outpos in (p0, p1):
-                    X = p1 if outpos == p0 else p0
-                    Y, Z = p2, p3
+                    xs_.append(p1 if outpos == p0 else p0)
                 else:
-                    X = p3 if outpos == p2 else p2
-                    Y, Z = p0, p1
-                ins[3 * j + 0], ins[3 * j + 1], ins[3 * j + 2] = slot(pos[X]), slot(pos[Y]), slot(pos[Z])
+                    xs_.append(p3 if outpos == p2 else p2)
+            assert len(xs_) == 2 and xs_[0] != xs_[1]
+            (w_,) = [q for q in pos if q not in xs_]
+            ins[0], ins[1], ins[2] = slot(pos[xs_[0]]), slot(pos[xs_[1]]), slot(pos[w_])
             if kind == "gggg":
                 prop = em.prop(self._canon_prop_legs(legs), "g")
         else:
