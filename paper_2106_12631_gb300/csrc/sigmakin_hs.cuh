@@ -83,12 +83,19 @@ struct HsLayout {
   static constexpr size_t o_vt = align_up(o_m2 + 8 * NT, 16);
   static constexpr size_t o_B = align_up(o_vt + (size_t(1) << P::NPAR) * P::NHEL, 1024);
   static constexpr size_t o_U = align_up(o_B + (TC ? NP * KP * 2 : 0), 1024);
-  // union: current variants + amputated chunk (phases 2-3), then the tensor-core A tiles (phase 4)
+  // union: current variants + amputated chunk (phases 2-3), then the tensor-core A tiles (phase 4).
+  // Per-event strides in 16-byte words, padded so that one slot of the CTA's
+  // events falls in different bank groups: the lanes of a warp take an item
+  // for several events at once (the plane stride, a multiple of 8 words for
+  // the processes' slot counts, would otherwise map them to one group).
+  static constexpr int EVPAD = EVCAP >= 8 ? 1 : 8 / EVCAP;
+  static constexpr int CUR_EV = P::HS_NSLOT * Slots<R, 1>::NPL + EVPAD;
+  static constexpr int X_EV = P::HS_XCAP * Slots<R, 1>::NPL + EVPAD;
   static constexpr size_t o_cur = o_U;
-  static constexpr size_t o_x = o_U + sizeof(W4<R>) * EVCAP * P::HS_NSLOT;
+  static constexpr size_t o_x = o_U + 16 * size_t(EVCAP) * CUR_EV;
   static constexpr size_t o_A = o_U;
   static constexpr size_t tileA = 128 * KP * 2;
-  static constexpr size_t u_bytes = sizeof(W4<R>) * EVCAP * (P::HS_NSLOT + P::HS_XBUFS * P::HS_XCAP);
+  static constexpr size_t u_bytes = 16 * size_t(EVCAP) * (CUR_EV + P::HS_XBUFS * X_EV);
   static constexpr size_t a_bytes = TC ? 3 * MBLK * tileA : 0;  // one component's three splits
   static constexpr size_t bytes = o_U + (u_bytes > a_bytes ? u_bytes : a_bytes);
   static constexpr uint32_t TMEM_COLS = tc::tmem_cols(MBLK * 2 * NP);
@@ -480,12 +487,12 @@ __device__ __forceinline__ HsGroup hs_group(bool cta_only, int ng, int ev, int n
   return g;
 }
 
-template <class P, class R, class L>
+// CUR_EV: 16-byte words from one event's current variants to the next's
+template <class P, class R, class L, int CUR_EV = P::HS_NSLOT * Slots<R, 1>::NPL>
 __device__ __forceinline__ void hs_tables(unsigned char* smem, const PhysParams& pp, const HsGroup& grp, uint4* curs,
                                           const Couplings<R>& cp) {
   constexpr int NM = P::NMOM, NPAR = P::NPAR;
   constexpr int NEXT = P::hs_level(1);  // external variants
-  constexpr int CUR_EV = P::HS_NSLOT * Slots<R, 1>::NPL;
   constexpr bool DF = sizeof(R) == 4;
   const int4* md = reinterpret_cast<const int4*>(smem + L::o_md);
   const int2* prop_tab = reinterpret_cast<const int2*>(smem + L::o_proptab);
@@ -561,6 +568,16 @@ __device__ __forceinline__ void hs_tables(unsigned char* smem, const PhysParams&
     }
   }
   grp.sync();
+}
+
+// Item of work index t when the lanes take items item-major: consecutive
+// lanes take one item for each of the group's nev events, so that a warp holds
+// 32 / nev items (of one vertex type wherever the generator's per-event type
+// segments are multiples of that) and reads each descriptor once for all
+// its events.
+template <class L>
+__device__ __forceinline__ int hs_item_of(int t, int nev) {
+  return nev == L::EVCAP ? t / L::EVCAP : t / nev;
 }
 
 // one current variant
@@ -741,7 +758,7 @@ __device__ __forceinline__ void hs_sigmakin_body(const SigArgs& a, const Couplin
   // per event: HS_NSLOT current slots, HS_XCAP amputated slots (16-byte planes)
   uint4* curs = reinterpret_cast<uint4*>(smem + L::o_cur);
   uint4* xbufs = reinterpret_cast<uint4*>(smem + L::o_x);
-  constexpr int CUR_EV = P::HS_NSLOT * Slots<R, 1>::NPL, X_EV = P::HS_XCAP * Slots<R, 1>::NPL;
+  constexpr int CUR_EV = L::CUR_EV, X_EV = L::X_EV;
   const int tid = threadIdx.x, lane = tid & 31;
   hs_setup_words<P, R, L>(smem, a.pp);
   // vt[S][ihel]: variant index of leg set S for helicity ihel (generated table)
@@ -844,16 +861,16 @@ __device__ __forceinline__ void hs_sigmakin_body(const SigArgs& a, const Couplin
         if (nevn > 0) hs_prefetch_momenta<P, L>(smem, a.mom, a.nevt, e0n, nevn);
       }
       // 1. per-event tables (the momenta are in p)
-      hs_tables<P, R, L>(smem, a.pp, grp, curs, cp);
+      hs_tables<P, R, L, CUR_EV>(smem, a.pp, grp, curs, cp);
       const cx<R>* prall = reinterpret_cast<const cx<R>*>(smem + L::o_pr);
       // 2. current variants, level by level (level 0, the external wavefunctions,
-      //    came with phase 1); consecutive threads take consecutive items of one event
+      //    came with phase 1); consecutive threads take one item for each event (hs_item_of)
 #pragma unroll
       for (int l = 1; l < P::HS_NLEVEL; ++l) {
         const int i0 = P::hs_level(l), ni = P::hs_level(l + 1) - i0, n = ni * grp.nev;
         for (int t = grp.j; t < n; t += grp.tpg) {
-          const int el = t / ni, e = grp.ev0 + el;
-          const HsItem it = items[i0 + t - el * ni];
+          const int ii = hs_item_of<L>(t, grp.nev), e = grp.ev0 + t - ii * grp.nev;
+          const HsItem it = items[i0 + ii];
           hs_item<P, R>(it, Slots<R, P::HS_NSLOT>{curs + e * CUR_EV}, Kall + e * P::NMOM * 4, prall + e * P::NPROP,
                         cp);
         }
@@ -883,8 +900,8 @@ __device__ __forceinline__ void hs_sigmakin_body(const SigArgs& a, const Couplin
         uint4* xb = xbufs + (P::HS_XBUFS == 2 ? (c & 1) * XBUF : 0);
         const int i0 = P::hs_xitem(c), ni = P::hs_xitem(c + 1) - i0, n = ni * grp.nev;
         for (int t = grp.j; t < n; t += grp.tpg) {
-          const int exl = t / ni, ex = grp.ev0 + exl;
-          const HsItem it = items[i0 + t - exl * ni];
+          const int ii = hs_item_of<L>(t, grp.nev), ex = grp.ev0 + t - ii * grp.nev;
+          const HsItem it = items[i0 + ii];
           hs_xitem<P, R>(it, Slots<R, P::HS_NSLOT>{curs + ex * CUR_EV}, Slots<R, P::HS_XCAP>{xb + ex * X_EV},
                          Kall + ex * P::NMOM * 4, cp);
         }
