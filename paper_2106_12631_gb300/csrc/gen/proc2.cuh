@@ -5,7 +5,7 @@
 #pragma once
 namespace mg {
 // helicity-shared program: 7 currents in 2 levels (20 variant slots), 3 amputated currents in 1 chunk(s) of <= 12 slots, 3 amplitudes; 4612 flops per event (all helicities)
-static __device__ const HsItem kHsItems2[32] = {{2, 0, -1, 1, 0, 0, {0, 0, 0, 0, 0, 0}, 0, 0, 0}, {2, 0, 1, 1, 0, 1, {0, 0, 0, 0, 0, 0}, 0, 0, 0}, {2, 1, -1, 1, 0, 2, {0, 0, 0, 0, 0, 0}, 1, 0, 0}, {2, 1, 1, 1, 0, 3, {0, 0, 0, 0, 0, 0}, 1, 0, 0}, {1, 2, -1, 1, 1, 4, {0, 0, 0, 0, 0, 0}, 2, 0, 0}, {1, 2, 1, 1, 1, 5, {0, 0, 0, 0, 0, 0}, 2, 0, 0}, {0, 3, -1, -1, 1, 6, {0, 0, 0, 0, 0, 0}, 3, 0, 0}, {0, 3, 1, -1, 1, 7, {0, 0, 0, 0, 0, 0}, 3, 0, 0}, {7, 0, 0, 0, 0, 8, {0, 2, 0, 0, 0, 0}, 4, 5, 0}, {7, 0, 0, 0, 0, 9, {1, 2, 0, 0, 0, 0}, 4, 5, 0}, {7, 0, 0, 0, 0, 10, {0, 3, 0, 0, 0, 0}, 4, 5, 0}, {7, 0, 0, 0, 0, 11, {1, 3, 0, 0, 0, 0}, 4, 5, 0}, {3, 0, 0, 0, 0, 12, {4, 0, 0, 0, 0, 0}, 7, 0, 1}, {3, 0, 0, 0, 0, 13, {4, 1, 0, 0, 0, 0}, 7, 0, 1}, {3, 0, 0, 0, 0, 14, {5, 0, 0, 0, 0, 0}, 7, 0, 1}, {3, 0, 0, 0, 0, 15, {5, 1, 0, 0, 0, 0}, 7, 0, 1}, {3, 0, 0, 0, 0, 16, {4, 2, 0, 0, 0, 0}, 8, 0, 2}, {3, 0, 0, 0, 0, 17, {4, 3, 0, 0, 0, 0}, 8, 0, 2}, {3, 0, 0, 0, 0, 18, {5, 2, 0, 0, 0, 0}, 8, 0, 2}, {3, 0, 0, 0, 0, 19, {5, 3, 0, 0, 0, 0}, 8, 0, 2}, {10, 0, 0, 0, 0, 0, {6, 0, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 1, {6, 1, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 2, {7, 0, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 3, {7, 1, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 4, {6, 2, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 5, {6, 3, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 6, {7, 2, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 7, {7, 3, 0, 0, 0, 0}, 0, 0, 0}, {11, 0, 0, 0, 0, 8, {4, 6, 0, 0, 0, 0}, 0, 0, 0}, {11, 0, 0, 0, 0, 9, {5, 6, 0, 0, 0, 0}, 0, 0, 0}, {11, 0, 0, 0, 0, 10, {4, 7, 0, 0, 0, 0}, 0, 0, 0}, {11, 0, 0, 0, 0, 11, {5, 7, 0, 0, 0, 0}, 0, 0, 0}};
+static __device__ const HsItem kHsItems2[32] = {{0, {0, 0, 0}, 2, 0, -1, 1, 0, 0, 0, 0}, {1, {0, 0, 0}, 2, 0, 1, 1, 0, 0, 0, 0}, {2, {0, 0, 0}, 2, 1, -1, 1, 0, 1, 0, 0}, {3, {0, 0, 0}, 2, 1, 1, 1, 0, 1, 0, 0}, {4, {0, 0, 0}, 1, 2, -1, 1, 1, 2, 0, 0}, {5, {0, 0, 0}, 1, 2, 1, 1, 1, 2, 0, 0}, {6, {0, 0, 0}, 0, 3, -1, -1, 1, 3, 0, 0}, {7, {0, 0, 0}, 0, 3, 1, -1, 1, 3, 0, 0}, {8, {0, 2, 0}, 7, 0, 0, 0, 0, 4, 5, 0}, {9, {1, 2, 0}, 7, 0, 0, 0, 0, 4, 5, 0}, {10, {0, 3, 0}, 7, 0, 0, 0, 0, 4, 5, 0}, {11, {1, 3, 0}, 7, 0, 0, 0, 0, 4, 5, 0}, {12, {4, 0, 0}, 3, 0, 0, 0, 0, 7, 0, 1}, {13, {4, 1, 0}, 3, 0, 0, 0, 0, 7, 0, 1}, {14, {5, 0, 0}, 3, 0, 0, 0, 0, 7, 0, 1}, {15, {5, 1, 0}, 3, 0, 0, 0, 0, 7, 0, 1}, {16, {4, 2, 0}, 3, 0, 0, 0, 0, 8, 0, 2}, {17, {4, 3, 0}, 3, 0, 0, 0, 0, 8, 0, 2}, {18, {5, 2, 0}, 3, 0, 0, 0, 0, 8, 0, 2}, {19, {5, 3, 0}, 3, 0, 0, 0, 0, 8, 0, 2}, {0, {6, 0, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {1, {6, 1, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {2, {7, 0, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {3, {7, 1, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {4, {6, 2, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {5, {6, 3, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {6, {7, 2, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {7, {7, 3, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {8, {4, 6, 0}, 11, 0, 0, 0, 0, 0, 0, 0}, {9, {5, 6, 0}, 11, 0, 0, 0, 0, 0, 0, 0}, {10, {4, 7, 0}, 11, 0, 0, 0, 0, 0, 0, 0}, {11, {5, 7, 0}, 11, 0, 0, 0, 0, 0, 0, 0}};
 static __constant__ int kHsXItem2[2] = {20, 32};  // item ranges of the amputated chunks
 static __device__ __align__(16) const uint8_t kHsVar2[256] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 1, 1, 0, 0, 0, 0, 1, 1, 1, 1, 0, 0, 0, 0, 1, 1, 1, 1, 0, 0, 0, 0, 2, 2, 2, 2, 1, 1, 1, 1, 3, 3, 3, 3, 0, 0, 1, 1, 0, 0, 1, 1, 0, 0, 1, 1, 0, 0, 1, 1, 0, 0, 2, 2, 0, 0, 2, 2, 1, 1, 3, 3, 1, 1, 3, 3, 0, 0, 2, 2, 1, 1, 3, 3, 0, 0, 2, 2, 1, 1, 3, 3, 0, 0, 4, 4, 2, 2, 6, 6, 1, 1, 5, 5, 3, 3, 7, 7, 0, 1, 0, 1, 0, 1, 0, 1, 0, 1, 0, 1, 0, 1, 0, 1, 0, 2, 0, 2, 0, 2, 0, 2, 1, 3, 1, 3, 1, 3, 1, 3, 0, 2, 0, 2, 1, 3, 1, 3, 0, 2, 0, 2, 1, 3, 1, 3, 0, 4, 0, 4, 2, 6, 2, 6, 1, 5, 1, 5, 3, 7, 3, 7, 0, 2, 1, 3, 0, 2, 1, 3, 0, 2, 1, 3, 0, 2, 1, 3, 0, 4, 2, 6, 0, 4, 2, 6, 1, 5, 3, 7, 1, 5, 3, 7, 0, 4, 2, 6, 1, 5, 3, 7, 0, 4, 2, 6, 1, 5, 3, 7, 0, 8, 4, 12, 2, 10, 6, 14, 1, 9, 5, 13, 3, 11, 7, 15};  // [leg set][helicity]
 // colour-matrix numerators as the BF16 B operand of the tensor-core colour sum

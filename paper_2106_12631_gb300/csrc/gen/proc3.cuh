@@ -5,7 +5,7 @@
 #pragma once
 namespace mg {
 // helicity-shared program: 20 currents in 3 levels (94 variant slots), 13 amputated currents in 1 chunk(s) of <= 100 slots, 18 amplitudes; 37916 flops per event (all helicities)
-static __device__ const HsItem kHsItems3[194] = {{2, 0, -1, 1, 0, 0, {0, 0, 0, 0, 0, 0}, 0, 0, 0}, {2, 0, 1, 1, 0, 1, {0, 0, 0, 0, 0, 0}, 0, 0, 0}, {2, 1, -1, 1, 0, 2, {0, 0, 0, 0, 0, 0}, 1, 0, 0}, {2, 1, 1, 1, 0, 3, {0, 0, 0, 0, 0, 0}, 1, 0, 0}, {1, 2, -1, 1, 1, 4, {0, 0, 0, 0, 0, 0}, 2, 0, 0}, {1, 2, 1, 1, 1, 5, {0, 0, 0, 0, 0, 0}, 2, 0, 0}, {0, 3, -1, -1, 1, 6, {0, 0, 0, 0, 0, 0}, 3, 0, 0}, {0, 3, 1, -1, 1, 7, {0, 0, 0, 0, 0, 0}, 3, 0, 0}, {2, 4, -1, -1, 0, 8, {0, 0, 0, 0, 0, 0}, 4, 0, 0}, {2, 4, 1, -1, 0, 9, {0, 0, 0, 0, 0, 0}, 4, 0, 0}, {4, 0, 0, 0, 0, 10, {6, 0, 0, 0, 0, 0}, 18, 0, 3}, {4, 0, 0, 0, 0, 11, {6, 1, 0, 0, 0, 0}, 18, 0, 3}, {4, 0, 0, 0, 0, 12, {7, 0, 0, 0, 0, 0}, 18, 0, 3}, {4, 0, 0, 0, 0, 13, {7, 1, 0, 0, 0, 0}, 18, 0, 3}, {4, 0, 0, 0, 0, 14, {6, 2, 0, 0, 0, 0}, 19, 0, 5}, {4, 0, 0, 0, 0, 15, {6, 3, 0, 0, 0, 0}, 19, 0, 5}, {4, 0, 0, 0, 0, 16, {7, 2, 0, 0, 0, 0}, 19, 0, 5}, {4, 0, 0, 0, 0, 17, {7, 3, 0, 0, 0, 0}, 19, 0, 5}, {4, 0, 0, 0, 0, 18, {6, 8, 0, 0, 0, 0}, 20, 0, 4}, {4, 0, 0, 0, 0, 19, {7, 8, 0, 0, 0, 0}, 20, 0, 4}, {4, 0, 0, 0, 0, 20, {6, 9, 0, 0, 0, 0}, 20, 0, 4}, {4, 0, 0, 0, 0, 21, {7, 9, 0, 0, 0, 0}, 20, 0, 4}, {7, 0, 0, 0, 0, 22, {0, 2, 0, 0, 0, 0}, 9, 6, 6}, {7, 0, 0, 0, 0, 23, {1, 2, 0, 0, 0, 0}, 9, 6, 6}, {7, 0, 0, 0, 0, 24, {0, 3, 0, 0, 0, 0}, 9, 6, 6}, {7, 0, 0, 0, 0, 25, {1, 3, 0, 0, 0, 0}, 9, 6, 6}, {7, 0, 0, 0, 0, 26, {0, 8, 0, 0, 0, 0}, 9, 7, 8}, {7, 0, 0, 0, 0, 27, {1, 8, 0, 0, 0, 0}, 9, 7, 8}, {7, 0, 0, 0, 0, 28, {0, 9, 0, 0, 0, 0}, 9, 7, 8}, {7, 0, 0, 0, 0, 29, {1, 9, 0, 0, 0, 0}, 9, 7, 8}, {7, 0, 0, 0, 0, 30, {2, 8, 0, 0, 0, 0}, 6, 7, 1}, {7, 0, 0, 0, 0, 31, {3, 8, 0, 0, 0, 0}, 6, 7, 1}, {7, 0, 0, 0, 0, 32, {2, 9, 0, 0, 0, 0}, 6, 7, 1}, {7, 0, 0, 0, 0, 33, {3, 9, 0, 0, 0, 0}, 6, 7, 1}, {8, 0, 0, 0, 0, 34, {2, 0, 8, 0, 0, 0}, 0, 0, 0}, {8, 0, 0, 0, 0, 35, {2, 1, 8, 0, 0, 0}, 0, 0, 0}, {8, 0, 0, 0, 0, 36, {3, 0, 8, 0, 0, 0}, 0, 0, 0}, {8, 0, 0, 0, 0, 37, {3, 1, 8, 0, 0, 0}, 0, 0, 0}, {8, 0, 0, 0, 0, 38, {2, 0, 9, 0, 0, 0}, 0, 0, 0}, {8, 0, 0, 0, 0, 39, {2, 1, 9, 0, 0, 0}, 0, 0, 0}, {8, 0, 0, 0, 0, 40, {3, 0, 9, 0, 0, 0}, 0, 0, 0}, {8, 0, 0, 0, 0, 41, {3, 1, 9, 0, 0, 0}, 0, 0, 0}, {8, 0, 0, 0, 0, 42, {8, 0, 2, 0, 0, 0}, 0, 0, 0}, {8, 0, 0, 0, 0, 43, {8, 1, 2, 0, 0, 0}, 0, 0, 0}, {8, 0, 0, 0, 0, 44, {8, 0, 3, 0, 0, 0}, 0, 0, 0}, {8, 0, 0, 0, 0, 45, {8, 1, 3, 0, 0, 0}, 0, 0, 0}, {8, 0, 0, 0, 0, 46, {9, 0, 2, 0, 0, 0}, 0, 0, 0}, {8, 0, 0, 0, 0, 47, {9, 1, 2, 0, 0, 0}, 0, 0, 0}, {8, 0, 0, 0, 0, 48, {9, 0, 3, 0, 0, 0}, 0, 0, 0}, {8, 0, 0, 0, 0, 49, {9, 1, 3, 0, 0, 0}, 0, 0, 0}, {8, 0, 0, 0, 0, 50, {8, 2, 0, 0, 0, 0}, 0, 0, 0}, {8, 0, 0, 0, 0, 51, {8, 2, 1, 0, 0, 0}, 0, 0, 0}, {8, 0, 0, 0, 0, 52, {8, 3, 0, 0, 0, 0}, 0, 0, 0}, {8, 0, 0, 0, 0, 53, {8, 3, 1, 0, 0, 0}, 0, 0, 0}, {8, 0, 0, 0, 0, 54, {9, 2, 0, 0, 0, 0}, 0, 0, 0}, {8, 0, 0, 0, 0, 55, {9, 2, 1, 0, 0, 0}, 0, 0, 0}, {8, 0, 0, 0, 0, 56, {9, 3, 0, 0, 0, 0}, 0, 0, 0}, {8, 0, 0, 0, 0, 57, {9, 3, 1, 0, 0, 0}, 0, 0, 0}, {3, 0, 0, 0, 0, 58, {4, 0, 0, 0, 0, 0}, 10, 0, 2}, {3, 0, 0, 0, 0, 59, {4, 1, 0, 0, 0, 0}, 10, 0, 2}, {3, 0, 0, 0, 0, 60, {5, 0, 0, 0, 0, 0}, 10, 0, 2}, {3, 0, 0, 0, 0, 61, {5, 1, 0, 0, 0, 0}, 10, 0, 2}, {3, 0, 0, 0, 0, 62, {4, 2, 0, 0, 0, 0}, 17, 0, 9}, {3, 0, 0, 0, 0, 63, {4, 3, 0, 0, 0, 0}, 17, 0, 9}, {3, 0, 0, 0, 0, 64, {5, 2, 0, 0, 0, 0}, 17, 0, 9}, {3, 0, 0, 0, 0, 65, {5, 3, 0, 0, 0, 0}, 17, 0, 9}, {3, 0, 0, 0, 0, 66, {4, 8, 0, 0, 0, 0}, 15, 0, 7}, {3, 0, 0, 0, 0, 67, {5, 8, 0, 0, 0, 0}, 15, 0, 7}, {3, 0, 0, 0, 0, 68, {4, 9, 0, 0, 0, 0}, 15, 0, 7}, {3, 0, 0, 0, 0, 69, {5, 9, 0, 0, 0, 0}, 15, 0, 7}, {7, 0, 0, 0, 0, 70, {0, 30, 0, 0, 0, 0}, 9, 8, 0}, {7, 0, 0, 0, 0, 71, {1, 30, 0, 0, 0, 0}, 9, 8, 0}, {7, 0, 0, 0, 0, 72, {0, 31, 0, 0, 0, 0}, 9, 8, 0}, {7, 0, 0, 0, 0, 73, {1, 31, 0, 0, 0, 0}, 9, 8, 0}, {7, 0, 0, 0, 0, 74, {0, 32, 0, 0, 0, 0}, 9, 8, 0}, {7, 0, 0, 0, 0, 75, {1, 32, 0, 0, 0, 0}, 9, 8, 0}, {7, 0, 0, 0, 0, 76, {0, 33, 0, 0, 0, 0}, 9, 8, 0}, {7, 0, 0, 0, 0, 77, {1, 33, 0, 0, 0, 0}, 9, 8, 0}, {7, 0, 0, 0, 0, 78, {22, 8, 0, 0, 0, 0}, 14, 7, 0}, {7, 0, 0, 0, 0, 79, {23, 8, 0, 0, 0, 0}, 14, 7, 0}, {7, 0, 0, 0, 0, 80, {24, 8, 0, 0, 0, 0}, 14, 7, 0}, {7, 0, 0, 0, 0, 81, {25, 8, 0, 0, 0, 0}, 14, 7, 0}, {7, 0, 0, 0, 0, 82, {22, 9, 0, 0, 0, 0}, 14, 7, 0}, {7, 0, 0, 0, 0, 83, {23, 9, 0, 0, 0, 0}, 14, 7, 0}, {7, 0, 0, 0, 0, 84, {24, 9, 0, 0, 0, 0}, 14, 7, 0}, {7, 0, 0, 0, 0, 85, {25, 9, 0, 0, 0, 0}, 14, 7, 0}, {7, 0, 0, 0, 0, 86, {26, 2, 0, 0, 0, 0}, 16, 6, 0}, {7, 0, 0, 0, 0, 87, {27, 2, 0, 0, 0, 0}, 16, 6, 0}, {7, 0, 0, 0, 0, 88, {26, 3, 0, 0, 0, 0}, 16, 6, 0}, {7, 0, 0, 0, 0, 89, {27, 3, 0, 0, 0, 0}, 16, 6, 0}, {7, 0, 0, 0, 0, 90, {28, 2, 0, 0, 0, 0}, 16, 6, 0}, {7, 0, 0, 0, 0, 91, {29, 2, 0, 0, 0, 0}, 16, 6, 0}, {7, 0, 0, 0, 0, 92, {28, 3, 0, 0, 0, 0}, 16, 6, 0}, {7, 0, 0, 0, 0, 93, {29, 3, 0, 0, 0, 0}, 16, 6, 0}, {10, 0, 0, 0, 0, 0, {14, 0, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 1, {14, 1, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 2, {15, 0, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 3, {15, 1, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 4, {16, 0, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 5, {16, 1, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 6, {17, 0, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 7, {17, 1, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 8, {10, 2, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 9, {11, 2, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 10, {10, 3, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 11, {11, 3, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 12, {12, 2, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 13, {13, 2, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 14, {12, 3, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 15, {13, 3, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 16, {6, 22, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 17, {6, 23, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 18, {6, 24, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 19, {6, 25, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 20, {7, 22, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 21, {7, 23, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 22, {7, 24, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 23, {7, 25, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 24, {18, 0, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 25, {18, 1, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 26, {19, 0, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 27, {19, 1, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 28, {20, 0, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 29, {20, 1, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 30, {21, 0, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 31, {21, 1, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 32, {6, 26, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 33, {6, 27, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 34, {7, 26, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 35, {7, 27, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 36, {6, 28, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 37, {6, 29, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 38, {7, 28, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 39, {7, 29, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 40, {10, 8, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 41, {11, 8, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 42, {12, 8, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 43, {13, 8, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 44, {10, 9, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 45, {11, 9, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 46, {12, 9, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 47, {13, 9, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 48, {18, 2, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 49, {18, 3, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 50, {19, 2, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 51, {19, 3, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 52, {20, 2, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 53, {20, 3, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 54, {21, 2, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 55, {21, 3, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 56, {14, 8, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 57, {15, 8, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 58, {16, 8, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 59, {17, 8, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 60, {14, 9, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 61, {15, 9, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 62, {16, 9, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 63, {17, 9, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 64, {6, 30, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 65, {6, 31, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 66, {7, 30, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 67, {7, 31, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 68, {6, 32, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 69, {6, 33, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 70, {7, 32, 0, 0, 0, 0}, 0, 0, 0}, {10, 0, 0, 0, 0, 71, {7, 33, 0, 0, 0, 0}, 0, 0, 0}, {11, 0, 0, 0, 0, 72, {4, 6, 0, 0, 0, 0}, 0, 0, 0}, {11, 0, 0, 0, 0, 73, {5, 6, 0, 0, 0, 0}, 0, 0, 0}, {11, 0, 0, 0, 0, 74, {4, 7, 0, 0, 0, 0}, 0, 0, 0}, {11, 0, 0, 0, 0, 75, {5, 7, 0, 0, 0, 0}, 0, 0, 0}, {9, 0, 0, 0, 0, 76, {4, 22, 0, 0, 0, 0}, 0, 0, 0}, {9, 0, 0, 0, 0, 77, {4, 23, 0, 0, 0, 0}, 0, 0, 0}, {9, 0, 0, 0, 0, 78, {4, 24, 0, 0, 0, 0}, 0, 0, 0}, {9, 0, 0, 0, 0, 79, {4, 25, 0, 0, 0, 0}, 0, 0, 0}, {9, 0, 0, 0, 0, 80, {5, 22, 0, 0, 0, 0}, 0, 0, 0}, {9, 0, 0, 0, 0, 81, {5, 23, 0, 0, 0, 0}, 0, 0, 0}, {9, 0, 0, 0, 0, 82, {5, 24, 0, 0, 0, 0}, 0, 0, 0}, {9, 0, 0, 0, 0, 83, {5, 25, 0, 0, 0, 0}, 0, 0, 0}, {9, 0, 0, 0, 0, 84, {4, 26, 0, 0, 0, 0}, 0, 0, 0}, {9, 0, 0, 0, 0, 85, {4, 27, 0, 0, 0, 0}, 0, 0, 0}, {9, 0, 0, 0, 0, 86, {5, 26, 0, 0, 0, 0}, 0, 0, 0}, {9, 0, 0, 0, 0, 87, {5, 27, 0, 0, 0, 0}, 0, 0, 0}, {9, 0, 0, 0, 0, 88, {4, 28, 0, 0, 0, 0}, 0, 0, 0}, {9, 0, 0, 0, 0, 89, {4, 29, 0, 0, 0, 0}, 0, 0, 0}, {9, 0, 0, 0, 0, 90, {5, 28, 0, 0, 0, 0}, 0, 0, 0}, {9, 0, 0, 0, 0, 91, {5, 29, 0, 0, 0, 0}, 0, 0, 0}, {9, 0, 0, 0, 0, 92, {4, 30, 0, 0, 0, 0}, 0, 0, 0}, {9, 0, 0, 0, 0, 93, {4, 31, 0, 0, 0, 0}, 0, 0, 0}, {9, 0, 0, 0, 0, 94, {5, 30, 0, 0, 0, 0}, 0, 0, 0}, {9, 0, 0, 0, 0, 95, {5, 31, 0, 0, 0, 0}, 0, 0, 0}, {9, 0, 0, 0, 0, 96, {4, 32, 0, 0, 0, 0}, 0, 0, 0}, {9, 0, 0, 0, 0, 97, {4, 33, 0, 0, 0, 0}, 0, 0, 0}, {9, 0, 0, 0, 0, 98, {5, 32, 0, 0, 0, 0}, 0, 0, 0}, {9, 0, 0, 0, 0, 99, {5, 33, 0, 0, 0, 0}, 0, 0, 0}};
+static __device__ const HsItem kHsItems3[194] = {{0, {0, 0, 0}, 2, 0, -1, 1, 0, 0, 0, 0}, {1, {0, 0, 0}, 2, 0, 1, 1, 0, 0, 0, 0}, {2, {0, 0, 0}, 2, 1, -1, 1, 0, 1, 0, 0}, {3, {0, 0, 0}, 2, 1, 1, 1, 0, 1, 0, 0}, {4, {0, 0, 0}, 1, 2, -1, 1, 1, 2, 0, 0}, {5, {0, 0, 0}, 1, 2, 1, 1, 1, 2, 0, 0}, {6, {0, 0, 0}, 0, 3, -1, -1, 1, 3, 0, 0}, {7, {0, 0, 0}, 0, 3, 1, -1, 1, 3, 0, 0}, {8, {0, 0, 0}, 2, 4, -1, -1, 0, 4, 0, 0}, {9, {0, 0, 0}, 2, 4, 1, -1, 0, 4, 0, 0}, {10, {6, 0, 0}, 4, 0, 0, 0, 0, 18, 0, 3}, {11, {6, 1, 0}, 4, 0, 0, 0, 0, 18, 0, 3}, {12, {7, 0, 0}, 4, 0, 0, 0, 0, 18, 0, 3}, {13, {7, 1, 0}, 4, 0, 0, 0, 0, 18, 0, 3}, {14, {6, 2, 0}, 4, 0, 0, 0, 0, 19, 0, 5}, {15, {6, 3, 0}, 4, 0, 0, 0, 0, 19, 0, 5}, {16, {7, 2, 0}, 4, 0, 0, 0, 0, 19, 0, 5}, {17, {7, 3, 0}, 4, 0, 0, 0, 0, 19, 0, 5}, {18, {6, 8, 0}, 4, 0, 0, 0, 0, 20, 0, 4}, {19, {7, 8, 0}, 4, 0, 0, 0, 0, 20, 0, 4}, {20, {6, 9, 0}, 4, 0, 0, 0, 0, 20, 0, 4}, {21, {7, 9, 0}, 4, 0, 0, 0, 0, 20, 0, 4}, {22, {0, 2, 0}, 7, 0, 0, 0, 0, 9, 6, 6}, {23, {1, 2, 0}, 7, 0, 0, 0, 0, 9, 6, 6}, {24, {0, 3, 0}, 7, 0, 0, 0, 0, 9, 6, 6}, {25, {1, 3, 0}, 7, 0, 0, 0, 0, 9, 6, 6}, {26, {0, 8, 0}, 7, 0, 0, 0, 0, 9, 7, 8}, {27, {1, 8, 0}, 7, 0, 0, 0, 0, 9, 7, 8}, {28, {0, 9, 0}, 7, 0, 0, 0, 0, 9, 7, 8}, {29, {1, 9, 0}, 7, 0, 0, 0, 0, 9, 7, 8}, {30, {2, 8, 0}, 7, 0, 0, 0, 0, 6, 7, 1}, {31, {3, 8, 0}, 7, 0, 0, 0, 0, 6, 7, 1}, {32, {2, 9, 0}, 7, 0, 0, 0, 0, 6, 7, 1}, {33, {3, 9, 0}, 7, 0, 0, 0, 0, 6, 7, 1}, {34, {2, 0, 8}, 8, 0, 0, 0, 0, 0, 0, 0}, {35, {2, 1, 8}, 8, 0, 0, 0, 0, 0, 0, 0}, {36, {3, 0, 8}, 8, 0, 0, 0, 0, 0, 0, 0}, {37, {3, 1, 8}, 8, 0, 0, 0, 0, 0, 0, 0}, {38, {2, 0, 9}, 8, 0, 0, 0, 0, 0, 0, 0}, {39, {2, 1, 9}, 8, 0, 0, 0, 0, 0, 0, 0}, {40, {3, 0, 9}, 8, 0, 0, 0, 0, 0, 0, 0}, {41, {3, 1, 9}, 8, 0, 0, 0, 0, 0, 0, 0}, {42, {8, 0, 2}, 8, 0, 0, 0, 0, 0, 0, 0}, {43, {8, 1, 2}, 8, 0, 0, 0, 0, 0, 0, 0}, {44, {8, 0, 3}, 8, 0, 0, 0, 0, 0, 0, 0}, {45, {8, 1, 3}, 8, 0, 0, 0, 0, 0, 0, 0}, {46, {9, 0, 2}, 8, 0, 0, 0, 0, 0, 0, 0}, {47, {9, 1, 2}, 8, 0, 0, 0, 0, 0, 0, 0}, {48, {9, 0, 3}, 8, 0, 0, 0, 0, 0, 0, 0}, {49, {9, 1, 3}, 8, 0, 0, 0, 0, 0, 0, 0}, {50, {8, 2, 0}, 8, 0, 0, 0, 0, 0, 0, 0}, {51, {8, 2, 1}, 8, 0, 0, 0, 0, 0, 0, 0}, {52, {8, 3, 0}, 8, 0, 0, 0, 0, 0, 0, 0}, {53, {8, 3, 1}, 8, 0, 0, 0, 0, 0, 0, 0}, {54, {9, 2, 0}, 8, 0, 0, 0, 0, 0, 0, 0}, {55, {9, 2, 1}, 8, 0, 0, 0, 0, 0, 0, 0}, {56, {9, 3, 0}, 8, 0, 0, 0, 0, 0, 0, 0}, {57, {9, 3, 1}, 8, 0, 0, 0, 0, 0, 0, 0}, {58, {4, 0, 0}, 3, 0, 0, 0, 0, 10, 0, 2}, {59, {4, 1, 0}, 3, 0, 0, 0, 0, 10, 0, 2}, {60, {5, 0, 0}, 3, 0, 0, 0, 0, 10, 0, 2}, {61, {5, 1, 0}, 3, 0, 0, 0, 0, 10, 0, 2}, {62, {4, 2, 0}, 3, 0, 0, 0, 0, 17, 0, 9}, {63, {4, 3, 0}, 3, 0, 0, 0, 0, 17, 0, 9}, {64, {5, 2, 0}, 3, 0, 0, 0, 0, 17, 0, 9}, {65, {5, 3, 0}, 3, 0, 0, 0, 0, 17, 0, 9}, {66, {4, 8, 0}, 3, 0, 0, 0, 0, 15, 0, 7}, {67, {5, 8, 0}, 3, 0, 0, 0, 0, 15, 0, 7}, {68, {4, 9, 0}, 3, 0, 0, 0, 0, 15, 0, 7}, {69, {5, 9, 0}, 3, 0, 0, 0, 0, 15, 0, 7}, {70, {0, 30, 0}, 7, 0, 0, 0, 0, 9, 8, 0}, {71, {1, 30, 0}, 7, 0, 0, 0, 0, 9, 8, 0}, {72, {0, 31, 0}, 7, 0, 0, 0, 0, 9, 8, 0}, {73, {1, 31, 0}, 7, 0, 0, 0, 0, 9, 8, 0}, {74, {0, 32, 0}, 7, 0, 0, 0, 0, 9, 8, 0}, {75, {1, 32, 0}, 7, 0, 0, 0, 0, 9, 8, 0}, {76, {0, 33, 0}, 7, 0, 0, 0, 0, 9, 8, 0}, {77, {1, 33, 0}, 7, 0, 0, 0, 0, 9, 8, 0}, {78, {22, 8, 0}, 7, 0, 0, 0, 0, 14, 7, 0}, {79, {23, 8, 0}, 7, 0, 0, 0, 0, 14, 7, 0}, {80, {24, 8, 0}, 7, 0, 0, 0, 0, 14, 7, 0}, {81, {25, 8, 0}, 7, 0, 0, 0, 0, 14, 7, 0}, {82, {22, 9, 0}, 7, 0, 0, 0, 0, 14, 7, 0}, {83, {23, 9, 0}, 7, 0, 0, 0, 0, 14, 7, 0}, {84, {24, 9, 0}, 7, 0, 0, 0, 0, 14, 7, 0}, {85, {25, 9, 0}, 7, 0, 0, 0, 0, 14, 7, 0}, {86, {26, 2, 0}, 7, 0, 0, 0, 0, 16, 6, 0}, {87, {27, 2, 0}, 7, 0, 0, 0, 0, 16, 6, 0}, {88, {26, 3, 0}, 7, 0, 0, 0, 0, 16, 6, 0}, {89, {27, 3, 0}, 7, 0, 0, 0, 0, 16, 6, 0}, {90, {28, 2, 0}, 7, 0, 0, 0, 0, 16, 6, 0}, {91, {29, 2, 0}, 7, 0, 0, 0, 0, 16, 6, 0}, {92, {28, 3, 0}, 7, 0, 0, 0, 0, 16, 6, 0}, {93, {29, 3, 0}, 7, 0, 0, 0, 0, 16, 6, 0}, {0, {14, 0, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {1, {14, 1, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {2, {15, 0, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {3, {15, 1, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {4, {16, 0, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {5, {16, 1, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {6, {17, 0, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {7, {17, 1, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {8, {10, 2, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {9, {11, 2, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {10, {10, 3, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {11, {11, 3, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {12, {12, 2, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {13, {13, 2, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {14, {12, 3, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {15, {13, 3, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {16, {6, 22, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {17, {6, 23, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {18, {6, 24, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {19, {6, 25, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {20, {7, 22, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {21, {7, 23, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {22, {7, 24, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {23, {7, 25, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {24, {18, 0, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {25, {18, 1, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {26, {19, 0, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {27, {19, 1, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {28, {20, 0, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {29, {20, 1, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {30, {21, 0, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {31, {21, 1, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {32, {6, 26, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {33, {6, 27, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {34, {7, 26, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {35, {7, 27, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {36, {6, 28, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {37, {6, 29, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {38, {7, 28, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {39, {7, 29, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {40, {10, 8, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {41, {11, 8, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {42, {12, 8, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {43, {13, 8, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {44, {10, 9, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {45, {11, 9, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {46, {12, 9, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {47, {13, 9, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {48, {18, 2, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {49, {18, 3, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {50, {19, 2, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {51, {19, 3, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {52, {20, 2, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {53, {20, 3, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {54, {21, 2, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {55, {21, 3, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {56, {14, 8, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {57, {15, 8, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {58, {16, 8, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {59, {17, 8, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {60, {14, 9, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {61, {15, 9, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {62, {16, 9, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {63, {17, 9, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {64, {6, 30, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {65, {6, 31, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {66, {7, 30, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {67, {7, 31, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {68, {6, 32, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {69, {6, 33, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {70, {7, 32, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {71, {7, 33, 0}, 10, 0, 0, 0, 0, 0, 0, 0}, {72, {4, 6, 0}, 11, 0, 0, 0, 0, 0, 0, 0}, {73, {5, 6, 0}, 11, 0, 0, 0, 0, 0, 0, 0}, {74, {4, 7, 0}, 11, 0, 0, 0, 0, 0, 0, 0}, {75, {5, 7, 0}, 11, 0, 0, 0, 0, 0, 0, 0}, {76, {4, 22, 0}, 9, 0, 0, 0, 0, 0, 0, 0}, {77, {4, 23, 0}, 9, 0, 0, 0, 0, 0, 0, 0}, {78, {4, 24, 0}, 9, 0, 0, 0, 0, 0, 0, 0}, {79, {4, 25, 0}, 9, 0, 0, 0, 0, 0, 0, 0}, {80, {5, 22, 0}, 9, 0, 0, 0, 0, 0, 0, 0}, {81, {5, 23, 0}, 9, 0, 0, 0, 0, 0, 0, 0}, {82, {5, 24, 0}, 9, 0, 0, 0, 0, 0, 0, 0}, {83, {5, 25, 0}, 9, 0, 0, 0, 0, 0, 0, 0}, {84, {4, 26, 0}, 9, 0, 0, 0, 0, 0, 0, 0}, {85, {4, 27, 0}, 9, 0, 0, 0, 0, 0, 0, 0}, {86, {5, 26, 0}, 9, 0, 0, 0, 0, 0, 0, 0}, {87, {5, 27, 0}, 9, 0, 0, 0, 0, 0, 0, 0}, {88, {4, 28, 0}, 9, 0, 0, 0, 0, 0, 0, 0}, {89, {4, 29, 0}, 9, 0, 0, 0, 0, 0, 0, 0}, {90, {5, 28, 0}, 9, 0, 0, 0, 0, 0, 0, 0}, {91, {5, 29, 0}, 9, 0, 0, 0, 0, 0, 0, 0}, {92, {4, 30, 0}, 9, 0, 0, 0, 0, 0, 0, 0}, {93, {4, 31, 0}, 9, 0, 0, 0, 0, 0, 0, 0}, {94, {5, 30, 0}, 9, 0, 0, 0, 0, 0, 0, 0}, {95, {5, 31, 0}, 9, 0, 0, 0, 0, 0, 0, 0}, {96, {4, 32, 0}, 9, 0, 0, 0, 0, 0, 0, 0}, {97, {4, 33, 0}, 9, 0, 0, 0, 0, 0, 0, 0}, {98, {5, 32, 0}, 9, 0, 0, 0, 0, 0, 0, 0}, {99, {5, 33, 0}, 9, 0, 0, 0, 0, 0, 0, 0}};
 static __constant__ int kHsXItem3[2] = {94, 194};  // item ranges of the amputated chunks
 static __device__ __align__(16) const uint8_t kHsVar3[1024] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 1, 1, 0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 1, 1, 0, 0, 0, 0, 0, 0, 0, 0, 2, 2, 2, 2, 2, 2, 2, 2, 1, 1, 1, 1, 1, 1, 1, 1, 3, 3, 3, 3, 3, 3, 3, 3, 0, 0, 0, 0, 1, 1, 1, 1, 0, 0, 0, 0, 1, 1, 1, 1, 0, 0, 0, 0, 1, 1, 1, 1, 0, 0, 0, 0, 1, 1, 1, 1, 0, 0, 0, 0, 2, 2, 2, 2, 0, 0, 0, 0, 2, 2, 2, 2, 1, 1, 1, 1, 3, 3, 3, 3, 1, 1, 1, 1, 3, 3, 3, 3, 0, 0, 0, 0, 2, 2, 2, 2, 1, 1, 1, 1, 3, 3, 3, 3, 0, 0, 0, 0, 2, 2, 2, 2, 1, 1, 1, 1, 3, 3, 3, 3, 0, 0, 0, 0, 4, 4, 4, 4, 2, 2, 2, 2, 6, 6, 6, 6, 1, 1, 1, 1, 5, 5, 5, 5, 3, 3, 3, 3, 7, 7, 7, 7, 0, 0, 1, 1, 0, 0, 1, 1, 0, 0, 1, 1, 0, 0, 1, 1, 0, 0, 1, 1, 0, 0, 1, 1, 0, 0, 1, 1, 0, 0, 1, 1, 0, 0, 2, 2, 0, 0, 2, 2, 0, 0, 2, 2, 0, 0, 2, 2, 1, 1, 3, 3, 1, 1, 3, 3, 1, 1, 3, 3, 1, 1, 3, 3, 0, 0, 2, 2, 0, 0, 2, 2, 1, 1, 3, 3, 1, 1, 3, 3, 0, 0, 2, 2, 0, 0, 2, 2, 1, 1, 3, 3, 1, 1, 3, 3, 0, 0, 4, 4, 0, 0, 4, 4, 2, 2, 6, 6, 2, 2, 6, 6, 1, 1, 5, 5, 1, 1, 5, 5, 3, 3, 7, 7, 3, 3, 7, 7, 0, 0, 2, 2, 1, 1, 3, 3, 0, 0, 2, 2, 1, 1, 3, 3, 0, 0, 2, 2, 1, 1, 3, 3, 0, 0, 2, 2, 1, 1, 3, 3, 0, 0, 4, 4, 2, 2, 6, 6, 0, 0, 4, 4, 2, 2, 6, 6, 1, 1, 5, 5, 3, 3, 7, 7, 1, 1, 5, 5, 3, 3, 7, 7, 0, 0, 4, 4, 2, 2, 6, 6, 1, 1, 5, 5, 3, 3, 7, 7, 0, 0, 4, 4, 2, 2, 6, 6, 1, 1, 5, 5, 3, 3, 7, 7, 0, 0, 8, 8, 4, 4, 12, 12, 2, 2, 10, 10, 6, 6, 14, 14, 1, 1, 9, 9, 5, 5, 13, 13, 3, 3, 11, 11, 7, 7, 15, 15, 0, 1, 0, 1, 0, 1, 0, 1, 0, 1, 0, 1, 0, 1, 0, 1, 0, 1, 0, 1, 0, 1, 0, 1, 0, 1, 0, 1, 0, 1, 0, 1, 0, 2, 0, 2, 0, 2, 0, 2, 0, 2, 0, 2, 0, 2, 0, 2, 1, 3, 1, 3, 1, 3, 1, 3, 1, 3, 1, 3, 1, 3, 1, 3, 0, 2, 0, 2, 0, 2, 0, 2, 1, 3, 1, 3, 1, 3, 1, 3, 0, 2, 0, 2, 0, 2, 0, 2, 1, 3, 1, 3, 1, 3, 1, 3, 0, 4, 0, 4, 0, 4, 0, 4, 2, 6, 2, 6, 2, 6, 2, 6, 1, 5, 1, 5, 1, 5, 1, 5, 3, 7, 3, 7, 3, 7, 3, 7, 0, 2, 0, 2, 1, 3, 1, 3, 0, 2, 0, 2, 1, 3, 1, 3, 0, 2, 0, 2, 1, 3, 1, 3, 0, 2, 0, 2, 1, 3, 1, 3, 0, 4, 0, 4, 2, 6, 2, 6, 0, 4, 0, 4, 2, 6, 2, 6, 1, 5, 1, 5, 3, 7, 3, 7, 1, 5, 1, 5, 3, 7, 3, 7, 0, 4, 0, 4, 2, 6, 2, 6, 1, 5, 1, 5, 3, 7, 3, 7, 0, 4, 0, 4, 2, 6, 2, 6, 1, 5, 1, 5, 3, 7, 3, 7, 0, 8, 0, 8, 4, 12, 4, 12, 2, 10, 2, 10, 6, 14, 6, 14, 1, 9, 1, 9, 5, 13, 5, 13, 3, 11, 3, 11, 7, 15, 7, 15, 0, 2, 1, 3, 0, 2, 1, 3, 0, 2, 1, 3, 0, 2, 1, 3, 0, 2, 1, 3, 0, 2, 1, 3, 0, 2, 1, 3, 0, 2, 1, 3, 0, 4, 2, 6, 0, 4, 2, 6, 0, 4, 2, 6, 0, 4, 2, 6, 1, 5, 3, 7, 1, 5, 3, 7, 1, 5, 3, 7, 1, 5, 3, 7, 0, 4, 2, 6, 0, 4, 2, 6, 1, 5, 3, 7, 1, 5, 3, 7, 0, 4, 2, 6, 0, 4, 2, 6, 1, 5, 3, 7, 1, 5, 3, 7, 0, 8, 4, 12, 0, 8, 4, 12, 2, 10, 6, 14, 2, 10, 6, 14, 1, 9, 5, 13, 1, 9, 5, 13, 3, 11, 7, 15, 3, 11, 7, 15, 0, 4, 2, 6, 1, 5, 3, 7, 0, 4, 2, 6, 1, 5, 3, 7, 0, 4, 2, 6, 1, 5, 3, 7, 0, 4, 2, 6, 1, 5, 3, 7, 0, 8, 4, 12, 2, 10, 6, 14, 0, 8, 4, 12, 2, 10, 6, 14, 1, 9, 5, 13, 3, 11, 7, 15, 1, 9, 5, 13, 3, 11, 7, 15, 0, 8, 4, 12, 2, 10, 6, 14, 1, 9, 5, 13, 3, 11, 7, 15, 0, 8, 4, 12, 2, 10, 6, 14, 1, 9, 5, 13, 3, 11, 7, 15, 0, 16, 8, 24, 4, 20, 12, 28, 2, 18, 10, 26, 6, 22, 14, 30, 1, 17, 9, 25, 5, 21, 13, 29, 3, 19, 11, 27, 7, 23, 15, 31};  // [leg set][helicity]
 // colour-matrix numerators as the BF16 B operand of the tensor-core colour sum

@@ -103,16 +103,17 @@ struct Couplings {
 // 8 four-gluon term; amputated: 9 row, 10 column, 11 fermion pair, 12 lepton
 // pair to Z, 13 three-gluon, 14 four-gluon term); a/b/c: type parameters
 // (external: leg, helicity, flow sign; pair: coupling 0 g_s / 1 e); flag:
-// external top mass; out/in: variant slots; k0/k1: momentum-table entries;
-// prop: propagator entry.
-struct HsItem {
+// external top mass; out/in: variant slots (a four-gluon term's three
+// operands X_0, X_1, W); k0/k1: momentum-table entries; prop: propagator
+// entry.  One aligned 16-byte word, read by one load.
+struct alignas(16) HsItem {
+  uint16_t out;
+  uint16_t in[3];
   uint8_t type;
   int8_t a, b, c;
-  uint8_t flag;
-  uint16_t out;
-  uint16_t in[6];
-  uint8_t k0, k1, prop;
+  uint8_t flag, k0, k1, prop;
 };
+static_assert(sizeof(HsItem) == 16, "item descriptor: one 16-byte word");
 // Physics parameters in FP64 (propagator denominators are formed in FP64 in
 // both precision modes).
 struct PhysParams {

@@ -1190,10 +1190,10 @@ class SharedProgram:
 
     def _item(self, d, v):
         """One variant of a current or amputated current:
-        (type, a, b, c, flag, out, in[6], k0, k1, prop)."""
+        (type, a, b, c, flag, out, in[3], k0, k1, prop)."""
         em, spec = self.em, self.p.spec
         out = (self.xoff[d] if d[0] == "X" else self.offset[d]) + v
-        ins = [0] * 6
+        ins = [0] * 3
         a = b = c = flag = 0
         k0 = k1 = prop = 0
         kind = self.kind(d)
@@ -1321,8 +1321,8 @@ class SharedProgram:
                    % (len(self.order), len(level_start) - 1, self.nslots, len(self.xoff), len(self.chunks),
                       self.xcap, len(amps), self.flops_items + nh * self.flops_amps_hel))
         out.append("static __device__ const HsItem kHsItems%d[%d] = {%s};" % (
-            pid, len(items), ", ".join("{%d, %d, %d, %d, %d, %d, {%s}, %d, %d, %d}" % (
-                t, a, b, c, flag, o, ", ".join(map(str, ins)), k0, k1, pr)
+            pid, len(items), ", ".join("{%d, {%s}, %d, %d, %d, %d, %d, %d, %d, %d}" % (
+                o, ", ".join(map(str, ins)), t, a, b, c, flag, k0, k1, pr)
                 for (t, a, b, c, flag, o, ins, k0, k1, pr) in items)))
         out.append("static __constant__ int kHsXItem%d[%d] = {%s};  // item ranges of the amputated chunks"
                    % (pid, len(xitem_start), ", ".join(map(str, xitem_start))))
