@@ -77,7 +77,12 @@ struct HsLayout {
   // the next group's momenta (FP64), copied asynchronously while this group runs
   static constexpr size_t o_ps = align_up(o_p + 8 * EVCAP * P::NPAR * 4, 16);
   static constexpr size_t o_K = align_up(o_ps + 8 * EVCAP * P::NPAR * 4, 16);
-  static constexpr size_t o_pr = align_up(o_K + sizeof(R) * EVCAP * P::NMOM * 4, 16);
+  // momentum-table entries (R) from one event to the next: an odd number of
+  // 16-byte words, so that one entry of the CTA's events falls in different
+  // bank groups (the lanes of a warp read it for several events at once)
+  static constexpr int KEV =
+      4 * P::NMOM + ((4 * P::NMOM * (int)sizeof(R) / 16) % 2 == 0 ? 16 / (int)sizeof(R) : 0);
+  static constexpr size_t o_pr = align_up(o_K + sizeof(R) * EVCAP * KEV, 16);
   static constexpr size_t o_m2 = align_up(o_pr + 2 * sizeof(R) * EVCAP * P::NPROP, 16);
   // variant of a leg set for a helicity: vt[S * NHEL + ihel]
   static constexpr size_t o_vt = align_up(o_m2 + 8 * NT, 16);
@@ -487,8 +492,9 @@ __device__ __forceinline__ HsGroup hs_group(bool cta_only, int ng, int ev, int n
   return g;
 }
 
-// CUR_EV: 16-byte words from one event's current variants to the next's
-template <class P, class R, class L, int CUR_EV = P::HS_NSLOT * Slots<R, 1>::NPL>
+// CUR_EV: 16-byte words from one event's current variants to the next's;
+// KEV: momentum-table entries (R) from one event's table to the next's
+template <class P, class R, class L, int CUR_EV = P::HS_NSLOT * Slots<R, 1>::NPL, int KEV = 4 * P::NMOM>
 __device__ __forceinline__ void hs_tables(unsigned char* smem, const PhysParams& pp, const HsGroup& grp, uint4* curs,
                                           const Couplings<R>& cp) {
   constexpr int NM = P::NMOM, NPAR = P::NPAR;
@@ -520,7 +526,7 @@ __device__ __forceinline__ void hs_tables(unsigned char* smem, const PhysParams&
           kf[mu] = make_float2(k.s, k.err);
           kv[mu] = k.value();
         }
-        reinterpret_cast<float4*>(K)[e * NM + j] = make_float4(kv[0], kv[1], kv[2], kv[3]);
+        *reinterpret_cast<float4*>(K + e * KEV + 4 * j) = make_float4(kv[0], kv[1], kv[2], kv[3]);
         const float4* mc = reinterpret_cast<const float4*>(smem + L::o_mconst);
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
@@ -542,7 +548,7 @@ __device__ __forceinline__ void hs_tables(unsigned char* smem, const PhysParams&
             s += c * q[l * 4 + mu];
           }
           k[mu] = s;
-          K[(e * NM + j) * 4 + mu] = R(s);
+          K[e * KEV + j * 4 + mu] = R(s);
         }
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
@@ -841,7 +847,7 @@ __device__ __forceinline__ void hs_sigmakin_body(const SigArgs& a, const Couplin
         const int e = t / RC::WORDS, w = t - e * RC::WORDS;
         const uint4 v = __ldcs(in + t);  // read once: streaming
         if (w < RC::CUR) curs[e * CUR_EV + w] = v;
-        else ks[e * RC::KW + (w - RC::CUR)] = v;
+        else ks[e * (L::KEV * (int)sizeof(R) / 16) + (w - RC::CUR)] = v;
       }
       __syncthreads();
     } else {
@@ -861,7 +867,7 @@ __device__ __forceinline__ void hs_sigmakin_body(const SigArgs& a, const Couplin
         if (nevn > 0) hs_prefetch_momenta<P, L>(smem, a.mom, a.nevt, e0n, nevn);
       }
       // 1. per-event tables (the momenta are in p)
-      hs_tables<P, R, L, CUR_EV>(smem, a.pp, grp, curs, cp);
+      hs_tables<P, R, L, CUR_EV, L::KEV>(smem, a.pp, grp, curs, cp);
       const cx<R>* prall = reinterpret_cast<const cx<R>*>(smem + L::o_pr);
       // 2. current variants, level by level (level 0, the external wavefunctions,
       //    came with phase 1); consecutive threads take one item for each event (hs_item_of)
@@ -871,7 +877,7 @@ __device__ __forceinline__ void hs_sigmakin_body(const SigArgs& a, const Couplin
         for (int t = grp.j; t < n; t += grp.tpg) {
           const int ii = hs_item_of<L>(t, grp.nev), e = grp.ev0 + t - ii * grp.nev;
           const HsItem it = items[i0 + ii];
-          hs_item<P, R>(it, Slots<R, P::HS_NSLOT>{curs + e * CUR_EV}, Kall + e * P::NMOM * 4, prall + e * P::NPROP,
+          hs_item<P, R>(it, Slots<R, P::HS_NSLOT>{curs + e * CUR_EV}, Kall + e * L::KEV, prall + e * P::NPROP,
                         cp);
         }
         if (l == P::HS_NLEVEL - 1) {
@@ -903,7 +909,7 @@ __device__ __forceinline__ void hs_sigmakin_body(const SigArgs& a, const Couplin
           const int ii = hs_item_of<L>(t, grp.nev), ex = grp.ev0 + t - ii * grp.nev;
           const HsItem it = items[i0 + ii];
           hs_xitem<P, R>(it, Slots<R, P::HS_NSLOT>{curs + ex * CUR_EV}, Slots<R, P::HS_XCAP>{xb + ex * X_EV},
-                         Kall + ex * P::NMOM * 4, cp);
+                         Kall + ex * L::KEV, cp);
         }
       }
       if (c > 0) {
