@@ -300,9 +300,9 @@ __global__ void __launch_bounds__(HsGradCfg<P, R>::NT) sigmakin_hs_grad_kernel(G
 #pragma unroll
   for (int l = 1; l < P::HS_NLEVEL; ++l) {
     const int i0 = P::hs_level(l), ni = P::hs_level(l + 1) - i0, n = ni * nev;
-    for (int t = tid; t < n; t += NT) {
-      const int e = t / ni;
-      const HsItem it = items[i0 + t - e * ni];
+    for (int t = tid; t < n; t += NT) {  // item-major lanes, as the forward kernel
+      const int ii = hs_item_of<L>(t, nev), e = t - ii * nev;
+      const HsItem it = items[i0 + ii];
       hs_item<P, R>(it, Slots<R, P::HS_NSLOT>{curs + e * CUR_EV}, Kall + e * P::NMOM * 4, prall + e * P::NPROP, cp);
     }
     __syncthreads();
@@ -310,8 +310,8 @@ __global__ void __launch_bounds__(HsGradCfg<P, R>::NT) sigmakin_hs_grad_kernel(G
   {
     const int i0 = P::hs_xitem(0), ni = P::hs_xitem(1) - i0, n = ni * nev;
     for (int t = tid; t < n; t += NT) {
-      const int e = t / ni;
-      const HsItem it = items[i0 + t - e * ni];
+      const int ii = hs_item_of<L>(t, nev), e = t - ii * nev;
+      const HsItem it = items[i0 + ii];
       hs_xitem<P, R>(it, Slots<R, P::HS_NSLOT>{curs + e * CUR_EV}, Slots<R, P::HS_XCAP>{xbufs + e * X_EV},
                      Kall + e * P::NMOM * 4, cp);
     }
