@@ -86,9 +86,9 @@ struct HsLayout {
   static constexpr size_t o_m2 = align_up(o_pr + 2 * sizeof(R) * EVCAP * P::NPROP, 16);
   // variant of a leg set for a helicity: vt[S * NHEL + ihel]
   static constexpr size_t o_vt = align_up(o_m2 + 8 * NT, 16);
-  static constexpr size_t o_B = align_up(o_vt + (size_t(1) << P::NPAR) * P::NHEL, 1024);
-  static constexpr size_t o_U = align_up(o_B + (TC ? NP * KP * 2 : 0), 1024);
-  // union: current variants + amputated chunk (phases 2-3), then the tensor-core A tiles (phase 4).
+  static constexpr size_t o_U = align_up(o_vt + (size_t(1) << P::NPAR) * P::NHEL, 1024);
+  // union: current variants + amputated chunk (phases 2-3), then the tensor-core
+  // A tiles and, after them, the colour matrix as the B operand (phase 4).
   // Per-event strides in 16-byte words, padded so that one slot of the CTA's
   // events falls in different bank groups: the lanes of a warp take an item
   // for several events at once (the plane stride, a multiple of 8 words for
@@ -102,7 +102,10 @@ struct HsLayout {
   static constexpr size_t tileA = 128 * KP * 2;
   static constexpr size_t u_bytes = 16 * size_t(EVCAP) * (CUR_EV + P::HS_XBUFS * X_EV);
   static constexpr size_t a_bytes = TC ? 3 * MBLK * tileA : 0;  // one component's three splits
-  static constexpr size_t bytes = o_U + (u_bytes > a_bytes ? u_bytes : a_bytes);
+  static constexpr size_t o_B = o_U + a_bytes;  // copied in for every group's colour sum
+  static constexpr size_t b_bytes = TC ? size_t(NP) * KP * 2 : 0;
+  static constexpr size_t bytes = o_U + (u_bytes > a_bytes + b_bytes ? u_bytes : a_bytes + b_bytes);
+  static_assert(o_B % 1024 == 0, "B operand on a 1024-byte boundary");
   static constexpr uint32_t TMEM_COLS = tc::tmem_cols(MBLK * 2 * NP);
   static_assert(!TC || NT % 128 == 0, "CTA rows must fill 128-row MMA blocks");
   static_assert(TMEM_COLS <= 512, "TMEM holds 512 columns");
@@ -120,6 +123,11 @@ __device__ __forceinline__ float colour_sum_tc_regs(unsigned char* smem, const c
   const int tid = threadIdx.x;
   const int b = tid >> 7, r = tid & 127;
   bool ok = true;
+  {  // the colour matrix (BF16 B operand) into the union, free from here on
+    const uint4* src = reinterpret_cast<const uint4*>(P::colour_bf16_image());
+    uint4* dst = reinterpret_cast<uint4*>(smem + L::o_B);
+    for (int i = tid; i < (int)(L::b_bytes / 16); i += L::NT) dst[i] = src[i];
+  }
 #pragma unroll
   for (int c = 0; c < 2; ++c) {
     if (c == 1) {
@@ -806,9 +814,6 @@ __device__ __forceinline__ void hs_sigmakin_body(const SigArgs& a, const Couplin
     if (tid < 32) tc::tmem_alloc(tc::smem_addr(misc + 1), L::TMEM_COLS);
     mbar = tc::smem_addr(misc + 4);
     if (tid == 0) tc::mbar_init(mbar, 1);
-    const uint4* src = reinterpret_cast<const uint4*>(P::colour_bf16_image());
-    uint4* dst = reinterpret_cast<uint4*>(smem + L::o_B);
-    for (int i = tid; i < C::NP * C::KP * 2 / 16; i += NT) dst[i] = src[i];
     tc::fence_async_shared();
     tc::fence_before_sync();
   }
