@@ -69,7 +69,13 @@ struct HsGradLayout {
   static constexpr size_t o_curb = o_cur + W * EVCAP * P::HS_NSLOT;
   static constexpr size_t o_x = o_curb + W * EVCAP * P::HS_NSLOT;
   static constexpr size_t o_xb = o_x + W * EVCAP * P::HS_XCAP;
-  static constexpr size_t bytes = o_xb + W * EVCAP * P::HS_XCAP;
+  // staging of the item adjoints' group sums, one W4 per thread: the forward
+  // amputated currents' storage (dead once the contraction adjoints are done)
+  // when it is large enough, else its own region
+  static constexpr size_t stage_bytes = W * NT;
+  static constexpr bool STAGE_IN_X = W * EVCAP * P::HS_XCAP >= stage_bytes;
+  static constexpr size_t o_stage = STAGE_IN_X ? o_x : o_xb + W * EVCAP * P::HS_XCAP;
+  static constexpr size_t bytes = STAGE_IN_X ? o_xb + W * EVCAP * P::HS_XCAP : o_stage + stage_bytes;
   static_assert(bytes <= 232448, "shared memory per CTA above the 227 KB limit");
 };
 
@@ -85,36 +91,53 @@ __device__ __forceinline__ void atomic_addc(cx<R>* d, cx<R> v) {
 }
 
 // Warp-aggregated adds for the item adjoints: the lanes of a warp that add into
-// the same destination (same key: its shared-memory address) first sum their
-// values with shuffles, and only the lowest lane of each such group adds the
-// sum, so no two lanes of a warp write one address.  The
-// lanes taking part are the ones executing together (__activemask), and every
-// collective below runs on all of them.
+// the same destination (same key: its shared-memory address) form a group, and
+// only the lowest lane of each group adds, the group's values summed in lane
+// order (its own first), so no two lanes of a warp write one address.  The
+// values pass through the warp's staging area in shared memory (32 lanes x NV,
+// at most 8 values of R per lane): every lane stores its values and each
+// leader reads its members' (a group of n lanes costs its leader n - 1 reads,
+// not n - 1 rounds of warp-wide shuffles).  The lanes taking part are the ones
+// executing together (__activemask), and every collective below runs on all
+// of them.
 template <int NV, class R>
-__device__ __forceinline__ bool warp_group_sum(unsigned key, R* v) {
+__device__ __forceinline__ bool warp_group_sum(unsigned key, R* v, R* stage) {
+  static_assert(NV <= 8, "staging holds 8 values per lane");
   const unsigned act = __activemask();
   const int lane = threadIdx.x & 31;
   const unsigned g = __match_any_sync(act, key);
+  if (!__any_sync(act, g != (1u << lane))) return true;  // every lane alone: no sums
+  R* mine = stage + 8 * lane;
+  if constexpr ((NV * sizeof(R)) % 16 == 0) {
+#pragma unroll
+    for (int i = 0; i < (int)(NV * sizeof(R) / 16); ++i)
+      reinterpret_cast<uint4*>(mine)[i] = reinterpret_cast<const uint4*>(v)[i];
+  } else {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) mine[i] = v[i];
+  }
+  __syncwarp(act);
   const bool leader = lane == __ffs(g) - 1;
-  const int nmax = __reduce_max_sync(act, (unsigned)__popc(g));
-  unsigned others = leader ? g & ~(1u << lane) : 0u;
-  R s[NV];
-#pragma unroll
-  for (int i = 0; i < NV; ++i) s[i] = v[i];
-  for (int j = 1; j < nmax; ++j) {
-    int src = lane;
-    if (others) {
-      src = __ffs(others) - 1;
+  if (leader) {
+    unsigned others = g & ~(1u << lane);
+    while (others) {
+      const int src = __ffs(others) - 1;
       others &= others - 1;
-    }
+      const R* o = stage + 8 * src;
+      if constexpr ((NV * sizeof(R)) % 16 == 0) {
+        R t[NV];
 #pragma unroll
-    for (int i = 0; i < NV; ++i) {
-      const R x = __shfl_sync(act, v[i], src);
-      if (src != lane) s[i] += x;
+        for (int i = 0; i < (int)(NV * sizeof(R) / 16); ++i)
+          reinterpret_cast<uint4*>(t)[i] = reinterpret_cast<const uint4*>(o)[i];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) v[i] += t[i];
+      } else {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) v[i] += o[i];
+      }
     }
   }
-#pragma unroll
-  for (int i = 0; i < NV; ++i) v[i] = s[i];
+  __syncwarp(act);
   return leader;
 }
 __device__ __forceinline__ unsigned smem_key(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -124,27 +147,27 @@ __device__ __forceinline__ unsigned smem_key(const void* p) { return (unsigned)_
 // the group sum with a plain read-modify-write; the caller separates rounds of
 // items with __syncwarp.
 template <class R>
-__device__ __forceinline__ void own_add4(R* d, const R* v) {
-  R t[4] = {v[0], v[1], v[2], v[3]};
-  if (warp_group_sum<4>(smem_key(d), t)) {
+__device__ __forceinline__ void own_add4(R* d, const R* v, R* stage) {
+  alignas(16) R t[4] = {v[0], v[1], v[2], v[3]};
+  if (warp_group_sum<4>(smem_key(d), t, stage)) {
 #pragma unroll
     for (int mu = 0; mu < 4; ++mu) d[mu] += t[mu];
   }
 }
 template <class R>
-__device__ __forceinline__ void own_addc(cx<R>* d, cx<R> v) {
-  R t[2] = {v.re, v.im};
-  if (warp_group_sum<2>(smem_key(d), t)) *d = cx<R>(d->re + t[0], d->im + t[1]);
+__device__ __forceinline__ void own_addc(cx<R>* d, cx<R> v, R* stage) {
+  alignas(16) R t[2] = {v.re, v.im};
+  if (warp_group_sum<2>(smem_key(d), t, stage)) *d = cx<R>(d->re + t[0], d->im + t[1]);
 }
 template <class R, int N>
-__device__ __forceinline__ void own_slot_add(const Slots<R, N>& s, int i, const W4<R>& w) {
-  R t[8];
+__device__ __forceinline__ void own_slot_add(const Slots<R, N>& s, int i, const W4<R>& w, R* stage) {
+  alignas(16) R t[8];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     t[2 * k] = w.w[k].re;
     t[2 * k + 1] = w.w[k].im;
   }
-  if (warp_group_sum<8>(smem_key(s.p + i), t)) {
+  if (warp_group_sum<8>(smem_key(s.p + i), t, stage)) {
     W4<R> o = s[i];
 #pragma unroll
     for (int k = 0; k < 4; ++k) o.w[k] = cx<R>(o.w[k].re + t[2 * k], o.w[k].im + t[2 * k + 1]);
@@ -156,7 +179,7 @@ __device__ __forceinline__ void own_slot_add(const Slots<R, N>& s, int i, const 
 template <class P, class R>
 __device__ __forceinline__ void hs_item_adj(const HsItem& it, const Slots<R, P::HS_NSLOT>& cur,
                                             const Slots<R, P::HS_NSLOT>& curb, const R* K, R* Kb, const cx<R>* pr,
-                                            cx<R>* prb, const Couplings<R>& cp) {
+                                            cx<R>* prb, const Couplings<R>& cp, R* stage) {
   const W4<R> ob = curb[it.out];
   W4<R> b[3];
 #pragma unroll
@@ -189,17 +212,17 @@ __device__ __forceinline__ void hs_item_adj(const HsItem& it, const Slots<R, P::
   }
 #pragma unroll
   for (int k = 0; k < 3; ++k)
-    if (k < nin) own_slot_add(curb, it.in[k], b[k]);
-  if (nk >= 1) own_add4(Kb + 4 * it.k0, kb0);
-  if (nk >= 2) own_add4(Kb + 4 * it.k1, kb1);
-  own_addc(prb + it.prop, pb);
+    if (k < nin) own_slot_add(curb, it.in[k], b[k], stage);
+  if (nk >= 1) own_add4(Kb + 4 * it.k0, kb0, stage);
+  if (nk >= 2) own_add4(Kb + 4 * it.k1, kb1, stage);
+  own_addc(prb + it.prop, pb, stage);
 }
 
 // adjoint of one amputated-current variant
 template <class P, class R>
 __device__ __forceinline__ void hs_xitem_adj(const HsItem& it, const Slots<R, P::HS_NSLOT>& cur,
                                              const Slots<R, P::HS_NSLOT>& curb, const Slots<R, P::HS_XCAP>& xbb,
-                                             const R* K, R* Kb, const Couplings<R>& cp) {
+                                             const R* K, R* Kb, const Couplings<R>& cp, R* stage) {
   const W4<R> ob = xbb[it.out];
   W4<R> b[3];
 #pragma unroll
@@ -223,10 +246,10 @@ __device__ __forceinline__ void hs_xitem_adj(const HsItem& it, const Slots<R, P:
   }
 #pragma unroll
   for (int k = 0; k < 3; ++k)
-    if (k < nin) own_slot_add(curb, it.in[k], b[k]);
+    if (k < nin) own_slot_add(curb, it.in[k], b[k], stage);
   if (mom) {
-    own_add4(Kb + 4 * it.k0, kb0);
-    own_add4(Kb + 4 * it.k1, kb1);
+    own_add4(Kb + 4 * it.k0, kb0, stage);
+    own_add4(Kb + 4 * it.k1, kb1, stage);
   }
 }
 
@@ -352,6 +375,7 @@ __global__ void __launch_bounds__(HsGradCfg<P, R>::NT) sigmakin_hs_grad_kernel(G
   //    one writing warp (plain adds, rounds of 32 items separated by __syncwarp)
   const int warp = tid >> 5, lane = tid & 31;
   constexpr int NW = NT / 32;
+  R* const wstage = reinterpret_cast<R*>(smem + L::o_stage) + warp * 32 * 8;  // the warp's group-sum staging
   {
     const int i0 = P::hs_xitem(0), ni = P::hs_xitem(1) - i0;
     for (int ex = warp; ex < nev; ex += NW) {
@@ -360,7 +384,7 @@ __global__ void __launch_bounds__(HsGradCfg<P, R>::NT) sigmakin_hs_grad_kernel(G
           const HsItem it = items[i0 + r0 + lane];
           hs_xitem_adj<P, R>(it, Slots<R, P::HS_NSLOT>{curs + ex * CUR_EV},
                              Slots<R, P::HS_NSLOT>{cursb + ex * CUR_EV}, Slots<R, P::HS_XCAP>{xbufsb + ex * X_EV},
-                             Kall + ex * P::NMOM * 4, Kball + ex * P::NMOM * 4, cp);
+                             Kall + ex * P::NMOM * 4, Kball + ex * P::NMOM * 4, cp, wstage);
         }
         __syncwarp();
       }
@@ -376,7 +400,7 @@ __global__ void __launch_bounds__(HsGradCfg<P, R>::NT) sigmakin_hs_grad_kernel(G
           const HsItem it = items[i0 + r0 + lane];
           hs_item_adj<P, R>(it, Slots<R, P::HS_NSLOT>{curs + ex * CUR_EV}, Slots<R, P::HS_NSLOT>{cursb + ex * CUR_EV},
                             Kall + ex * P::NMOM * 4, Kball + ex * P::NMOM * 4, prall + ex * P::NPROP,
-                            prball + ex * P::NPROP, cp);
+                            prball + ex * P::NPROP, cp, wstage);
         }
         __syncwarp();
       }
