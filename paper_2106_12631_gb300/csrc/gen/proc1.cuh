@@ -63,7 +63,9 @@ struct Proc1 {
   // adjoint of hs_contract: Jb -> atomic adds into curb (operands) and xbb (amputated);
   // full = the warp's lanes are consecutive helicities of its event(s), all good;
   // act = this lane has an (event, helicity) (lanes without one add zeros)
-  template <class R, class CUR, class XB>
+  // PASS bit 0: the operand adjoints Yb (read X); bit 1: the amputated-current
+  // adjoints Xb (read Y), so that Xb can overwrite X in a second pass
+  template <int PASS, class R, class CUR, class XB>
   static __device__ __forceinline__ void hs_contract_adj(int c, const CUR& cur, const XB& xb, const uint8_t* __restrict__ vt, const cx<R>* Jb, const CUR& curb, const XB& xbb, bool full, int lane, bool act) {
     switch (c) {
       case 0: {
@@ -75,18 +77,22 @@ struct Proc1 {
             const int vy = vt[48];
             W4<R> Y = cur[8 + vy];
             const cx<R> ab = Jb[0];
-            w4_acc_conj(Xb, Y, ab);
-            const W4<R> Yb = w4_conj_scale(X, ab);
-            if (full) {
-              w4_warp_reduce_add<3u, false>(Yb, curb, 8 + vy, lane, act);
-            } else {
-              curb.atomic_add(8 + vy, Yb);
+            if constexpr ((PASS & 2) != 0) w4_acc_conj(Xb, Y, ab);
+            if constexpr ((PASS & 1) != 0) {
+              const W4<R> Yb = w4_conj_scale(X, ab);
+              if (full) {
+                w4_warp_reduce_add<3u, false>(Yb, curb, 8 + vy, lane, act);
+              } else {
+                curb.atomic_add(8 + vy, Yb);
+              }
             }
           }
-          if (full) {
-            w4_warp_reduce_add<12u, false>(Xb, xbb, 0 + vx, lane, act);
-          } else {
-            xbb.atomic_add(0 + vx, Xb);
+          if constexpr ((PASS & 2) != 0) {
+            if (full) {
+              w4_warp_reduce_add<12u, false>(Xb, xbb, 0 + vx, lane, act);
+            } else {
+              xbb.atomic_add(0 + vx, Xb);
+            }
           }
         }
         {
@@ -97,18 +103,22 @@ struct Proc1 {
             const int vy = vt[48];
             W4<R> Y = cur[12 + vy];
             const cx<R> ab = Jb[0];
-            w4_acc_conj(Xb, Y, ab);
-            const W4<R> Yb = w4_conj_scale(X, ab);
-            if (full) {
-              w4_warp_reduce_add<3u, false>(Yb, curb, 12 + vy, lane, act);
-            } else {
-              curb.atomic_add(12 + vy, Yb);
+            if constexpr ((PASS & 2) != 0) w4_acc_conj(Xb, Y, ab);
+            if constexpr ((PASS & 1) != 0) {
+              const W4<R> Yb = w4_conj_scale(X, ab);
+              if (full) {
+                w4_warp_reduce_add<3u, false>(Yb, curb, 12 + vy, lane, act);
+              } else {
+                curb.atomic_add(12 + vy, Yb);
+              }
             }
           }
-          if (full) {
-            w4_warp_reduce_add<12u, false>(Xb, xbb, 4 + vx, lane, act);
-          } else {
-            xbb.atomic_add(4 + vx, Xb);
+          if constexpr ((PASS & 2) != 0) {
+            if (full) {
+              w4_warp_reduce_add<12u, false>(Xb, xbb, 4 + vx, lane, act);
+            } else {
+              xbb.atomic_add(4 + vx, Xb);
+            }
           }
         }
       } break;

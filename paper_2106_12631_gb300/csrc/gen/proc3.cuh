@@ -132,7 +132,9 @@ struct Proc3 {
   // adjoint of hs_contract: Jb -> atomic adds into curb (operands) and xbb (amputated);
   // full = the warp's lanes are consecutive helicities of its event(s), all good;
   // act = this lane has an (event, helicity) (lanes without one add zeros)
-  template <class R, class CUR, class XB>
+  // PASS bit 0: the operand adjoints Yb (read X); bit 1: the amputated-current
+  // adjoints Xb (read Y), so that Xb can overwrite X in a second pass
+  template <int PASS, class R, class CUR, class XB>
   static __device__ __forceinline__ void hs_contract_adj(int c, const CUR& cur, const XB& xb, const uint8_t* __restrict__ vt, const cx<R>* Jb, const CUR& curb, const XB& xbb, bool full, int lane, bool act) {
     switch (c) {
       case 0: {
@@ -144,18 +146,22 @@ struct Proc3 {
             const int vy = vt[640];
             W4<R> Y = cur[66 + vy];
             const cx<R> ab = Jb[4];
-            w4_acc_conj(Xb, Y, ab);
-            const W4<R> Yb = w4_conj_scale(X, ab);
-            if (full) {
-              w4_warp_reduce_add<26u, false>(Yb, curb, 66 + vy, lane, act);
-            } else {
-              curb.atomic_add(66 + vy, Yb);
+            if constexpr ((PASS & 2) != 0) w4_acc_conj(Xb, Y, ab);
+            if constexpr ((PASS & 1) != 0) {
+              const W4<R> Yb = w4_conj_scale(X, ab);
+              if (full) {
+                w4_warp_reduce_add<26u, false>(Yb, curb, 66 + vy, lane, act);
+              } else {
+                curb.atomic_add(66 + vy, Yb);
+              }
             }
           }
-          if (full) {
-            w4_warp_reduce_add<5u, false>(Xb, xbb, 0 + vx, lane, act);
-          } else {
-            xbb.atomic_add(0 + vx, Xb);
+          if constexpr ((PASS & 2) != 0) {
+            if (full) {
+              w4_warp_reduce_add<5u, false>(Xb, xbb, 0 + vx, lane, act);
+            } else {
+              xbb.atomic_add(0 + vx, Xb);
+            }
           }
         }
         {
@@ -166,18 +172,22 @@ struct Proc3 {
             const int vy = vt[640];
             W4<R> Y = cur[66 + vy];
             const cx<R> ab = Jb[5];
-            w4_acc_conj(Xb, Y, ab);
-            const W4<R> Yb = w4_conj_scale(X, ab);
-            if (full) {
-              w4_warp_reduce_add<26u, false>(Yb, curb, 66 + vy, lane, act);
-            } else {
-              curb.atomic_add(66 + vy, Yb);
+            if constexpr ((PASS & 2) != 0) w4_acc_conj(Xb, Y, ab);
+            if constexpr ((PASS & 1) != 0) {
+              const W4<R> Yb = w4_conj_scale(X, ab);
+              if (full) {
+                w4_warp_reduce_add<26u, false>(Yb, curb, 66 + vy, lane, act);
+              } else {
+                curb.atomic_add(66 + vy, Yb);
+              }
             }
           }
-          if (full) {
-            w4_warp_reduce_add<5u, false>(Xb, xbb, 8 + vx, lane, act);
-          } else {
-            xbb.atomic_add(8 + vx, Xb);
+          if constexpr ((PASS & 2) != 0) {
+            if (full) {
+              w4_warp_reduce_add<5u, false>(Xb, xbb, 8 + vx, lane, act);
+            } else {
+              xbb.atomic_add(8 + vx, Xb);
+            }
           }
         }
         {
@@ -188,18 +198,22 @@ struct Proc3 {
             const int vy = vt[640];
             W4<R> Y = cur[66 + vy];
             const cx<R> ab = mul_i(Jb[4]) + mul_mi(Jb[5]);
-            w4_acc_conj(Xb, Y, ab);
-            const W4<R> Yb = w4_conj_scale(X, ab);
-            if (full) {
-              w4_warp_reduce_add<26u, false>(Yb, curb, 66 + vy, lane, act);
-            } else {
-              curb.atomic_add(66 + vy, Yb);
+            if constexpr ((PASS & 2) != 0) w4_acc_conj(Xb, Y, ab);
+            if constexpr ((PASS & 1) != 0) {
+              const W4<R> Yb = w4_conj_scale(X, ab);
+              if (full) {
+                w4_warp_reduce_add<26u, false>(Yb, curb, 66 + vy, lane, act);
+              } else {
+                curb.atomic_add(66 + vy, Yb);
+              }
             }
           }
-          if (full) {
-            w4_warp_reduce_add<5u, false>(Xb, xbb, 16 + vx, lane, act);
-          } else {
-            xbb.atomic_add(16 + vx, Xb);
+          if constexpr ((PASS & 2) != 0) {
+            if (full) {
+              w4_warp_reduce_add<5u, false>(Xb, xbb, 16 + vx, lane, act);
+            } else {
+              xbb.atomic_add(16 + vx, Xb);
+            }
           }
         }
         {
@@ -210,18 +224,22 @@ struct Proc3 {
             const int vy = vt[192];
             W4<R> Y = cur[62 + vy];
             const cx<R> ab = Jb[2];
-            w4_acc_conj(Xb, Y, ab);
-            const W4<R> Yb = w4_conj_scale(X, ab);
-            if (full) {
-              w4_warp_reduce_add<19u, false>(Yb, curb, 62 + vy, lane, act);
-            } else {
-              curb.atomic_add(62 + vy, Yb);
+            if constexpr ((PASS & 2) != 0) w4_acc_conj(Xb, Y, ab);
+            if constexpr ((PASS & 1) != 0) {
+              const W4<R> Yb = w4_conj_scale(X, ab);
+              if (full) {
+                w4_warp_reduce_add<19u, false>(Yb, curb, 62 + vy, lane, act);
+              } else {
+                curb.atomic_add(62 + vy, Yb);
+              }
             }
           }
-          if (full) {
-            w4_warp_reduce_add<12u, false>(Xb, xbb, 24 + vx, lane, act);
-          } else {
-            xbb.atomic_add(24 + vx, Xb);
+          if constexpr ((PASS & 2) != 0) {
+            if (full) {
+              w4_warp_reduce_add<12u, false>(Xb, xbb, 24 + vx, lane, act);
+            } else {
+              xbb.atomic_add(24 + vx, Xb);
+            }
           }
         }
         {
@@ -232,18 +250,22 @@ struct Proc3 {
             const int vy = vt[192];
             W4<R> Y = cur[62 + vy];
             const cx<R> ab = mul_i(Jb[2]) + mul_mi(Jb[3]);
-            w4_acc_conj(Xb, Y, ab);
-            const W4<R> Yb = w4_conj_scale(X, ab);
-            if (full) {
-              w4_warp_reduce_add<19u, false>(Yb, curb, 62 + vy, lane, act);
-            } else {
-              curb.atomic_add(62 + vy, Yb);
+            if constexpr ((PASS & 2) != 0) w4_acc_conj(Xb, Y, ab);
+            if constexpr ((PASS & 1) != 0) {
+              const W4<R> Yb = w4_conj_scale(X, ab);
+              if (full) {
+                w4_warp_reduce_add<19u, false>(Yb, curb, 62 + vy, lane, act);
+              } else {
+                curb.atomic_add(62 + vy, Yb);
+              }
             }
           }
-          if (full) {
-            w4_warp_reduce_add<12u, false>(Xb, xbb, 32 + vx, lane, act);
-          } else {
-            xbb.atomic_add(32 + vx, Xb);
+          if constexpr ((PASS & 2) != 0) {
+            if (full) {
+              w4_warp_reduce_add<12u, false>(Xb, xbb, 32 + vx, lane, act);
+            } else {
+              xbb.atomic_add(32 + vx, Xb);
+            }
           }
         }
         {
@@ -254,18 +276,22 @@ struct Proc3 {
             const int vy = vt[192];
             W4<R> Y = cur[62 + vy];
             const cx<R> ab = Jb[3];
-            w4_acc_conj(Xb, Y, ab);
-            const W4<R> Yb = w4_conj_scale(X, ab);
-            if (full) {
-              w4_warp_reduce_add<19u, false>(Yb, curb, 62 + vy, lane, act);
-            } else {
-              curb.atomic_add(62 + vy, Yb);
+            if constexpr ((PASS & 2) != 0) w4_acc_conj(Xb, Y, ab);
+            if constexpr ((PASS & 1) != 0) {
+              const W4<R> Yb = w4_conj_scale(X, ab);
+              if (full) {
+                w4_warp_reduce_add<19u, false>(Yb, curb, 62 + vy, lane, act);
+              } else {
+                curb.atomic_add(62 + vy, Yb);
+              }
             }
           }
-          if (full) {
-            w4_warp_reduce_add<12u, false>(Xb, xbb, 40 + vx, lane, act);
-          } else {
-            xbb.atomic_add(40 + vx, Xb);
+          if constexpr ((PASS & 2) != 0) {
+            if (full) {
+              w4_warp_reduce_add<12u, false>(Xb, xbb, 40 + vx, lane, act);
+            } else {
+              xbb.atomic_add(40 + vx, Xb);
+            }
           }
         }
         {
@@ -276,18 +302,22 @@ struct Proc3 {
             const int vy = vt[160];
             W4<R> Y = cur[58 + vy];
             const cx<R> ab = Jb[0];
-            w4_acc_conj(Xb, Y, ab);
-            const W4<R> Yb = w4_conj_scale(X, ab);
-            if (full) {
-              w4_warp_reduce_add<11u, false>(Yb, curb, 58 + vy, lane, act);
-            } else {
-              curb.atomic_add(58 + vy, Yb);
+            if constexpr ((PASS & 2) != 0) w4_acc_conj(Xb, Y, ab);
+            if constexpr ((PASS & 1) != 0) {
+              const W4<R> Yb = w4_conj_scale(X, ab);
+              if (full) {
+                w4_warp_reduce_add<11u, false>(Yb, curb, 58 + vy, lane, act);
+              } else {
+                curb.atomic_add(58 + vy, Yb);
+              }
             }
           }
-          if (full) {
-            w4_warp_reduce_add<20u, false>(Xb, xbb, 48 + vx, lane, act);
-          } else {
-            xbb.atomic_add(48 + vx, Xb);
+          if constexpr ((PASS & 2) != 0) {
+            if (full) {
+              w4_warp_reduce_add<20u, false>(Xb, xbb, 48 + vx, lane, act);
+            } else {
+              xbb.atomic_add(48 + vx, Xb);
+            }
           }
         }
         {
@@ -298,18 +328,22 @@ struct Proc3 {
             const int vy = vt[160];
             W4<R> Y = cur[58 + vy];
             const cx<R> ab = Jb[1];
-            w4_acc_conj(Xb, Y, ab);
-            const W4<R> Yb = w4_conj_scale(X, ab);
-            if (full) {
-              w4_warp_reduce_add<11u, false>(Yb, curb, 58 + vy, lane, act);
-            } else {
-              curb.atomic_add(58 + vy, Yb);
+            if constexpr ((PASS & 2) != 0) w4_acc_conj(Xb, Y, ab);
+            if constexpr ((PASS & 1) != 0) {
+              const W4<R> Yb = w4_conj_scale(X, ab);
+              if (full) {
+                w4_warp_reduce_add<11u, false>(Yb, curb, 58 + vy, lane, act);
+              } else {
+                curb.atomic_add(58 + vy, Yb);
+              }
             }
           }
-          if (full) {
-            w4_warp_reduce_add<20u, false>(Xb, xbb, 56 + vx, lane, act);
-          } else {
-            xbb.atomic_add(56 + vx, Xb);
+          if constexpr ((PASS & 2) != 0) {
+            if (full) {
+              w4_warp_reduce_add<20u, false>(Xb, xbb, 56 + vx, lane, act);
+            } else {
+              xbb.atomic_add(56 + vx, Xb);
+            }
           }
         }
         {
@@ -320,18 +354,22 @@ struct Proc3 {
             const int vy = vt[160];
             W4<R> Y = cur[58 + vy];
             const cx<R> ab = mul_i(Jb[0]) + mul_mi(Jb[1]);
-            w4_acc_conj(Xb, Y, ab);
-            const W4<R> Yb = w4_conj_scale(X, ab);
-            if (full) {
-              w4_warp_reduce_add<11u, false>(Yb, curb, 58 + vy, lane, act);
-            } else {
-              curb.atomic_add(58 + vy, Yb);
+            if constexpr ((PASS & 2) != 0) w4_acc_conj(Xb, Y, ab);
+            if constexpr ((PASS & 1) != 0) {
+              const W4<R> Yb = w4_conj_scale(X, ab);
+              if (full) {
+                w4_warp_reduce_add<11u, false>(Yb, curb, 58 + vy, lane, act);
+              } else {
+                curb.atomic_add(58 + vy, Yb);
+              }
             }
           }
-          if (full) {
-            w4_warp_reduce_add<20u, false>(Xb, xbb, 64 + vx, lane, act);
-          } else {
-            xbb.atomic_add(64 + vx, Xb);
+          if constexpr ((PASS & 2) != 0) {
+            if (full) {
+              w4_warp_reduce_add<20u, false>(Xb, xbb, 64 + vx, lane, act);
+            } else {
+              xbb.atomic_add(64 + vx, Xb);
+            }
           }
         }
         {
@@ -343,17 +381,19 @@ struct Proc3 {
             W4<R> Y = cur[34 + vy];
             Y = w4_add(Y, cur[78 + vy]);
             const cx<R> ab = -Jb[0] + Jb[2] + Jb[4] + -Jb[5];
-            w4_acc_conj(Xb, Y, ab);
-            const W4<R> Yb = w4_conj_scale(X, ab);
-            if (full) {
-              w4_warp_reduce_add<6u, false>(Yb, curb, 34 + vy, lane, act);
-            } else {
-              curb.atomic_add(34 + vy, Yb);
-            }
-            if (full) {
-              w4_warp_reduce_add<6u, false>(Yb, curb, 78 + vy, lane, act);
-            } else {
-              curb.atomic_add(78 + vy, Yb);
+            if constexpr ((PASS & 2) != 0) w4_acc_conj(Xb, Y, ab);
+            if constexpr ((PASS & 1) != 0) {
+              const W4<R> Yb = w4_conj_scale(X, ab);
+              if (full) {
+                w4_warp_reduce_add<6u, false>(Yb, curb, 34 + vy, lane, act);
+              } else {
+                curb.atomic_add(34 + vy, Yb);
+              }
+              if (full) {
+                w4_warp_reduce_add<6u, false>(Yb, curb, 78 + vy, lane, act);
+              } else {
+                curb.atomic_add(78 + vy, Yb);
+              }
             }
           }
           {
@@ -361,17 +401,19 @@ struct Proc3 {
             W4<R> Y = cur[42 + vy];
             Y = w4_add(Y, cur[86 + vy]);
             const cx<R> ab = -Jb[1] + Jb[2] + -Jb[3] + Jb[4];
-            w4_acc_conj(Xb, Y, ab);
-            const W4<R> Yb = w4_conj_scale(X, ab);
-            if (full) {
-              w4_warp_reduce_add<6u, false>(Yb, curb, 42 + vy, lane, act);
-            } else {
-              curb.atomic_add(42 + vy, Yb);
-            }
-            if (full) {
-              w4_warp_reduce_add<6u, false>(Yb, curb, 86 + vy, lane, act);
-            } else {
-              curb.atomic_add(86 + vy, Yb);
+            if constexpr ((PASS & 2) != 0) w4_acc_conj(Xb, Y, ab);
+            if constexpr ((PASS & 1) != 0) {
+              const W4<R> Yb = w4_conj_scale(X, ab);
+              if (full) {
+                w4_warp_reduce_add<6u, false>(Yb, curb, 42 + vy, lane, act);
+              } else {
+                curb.atomic_add(42 + vy, Yb);
+              }
+              if (full) {
+                w4_warp_reduce_add<6u, false>(Yb, curb, 86 + vy, lane, act);
+              } else {
+                curb.atomic_add(86 + vy, Yb);
+              }
             }
           }
           {
@@ -379,23 +421,27 @@ struct Proc3 {
             W4<R> Y = cur[50 + vy];
             Y = w4_sub(Y, cur[70 + vy]);
             const cx<R> ab = Jb[0] + -Jb[1] + -Jb[3] + Jb[5];
-            w4_acc_conj(Xb, Y, ab);
-            const W4<R> Yb = w4_conj_scale(X, ab);
-            if (full) {
-              w4_warp_reduce_add<6u, false>(Yb, curb, 50 + vy, lane, act);
-            } else {
-              curb.atomic_add(50 + vy, Yb);
-            }
-            if (full) {
-              w4_warp_reduce_add<6u, false>(w4_neg(Yb), curb, 70 + vy, lane, act);
-            } else {
-              curb.atomic_add(70 + vy, w4_neg(Yb));
+            if constexpr ((PASS & 2) != 0) w4_acc_conj(Xb, Y, ab);
+            if constexpr ((PASS & 1) != 0) {
+              const W4<R> Yb = w4_conj_scale(X, ab);
+              if (full) {
+                w4_warp_reduce_add<6u, false>(Yb, curb, 50 + vy, lane, act);
+              } else {
+                curb.atomic_add(50 + vy, Yb);
+              }
+              if (full) {
+                w4_warp_reduce_add<6u, false>(w4_neg(Yb), curb, 70 + vy, lane, act);
+              } else {
+                curb.atomic_add(70 + vy, w4_neg(Yb));
+              }
             }
           }
-          if (full) {
-            w4_warp_reduce_add<25u, false>(Xb, xbb, 72 + vx, lane, act);
-          } else {
-            xbb.atomic_add(72 + vx, Xb);
+          if constexpr ((PASS & 2) != 0) {
+            if (full) {
+              w4_warp_reduce_add<25u, false>(Xb, xbb, 72 + vx, lane, act);
+            } else {
+              xbb.atomic_add(72 + vx, Xb);
+            }
           }
         }
         {
@@ -406,18 +452,22 @@ struct Proc3 {
             const int vy = vt[768];
             W4<R> Y = cur[18 + vy];
             const cx<R> ab = mul_i(Jb[0]) + mul_mi(Jb[2]);
-            w4_acc_conj(Xb, Y, ab);
-            const W4<R> Yb = w4_conj_scale(X, ab);
-            if (full) {
-              w4_warp_reduce_add<28u, false>(Yb, curb, 18 + vy, lane, act);
-            } else {
-              curb.atomic_add(18 + vy, Yb);
+            if constexpr ((PASS & 2) != 0) w4_acc_conj(Xb, Y, ab);
+            if constexpr ((PASS & 1) != 0) {
+              const W4<R> Yb = w4_conj_scale(X, ab);
+              if (full) {
+                w4_warp_reduce_add<28u, false>(Yb, curb, 18 + vy, lane, act);
+              } else {
+                curb.atomic_add(18 + vy, Yb);
+              }
             }
           }
-          if (full) {
-            w4_warp_reduce_add<3u, false>(Xb, xbb, 76 + vx, lane, act);
-          } else {
-            xbb.atomic_add(76 + vx, Xb);
+          if constexpr ((PASS & 2) != 0) {
+            if (full) {
+              w4_warp_reduce_add<3u, false>(Xb, xbb, 76 + vx, lane, act);
+            } else {
+              xbb.atomic_add(76 + vx, Xb);
+            }
           }
         }
         {
@@ -428,18 +478,22 @@ struct Proc3 {
             const int vy = vt[320];
             W4<R> Y = cur[14 + vy];
             const cx<R> ab = mul_i(Jb[1]) + mul_mi(Jb[4]);
-            w4_acc_conj(Xb, Y, ab);
-            const W4<R> Yb = w4_conj_scale(X, ab);
-            if (full) {
-              w4_warp_reduce_add<21u, false>(Yb, curb, 14 + vy, lane, act);
-            } else {
-              curb.atomic_add(14 + vy, Yb);
+            if constexpr ((PASS & 2) != 0) w4_acc_conj(Xb, Y, ab);
+            if constexpr ((PASS & 1) != 0) {
+              const W4<R> Yb = w4_conj_scale(X, ab);
+              if (full) {
+                w4_warp_reduce_add<21u, false>(Yb, curb, 14 + vy, lane, act);
+              } else {
+                curb.atomic_add(14 + vy, Yb);
+              }
             }
           }
-          if (full) {
-            w4_warp_reduce_add<10u, false>(Xb, xbb, 84 + vx, lane, act);
-          } else {
-            xbb.atomic_add(84 + vx, Xb);
+          if constexpr ((PASS & 2) != 0) {
+            if (full) {
+              w4_warp_reduce_add<10u, false>(Xb, xbb, 84 + vx, lane, act);
+            } else {
+              xbb.atomic_add(84 + vx, Xb);
+            }
           }
         }
         {
@@ -450,18 +504,22 @@ struct Proc3 {
             const int vy = vt[288];
             W4<R> Y = cur[10 + vy];
             const cx<R> ab = mul_i(Jb[3]) + mul_mi(Jb[5]);
-            w4_acc_conj(Xb, Y, ab);
-            const W4<R> Yb = w4_conj_scale(X, ab);
-            if (full) {
-              w4_warp_reduce_add<13u, false>(Yb, curb, 10 + vy, lane, act);
-            } else {
-              curb.atomic_add(10 + vy, Yb);
+            if constexpr ((PASS & 2) != 0) w4_acc_conj(Xb, Y, ab);
+            if constexpr ((PASS & 1) != 0) {
+              const W4<R> Yb = w4_conj_scale(X, ab);
+              if (full) {
+                w4_warp_reduce_add<13u, false>(Yb, curb, 10 + vy, lane, act);
+              } else {
+                curb.atomic_add(10 + vy, Yb);
+              }
             }
           }
-          if (full) {
-            w4_warp_reduce_add<18u, false>(Xb, xbb, 92 + vx, lane, act);
-          } else {
-            xbb.atomic_add(92 + vx, Xb);
+          if constexpr ((PASS & 2) != 0) {
+            if (full) {
+              w4_warp_reduce_add<18u, false>(Xb, xbb, 92 + vx, lane, act);
+            } else {
+              xbb.atomic_add(92 + vx, Xb);
+            }
           }
         }
       } break;

@@ -67,15 +67,12 @@ struct HsGradLayout {
   static constexpr size_t o_vt = align_up(o_m2 + 8 * NT, 16);
   static constexpr size_t o_cur = align_up(o_vt + (size_t(1) << P::NPAR) * P::NHEL, 128);
   static constexpr size_t o_curb = o_cur + W * EVCAP * P::HS_NSLOT;
+  // the amputated currents X, then (second pass of the contraction adjoints)
+  // their adjoints Xb in the same storage
   static constexpr size_t o_x = o_curb + W * EVCAP * P::HS_NSLOT;
-  static constexpr size_t o_xb = o_x + W * EVCAP * P::HS_XCAP;
-  // staging of the item adjoints' group sums, one W4 per thread: the forward
-  // amputated currents' storage (dead once the contraction adjoints are done)
-  // when it is large enough, else its own region
-  static constexpr size_t stage_bytes = W * NT;
-  static constexpr bool STAGE_IN_X = W * EVCAP * P::HS_XCAP >= stage_bytes;
-  static constexpr size_t o_stage = STAGE_IN_X ? o_x : o_xb + W * EVCAP * P::HS_XCAP;
-  static constexpr size_t bytes = STAGE_IN_X ? o_xb + W * EVCAP * P::HS_XCAP : o_stage + stage_bytes;
+  // staging of the item adjoints' group sums, one W4 per thread
+  static constexpr size_t o_stage = o_x + W * EVCAP * P::HS_XCAP;
+  static constexpr size_t bytes = o_stage + W * NT;
   static_assert(bytes <= 232448, "shared memory per CTA above the 227 KB limit");
 };
 
@@ -271,7 +268,7 @@ __global__ void __launch_bounds__(HsGradCfg<P, R>::NT) sigmakin_hs_grad_kernel(G
   uint4* curs = reinterpret_cast<uint4*>(smem + L::o_cur);
   uint4* cursb = reinterpret_cast<uint4*>(smem + L::o_curb);
   uint4* xbufs = reinterpret_cast<uint4*>(smem + L::o_x);
-  uint4* xbufsb = reinterpret_cast<uint4*>(smem + L::o_xb);
+  uint4* xbufsb = xbufs;  // Xb overwrites X in the second contraction-adjoint pass
   const int tid = threadIdx.x;
   // 0. tables, zeroed adjoints
   hs_setup_words<P, R, L>(smem, a.pp);
@@ -283,8 +280,7 @@ __global__ void __launch_bounds__(HsGradCfg<P, R>::NT) sigmakin_hs_grad_kernel(G
     reinterpret_cast<uint4*>(vtab)[i] = reinterpret_cast<const uint4*>(P::hs_variants())[i];
   {
     const uint4 z = make_uint4(0, 0, 0, 0);
-    uint4* zb = cursb;  // curb, x (harmless), xb are one contiguous range from o_curb
-    for (int i = tid; i < (int)((L::bytes - L::o_curb) / 16); i += NT) zb[i] = z;
+    for (int i = tid; i < (int)((L::o_x - L::o_curb) / 16); i += NT) cursb[i] = z;
     for (int i = tid; i < (int)((L::o_pr - L::o_Kb) / 16); i += NT) reinterpret_cast<uint4*>(Kball)[i] = z;
     for (int i = tid; i < (int)((L::o_m2 - L::o_prb) / 16); i += NT) reinterpret_cast<uint4*>(prball)[i] = z;
     for (int i = tid; i < (int)((L::o_K - L::o_pb) / 16); i += NT) reinterpret_cast<uint4*>(&pbs[0][0][0])[i] = z;
@@ -367,7 +363,14 @@ __global__ void __launch_bounds__(HsGradCfg<P, R>::NT) sigmakin_hs_grad_kernel(G
     }
     // lanes = consecutive helicities of whole events when every helicity is good
     const bool full = ng == P::NHEL && (P::NHEL % 32 == 0 || 32 % P::NHEL == 0);
-    P::template hs_contract_adj<R>(0, cur, xb, vtab + ih, Jb, curb, xbb, full, tid & 31, active);
+    // two passes, so that Xb needs no storage of its own: the operand adjoints
+    // (they read X), then, with X dead and its storage zeroed, the amputated
+    // currents' adjoints into that storage (they read the operands Y)
+    P::template hs_contract_adj<1, R>(0, cur, xb, vtab + ih, Jb, curb, xbb, full, tid & 31, active);
+    __syncthreads();
+    for (int i = tid; i < L::EVCAP * X_EV; i += NT) xbufs[i] = make_uint4(0, 0, 0, 0);
+    __syncthreads();
+    P::template hs_contract_adj<2, R>(0, cur, xb, vtab + ih, Jb, curb, xbb, full, tid & 31, active);
   }
   __syncthreads();
   // 4. amputated currents, then the current levels in reverse; the items of

@@ -1448,10 +1448,16 @@ class SharedProgram:
                     "            %s.atomic_add(%s, %s);" % (target, slot, value),
                     "          }"]
 
+        def xb_add(xo, mask):
+            return (["          if constexpr ((PASS & 2) != 0) {"]
+                    + ["  " + ln for ln in add("xbb", "%d + vx" % xo, "Xb", mask)] + ["          }"])
+
         lines = ["  // adjoint of hs_contract: Jb -> atomic adds into curb (operands) and xbb (amputated);",
                  "  // full = the warp's lanes are consecutive helicities of its event(s), all good;",
                  "  // act = this lane has an (event, helicity) (lanes without one add zeros)",
-                 "  template <class R, class CUR, class XB>",
+                 "  // PASS bit 0: the operand adjoints Yb (read X); bit 1: the amputated-current",
+                 "  // adjoints Xb (read Y), so that Xb can overwrite X in a second pass",
+                 "  template <int PASS, class R, class CUR, class XB>",
                  "  static __device__ __forceinline__ void hs_contract_adj(int c, const CUR& cur, const XB& xb,"
                  " const uint8_t* __restrict__ vt, const cx<R>* Jb, const CUR& curb, const XB& xbb, bool full,"
                  " int lane, bool act) {",
@@ -1466,7 +1472,7 @@ class SharedProgram:
                 xlegs = set(l for l in range(self.n) if g["xset"] >> l & 1)
                 if g["xo"] != last_x:
                     if last_x is not None:
-                        lines += add("xbb", "%d + vx" % last_x, "Xb", last_mask)
+                        lines += xb_add(last_x, last_mask)
                         lines.append("        }")
                     lines.append("        {")
                     lines.append("          const int vx = vt[%d];" % (g["xset"] * nh))
@@ -1483,13 +1489,15 @@ class SharedProgram:
                 for (yo, r) in g["ys"][1:]:
                     lines.append("            Y = %s(Y, cur[%d + vy]);" % (acc[r], yo))
                 lines.append("            const cx<R> ab = %s;" % ab)
-                lines.append("            w4_acc_conj(Xb, Y, ab);")
-                lines.append("            const W4<R> Yb = w4_conj_scale(X, ab);")
+                lines.append("            if constexpr ((PASS & 2) != 0) w4_acc_conj(Xb, Y, ab);")
+                lines.append("            if constexpr ((PASS & 1) != 0) {")
+                lines.append("              const W4<R> Yb = w4_conj_scale(X, ab);")
                 for (yo, r) in g["ys"]:
-                    lines += ["  " + ln for ln in add("curb", "%d + vy" % yo, ph[r], lane_mask(xlegs))]
+                    lines += ["    " + ln for ln in add("curb", "%d + vy" % yo, ph[r], lane_mask(xlegs))]
+                lines.append("            }")
                 lines.append("          }")
             if last_x is not None:
-                lines += add("xbb", "%d + vx" % last_x, "Xb", last_mask)
+                lines += xb_add(last_x, last_mask)
                 lines.append("        }")
             lines.append("      } break;")
         lines += ["      default: break;", "    }", "  }"]
