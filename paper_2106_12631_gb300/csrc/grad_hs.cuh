@@ -63,8 +63,9 @@ struct HsGradLayout {
   static constexpr size_t o_Kb = align_up(o_K + sizeof(R) * EVCAP * P::NMOM * 4, 16);  // R [EV][NMOM][4]
   static constexpr size_t o_pr = align_up(o_Kb + sizeof(R) * EVCAP * P::NMOM * 4, 16);  // cx<R> [EV][NPROP]
   static constexpr size_t o_prb = align_up(o_pr + 2 * sizeof(R) * EVCAP * P::NPROP, 16);
-  static constexpr size_t o_m2 = align_up(o_prb + 2 * sizeof(R) * EVCAP * P::NPROP, 16);  // double [NT]
-  static constexpr size_t o_vt = align_up(o_m2 + 8 * NT, 16);
+  // R [NT]: each thread's |M_h|^2, formed in R (stored exactly; summed in FP64)
+  static constexpr size_t o_m2 = align_up(o_prb + 2 * sizeof(R) * EVCAP * P::NPROP, 16);
+  static constexpr size_t o_vt = align_up(o_m2 + sizeof(R) * NT, 16);
   static constexpr size_t o_cur = align_up(o_vt + (size_t(1) << P::NPAR) * P::NHEL, 128);
   static constexpr size_t o_curb = o_cur + W * EVCAP * P::HS_NSLOT;
   // the amputated currents X, then (second pass of the contraction adjoints)
@@ -258,7 +259,7 @@ __global__ void __launch_bounds__(HsGradCfg<P, R>::NT) sigmakin_hs_grad_kernel(G
   extern __shared__ __align__(1024) unsigned char smem[];
   int* good = reinterpret_cast<int*>(smem + L::o_good);
   int* misc = reinterpret_cast<int*>(smem + L::o_misc);
-  double* sm2 = reinterpret_cast<double*>(smem + L::o_m2);
+  R* sm2 = reinterpret_cast<R*>(smem + L::o_m2);
   uint8_t* vtab = reinterpret_cast<uint8_t*>(smem + L::o_vt);
   auto pbs = reinterpret_cast<double(*)[P::NPAR][4]>(smem + L::o_pb);
   R* Kall = reinterpret_cast<R*>(smem + L::o_K);
@@ -345,8 +346,8 @@ __global__ void __launch_bounds__(HsGradCfg<P, R>::NT) sigmakin_hs_grad_kernel(G
 #pragma unroll
   for (int s = 0; s < NC; ++s) J[s] = cx<R>(R(0), R(0));
   P::template hs_contract<R>(0, cur, xb, vtab + ih, J);
-  const double m2 = (double)colour_sum_sym<P, R>(J);
-  sm2[tid] = active ? m2 : 0.0;
+  const R m2 = colour_sum_sym<P, R>(J);
+  sm2[tid] = active ? m2 : R(0);
   // 3. colour-sum adjoint, adjoint contractions (every thread takes part: the
   //    warp sums before the atomic adds need whole warps; idle threads add 0)
   {
