@@ -8,8 +8,9 @@
 //   * every diagram's amplitude is formed at a vertex chosen by the generator,
 //     with one operand Y left out: A = sum_i X_i Y_i, where the amputated
 //     current X of the other operands is again shared across helicities;
-//   * currents, amputated currents and amplitudes are tables walked by short
-//     loops, so the program stays in the instruction cache.
+//   * currents and amputated currents are item tables walked by short loops
+//     (lanes take one item for each of the CTA's events); the contractions of
+//     a chunk's amplitudes are generated straight-line code.
 // CTA of NT threads = EV events x ngood helicities.  Phases:
 //   1. per-event momenta, momentum sums and FP64 propagator factors (as SIGMAKIN);
 //   2. current variants, level by level (a level only reads earlier levels);
