@@ -41,11 +41,11 @@ SM_MAX_MHZ = 2070.0
 # (dram__bytes_read.sum + dram__bytes_write.sum of one launch over 2^18 events,
 # scaled by events; it reads the momenta once and writes |M|^2), valid only
 # while the kernel sources are the ones captured.
-SIGMAKIN_TRAFFIC = {"bytes_per_event": 192.67, "sources_sha1": "428efe228f9c4311255d1b808f22b0e6b9376898"}
+SIGMAKIN_TRAFFIC = {"bytes_per_event": 192.69, "sources_sha1": "ceea71af37bc050e8c44025841035afdf399fe92"}
 # Tensor-pipe activity of the tcgen05 colour-sum variant from the same kind of
 # capture (sm__pipe_tensor_cycles_active, fraction of its peak), valid while
 # the kernel sources are the ones captured.
-TC_TENSOR_PIPE = {"frac": 0.0166, "sources_sha1": "428efe228f9c4311255d1b808f22b0e6b9376898"}
+TC_TENSOR_PIPE = {"frac": 0.0167, "sources_sha1": "ceea71af37bc050e8c44025841035afdf399fe92"}
 SIGMAKIN_SOURCES = ["paper_2106_12631_gb300/csrc/" + f for f in
                     ("sigmakin_hs.cuh", "sigmakin_launch.cuh", "sigmakin.cuh", "helas.cuh", "colour_tc.cuh",
                      "mg_types.cuh", "process.cuh", "gen/proc4.cuh")]
