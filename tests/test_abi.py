@@ -135,3 +135,69 @@ def test_generator_merged_contractions_keep_every_amplitude(pid):
         for yo, r in g["ys"]:
             remaining.remove((g["ch"], g["xo"], yo, sp._rotate(g["flows"], r)))
     assert remaining == []
+
+
+def shared_program(pid):
+    from paper_2106_12631_gb300.gen import procgen
+    proc = procgen.Process(procgen.PROCS[pid])
+    em = procgen.Emitter(proc)
+    for leg in range(proc.n):
+        em.momentum_phys(leg)
+    em.emit()
+    sp = procgen.SharedProgram(proc, em)
+    sp.emit_tables(pid)
+    return sp
+
+
+@pytest.mark.parametrize("pid", [1, 2, 3, 4])
+def test_generator_chunks_fill_whole_rounds(pid):
+    """Amputated-current chunks: every amputated current in exactly one chunk,
+    within the chunk capacity; with several chunks the capacity is a multiple
+    of the chunk quantum, and for gg -> t t~ g g all four chunks are full
+    (192 slots per event: three rounds of the 4-event, 256-thread CTA)."""
+    sp = shared_program(pid)
+    sizes = [sum(sp.nvar(X) for X in c) for c in sp.chunks]
+    assert sorted(X for c in sp.chunks for X in c) == sorted(sp.xoff)
+    assert max(sizes) <= sp.xcap
+    if len(sp.chunks) > 1:
+        assert sp.xcap % sp.CHUNK_QUANTUM == 0
+    if pid == 4:
+        assert sizes == [192] * 4
+
+
+@pytest.mark.parametrize("pid", [3, 4])
+def test_generator_four_gluon_items_three_operands(pid):
+    """A four-gluon item names its three distinct operand slots {X_0, X_1, W}
+    and the kernels form X_0 (X_1 . W) - X_1 (X_0 . W).  Against the two
+    products read off the vertex's pairings (each pairs the output with one
+    operand X_j and dots the other two: X_0 (Y_0 . Z_0) - X_1 (Y_1 . Z_1)),
+    evaluated on random complex vectors per slot: equal for every variant."""
+    from paper_2106_12631_gb300.gen import procgen
+    sp = shared_program(pid)
+    rng = np.random.default_rng(pid)
+    eta = np.array([1.0, -1.0, -1.0, -1.0])
+
+    def vdot(a, b):
+        return np.sum(eta * a * b)
+
+    n = 0
+    for d in list(sp.order) + list(sp.xoff):
+        if sp.kind(d) not in ("gggg", "agggg"):
+            continue
+        term, outpos, pos = sp._gggg_positions(d)
+        for v in range(sp.nvar(d)):
+            ins = sp._item(d, v)[6]
+            assert len(set(ins)) == 3
+            six = []
+            for (p0, p1), (p2, p3) in procgen.VVVV_PAIRS[term]:
+                if outpos in (p0, p1):
+                    x, y, z = (p1 if outpos == p0 else p0), p2, p3
+                else:
+                    x, y, z = (p3 if outpos == p2 else p2), p0, p1
+                six += [sp.offset[pos[q]] + sp.sub_variant(pos[q], d, v) for q in (x, y, z)]
+            V = {s: rng.normal(size=4) + 1j * rng.normal(size=4) for s in set(six) | set(ins)}
+            old = V[six[0]] * vdot(V[six[1]], V[six[2]]) - V[six[3]] * vdot(V[six[4]], V[six[5]])
+            new = V[ins[0]] * vdot(V[ins[1]], V[ins[2]]) - V[ins[1]] * vdot(V[ins[0]], V[ins[2]])
+            np.testing.assert_allclose(new, old, rtol=1e-12, atol=1e-12)
+            n += 1
+    assert n > 0
