@@ -56,3 +56,49 @@ def test_default_kernels_do_not_spill():
                 assert (stack, st, ld) == (0, 0, 0), (name, stack, st, ld)
                 checked += 1
     assert checked >= 6, checked
+
+
+LAYOUT_PROBE = r'''
+#include "sigmakin_hs.cuh"
+#include "gen/proc3.cuh"
+#include "gen/proc4.cuh"
+#include <cstdio>
+template <class P, class R, int CS> void show(const char* name) {
+  using L = mg::HsLayout<P, R, CS>;
+  std::printf("%s %zu %d\n", name, (size_t)L::bytes, mg::HsCfg<P, R>::CTAS);
+}
+int main() {
+  show<mg::Proc4, float, 0>("p4_simt");
+  show<mg::Proc4, float, 1>("p4_tc");
+  show<mg::Proc3, float, 0>("p3_simt");
+  return 0;
+}
+'''
+
+
+@pytest.mark.skipif(shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"),
+                    reason="nvcc not available")
+def test_layouts_admit_their_ctas_per_sm():
+    """The helicity-shared FP32 kernels are tuned for a fixed number of CTAs per
+    SM (two for gg -> t t~ g g, three for gg -> t t~ g): their shared memory
+    plus the 1 KB the GPU reserves per CTA must fit the SM's 228 KB that many
+    times, for the CUDA-core and the tcgen05 colour sum alike (a layout
+    1 KB too large halves the resident warps)."""
+    with tempfile.TemporaryDirectory() as d:
+        src, exe = os.path.join(d, "probe.cu"), os.path.join(d, "probe")
+        with open(src, "w") as f:
+            f.write(LAYOUT_PROBE)
+        r = subprocess.run([B.nvcc(), *B.ARCH, "-std=c++17", "--expt-relaxed-constexpr", "-I", B.CSRC,
+                            "-I", os.path.join(os.path.dirname(B.CSRC), "..", "include"), src, "-o", exe],
+                           capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr[-2000:]
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split("\n")
+    sm_bytes, reserved = 233472, 1024
+    seen = 0
+    for ln in out:
+        if not ln.strip():
+            continue
+        name, nbytes, ctas = ln.split()
+        assert (int(nbytes) + reserved) * int(ctas) <= sm_bytes, (name, nbytes, ctas)
+        seen += 1
+    assert seen == 3
