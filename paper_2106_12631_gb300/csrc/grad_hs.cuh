@@ -7,8 +7,10 @@
 //   2. tables, current variants, amputated currents, contractions, colour sum
 //      (as SIGMAKIN, one chunk of amputated currents);
 //   3. per (event, helicity): Jb = dL/dJ from the colour sum,
-//      Jb_s = (dL/dme) NORM 2 (C J)_s / CDEN, then the adjoint contractions add
-//      into the shared adjoint slots of the operands and amputated currents;
+//      Jb_s = (dL/dme) NORM 2 (C J)_s / CDEN, then the adjoint contractions in
+//      two passes: into the shared adjoint slots of the operands (they read
+//      the amputated currents X), then into the amputated currents' adjoints,
+//      which take X's storage (they read only the operands);
 //   4. the amputated currents' and currents' adjoints, level by level in
 //      reverse, into their inputs, the momentum table and the propagators;
 //   5. external wavefunctions (forward-mode momentum Jacobians) and the
@@ -18,9 +20,10 @@
 // does not consume get 0.  Many helicities share a variant: the adjoint
 // contractions sum them with warp shuffles (shared-memory atomics when the
 // helicities of an event do not fill whole warps); the item adjoints of an
-// event run on one warp, whose lanes with the same destination sum with
-// shuffles before one lane adds (no atomics); the external and propagator
-// adjoints add atomically, so the last bits of a result may vary between runs.
+// event run on one warp, whose lanes with the same destination sum through a
+// shared-memory staging area before one lane adds (no atomics); the external
+// and propagator adjoints add atomically, so the last bits of a result may
+// vary between runs.
 // Adjoint convention of helas_adj.cuh: zb = dL/dRe z + i dL/dIm z.
 #pragma once
 #include "grad.cuh"
